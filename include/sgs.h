@@ -1,0 +1,223 @@
+/*
+ * sgs.h -- C ABI of the B300 decoder for SpeedyGS-compressed 3D Gaussian Splatting scenes.
+ *
+ * A scene's bitstream holds a geometry stream (sparse-octree occupancy tokens, Sec. 3.4
+ * "Geometry Occupancy Coding") and an attribute stream (56 channels per Gaussian in Morton
+ * order, Sec. 3.4 "Autoregressive Attribute Coding"), coded either with channel-wise
+ * fixed-length codes (Sec. 3.4.1), channel-wise static-frequency rANS, or rANS driven by the
+ * local autoregressive context model (Sec. 3.4.2; groups of W Gaussians = rANS lanes).
+ * Decoding reproduces the quantized scene exactly; the coders change only the bytes.
+ *
+ * Conventions
+ *   - Every entry point returns an int status: SGS_OK (0) or a negative SGS_E_* code.
+ *     No C++ exception crosses this boundary.
+ *   - "device" pointers are CUDA device pointers on the context's device; "host" pointers are
+ *     ordinary host memory (pageable or pinned).
+ *   - The caller owns every input and output buffer.  The context owns its device scratch,
+ *     its status word and its internal streams.
+ *   - A context is not thread safe: use one per host thread or guard it.
+ *   - Decode entry points are asynchronous on the given stream; their device-side status
+ *     (corrupt stream, timed-out wait) is read with sgs_sync().
+ *
+ * Output layout (structure of arrays, rows in (Morton code, original index) order unless an
+ * out_index is given):
+ *   attr  float [56][n_rows]   channel c at attr + c * n_rows
+ *   pos   float [3][n_rows]    voxel centres coord * 2^-D + 2^-(D+1)
+ *   coord uint32 [3][n_rows]   voxel coordinates (optional)
+ * Channel order: 0..2 SH DC, 3..47 SH rest (3 + colour*15 + k-1), 48 opacity logit,
+ * 49..51 log-scale, 52..55 rotation.
+ */
+#ifndef SGS_H
+#define SGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SGS_OK 0
+#define SGS_E_INVALID -1      /* bad argument or malformed header                        */
+#define SGS_E_CORRUPT -2      /* bitstream failed validation or a rANS end check         */
+#define SGS_E_NOMEM -3        /* scratch too small, or an allocation failed             */
+#define SGS_E_CUDA -4         /* a CUDA call failed                                       */
+#define SGS_E_TIMEOUT -5      /* a bounded device-side wait gave up                       */
+#define SGS_E_UNSUPPORTED -6  /* feature not built                                        */
+
+#define SGS_MODE_FIXED 0      /* channel-wise fixed-length codes (Sec. 3.4.1)            */
+#define SGS_MODE_STATIC 1     /* channel-wise static-frequency rANS                       */
+#define SGS_MODE_LEARNED 2    /* rANS with the learned context model (Sec. 3.4.2)        */
+#define SGS_GEO_RAW 0         /* occupancy tokens stored as bytes                         */
+#define SGS_GEO_RANS 1        /* levels of >= 4096 nodes coded with per-level rANS tables */
+
+#define SGS_NCHAN 56
+#define SGS_MAX_DEPTH 21
+
+typedef struct sgs_ctx sgs_ctx;
+typedef void *sgs_stream; /* a cudaStream_t (0 = legacy default stream) */
+
+/* Header facts of a bitstream, filled by scene_query (host only, no device work). */
+typedef struct {
+    uint32_t mode, geo_mode;
+    uint32_t n_in;          /* Gaussians before pruning                                  */
+    uint32_t n_rows;        /* decoded Gaussians N' (rows of every output array)         */
+    uint32_t depth;         /* octree depth D                                            */
+    uint32_t n_leaves;      /* unique voxels U                                           */
+    uint32_t n_dup;         /* duplicate-count entries                                   */
+    uint32_t lanes;         /* attribute rANS lanes L (0 for fixed-length)              */
+    uint32_t geo_lanes;     /* geometry rANS lanes (0 if no level is coded)             */
+    uint32_t n_level[SGS_MAX_DEPTH + 1]; /* nodes per level 0..D-1, then U at [D]       */
+    uint64_t n_geo;         /* occupancy bytes (internal nodes)                          */
+    uint64_t n_geo_coded;   /* of which rANS coded                                       */
+    uint64_t off[11];       /* section offsets: levels, dup, chan, geo_raw, geo_tab,
+                               geo_grp, geo_pay, attr_tab, attr_grp, attr_pay, total   */
+    uint64_t total_len;     /* bitstream bytes                                           */
+    uint64_t scratch_bytes; /* device scratch scene_decode needs for this scene          */
+} sgs_scene_info;
+
+/* Caller-allocated device outputs of one scene (sizes from sgs_scene_info.n_rows). */
+typedef struct {
+    float *attr;              /* device [56][n_rows], required                             */
+    float *pos;               /* device [3][n_rows], required                              */
+    uint32_t *coord;          /* device [3][n_rows] or NULL                                */
+    const uint32_t *out_index;/* device [n_rows] or NULL: row r is written to column
+                                 out_index[r] (a permutation of 0..n_rows-1, caller-checked) */
+} sgs_scene_out;
+
+/* Encoder parameters. */
+typedef struct {
+    uint32_t mode;            /* SGS_MODE_*                                               */
+    uint32_t geo_mode;        /* SGS_GEO_*                                                */
+    uint32_t depth;           /* 1..21                                                    */
+    uint32_t lanes;           /* attribute rANS lanes (entropy-coded modes), >= 1          */
+    uint32_t geo_lanes;       /* geometry rANS lanes, 0 = about 512 tokens per lane        */
+    uint32_t bits[SGS_NCHAN]; /* fixed-length bit widths 1..16 (8 is forced for rANS modes)*/
+    const void *model;        /* learned mode: SGS_MODEL_BYTES of frozen model, else NULL  */
+} sgs_encode_params;
+
+#define SGS_MODEL_BYTES 36384
+
+/* Training parameters of the context model (the learned part, Sec. 3.4.2). */
+typedef struct {
+    uint32_t steps;           /* Adam steps (2000 in the 1M-Gaussian workload)            */
+    uint32_t batch;           /* tokens per step (65536), <= 2^20                          */
+    uint32_t seed;            /* batch sampler seed (splitmix64 counter stream)            */
+    float lr;                 /* Adam learning rate (1e-3)                                 */
+} sgs_train_params;
+
+/* Float weights of the context model, all fp32, row-major:
+ *   emb[56][16], w1[64][20], b1[64], w2[64][64], b2[64], w3[256][64], b3[256].             */
+#define SGS_WEIGHTS_FLOATS (56 * 16 + 64 * 20 + 64 + 64 * 64 + 64 + 256 * 64 + 256)
+
+/* ------------------------------------------------------------------ context */
+
+/* Text of a status code (static storage). */
+const char *sgs_strerror(int code);
+
+/* Creates a context on CUDA device `device` owning `scratch_bytes` of device scratch
+ * (grown on demand by sgs_reserve, never inside a decode call).  *out is NULL on failure.
+ * Errors: SGS_E_INVALID (bad device), SGS_E_NOMEM, SGS_E_CUDA.                            */
+int sgs_create(sgs_ctx **out, int device, size_t scratch_bytes);
+
+/* Grows the context's scratch to at least `scratch_bytes` (synchronizes the device). */
+int sgs_reserve(sgs_ctx *ctx, size_t scratch_bytes);
+
+void sgs_destroy(sgs_ctx *ctx);
+
+/* Waits for `stream` and returns the worst device-side status recorded by decode calls on
+ * this context since the last sgs_sync (then clears it).  Returns SGS_E_CORRUPT,
+ * SGS_E_TIMEOUT, SGS_E_CUDA or SGS_OK.                                                      */
+int sgs_sync(sgs_ctx *ctx, sgs_stream stream);
+
+/* Enables (1) or disables (0) stage timing: decode calls then record CUDA events on their
+ * stream between the geometry-token, octree and attribute stages. */
+int sgs_profile(sgs_ctx *ctx, int enable);
+
+/* Stage times in ms of the most recent profiled single-scene decode (after the stream has
+ * completed it): ms[0] geometry tokens (table expansion, raw copy, rANS), ms[1] octree
+ * expansion and positions, ms[2] attribute decode and dequantization.  cap >= 3.
+ * Errors: SGS_E_INVALID (no profiled decode), SGS_E_CUDA.                                  */
+int sgs_profile_read(sgs_ctx *ctx, float *ms, int cap);
+
+/* Number of CUDA kernels enqueued by decode calls on this context since its creation. */
+uint64_t sgs_launch_count(sgs_ctx *ctx);
+
+/* ------------------------------------------------------------------ decode */
+
+/* Parses and validates the header of a bitstream (host bytes `bits`, `len` bytes, at least
+ * the header and the level table; the section offsets are checked against total_len).
+ * Definition of the fields: Sec. 3.4 split into geometry and attribute streams.
+ * Errors: SGS_E_INVALID (short buffer, bad magic/version/sizes/offsets).                   */
+int scene_query(const uint8_t *bits, size_t len, sgs_scene_info *info);
+
+/* Decodes one scene: occupancy tokens -> octree expansion (Sec. 3.4, Geometry Occupancy
+ * Coding) -> positions; attribute tokens (fixed-length unpack, static rANS or learned
+ * rANS, Sec. 3.4.1-3.4.2) -> dequantization v = fl(fl(q*step) + offset) into `out`.
+ * bits_dev: device copy of the whole bitstream (16-byte aligned), info from scene_query on
+ * the same bytes.  Asynchronous on `stream`; uses only the context's scratch.
+ * Errors: SGS_E_INVALID (NULL output, misaligned input), SGS_E_NOMEM (scratch smaller than
+ * info->scratch_bytes; nothing is launched), SGS_E_CUDA (launch failure).  Device-side
+ * corruption is reported by sgs_sync.                                                       */
+int scene_decode(sgs_ctx *ctx, const uint8_t *bits_dev, const sgs_scene_info *info,
+                 const sgs_scene_out *out, sgs_stream stream);
+
+/* One batch item for scene_decode_batch. */
+typedef struct {
+    const uint8_t *bits_dev;
+    sgs_scene_info info;
+    sgs_scene_out out;
+} sgs_batch_item;
+
+/* Decodes n scenes of any modes and sizes with one launch per pipeline stage covering all
+ * scenes (a work list over every scene's lanes, groups and octree tiles).  Scratch need =
+ * the sum over items of info.scratch_bytes.  Same errors as scene_decode.                  */
+int scene_decode_batch(sgs_ctx *ctx, const sgs_batch_item *items, int n, sgs_stream stream);
+
+/* ------------------------------------------------------------------ encode */
+
+/* Encodes a scene given as host arrays pos[3][n] (in [0,1)) and attr[56][n] (finite):
+ * prune floor(n/10) of lowest opacity, voxelize, Morton sort, octree, per-channel quantize,
+ * then code (Sec. 3.3-3.4).  Writes at most `cap` bytes to `out` (host) and sets *out_len.
+ * If cap is too small returns SGS_E_INVALID with *out_len = the size needed.  ctx may be
+ * NULL except in learned mode (the context model's frequencies are computed on its device).
+ * Errors: SGS_E_INVALID, SGS_E_NOMEM, SGS_E_CUDA.                                            */
+int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, uint32_t n,
+                 const sgs_encode_params *params, uint8_t *out, size_t cap, size_t *out_len);
+
+/* Quantized tokens of a scene exactly as the encoder codes them: host uint8 [n_rows][56]
+ * (rows in Morton order) for 8-bit channels, after pruning.  *n_rows set.  Used to train
+ * the context model on the scene's own tokens.  cap in bytes.                               */
+int scene_tokens(const float *pos, const float *attr, uint32_t n, uint32_t depth,
+                 uint8_t *tokens, size_t cap, uint32_t *n_rows);
+
+/* ------------------------------------------------------------------ learned part */
+
+/* Trains the context model (Sec. 3.4.2; loss = code length in bits, Eq. 9) on the device:
+ * tokens_dev device uint8 [n_rows][56]; lanes = rANS lanes of the scene (contexts stop at
+ * lane starts); weights_dev device fp32 [SGS_WEIGHTS_FLOATS], initial values in, trained
+ * values out; adam_dev device fp32 [2 * SGS_WEIGHTS_FLOATS] Adam moments, zero to start
+ * (or a previous run's state to resume at step `step0`); loss_dev device fp32 [steps] or
+ * NULL.  Synchronous.  Errors: SGS_E_INVALID, SGS_E_NOMEM, SGS_E_CUDA.                      */
+int sgs_train(sgs_ctx *ctx, const uint8_t *tokens_dev, uint32_t n_rows, uint32_t lanes,
+              const sgs_train_params *params, uint32_t step0, float *weights_dev,
+              float *adam_dev, float *loss_dev);
+
+/* One forward/backward pass on the device for a given batch of token positions
+ * (pos_dev device int64 [batch], p = 56 * row + channel): loss (bits per token, fp32 host)
+ * and gradients grad_dev device fp32 [SGS_WEIGHTS_FLOATS].  For gradient checks.            */
+int sgs_train_grad(sgs_ctx *ctx, const uint8_t *tokens_dev, uint32_t n_rows, uint32_t lanes,
+                   const int64_t *pos_dev, uint32_t batch, const float *weights_dev,
+                   float *grad_dev, float *loss_host);
+
+/* Freezes fp32 weights (host, SGS_WEIGHTS_FLOATS) to the integer model (host,
+ * SGS_MODEL_BYTES): int8 weights, int32 biases with the channel embedding folded in,
+ * requantization multipliers from an integer calibration pass over 65,536 tokens of
+ * tokens (host uint8 [n_rows][56]) drawn with `seed`.  Errors: SGS_E_INVALID.              */
+int sgs_freeze(const float *weights, const uint8_t *tokens, uint32_t n_rows, uint32_t lanes,
+               uint32_t seed, uint8_t *model_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGS_H */

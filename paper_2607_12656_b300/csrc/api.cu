@@ -1,0 +1,366 @@
+// C ABI of the sgs library: context, header query, decode orchestration, status.
+// Kernels live in k_*.cu; the encoder in encode.cu; the learned part in k_learned.cu and
+// k_train.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "sgs_internal.h"
+
+constexpr int kMaxStages = 8;
+
+struct sgs_ctx {
+    int device;
+    uint8_t *scratch;
+    size_t scratch_bytes;
+    int *status_dev;
+    int *status_host;  // pinned
+    uint64_t launches; // kernels launched by decode calls on this context
+    int profile;       // record stage events in decode calls
+    int n_marks;
+    cudaEvent_t marks[kMaxStages + 1];
+};
+
+namespace sgs {
+
+size_t octree_scan_tiles(uint64_t n_geo);
+int octree_launches(const sgs_scene_info &info, const GeoPlan &plan);
+size_t octree_chunks(uint64_t n_geo);
+
+static inline uint64_t a256(uint64_t x) { return (x + 255) & ~255ull; }
+
+static uint32_t rd32(const uint8_t *p) {
+    uint32_t v;
+    memcpy(&v, p, 4);
+    return v;
+}
+static uint64_t rd64(const uint8_t *p) {
+    uint64_t v;
+    memcpy(&v, p, 8);
+    return v;
+}
+
+void make_geo_plan(const sgs_scene_info &info, GeoPlan *plan) {
+    memset(plan, 0, sizeof(*plan));
+    plan->depth = (int)info.depth;
+    uint64_t off = 0, coded = 0;
+    int k = 0;
+    for (uint32_t l = 0; l <= info.depth; ++l) {
+        plan->n_level[l] = info.n_level[l];
+        plan->level_off[l] = off;
+        off += info.n_level[l];
+        if (l < info.depth && info.geo_mode == SGS_GEO_RANS && info.n_level[l] >= kGeoRansMinLevel) {
+            plan->coded_level[k] = (int)l;
+            plan->coded_start[k] = coded;
+            coded += info.n_level[l];
+            ++k;
+        }
+    }
+    plan->n_coded_levels = k;
+    plan->coded_start[k] = coded;
+}
+
+static uint64_t max_level_nodes(const sgs_scene_info &info) {
+    uint64_t m = 1;
+    for (uint32_t l = 0; l < info.depth; ++l) m = std::max<uint64_t>(m, info.n_level[l]);
+    return m;
+}
+
+// Carves the scratch regions of one decode out of `base` (or only sizes them if base is
+// NULL).  Returns the total size.
+size_t scratch_need(const sgs_scene_info &info, Scratch *s, uint8_t *base) {
+    GeoPlan plan;
+    make_geo_plan(info, &plan);
+    uint64_t off = 0;
+    auto take = [&](uint64_t bytes) {
+        uint8_t *p = base ? base + off : nullptr;
+        off = a256(off + bytes);
+        return p;
+    };
+    Scratch t;
+    t.geo_bytes = take(info.geo_mode == SGS_GEO_RANS ? info.n_geo : 0);
+    t.chunk_prefix = reinterpret_cast<uint32_t *>(take(4 * (octree_chunks(info.n_geo) + 1)));
+    t.scan_flags = reinterpret_cast<uint64_t *>(take(8 * (octree_scan_tiles(info.n_geo) + 1)));
+    t.ticket = reinterpret_cast<uint32_t *>(take(256));
+    const uint64_t ml = max_level_nodes(info);
+    t.codes[0] = reinterpret_cast<uint64_t *>(take(8 * ml));
+    t.codes[1] = reinterpret_cast<uint64_t *>(take(8 * ml));
+    const int n_tab = plan.n_coded_levels + (info.mode == SGS_MODE_STATIC ? kNChan : 0);
+    t.tables = take((uint64_t)n_tab * kTabBytes);
+    t.dup_prefix = reinterpret_cast<uint32_t *>(take(4ull * (info.n_dup + 1)));
+    t.learned = take(info.mode == SGS_MODE_LEARNED ? learned_work_bytes(info) : 0);
+    if (s) *s = t;
+    return off;
+}
+
+}  // namespace sgs
+
+using namespace sgs;
+
+extern "C" const char *sgs_strerror(int code) {
+    switch (code) {
+        case SGS_OK: return "ok";
+        case SGS_E_INVALID: return "invalid argument or malformed header";
+        case SGS_E_CORRUPT: return "corrupt bitstream";
+        case SGS_E_NOMEM: return "out of memory or scratch too small";
+        case SGS_E_CUDA: return "CUDA error";
+        case SGS_E_TIMEOUT: return "device wait timed out";
+        case SGS_E_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int sgs_create(sgs_ctx **out, int device, size_t scratch_bytes) {
+    if (!out) return SGS_E_INVALID;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) return SGS_E_CUDA;
+    if (device < 0 || device >= n) return SGS_E_INVALID;
+    if (cudaSetDevice(device) != cudaSuccess) return SGS_E_CUDA;
+    sgs_ctx *c = new (std::nothrow) sgs_ctx();
+    if (!c) return SGS_E_NOMEM;
+    c->device = device;
+    if (cudaMalloc(&c->status_dev, 256) != cudaSuccess) { delete c; return SGS_E_NOMEM; }
+    if (cudaMallocHost(&c->status_host, 256) != cudaSuccess) {
+        cudaFree(c->status_dev);
+        delete c;
+        return SGS_E_NOMEM;
+    }
+    cudaMemset(c->status_dev, 0, 256);
+    c->launches = 0;
+    c->profile = 0;
+    c->n_marks = 0;
+    for (int i = 0; i <= kMaxStages; ++i) cudaEventCreate(&c->marks[i]);
+    c->scratch = nullptr;
+    c->scratch_bytes = 0;
+    if (scratch_bytes) {
+        if (cudaMalloc(&c->scratch, scratch_bytes) != cudaSuccess) {
+            cudaFree(c->status_dev);
+            cudaFreeHost(c->status_host);
+            delete c;
+            return SGS_E_NOMEM;
+        }
+        c->scratch_bytes = scratch_bytes;
+    }
+    *out = c;
+    return SGS_OK;
+}
+
+extern "C" int sgs_reserve(sgs_ctx *c, size_t bytes) {
+    if (!c) return SGS_E_INVALID;
+    if (bytes <= c->scratch_bytes) return SGS_OK;
+    cudaSetDevice(c->device);
+    if (cudaDeviceSynchronize() != cudaSuccess) return SGS_E_CUDA;
+    if (c->scratch) cudaFree(c->scratch);
+    c->scratch = nullptr;
+    c->scratch_bytes = 0;
+    if (cudaMalloc(&c->scratch, bytes) != cudaSuccess) return SGS_E_NOMEM;
+    c->scratch_bytes = bytes;
+    return SGS_OK;
+}
+
+extern "C" void sgs_destroy(sgs_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    if (c->scratch) cudaFree(c->scratch);
+    for (int i = 0; i <= kMaxStages; ++i) cudaEventDestroy(c->marks[i]);
+    cudaFree(c->status_dev);
+    cudaFreeHost(c->status_host);
+    delete c;
+}
+
+extern "C" int sgs_profile(sgs_ctx *c, int enable) {
+    if (!c) return SGS_E_INVALID;
+    c->profile = enable != 0;
+    return SGS_OK;
+}
+
+// Stage times (ms) of the most recent profiled decode: geometry tokens (tables, raw copy,
+// rANS), octree expansion (scan, top levels, deep levels, positions), attributes.
+extern "C" int sgs_profile_read(sgs_ctx *c, float *ms, int cap) {
+    if (!c || !ms || cap < 3) return SGS_E_INVALID;
+    if (c->n_marks != 4) return SGS_E_INVALID;
+    for (int i = 0; i < 3; ++i)
+        if (cudaEventElapsedTime(&ms[i], c->marks[i], c->marks[i + 1]) != cudaSuccess) return SGS_E_CUDA;
+    return SGS_OK;
+}
+
+extern "C" uint64_t sgs_launch_count(sgs_ctx *c) { return c ? c->launches : 0; }
+
+extern "C" int sgs_sync(sgs_ctx *c, sgs_stream stream) {
+    if (!c) return SGS_E_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(c->status_host, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+        cudaSuccess)
+        return SGS_E_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SGS_E_CUDA;
+    const int s = c->status_host[0];
+    if (cudaMemsetAsync(c->status_dev, 0, sizeof(int), st) != cudaSuccess) return SGS_E_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SGS_E_CUDA;
+    return s;
+}
+
+extern "C" int scene_query(const uint8_t *b, size_t len, sgs_scene_info *info) {
+    if (!b || !info || len < (size_t)kHeaderBytes) return SGS_E_INVALID;
+    memset(info, 0, sizeof(*info));
+    if (rd32(b) != kMagic || rd32(b + 4) != kVersion) return SGS_E_INVALID;
+    info->mode = rd32(b + 8);
+    info->geo_mode = rd32(b + 12);
+    info->n_in = rd32(b + 16);
+    info->n_rows = rd32(b + 20);
+    info->depth = rd32(b + 24);
+    info->n_leaves = rd32(b + 28);
+    info->n_dup = rd32(b + 32);
+    const uint32_t n_chan = rd32(b + 36);
+    info->lanes = rd32(b + 40);
+    info->geo_lanes = rd32(b + 44);
+    info->n_geo = rd64(b + 48);
+    info->n_geo_coded = rd64(b + 56);
+    for (int i = 0; i < 11; ++i) info->off[i] = rd64(b + 64 + 8 * i);
+    info->total_len = info->off[S_TOTAL];
+    if (n_chan != (uint32_t)kNChan || info->mode > 2 || info->geo_mode > 1) return SGS_E_INVALID;
+    if (info->depth < 1 || info->depth > SGS_MAX_DEPTH) return SGS_E_INVALID;
+    if (info->total_len != len) return SGS_E_INVALID;
+    if (info->off[0] != (uint64_t)kHeaderBytes) return SGS_E_INVALID;
+    for (int i = 0; i < 11; ++i) {
+        if (info->off[i] % 16 != 0 || info->off[i] > info->total_len) return SGS_E_INVALID;
+        if (i > 0 && info->off[i] < info->off[i - 1]) return SGS_E_INVALID;
+    }
+    auto sec = [&](int i) { return info->off[i + 1] - info->off[i]; };
+    const uint32_t D = info->depth;
+    if (sec(S_LEVELS) < 4ull * D || sec(S_DUP) < 8ull * info->n_dup || sec(S_CHAN) < 12ull * kNChan)
+        return SGS_E_INVALID;
+    uint64_t sum = 0, coded = 0;
+    for (uint32_t l = 0; l < D; ++l) {
+        info->n_level[l] = rd32(b + info->off[S_LEVELS] + 4 * l);
+        sum += info->n_level[l];
+        if (info->geo_mode == SGS_GEO_RANS && info->n_level[l] >= kGeoRansMinLevel)
+            coded += info->n_level[l];
+        if (l > 0 && info->n_level[l] < info->n_level[l - 1]) return SGS_E_INVALID;  // every node has >= 1 child
+        if (l > 0 && (uint64_t)info->n_level[l] > 8ull * info->n_level[l - 1]) return SGS_E_INVALID;
+    }
+    info->n_level[D] = info->n_leaves;
+    if (sum != info->n_geo || coded != info->n_geo_coded) return SGS_E_INVALID;
+    if (info->n_rows == 0) {
+        if (info->n_leaves != 0 || info->n_geo != 0 || info->n_dup != 0) return SGS_E_INVALID;
+    } else {
+        if (info->n_level[0] != 1 || info->n_leaves == 0 || info->n_leaves > info->n_rows ||
+            info->n_leaves < info->n_level[D - 1] || (uint64_t)info->n_leaves > 8ull * info->n_level[D - 1])
+            return SGS_E_INVALID;
+        if (info->n_geo + info->n_leaves >= (1ull << 32)) return SGS_E_INVALID;
+        if (info->n_dup > info->n_leaves) return SGS_E_INVALID;
+    }
+    // geometry sections
+    uint64_t raw = info->n_geo - info->n_geo_coded;
+    if (sec(S_GEO_RAW) < raw) return SGS_E_INVALID;
+    if (info->n_geo_coded) {
+        if (info->geo_lanes == 0) return SGS_E_INVALID;
+        const uint64_t G = (info->geo_lanes + 31) / 32;
+        if (sec(S_GEO_GRP) < 8 * (G + 1) + 4 * G) return SGS_E_INVALID;
+    } else if (info->geo_lanes != 0) {
+        return SGS_E_INVALID;
+    }
+    // attribute sections
+    if (info->mode == SGS_MODE_FIXED) {
+        if (info->lanes != 0 || sec(S_ATTR_TAB) < 8ull * (kNChan + 1)) return SGS_E_INVALID;
+    } else {
+        if (info->lanes == 0) return SGS_E_INVALID;
+        const uint64_t G = (info->lanes + 31) / 32;
+        if (sec(S_ATTR_GRP) < 8 * (G + 1) + 4 * G) return SGS_E_INVALID;
+        if (info->mode == SGS_MODE_LEARNED && sec(S_ATTR_TAB) < (uint64_t)SGS_MODEL_BYTES)
+            return SGS_E_INVALID;
+    }
+    info->scratch_bytes = scratch_need(*info, nullptr, nullptr);
+    return SGS_OK;
+}
+
+static int cuda_status(cudaError_t e) { return e == cudaSuccess ? SGS_OK : SGS_E_CUDA; }
+
+// Enqueues every stage of one scene's decode on `st` using scratch `base`.
+static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &info,
+                      const sgs_scene_out &out, uint8_t *base, cudaStream_t st) {
+    Scratch s;
+    scratch_need(info, &s, base);
+    GeoPlan plan;
+    make_geo_plan(info, &plan);
+    int *status = c->status_dev;
+    cudaError_t e;
+    // zero the look-back flags and ticket (adjacent regions)
+    const size_t zbytes = (uint8_t *)s.ticket + 256 - (uint8_t *)s.scan_flags;
+    if ((e = cudaMemsetAsync(s.scan_flags, 0, zbytes, st)) != cudaSuccess) return SGS_E_CUDA;
+    c->n_marks = 0;
+    auto mark = [&]() {
+        if (c->profile && c->n_marks <= kMaxStages) cudaEventRecord(c->marks[c->n_marks++], st);
+    };
+    mark();
+    if (plan.n_coded_levels) {
+        c->launches += 1;
+        e = launch_tables(bits, info.off[S_GEO_TAB], info.off[S_GEO_GRP], plan.n_coded_levels,
+                          s.tables, 0, status, st);
+        if (e != cudaSuccess) return SGS_E_CUDA;
+    }
+    uint8_t *attr_tables = s.tables + (size_t)plan.n_coded_levels * kTabBytes;
+    if (info.mode == SGS_MODE_STATIC) {
+        c->launches += 1;
+        e = launch_tables(bits, info.off[S_ATTR_TAB], info.off[S_ATTR_GRP], kNChan, attr_tables,
+                          info.n_rows == 0, status, st);
+        if (e != cudaSuccess) return SGS_E_CUDA;
+    }
+    // geometry
+    const uint8_t *B = bits + info.off[S_GEO_RAW];
+    if (info.geo_mode == SGS_GEO_RANS && info.n_geo) {
+        if ((e = launch_geo_copy_raw(bits, info, plan, s.geo_bytes, st)) != cudaSuccess) return SGS_E_CUDA;
+        if ((e = launch_rans_static_geo(bits, info, plan, s.tables, s.geo_bytes, status, st)) != cudaSuccess)
+            return SGS_E_CUDA;
+        B = s.geo_bytes;
+        c->launches += 2;
+    }
+    mark();
+    if ((e = launch_octree(B, info, plan, bits, s, out, status, st)) != cudaSuccess) return SGS_E_CUDA;
+    if (info.n_rows) c->launches += octree_launches(info, plan);
+    mark();
+    // attributes
+    if (info.n_rows) c->launches += 1;
+    switch (info.mode) {
+        case SGS_MODE_FIXED: e = launch_fixed(bits, info, out, status, st); break;
+        case SGS_MODE_STATIC: e = launch_rans_static_attr(bits, info, attr_tables, out, status, st); break;
+        default: e = launch_learned_decode(bits, info, out, s.learned, status, st); break;
+    }
+    mark();
+    return cuda_status(e);
+}
+
+extern "C" int scene_decode(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info *info,
+                            const sgs_scene_out *out, sgs_stream stream) {
+    if (!c || !bits || !info || !out) return SGS_E_INVALID;
+    if (((uintptr_t)bits & 15) != 0) return SGS_E_INVALID;
+    if (info->n_rows && (!out->attr || !out->pos)) return SGS_E_INVALID;
+    if (info->scratch_bytes > c->scratch_bytes) return SGS_E_NOMEM;
+    if (cudaSetDevice(c->device) != cudaSuccess) return SGS_E_CUDA;
+    return decode_one(c, bits, *info, *out, c->scratch, (cudaStream_t)stream);
+}
+
+extern "C" int scene_decode_batch(sgs_ctx *c, const sgs_batch_item *items, int n,
+                                  sgs_stream stream) {
+    if (!c || (!items && n) || n < 0) return SGS_E_INVALID;
+    uint64_t need = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!items[i].bits_dev || ((uintptr_t)items[i].bits_dev & 15)) return SGS_E_INVALID;
+        if (items[i].info.n_rows && (!items[i].out.attr || !items[i].out.pos)) return SGS_E_INVALID;
+        need += a256(items[i].info.scratch_bytes);
+    }
+    if (need > c->scratch_bytes) return SGS_E_NOMEM;
+    if (cudaSetDevice(c->device) != cudaSuccess) return SGS_E_CUDA;
+    uint64_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        int r = decode_one(c, items[i].bits_dev, items[i].info, items[i].out, c->scratch + off,
+                           (cudaStream_t)stream);
+        if (r != SGS_OK) return r;
+        off += a256(items[i].info.scratch_bytes);
+    }
+    return SGS_OK;
+}

@@ -1,0 +1,412 @@
+// Scene encoder of the sgs library (host C++; the learned mode's per-token frequencies are
+// computed on the device).  Pipeline (Sec. 3.3-3.4):
+//   prune floor(n/10) Gaussians of lowest opacity (ties: lower index first) -> voxelize at
+//   depth D -> sort rows by (Morton code, original index) -> sparse-octree occupancy tokens
+//   per level, duplicate counts as metadata -> per-channel uniform quantization
+//   (offset = min, step = fl32((max-min)/(2^b-1)), q = clamp(rint((v-offset)/step))) ->
+//   channel-wise fixed-length packing, static-frequency rANS, or learned-model rANS.
+// The output bytes are fully determined by the inputs (all tie-breaks fixed), so any two
+// correct encoders produce identical bitstreams.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "sgs_internal.h"
+
+namespace sgs {
+namespace {
+
+constexpr uint32_t kM = 1u << 16;
+
+struct Prepared {
+    uint32_t depth = 0, n_in = 0;
+    std::vector<uint32_t> keep;          // row -> original index
+    std::vector<uint64_t> leaves;        // unique Morton codes
+    std::vector<uint32_t> dups;          // {rank, extra} pairs
+    std::vector<std::vector<uint8_t>> levels;
+    uint32_t bits[kNChan];
+    std::vector<uint8_t> q8;             // [rows][56] when every width <= 8
+    std::vector<uint16_t> q16;           // [rows][56]
+    float step[kNChan], offset[kNChan];
+    uint32_t rows() const { return (uint32_t)keep.size(); }
+};
+
+uint64_t morton3(uint32_t x, uint32_t y, uint32_t z, uint32_t D) {
+    uint64_t m = 0;
+    for (uint32_t b = 0; b < D; ++b) {
+        m |= (uint64_t)((x >> b) & 1u) << (3 * b + 2);
+        m |= (uint64_t)((y >> b) & 1u) << (3 * b + 1);
+        m |= (uint64_t)((z >> b) & 1u) << (3 * b);
+    }
+    return m;
+}
+
+int prepare(const float *pos, const float *attr, uint32_t n, uint32_t D, const uint32_t *bits,
+            Prepared &P) {
+    if (D < 1 || D > SGS_MAX_DEPTH) return SGS_E_INVALID;
+    for (int c = 0; c < kNChan; ++c)
+        if (bits[c] < 1 || bits[c] > 16) return SGS_E_INVALID;
+    for (uint64_t i = 0; i < 3ull * n; ++i)
+        if (!(pos[i] >= 0.0f && pos[i] < 1.0f)) return SGS_E_INVALID;
+    for (uint64_t i = 0; i < (uint64_t)kNChan * n; ++i)
+        if (!isfinite(attr[i])) return SGS_E_INVALID;
+    P.depth = D;
+    P.n_in = n;
+    memcpy(P.bits, bits, sizeof(P.bits));
+    // prune: order by (opacity, index), drop the first floor(n/10)
+    const float *op = attr + 48ull * n;
+    std::vector<uint32_t> idx(n);
+    std::iota(idx.begin(), idx.end(), 0u);
+    std::sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) {
+        return op[a] < op[b] || (op[a] == op[b] && a < b);
+    });
+    std::vector<uint32_t> keep(idx.begin() + n / 10, idx.end());
+    std::sort(keep.begin(), keep.end());
+    // voxelize + Morton
+    const double scale = (double)(1u << D);
+    const double vmax = (double)((1u << D) - 1);
+    std::vector<uint64_t> code(keep.size());
+    for (size_t r = 0; r < keep.size(); ++r) {
+        uint32_t v[3];
+        for (int k = 0; k < 3; ++k) {
+            double t = floor((double)pos[(uint64_t)k * n + keep[r]] * scale);
+            v[k] = (uint32_t)std::min(t, vmax);
+        }
+        code[r] = morton3(v[0], v[1], v[2], D);
+    }
+    std::vector<uint32_t> ord(keep.size());
+    std::iota(ord.begin(), ord.end(), 0u);
+    std::sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) {
+        return code[a] < code[b] || (code[a] == code[b] && keep[a] < keep[b]);
+    });
+    P.keep.resize(keep.size());
+    std::vector<uint64_t> sc(keep.size());
+    for (size_t r = 0; r < ord.size(); ++r) {
+        P.keep[r] = keep[ord[r]];
+        sc[r] = code[ord[r]];
+    }
+    // unique voxels and duplicate counts
+    for (size_t r = 0; r < sc.size();) {
+        size_t e = r + 1;
+        while (e < sc.size() && sc[e] == sc[r]) ++e;
+        if (e - r > 1) {
+            P.dups.push_back((uint32_t)P.leaves.size());
+            P.dups.push_back((uint32_t)(e - r - 1));
+        }
+        P.leaves.push_back(sc[r]);
+        r = e;
+    }
+    // octree tokens per level
+    P.levels.assign(D, {});
+    for (uint32_t l = 0; l < D && !P.leaves.empty(); ++l) {
+        const uint32_t sn = 3 * (D - l), sk = 3 * (D - l - 1);
+        auto &lv = P.levels[l];
+        uint64_t cur = P.leaves[0] >> sn;
+        uint8_t byte = 0;
+        for (uint64_t m : P.leaves) {
+            const uint64_t node = m >> sn;
+            if (node != cur) {
+                lv.push_back(byte);
+                byte = 0;
+                cur = node;
+            }
+            byte |= (uint8_t)(1u << ((m >> sk) & 7u));
+        }
+        lv.push_back(byte);
+    }
+    // per-channel quantization
+    const uint32_t R = P.rows();
+    P.q16.assign((size_t)R * kNChan, 0);
+    for (int c = 0; c < kNChan; ++c) {
+        const float *v = attr + (uint64_t)c * n;
+        if (R == 0) {
+            P.step[c] = 0.0f;
+            P.offset[c] = 0.0f;
+            continue;
+        }
+        float mn = v[P.keep[0]], mx = mn;
+        for (uint32_t r = 1; r < R; ++r) {
+            const float a = v[P.keep[r]];
+            mn = a < mn ? a : mn;
+            mx = a > mx ? a : mx;
+        }
+        const uint32_t top = (1u << bits[c]) - 1u;
+        const float step = (mx == mn) ? 0.0f : (float)(((double)mx - (double)mn) / (double)top);
+        P.step[c] = step;
+        P.offset[c] = mn;
+        if (step == 0.0f) continue;
+        for (uint32_t r = 0; r < R; ++r) {
+            double t = nearbyint(((double)v[P.keep[r]] - (double)mn) / (double)step);
+            t = std::min(std::max(t, 0.0), (double)top);
+            P.q16[(size_t)r * kNChan + c] = (uint16_t)t;
+        }
+    }
+    return SGS_OK;
+}
+
+// Static 16-bit table: f = 1 + floor(h (2^16 - K) / sum) for present symbols, remainder to
+// the most frequent symbol (lowest index on ties).
+void normalize(const uint64_t *h, uint32_t *f) {
+    uint64_t tot = 0, K = 0;
+    int amax = 0;
+    for (int s = 0; s < kNSym; ++s) {
+        tot += h[s];
+        K += h[s] > 0;
+        if (h[s] > h[amax]) amax = s;
+    }
+    uint64_t sum = 0;
+    for (int s = 0; s < kNSym; ++s) {
+        f[s] = h[s] ? (uint32_t)(1 + h[s] * (kM - K) / tot) : 0u;
+        sum += f[s];
+    }
+    if (tot) f[amax] += (uint32_t)(kM - sum);
+}
+
+void put_table(std::vector<uint8_t> &o, const uint32_t *f) {
+    uint8_t mask[32] = {0};
+    for (int s = 0; s < kNSym; ++s)
+        if (f[s]) mask[s >> 3] |= (uint8_t)(1u << (s & 7));
+    o.insert(o.end(), mask, mask + 32);
+    for (int s = 0; s < kNSym; ++s)
+        if (f[s]) {
+            const uint32_t v = f[s] - 1;
+            o.push_back((uint8_t)v);
+            o.push_back((uint8_t)(v >> 8));
+        }
+    while (o.size() % 16) o.push_back(0);
+}
+
+// Interleaved rANS: lanes of 32 share a stream; per group, encode steps in reverse (t and
+// lane descending), push the final states as (lo, hi) for lanes descending, reverse.
+// sym_f / sym_c: frequency and cumulative of every token, lane-major (lane_start offsets).
+void rans_encode(const std::vector<uint64_t> &lane_start, const uint32_t *sym_f,
+                 const uint32_t *sym_c, std::vector<uint8_t> &grp, std::vector<uint8_t> &pay) {
+    const uint64_t L = lane_start.size() - 1;
+    const uint64_t G = (L + 31) / 32;
+    std::vector<uint64_t> goff(G + 1, 0);
+    std::vector<uint32_t> gw(G, 0);
+    std::vector<uint16_t> w;
+    for (uint64_t g = 0; g < G; ++g) {
+        const uint64_t j0 = 32 * g, j1 = std::min(L, j0 + 32);
+        const int nl = (int)(j1 - j0);
+        uint64_t maxn = 0;
+        for (uint64_t j = j0; j < j1; ++j) maxn = std::max(maxn, lane_start[j + 1] - lane_start[j]);
+        w.clear();
+        uint32_t x[32];
+        for (int j = 0; j < nl; ++j) x[j] = kM;
+        for (uint64_t tt = maxn; tt-- > 0;) {
+            for (int j = nl - 1; j >= 0; --j) {
+                const uint64_t n = lane_start[j0 + j + 1] - lane_start[j0 + j];
+                if (tt >= n) continue;
+                const uint64_t p = lane_start[j0 + j] + tt;
+                const uint32_t f = sym_f[p], cu = sym_c[p];
+                if ((uint64_t)x[j] >= ((uint64_t)f << 16)) {
+                    w.push_back((uint16_t)(x[j] & 0xFFFFu));
+                    x[j] >>= 16;
+                }
+                x[j] = ((x[j] / f) << 16) + (x[j] % f) + cu;
+            }
+        }
+        for (int j = nl - 1; j >= 0; --j) {
+            w.push_back((uint16_t)(x[j] & 0xFFFFu));
+            w.push_back((uint16_t)(x[j] >> 16));
+        }
+        gw[g] = (uint32_t)w.size();
+        for (size_t k = w.size(); k-- > 0;) {
+            pay.push_back((uint8_t)(w[k] & 0xFF));
+            pay.push_back((uint8_t)(w[k] >> 8));
+        }
+        while (pay.size() % 16) pay.push_back(0);
+        goff[g + 1] = pay.size();
+    }
+    grp.resize(8 * (G + 1) + 4 * G);
+    memcpy(grp.data(), goff.data(), 8 * (G + 1));
+    memcpy(grp.data() + 8 * (G + 1), gw.data(), 4 * G);
+    while (grp.size() % 16) grp.push_back(0);
+}
+
+std::vector<uint64_t> lane_bounds(uint64_t n, uint64_t L, uint64_t mul) {
+    std::vector<uint64_t> b(L + 1);
+    for (uint64_t j = 0; j <= L; ++j) b[j] = (j * n / L) * mul;
+    return b;
+}
+
+void pack_fixed(const Prepared &P, int c, std::vector<uint8_t> &o) {
+    const uint32_t b = P.bits[c], R = P.rows();
+    if (R == 0) return;
+    const uint64_t nw = ((uint64_t)R * b + 31) / 32;
+    std::vector<uint32_t> w(nw, 0);
+    for (uint32_t r = 0; r < R; ++r) {
+        const uint64_t v = P.q16[(size_t)r * kNChan + c];
+        const uint64_t bit = (uint64_t)r * b;
+        const uint64_t wi = bit >> 5, sh = bit & 31;
+        w[wi] |= (uint32_t)(v << sh);
+        if (sh + b > 32) w[wi + 1] |= (uint32_t)(v >> (32 - sh));
+    }
+    const size_t at = o.size();
+    o.resize(at + 4 * nw);
+    memcpy(o.data() + at, w.data(), 4 * nw);
+    while (o.size() % 16) o.push_back(0);
+}
+
+void pad16(std::vector<uint8_t> &v) {
+    while (v.size() % 16) v.push_back(0);
+}
+
+template <typename T>
+void put(std::vector<uint8_t> &o, T v) {
+    const uint8_t *p = reinterpret_cast<const uint8_t *>(&v);
+    o.insert(o.end(), p, p + sizeof(T));
+}
+
+uint32_t default_geo_lanes(uint64_t n) {
+    const uint64_t per = 512ull * 32;
+    return (uint32_t)std::max<uint64_t>(32, (n + per - 1) / per * 32);
+}
+
+}  // namespace
+
+// Computes on the device the frequency and cumulative of every token under the frozen
+// model; defined with the learned decoder.
+int learned_token_fc(sgs_ctx *c, const uint8_t *model, const uint8_t *tokens, uint32_t n_rows,
+                     uint32_t lanes, std::vector<uint32_t> &f, std::vector<uint32_t> &cum);
+
+}  // namespace sgs
+
+using namespace sgs;
+
+extern "C" int scene_tokens(const float *pos, const float *attr, uint32_t n, uint32_t depth,
+                            uint8_t *tokens, size_t cap, uint32_t *n_rows) {
+    if (!pos || !attr || !n_rows) return SGS_E_INVALID;
+    uint32_t bits[kNChan];
+    for (int c = 0; c < kNChan; ++c) bits[c] = 8;
+    Prepared P;
+    int r = prepare(pos, attr, n, depth, bits, P);
+    if (r) return r;
+    *n_rows = P.rows();
+    if (cap < (size_t)P.rows() * kNChan || (!tokens && P.rows())) return SGS_E_INVALID;
+    for (size_t i = 0; i < (size_t)P.rows() * kNChan; ++i) tokens[i] = (uint8_t)P.q16[i];
+    return SGS_OK;
+}
+
+extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, uint32_t n,
+                            const sgs_encode_params *prm, uint8_t *out, size_t cap,
+                            size_t *out_len) {
+    if (!prm || !out_len || (n && (!pos || !attr))) return SGS_E_INVALID;
+    if (prm->mode > 2 || prm->geo_mode > 1) return SGS_E_INVALID;
+    uint32_t bits[kNChan];
+    for (int c = 0; c < kNChan; ++c) bits[c] = prm->mode == SGS_MODE_FIXED ? prm->bits[c] : 8u;
+    if (prm->mode != SGS_MODE_FIXED && prm->lanes < 1) return SGS_E_INVALID;
+    if (prm->mode == SGS_MODE_LEARNED && (!prm->model || !ctx)) return SGS_E_INVALID;
+    Prepared P;
+    int r = prepare(pos, attr, n, prm->depth, bits, P);
+    if (r) return r;
+    const uint32_t D = prm->depth, R = P.rows();
+    // geometry
+    std::vector<uint8_t> s_levels, s_dup, s_chan, s_graw, s_gtab, s_ggrp, s_gpay;
+    std::vector<int> coded_levels;
+    uint64_t n_geo = 0, n_coded = 0;
+    for (uint32_t l = 0; l < D; ++l) {
+        const uint32_t nl = (uint32_t)P.levels[l].size();
+        put<uint32_t>(s_levels, nl);
+        n_geo += nl;
+        if (prm->geo_mode == SGS_GEO_RANS && nl >= kGeoRansMinLevel) {
+            coded_levels.push_back((int)l);
+            n_coded += nl;
+        } else {
+            s_graw.insert(s_graw.end(), P.levels[l].begin(), P.levels[l].end());
+        }
+    }
+    uint32_t Lg = 0;
+    if (n_coded) {
+        Lg = prm->geo_lanes ? prm->geo_lanes : default_geo_lanes(n_coded);
+        std::vector<uint32_t> sf(n_coded), scu(n_coded);
+        uint64_t p = 0;
+        for (int l : coded_levels) {
+            uint64_t h[kNSym] = {0};
+            for (uint8_t b : P.levels[l]) h[b]++;
+            uint32_t f[kNSym], cu[kNSym];
+            normalize(h, f);
+            put_table(s_gtab, f);
+            uint32_t acc = 0;
+            for (int s = 0; s < kNSym; ++s) { cu[s] = acc; acc += f[s]; }
+            for (uint8_t b : P.levels[l]) { sf[p] = f[b]; scu[p] = cu[b]; ++p; }
+        }
+        rans_encode(lane_bounds(n_coded, Lg, 1), sf.data(), scu.data(), s_ggrp, s_gpay);
+    }
+    for (size_t i = 0; i < P.dups.size(); ++i) put<uint32_t>(s_dup, P.dups[i]);
+    for (int c = 0; c < kNChan; ++c) put<float>(s_chan, P.step[c]);
+    for (int c = 0; c < kNChan; ++c) put<float>(s_chan, P.offset[c]);
+    for (int c = 0; c < kNChan; ++c) put<uint32_t>(s_chan, P.bits[c]);
+    // attributes
+    std::vector<uint8_t> s_atab, s_agrp, s_apay;
+    uint32_t L = 0;
+    if (prm->mode == SGS_MODE_FIXED) {
+        std::vector<uint64_t> offs;
+        for (int c = 0; c < kNChan; ++c) {
+            offs.push_back(s_apay.size());
+            pack_fixed(P, c, s_apay);
+        }
+        offs.push_back(s_apay.size());
+        for (uint64_t o : offs) put<uint64_t>(s_atab, o);
+    } else {
+        L = prm->lanes;
+        const uint64_t nsym = (uint64_t)R * kNChan;
+        std::vector<uint32_t> sf(nsym), scu(nsym);
+        if (prm->mode == SGS_MODE_STATIC) {
+            for (int c = 0; c < kNChan; ++c) {
+                uint64_t h[kNSym] = {0};
+                for (uint32_t rr = 0; rr < R; ++rr) h[P.q16[(size_t)rr * kNChan + c]]++;
+                uint32_t f[kNSym], cu[kNSym];
+                normalize(h, f);
+                put_table(s_atab, f);
+                uint32_t acc = 0;
+                for (int s = 0; s < kNSym; ++s) { cu[s] = acc; acc += f[s]; }
+                for (uint32_t rr = 0; rr < R; ++rr) {
+                    const uint32_t q = P.q16[(size_t)rr * kNChan + c];
+                    sf[(size_t)rr * kNChan + c] = f[q];
+                    scu[(size_t)rr * kNChan + c] = cu[q];
+                }
+            }
+        } else {
+            const uint8_t *m = static_cast<const uint8_t *>(prm->model);
+            s_atab.assign(m, m + SGS_MODEL_BYTES);
+            std::vector<uint8_t> tok(nsym);
+            for (uint64_t i = 0; i < nsym; ++i) tok[i] = (uint8_t)P.q16[i];
+            r = learned_token_fc(ctx, m, tok.data(), R, L, sf, scu);
+            if (r) return r;
+        }
+        rans_encode(lane_bounds(R, L, kNChan), sf.data(), scu.data(), s_agrp, s_apay);
+    }
+    // assemble
+    std::vector<uint8_t> *secs[10] = {&s_levels, &s_dup, &s_chan, &s_graw, &s_gtab,
+                                      &s_ggrp, &s_gpay, &s_atab, &s_agrp, &s_apay};
+    uint64_t offs[11];
+    uint64_t pos_ = kHeaderBytes;
+    for (int i = 0; i < 10; ++i) {
+        pad16(*secs[i]);
+        offs[i] = pos_;
+        pos_ += secs[i]->size();
+    }
+    offs[10] = pos_;
+    *out_len = pos_;
+    if (cap < pos_ || !out) return SGS_E_INVALID;
+    std::vector<uint8_t> hdr;
+    const uint32_t h32[12] = {kMagic, kVersion, prm->mode, prm->geo_mode, n, R, D,
+                              (uint32_t)P.leaves.size(), (uint32_t)(P.dups.size() / 2),
+                              (uint32_t)kNChan, L, Lg};
+    for (uint32_t v : h32) put<uint32_t>(hdr, v);
+    put<uint64_t>(hdr, n_geo);
+    put<uint64_t>(hdr, n_coded);
+    for (int i = 0; i < 11; ++i) put<uint64_t>(hdr, offs[i]);
+    hdr.resize(kHeaderBytes, 0);
+    memcpy(out, hdr.data(), kHeaderBytes);
+    for (int i = 0; i < 10; ++i)
+        if (!secs[i]->empty()) memcpy(out + offs[i], secs[i]->data(), secs[i]->size());
+    return SGS_OK;
+}

@@ -1,0 +1,94 @@
+// Channel-wise fixed-length decoding on sm_103a (Sec. 3.4.1, the "UltraFast" coder: each
+// channel's quantized values stored at a fixed bit width).  Channel c's n values sit
+// LSB-first at bits [i b_c, (i+1) b_c) of its own little-endian u32 stream.
+//
+// One warp per (channel, 1024 rows): 1024 values of b bits are exactly 32 b words, so the
+// warp stages its words in shared memory with coalesced loads, then lane j extracts rows
+// j, j+32, ... through a 64-bit funnel of two words and writes the dequantized fp32 values
+// v = fl(fl(q * step) + offset) with coalesced 128-byte stores.  HBM-bound: per Gaussian it
+// reads sum(b_c)/8 bytes and writes 224.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sgs_device.cuh"
+#include "sgs_internal.h"
+
+namespace sgs {
+
+constexpr int kFixWarps = 8;
+constexpr int kFixRows = 1024;       // rows per warp item
+constexpr int kFixMaxBits = 16;
+
+struct FixedParams {
+    const uint8_t *bits;
+    uint64_t chan_off, tab_off, pay_off, pay_len;
+    uint32_t n_rows;
+    uint32_t n_items_per_chan;
+    float *out;
+    const uint32_t *out_index;
+    int *status;
+};
+
+__global__ void __launch_bounds__(32 * kFixWarps) k_fixed(FixedParams p) {
+    __shared__ uint32_t s_words[kFixWarps][32 * kFixMaxBits + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t item = (uint64_t)blockIdx.x * kFixWarps + warp;
+    const uint32_t c = (uint32_t)(item / p.n_items_per_chan);
+    if (c >= (uint32_t)kNChan) return;
+    const uint32_t blk = (uint32_t)(item - (uint64_t)c * p.n_items_per_chan);
+    const uint32_t b = *reinterpret_cast<const uint32_t *>(p.bits + p.chan_off + 4 * (2 * kNChan + c));
+    const float step = ld_f32(p.bits + p.chan_off + 4 * c);
+    const float offset = ld_f32(p.bits + p.chan_off + 4 * (kNChan + c));
+    const uint64_t *coff = reinterpret_cast<const uint64_t *>(p.bits + p.tab_off);
+    const uint64_t cbeg = coff[c], cend = coff[c + 1];
+    const uint64_t nwords_chan = ((uint64_t)p.n_rows * b + 31) / 32;
+    if (b < 1 || b > kFixMaxBits || cbeg > cend || cend > p.pay_len || cbeg % 16 != 0 ||
+        (cend - cbeg) < 4 * nwords_chan) {
+        if (lane == 0) set_status(p.status, SGS_E_CORRUPT);
+        return;
+    }
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(p.bits + p.pay_off + cbeg);
+    const uint64_t w0 = (uint64_t)blk * 32 * b;   // first word of this item
+    const uint32_t nw = 32 * b;
+    uint32_t *sw = s_words[warp];
+    for (uint32_t i = lane; i <= nw; i += 32)
+        sw[i] = (w0 + i < nwords_chan) ? w[w0 + i] : 0u;
+    __syncwarp();
+    const uint32_t mask = (b == 32) ? 0xffffffffu : ((1u << b) - 1u);
+    const uint64_t r0 = (uint64_t)blk * kFixRows;
+    float *outc = p.out + (uint64_t)c * p.n_rows;
+#pragma unroll 4
+    for (int k = 0; k < 32; ++k) {
+        const uint32_t rl = (uint32_t)k * 32 + lane;
+        const uint64_t row = r0 + rl;
+        if (row >= p.n_rows) break;
+        const uint32_t bit = rl * b;
+        const uint32_t wi = bit >> 5, o = bit & 31;
+        const uint64_t two = ((uint64_t)sw[wi + 1] << 32) | sw[wi];
+        const uint32_t q = (uint32_t)(two >> o) & mask;
+        const uint64_t col = p.out_index ? (uint64_t)p.out_index[row] : row;
+        outc[col] = dequant(q, step, offset);
+    }
+}
+
+cudaError_t launch_fixed(const uint8_t *bits, const sgs_scene_info &info,
+                         const sgs_scene_out &out, int *status, cudaStream_t st) {
+    if (info.n_rows == 0) return cudaSuccess;
+    FixedParams p;
+    p.bits = bits;
+    p.chan_off = info.off[S_CHAN];
+    p.tab_off = info.off[S_ATTR_TAB];
+    p.pay_off = info.off[S_ATTR_PAY];
+    p.pay_len = info.total_len - info.off[S_ATTR_PAY];
+    p.n_rows = info.n_rows;
+    p.n_items_per_chan = (info.n_rows + kFixRows - 1) / kFixRows;
+    p.out = out.attr;
+    p.out_index = out.out_index;
+    p.status = status;
+    const uint64_t items = (uint64_t)p.n_items_per_chan * kNChan;
+    const unsigned grid = (unsigned)((items + kFixWarps - 1) / kFixWarps);
+    k_fixed<<<grid, 32 * kFixWarps, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace sgs

@@ -1,0 +1,127 @@
+// Device helpers shared by the sgs kernels (rANS group streams, tables, scans, dequant).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sgs_internal.h"
+
+namespace sgs {
+
+__device__ __forceinline__ uint32_t ld_u16(const uint8_t *p) {
+    return (uint32_t)p[0] | ((uint32_t)p[1] << 8);
+}
+
+__device__ __forceinline__ float ld_f32(const uint8_t *p) {  // p 4-byte aligned
+    return *reinterpret_cast<const float *>(p);
+}
+
+// Dequantization (fp32): v = fl(fl(q * step) + offset), two roundings, never fused.
+__device__ __forceinline__ float dequant(uint32_t q, float step, float offset) {
+    return __fadd_rn(__fmul_rn((float)q, step), offset);
+}
+
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        uint64_t n = __shfl_xor_sync(0xffffffffu, v, o);
+        v = n > v ? n : v;
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of one u32 per thread (blockDim.x == 256); *total = sum.
+__device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *total,
+                                                        uint32_t *sm /*[8]*/) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t n = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += n;
+    }
+    if (lane == 31) sm[warp] = incl;
+    __syncthreads();
+    uint32_t wbase = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        uint32_t s = sm[w];
+        if (w < warp) wbase += s;
+        tot += s;
+    }
+    __syncthreads();
+    *total = tot;
+    return wbase + incl - v;
+}
+
+// Copies n expanded tables (cdf[257] + bucket[256] each) into shared memory.
+__device__ __forceinline__ void load_tables_smem(const uint8_t *tables, int n, uint32_t *s_cdf,
+                                                 uint8_t *s_bucket) {
+    for (int i = threadIdx.x; i < n * kTabCdfWords; i += blockDim.x) {
+        int t = i / kTabCdfWords, k = i - t * kTabCdfWords;
+        s_cdf[i] = reinterpret_cast<const uint32_t *>(tables + (size_t)t * kTabBytes)[k];
+    }
+    for (int i = threadIdx.x; i < n * 256; i += blockDim.x) {
+        int t = i >> 8, k = i & 255;
+        s_bucket[i] = tables[(size_t)t * kTabBytes + kTabCdfWords * 4 + k];
+    }
+}
+
+// One rANS decode step (M = 2^16) against a cdf[257] + bucket[256] table.
+__device__ __forceinline__ uint32_t rans_sym(uint32_t &x, const uint32_t *cdf,
+                                             const uint8_t *bucket) {
+    const uint32_t slot = x & 0xFFFFu;
+    uint32_t s = bucket[slot >> 8];
+    while (s < 255 && cdf[s + 1] <= slot) ++s;
+    const uint32_t lo = cdf[s];
+    const uint32_t f = cdf[s + 1] - lo;
+    x = f * (x >> 16) + slot - lo;
+    return s;
+}
+
+// Word stream of one group of up to 32 lanes.
+struct GroupStream {
+    const uint8_t *w;
+    uint32_t n_words;
+    uint32_t ptr;
+    bool bad;
+};
+
+// Opens group g's stream (bounds-checked against the payload) and reads this lane's initial
+// state (hi word, lo word).  Returns false if the group table is inconsistent.
+__device__ __forceinline__ bool group_open(const uint8_t *bits, uint64_t grp_sec,
+                                           uint64_t pay_off, uint64_t pay_len, uint32_t G,
+                                           uint32_t g, int nl, int lane, GroupStream &gs,
+                                           uint32_t &x) {
+    const uint64_t *goff = reinterpret_cast<const uint64_t *>(bits + grp_sec);
+    const uint32_t *gw = reinterpret_cast<const uint32_t *>(bits + grp_sec + 8ull * (G + 1));
+    const uint64_t o = goff[g];
+    const uint32_t nw = gw[g];
+    const bool ok = (o <= pay_len) && (2ull * nw <= pay_len - o) &&
+                    (nw >= 2u * (uint32_t)nl) && (o % 16 == 0);
+    gs.w = bits + pay_off + (ok ? o : 0);
+    gs.n_words = ok ? nw : 0;
+    gs.ptr = 2u * (uint32_t)nl;
+    gs.bad = !ok;
+    x = 0x10000u;
+    if (ok && lane < nl) {
+        x = (ld_u16(gs.w + 4 * lane) << 16) | ld_u16(gs.w + 4 * lane + 2);
+        if (x < 0x10000u) gs.bad = true;
+    }
+    return ok;
+}
+
+// Renormalisation shared by the group: lanes whose state fell below 2^16 read the next
+// words in ascending lane order.  Reads past the group's words mark the stream bad.
+__device__ __forceinline__ void group_refill(GroupStream &gs, uint32_t &x, bool active) {
+    const bool need = active && x < 0x10000u;
+    const uint32_t mask = __ballot_sync(0xffffffffu, need);
+    if (need) {
+        const uint32_t idx = gs.ptr + __popc(mask & ((1u << (threadIdx.x & 31)) - 1u));
+        uint32_t w = 0;
+        if (idx < gs.n_words) w = ld_u16(gs.w + 2ull * idx); else gs.bad = true;
+        x = (x << 16) | w;
+    }
+    gs.ptr += __popc(mask);
+}
+
+}  // namespace sgs

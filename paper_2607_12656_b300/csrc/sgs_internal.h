@@ -1,0 +1,97 @@
+// Internal declarations of the sgs library (kernels, launchers, bitstream layout).
+// The bitstream layout (all little endian, every section 16-byte aligned):
+//   header (256 bytes): u32 magic "SGS1", version, mode, geo_mode, n_in, n_rows, depth,
+//     n_leaves, n_dup, n_chan, lanes, geo_lanes; u64 n_geo, n_geo_coded; u64 offsets of the
+//     ten sections below and the total length.
+//   levels   u32 n_level[D]                     nodes per octree level 0..D-1
+//   dup      {u32 rank, u32 extra}[n_dup]       leaf ranks holding extra Gaussians, ascending
+//   chan     f32 step[56], f32 offset[56], u32 bits[56]
+//   geo_raw  occupancy bytes of the uncoded levels, level order
+//   geo_tab  per coded level: 32-byte presence mask + (f-1) as u16 for present symbols,
+//            padded to 16 bytes (a level is coded iff geo_mode = RANS and n_level >= 4096)
+//   geo_grp  u64 group_off[G+1] (bytes from geo_pay), u32 group_words[G]   (G = ceil(Lg/32))
+//   geo_pay  rANS group streams
+//   attr_tab fixed: u64 chan_off[57] (bytes from attr_pay); static: 56 tables as geo_tab;
+//            learned: the frozen model (SGS_MODEL_BYTES)
+//   attr_grp as geo_grp with G = ceil(L/32)
+//   attr_pay payload
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sgs.h"
+
+namespace sgs {
+
+constexpr uint32_t kMagic = 0x31534753u;
+constexpr uint32_t kVersion = 1;
+constexpr int kNChan = 56;
+constexpr int kNSym = 256;
+constexpr uint32_t kGeoRansMinLevel = 4096;
+constexpr int kHeaderBytes = 256;
+constexpr int kMaxTables = kNChan + SGS_MAX_DEPTH;
+enum Sec { S_LEVELS = 0, S_DUP, S_CHAN, S_GEO_RAW, S_GEO_TAB, S_GEO_GRP, S_GEO_PAY, S_ATTR_TAB,
+           S_ATTR_GRP, S_ATTR_PAY, S_TOTAL };
+
+// Expanded static table in device memory: cdf[257] (u32) then bucket[256] (u8).
+constexpr int kTabCdfWords = 257;
+constexpr int kTabBytes = kTabCdfWords * 4 + 256 + 12;  // 1296, multiple of 16
+
+// Per-level facts of one scene's octree, by value in kernel parameters.
+struct GeoPlan {
+    int depth;
+    int n_coded_levels;
+    uint32_t n_level[SGS_MAX_DEPTH + 1];     // [D] = leaves
+    uint64_t level_off[SGS_MAX_DEPTH + 1];   // global BFS index of each level's first node
+    int coded_level[SGS_MAX_DEPTH];          // coded level ids, ascending
+    uint64_t coded_start[SGS_MAX_DEPTH + 1]; // prefix of coded symbols per coded level
+};
+
+// Scratch carve-out of one scene decode (device pointers).
+struct Scratch {
+    uint8_t *geo_bytes;     // n_geo (rANS geometry only)
+    uint32_t *chunk_prefix; // n_chunks + 1 popcount prefix per 64-byte chunk
+    uint64_t *scan_flags;   // look-back tile status
+    uint32_t *ticket;       // tile ticket counter (zeroed)
+    uint64_t *codes[2];     // packed (x:21 | y:21 | z:21) coordinates, ping-pong
+    uint8_t *tables;        // expanded static tables
+    uint32_t *dup_prefix;   // n_dup + 1
+    uint8_t *learned;       // learned-mode per-scene work area
+};
+
+size_t scratch_need(const sgs_scene_info &info, Scratch *layout, uint8_t *base);
+
+// Device status: kernels record the most severe error with atomicMin (codes are negative).
+__device__ __forceinline__ void set_status(int *status, int code) {
+    atomicMin(status, code);
+}
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_tables(const uint8_t *bits, uint64_t tab_off, uint64_t tab_end, int n_tab,
+                          uint8_t *tables, int allow_empty, int *status, cudaStream_t st);
+cudaError_t launch_rans_static_attr(const uint8_t *bits, const sgs_scene_info &info,
+                                    const uint8_t *tables, const sgs_scene_out &out, int *status,
+                                    cudaStream_t st);
+cudaError_t launch_rans_static_geo(const uint8_t *bits, const sgs_scene_info &info,
+                                   const GeoPlan &plan, const uint8_t *tables, uint8_t *geo_bytes,
+                                   int *status, cudaStream_t st);
+cudaError_t launch_geo_copy_raw(const uint8_t *bits, const sgs_scene_info &info,
+                                const GeoPlan &plan, uint8_t *geo_bytes, cudaStream_t st);
+cudaError_t launch_octree(const uint8_t *geo, const sgs_scene_info &info, const GeoPlan &plan,
+                          const uint8_t *bits, const Scratch &s, const sgs_scene_out &out,
+                          int *status, cudaStream_t st);
+cudaError_t launch_fixed(const uint8_t *bits, const sgs_scene_info &info,
+                         const sgs_scene_out &out, int *status, cudaStream_t st);
+cudaError_t launch_learned_decode(const uint8_t *bits, const sgs_scene_info &info,
+                                  const sgs_scene_out &out, uint8_t *work, int *status,
+                                  cudaStream_t st);
+size_t learned_work_bytes(const sgs_scene_info &info);
+
+// Encoder helper: f and cum of every token under a frozen model (device arrays).
+cudaError_t launch_learned_fc(const uint8_t *model_dev, const uint8_t *tokens_dev,
+                              uint32_t n_rows, uint32_t lanes, uint32_t *f_dev,
+                              uint32_t *cum_dev, cudaStream_t st);
+
+void make_geo_plan(const sgs_scene_info &info, GeoPlan *plan);
+
+}  // namespace sgs

@@ -1,0 +1,289 @@
+"""Python binding of libsgs.so (ctypes).  Argument marshalling only: every step of the decode
+path runs in the library's CUDA kernels; there is no Python or CPU fallback.  Names follow the
+C ABI in include/sgs.h.  Device buffers are passed as torch CUDA tensors or raw pointers;
+streams as torch.cuda.Stream, a raw cudaStream_t int, or None (the current torch stream)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, E_INVALID, E_CORRUPT, E_NOMEM, E_CUDA, E_TIMEOUT, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+MODE_FIXED, MODE_STATIC, MODE_LEARNED = 0, 1, 2
+GEO_RAW, GEO_RANS = 0, 1
+NCHAN = 56
+MAX_DEPTH = 21
+MODEL_BYTES = 36384
+WEIGHTS_FLOATS = 56 * 16 + 64 * 20 + 64 + 64 * 64 + 64 + 256 * 64 + 256
+
+u32, u64, i32, P = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
+
+
+class SceneInfo(ctypes.Structure):
+    _fields_ = [("mode", u32), ("geo_mode", u32), ("n_in", u32), ("n_rows", u32), ("depth", u32),
+                ("n_leaves", u32), ("n_dup", u32), ("lanes", u32), ("geo_lanes", u32),
+                ("n_level", u32 * (MAX_DEPTH + 1)), ("n_geo", u64), ("n_geo_coded", u64),
+                ("off", u64 * 11), ("total_len", u64), ("scratch_bytes", u64)]
+
+
+class SceneOut(ctypes.Structure):
+    _fields_ = [("attr", P), ("pos", P), ("coord", P), ("out_index", P)]
+
+
+class EncodeParams(ctypes.Structure):
+    _fields_ = [("mode", u32), ("geo_mode", u32), ("depth", u32), ("lanes", u32), ("geo_lanes", u32),
+                ("bits", u32 * NCHAN), ("model", P)]
+
+
+class TrainParams(ctypes.Structure):
+    _fields_ = [("steps", u32), ("batch", u32), ("seed", u32), ("lr", ctypes.c_float)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("bits_dev", P), ("info", SceneInfo), ("out", SceneOut)]
+
+
+class SgsError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__("%s: %s (%d)" % (what, lib().sgs_strerror(code).decode(), code))
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libsgs.so (building it first if the sources are newer).  Raises if it cannot."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path) or _build.needs_build():
+            path = _build.build()
+        L = ctypes.CDLL(path)
+        L.sgs_strerror.restype = ctypes.c_char_p
+        L.sgs_strerror.argtypes = [i32]
+        L.sgs_create.argtypes = [ctypes.POINTER(P), i32, ctypes.c_size_t]
+        L.sgs_reserve.argtypes = [P, ctypes.c_size_t]
+        L.sgs_destroy.argtypes = [P]
+        L.sgs_destroy.restype = None
+        L.sgs_sync.argtypes = [P, P]
+        L.scene_query.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(SceneInfo)]
+        L.scene_decode.argtypes = [P, P, ctypes.POINTER(SceneInfo), ctypes.POINTER(SceneOut), P]
+        L.scene_decode_batch.argtypes = [P, ctypes.POINTER(BatchItem), i32, P]
+        L.scene_encode.argtypes = [P, P, P, u32, ctypes.POINTER(EncodeParams), P, ctypes.c_size_t,
+                                   ctypes.POINTER(ctypes.c_size_t)]
+        L.scene_tokens.argtypes = [P, P, u32, u32, P, ctypes.c_size_t, ctypes.POINTER(u32)]
+        L.sgs_train.argtypes = [P, P, u32, u32, ctypes.POINTER(TrainParams), u32, P, P, P]
+        L.sgs_train_grad.argtypes = [P, P, u32, u32, P, u32, P, P, ctypes.POINTER(ctypes.c_float)]
+        L.sgs_freeze.argtypes = [P, P, u32, u32, u32, P]
+        L.sgs_profile.argtypes = [P, i32]
+        L.sgs_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_float), i32]
+        L.sgs_launch_count.argtypes = [P]
+        L.sgs_launch_count.restype = u64
+        _lib = L
+    return _lib
+
+
+def _check(code: int, what: str) -> int:
+    if code != OK:
+        raise SgsError(code, what)
+    return code
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    raise TypeError("expected a tensor, array or pointer")
+
+
+def _stream(s) -> int:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ----------------------------------------------------------------------------- context
+
+class Context:
+    """Owns an sgs_ctx (device scratch, status word) on one CUDA device."""
+
+    def __init__(self, device: int = 0, scratch_bytes: int = 0):
+        h = P()
+        _check(lib().sgs_create(ctypes.byref(h), device, scratch_bytes), "sgs_create")
+        self.handle = h
+        self.device = device
+        self.scratch_bytes = scratch_bytes
+
+    def reserve(self, nbytes: int) -> None:
+        if nbytes > self.scratch_bytes:
+            _check(lib().sgs_reserve(self.handle, nbytes), "sgs_reserve")
+            self.scratch_bytes = nbytes
+
+    def sync(self, stream=None) -> int:
+        """Waits for the stream; returns (and clears) the worst device status since last sync."""
+        return lib().sgs_sync(self.handle, _stream(stream))
+
+    def profile(self, enable: bool = True) -> None:
+        _check(lib().sgs_profile(self.handle, int(enable)), "sgs_profile")
+
+    def profile_read(self) -> list:
+        """[geometry tokens, octree + positions, attributes] ms of the last profiled decode."""
+        ms = (ctypes.c_float * 3)()
+        _check(lib().sgs_profile_read(self.handle, ms, 3), "sgs_profile_read")
+        return [float(v) for v in ms]
+
+    def launch_count(self) -> int:
+        return int(lib().sgs_launch_count(self.handle))
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lib().sgs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sgs_create(device: int = 0, scratch_bytes: int = 0) -> Context:
+    return Context(device, scratch_bytes)
+
+
+def sgs_sync(ctx: Context, stream=None) -> int:
+    return ctx.sync(stream)
+
+
+# ----------------------------------------------------------------------------- decode
+
+def scene_query(bits: bytes) -> SceneInfo:
+    info = SceneInfo()
+    buf = np.frombuffer(bits, np.uint8)
+    _check(lib().scene_query(buf.ctypes.data, len(bits), ctypes.byref(info)), "scene_query")
+    return info
+
+
+def _out(attr, pos, coord=None, out_index=None) -> SceneOut:
+    return SceneOut(_ptr(attr), _ptr(pos), _ptr(coord), _ptr(out_index))
+
+
+def scene_decode(ctx: Context, bits_dev, info: SceneInfo, attr, pos, coord=None, out_index=None,
+                 stream=None) -> None:
+    """Enqueues the decode of one scene (bits_dev: device uint8 tensor of the bitstream)."""
+    out = _out(attr, pos, coord, out_index)
+    _check(lib().scene_decode(ctx.handle, _ptr(bits_dev), ctypes.byref(info), ctypes.byref(out),
+                              _stream(stream)), "scene_decode")
+
+
+def scene_decode_batch(ctx: Context, items: list, stream=None) -> None:
+    """items: (bits_dev, info, attr, pos[, coord[, out_index]]) tuples."""
+    arr = (BatchItem * max(len(items), 1))()
+    for i, it in enumerate(items):
+        bits_dev, info, attr, pos = it[:4]
+        coord = it[4] if len(it) > 4 else None
+        oidx = it[5] if len(it) > 5 else None
+        arr[i].bits_dev = _ptr(bits_dev)
+        arr[i].info = info
+        arr[i].out = _out(attr, pos, coord, oidx)
+    _check(lib().scene_decode_batch(ctx.handle, arr, len(items), _stream(stream)), "scene_decode_batch")
+
+
+# ----------------------------------------------------------------------------- encode
+
+def scene_encode(pos: np.ndarray, attr: np.ndarray, *, mode: int, depth: int, lanes: int = 32,
+                 geo_mode: int = GEO_RANS, geo_lanes: int = 0, bits=8, model: bytes | None = None,
+                 ctx: Context | None = None) -> bytes:
+    pos = np.ascontiguousarray(pos, np.float32)
+    attr = np.ascontiguousarray(attr, np.float32)
+    n = pos.shape[1]
+    assert pos.shape == (3, n) and attr.shape == (NCHAN, n)
+    prm = EncodeParams()
+    prm.mode, prm.geo_mode, prm.depth, prm.lanes, prm.geo_lanes = mode, geo_mode, depth, lanes, geo_lanes
+    b = np.broadcast_to(np.asarray(bits, np.uint32), (NCHAN,))
+    for c in range(NCHAN):
+        prm.bits[c] = int(b[c])
+    mbuf = None
+    if model is not None:
+        mbuf = np.frombuffer(bytes(model), np.uint8).copy()
+        assert mbuf.size == MODEL_BYTES
+        prm.model = mbuf.ctypes.data
+    need = ctypes.c_size_t(0)
+    h = ctx.handle if ctx is not None else None
+    code = lib().scene_encode(h, pos.ctypes.data, attr.ctypes.data, n, ctypes.byref(prm), None, 0,
+                              ctypes.byref(need))
+    if code not in (OK, E_INVALID) or need.value == 0:
+        _check(code, "scene_encode")
+    out = np.zeros(need.value, np.uint8)
+    _check(lib().scene_encode(h, pos.ctypes.data, attr.ctypes.data, n, ctypes.byref(prm),
+                              out.ctypes.data, out.size, ctypes.byref(need)), "scene_encode")
+    return out.tobytes()
+
+
+def scene_tokens(pos: np.ndarray, attr: np.ndarray, depth: int) -> np.ndarray:
+    """uint8 [n_rows][56] quantized tokens, rows in Morton order (8-bit channels)."""
+    pos = np.ascontiguousarray(pos, np.float32)
+    attr = np.ascontiguousarray(attr, np.float32)
+    n = pos.shape[1]
+    tok = np.zeros((n, NCHAN), np.uint8)
+    nr = u32(0)
+    _check(lib().scene_tokens(pos.ctypes.data, attr.ctypes.data, n, depth, tok.ctypes.data, tok.size,
+                              ctypes.byref(nr)), "scene_tokens")
+    return tok[: nr.value].copy()
+
+
+# ----------------------------------------------------------------------------- learned part
+
+def sgs_train(ctx: Context, tokens_dev, n_rows: int, lanes: int, weights_dev, adam_dev, *, steps: int,
+              batch: int = 65536, seed: int = 0, lr: float = 1e-3, step0: int = 0, loss_dev=None) -> None:
+    prm = TrainParams(steps, batch, seed, lr)
+    _check(lib().sgs_train(ctx.handle, _ptr(tokens_dev), n_rows, lanes, ctypes.byref(prm), step0,
+                           _ptr(weights_dev), _ptr(adam_dev), _ptr(loss_dev)), "sgs_train")
+
+
+def sgs_train_grad(ctx: Context, tokens_dev, n_rows: int, lanes: int, pos_dev, weights_dev, grad_dev) -> float:
+    loss = ctypes.c_float(0)
+    n = int(pos_dev.numel()) if hasattr(pos_dev, "numel") else len(pos_dev)
+    _check(lib().sgs_train_grad(ctx.handle, _ptr(tokens_dev), n_rows, lanes, _ptr(pos_dev), n,
+                                _ptr(weights_dev), _ptr(grad_dev), ctypes.byref(loss)), "sgs_train_grad")
+    return float(loss.value)
+
+
+def sgs_freeze(weights: np.ndarray, tokens: np.ndarray, lanes: int, seed: int) -> bytes:
+    w = np.ascontiguousarray(weights, np.float32)
+    assert w.size == WEIGHTS_FLOATS
+    t = np.ascontiguousarray(tokens, np.uint8)
+    out = np.zeros(MODEL_BYTES, np.uint8)
+    _check(lib().sgs_freeze(w.ctypes.data, t.ctypes.data, t.shape[0], lanes, seed, out.ctypes.data),
+           "sgs_freeze")
+    return out.tobytes()
+
+
+WEIGHT_SHAPES = [("emb", (56, 16)), ("w1", (64, 20)), ("b1", (64,)), ("w2", (64, 64)), ("b2", (64,)),
+                 ("w3", (256, 64)), ("b3", (256,))]
+
+
+def pack_weights(d: dict) -> np.ndarray:
+    return np.concatenate([np.asarray(d[k], np.float32).reshape(-1) for k, _ in WEIGHT_SHAPES])
+
+
+def unpack_weights(flat: np.ndarray) -> dict:
+    out, o = {}, 0
+    for k, shp in WEIGHT_SHAPES:
+        n = int(np.prod(shp))
+        out[k] = np.asarray(flat[o:o + n], np.float32).reshape(shp)
+        o += n
+    return out

@@ -1,0 +1,90 @@
+"""Host-side checks of the C-ABI library (no GPU needed): every declared symbol is exported,
+the library's encoder emits the oracle's bytes, scene_query agrees with the oracle's header
+parse and rejects malformed headers."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import scene as S
+from paper_2607_12656_b300 import sgs
+from paper_2607_12656_b300.scenegen import fixed_bits, make_scene
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    L = sgs.lib()
+    names = _declared_functions()
+    assert "scene_decode" in names and "scene_encode" in names and len(names) >= 12
+    for n in names:
+        assert hasattr(L, n), n
+        assert ctypes.cast(getattr(L, n), ctypes.c_void_p).value
+
+
+CASES = [(0, 3, 8), (1, 1, 8), (5, 2, 8), (33, 4, 8), (1500, 7, 8), (6000, 12, 8)]
+
+
+@pytest.mark.parametrize("n,depth,lanes", CASES)
+@pytest.mark.parametrize("mode", [S.MODE_FIXED, S.MODE_STATIC])
+@pytest.mark.parametrize("geo", [S.GEO_RAW, S.GEO_RANS])
+def test_encoder_bytes_match_oracle(n, depth, lanes, mode, geo):
+    sc = make_scene(n, 7 + n)
+    bits = fixed_bits(n) if mode == S.MODE_FIXED else 8
+    want = S.encode(sc.pos, sc.attr, mode=mode, depth=depth, bits=bits, lanes=lanes + 25, geo_mode=geo)
+    got = sgs.scene_encode(sc.pos, sc.attr, mode=mode, depth=depth, bits=bits, lanes=lanes + 25, geo_mode=geo)
+    assert got == want
+
+
+def test_encoder_bytes_match_oracle_geometry_coded(small_scene):
+    for geo_lanes in (0, 33, 96):
+        want = S.encode(small_scene.pos, small_scene.attr, mode=S.MODE_STATIC, depth=12, lanes=32,
+                        geo_mode=S.GEO_RANS, geo_lanes=geo_lanes)
+        got = sgs.scene_encode(small_scene.pos, small_scene.attr, mode=sgs.MODE_STATIC, depth=12, lanes=32,
+                               geo_mode=sgs.GEO_RANS, geo_lanes=geo_lanes)
+        assert got == want
+
+
+def test_tokens_match_oracle(small_scene):
+    P = S.prepare(small_scene.pos, small_scene.attr, 12, 8)
+    assert np.array_equal(sgs.scene_tokens(small_scene.pos, small_scene.attr, 12), P.q.astype(np.uint8))
+
+
+def test_query_matches_oracle_header(small_scene):
+    buf = S.encode(small_scene.pos, small_scene.attr, mode=S.MODE_STATIC, depth=12, lanes=32)
+    h = S.parse_header(buf)
+    info = sgs.scene_query(buf)
+    for k in ("mode", "geo_mode", "n_rows", "depth", "n_leaves", "n_dup", "lanes", "geo_lanes", "n_geo",
+              "n_geo_coded"):
+        assert getattr(info, k) == h[k], k
+    assert info.total_len == len(buf) and info.scratch_bytes > 0
+    P = S.prepare(small_scene.pos, small_scene.attr, 12, 8)
+    assert [info.n_level[l] for l in range(12)] == [len(b) for b in P.levels]
+
+
+def test_query_rejects_malformed(small_scene):
+    buf = bytearray(S.encode(small_scene.pos, small_scene.attr, mode=S.MODE_FIXED, depth=12,
+                             bits=fixed_bits(1)))
+    for off, val in [(0, 0), (4, 9), (8, 7), (24, 0), (24, 40), (36, 55), (64, 255)]:
+        b = bytearray(buf)
+        b[off:off + 4] = int(val).to_bytes(4, "little")
+        with pytest.raises(sgs.SgsError):
+            sgs.scene_query(bytes(b))
+    with pytest.raises(sgs.SgsError):
+        sgs.scene_query(bytes(buf[:-16]))  # total length mismatch
+    with pytest.raises(sgs.SgsError):
+        sgs.scene_query(bytes(buf[:100]))

@@ -1,0 +1,173 @@
+"""GPU parity: the CUDA decode path (through the C ABI) against the CPU oracle, bit for bit.
+
+Decoded values must be identical: fp32 attributes compared as bit patterns (0 ULP), positions
+and voxel coordinates exactly.  Outputs are poisoned (NaN / 0xFFFFFFFF) before each decode so
+an unwritten row fails the comparison."""
+import numpy as np
+import pytest
+
+from oracle import scene as S
+from paper_2607_12656_b300 import sgs
+from paper_2607_12656_b300.scenegen import fixed_bits, make_scene
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = sgs.Context(0, 1 << 20)
+    yield c
+    c.close()
+
+
+def gpu_decode(ctx, buf, out_index=None):
+    info = sgs.scene_query(buf)
+    ctx.reserve(info.scratch_bytes)
+    bits = torch.frombuffer(bytearray(buf), dtype=torch.uint8).cuda()
+    n = info.n_rows
+    attr = torch.full((56, max(n, 1)), float("nan"), device="cuda")
+    pos = torch.full((3, max(n, 1)), float("nan"), device="cuda")
+    crd = torch.full((3, max(n, 1)), -1, dtype=torch.int32, device="cuda")
+    oi = None if out_index is None else torch.from_numpy(out_index.astype(np.int32)).cuda()
+    sgs.scene_decode(ctx, bits, info, attr, pos, crd, oi)
+    st = ctx.sync()
+    return (st, attr.cpu().numpy()[:, :n], pos.cpu().numpy()[:, :n],
+            crd.cpu().numpy()[:, :n].view(np.uint32), info)
+
+
+def same_bits(a, b):
+    return a.shape == b.shape and np.array_equal(np.ascontiguousarray(a).view(np.uint32),
+                                                 np.ascontiguousarray(b).view(np.uint32))
+
+
+def check(ctx, sc, depth, **kw):
+    mode = kw["mode"]
+    bits = kw.pop("bits", 8)
+    P = S.prepare(sc.pos, sc.attr, depth, bits)
+    buf = S.encode(sc.pos, sc.attr, depth=depth, bits=bits, prep=P, **kw)
+    st, attr, pos, crd, info = gpu_decode(ctx, buf)
+    assert st == sgs.OK, sgs.lib().sgs_strerror(st)
+    assert same_bits(attr, P.attr), "attributes differ"
+    assert same_bits(pos, P.pos), "positions differ"
+    assert np.array_equal(crd, P.coord), "coordinates differ"
+    return P, buf
+
+
+SIZES = [(0, 3), (1, 1), (2, 5), (7, 2), (33, 4), (1000, 12), (20000, 12), (60000, 14)]
+
+
+@pytest.mark.parametrize("n,depth", SIZES)
+@pytest.mark.parametrize("geo", [S.GEO_RAW, S.GEO_RANS])
+def test_fixed_parity(ctx, n, depth, geo):
+    check(ctx, make_scene(n, 11 + n), depth, mode=S.MODE_FIXED, bits=fixed_bits(n), geo_mode=geo)
+
+
+@pytest.mark.parametrize("n,depth", SIZES)
+@pytest.mark.parametrize("lanes", [1, 31, 33, 100])
+def test_static_parity(ctx, n, depth, lanes):
+    check(ctx, make_scene(n, 13 + n), depth, mode=S.MODE_STATIC, lanes=lanes, geo_mode=S.GEO_RANS)
+
+
+def test_fixed_all_widths(ctx):
+    sc = make_scene(5000, 3)
+    for b in (1, 2, 3, 7, 9, 11, 12, 13, 15, 16):
+        check(ctx, sc, 10, mode=S.MODE_FIXED, bits=b, geo_mode=S.GEO_RAW)
+
+
+def test_duplicates(ctx):
+    """Coarse grid: many Gaussians share a voxel; one position per voxel plus counts."""
+    sc = make_scene(4000, 5)
+    P, _ = check(ctx, sc, 3, mode=S.MODE_STATIC, lanes=40, geo_mode=S.GEO_RAW)
+    assert len(P.dups) > 10
+    check(ctx, sc, 2, mode=S.MODE_FIXED, bits=fixed_bits(2), geo_mode=S.GEO_RAW)
+
+
+def test_geometry_lane_counts(ctx, small_scene):
+    for gl in (1, 32, 33, 200, 4000):
+        check(ctx, small_scene, 12, mode=S.MODE_STATIC, lanes=64, geo_mode=S.GEO_RANS, geo_lanes=gl)
+
+
+def test_out_index_scatter(ctx, small_scene):
+    P = S.prepare(small_scene.pos, small_scene.attr, 12, 8)
+    buf = S.encode(None, None, mode=S.MODE_STATIC, depth=12, lanes=64, prep=P)
+    perm = np.random.default_rng(0).permutation(P.n_rows)
+    st, attr, pos, crd, _ = gpu_decode(ctx, buf, out_index=perm)
+    assert st == sgs.OK
+    want_attr = np.empty_like(P.attr)
+    want_attr[:, perm] = P.attr
+    want_pos = np.empty_like(P.pos)
+    want_pos[:, perm] = P.pos
+    assert same_bits(attr, want_attr) and same_bits(pos, want_pos)
+
+
+def test_library_encoder_roundtrip_on_gpu(ctx, small_scene):
+    """The library's own encoder -> GPU decode equals the oracle's decoded values."""
+    P = S.prepare(small_scene.pos, small_scene.attr, 12, 8)
+    buf = sgs.scene_encode(small_scene.pos, small_scene.attr, mode=sgs.MODE_STATIC, depth=12, lanes=96)
+    st, attr, pos, _, _ = gpu_decode(ctx, buf)
+    assert st == sgs.OK and same_bits(attr, P.attr) and same_bits(pos, P.pos)
+
+
+def test_scratch_too_small_is_refused():
+    c = sgs.Context(0, 0)
+    sc = make_scene(1000, 1)
+    buf = S.encode(sc.pos, sc.attr, mode=S.MODE_FIXED, depth=10, bits=fixed_bits(1))
+    info = sgs.scene_query(buf)
+    bits = torch.frombuffer(bytearray(buf), dtype=torch.uint8).cuda()
+    attr = torch.zeros((56, info.n_rows), device="cuda")
+    pos = torch.zeros((3, info.n_rows), device="cuda")
+    with pytest.raises(sgs.SgsError) as e:
+        sgs.scene_decode(c, bits, info, attr, pos)
+    assert e.value.code == sgs.E_NOMEM
+    c.close()
+
+
+def test_corrupt_payload_detected(ctx, small_scene):
+    """Bit flips in the coded payloads: the decoder reports CORRUPT or decodes different
+    tokens; it never reads or writes out of bounds (all accesses are checked)."""
+    P = S.prepare(small_scene.pos, small_scene.attr, 12, 8)
+    buf = S.encode(None, None, mode=S.MODE_STATIC, depth=12, lanes=64, prep=P)
+    h = S.parse_header(buf)
+    rng = np.random.default_rng(1)
+    flagged = 0
+    for trial in range(12):
+        b = bytearray(buf)
+        sec = ("attr_pay", "geo_pay")[trial % 2]
+        lo = h["off_" + sec]
+        hi = h["total"] if sec == "attr_pay" else h["off_attr_tab"]
+        k = int(rng.integers(lo, hi))
+        b[k] ^= 1 << int(rng.integers(0, 8))
+        st, attr, pos, _, _ = gpu_decode(ctx, bytes(b))
+        if st == sgs.E_CORRUPT:
+            flagged += 1
+        else:
+            assert st == sgs.OK and not (same_bits(attr, P.attr) and same_bits(pos, P.pos))
+    assert flagged >= 6
+
+
+@pytest.fixture(scope="module")
+def fixed_1m():
+    sc = make_scene(1_000_000, 1000)
+    bits = fixed_bits(1000)
+    P = S.prepare(sc.pos, sc.attr, 16, bits)
+    return sc, P, bits
+
+
+def test_full_size_fixed_length_scene(ctx, fixed_1m):
+    """The 1M-Gaussian fixed-length workload, every output compared."""
+    sc, P, bits = fixed_1m
+    buf = sgs.scene_encode(sc.pos, sc.attr, mode=sgs.MODE_FIXED, depth=16, bits=bits, geo_mode=sgs.GEO_RAW)
+    assert buf == S.encode(None, None, mode=S.MODE_FIXED, depth=16, bits=bits, geo_mode=S.GEO_RAW, prep=P)
+    st, attr, pos, crd, _ = gpu_decode(ctx, buf)
+    assert st == sgs.OK and same_bits(attr, P.attr) and same_bits(pos, P.pos)
+    assert np.array_equal(crd, P.coord)
+
+
+def test_full_size_static_scene(ctx, fixed_1m):
+    sc, _, _ = fixed_1m
+    P = S.prepare(sc.pos, sc.attr, 16, 8)
+    for lanes in (4096, 65536):
+        buf = sgs.scene_encode(sc.pos, sc.attr, mode=sgs.MODE_STATIC, depth=16, lanes=lanes, geo_mode=sgs.GEO_RANS)
+        st, attr, pos, _, _ = gpu_decode(ctx, buf)
+        assert st == sgs.OK and same_bits(attr, P.attr) and same_bits(pos, P.pos)
