@@ -1,0 +1,28 @@
+"""The learned part end to end: train the context model on a scene's own tokens with the
+library's GPU training kernels, then freeze it to the integer model the bitstream carries
+(Sec. 3.4.2; training loss = attribute rate of Eq. 9 in bits per token)."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import sgs
+from .scenegen import kaiming_init
+
+
+def train_and_freeze(ctx: sgs.Context, scene, depth: int, lanes: int, *, steps: int = 2000,
+                     batch: int = 65536, seed: int = 1, lr: float = 1e-3, init_seed: int = 1,
+                     return_losses: bool = False):
+    import torch
+    tokens = sgs.scene_tokens(scene.pos, scene.attr, depth)
+    dev = torch.device("cuda", ctx.device)
+    tok_dev = torch.from_numpy(tokens).to(dev)
+    w = torch.from_numpy(sgs.pack_weights(kaiming_init(init_seed))).to(dev)
+    adam = torch.zeros(2 * sgs.WEIGHTS_FLOATS, dtype=torch.float32, device=dev)
+    losses = torch.zeros(max(steps, 1), dtype=torch.float32, device=dev)
+    sgs.sgs_train(ctx, tok_dev, tokens.shape[0], lanes, w, adam, steps=steps, batch=batch, seed=seed,
+                  lr=lr, loss_dev=losses)
+    weights = w.cpu().numpy()
+    model = sgs.sgs_freeze(weights, tokens, lanes, seed)
+    if return_losses:
+        return model, weights, losses.cpu().numpy()[:steps]
+    return model

@@ -1,0 +1,163 @@
+"""Continuous-batching decode server on one GPU.
+
+Requests (scene bitstreams with arrival times) are admitted as soon as a slot and HBM budget
+are free: admission charges each request its device footprint (bitstream + decoded outputs +
+decode scratch) against the budget.  Each slot owns a CUDA stream and a library context (its
+own scratch and status word), so admitted decodes overlap on the device while the host loop
+keeps admitting and retiring.  Latency = completion event time - arrival time.
+
+Only orchestration lives here; every decode runs in the library's kernels through
+``scene_decode``.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+from . import sgs
+
+
+@dataclasses.dataclass
+class Scene:
+    """A coded scene held in pinned host memory."""
+    bits: bytes
+    info: sgs.SceneInfo = None
+    host: object = None  # pinned uint8 tensor
+
+    def __post_init__(self):
+        import torch
+        if self.info is None:
+            self.info = sgs.scene_query(self.bits)
+        if self.host is None:
+            self.host = torch.frombuffer(bytearray(self.bits), dtype=torch.uint8).pin_memory()
+
+    @property
+    def n_rows(self) -> int:
+        return int(self.info.n_rows)
+
+    def footprint(self) -> int:
+        return int(self.info.total_len) + 4 * 59 * self.n_rows + int(self.info.scratch_bytes)
+
+
+@dataclasses.dataclass
+class Result:
+    req: int
+    scene: int
+    arrival: float
+    admitted: float
+    done: float
+    status: int
+    attr: object = None
+    pos: object = None
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+class _Slot:
+    def __init__(self, device: int, scratch: int):
+        import torch
+        self.stream = torch.cuda.Stream(device=device)
+        self.ctx = sgs.Context(device, scratch)
+        self.busy = None  # (req, scene_id, arrival, admitted, ev_start, ev_end, bufs)
+
+
+class DecodeServer:
+    def __init__(self, scenes: list[Scene], *, slots: int = 8, hbm_budget: int = 120 << 30,
+                 device: int = 0, keep_outputs: bool = False):
+        import torch
+        self.torch = torch
+        self.scenes = scenes
+        self.device = device
+        self.budget = hbm_budget
+        self.keep = keep_outputs
+        scratch = max(s.info.scratch_bytes for s in scenes)
+        self.slots = [_Slot(device, scratch) for _ in range(slots)]
+        self.in_use = 0
+
+    def _launch(self, slot: _Slot, req: int, sid: int, arrival: float, now: float):
+        torch = self.torch
+        sc = self.scenes[sid]
+        dev = torch.device("cuda", self.device)
+        with torch.cuda.stream(slot.stream):
+            bits = torch.empty(len(sc.bits), dtype=torch.uint8, device=dev)
+            attr = torch.empty((56, max(sc.n_rows, 1)), device=dev)
+            pos = torch.empty((3, max(sc.n_rows, 1)), device=dev)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(slot.stream)
+            bits.copy_(sc.host, non_blocking=True)
+            sgs.scene_decode(slot.ctx, bits, sc.info, attr, pos, None, None, slot.stream)
+            ev1.record(slot.stream)
+        slot.busy = (req, sid, arrival, now, ev0, ev1, (bits, attr, pos))
+        self.in_use += sc.footprint()
+
+    def run(self, requests: list[tuple[float, int]]) -> list[Result]:
+        """requests: (arrival offset in s, scene index), sorted by arrival.  Returns results in
+        completion order."""
+        pending = collections.deque((i, t, s) for i, (t, s) in enumerate(requests))
+        queue = collections.deque()
+        results = []
+        t0 = time.perf_counter()
+        while pending or queue or any(sl.busy for sl in self.slots):
+            now = time.perf_counter() - t0
+            while pending and pending[0][1] <= now:
+                queue.append(pending.popleft())
+            # retire finished decodes
+            for sl in self.slots:
+                if sl.busy and sl.busy[5].query():
+                    req, sid, arr, adm, ev0, ev1, bufs = sl.busy
+                    st = sl.ctx.sync(sl.stream)
+                    done = time.perf_counter() - t0
+                    r = Result(req, sid, arr, adm, done, st)
+                    if self.keep:
+                        r.attr, r.pos = bufs[1][:, :self.scenes[sid].n_rows].cpu(), bufs[2][:, :self.scenes[sid].n_rows].cpu()
+                    results.append(r)
+                    self.in_use -= self.scenes[sid].footprint()
+                    sl.busy = None
+            # admit in arrival order while a slot and memory are free
+            while queue:
+                free = [sl for sl in self.slots if sl.busy is None]
+                req, arr, sid = queue[0]
+                if not free or self.in_use + self.scenes[sid].footprint() > self.budget:
+                    break
+                queue.popleft()
+                self._launch(free[0], req, sid, arr, time.perf_counter() - t0)
+            if not queue and pending:
+                wait = pending[0][1] - (time.perf_counter() - t0)
+                if wait > 0 and not any(sl.busy for sl in self.slots):
+                    time.sleep(min(wait, 0.002))
+        return results
+
+    def close(self):
+        for sl in self.slots:
+            sl.ctx.close()
+
+
+def poisson_arrivals(rate: float, n: int, n_scenes: int, seed: int) -> list[tuple[float, int]]:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate, size=n)
+    t = np.cumsum(gaps)
+    which = rng.integers(0, n_scenes, size=n)
+    return [(float(a), int(b)) for a, b in zip(t, which)]
+
+
+def summarize(results: list[Result], scenes: list[Scene], modes: dict | None = None) -> dict:
+    lat = np.array([r.latency for r in results]) * 1e3
+    span = max(r.done for r in results) - min(r.arrival for r in results)
+    out = {"requests": len(results), "p50_ms": float(np.percentile(lat, 50)),
+           "p99_ms": float(np.percentile(lat, 99)),
+           "gaussians_per_s": sum(scenes[r.scene].n_rows for r in results) / span,
+           "bad_status": sum(1 for r in results if r.status != sgs.OK)}
+    if modes:
+        for name, ids in modes.items():
+            sel = [r for r in results if r.scene in ids]
+            if sel:
+                l2 = np.array([r.latency for r in sel]) * 1e3
+                out[name] = {"requests": len(sel), "p50_ms": float(np.percentile(l2, 50)),
+                             "p99_ms": float(np.percentile(l2, 99))}
+    return out

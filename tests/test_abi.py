@@ -88,3 +88,25 @@ def test_query_rejects_malformed(small_scene):
         sgs.scene_query(bytes(buf[:-16]))  # total length mismatch
     with pytest.raises(sgs.SgsError):
         sgs.scene_query(bytes(buf[:100]))
+
+
+def test_library_exp2q_table_matches_oracle():
+    from oracle.exp2q import exp2q_table
+    text = open(os.path.join(ROOT, "paper_2607_12656_b300", "csrc", "exp2q_table.h")).read()
+    vals = [int(v) for v in re.findall(r"(\d+)u", text)]
+    assert vals == list(exp2q_table())
+
+
+def test_freeze_matches_oracle(small_scene):
+    """Given the same fp32 weights and tokens, the library's freeze emits the oracle's model."""
+    from oracle import model as M
+    from paper_2607_12656_b300.scenegen import kaiming_init
+    P = S.prepare(small_scene.pos, small_scene.attr, 12, 8)
+    q = P.q.astype(np.uint8)
+    for lanes, seed, wseed in ((32, 3, 1), (7, 11, 2), (4096, 5, 3)):
+        w = kaiming_init(wseed)
+        rng = np.random.default_rng(wseed)
+        w = {k: (v + 0.05 * rng.standard_normal(v.shape)).astype(np.float32) for k, v in w.items()}
+        want = S.model_bytes(M.freeze(w, q, S.lane_bounds(P.n_rows, lanes), seed))
+        got = sgs.sgs_freeze(sgs.pack_weights(w), q, lanes, seed)
+        assert got == want
