@@ -136,8 +136,9 @@ int sgs_profile(sgs_ctx *ctx, int enable);
 
 /* Stage times in ms of the most recent profiled single-scene decode (after the stream has
  * completed it): ms[0] geometry tokens (table expansion, raw copy, rANS), ms[1] octree
- * expansion and positions, ms[2] attribute decode and dequantization.  cap >= 3.
- * Errors: SGS_E_INVALID (no profiled decode), SGS_E_CUDA.                                  */
+ * expansion and positions, ms[2] attribute decode and dequantization (measured on the
+ * context's attribute stream, where it runs concurrently with ms[0] and ms[1]), ms[3] the
+ * whole decode.  cap >= 4.  Errors: SGS_E_INVALID (no profiled decode), SGS_E_CUDA.         */
 int sgs_profile_read(sgs_ctx *ctx, float *ms, int cap);
 
 /* Number of CUDA kernels enqueued by decode calls on this context since its creation. */

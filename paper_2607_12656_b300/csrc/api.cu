@@ -21,7 +21,10 @@ struct sgs_ctx {
     uint64_t launches; // kernels launched by decode calls on this context
     int profile;       // record stage events in decode calls
     int n_marks;
-    cudaEvent_t marks[kMaxStages + 1];
+    cudaEvent_t marks[kMaxStages + 1];  // caller's stream: start, tokens, octree, end
+    cudaEvent_t amarks[2];              // attribute stream: start, end
+    cudaStream_t aux;                   // attribute decode runs here, forked from the caller
+    cudaEvent_t fork, join;
 };
 
 namespace sgs {
@@ -29,6 +32,8 @@ namespace sgs {
 size_t octree_scan_tiles(uint64_t n_geo);
 int octree_launches(const sgs_scene_info &info, const GeoPlan &plan);
 size_t octree_chunks(uint64_t n_geo);
+void octree_code_buffers(const sgs_scene_info &info, const GeoPlan &plan, uint64_t *pingpong,
+                         uint64_t *all);
 
 static inline uint64_t a256(uint64_t x) { return (x + 255) & ~255ull; }
 
@@ -63,12 +68,6 @@ void make_geo_plan(const sgs_scene_info &info, GeoPlan *plan) {
     plan->coded_start[k] = coded;
 }
 
-static uint64_t max_level_nodes(const sgs_scene_info &info) {
-    uint64_t m = 1;
-    for (uint32_t l = 0; l < info.depth; ++l) m = std::max<uint64_t>(m, info.n_level[l]);
-    return m;
-}
-
 // Carves the scratch regions of one decode out of `base` (or only sizes them if base is
 // NULL).  Returns the total size.
 size_t scratch_need(const sgs_scene_info &info, Scratch *s, uint8_t *base) {
@@ -85,9 +84,11 @@ size_t scratch_need(const sgs_scene_info &info, Scratch *s, uint8_t *base) {
     t.chunk_prefix = reinterpret_cast<uint32_t *>(take(4 * (octree_chunks(info.n_geo) + 1)));
     t.scan_flags = reinterpret_cast<uint64_t *>(take(8 * (octree_scan_tiles(info.n_geo) + 1)));
     t.ticket = reinterpret_cast<uint32_t *>(take(256));
-    const uint64_t ml = max_level_nodes(info);
-    t.codes[0] = reinterpret_cast<uint64_t *>(take(8 * ml));
-    t.codes[1] = reinterpret_cast<uint64_t *>(take(8 * ml));
+    uint64_t pp, all;
+    octree_code_buffers(info, plan, &pp, &all);
+    t.codes[0] = reinterpret_cast<uint64_t *>(take(pp));
+    t.codes[1] = reinterpret_cast<uint64_t *>(take(pp));
+    t.codes[2] = reinterpret_cast<uint64_t *>(take(all));
     const int n_tab = plan.n_coded_levels + (info.mode == SGS_MODE_STATIC ? kNChan : 0);
     t.tables = take((uint64_t)n_tab * kTabBytes);
     t.dup_prefix = reinterpret_cast<uint32_t *>(take(4ull * (info.n_dup + 1)));
@@ -134,6 +135,15 @@ extern "C" int sgs_create(sgs_ctx **out, int device, size_t scratch_bytes) {
     c->profile = 0;
     c->n_marks = 0;
     for (int i = 0; i <= kMaxStages; ++i) cudaEventCreate(&c->marks[i]);
+    for (int i = 0; i < 2; ++i) cudaEventCreate(&c->amarks[i]);
+    if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaFree(c->status_dev);
+        cudaFreeHost(c->status_host);
+        delete c;
+        return SGS_E_CUDA;
+    }
     c->scratch = nullptr;
     c->scratch_bytes = 0;
     if (scratch_bytes) {
@@ -168,6 +178,10 @@ extern "C" void sgs_destroy(sgs_ctx *c) {
     cudaDeviceSynchronize();
     if (c->scratch) cudaFree(c->scratch);
     for (int i = 0; i <= kMaxStages; ++i) cudaEventDestroy(c->marks[i]);
+    for (int i = 0; i < 2; ++i) cudaEventDestroy(c->amarks[i]);
+    cudaEventDestroy(c->fork);
+    cudaEventDestroy(c->join);
+    cudaStreamDestroy(c->aux);
     cudaFree(c->status_dev);
     cudaFreeHost(c->status_host);
     delete c;
@@ -179,13 +193,16 @@ extern "C" int sgs_profile(sgs_ctx *c, int enable) {
     return SGS_OK;
 }
 
-// Stage times (ms) of the most recent profiled decode: geometry tokens (tables, raw copy,
-// rANS), octree expansion (scan, top levels, deep levels, positions), attributes.
+// Stage times (ms) of the most recent profiled decode: [0] geometry tokens (tables, raw
+// copy, rANS), [1] octree expansion and positions, [2] attribute decode (on the attribute
+// stream, concurrent with [0] and [1]), [3] the whole decode.
 extern "C" int sgs_profile_read(sgs_ctx *c, float *ms, int cap) {
-    if (!c || !ms || cap < 3) return SGS_E_INVALID;
+    if (!c || !ms || cap < 4) return SGS_E_INVALID;
     if (c->n_marks != 4) return SGS_E_INVALID;
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 2; ++i)
         if (cudaEventElapsedTime(&ms[i], c->marks[i], c->marks[i + 1]) != cudaSuccess) return SGS_E_CUDA;
+    if (cudaEventElapsedTime(&ms[2], c->amarks[0], c->amarks[1]) != cudaSuccess) return SGS_E_CUDA;
+    if (cudaEventElapsedTime(&ms[3], c->marks[0], c->marks[3]) != cudaSuccess) return SGS_E_CUDA;
     return SGS_OK;
 }
 
@@ -278,9 +295,9 @@ extern "C" int scene_query(const uint8_t *b, size_t len, sgs_scene_info *info) {
     return SGS_OK;
 }
 
-static int cuda_status(cudaError_t e) { return e == cudaSuccess ? SGS_OK : SGS_E_CUDA; }
-
-// Enqueues every stage of one scene's decode on `st` using scratch `base`.
+// Enqueues every stage of one scene's decode using scratch `base`.  The attribute decode is
+// forked onto the context's attribute stream (it does not depend on the geometry) and joined
+// back into `st` at the end, so the two halves overlap on the device.
 static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &info,
                       const sgs_scene_out &out, uint8_t *base, cudaStream_t st) {
     Scratch s;
@@ -289,14 +306,14 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
     make_geo_plan(info, &plan);
     int *status = c->status_dev;
     cudaError_t e;
-    // zero the look-back flags and ticket (adjacent regions)
-    const size_t zbytes = (uint8_t *)s.ticket + 256 - (uint8_t *)s.scan_flags;
-    if ((e = cudaMemsetAsync(s.scan_flags, 0, zbytes, st)) != cudaSuccess) return SGS_E_CUDA;
     c->n_marks = 0;
     auto mark = [&]() {
         if (c->profile && c->n_marks <= kMaxStages) cudaEventRecord(c->marks[c->n_marks++], st);
     };
     mark();
+    // zero the look-back flags and ticket (adjacent regions)
+    const size_t zbytes = (uint8_t *)s.ticket + 256 - (uint8_t *)s.scan_flags;
+    if ((e = cudaMemsetAsync(s.scan_flags, 0, zbytes, st)) != cudaSuccess) return SGS_E_CUDA;
     if (plan.n_coded_levels) {
         c->launches += 1;
         e = launch_tables(bits, info.off[S_GEO_TAB], info.off[S_GEO_GRP], plan.n_coded_levels,
@@ -310,7 +327,20 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
                           info.n_rows == 0, status, st);
         if (e != cudaSuccess) return SGS_E_CUDA;
     }
-    // geometry
+    // fork: attributes on the attribute stream
+    if (cudaEventRecord(c->fork, st) != cudaSuccess || cudaStreamWaitEvent(c->aux, c->fork, 0) != cudaSuccess)
+        return SGS_E_CUDA;
+    if (c->profile) cudaEventRecord(c->amarks[0], c->aux);
+    if (info.n_rows) c->launches += 1;
+    switch (info.mode) {
+        case SGS_MODE_FIXED: e = launch_fixed(bits, info, out, status, c->aux); break;
+        case SGS_MODE_STATIC: e = launch_rans_static_attr(bits, info, attr_tables, out, status, c->aux); break;
+        default: e = launch_learned_decode(bits, info, out, s.learned, status, c->aux); break;
+    }
+    if (e != cudaSuccess) return SGS_E_CUDA;
+    if (c->profile) cudaEventRecord(c->amarks[1], c->aux);
+    if (cudaEventRecord(c->join, c->aux) != cudaSuccess) return SGS_E_CUDA;
+    // geometry on the caller's stream
     const uint8_t *B = bits + info.off[S_GEO_RAW];
     if (info.geo_mode == SGS_GEO_RANS && info.n_geo) {
         if ((e = launch_geo_copy_raw(bits, info, plan, s.geo_bytes, st)) != cudaSuccess) return SGS_E_CUDA;
@@ -323,15 +353,10 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
     if ((e = launch_octree(B, info, plan, bits, s, out, status, st)) != cudaSuccess) return SGS_E_CUDA;
     if (info.n_rows) c->launches += octree_launches(info, plan);
     mark();
-    // attributes
-    if (info.n_rows) c->launches += 1;
-    switch (info.mode) {
-        case SGS_MODE_FIXED: e = launch_fixed(bits, info, out, status, st); break;
-        case SGS_MODE_STATIC: e = launch_rans_static_attr(bits, info, attr_tables, out, status, st); break;
-        default: e = launch_learned_decode(bits, info, out, s.learned, status, st); break;
-    }
+    // join
+    if (cudaStreamWaitEvent(st, c->join, 0) != cudaSuccess) return SGS_E_CUDA;
     mark();
-    return cuda_status(e);
+    return SGS_OK;
 }
 
 extern "C" int scene_decode(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info *info,

@@ -109,33 +109,45 @@ __global__ void __launch_bounds__(kScanThreads) k_octree_scan(const uint8_t *B, 
     }
     uint32_t agg;
     const uint32_t local = block_excl_scan_256(sum, &agg, sm);
-    if (threadIdx.x == 0) {
-        uint32_t prefix = 0;
+    // decoupled look-back, 32 predecessors per step (flag 1 = aggregate, 2 = inclusive prefix)
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
         volatile unsigned long long *vf = reinterpret_cast<volatile unsigned long long *>(flags);
-        if (tile == 0) {
+        if (lane == 0) {
+            vf[tile] = ((tile == 0 ? 2ull : 1ull) << 32) | agg;
             __threadfence();
-            vf[0] = (2ull << 32) | agg;
-        } else {
-            vf[tile] = (1ull << 32) | agg;
-            __threadfence();
-            int64_t i = (int64_t)tile - 1;
-            uint32_t spins = 0;
-            while (i >= 0) {
-                const unsigned long long v = vf[i];
-                const uint32_t flag = (uint32_t)(v >> 32);
-                if (flag == 0) {
-                    if (++spins > kSpinLimit) { set_status(status, SGS_E_TIMEOUT); break; }
-                    __nanosleep(32);
-                    continue;
-                }
-                prefix += (uint32_t)v;
-                if (flag == 2) break;
-                --i;
-            }
-            __threadfence();
-            vf[tile] = (2ull << 32) | (uint64_t)(prefix + agg);
         }
-        s_prefix = prefix;
+        uint32_t prefix = 0;
+        int64_t hi = (int64_t)tile - 1;  // newest predecessor not yet summed
+        uint32_t spins = 0;
+        while (hi >= 0) {
+            const int64_t idx = hi - lane;
+            unsigned long long v = idx >= 0 ? vf[idx] : (2ull << 32);
+            while (__any_sync(0xffffffffu, (v >> 32) == 0)) {
+                if (++spins > kSpinLimit) break;
+                __nanosleep(32);
+                if ((v >> 32) == 0) v = vf[idx];
+            }
+            if (spins > kSpinLimit) {
+                if (lane == 0) set_status(status, SGS_E_TIMEOUT);
+                break;
+            }
+            const uint32_t incl = __ballot_sync(0xffffffffu, (v >> 32) == 2);
+            const int stop = incl ? __ffs(incl) - 1 : 31;  // lanes 0..stop contribute
+            uint32_t val = (lane <= stop) ? (uint32_t)v : 0u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+            prefix += val;
+            if (incl) break;
+            hi -= 32;
+        }
+        if (lane == 0) {
+            if (tile != 0) {
+                __threadfence();
+                vf[tile] = (2ull << 32) | (uint64_t)(prefix + agg);
+            }
+            s_prefix = prefix;
+        }
     }
     __syncthreads();
     if (k < n_chunks) chunk_prefix[k] = s_prefix + local;
@@ -263,58 +275,139 @@ __global__ void __launch_bounds__(kTopThreads) k_octree_top(TopParams p) {
     }
 }
 
-// ------------------------------------------------------------------ one deep level
+// ------------------------------------------------------------------ deep levels
+
+// Expands one chunk of up to kLvlTile consecutive nodes [x0, x1) of level l: round q handles
+// nodes x0 + 256 q + tid (coalesced), a block scan orders their children.  p_x0 = P(x0).
+// Children of level l go to codes_out[global child index - out_base], or to the leaves.
+// Returns the number of children (block-uniform).
+__device__ __forceinline__ uint32_t expand_chunk(const uint8_t *B, uint64_t x0, uint64_t x1,
+                                                 uint32_t p_x0, const uint64_t *codes_in,
+                                                 uint64_t in_base, uint64_t *codes_out,
+                                                 uint64_t out_base, uint64_t out_hi,
+                                                 const LeafOut *leaf, uint64_t leaf_base,
+                                                 uint32_t *sm, int *status) {
+    uint32_t carry = 0;
+    for (uint64_t r = x0; r < x1; r += kLvlThreads) {
+        const uint64_t x = r + threadIdx.x;
+        const uint32_t byte = x < x1 ? B[x] : 0u;
+        const uint64_t pc = x < x1 ? codes_in[x - in_base] : 0ull;
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan_256(__popc(byte), &tot, sm);
+        uint64_t child = 1ull + p_x0 + carry + ex;  // global BFS index of the first child
+        uint32_t b = byte;
+        while (b) {
+            const uint32_t k = __ffs(b) - 1;
+            b &= b - 1;
+            if (child >= out_hi) { set_status(status, SGS_E_CORRUPT); break; }
+            const uint64_t cc = child_code(pc, k);
+            if (leaf) write_leaf(*leaf, (uint32_t)(child - leaf_base), cc, status);
+            else codes_out[child - out_base] = cc;
+            ++child;
+        }
+        carry += tot;
+    }
+    return carry;
+}
 
 struct LevelParams {
     const uint8_t *B;
     const uint32_t *chunk_prefix;
     uint64_t lo, n;          // level's BFS offset and node count
-    uint32_t n_next;
-    const uint64_t *codes_in;
-    uint64_t *codes_out;     // NULL when the next level is the leaves
+    uint64_t next_lo, n_next;
+    const uint64_t *codes_in;   // indexed by x - in_base
+    uint64_t in_base;
+    uint64_t *codes_out;        // indexed by child - out_base; NULL when the next level is the leaves
+    uint64_t out_base;
     LeafOut leaf;
     int *status;
 };
 
 __global__ void __launch_bounds__(kLvlThreads) k_octree_level(LevelParams p) {
     __shared__ uint32_t sm[8];
-    __shared__ uint32_t s_base;
-    const uint64_t t0 = (uint64_t)blockIdx.x * kLvlTile;
+    __shared__ uint32_t s_p;
+    const uint64_t x0 = p.lo + (uint64_t)blockIdx.x * kLvlTile;
+    const uint64_t x1 = x0 + kLvlTile < p.lo + p.n ? x0 + kLvlTile : p.lo + p.n;
     if (threadIdx.x < 32) {
-        const uint32_t p_lo = prefix_at_warp(p.B, p.chunk_prefix, p.lo);
-        const uint32_t p_g0 = prefix_at_warp(p.B, p.chunk_prefix, p.lo + t0);
-        if (threadIdx.x == 0) s_base = p_g0 - p_lo;
-        if (blockIdx.x == 0) {
+        const uint32_t pg = prefix_at_warp(p.B, p.chunk_prefix, x0);
+        if (threadIdx.x == 0) s_p = pg;
+        if (blockIdx.x == 0) {  // sum of popcounts of the level = nodes of the next level
+            const uint32_t p_lo = prefix_at_warp(p.B, p.chunk_prefix, p.lo);
             const uint32_t p_hi = prefix_at_warp(p.B, p.chunk_prefix, p.lo + p.n);
-            if (threadIdx.x == 0 && p_hi - p_lo != p.n_next) set_status(p.status, SGS_E_CORRUPT);
+            if (threadIdx.x == 0 && (p_hi - p_lo != p.n_next || 1ull + p_lo != p.next_lo))
+                set_status(p.status, SGS_E_CORRUPT);
         }
     }
-    const uint64_t i0 = t0 + (uint64_t)threadIdx.x * kLvlPer;
-    uint32_t bytes[kLvlPer];
-    uint32_t cnt = 0;
-#pragma unroll
-    for (int q = 0; q < kLvlPer; ++q) {
-        bytes[q] = (i0 + q < p.n) ? p.B[p.lo + i0 + q] : 0u;
-        cnt += __popc(bytes[q]);
-    }
-    uint32_t tot;
-    const uint32_t ex = block_excl_scan_256(cnt, &tot, sm);  // also orders s_base
-    uint32_t idx = s_base + ex;
-#pragma unroll
-    for (int q = 0; q < kLvlPer; ++q) {
-        if (i0 + q >= p.n) break;
-        const uint64_t pc = p.codes_in[i0 + q];
-        uint32_t b = bytes[q];
-        while (b) {
-            const uint32_t k = __ffs(b) - 1;
-            b &= b - 1;
-            if (idx >= p.n_next) { set_status(p.status, SGS_E_CORRUPT); b = 0; break; }
-            const uint64_t cc = child_code(pc, k);
-            if (p.codes_out) p.codes_out[idx] = cc;
-            else write_leaf(p.leaf, idx, cc, p.status);
-            ++idx;
+    __syncthreads();
+    expand_chunk(p.B, x0, x1, s_p, p.codes_in, p.in_base, p.codes_out, p.out_base,
+                 p.next_lo + p.n_next, p.codes_out ? nullptr : &p.leaf, p.next_lo, sm, p.status);
+}
+
+// Subtree walk: CTA t owns nodes [lo + t*kLvlTile, ...) of level lc and expands all their
+// descendants down to the leaves.  Below lc the tree is nearly a set of chains, so the
+// descendants of a tile stay about one tile wide per level; ranges are contiguous in
+// breadth-first order, the child range of [a, b) being [1 + P(a), 1 + P(b)).
+struct SubtreeParams {
+    const uint8_t *B;
+    const uint32_t *chunk_prefix;
+    int lc, depth;
+    uint64_t level_off[SGS_MAX_DEPTH + 2];
+    uint64_t *codes_all;  // levels lc..D-1, indexed by BFS index - level_off[lc]
+    LeafOut leaf;
+    int *status;
+};
+
+__global__ void __launch_bounds__(kLvlThreads) k_octree_subtree(SubtreeParams p) {
+    __shared__ uint32_t sm[8];
+    __shared__ uint32_t s_p;
+    const uint64_t base = p.level_off[p.lc];
+    uint64_t a = base + (uint64_t)blockIdx.x * kLvlTile;
+    uint64_t b = a + kLvlTile < p.level_off[p.lc + 1] ? a + kLvlTile : p.level_off[p.lc + 1];
+    const bool last = (b == p.level_off[p.lc + 1]);
+    const uint64_t leaf_base = p.level_off[p.depth];
+    for (int l = p.lc; l < p.depth; ++l) {
+        if (threadIdx.x < 32) {
+            const uint32_t pa = prefix_at_warp(p.B, p.chunk_prefix, a);
+            if (threadIdx.x == 0) s_p = pa;
         }
+        __syncthreads();
+        const uint32_t pa = s_p;
+        const bool to_leaves = (l + 1 == p.depth);
+        uint32_t total = 0;
+        for (uint64_t c0 = a; c0 < b; c0 += kLvlTile) {
+            const uint64_t c1 = c0 + kLvlTile < b ? c0 + kLvlTile : b;
+            total += expand_chunk(p.B, c0, c1, pa + total, p.codes_all, base, p.codes_all, base,
+                                  p.level_off[l + 2], to_leaves ? &p.leaf : nullptr, leaf_base, sm,
+                                  p.status);
+        }
+        const uint64_t na = 1ull + pa, nb = na + total;
+        if (threadIdx.x == 0 && (na < p.level_off[l + 1] || nb > p.level_off[l + 2] ||
+                                 (last && nb != p.level_off[l + 2]) ||
+                                 (blockIdx.x == 0 && na != p.level_off[l + 1])))
+            set_status(p.status, SGS_E_CORRUPT);
+        a = na < p.level_off[l + 1] ? p.level_off[l + 1] : na;
+        b = nb > p.level_off[l + 2] ? p.level_off[l + 2] : nb;
+        if (a > b) a = b;
+        __syncthreads();
     }
+}
+
+// First level of the subtree walk: the shallowest level >= l1 below which every level grows
+// by at most 5/4 (chain-like); D if there is none.
+int octree_subtree_level(const GeoPlan &plan, int l1) {
+    const int D = plan.depth;
+    int lc = D;
+    for (int l = D - 1; l >= l1; --l) {
+        if ((uint64_t)plan.n_level[l + 1] * 4 > (uint64_t)plan.n_level[l] * 5) break;
+        lc = l;
+    }
+    return lc;
+}
+
+int octree_top_level(const GeoPlan &plan) {
+    int l1 = 1;
+    while (l1 < plan.depth && plan.n_level[l1] <= kTopCap) ++l1;
+    return l1;
 }
 
 // ------------------------------------------------------------------ launcher
@@ -342,50 +435,80 @@ cudaError_t launch_octree(const uint8_t *B, const sgs_scene_info &info, const Ge
                                         s.dup_prefix, status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    // popcount prefix over all tokens
     const uint64_t n_chunks = (info.n_geo + kChunk - 1) / kChunk;
     const uint64_t n_tiles = (info.n_geo + kScanTile - 1) / kScanTile;
     k_octree_scan<<<(unsigned)n_tiles, kScanThreads, 0, st>>>(B, info.n_geo, s.chunk_prefix,
                                                               n_chunks, s.scan_flags, s.ticket,
                                                               status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // top levels in one CTA
-    int l1 = 1;
-    while (l1 < D && plan.n_level[l1] <= kTopCap) ++l1;
+    const int l1 = octree_top_level(plan);
+    const int lc = octree_subtree_level(plan, l1);
+    uint64_t *codes_all = s.codes[2];
+    auto dst = [&](int l) -> uint64_t * { return l >= lc ? codes_all : s.codes[l & 1]; };
+    auto dst_base = [&](int l) -> uint64_t { return l >= lc ? plan.level_off[lc] : plan.level_off[l]; };
     TopParams tp;
     tp.B = B;
     tp.plan = plan;
     tp.l1 = l1;
-    tp.codes_out = s.codes[0];
+    tp.codes_out = (l1 < D) ? dst(l1) + (plan.level_off[l1] - dst_base(l1)) : nullptr;
     tp.leaf = lo;
     tp.status = status;
     k_octree_top<<<1, kTopThreads, 0, st>>>(tp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    int cur = 0;
-    for (int l = l1; l < D; ++l) {
+    for (int l = l1; l < lc; ++l) {
         LevelParams lp;
         lp.B = B;
         lp.chunk_prefix = s.chunk_prefix;
         lp.lo = plan.level_off[l];
         lp.n = plan.n_level[l];
+        lp.next_lo = plan.level_off[l + 1];
         lp.n_next = plan.n_level[l + 1];
-        lp.codes_in = s.codes[cur];
-        lp.codes_out = (l + 1 < D) ? s.codes[cur ^ 1] : nullptr;
+        lp.codes_in = dst(l);
+        lp.in_base = dst_base(l);
+        lp.codes_out = (l + 1 < D) ? dst(l + 1) : nullptr;
+        lp.out_base = (l + 1 < D) ? dst_base(l + 1) : 0;
         lp.leaf = lo;
         lp.status = status;
         const unsigned grid = (unsigned)((lp.n + kLvlTile - 1) / kLvlTile);
         if (grid) k_octree_level<<<grid, kLvlThreads, 0, st>>>(lp);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        cur ^= 1;
+    }
+    if (lc < D) {
+        SubtreeParams sp;
+        sp.B = B;
+        sp.chunk_prefix = s.chunk_prefix;
+        sp.lc = lc;
+        sp.depth = D;
+        for (int l = 0; l <= D; ++l) sp.level_off[l] = plan.level_off[l];
+        sp.level_off[D + 1] = plan.level_off[D] + plan.n_level[D];
+        sp.codes_all = codes_all;
+        sp.leaf = lo;
+        sp.status = status;
+        const unsigned grid = (unsigned)((plan.n_level[lc] + kLvlTile - 1) / kLvlTile);
+        k_octree_subtree<<<grid, kLvlThreads, 0, st>>>(sp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
+// Scratch of the octree stage (bytes of the three code buffers).
+void octree_code_buffers(const sgs_scene_info &info, const GeoPlan &plan, uint64_t *pingpong,
+                         uint64_t *all) {
+    const int l1 = octree_top_level(plan);
+    const int lc = octree_subtree_level(plan, l1);
+    uint64_t m = 1, a = 1;
+    for (int l = l1; l < lc && l < plan.depth; ++l) m = m > plan.n_level[l] ? m : plan.n_level[l];
+    for (int l = lc; l < plan.depth; ++l) a += plan.n_level[l];
+    if (info.n_rows == 0) m = a = 1;
+    *pingpong = 8 * m;
+    *all = 8 * a;
+}
+
 // Kernels launch_octree enqueues for a non-empty scene.
 int octree_launches(const sgs_scene_info &info, const GeoPlan &plan) {
-    int l1 = 1;
-    while (l1 < plan.depth && plan.n_level[l1] <= kTopCap) ++l1;
-    return (info.n_dup ? 1 : 0) + 2 + (plan.depth - l1);
+    const int l1 = octree_top_level(plan);
+    const int lc = octree_subtree_level(plan, l1);
+    return (info.n_dup ? 1 : 0) + 2 + (lc - l1) + (lc < plan.depth ? 1 : 0);
 }
 
 size_t octree_scan_tiles(uint64_t n_geo) { return (n_geo + kScanTile - 1) / kScanTile; }

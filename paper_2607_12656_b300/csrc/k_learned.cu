@@ -14,6 +14,7 @@
 // restricted to the quarter holding each lane's slot, and finally warp 0 advances the 32
 // rANS states and refills them from the group's shared word stream.
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <vector>
@@ -44,6 +45,7 @@ struct LSmem {
     int8_t h1[32 * kRS];
     int8_t h2[32 * kRS];
     uint8_t ctx[32 * 4 * kNChan];  // [lane][ring row][channel]
+    alignas(16) uint16_t win[kWinWords];  // word-stream window of warp 0
     int32_t red_max[4][32];
     int32_t red_idx[4][32];
     uint32_t red_sum[4][32];
@@ -134,6 +136,8 @@ __device__ bool load_model(LSmem &S, const uint8_t *m, int *status) {
     return true;
 }
 
+static_assert(offsetof(LSmem, win) % 16 == 0, "window must be 16-byte aligned");
+
 struct LearnedParams {
     const uint8_t *bits;
     uint64_t model_off, chan_off, grp_sec, pay_off, pay_len;
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_learned_decode(LearnedParams p
     GroupStream gs;
     uint32_t x = 0x10000u;
     if (warp == 0) {
-        group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, grp, nl, lane, gs, x);
+        group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, grp, nl, lane, gs, x, S.win);
         S.slot[lane] = x & 0xFFFFu;
     }
     __syncthreads();

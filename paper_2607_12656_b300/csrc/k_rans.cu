@@ -82,8 +82,10 @@ struct AttrParams {
     int *status;
 };
 
-constexpr int kAttrWarps = 4;
-constexpr size_t kAttrSmem = kNChan * kTabCdfWords * 4 + kNChan * 256 + 2 * kNChan * 4;
+constexpr int kAttrWarps = 8;
+constexpr size_t kAttrTabSmem = kNChan * kTabCdfWords * 4 + kNChan * 256 + 2 * kNChan * 4;
+constexpr size_t kAttrSmem = kAttrTabSmem + kAttrWarps * kWinWords * 2;
+static_assert(kAttrTabSmem % 16 == 0, "window must be 16-byte aligned");
 
 __global__ void __launch_bounds__(32 * kAttrWarps) k_rans_attr(AttrParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -91,6 +93,7 @@ __global__ void __launch_bounds__(32 * kAttrWarps) k_rans_attr(AttrParams p) {
     uint8_t *s_bucket = smem + kNChan * kTabCdfWords * 4;         // [56][256]
     float *s_step = (float *)(s_bucket + kNChan * 256);           // [56]
     float *s_off = s_step + kNChan;                               // [56]
+    uint16_t *s_win = reinterpret_cast<uint16_t *>(smem + kAttrTabSmem) + (threadIdx.x >> 5) * kWinWords;
     load_tables_smem(p.tables, kNChan, s_cdf, s_bucket);
     if (threadIdx.x < kNChan) {
         s_step[threadIdx.x] = ld_f32(p.bits + p.chan_off + 4 * threadIdx.x);
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(32 * kAttrWarps) k_rans_attr(AttrParams p) {
     const uint64_t n = (r1 - r0) * kNChan;
     GroupStream gs;
     uint32_t x;
-    group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, g, nl, lane, gs, x);
+    group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, g, nl, lane, gs, x, s_win);
     const uint64_t maxn = warp_max_u64(n);
     uint64_t row = r0;
     int c = 0;
@@ -170,13 +173,16 @@ struct GeoParams {
     int *status;
 };
 
-constexpr int kGeoWarps = 4;
+constexpr int kGeoWarps = 8;
+constexpr size_t kGeoTabSmem = (SGS_MAX_DEPTH * (kTabCdfWords * 4 + 256) + 15) & ~size_t(15);
+static_assert(kGeoTabSmem % 16 == 0, "window must be 16-byte aligned");
 
 __global__ void __launch_bounds__(32 * kGeoWarps) k_rans_geo(GeoParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int nt = p.plan.n_coded_levels;
     uint32_t *s_cdf = (uint32_t *)smem;
     uint8_t *s_bucket = smem + (size_t)nt * kTabCdfWords * 4;
+    uint16_t *s_win = reinterpret_cast<uint16_t *>(smem + kGeoTabSmem) + (threadIdx.x >> 5) * kWinWords;
     load_tables_smem(p.tables, nt, s_cdf, s_bucket);
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -192,7 +198,7 @@ __global__ void __launch_bounds__(32 * kGeoWarps) k_rans_geo(GeoParams p) {
     const uint64_t n = i1 - i0;
     GroupStream gs;
     uint32_t x;
-    group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, g, nl, lane, gs, x);
+    group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, g, nl, lane, gs, x, s_win);
     const uint64_t maxn = warp_max_u64(n);
     int k = 0;  // coded level of symbol i0
     while (k + 1 < nt && p.plan.coded_start[k + 1] <= i0) ++k;
@@ -228,11 +234,11 @@ cudaError_t launch_rans_static_geo(const uint8_t *bits, const sgs_scene_info &in
     p.plan = plan;
     p.geo_bytes = geo_bytes;
     p.status = status;
-    const size_t smem = (size_t)plan.n_coded_levels * (kTabCdfWords * 4 + 256);
+    const size_t smem = kGeoTabSmem + kGeoWarps * kWinWords * 2;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_rans_geo, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(SGS_MAX_DEPTH * (kTabCdfWords * 4 + 256)));
+                                             (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }

@@ -78,33 +78,57 @@ __device__ __forceinline__ uint32_t rans_sym(uint32_t &x, const uint32_t *cdf,
     return s;
 }
 
-// Word stream of one group of up to 32 lanes.
+// Word stream of one group of up to 32 lanes, read through a shared-memory window of
+// kWinWords words that the warp refills with coalesced 16-byte loads.
+constexpr uint32_t kWinWords = 2048;
+
 struct GroupStream {
-    const uint8_t *w;
+    const uint8_t *w;   // group stream (16-byte aligned)
     uint32_t n_words;
-    uint32_t ptr;
+    uint32_t ptr;       // next word to read
+    uint32_t wbase;     // first word held in the window
+    uint16_t *win;      // this warp's window
     bool bad;
 };
 
-// Opens group g's stream (bounds-checked against the payload) and reads this lane's initial
-// state (hi word, lo word).  Returns false if the group table is inconsistent.
+// Loads words [base, base + kWinWords) of the stream into the window (zero past the end).
+__device__ __forceinline__ void window_fill(GroupStream &gs, uint32_t base) {
+    const int lane = threadIdx.x & 31;
+    gs.wbase = base;
+    const uint4 *src = reinterpret_cast<const uint4 *>(gs.w) + (base >> 3);
+    uint4 *dst = reinterpret_cast<uint4 *>(gs.win);
+    const uint32_t n16 = (gs.n_words + 7) >> 3;  // 16-byte units holding stream words
+#pragma unroll
+    for (uint32_t i = lane; i < kWinWords / 8; i += 32) {
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if ((base >> 3) + i < n16) v = src[i];
+        dst[i] = v;
+    }
+    __syncwarp();
+}
+
+// Opens group g's stream (bounds-checked against the payload), fills the window and reads
+// this lane's initial state (hi word, lo word).  Returns false if the group table is bad.
 __device__ __forceinline__ bool group_open(const uint8_t *bits, uint64_t grp_sec,
                                            uint64_t pay_off, uint64_t pay_len, uint32_t G,
                                            uint32_t g, int nl, int lane, GroupStream &gs,
-                                           uint32_t &x) {
+                                           uint32_t &x, uint16_t *win) {
     const uint64_t *goff = reinterpret_cast<const uint64_t *>(bits + grp_sec);
     const uint32_t *gw = reinterpret_cast<const uint32_t *>(bits + grp_sec + 8ull * (G + 1));
     const uint64_t o = goff[g];
     const uint32_t nw = gw[g];
-    const bool ok = (o <= pay_len) && (2ull * nw <= pay_len - o) &&
+    // the window reads whole 16-byte units: the padded stream must hold them
+    const bool ok = (o <= pay_len) && (((2ull * nw + 15) & ~15ull) <= pay_len - o) &&
                     (nw >= 2u * (uint32_t)nl) && (o % 16 == 0);
     gs.w = bits + pay_off + (ok ? o : 0);
     gs.n_words = ok ? nw : 0;
     gs.ptr = 2u * (uint32_t)nl;
+    gs.win = win;
     gs.bad = !ok;
+    window_fill(gs, 0);
     x = 0x10000u;
     if (ok && lane < nl) {
-        x = (ld_u16(gs.w + 4 * lane) << 16) | ld_u16(gs.w + 4 * lane + 2);
+        x = ((uint32_t)win[2 * lane] << 16) | win[2 * lane + 1];
         if (x < 0x10000u) gs.bad = true;
     }
     return ok;
@@ -115,10 +139,12 @@ __device__ __forceinline__ bool group_open(const uint8_t *bits, uint64_t grp_sec
 __device__ __forceinline__ void group_refill(GroupStream &gs, uint32_t &x, bool active) {
     const bool need = active && x < 0x10000u;
     const uint32_t mask = __ballot_sync(0xffffffffu, need);
+    if (mask == 0) return;
+    if (gs.ptr + 32 > gs.wbase + kWinWords) window_fill(gs, gs.ptr & ~7u);
     if (need) {
         const uint32_t idx = gs.ptr + __popc(mask & ((1u << (threadIdx.x & 31)) - 1u));
         uint32_t w = 0;
-        if (idx < gs.n_words) w = ld_u16(gs.w + 2ull * idx); else gs.bad = true;
+        if (idx < gs.n_words) w = gs.win[idx - gs.wbase]; else gs.bad = true;
         x = (x << 16) | w;
     }
     gs.ptr += __popc(mask);

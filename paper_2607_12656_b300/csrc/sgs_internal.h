@@ -53,7 +53,8 @@ struct Scratch {
     uint32_t *chunk_prefix; // n_chunks + 1 popcount prefix per 64-byte chunk
     uint64_t *scan_flags;   // look-back tile status
     uint32_t *ticket;       // tile ticket counter (zeroed)
-    uint64_t *codes[2];     // packed (x:21 | y:21 | z:21) coordinates, ping-pong
+    uint64_t *codes[3];     // packed (x:21 | y:21 | z:21) coordinates: ping-pong for the
+                            // per-level kernels, then every level of the subtree walk
     uint8_t *tables;        // expanded static tables
     uint32_t *dup_prefix;   // n_dup + 1
     uint8_t *learned;       // learned-mode per-scene work area

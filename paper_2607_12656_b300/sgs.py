@@ -140,9 +140,10 @@ class Context:
         _check(lib().sgs_profile(self.handle, int(enable)), "sgs_profile")
 
     def profile_read(self) -> list:
-        """[geometry tokens, octree + positions, attributes] ms of the last profiled decode."""
-        ms = (ctypes.c_float * 3)()
-        _check(lib().sgs_profile_read(self.handle, ms, 3), "sgs_profile_read")
+        """[geometry tokens, octree + positions, attributes (own stream), whole decode] ms of
+        the last profiled decode."""
+        ms = (ctypes.c_float * 4)()
+        _check(lib().sgs_profile_read(self.handle, ms, 4), "sgs_profile_read")
         return [float(v) for v in ms]
 
     def launch_count(self) -> int:
