@@ -74,6 +74,8 @@ typedef struct {
                                geo_grp, geo_pay, attr_tab, attr_grp, attr_pay, total   */
     uint64_t total_len;     /* bitstream bytes                                           */
     uint64_t scratch_bytes; /* device scratch scene_decode needs for this scene          */
+    uint32_t n_tables;      /* static tables: coded octree levels, then 56 attribute ones */
+    uint32_t table_off[SGS_NCHAN + SGS_MAX_DEPTH]; /* byte offset of each table in the bitstream */
 } sgs_scene_info;
 
 /* Caller-allocated device outputs of one scene (sizes from sgs_scene_info.n_rows). */

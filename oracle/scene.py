@@ -196,6 +196,31 @@ def lane_bounds(n: int, lanes: int) -> np.ndarray:
     return (j * n) // lanes
 
 
+def static_row_order(n: int, lanes: int) -> tuple[np.ndarray, np.ndarray]:
+    """Row order of channel-wise static coding and its lane boundaries.
+
+    Group g of 32 lanes owns the rows that its lanes would own as contiguous chunks
+    (rows [floor(32 g n / L), floor(min(32 g + 32, L) n / L))), and deals them round robin to
+    its n_g lanes: lane j of the group codes rows R_g + j, R_g + j + n_g, ...  Static coding
+    has no context between rows, so this changes no code length; it only makes the 32 lanes
+    of a group hold 32 consecutive rows at every step.  Returns (perm, lane_start): the rows in
+    lane-major coding order and the offsets of each lane's rows in perm."""
+    perm = np.empty(n, np.int64)
+    lane_start = np.zeros(lanes + 1, np.int64)
+    lb = lane_bounds(n, lanes)
+    pos = 0
+    for g in range((lanes + 31) // 32):
+        j0, j1 = 32 * g, min(lanes, 32 * g + 32)
+        nl = j1 - j0
+        R0, R1 = int(lb[j0]), int(lb[j1])
+        for jj in range(nl):
+            rows = np.arange(R0 + jj, R1, nl, dtype=np.int64)
+            perm[pos:pos + len(rows)] = rows
+            pos += len(rows)
+            lane_start[j0 + jj + 1] = pos
+    return perm, lane_start
+
+
 def rans_encode(lane_start: np.ndarray, f: np.ndarray, c: np.ndarray, lane_lo: int = 0,
                 lane_hi: int | None = None):
     """Interleaved rANS of lanes [lane_lo, lane_hi); f, c indexed by absolute position."""
@@ -468,14 +493,16 @@ def encode(pos: np.ndarray, attr: np.ndarray, *, mode: int, depth: int, bits=8, 
             tabs = [normalize_freq(np.bincount(syms[:, c], minlength=NSYM)) for c in range(NCHAN)]
             attr_tab = b"".join(table_bytes(t) for t in tabs)
             tab_id = np.tile(np.arange(NCHAN, dtype=np.uint8), nr)
-            f, cc = static_fc(syms.ravel(), tab_id, tabs) if nr else (np.zeros(0), np.zeros(0))
+            perm, rows_start = static_row_order(nr, L)
+            f, cc = static_fc(syms[perm].ravel(), tab_id, tabs) if nr else (np.zeros(0), np.zeros(0))
         else:
             if model is None:
                 raise ValueError("learned mode needs a model")
             validate_model(_model_arrays(model))
             attr_tab = model_bytes(model)
             f, cc = learned_fc(model, syms, lane_row, 0, L)
-        attr_pay, goff, gw = rans_encode(lane_row * NCHAN, f, cc)
+        starts = rows_start * NCHAN if mode == MODE_STATIC else lane_row * NCHAN
+        attr_pay, goff, gw = rans_encode(starts, f, cc)
         attr_grp = group_table_bytes(goff, gw)
     dup = P.dups.astype("<u4").tobytes()
     chan = P.step.astype("<f4").tobytes() + P.offset.astype("<f4").tobytes() + P.bits.astype("<u4").tobytes()
@@ -499,8 +526,8 @@ def encode(pos: np.ndarray, attr: np.ndarray, *, mode: int, depth: int, bits=8, 
 
 
 def default_geo_lanes(n_coded: int) -> int:
-    """About 512 occupancy bytes per geometry lane, in whole groups of 32 lanes."""
-    return max(32, (n_coded + 512 * 32 - 1) // (512 * 32) * 32)
+    """About 128 occupancy bytes per geometry lane, in whole groups of 32 lanes."""
+    return max(32, (n_coded + 128 * 32 - 1) // (128 * 32) * 32)
 
 
 def group_table_bytes(goff: np.ndarray, gw: np.ndarray) -> bytes:
@@ -606,8 +633,10 @@ def decode(buf: bytes) -> dict:
         if mode == MODE_STATIC:
             tabs, _ = parse_tables(buf, h["off_attr_tab"], NCHAN)
             tab_id = np.tile(np.arange(NCHAN, dtype=np.uint8), nr)
-            syms = rans_decode_static(lane_row * NCHAN, tab_id, tabs, pay, goff, gw)
-            q = syms.reshape(nr, NCHAN).astype(np.uint32)
+            perm, rows_start = static_row_order(nr, L)
+            syms = rans_decode_static(rows_start * NCHAN, tab_id, tabs, pay, goff, gw)
+            q = np.zeros((nr, NCHAN), np.uint32)
+            q[perm] = syms.reshape(nr, NCHAN)
         else:
             model = parse_model(buf, h["off_attr_tab"])
             q = rans_decode_learned(model, lane_row, 0, L, pay, goff, gw, nr).astype(np.uint32)

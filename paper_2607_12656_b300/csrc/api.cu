@@ -24,7 +24,8 @@ struct sgs_ctx {
     cudaEvent_t marks[kMaxStages + 1];  // caller's stream: start, tokens, octree, end
     cudaEvent_t amarks[2];              // attribute stream: start, end
     cudaStream_t aux;                   // attribute decode runs here, forked from the caller
-    cudaEvent_t fork, join;
+    cudaStream_t aux2;                  // octree top levels, concurrent with the scan
+    cudaEvent_t fork, join, top_fork, top_join;
 };
 
 namespace sgs {
@@ -137,8 +138,11 @@ extern "C" int sgs_create(sgs_ctx **out, int device, size_t scratch_bytes) {
     for (int i = 0; i <= kMaxStages; ++i) cudaEventCreate(&c->marks[i]);
     for (int i = 0; i < 2; ++i) cudaEventCreate(&c->amarks[i]);
     if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->aux2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->top_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->top_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaFree(c->status_dev);
         cudaFreeHost(c->status_host);
         delete c;
@@ -181,7 +185,10 @@ extern "C" void sgs_destroy(sgs_ctx *c) {
     for (int i = 0; i < 2; ++i) cudaEventDestroy(c->amarks[i]);
     cudaEventDestroy(c->fork);
     cudaEventDestroy(c->join);
+    cudaEventDestroy(c->top_fork);
+    cudaEventDestroy(c->top_join);
     cudaStreamDestroy(c->aux);
+    cudaStreamDestroy(c->aux2);
     cudaFree(c->status_dev);
     cudaFreeHost(c->status_host);
     delete c;
@@ -291,6 +298,26 @@ extern "C" int scene_query(const uint8_t *b, size_t len, sgs_scene_info *info) {
         if (info->mode == SGS_MODE_LEARNED && sec(S_ATTR_TAB) < (uint64_t)SGS_MODEL_BYTES)
             return SGS_E_INVALID;
     }
+    // static tables: walk the variable-size tables once (presence mask, then (f-1) per
+    // present symbol, padded to 16 bytes) and record where each one starts
+    auto walk = [&](uint64_t off, uint64_t end, int count) -> bool {
+        for (int t = 0; t < count; ++t) {
+            if (off + 32 > end || info->n_tables >= (uint32_t)(SGS_NCHAN + SGS_MAX_DEPTH)) return false;
+            uint32_t K = 0;
+            for (int i = 0; i < 32; ++i) K += (uint32_t)__builtin_popcount(b[off + i]);
+            const uint64_t size = 32 + ((2ull * K + 15) & ~15ull);
+            if (off + size > end || off >= (1ull << 32)) return false;
+            info->table_off[info->n_tables++] = (uint32_t)off;
+            off += size;
+        }
+        return true;
+    };
+    int n_geo_tab = 0;
+    for (uint32_t l = 0; l < D; ++l)
+        if (info->geo_mode == SGS_GEO_RANS && info->n_level[l] >= kGeoRansMinLevel) ++n_geo_tab;
+    if (!walk(info->off[S_GEO_TAB], info->off[S_GEO_GRP], n_geo_tab)) return SGS_E_INVALID;
+    if (info->mode == SGS_MODE_STATIC && !walk(info->off[S_ATTR_TAB], info->off[S_ATTR_GRP], kNChan))
+        return SGS_E_INVALID;
     info->scratch_bytes = scratch_need(*info, nullptr, nullptr);
     return SGS_OK;
 }
@@ -314,19 +341,12 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
     // zero the look-back flags and ticket (adjacent regions)
     const size_t zbytes = (uint8_t *)s.ticket + 256 - (uint8_t *)s.scan_flags;
     if ((e = cudaMemsetAsync(s.scan_flags, 0, zbytes, st)) != cudaSuccess) return SGS_E_CUDA;
-    if (plan.n_coded_levels) {
+    if (info.n_tables) {
         c->launches += 1;
-        e = launch_tables(bits, info.off[S_GEO_TAB], info.off[S_GEO_GRP], plan.n_coded_levels,
-                          s.tables, 0, status, st);
+        e = launch_tables(bits, info, plan.n_coded_levels, s.tables, status, st);
         if (e != cudaSuccess) return SGS_E_CUDA;
     }
     uint8_t *attr_tables = s.tables + (size_t)plan.n_coded_levels * kTabBytes;
-    if (info.mode == SGS_MODE_STATIC) {
-        c->launches += 1;
-        e = launch_tables(bits, info.off[S_ATTR_TAB], info.off[S_ATTR_GRP], kNChan, attr_tables,
-                          info.n_rows == 0, status, st);
-        if (e != cudaSuccess) return SGS_E_CUDA;
-    }
     // fork: attributes on the attribute stream
     if (cudaEventRecord(c->fork, st) != cudaSuccess || cudaStreamWaitEvent(c->aux, c->fork, 0) != cudaSuccess)
         return SGS_E_CUDA;
@@ -350,7 +370,9 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
         c->launches += 2;
     }
     mark();
-    if ((e = launch_octree(B, info, plan, bits, s, out, status, st)) != cudaSuccess) return SGS_E_CUDA;
+    if ((e = launch_octree(B, info, plan, bits, s, out, status, st, c->aux2, c->top_fork, c->top_join)) !=
+        cudaSuccess)
+        return SGS_E_CUDA;
     if (info.n_rows) c->launches += octree_launches(info, plan);
     mark();
     // join

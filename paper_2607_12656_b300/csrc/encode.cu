@@ -230,6 +230,24 @@ void rans_encode(const std::vector<uint64_t> &lane_start, const uint32_t *sym_f,
     while (grp.size() % 16) grp.push_back(0);
 }
 
+// Channel-wise static coding: group g of 32 lanes owns the rows its lanes would own as
+// contiguous chunks and deals them round robin to its lanes (lane j: rows R_g + j + k n_g),
+// so the 32 lanes of a group always hold 32 consecutive rows.  Returns the rows in
+// lane-major coding order and each lane's start offset (in rows).
+void static_row_order(uint64_t n, uint64_t L, std::vector<uint32_t> &perm, std::vector<uint64_t> &start) {
+    perm.resize(n);
+    start.assign(L + 1, 0);
+    uint64_t pos = 0;
+    for (uint64_t j0 = 0; j0 < L; j0 += 32) {
+        const uint64_t j1 = std::min(L, j0 + 32), nl = j1 - j0;
+        const uint64_t R0 = j0 * n / L, R1 = j1 * n / L;
+        for (uint64_t jj = 0; jj < nl; ++jj) {
+            for (uint64_t r = R0 + jj; r < R1; r += nl) perm[pos++] = (uint32_t)r;
+            start[j0 + jj + 1] = pos;
+        }
+    }
+}
+
 std::vector<uint64_t> lane_bounds(uint64_t n, uint64_t L, uint64_t mul) {
     std::vector<uint64_t> b(L + 1);
     for (uint64_t j = 0; j <= L; ++j) b[j] = (j * n / L) * mul;
@@ -265,7 +283,7 @@ void put(std::vector<uint8_t> &o, T v) {
 }
 
 uint32_t default_geo_lanes(uint64_t n) {
-    const uint64_t per = 512ull * 32;
+    const uint64_t per = 128ull * 32;
     return (uint32_t)std::max<uint64_t>(32, (n + per - 1) / per * 32);
 }
 
@@ -358,7 +376,12 @@ extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, u
         L = prm->lanes;
         const uint64_t nsym = (uint64_t)R * kNChan;
         std::vector<uint32_t> sf(nsym), scu(nsym);
+        std::vector<uint64_t> starts = lane_bounds(R, L, kNChan);
         if (prm->mode == SGS_MODE_STATIC) {
+            std::vector<uint32_t> perm;
+            std::vector<uint64_t> rstart;
+            static_row_order(R, L, perm, rstart);
+            for (uint64_t j = 0; j <= L; ++j) starts[j] = rstart[j] * kNChan;
             for (int c = 0; c < kNChan; ++c) {
                 uint64_t h[kNSym] = {0};
                 for (uint32_t rr = 0; rr < R; ++rr) h[P.q16[(size_t)rr * kNChan + c]]++;
@@ -367,10 +390,10 @@ extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, u
                 put_table(s_atab, f);
                 uint32_t acc = 0;
                 for (int s = 0; s < kNSym; ++s) { cu[s] = acc; acc += f[s]; }
-                for (uint32_t rr = 0; rr < R; ++rr) {
-                    const uint32_t q = P.q16[(size_t)rr * kNChan + c];
-                    sf[(size_t)rr * kNChan + c] = f[q];
-                    scu[(size_t)rr * kNChan + c] = cu[q];
+                for (uint64_t p = 0; p < R; ++p) {
+                    const uint32_t q = P.q16[(size_t)perm[p] * kNChan + c];
+                    sf[p * kNChan + c] = f[q];
+                    scu[p * kNChan + c] = cu[q];
                 }
             }
         } else {
@@ -381,7 +404,7 @@ extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, u
             r = learned_token_fc(ctx, m, tok.data(), R, L, sf, scu);
             if (r) return r;
         }
-        rans_encode(lane_bounds(R, L, kNChan), sf.data(), scu.data(), s_agrp, s_apay);
+        rans_encode(starts, sf.data(), scu.data(), s_agrp, s_apay);
     }
     // assemble
     std::vector<uint8_t> *secs[10] = {&s_levels, &s_dup, &s_chan, &s_graw, &s_gtab,

@@ -29,6 +29,9 @@ struct FixedParams {
     int *status;
 };
 
+// VEC: every channel's output base is 16-byte aligned and there is no out_index, so lane j
+// writes rows 4j..4j+3 (+128 k) with one 16-byte store; otherwise one 4-byte store per row.
+template <bool VEC>
 __global__ void __launch_bounds__(32 * kFixWarps) k_fixed(FixedParams p) {
     __shared__ uint32_t s_words[kFixWarps][32 * kFixMaxBits + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -54,20 +57,41 @@ __global__ void __launch_bounds__(32 * kFixWarps) k_fixed(FixedParams p) {
     for (uint32_t i = lane; i <= nw; i += 32)
         sw[i] = (w0 + i < nwords_chan) ? w[w0 + i] : 0u;
     __syncwarp();
-    const uint32_t mask = (b == 32) ? 0xffffffffu : ((1u << b) - 1u);
-    const uint64_t r0 = (uint64_t)blk * kFixRows;
-    float *outc = p.out + (uint64_t)c * p.n_rows;
+    const uint32_t mask = (1u << b) - 1u;  // b <= 16
+    const uint32_t r0 = blk * kFixRows;
+    const uint32_t rows = p.n_rows - r0 < (uint32_t)kFixRows ? p.n_rows - r0 : (uint32_t)kFixRows;
+    float *outc = p.out + (size_t)c * p.n_rows + r0;
+    if (VEC) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t rl = (uint32_t)k * 128 + 4 * lane;
+            uint32_t bit = rl * b;
+            float v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t wi = bit >> 5;
+                v[q] = dequant(__funnelshift_r(sw[wi], sw[wi + 1], bit & 31) & mask, step, offset);
+                bit += b;
+            }
+            if (rl + 4 <= rows) {
+                *reinterpret_cast<float4 *>(outc + rl) = make_float4(v[0], v[1], v[2], v[3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (rl + q < rows) outc[rl + q] = v[q];
+            }
+        }
+    } else {
 #pragma unroll 4
-    for (int k = 0; k < 32; ++k) {
-        const uint32_t rl = (uint32_t)k * 32 + lane;
-        const uint64_t row = r0 + rl;
-        if (row >= p.n_rows) break;
-        const uint32_t bit = rl * b;
-        const uint32_t wi = bit >> 5, o = bit & 31;
-        const uint64_t two = ((uint64_t)sw[wi + 1] << 32) | sw[wi];
-        const uint32_t q = (uint32_t)(two >> o) & mask;
-        const uint64_t col = p.out_index ? (uint64_t)p.out_index[row] : row;
-        outc[col] = dequant(q, step, offset);
+        for (int k = 0; k < 32; ++k) {
+            const uint32_t rl = (uint32_t)k * 32 + lane;
+            if (rl >= rows) break;
+            const uint32_t bit = rl * b;
+            const uint32_t wi = bit >> 5;
+            const float v = dequant(__funnelshift_r(sw[wi], sw[wi + 1], bit & 31) & mask, step, offset);
+            if (p.out_index) p.out[(size_t)c * p.n_rows + p.out_index[r0 + rl]] = v;
+            else outc[rl] = v;
+        }
     }
 }
 
@@ -87,7 +111,9 @@ cudaError_t launch_fixed(const uint8_t *bits, const sgs_scene_info &info,
     p.status = status;
     const uint64_t items = (uint64_t)p.n_items_per_chan * kNChan;
     const unsigned grid = (unsigned)((items + kFixWarps - 1) / kFixWarps);
-    k_fixed<<<grid, 32 * kFixWarps, 0, st>>>(p);
+    const bool vec = !out.out_index && (info.n_rows % 4 == 0) && (((uintptr_t)out.attr & 15) == 0);
+    if (vec) k_fixed<true><<<grid, 32 * kFixWarps, 0, st>>>(p);
+    else k_fixed<false><<<grid, 32 * kFixWarps, 0, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -212,12 +212,20 @@ struct TopParams {
     int *status;
 };
 
+constexpr uint32_t kTopStage = 8192;  // top-level tokens staged in shared memory
+
 __global__ void __launch_bounds__(kTopThreads) k_octree_top(TopParams p) {
     __shared__ uint64_t codes[2][kTopCap];
+    __shared__ uint8_t stage[kTopStage];
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t s_carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) codes[0][0] = 0;
+    // all top-level tokens in one coalesced pass (they are contiguous from BFS index 0)
+    const uint64_t n_top = p.plan.level_off[p.l1];
+    const bool staged = n_top <= kTopStage;
+    if (staged)
+        for (uint32_t i = threadIdx.x; i < n_top; i += kTopThreads) stage[i] = p.B[i];
     __syncthreads();
     int cur = 0;
     for (int l = 0; l < p.l1; ++l) {
@@ -225,7 +233,7 @@ __global__ void __launch_bounds__(kTopThreads) k_octree_top(TopParams p) {
         const uint32_t n_next = p.plan.n_level[l + 1];
         const bool to_leaves = (l + 1 == p.plan.depth);
         const bool to_global = (l + 1 == p.l1) && !to_leaves;
-        const uint8_t *Bl = p.B + p.plan.level_off[l];
+        const uint8_t *Bl = (staged ? stage : p.B) + p.plan.level_off[l];
         if (threadIdx.x == 0) s_carry = 0;
         __syncthreads();
         for (uint32_t base = 0; base < n; base += kTopThreads) {
@@ -277,37 +285,71 @@ __global__ void __launch_bounds__(kTopThreads) k_octree_top(TopParams p) {
 
 // ------------------------------------------------------------------ deep levels
 
-// Expands one chunk of up to kLvlTile consecutive nodes [x0, x1) of level l: round q handles
-// nodes x0 + 256 q + tid (coalesced), a block scan orders their children.  p_x0 = P(x0).
-// Children of level l go to codes_out[global child index - out_base], or to the leaves.
-// Returns the number of children (block-uniform).
+// Expands one chunk of up to kLvlTile consecutive nodes [x0, x1) of level l.  Thread tid
+// handles nodes x0 + 256 q + tid (q < 8, coalesced); all 8 rounds are loaded first, then one
+// two-level block scan (warp scans per round, warp totals through shared memory) orders the
+// children.  p_x0 = P(x0).  Children go to codes_out[global child index - out_base], or to the
+// leaves.  Returns the number of children (block-uniform).  sm: 64 words of shared memory.
 __device__ __forceinline__ uint32_t expand_chunk(const uint8_t *B, uint64_t x0, uint64_t x1,
                                                  uint32_t p_x0, const uint64_t *codes_in,
                                                  uint64_t in_base, uint64_t *codes_out,
                                                  uint64_t out_base, uint64_t out_hi,
                                                  const LeafOut *leaf, uint64_t leaf_base,
                                                  uint32_t *sm, int *status) {
-    uint32_t carry = 0;
-    for (uint64_t r = x0; r < x1; r += kLvlThreads) {
-        const uint64_t x = r + threadIdx.x;
-        const uint32_t byte = x < x1 ? B[x] : 0u;
-        const uint64_t pc = x < x1 ? codes_in[x - in_base] : 0ull;
-        uint32_t tot;
-        const uint32_t ex = block_excl_scan_256(__popc(byte), &tot, sm);
-        uint64_t child = 1ull + p_x0 + carry + ex;  // global BFS index of the first child
-        uint32_t b = byte;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int Q = kLvlTile / kLvlThreads;
+    constexpr int NW = kLvlThreads / 32;
+    uint32_t byte[Q];
+    uint64_t pc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const uint64_t x = x0 + (uint64_t)q * kLvlThreads + threadIdx.x;
+        byte[q] = x < x1 ? B[x] : 0u;
+        pc[q] = x < x1 ? codes_in[x - in_base] : 0ull;
+    }
+    uint32_t ex[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const uint32_t v = __popc(byte[q]);
+        uint32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t n = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += n;
+        }
+        ex[q] = incl - v;
+        if (lane == 31) sm[q * NW + warp] = incl;
+    }
+    __syncthreads();
+    uint32_t total = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        uint32_t before = 0, round = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t t = sm[q * NW + w];
+            before += w < warp ? t : 0u;
+            round += t;
+        }
+        ex[q] += total + before;
+        total += round;
+    }
+    __syncthreads();  // sm is reused by the next chunk
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        uint64_t child = 1ull + p_x0 + ex[q];  // global BFS index of the first child
+        uint32_t b = byte[q];
         while (b) {
             const uint32_t k = __ffs(b) - 1;
             b &= b - 1;
             if (child >= out_hi) { set_status(status, SGS_E_CORRUPT); break; }
-            const uint64_t cc = child_code(pc, k);
+            const uint64_t cc = child_code(pc[q], k);
             if (leaf) write_leaf(*leaf, (uint32_t)(child - leaf_base), cc, status);
             else codes_out[child - out_base] = cc;
             ++child;
         }
-        carry += tot;
     }
-    return carry;
+    return total;
 }
 
 struct LevelParams {
@@ -324,7 +366,7 @@ struct LevelParams {
 };
 
 __global__ void __launch_bounds__(kLvlThreads) k_octree_level(LevelParams p) {
-    __shared__ uint32_t sm[8];
+    __shared__ uint32_t sm[64];
     __shared__ uint32_t s_p;
     const uint64_t x0 = p.lo + (uint64_t)blockIdx.x * kLvlTile;
     const uint64_t x1 = x0 + kLvlTile < p.lo + p.n ? x0 + kLvlTile : p.lo + p.n;
@@ -358,7 +400,7 @@ struct SubtreeParams {
 };
 
 __global__ void __launch_bounds__(kLvlThreads) k_octree_subtree(SubtreeParams p) {
-    __shared__ uint32_t sm[8];
+    __shared__ uint32_t sm[64];
     __shared__ uint32_t s_p;
     const uint64_t base = p.level_off[p.lc];
     uint64_t a = base + (uint64_t)blockIdx.x * kLvlTile;
@@ -414,7 +456,8 @@ int octree_top_level(const GeoPlan &plan) {
 
 cudaError_t launch_octree(const uint8_t *B, const sgs_scene_info &info, const GeoPlan &plan,
                           const uint8_t *bits, const Scratch &s, const sgs_scene_out &out,
-                          int *status, cudaStream_t st) {
+                          int *status, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_a,
+                          cudaEvent_t ev_b) {
     if (info.n_rows == 0 || info.n_leaves == 0) return cudaSuccess;
     const int D = plan.depth;
     LeafOut lo;
@@ -437,15 +480,16 @@ cudaError_t launch_octree(const uint8_t *B, const sgs_scene_info &info, const Ge
     }
     const uint64_t n_chunks = (info.n_geo + kChunk - 1) / kChunk;
     const uint64_t n_tiles = (info.n_geo + kScanTile - 1) / kScanTile;
-    k_octree_scan<<<(unsigned)n_tiles, kScanThreads, 0, st>>>(B, info.n_geo, s.chunk_prefix,
-                                                              n_chunks, s.scan_flags, s.ticket,
-                                                              status);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int l1 = octree_top_level(plan);
     const int lc = octree_subtree_level(plan, l1);
     uint64_t *codes_all = s.codes[2];
     auto dst = [&](int l) -> uint64_t * { return l >= lc ? codes_all : s.codes[l & 1]; };
     auto dst_base = [&](int l) -> uint64_t { return l >= lc ? plan.level_off[lc] : plan.level_off[l]; };
+    // the top levels need no prefix: they run on st2 while the scan runs on st
+    if (st2 != st) {
+        if (cudaEventRecord(ev_a, st) != cudaSuccess || cudaStreamWaitEvent(st2, ev_a, 0) != cudaSuccess)
+            return cudaErrorUnknown;
+    }
     TopParams tp;
     tp.B = B;
     tp.plan = plan;
@@ -453,8 +497,14 @@ cudaError_t launch_octree(const uint8_t *B, const sgs_scene_info &info, const Ge
     tp.codes_out = (l1 < D) ? dst(l1) + (plan.level_off[l1] - dst_base(l1)) : nullptr;
     tp.leaf = lo;
     tp.status = status;
-    k_octree_top<<<1, kTopThreads, 0, st>>>(tp);
+    k_octree_top<<<1, kTopThreads, 0, st2>>>(tp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (st2 != st && cudaEventRecord(ev_b, st2) != cudaSuccess) return cudaErrorUnknown;
+    k_octree_scan<<<(unsigned)n_tiles, kScanThreads, 0, st>>>(B, info.n_geo, s.chunk_prefix,
+                                                              n_chunks, s.scan_flags, s.ticket,
+                                                              status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (st2 != st && cudaStreamWaitEvent(st, ev_b, 0) != cudaSuccess) return cudaErrorUnknown;
     for (int l = l1; l < lc; ++l) {
         LevelParams lp;
         lp.B = B;

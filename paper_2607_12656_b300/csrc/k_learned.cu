@@ -27,39 +27,11 @@ namespace sgs {
 
 __constant__ uint32_t kExp2Q[256] = {SGS_EXP2Q_VALUES};
 
-constexpr int kLThreads = 256;
 constexpr int kRS = 80;  // smem row stride (bytes) of int8 rows of 64: conflict-free fragments
 
 // Frozen model blob offsets (bytes).
 constexpr int kMB_B1 = 32, kMB_B2 = 14368, kMB_B3 = 14624, kMB_W1 = 15648, kMB_W2 = 15904,
               kMB_W3 = 20000;
-
-struct LSmem {
-    int8_t w1[64 * 4];
-    int32_t b1[kNChan * 64];
-    int8_t w2[64 * kRS];
-    int32_t b2[64];
-    int8_t w3[256 * kRS];
-    int32_t b3[256];
-    uint32_t exp2q[256];
-    int8_t h1[32 * kRS];
-    int8_t h2[32 * kRS];
-    uint8_t ctx[32 * 4 * kNChan];  // [lane][ring row][channel]
-    alignas(16) uint16_t win[kWinWords];  // word-stream window of warp 0
-    int32_t red_max[4][32];
-    int32_t red_idx[4][32];
-    uint32_t red_sum[4][32];
-    uint32_t red_T[4][32];
-    uint32_t R[32];
-    uint32_t slot[32];
-    uint32_t res_s[32], res_f[32], res_c[32];
-    uint32_t nrows[32];
-    uint64_t row0[32];
-    float step[kNChan], offset[kNChan];
-    int32_t m1, sh1, m2, sh2;
-    uint32_t ms, ss;
-    int bad;
-};
 
 __device__ __forceinline__ int32_t requant(int32_t acc, int32_t m, int32_t sh) {
     int64_t v = ((int64_t)acc * (int64_t)m + ((int64_t)1 << (sh - 1))) >> sh;
@@ -96,8 +68,88 @@ __device__ __forceinline__ void tile_16x8x64(int32_t (&acc)[4], const int8_t *A,
     }
 }
 
-// Loads and validates the frozen model; returns false (and marks the stream) if invalid.
-__device__ bool load_model(LSmem &S, const uint8_t *m, int *status) {
+struct LearnedParams {
+    const uint8_t *bits;
+    uint64_t model_off, chan_off, grp_sec, pay_off, pay_len;
+    uint32_t L, G, n_rows;
+    float *out;
+    const uint32_t *out_index;
+    int *status;
+};
+
+// Pipelined decoder: 16 producer warps compute, step by step (Gaussian i, channel c), the
+// 32 lanes' frequency tables -- layer 1 on the ALU, layers 2-3 as int8 mma.sync, the
+// integer softmax -- and store them as u16 cumulative tables in a ring of kNB buffers; one
+// consumer warp runs the 32 rANS chains, binary-searching its lane's table.  Only the search
+// is on the sequential chain; the context of step (i+1, c) needs only (i, c), 56 steps back,
+// so producers run up to kNB steps ahead.  Hand-offs use mbarriers with bounded waits.
+constexpr int kPW = 16;                  // producer warps
+constexpr int kPT = 32 * kPW;            // producer threads
+constexpr int kLT = kPT + 32;            // + consumer warp
+constexpr int kNB = 4;                   // pipeline depth (steps)
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+struct LSmem2 {
+    int8_t w1[64 * 4];
+    int32_t b1[kNChan * 64];
+    int8_t w2[64 * kRS];
+    int32_t b2[64];
+    int8_t w3[256 * kRS];
+    int32_t b3[256];
+    uint32_t exp2q[256];
+    int8_t h1[32 * kRS];
+    int8_t h2[32 * kRS];
+    uint8_t ctx[32 * 4 * kNChan];            // [lane][ring row][channel]
+    alignas(16) uint16_t cdf[kNB][32][256];  // cumulative frequency of each symbol
+    alignas(16) uint16_t win[kWinWords];     // consumer's word-stream window
+    int32_t red_max[8][32];
+    int32_t red_idx[8][32];
+    uint32_t red_sum[8][32];
+    uint32_t red_T[8][32];
+    uint32_t nrows[32];
+    uint64_t row0[32];
+    float step[kNChan], offset[kNChan];
+    alignas(8) uint64_t full[kNB], empty[kNB];
+    int32_t m1, sh1, m2, sh2;
+    uint32_t ms, ss;
+    int bad;
+    int abort_;
+};
+static_assert(offsetof(LSmem2, cdf) % 16 == 0 && offsetof(LSmem2, win) % 16 == 0, "alignment");
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of `parity` to complete; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_) {
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if (*abort_) return false;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+__device__ __forceinline__ void producer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"r"(kPT) : "memory");
+}
+
+__device__ bool load_model2(LSmem2 &S, const uint8_t *m, int *status) {
     const int tid = threadIdx.x;
     if (tid == 0) {
         const int32_t *h = reinterpret_cast<const int32_t *>(m);
@@ -105,27 +157,28 @@ __device__ bool load_model(LSmem &S, const uint8_t *m, int *status) {
         S.ms = (uint32_t)h[4]; S.ss = (uint32_t)h[5];
         S.bad = !(S.sh1 >= 1 && S.sh1 <= 47 && S.sh2 >= 1 && S.sh2 <= 47 && S.m1 >= 0 && S.m2 >= 0 &&
                   S.ms >= 1 && S.ms < (1u << 24) && S.ss <= 24);
+        S.abort_ = 0;
     }
     const int32_t *b1 = reinterpret_cast<const int32_t *>(m + kMB_B1);
     const int32_t *b2 = reinterpret_cast<const int32_t *>(m + kMB_B2);
     const int32_t *b3 = reinterpret_cast<const int32_t *>(m + kMB_B3);
     bool badb = false;
-    for (int i = tid; i < kNChan * 64; i += kLThreads) {
+    for (int i = tid; i < kNChan * 64; i += kLT) {
         S.b1[i] = b1[i];
         badb |= (b1[i] >= (1 << 24) || b1[i] <= -(1 << 24));
     }
-    for (int i = tid; i < 64; i += kLThreads) {
+    for (int i = tid; i < 64; i += kLT) {
         S.b2[i] = b2[i];
         badb |= (b2[i] >= (1 << 24) || b2[i] <= -(1 << 24));
     }
-    for (int i = tid; i < 256; i += kLThreads) {
+    for (int i = tid; i < 256; i += kLT) {
         S.b3[i] = b3[i];
         badb |= (b3[i] >= (1 << 24) || b3[i] <= -(1 << 24));
         S.exp2q[i] = kExp2Q[i];
+        S.w1[i] = (int8_t)m[kMB_W1 + i];
     }
-    for (int i = tid; i < 256; i += kLThreads) S.w1[i] = (int8_t)m[kMB_W1 + i];
-    for (int i = tid; i < 64 * 64; i += kLThreads) S.w2[(i >> 6) * kRS + (i & 63)] = (int8_t)m[kMB_W2 + i];
-    for (int i = tid; i < 256 * 64; i += kLThreads) S.w3[(i >> 6) * kRS + (i & 63)] = (int8_t)m[kMB_W3 + i];
+    for (int i = tid; i < 64 * 64; i += kLT) S.w2[(i >> 6) * kRS + (i & 63)] = (int8_t)m[kMB_W2 + i];
+    for (int i = tid; i < 256 * 64; i += kLT) S.w3[(i >> 6) * kRS + (i & 63)] = (int8_t)m[kMB_W3 + i];
     __syncthreads();
     if (badb) atomicOr(&S.bad, 1);
     __syncthreads();
@@ -136,25 +189,173 @@ __device__ bool load_model(LSmem &S, const uint8_t *m, int *status) {
     return true;
 }
 
-static_assert(offsetof(LSmem, win) % 16 == 0, "window must be 16-byte aligned");
-
-struct LearnedParams {
-    const uint8_t *bits;
-    uint64_t model_off, chan_off, grp_sec, pay_off, pay_len;
-    uint32_t L, G, n_rows;
-    float *out;
-    const uint32_t *out_index;
-    int *status;
-};
-
-__global__ void __launch_bounds__(kLThreads, 1) k_learned_decode(LearnedParams p) {
-    extern __shared__ __align__(16) uint8_t smem_raw[];
-    LSmem &S = *reinterpret_cast<LSmem *>(smem_raw);
+// One producer step: frequency tables of the 32 lanes' rows for (i, c) into cdf[b].
+__device__ __forceinline__ void produce_step(LSmem2 &S, uint32_t i, int c, int b) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
+    // layer 1 (ALU): row r = tid >> 4, outputs 4 (tid & 15) .. +3
+    {
+        const int r = tid >> 4, o0 = (tid & 15) * 4;
+        int32_t u[4];
+#pragma unroll
+        for (int j = 1; j <= 4; ++j)
+            u[j - 1] = (i >= (uint32_t)j) ? (int32_t)S.ctx[(r * 4 + ((i - j) & 3)) * kNChan + c] - 128 : 0;
+#pragma unroll
+        for (int o = o0; o < o0 + 4; ++o) {
+            int32_t acc = S.b1[c * 64 + o];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc += (int32_t)S.w1[o * 4 + j] * u[j];
+            S.h1[r * kRS + o] = (int8_t)requant(acc, S.m1, S.sh1);
+        }
+    }
+    producer_sync();
+    // layer 2: warp -> rows 16 (warp & 1), cols 8 (warp >> 1)
+    {
+        const int r0 = (warp & 1) * 16, n0 = (warp >> 1) * 8;
+        int32_t acc[4] = {0, 0, 0, 0};
+        tile_16x8x64(acc, S.h1, r0, S.w2, n0, g, t);
+        const int col = n0 + 2 * t;
+        S.h2[(r0 + g) * kRS + col] = (int8_t)requant(acc[0] + S.b2[col], S.m2, S.sh2);
+        S.h2[(r0 + g) * kRS + col + 1] = (int8_t)requant(acc[1] + S.b2[col + 1], S.m2, S.sh2);
+        S.h2[(r0 + g + 8) * kRS + col] = (int8_t)requant(acc[2] + S.b2[col], S.m2, S.sh2);
+        S.h2[(r0 + g + 8) * kRS + col + 1] = (int8_t)requant(acc[3] + S.b2[col + 1], S.m2, S.sh2);
+    }
+    producer_sync();
+    // layer 3: warp -> rows 16 (warp & 1), column slice cs = warp >> 1 (32 columns)
+    const int r0 = (warp & 1) * 16, cs = warp >> 1;
+    const int rA = r0 + g, rB = r0 + g + 8;
+    int32_t z[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+        const int n0 = cs * 32 + nt * 8;
+        z[nt][0] = z[nt][1] = z[nt][2] = z[nt][3] = 0;
+        tile_16x8x64(z[nt], S.h2, r0, S.w3, n0, g, t);
+        const int col = n0 + 2 * t;
+        z[nt][0] += S.b3[col];
+        z[nt][1] += S.b3[col + 1];
+        z[nt][2] += S.b3[col];
+        z[nt][3] += S.b3[col + 1];
+    }
+    // (a) row max, lowest argmax
+    {
+        int32_t mA = z[0][0], mB = z[0][2];
+        int32_t iA = cs * 32 + 2 * t, iB = iA;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                const int32_t col = cs * 32 + nt * 8 + 2 * t + v;
+                if (z[nt][v] > mA) { mA = z[nt][v]; iA = col; }
+                if (z[nt][2 + v] > mB) { mB = z[nt][2 + v]; iB = col; }
+            }
+#pragma unroll
+        for (int o = 1; o <= 2; o <<= 1) {
+            const int32_t omA = __shfl_xor_sync(0xffffffffu, mA, o), oiA = __shfl_xor_sync(0xffffffffu, iA, o);
+            const int32_t omB = __shfl_xor_sync(0xffffffffu, mB, o), oiB = __shfl_xor_sync(0xffffffffu, iB, o);
+            if (omA > mA || (omA == mA && oiA < iA)) { mA = omA; iA = oiA; }
+            if (omB > mB || (omB == mB && oiB < iB)) { mB = omB; iB = oiB; }
+        }
+        if (t == 0) {
+            S.red_max[cs][rA] = mA; S.red_idx[cs][rA] = iA;
+            S.red_max[cs][rB] = mB; S.red_idx[cs][rB] = iB;
+        }
+    }
+    producer_sync();
+    int32_t zmA = S.red_max[0][rA], amA = S.red_idx[0][rA];
+    int32_t zmB = S.red_max[0][rB], amB = S.red_idx[0][rB];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) {
+        if (S.red_max[q][rA] > zmA) { zmA = S.red_max[q][rA]; amA = S.red_idx[q][rA]; }
+        if (S.red_max[q][rB] > zmB) { zmB = S.red_max[q][rB]; amB = S.red_idx[q][rB]; }
+    }
+    // (b) e_k and partial sums
+    {
+        uint32_t sA = 0, sB = 0;
+        const uint32_t ms = S.ms, ss = S.ss;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const uint32_t d = (uint32_t)((v < 2 ? zmA : zmB) - z[nt][v]);
+                const uint64_t tt = ((uint64_t)d * ms) >> ss;
+                const uint32_t tk = tt > 6144 ? 6144u : (uint32_t)tt;
+                const uint32_t e = S.exp2q[tk & 255] >> (tk >> 8);
+                z[nt][v] = (int32_t)e;
+                if (v < 2) sA += e; else sB += e;
+            }
+        sA += __shfl_xor_sync(0xffffffffu, sA, 1);
+        sA += __shfl_xor_sync(0xffffffffu, sA, 2);
+        sB += __shfl_xor_sync(0xffffffffu, sB, 1);
+        sB += __shfl_xor_sync(0xffffffffu, sB, 2);
+        if (t == 0) { S.red_sum[cs][rA] = sA; S.red_sum[cs][rB] = sB; }
+    }
+    producer_sync();
+    uint32_t RA, RB;
+    {
+        uint64_t EA = 0, EB = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { EA += S.red_sum[q][rA]; EB += S.red_sum[q][rB]; }
+        RA = (uint32_t)((65280ull << 32) / EA);
+        RB = (uint32_t)((65280ull << 32) / EB);
+    }
+    // (c) floor terms and per-slice sums
+    {
+        uint32_t TA = 0, TB = 0;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const uint32_t fl = __umulhi((uint32_t)z[nt][v], v < 2 ? RA : RB);
+                z[nt][v] = (int32_t)fl;
+                if (v < 2) TA += fl; else TB += fl;
+            }
+        TA += __shfl_xor_sync(0xffffffffu, TA, 1);
+        TA += __shfl_xor_sync(0xffffffffu, TA, 2);
+        TB += __shfl_xor_sync(0xffffffffu, TB, 1);
+        TB += __shfl_xor_sync(0xffffffffu, TB, 2);
+        if (t == 0) { S.red_T[cs][rA] = TA; S.red_T[cs][rB] = TB; }
+    }
+    producer_sync();
+    // (d) cumulative frequencies: f_k = 1 + floor term (+ remainder at the argmax)
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int r = half ? rB : rA;
+        const int32_t am = half ? amB : amA;
+        uint32_t T[8], Tsum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { T[q] = S.red_T[q][r]; Tsum += T[q]; }
+        const uint32_t rem = 65536u - 256u - Tsum;
+        uint32_t cum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < cs) cum += 32u + T[q] + ((am >> 5) == q ? rem : 0u);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int k0 = cs * 32 + nt * 8 + 2 * t;
+            const uint32_t f0 = 1u + (uint32_t)z[nt][2 * half] + (k0 == am ? rem : 0u);
+            const uint32_t f1 = 1u + (uint32_t)z[nt][2 * half + 1] + (k0 + 1 == am ? rem : 0u);
+            const uint32_t mine = f0 + f1;
+            uint32_t incl = mine;
+            const uint32_t n1 = __shfl_up_sync(0xffffffffu, incl, 1, 4);
+            if (t >= 1) incl += n1;
+            const uint32_t n2 = __shfl_up_sync(0xffffffffu, incl, 2, 4);
+            if (t >= 2) incl += n2;
+            const uint32_t tsum = __shfl_sync(0xffffffffu, incl, 3, 4);
+            const uint32_t start = cum + incl - mine;
+            // cdf[k] <= 65535 for every k <= 255 since every f >= 1
+            *reinterpret_cast<uint32_t *>(&S.cdf[b][r][k0]) = (start & 0xFFFFu) | ((start + f0) << 16);
+            cum += tsum;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kLT, 1) k_learned_decode(LearnedParams p) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    LSmem2 &S = *reinterpret_cast<LSmem2 *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t grp = blockIdx.x;
     const int nl = (int)min(32u, p.L - grp * 32);
-    if (!load_model(S, p.bits + p.model_off, p.status)) return;
+    if (!load_model2(S, p.bits + p.model_off, p.status)) return;
     if (tid < kNChan) {
         S.step[tid] = ld_f32(p.bits + p.chan_off + 4 * tid);
         S.offset[tid] = ld_f32(p.bits + p.chan_off + 4 * (kNChan + tid));
@@ -169,205 +370,75 @@ __global__ void __launch_bounds__(kLThreads, 1) k_learned_decode(LearnedParams p
         S.row0[tid] = r0;
         S.nrows[tid] = (uint32_t)(r1 - r0);
     }
-    for (int i = tid; i < 32 * 4 * kNChan; i += kLThreads) S.ctx[i] = 0;
-    GroupStream gs;
-    uint32_t x = 0x10000u;
-    if (warp == 0) {
-        group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, grp, nl, lane, gs, x, S.win);
-        S.slot[lane] = x & 0xFFFFu;
+    for (int i = tid; i < 32 * 4 * kNChan; i += kLT) S.ctx[i] = 0;
+    if (tid == 0) {
+        for (int b = 0; b < kNB; ++b) {
+            mbar_init(&S.full[b], kPW);
+            mbar_init(&S.empty[b], 1);
+        }
     }
     __syncthreads();
     uint32_t maxrows = 0;
     for (int r = 0; r < 32; ++r) maxrows = max(maxrows, S.nrows[r]);
+    const uint32_t K = maxrows * kNChan;  // steps
+    volatile int *abort_ = &S.abort_;
 
-    for (uint32_t i = 0; i < maxrows; ++i) {
-        for (int c = 0; c < kNChan; ++c) {
-            // ---- layer 1 (ALU): row r = tid >> 3, outputs 8 (tid & 7) .. +7
-            {
-                const int r = tid >> 3, o0 = (tid & 7) * 8;
-                int32_t u[4];
-#pragma unroll
-                for (int j = 1; j <= 4; ++j)
-                    u[j - 1] = (i >= (uint32_t)j) ? (int32_t)S.ctx[(r * 4 + ((i - j) & 3)) * kNChan + c] - 128 : 0;
-#pragma unroll
-                for (int o = o0; o < o0 + 8; ++o) {
-                    int32_t acc = S.b1[c * 64 + o];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc += (int32_t)S.w1[o * 4 + j] * u[j];
-                    S.h1[r * kRS + o] = (int8_t)requant(acc, S.m1, S.sh1);
-                }
+    if (warp < kPW) {
+        // ---------------- producers
+        for (uint32_t k = 0; k < K; ++k) {
+            const int b = (int)(k % kNB);
+            // every producer thread acquires the consumer's release of buffer b (and with it
+            // the tokens the consumer wrote into the context ring)
+            if (k >= (uint32_t)kNB && !mbar_wait(&S.empty[b], ((k / kNB) - 1) & 1, abort_)) {
+                *abort_ = 1;
+                if (tid == 0) set_status(p.status, SGS_E_TIMEOUT);
             }
-            __syncthreads();
-            // ---- layer 2 (mma): warp -> rows 16 (warp & 1), cols 16 (warp >> 1) .. +15
-            {
-                const int r0 = (warp & 1) * 16;
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int n0 = (warp >> 1) * 16 + q * 8;
-                    int32_t acc[4] = {0, 0, 0, 0};
-                    tile_16x8x64(acc, S.h1, r0, S.w2, n0, g, t);
-                    const int col = n0 + 2 * t;
-                    S.h2[(r0 + g) * kRS + col] = (int8_t)requant(acc[0] + S.b2[col], S.m2, S.sh2);
-                    S.h2[(r0 + g) * kRS + col + 1] = (int8_t)requant(acc[1] + S.b2[col + 1], S.m2, S.sh2);
-                    S.h2[(r0 + g + 8) * kRS + col] = (int8_t)requant(acc[2] + S.b2[col], S.m2, S.sh2);
-                    S.h2[(r0 + g + 8) * kRS + col + 1] = (int8_t)requant(acc[3] + S.b2[col + 1], S.m2, S.sh2);
-                }
-            }
-            __syncthreads();
-            // ---- layer 3 (mma): warp -> rows 16 (warp & 1), column quarter qw = warp >> 1
-            const int r0 = (warp & 1) * 16, qw = warp >> 1;
-            const int rA = r0 + g, rB = r0 + g + 8;
-            int32_t z[8][4];
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const int n0 = qw * 64 + nt * 8;
-                z[nt][0] = z[nt][1] = z[nt][2] = z[nt][3] = 0;
-                tile_16x8x64(z[nt], S.h2, r0, S.w3, n0, g, t);
-                const int col = n0 + 2 * t;
-                z[nt][0] += S.b3[col];
-                z[nt][1] += S.b3[col + 1];
-                z[nt][2] += S.b3[col];
-                z[nt][3] += S.b3[col + 1];
-            }
-            // (a) row max and lowest argmax
-            {
-                int32_t mA = z[0][0], mB = z[0][2];
-                int32_t iA = qw * 64 + 2 * t, iB = iA;
-#pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
-#pragma unroll
-                    for (int v = 0; v < 2; ++v) {
-                        const int32_t col = qw * 64 + nt * 8 + 2 * t + v;
-                        if (z[nt][v] > mA) { mA = z[nt][v]; iA = col; }
-                        if (z[nt][2 + v] > mB) { mB = z[nt][2 + v]; iB = col; }
-                    }
-                }
-#pragma unroll
-                for (int o = 1; o <= 2; o <<= 1) {
-                    const int32_t omA = __shfl_xor_sync(0xffffffffu, mA, o), oiA = __shfl_xor_sync(0xffffffffu, iA, o);
-                    const int32_t omB = __shfl_xor_sync(0xffffffffu, mB, o), oiB = __shfl_xor_sync(0xffffffffu, iB, o);
-                    if (omA > mA || (omA == mA && oiA < iA)) { mA = omA; iA = oiA; }
-                    if (omB > mB || (omB == mB && oiB < iB)) { mB = omB; iB = oiB; }
-                }
-                if (t == 0) {
-                    S.red_max[qw][rA] = mA; S.red_idx[qw][rA] = iA;
-                    S.red_max[qw][rB] = mB; S.red_idx[qw][rB] = iB;
-                }
-            }
-            __syncthreads();
-            int32_t zmA = S.red_max[0][rA], amA = S.red_idx[0][rA];
-            int32_t zmB = S.red_max[0][rB], amB = S.red_idx[0][rB];
-#pragma unroll
-            for (int q = 1; q < 4; ++q) {
-                if (S.red_max[q][rA] > zmA) { zmA = S.red_max[q][rA]; amA = S.red_idx[q][rA]; }
-                if (S.red_max[q][rB] > zmB) { zmB = S.red_max[q][rB]; amB = S.red_idx[q][rB]; }
-            }
-            // (b) e_k (kept in z) and partial sums
-            {
-                uint32_t sA = 0, sB = 0;
-#pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        const uint32_t d = (uint32_t)((v < 2 ? zmA : zmB) - z[nt][v]);
-                        uint64_t tt = ((uint64_t)d * S.ms) >> S.ss;
-                        const uint32_t tk = tt > 6144 ? 6144u : (uint32_t)tt;
-                        const uint32_t e = S.exp2q[tk & 255] >> (tk >> 8);
-                        z[nt][v] = (int32_t)e;
-                        if (v < 2) sA += e; else sB += e;
-                    }
-                }
-                sA += __shfl_xor_sync(0xffffffffu, sA, 1);
-                sA += __shfl_xor_sync(0xffffffffu, sA, 2);
-                sB += __shfl_xor_sync(0xffffffffu, sB, 1);
-                sB += __shfl_xor_sync(0xffffffffu, sB, 2);
-                if (t == 0) { S.red_sum[qw][rA] = sA; S.red_sum[qw][rB] = sB; }
-            }
-            __syncthreads();
-            if (tid < 32) {
-                const uint64_t E = (uint64_t)S.red_sum[0][tid] + S.red_sum[1][tid] + S.red_sum[2][tid] + S.red_sum[3][tid];
-                S.R[tid] = (uint32_t)((65280ull << 32) / E);
-            }
-            __syncthreads();
-            // (c) floor terms f_k - 1 = umulhi(e_k, R), per-quarter sums
-            const uint32_t RA = S.R[rA], RB = S.R[rB];
-            {
-                uint32_t TA = 0, TB = 0;
-#pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        const uint32_t fl = __umulhi((uint32_t)z[nt][v], v < 2 ? RA : RB);
-                        z[nt][v] = (int32_t)fl;
-                        if (v < 2) TA += fl; else TB += fl;
-                    }
-                }
-                TA += __shfl_xor_sync(0xffffffffu, TA, 1);
-                TA += __shfl_xor_sync(0xffffffffu, TA, 2);
-                TB += __shfl_xor_sync(0xffffffffu, TB, 1);
-                TB += __shfl_xor_sync(0xffffffffu, TB, 2);
-                if (t == 0) { S.red_T[qw][rA] = TA; S.red_T[qw][rB] = TB; }
-            }
-            __syncthreads();
-            // (d) CDF search inside the quarter that holds the lane's slot
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int r = half ? rB : rA;
-                const int32_t am = half ? amB : amA;
-                const bool live = r < nl && i < S.nrows[r];
-                const uint32_t T0 = S.red_T[0][r], T1 = S.red_T[1][r], T2 = S.red_T[2][r], T3 = S.red_T[3][r];
-                const uint32_t rem = 65536u - 256u - (T0 + T1 + T2 + T3);
-                const uint32_t Tq[4] = {T0, T1, T2, T3};
-                uint32_t base = 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q < qw) base += 64u + Tq[q] + ((am >> 6) == q ? rem : 0u);
-                const uint32_t qtot = 64u + Tq[qw] + ((am >> 6) == qw ? rem : 0u);
-                const uint32_t slot = S.slot[r];
-                // uniform per quad; the loop runs in every thread so the shuffles see the whole warp
-                const bool mine = live && slot >= base && slot < base + qtot;
-                uint32_t cum = base;
-#pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
-                    const int k0 = qw * 64 + nt * 8 + 2 * t;
-                    const uint32_t f0 = 1u + (uint32_t)z[nt][2 * half] + (k0 == am ? rem : 0u);
-                    const uint32_t f1 = 1u + (uint32_t)z[nt][2 * half + 1] + (k0 + 1 == am ? rem : 0u);
-                    const uint32_t mine_sum = f0 + f1;
-                    uint32_t incl = mine_sum;
-                    const uint32_t n1 = __shfl_up_sync(0xffffffffu, incl, 1, 4);
-                    if (t >= 1) incl += n1;
-                    const uint32_t n2 = __shfl_up_sync(0xffffffffu, incl, 2, 4);
-                    if (t >= 2) incl += n2;
-                    const uint32_t tsum = __shfl_sync(0xffffffffu, incl, 3, 4);
-                    const uint32_t start = cum + incl - mine_sum;
-                    if (mine && slot >= start && slot < start + mine_sum) {
-                        const bool first = slot < start + f0;
-                        S.res_s[r] = first ? (uint32_t)k0 : (uint32_t)k0 + 1;
-                        S.res_f[r] = first ? f0 : f1;
-                        S.res_c[r] = first ? start : start + f0;
-                    }
-                    cum += tsum;
-                }
-            }
-            __syncthreads();
-            // (e) warp 0: advance the 32 rANS states, emit tokens, refill from the stream
-            if (warp == 0) {
-                const bool live = lane < nl && i < S.nrows[lane];
-                if (live) {
-                    const uint32_t s = S.res_s[lane];
-                    x = S.res_f[lane] * (x >> 16) + S.slot[lane] - S.res_c[lane];
-                    S.ctx[(lane * 4 + (i & 3)) * kNChan + c] = (uint8_t)s;
-                    const uint64_t row = S.row0[lane] + i;
-                    const uint64_t col = p.out_index ? (uint64_t)p.out_index[row] : row;
-                    p.out[(uint64_t)c * p.n_rows + col] = dequant(s, S.step[c], S.offset[c]);
-                }
-                group_refill(gs, x, live);
-                S.slot[lane] = x & 0xFFFFu;
-            }
-            __syncthreads();
+            producer_sync();  // uniform exit: every producer sees the same abort flag
+            if (*abort_) break;
+            const uint32_t i = k / kNChan;
+            produce_step(S, i, (int)(k - i * kNChan), b);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.full[b]);
         }
+        return;
     }
-    if (warp == 0) {
+    // ---------------- consumer: the 32 rANS chains
+    GroupStream gs;
+    uint32_t x = 0x10000u;
+    group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, grp, nl, lane, gs, x, S.win);
+    bool aborted = false;
+    for (uint32_t k = 0; k < K; ++k) {
+        const int b = (int)(k % kNB);
+        // every lane acquires the producers' release of buffer b
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&S.full[b], (k / kNB) & 1, abort_));
+        if (!ok) {
+            if (lane == 0) { *abort_ = 1; set_status(p.status, SGS_E_TIMEOUT); }
+            aborted = true;
+            break;
+        }
+        const uint32_t i = k / kNChan;
+        const int c = (int)(k - i * kNChan);
+        const bool live = lane < nl && i < S.nrows[lane];
+        if (live) {
+            const uint32_t slot = x & 0xFFFFu;
+            const uint16_t *cdf = S.cdf[b][lane];
+            uint32_t s = 0;
+#pragma unroll
+            for (uint32_t st = 128; st > 0; st >>= 1)
+                if (cdf[s + st] <= slot) s += st;
+            const uint32_t lo = cdf[s];
+            const uint32_t hi = s < 255 ? cdf[s + 1] : 65536u;
+            x = (hi - lo) * (x >> 16) + slot - lo;
+            S.ctx[(lane * 4 + (i & 3)) * kNChan + c] = (uint8_t)s;
+            const uint64_t row = S.row0[lane] + i;
+            const uint64_t col = p.out_index ? (uint64_t)p.out_index[row] : row;
+            p.out[(uint64_t)c * p.n_rows + col] = dequant(s, S.step[c], S.offset[c]);
+        }
+        group_refill(gs, x, live);
+        __syncwarp();
+        if (lane == 0 && k + kNB < K) mbar_arrive(&S.empty[b]);
+    }
+    if (!aborted) {
         const bool bad = gs.bad || (lane < nl && x != 0x10000u) || (gs.ptr != gs.n_words);
         if (bad) set_status(p.status, SGS_E_CORRUPT);
     }
@@ -391,7 +462,7 @@ cudaError_t launch_learned_decode(const uint8_t *bits, const sgs_scene_info &inf
     p.out = out.attr;
     p.out_index = out.out_index;
     p.status = status;
-    const size_t smem = sizeof(LSmem);
+    const size_t smem = sizeof(LSmem2);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_learned_decode, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -399,7 +470,7 @@ cudaError_t launch_learned_decode(const uint8_t *bits, const sgs_scene_info &inf
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_learned_decode<<<p.G, kLThreads, smem, st>>>(p);
+    k_learned_decode<<<p.G, kLT, smem, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -16,56 +16,54 @@
 
 namespace sgs {
 
-// Expands n_tab compact tables (32-byte presence mask, then (f-1) as u16 per present
-// symbol, padded to 16 bytes, back to back from tab_off, all before tab_end) into
-// cdf[257] + bucket[256].  A table whose frequencies do not sum to 2^16 marks the stream
-// corrupt (an all-zero table is allowed where allow_empty: channels of an empty scene).
-__global__ void __launch_bounds__(256) k_tables(const uint8_t *bits, uint64_t tab_off,
-                                                uint64_t tab_end, int n_tab, uint8_t *tables,
-                                                int allow_empty, int *status) {
+// Expands static tables (32-byte presence mask, then (f-1) as u16 per present symbol; each
+// table's offset and size were validated by scene_query) into cdf[257] + bucket[256]; one
+// CTA per table.  A table whose frequencies do not sum to 2^16 marks the stream corrupt (an
+// all-zero attribute table is allowed for an empty scene).
+struct TableOffsets {
+    uint32_t off[kMaxTables];
+};
+
+__global__ void __launch_bounds__(256) k_tables(const uint8_t *bits, TableOffsets to,
+                                                uint8_t *tables, int n_geo_tables,
+                                                int allow_empty_attr, int *status) {
     __shared__ uint32_t sm[8];
     __shared__ uint32_t cdf[kTabCdfWords];
-    const int s = threadIdx.x;
-    uint64_t off = tab_off;
-    for (int t = 0; t < n_tab; ++t) {
-        const bool ok_hdr = off + 32 <= tab_end;
-        uint32_t present = 0;
-        if (ok_hdr) present = (bits[off + (s >> 3)] >> (s & 7)) & 1u;
-        uint32_t K;
-        const uint32_t rank = block_excl_scan_256(present, &K, sm);
-        const uint64_t body = off + 32;
-        const bool ok = ok_hdr && body + 2ull * K <= tab_end;
-        uint32_t f = 0;
-        if (ok && present) f = ld_u16(bits + body + 2ull * rank) + 1u;
-        uint32_t tot;
-        const uint32_t c = block_excl_scan_256(f, &tot, sm);
-        cdf[s] = c;
-        if (s == 0) cdf[256] = tot;
-        if (s == 0 && (!ok || !(tot == 65536u || (allow_empty && tot == 0))))
-            set_status(status, SGS_E_CORRUPT);
-        __syncthreads();
-        uint32_t *out_cdf = (uint32_t *)(tables + (size_t)t * kTabBytes);
-        uint8_t *out_bucket = tables + (size_t)t * kTabBytes + kTabCdfWords * 4;
-        out_cdf[s] = cdf[s];
-        if (s == 0) out_cdf[256] = cdf[256];
-        // bucket[b]: largest symbol whose cdf <= b * 256 (a lower bound for any slot >= b*256)
-        const uint32_t key = (uint32_t)s << 8;
-        int lo = 0, hi = 255;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (cdf[mid] <= key) lo = mid; else hi = mid - 1;
-        }
-        out_bucket[s] = (uint8_t)lo;
-        __syncthreads();
-        off = body + ((2ull * K + 15) & ~15ull);
-        // the mask (32 bytes) is already 16-aligned; the body is padded to 16
+    const int s = threadIdx.x, t = blockIdx.x;
+    const uint64_t off = to.off[t];
+    const uint32_t present = (bits[off + (s >> 3)] >> (s & 7)) & 1u;
+    uint32_t K;
+    const uint32_t rank = block_excl_scan_256(present, &K, sm);
+    const uint32_t f = present ? ld_u16(bits + off + 32 + 2ull * rank) + 1u : 0u;
+    uint32_t tot;
+    const uint32_t c = block_excl_scan_256(f, &tot, sm);
+    cdf[s] = c;
+    if (s == 0) {
+        cdf[256] = tot;
+        const bool empty_ok = allow_empty_attr && t >= n_geo_tables && tot == 0;
+        if (!(tot == 65536u || empty_ok)) set_status(status, SGS_E_CORRUPT);
     }
+    __syncthreads();
+    uint32_t *out_cdf = reinterpret_cast<uint32_t *>(tables + (size_t)t * kTabBytes);
+    uint8_t *out_bucket = tables + (size_t)t * kTabBytes + kTabCdfWords * 4;
+    out_cdf[s] = cdf[s];
+    if (s == 0) out_cdf[256] = cdf[256];
+    // bucket[b]: largest symbol whose cdf <= b * 256 (a lower bound for any slot >= b*256)
+    const uint32_t key = (uint32_t)s << 8;
+    int lo = 0, hi = 255;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cdf[mid] <= key) lo = mid; else hi = mid - 1;
+    }
+    out_bucket[s] = (uint8_t)lo;
 }
 
-cudaError_t launch_tables(const uint8_t *bits, uint64_t tab_off, uint64_t tab_end, int n_tab,
-                          uint8_t *tables, int allow_empty, int *status, cudaStream_t st) {
-    if (n_tab <= 0) return cudaSuccess;
-    k_tables<<<1, 256, 0, st>>>(bits, tab_off, tab_end, n_tab, tables, allow_empty, status);
+cudaError_t launch_tables(const uint8_t *bits, const sgs_scene_info &info, int n_geo_tables,
+                          uint8_t *tables, int *status, cudaStream_t st) {
+    if (info.n_tables == 0) return cudaSuccess;
+    TableOffsets to;
+    for (uint32_t i = 0; i < info.n_tables; ++i) to.off[i] = info.table_off[i];
+    k_tables<<<info.n_tables, 256, 0, st>>>(bits, to, tables, n_geo_tables, info.n_rows == 0, status);
     return cudaGetLastError();
 }
 
@@ -103,19 +101,17 @@ __global__ void __launch_bounds__(32 * kAttrWarps) k_rans_attr(AttrParams p) {
     const int lane = threadIdx.x & 31;
     const uint32_t g = blockIdx.x * kAttrWarps + (threadIdx.x >> 5);
     if (g >= p.G) return;
-    const uint32_t j = g * 32 + lane;
+    // the group's rows, dealt round robin to its lanes: lane j holds rows R0 + j + k nl
     const int nl = (int)min(32u, p.L - g * 32);
-    uint64_t r0 = 0, r1 = 0;
-    if (lane < nl) {
-        r0 = (uint64_t)j * p.n_rows / p.L;
-        r1 = (uint64_t)(j + 1) * p.n_rows / p.L;
-    }
-    const uint64_t n = (r1 - r0) * kNChan;
+    const uint64_t R0 = (uint64_t)g * 32 * p.n_rows / p.L;
+    const uint64_t R1 = (uint64_t)(g * 32 + nl) * p.n_rows / p.L;
+    const uint64_t my_rows = (lane < nl && R0 + lane < R1) ? (R1 - R0 - lane + nl - 1) / nl : 0;
+    const uint64_t n = my_rows * kNChan;
     GroupStream gs;
     uint32_t x;
     group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, g, nl, lane, gs, x, s_win);
     const uint64_t maxn = warp_max_u64(n);
-    uint64_t row = r0;
+    uint64_t row = R0 + lane;
     int c = 0;
     for (uint64_t t = 0; t < maxn; ++t) {
         const bool active = t < n;
@@ -123,7 +119,7 @@ __global__ void __launch_bounds__(32 * kAttrWarps) k_rans_attr(AttrParams p) {
             const uint32_t s = rans_sym(x, s_cdf + c * kTabCdfWords, s_bucket + c * 256);
             const uint64_t col = p.out_index ? (uint64_t)p.out_index[row] : row;
             p.out[(uint64_t)c * p.n_rows + col] = dequant(s, s_step[c], s_off[c]);
-            if (++c == kNChan) { c = 0; ++row; }
+            if (++c == kNChan) { c = 0; row += nl; }
         }
         group_refill(gs, x, active);
     }

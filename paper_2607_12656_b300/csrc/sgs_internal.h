@@ -68,8 +68,8 @@ __device__ __forceinline__ void set_status(int *status, int code) {
 }
 
 // Launchers (return cudaError_t of the launch).
-cudaError_t launch_tables(const uint8_t *bits, uint64_t tab_off, uint64_t tab_end, int n_tab,
-                          uint8_t *tables, int allow_empty, int *status, cudaStream_t st);
+cudaError_t launch_tables(const uint8_t *bits, const sgs_scene_info &info, int n_geo_tables,
+                          uint8_t *tables, int *status, cudaStream_t st);
 cudaError_t launch_rans_static_attr(const uint8_t *bits, const sgs_scene_info &info,
                                     const uint8_t *tables, const sgs_scene_out &out, int *status,
                                     cudaStream_t st);
@@ -78,9 +78,12 @@ cudaError_t launch_rans_static_geo(const uint8_t *bits, const sgs_scene_info &in
                                    int *status, cudaStream_t st);
 cudaError_t launch_geo_copy_raw(const uint8_t *bits, const sgs_scene_info &info,
                                 const GeoPlan &plan, uint8_t *geo_bytes, cudaStream_t st);
+// The top levels run on st2 (forked from st with ev_a, joined with ev_b) concurrently with
+// the popcount scan; pass st2 == st to run everything on one stream.
 cudaError_t launch_octree(const uint8_t *geo, const sgs_scene_info &info, const GeoPlan &plan,
                           const uint8_t *bits, const Scratch &s, const sgs_scene_out &out,
-                          int *status, cudaStream_t st);
+                          int *status, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_a,
+                          cudaEvent_t ev_b);
 cudaError_t launch_fixed(const uint8_t *bits, const sgs_scene_info &info,
                          const sgs_scene_out &out, int *status, cudaStream_t st);
 cudaError_t launch_learned_decode(const uint8_t *bits, const sgs_scene_info &info,

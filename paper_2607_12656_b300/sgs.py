@@ -26,7 +26,8 @@ class SceneInfo(ctypes.Structure):
     _fields_ = [("mode", u32), ("geo_mode", u32), ("n_in", u32), ("n_rows", u32), ("depth", u32),
                 ("n_leaves", u32), ("n_dup", u32), ("lanes", u32), ("geo_lanes", u32),
                 ("n_level", u32 * (MAX_DEPTH + 1)), ("n_geo", u64), ("n_geo_coded", u64),
-                ("off", u64 * 11), ("total_len", u64), ("scratch_bytes", u64)]
+                ("off", u64 * 11), ("total_len", u64), ("scratch_bytes", u64),
+                ("n_tables", u32), ("table_off", u32 * (NCHAN + MAX_DEPTH))]
 
 
 class SceneOut(ctypes.Structure):
