@@ -165,6 +165,31 @@ int scene_query(const uint8_t *bits, size_t len, sgs_scene_info *info);
 int scene_decode(sgs_ctx *ctx, const uint8_t *bits_dev, const sgs_scene_info *info,
                  const sgs_scene_out *out, sgs_stream stream);
 
+/* Size of the fixed device scratch area scene_decode_noalloc uses (64 MiB; enough for the
+ * 1,000,000-Gaussian depth-16 fixed-length scene). */
+#define SGS_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* Decodes one scene without allocating anything: for callers that cannot allocate device
+ * memory (an engine or renderer that owns all device memory and forbids allocation after
+ * start-up, or a latency-critical loop where cudaMalloc / cudaFree could synchronize the
+ * device), and so cannot create an sgs_ctx.  The paper has no counterpart; this is runtime
+ * plumbing.  Instead of a context's scratch it uses a fixed device array of
+ * SGS_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that loads the
+ * library holds until the process exits.  Arguments are those of scene_decode (bits_dev:
+ * device copy of the whole bitstream, 16-byte aligned; info from scene_query; out:
+ * caller-allocated device outputs), on the current CUDA device, on `stream`.
+ *   - Synchronous: returns after the decode has completed on `stream`, with its status
+ *     (SGS_OK, SGS_E_CORRUPT, SGS_E_TIMEOUT).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call on a device shares the one array and finds the previous call's contents
+ *     (the call clears what must start at zero).  Calls that overlap on the GPU -- from two
+ *     host threads, or on two streams -- race on the array and must not be made.
+ * Errors: SGS_E_INVALID (NULL or misaligned arguments), SGS_E_NOMEM (the scene needs more
+ * scratch than SGS_NOALLOC_SCRATCH_BYTES minus 256 bytes; nothing is launched), SGS_E_CUDA. */
+int scene_decode_noalloc(const uint8_t *bits_dev, const sgs_scene_info *info,
+                         const sgs_scene_out *out, sgs_stream stream);
+
 /* One batch item for scene_decode_batch. */
 typedef struct {
     const uint8_t *bits_dev;

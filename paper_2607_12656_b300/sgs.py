@@ -84,6 +84,7 @@ def lib() -> ctypes.CDLL:
         L.sgs_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_float), i32]
         L.sgs_launch_count.argtypes = [P]
         L.sgs_launch_count.restype = u64
+        L.scene_decode_noalloc.argtypes = [P, ctypes.POINTER(SceneInfo), ctypes.POINTER(SceneOut), P]
         _lib = L
     return _lib
 
@@ -189,6 +190,21 @@ def scene_decode(ctx: Context, bits_dev, info: SceneInfo, attr, pos, coord=None,
     out = _out(attr, pos, coord, out_index)
     _check(lib().scene_decode(ctx.handle, _ptr(bits_dev), ctypes.byref(info), ctypes.byref(out),
                               _stream(stream)), "scene_decode")
+
+
+NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def scene_decode_noalloc(bits_dev, info: SceneInfo, attr, pos, coord=None, out_index=None,
+                         stream=None) -> int:
+    """Decodes one scene with the library's fixed scratch array (no allocation, no context);
+    synchronous; returns the decode status (raises on argument or size errors)."""
+    out = _out(attr, pos, coord, out_index)
+    code = lib().scene_decode_noalloc(_ptr(bits_dev), ctypes.byref(info), ctypes.byref(out),
+                                      _stream(stream))
+    if code in (E_INVALID, E_NOMEM, E_CUDA, E_UNSUPPORTED):
+        raise SgsError(code, "scene_decode_noalloc")
+    return code
 
 
 def scene_decode_batch(ctx: Context, items: list, stream=None) -> None:
