@@ -117,7 +117,8 @@ def make_bitstream(w: dict, ctx=None):
     model = None
     if w["mode"] == 2:
         from paper_2607_12656_b300 import learned
-        model = learned.train_and_freeze(ctx, sc, w["depth"], w["lanes"], steps=2000, batch=65536, seed=1)
+        model = learned.train_and_freeze(ctx, sc, w["depth"], w["lanes"], steps=w.get("train_steps", 2000),
+                                         batch=65536, seed=1)
         kw["model"] = model
         kw["ctx"] = ctx
     return sc, sgs.scene_encode(sc.pos, sc.attr, **kw)
@@ -309,8 +310,19 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture")
+    ap.add_argument("--n", type=int, default=None, help="override the workload's Gaussian count")
+    ap.add_argument("--lanes", type=int, default=None, help="override the workload's rANS lanes")
+    ap.add_argument("--train-steps", type=int, default=None, help="override the learned model's steps")
     args = ap.parse_args()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.n is not None:
+        w["n"] = args.n
+        w["desc"] += " [resized: N=%d]" % args.n
+    if args.lanes is not None:
+        w["lanes"] = args.lanes
+        w["desc"] += " [lanes=%d]" % args.lanes
+    if args.train_steps is not None:
+        w["train_steps"] = args.train_steps
     if args.impl == "reference":
         run_reference(args, w)
     else:

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <cuda_bf16.h>
 
 #include <vector>
 
@@ -27,7 +28,6 @@ namespace sgs {
 
 __constant__ uint32_t kExp2Q[256] = {SGS_EXP2Q_VALUES};
 
-constexpr int kRS = 80;  // smem row stride (bytes) of int8 rows of 64: conflict-free fragments
 
 // Frozen model blob offsets (bytes).
 constexpr int kMB_B1 = 32, kMB_B2 = 14368, kMB_B3 = 14624, kMB_W1 = 15648, kMB_W2 = 15904,
@@ -39,34 +39,45 @@ __device__ __forceinline__ int32_t requant(int32_t acc, int32_t m, int32_t sh) {
     return (int32_t)(v > 127 ? 127 : v);
 }
 
-__device__ __forceinline__ void mma_s8(int32_t (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                       uint32_t a3, uint32_t b0, uint32_t b1) {
+// Layers 2-3 on the tensor cores in bf16 with fp32 accumulation.  This is exact: int8
+// weights and activations in [0, 127] are exact in bf16, their products exact in fp32, and
+// every partial sum of 64 products is an integer below 2^21 < 2^24.  (B300 has no tcgen05
+// int8 kind and a far slower int8 mma path.)
+constexpr int kBS = 72;  // smem row stride in bf16 elements (64 used): conflict-free fragments
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
     asm volatile(
-        "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};"
-        : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ uint32_t lds32(const int8_t *p) {
+__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16 *p) {
     return *reinterpret_cast<const uint32_t *>(p);
 }
 
-// acc(16 x 8 tile at rows r0.., cols n0..) += A[r0.., 0..63] * W[n0.., 0..63]^T (both int8 rows
-// of stride kRS in smem).
-__device__ __forceinline__ void tile_16x8x64(int32_t (&acc)[4], const int8_t *A, int r0,
-                                             const int8_t *W, int n0, int g, int t) {
+// acc(16 x 8 tile at rows r0.., cols n0..) += A[r0.., 0..63] * W[n0.., 0..63]^T, both bf16
+// rows of stride kBS in shared memory; returns the exact integer sums.
+__device__ __forceinline__ void tile_16x8x64(int32_t (&out)[4], const __nv_bfloat16 *A, int r0,
+                                             const __nv_bfloat16 *W, int n0, int g, int t) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int kk = 0; kk < 64; kk += 32) {
-        const uint32_t a0 = lds32(A + (r0 + g) * kRS + kk + 4 * t);
-        const uint32_t a1 = lds32(A + (r0 + g + 8) * kRS + kk + 4 * t);
-        const uint32_t a2 = lds32(A + (r0 + g) * kRS + kk + 16 + 4 * t);
-        const uint32_t a3 = lds32(A + (r0 + g + 8) * kRS + kk + 16 + 4 * t);
-        const uint32_t b0 = lds32(W + (n0 + g) * kRS + kk + 4 * t);
-        const uint32_t b1 = lds32(W + (n0 + g) * kRS + kk + 16 + 4 * t);
-        mma_s8(acc, a0, a1, a2, a3, b0, b1);
+    for (int kk = 0; kk < 64; kk += 16) {
+        const uint32_t a0 = lds32(A + (r0 + g) * kBS + kk + 2 * t);
+        const uint32_t a1 = lds32(A + (r0 + g + 8) * kBS + kk + 2 * t);
+        const uint32_t a2 = lds32(A + (r0 + g) * kBS + kk + 8 + 2 * t);
+        const uint32_t a3 = lds32(A + (r0 + g + 8) * kBS + kk + 8 + 2 * t);
+        const uint32_t b0 = lds32(W + (n0 + g) * kBS + kk + 2 * t);
+        const uint32_t b1 = lds32(W + (n0 + g) * kBS + kk + 8 + 2 * t);
+        mma_bf16(acc, a0, a1, a2, a3, b0, b1);
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out[i] = __float2int_rn(acc[i]);
 }
+
+__device__ __forceinline__ __nv_bfloat16 bf(int v) { return __int2bfloat16_rn(v); }
 
 struct LearnedParams {
     const uint8_t *bits;
@@ -92,13 +103,13 @@ constexpr uint32_t kWaitLimit = 1u << 24;
 struct LSmem2 {
     int8_t w1[64 * 4];
     int32_t b1[kNChan * 64];
-    int8_t w2[64 * kRS];
+    alignas(16) __nv_bfloat16 w2[64 * kBS];
     int32_t b2[64];
-    int8_t w3[256 * kRS];
+    alignas(16) __nv_bfloat16 w3[256 * kBS];
     int32_t b3[256];
     uint32_t exp2q[256];
-    int8_t h1[32 * kRS];
-    int8_t h2[32 * kRS];
+    alignas(16) __nv_bfloat16 h1[32 * kBS];
+    alignas(16) __nv_bfloat16 h2[32 * kBS];
     uint8_t ctx[32 * 4 * kNChan];            // [lane][ring row][channel]
     alignas(16) uint16_t cdf[kNB][32][256];  // cumulative frequency of each symbol
     alignas(16) uint16_t win[kWinWords];     // consumer's word-stream window
@@ -177,8 +188,8 @@ __device__ bool load_model2(LSmem2 &S, const uint8_t *m, int *status) {
         S.exp2q[i] = kExp2Q[i];
         S.w1[i] = (int8_t)m[kMB_W1 + i];
     }
-    for (int i = tid; i < 64 * 64; i += kLT) S.w2[(i >> 6) * kRS + (i & 63)] = (int8_t)m[kMB_W2 + i];
-    for (int i = tid; i < 256 * 64; i += kLT) S.w3[(i >> 6) * kRS + (i & 63)] = (int8_t)m[kMB_W3 + i];
+    for (int i = tid; i < 64 * 64; i += kLT) S.w2[(i >> 6) * kBS + (i & 63)] = bf((int8_t)m[kMB_W2 + i]);
+    for (int i = tid; i < 256 * 64; i += kLT) S.w3[(i >> 6) * kBS + (i & 63)] = bf((int8_t)m[kMB_W3 + i]);
     __syncthreads();
     if (badb) atomicOr(&S.bad, 1);
     __syncthreads();
@@ -205,7 +216,7 @@ __device__ __forceinline__ void produce_step(LSmem2 &S, uint32_t i, int c, int b
             int32_t acc = S.b1[c * 64 + o];
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc += (int32_t)S.w1[o * 4 + j] * u[j];
-            S.h1[r * kRS + o] = (int8_t)requant(acc, S.m1, S.sh1);
+            S.h1[r * kBS + o] = bf(requant(acc, S.m1, S.sh1));
         }
     }
     producer_sync();
@@ -215,10 +226,10 @@ __device__ __forceinline__ void produce_step(LSmem2 &S, uint32_t i, int c, int b
         int32_t acc[4] = {0, 0, 0, 0};
         tile_16x8x64(acc, S.h1, r0, S.w2, n0, g, t);
         const int col = n0 + 2 * t;
-        S.h2[(r0 + g) * kRS + col] = (int8_t)requant(acc[0] + S.b2[col], S.m2, S.sh2);
-        S.h2[(r0 + g) * kRS + col + 1] = (int8_t)requant(acc[1] + S.b2[col + 1], S.m2, S.sh2);
-        S.h2[(r0 + g + 8) * kRS + col] = (int8_t)requant(acc[2] + S.b2[col], S.m2, S.sh2);
-        S.h2[(r0 + g + 8) * kRS + col + 1] = (int8_t)requant(acc[3] + S.b2[col + 1], S.m2, S.sh2);
+        S.h2[(r0 + g) * kBS + col] = bf(requant(acc[0] + S.b2[col], S.m2, S.sh2));
+        S.h2[(r0 + g) * kBS + col + 1] = bf(requant(acc[1] + S.b2[col + 1], S.m2, S.sh2));
+        S.h2[(r0 + g + 8) * kBS + col] = bf(requant(acc[2] + S.b2[col], S.m2, S.sh2));
+        S.h2[(r0 + g + 8) * kBS + col + 1] = bf(requant(acc[3] + S.b2[col + 1], S.m2, S.sh2));
     }
     producer_sync();
     // layer 3: warp -> rows 16 (warp & 1), column slice cs = warp >> 1 (32 columns)
