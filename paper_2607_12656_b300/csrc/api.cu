@@ -32,9 +32,8 @@ namespace sgs {
 
 size_t octree_scan_tiles(uint64_t n_geo);
 int octree_launches(const sgs_scene_info &info, const GeoPlan &plan);
-size_t octree_chunks(uint64_t n_geo);
-void octree_code_buffers(const sgs_scene_info &info, const GeoPlan &plan, uint64_t *pingpong,
-                         uint64_t *all);
+size_t octree_words(uint64_t n_geo);
+void octree_code_buffers(const sgs_scene_info &info, const GeoPlan &plan, uint64_t *pingpong);
 
 static inline uint64_t a256(uint64_t x) { return (x + 255) & ~255ull; }
 
@@ -82,14 +81,13 @@ size_t scratch_need(const sgs_scene_info &info, Scratch *s, uint8_t *base) {
     };
     Scratch t;
     t.geo_bytes = take(info.geo_mode == SGS_GEO_RANS ? info.n_geo : 0);
-    t.chunk_prefix = reinterpret_cast<uint32_t *>(take(4 * (octree_chunks(info.n_geo) + 1)));
+    t.p4 = reinterpret_cast<uint32_t *>(take(4 * (octree_words(info.n_geo) + 16)));
     t.scan_flags = reinterpret_cast<uint64_t *>(take(8 * (octree_scan_tiles(info.n_geo) + 1)));
     t.ticket = reinterpret_cast<uint32_t *>(take(256));
-    uint64_t pp, all;
-    octree_code_buffers(info, plan, &pp, &all);
+    uint64_t pp;
+    octree_code_buffers(info, plan, &pp);
     t.codes[0] = reinterpret_cast<uint64_t *>(take(pp));
     t.codes[1] = reinterpret_cast<uint64_t *>(take(pp));
-    t.codes[2] = reinterpret_cast<uint64_t *>(take(all));
     const int n_tab = plan.n_coded_levels + (info.mode == SGS_MODE_STATIC ? kNChan : 0);
     t.tables = take((uint64_t)n_tab * kTabBytes);
     t.dup_prefix = reinterpret_cast<uint32_t *>(take(4ull * (info.n_dup + 1)));

@@ -2,14 +2,16 @@
 // tokens, one per internal node, level by level; one position per voxel plus duplicate
 // counts as metadata).
 //
-// The tokens of all levels form one breadth-first array B.  With P(g) = sum of popc(B[h])
-// for h < g, the children of node g are the nodes 1 + P(g) + j (j < popc(B[g])), leaves
-// numbered after the internal nodes.  So one device-wide scan of popcounts (decoupled
-// look-back, one pass over B) fixes every parent -> child index; expansion is then a map per
-// level: each node writes its children's packed coordinates (x:21 | y:21 | z:21 bits).
-// The few small top levels are expanded by one CTA in shared memory; each deeper level is
-// one launch over tiles of 2048 nodes.  Leaves write the fp32 voxel-centre positions of
-// their rows (a leaf with duplicates owns several consecutive rows).
+// The tokens of all levels form one breadth-first array B.  With P(x) = sum of popc(B[h])
+// for h < x, the children of node x are the nodes 1 + P(x) + j (j < popc(B[x])), leaves
+// numbered after the internal nodes.  One device-wide scan (decoupled look-back) writes P at
+// every 4-byte word of B, so any node's children follow from two loads: P4[x / 4] plus the
+// popcount of the bytes of its word below x.  Expansion is then a map with no block-wide
+// synchronisation: a thread takes one node and walks its subtree depth first through up to
+// kMaxFuse levels (a small stack of child iterators in shared memory), writing the packed
+// coordinates (x:21 | y:21 | z:21) of the nodes at the end of its levels or, at the last
+// level, the voxel-centre positions of the leaf rows.  The few small top levels are
+// expanded by one CTA, concurrently with the scan.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -19,14 +21,11 @@
 namespace sgs {
 
 constexpr int kScanThreads = 256;
-constexpr int kChunk = 64;                         // bytes per scan chunk
-constexpr int kScanTile = kScanThreads * kChunk;   // 16 KiB of tokens per tile
 constexpr uint32_t kSpinLimit = 1u << 22;          // bounded look-back wait
 constexpr int kTopThreads = 1024;
 constexpr uint32_t kTopCap = 2048;                 // levels the top kernel keeps in smem
-constexpr int kLvlThreads = 256;
-constexpr int kLvlPer = 8;                         // nodes per thread
-constexpr int kLvlTile = kLvlThreads * kLvlPer;
+constexpr int kExpThreads = 128;
+constexpr int kMaxFuse = 12;                       // levels one expansion thread walks
 constexpr uint64_t kM21 = (1ull << 21) - 1;
 
 struct LeafOut {
@@ -79,34 +78,45 @@ __device__ __forceinline__ void write_leaf(const LeafOut &o, uint32_t u, uint64_
 
 // ------------------------------------------------------------------ popcount scan
 
-__device__ __forceinline__ uint32_t popc_bytes(const uint8_t *B, uint64_t a, uint64_t b) {
-    uint32_t s = 0;
-    for (uint64_t i = a; i < b; ++i) s += __popc((uint32_t)B[i]);
-    return s;
+
+// Word k of B with the bytes at or past n cleared.
+__device__ __forceinline__ uint32_t word_at(const uint8_t *B, uint64_t n, uint64_t k) {
+    if (4 * k + 4 <= n) return reinterpret_cast<const uint32_t *>(B)[k];
+    uint32_t w = 0;
+    for (uint64_t i = 4 * k; i < n; ++i) w |= (uint32_t)B[i] << (8 * (i - 4 * k));
+    return w;
 }
 
+// P4[k] = popcount of B[0, 4k) for k = 0 .. ceil(n/4).  Tile = 256 threads x 64 bytes.
 __global__ void __launch_bounds__(kScanThreads) k_octree_scan(const uint8_t *B, uint64_t n,
-                                                              uint32_t *chunk_prefix,
-                                                              uint64_t n_chunks, uint64_t *flags,
-                                                              uint32_t *ticket, int *status) {
+                                                              uint32_t *P4, uint64_t n_words,
+                                                              uint64_t *flags, uint32_t *ticket,
+                                                              int *status) {
     __shared__ uint32_t sm[8];
     __shared__ uint32_t s_tile, s_prefix;
     if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
-    const uint64_t k = (uint64_t)tile * kScanThreads + threadIdx.x;
-    const uint64_t a = k * kChunk;
+    const uint64_t k = (uint64_t)tile * kScanThreads + threadIdx.x;  // 64-byte chunk
+    const uint64_t w0 = 16 * k;                                      // its first word
+    uint32_t cnt[16];
     uint32_t sum = 0;
-    if (a + kChunk <= n) {
-        const uint4 *p = reinterpret_cast<const uint4 *>(B + a);
+    if (64 * k + 64 <= n) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(B + 64 * k);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const uint4 v = p[i];
-            sum += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+            cnt[4 * i] = __popc(v.x);
+            cnt[4 * i + 1] = __popc(v.y);
+            cnt[4 * i + 2] = __popc(v.z);
+            cnt[4 * i + 3] = __popc(v.w);
         }
-    } else if (a < n) {
-        sum = popc_bytes(B, a, n);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) cnt[i] = (w0 + i) * 4 < n ? __popc(word_at(B, n, w0 + i)) : 0u;
     }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) sum += cnt[i];
     uint32_t agg;
     const uint32_t local = block_excl_scan_256(sum, &agg, sm);
     // decoupled look-back, 32 predecessors per step (flag 1 = aggregate, 2 = inclusive prefix)
@@ -150,27 +160,21 @@ __global__ void __launch_bounds__(kScanThreads) k_octree_scan(const uint8_t *B, 
         }
     }
     __syncthreads();
-    if (k < n_chunks) chunk_prefix[k] = s_prefix + local;
-    if (k + 1 == n_chunks) chunk_prefix[n_chunks] = s_prefix + local + sum;
-}
-
-// P(g): popcount of B[0, g).
-__device__ __forceinline__ uint32_t prefix_at(const uint8_t *B, const uint32_t *chunk_prefix,
-                                              uint64_t g) {
-    const uint64_t c = g / kChunk;
-    return chunk_prefix[c] + popc_bytes(B, c * kChunk, g);
-}
-
-// Warp-cooperative P(g) (all 32 lanes call; result in every lane).
-__device__ __forceinline__ uint32_t prefix_at_warp(const uint8_t *B, const uint32_t *chunk_prefix,
-                                                   uint64_t g) {
-    const int lane = threadIdx.x & 31;
-    const uint64_t c = g / kChunk, base = c * kChunk;
-    uint32_t s = 0;
-    for (uint64_t i = base + lane; i < g; i += 32) s += __popc((uint32_t)B[i]);
+    uint32_t run = s_prefix + local;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return chunk_prefix[c] + s;
+    for (int i = 0; i < 16; ++i) {
+        if (w0 + i <= n_words) P4[w0 + i] = run;  // P4[n_words] = total
+        run += cnt[i];
+    }
+}
+
+// Node x of B: its token and P(x) from the word prefix.
+__device__ __forceinline__ void node_at(const uint8_t *B, uint64_t n, const uint32_t *P4,
+                                        uint64_t x, uint32_t &byte, uint32_t &p) {
+    const uint32_t w = word_at(B, n, x >> 2);
+    const uint32_t sh = 8u * (uint32_t)(x & 3);
+    byte = (w >> sh) & 0xFFu;
+    p = P4[x >> 2] + __popc(w & ((1u << sh) - 1u));
 }
 
 // ------------------------------------------------------------------ duplicates
@@ -283,167 +287,76 @@ __global__ void __launch_bounds__(kTopThreads) k_octree_top(TopParams p) {
     }
 }
 
-// ------------------------------------------------------------------ deep levels
+// ------------------------------------------------------------------ fused levels
 
-// Expands one chunk of up to kLvlTile consecutive nodes [x0, x1) of level l.  Thread tid
-// handles nodes x0 + 256 q + tid (q < 8, coalesced); all 8 rounds are loaded first, then one
-// two-level block scan (warp scans per round, warp totals through shared memory) orders the
-// children.  p_x0 = P(x0).  Children go to codes_out[global child index - out_base], or to the
-// leaves.  Returns the number of children (block-uniform).  sm: 64 words of shared memory.
-__device__ __forceinline__ uint32_t expand_chunk(const uint8_t *B, uint64_t x0, uint64_t x1,
-                                                 uint32_t p_x0, const uint64_t *codes_in,
-                                                 uint64_t in_base, uint64_t *codes_out,
-                                                 uint64_t out_base, uint64_t out_hi,
-                                                 const LeafOut *leaf, uint64_t leaf_base,
-                                                 uint32_t *sm, int *status) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int Q = kLvlTile / kLvlThreads;
-    constexpr int NW = kLvlThreads / 32;
-    uint32_t byte[Q];
-    uint64_t pc[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const uint64_t x = x0 + (uint64_t)q * kLvlThreads + threadIdx.x;
-        byte[q] = x < x1 ? B[x] : 0u;
-        pc[q] = x < x1 ? codes_in[x - in_base] : 0ull;
-    }
-    uint32_t ex[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const uint32_t v = __popc(byte[q]);
-        uint32_t incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t n = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += n;
-        }
-        ex[q] = incl - v;
-        if (lane == 31) sm[q * NW + warp] = incl;
-    }
-    __syncthreads();
-    uint32_t total = 0;
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        uint32_t before = 0, round = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const uint32_t t = sm[q * NW + w];
-            before += w < warp ? t : 0u;
-            round += t;
-        }
-        ex[q] += total + before;
-        total += round;
-    }
-    __syncthreads();  // sm is reused by the next chunk
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        uint64_t child = 1ull + p_x0 + ex[q];  // global BFS index of the first child
-        uint32_t b = byte[q];
-        while (b) {
-            const uint32_t k = __ffs(b) - 1;
-            b &= b - 1;
-            if (child >= out_hi) { set_status(status, SGS_E_CORRUPT); break; }
-            const uint64_t cc = child_code(pc[q], k);
-            if (leaf) write_leaf(*leaf, (uint32_t)(child - leaf_base), cc, status);
-            else codes_out[child - out_base] = cc;
-            ++child;
-        }
-    }
-    return total;
-}
-
-struct LevelParams {
+// Thread per node x of level ls: depth-first through levels ls .. le-1, emitting the nodes of
+// level le (codes) or, when le = D, the leaf rows.  The stack holds one child iterator per
+// level (P of the node, remaining child mask, children taken, packed coordinates).
+struct ExpandParams {
     const uint8_t *B;
-    const uint32_t *chunk_prefix;
-    uint64_t lo, n;          // level's BFS offset and node count
-    uint64_t next_lo, n_next;
-    const uint64_t *codes_in;   // indexed by x - in_base
-    uint64_t in_base;
-    uint64_t *codes_out;        // indexed by child - out_base; NULL when the next level is the leaves
-    uint64_t out_base;
+    uint64_t n_geo;
+    const uint32_t *P4;
+    int ls, le, depth;
+    uint64_t level_off[SGS_MAX_DEPTH + 2];  // BFS offset of each level, [D+1] = end of leaves
+    const uint64_t *codes_in;               // level ls, indexed by x - level_off[ls]
+    uint64_t *codes_out;                    // level le (NULL when le = D)
     LeafOut leaf;
+    int check;                              // CTA 0 verifies the level counts
     int *status;
 };
 
-__global__ void __launch_bounds__(kLvlThreads) k_octree_level(LevelParams p) {
-    __shared__ uint32_t sm[64];
-    __shared__ uint32_t s_p;
-    const uint64_t x0 = p.lo + (uint64_t)blockIdx.x * kLvlTile;
-    const uint64_t x1 = x0 + kLvlTile < p.lo + p.n ? x0 + kLvlTile : p.lo + p.n;
-    if (threadIdx.x < 32) {
-        const uint32_t pg = prefix_at_warp(p.B, p.chunk_prefix, x0);
-        if (threadIdx.x == 0) s_p = pg;
-        if (blockIdx.x == 0) {  // sum of popcounts of the level = nodes of the next level
-            const uint32_t p_lo = prefix_at_warp(p.B, p.chunk_prefix, p.lo);
-            const uint32_t p_hi = prefix_at_warp(p.B, p.chunk_prefix, p.lo + p.n);
-            if (threadIdx.x == 0 && (p_hi - p_lo != p.n_next || 1ull + p_lo != p.next_lo))
-                set_status(p.status, SGS_E_CORRUPT);
-        }
-    }
-    __syncthreads();
-    expand_chunk(p.B, x0, x1, s_p, p.codes_in, p.in_base, p.codes_out, p.out_base,
-                 p.next_lo + p.n_next, p.codes_out ? nullptr : &p.leaf, p.next_lo, sm, p.status);
-}
-
-// Subtree walk: CTA t owns nodes [lo + t*kLvlTile, ...) of level lc and expands all their
-// descendants down to the leaves.  Below lc the tree is nearly a set of chains, so the
-// descendants of a tile stay about one tile wide per level; ranges are contiguous in
-// breadth-first order, the child range of [a, b) being [1 + P(a), 1 + P(b)).
-struct SubtreeParams {
-    const uint8_t *B;
-    const uint32_t *chunk_prefix;
-    int lc, depth;
-    uint64_t level_off[SGS_MAX_DEPTH + 2];
-    uint64_t *codes_all;  // levels lc..D-1, indexed by BFS index - level_off[lc]
-    LeafOut leaf;
-    int *status;
-};
-
-__global__ void __launch_bounds__(kLvlThreads) k_octree_subtree(SubtreeParams p) {
-    __shared__ uint32_t sm[64];
-    __shared__ uint32_t s_p;
-    const uint64_t base = p.level_off[p.lc];
-    uint64_t a = base + (uint64_t)blockIdx.x * kLvlTile;
-    uint64_t b = a + kLvlTile < p.level_off[p.lc + 1] ? a + kLvlTile : p.level_off[p.lc + 1];
-    const bool last = (b == p.level_off[p.lc + 1]);
-    const uint64_t leaf_base = p.level_off[p.depth];
-    for (int l = p.lc; l < p.depth; ++l) {
-        if (threadIdx.x < 32) {
-            const uint32_t pa = prefix_at_warp(p.B, p.chunk_prefix, a);
-            if (threadIdx.x == 0) s_p = pa;
-        }
-        __syncthreads();
-        const uint32_t pa = s_p;
-        const bool to_leaves = (l + 1 == p.depth);
-        uint32_t total = 0;
-        for (uint64_t c0 = a; c0 < b; c0 += kLvlTile) {
-            const uint64_t c1 = c0 + kLvlTile < b ? c0 + kLvlTile : b;
-            total += expand_chunk(p.B, c0, c1, pa + total, p.codes_all, base, p.codes_all, base,
-                                  p.level_off[l + 2], to_leaves ? &p.leaf : nullptr, leaf_base, sm,
-                                  p.status);
-        }
-        const uint64_t na = 1ull + pa, nb = na + total;
-        if (threadIdx.x == 0 && (na < p.level_off[l + 1] || nb > p.level_off[l + 2] ||
-                                 (last && nb != p.level_off[l + 2]) ||
-                                 (blockIdx.x == 0 && na != p.level_off[l + 1])))
+__global__ void __launch_bounds__(kExpThreads) k_octree_expand(ExpandParams p) {
+    __shared__ uint32_t s_p[kMaxFuse][kExpThreads];
+    __shared__ uint32_t s_it[kMaxFuse][kExpThreads];  // remaining mask | taken << 8
+    __shared__ uint64_t s_code[kMaxFuse][kExpThreads];
+    const int tid = threadIdx.x;
+    if (p.check && blockIdx.x == 0 && tid < p.depth) {
+        // sum of the popcounts of level l = nodes of level l+1, and the first child of the
+        // level's first node is the next level's first node
+        const int l = tid;
+        uint32_t b0, p0, b1, p1;
+        node_at(p.B, p.n_geo, p.P4, p.level_off[l], b0, p0);
+        node_at(p.B, p.n_geo, p.P4, p.level_off[l + 1], b1, p1);
+        if (1ull + p0 != p.level_off[l + 1] || (uint64_t)(p1 - p0) != p.level_off[l + 2] - p.level_off[l + 1])
             set_status(p.status, SGS_E_CORRUPT);
-        a = na < p.level_off[l + 1] ? p.level_off[l + 1] : na;
-        b = nb > p.level_off[l + 2] ? p.level_off[l + 2] : nb;
-        if (a > b) a = b;
-        __syncthreads();
     }
-}
-
-// First level of the subtree walk: the shallowest level >= l1 below which every level grows
-// by at most 5/4 (chain-like); D if there is none.
-int octree_subtree_level(const GeoPlan &plan, int l1) {
-    const int D = plan.depth;
-    int lc = D;
-    for (int l = D - 1; l >= l1; --l) {
-        if ((uint64_t)plan.n_level[l + 1] * 4 > (uint64_t)plan.n_level[l] * 5) break;
-        lc = l;
+    const uint64_t lo = p.level_off[p.ls];
+    const uint64_t x = lo + (uint64_t)blockIdx.x * kExpThreads + tid;
+    if (x >= p.level_off[p.ls + 1]) return;
+    uint32_t byte, px;
+    node_at(p.B, p.n_geo, p.P4, x, byte, px);
+    s_p[0][tid] = px;
+    s_it[0][tid] = byte;
+    s_code[0][tid] = p.codes_in[x - lo];
+    const int K = p.le - p.ls;
+    const uint64_t leaf_base = p.level_off[p.depth];
+    int d = 0;
+    while (d >= 0) {
+        const uint32_t it = s_it[d][tid];
+        const uint32_t mask = it & 0xFFu;
+        if (!mask) { --d; continue; }
+        const uint32_t k = __ffs(mask) - 1;
+        const uint32_t taken = it >> 8;
+        s_it[d][tid] = (mask & (mask - 1)) | ((taken + 1) << 8);
+        const uint64_t child = 1ull + s_p[d][tid] + taken;
+        const int lc = p.ls + d + 1;  // level of the child
+        if (child < p.level_off[lc] || child >= p.level_off[lc + 1]) {
+            set_status(p.status, SGS_E_CORRUPT);
+            return;
+        }
+        const uint64_t cc = child_code(s_code[d][tid], k);
+        if (d + 1 == K) {
+            if (lc == p.depth) write_leaf(p.leaf, (uint32_t)(child - leaf_base), cc, p.status);
+            else p.codes_out[child - p.level_off[lc]] = cc;
+        } else {
+            uint32_t cb, cp;
+            node_at(p.B, p.n_geo, p.P4, child, cb, cp);
+            ++d;
+            s_p[d][tid] = cp;
+            s_it[d][tid] = cb;
+            s_code[d][tid] = cc;
+        }
     }
-    return lc;
 }
 
 int octree_top_level(const GeoPlan &plan) {
@@ -451,6 +364,24 @@ int octree_top_level(const GeoPlan &plan) {
     while (l1 < plan.depth && plan.n_level[l1] <= kTopCap) ++l1;
     return l1;
 }
+
+// Level groups [ls, le) of the fused expansion: extend while the frontier stays within 4x of
+// the group's start and the group holds at most kMaxFuse levels.
+int octree_groups(const GeoPlan &plan, int *starts) {
+    const int D = plan.depth;
+    int n = 0;
+    int ls = octree_top_level(plan);
+    while (ls < D) {
+        int le = ls + 1;
+        while (le < D && le - ls < kMaxFuse && (uint64_t)plan.n_level[le] <= 4ull * plan.n_level[ls]) ++le;
+        starts[n++] = ls;
+        ls = le;
+    }
+    starts[n] = D;
+    return n;
+}
+
+size_t octree_scan_tiles(uint64_t n_geo);
 
 // ------------------------------------------------------------------ launcher
 
@@ -478,13 +409,11 @@ cudaError_t launch_octree(const uint8_t *B, const sgs_scene_info &info, const Ge
                                         s.dup_prefix, status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const uint64_t n_chunks = (info.n_geo + kChunk - 1) / kChunk;
-    const uint64_t n_tiles = (info.n_geo + kScanTile - 1) / kScanTile;
+    const uint64_t n_words = (info.n_geo + 3) / 4;
+    const uint64_t n_tiles = octree_scan_tiles(info.n_geo);
+    int starts[SGS_MAX_DEPTH + 2];
+    const int n_groups = octree_groups(plan, starts);
     const int l1 = octree_top_level(plan);
-    const int lc = octree_subtree_level(plan, l1);
-    uint64_t *codes_all = s.codes[2];
-    auto dst = [&](int l) -> uint64_t * { return l >= lc ? codes_all : s.codes[l & 1]; };
-    auto dst_base = [&](int l) -> uint64_t { return l >= lc ? plan.level_off[lc] : plan.level_off[l]; };
     // the top levels need no prefix: they run on st2 while the scan runs on st
     if (st2 != st) {
         if (cudaEventRecord(ev_a, st) != cudaSuccess || cudaStreamWaitEvent(st2, ev_a, 0) != cudaSuccess)
@@ -494,74 +423,58 @@ cudaError_t launch_octree(const uint8_t *B, const sgs_scene_info &info, const Ge
     tp.B = B;
     tp.plan = plan;
     tp.l1 = l1;
-    tp.codes_out = (l1 < D) ? dst(l1) + (plan.level_off[l1] - dst_base(l1)) : nullptr;
+    tp.codes_out = (l1 < D) ? s.codes[0] : nullptr;
     tp.leaf = lo;
     tp.status = status;
     k_octree_top<<<1, kTopThreads, 0, st2>>>(tp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (st2 != st && cudaEventRecord(ev_b, st2) != cudaSuccess) return cudaErrorUnknown;
-    k_octree_scan<<<(unsigned)n_tiles, kScanThreads, 0, st>>>(B, info.n_geo, s.chunk_prefix,
-                                                              n_chunks, s.scan_flags, s.ticket,
-                                                              status);
+    k_octree_scan<<<(unsigned)n_tiles, kScanThreads, 0, st>>>(B, info.n_geo, s.p4, n_words,
+                                                              s.scan_flags, s.ticket, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (st2 != st && cudaStreamWaitEvent(st, ev_b, 0) != cudaSuccess) return cudaErrorUnknown;
-    for (int l = l1; l < lc; ++l) {
-        LevelParams lp;
-        lp.B = B;
-        lp.chunk_prefix = s.chunk_prefix;
-        lp.lo = plan.level_off[l];
-        lp.n = plan.n_level[l];
-        lp.next_lo = plan.level_off[l + 1];
-        lp.n_next = plan.n_level[l + 1];
-        lp.codes_in = dst(l);
-        lp.in_base = dst_base(l);
-        lp.codes_out = (l + 1 < D) ? dst(l + 1) : nullptr;
-        lp.out_base = (l + 1 < D) ? dst_base(l + 1) : 0;
-        lp.leaf = lo;
-        lp.status = status;
-        const unsigned grid = (unsigned)((lp.n + kLvlTile - 1) / kLvlTile);
-        if (grid) k_octree_level<<<grid, kLvlThreads, 0, st>>>(lp);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    if (lc < D) {
-        SubtreeParams sp;
-        sp.B = B;
-        sp.chunk_prefix = s.chunk_prefix;
-        sp.lc = lc;
-        sp.depth = D;
-        for (int l = 0; l <= D; ++l) sp.level_off[l] = plan.level_off[l];
-        sp.level_off[D + 1] = plan.level_off[D] + plan.n_level[D];
-        sp.codes_all = codes_all;
-        sp.leaf = lo;
-        sp.status = status;
-        const unsigned grid = (unsigned)((plan.n_level[lc] + kLvlTile - 1) / kLvlTile);
-        k_octree_subtree<<<grid, kLvlThreads, 0, st>>>(sp);
+    ExpandParams ep;
+    ep.B = B;
+    ep.n_geo = info.n_geo;
+    ep.P4 = s.p4;
+    ep.depth = D;
+    for (int l = 0; l <= D; ++l) ep.level_off[l] = plan.level_off[l];
+    ep.level_off[D + 1] = plan.level_off[D] + plan.n_level[D];
+    ep.leaf = lo;
+    ep.status = status;
+    for (int gi = 0; gi < n_groups; ++gi) {
+        ep.ls = starts[gi];
+        ep.le = starts[gi + 1];
+        ep.codes_in = s.codes[gi & 1];
+        ep.codes_out = ep.le < D ? s.codes[(gi + 1) & 1] : nullptr;
+        ep.check = gi == 0;
+        const unsigned grid = (unsigned)((plan.n_level[ep.ls] + kExpThreads - 1) / kExpThreads);
+        k_octree_expand<<<grid, kExpThreads, 0, st>>>(ep);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-// Scratch of the octree stage (bytes of the three code buffers).
-void octree_code_buffers(const sgs_scene_info &info, const GeoPlan &plan, uint64_t *pingpong,
-                         uint64_t *all) {
-    const int l1 = octree_top_level(plan);
-    const int lc = octree_subtree_level(plan, l1);
-    uint64_t m = 1, a = 1;
-    for (int l = l1; l < lc && l < plan.depth; ++l) m = m > plan.n_level[l] ? m : plan.n_level[l];
-    for (int l = lc; l < plan.depth; ++l) a += plan.n_level[l];
-    if (info.n_rows == 0) m = a = 1;
+// Scratch of the octree stage: bytes of each ping-pong code buffer (the widest level that
+// starts a fused group, or level l1 written by the top kernel).
+void octree_code_buffers(const sgs_scene_info &info, const GeoPlan &plan, uint64_t *pingpong) {
+    int starts[SGS_MAX_DEPTH + 2];
+    const int n = octree_groups(plan, starts);
+    uint64_t m = 1;
+    for (int i = 0; i < n; ++i) m = m > plan.n_level[starts[i]] ? m : plan.n_level[starts[i]];
+    if (info.n_rows == 0) m = 1;
     *pingpong = 8 * m;
-    *all = 8 * a;
 }
 
 // Kernels launch_octree enqueues for a non-empty scene.
 int octree_launches(const sgs_scene_info &info, const GeoPlan &plan) {
-    const int l1 = octree_top_level(plan);
-    const int lc = octree_subtree_level(plan, l1);
-    return (info.n_dup ? 1 : 0) + 2 + (lc - l1) + (lc < plan.depth ? 1 : 0);
+    int starts[SGS_MAX_DEPTH + 2];
+    return (info.n_dup ? 1 : 0) + 2 + octree_groups(plan, starts);
 }
 
-size_t octree_scan_tiles(uint64_t n_geo) { return (n_geo + kScanTile - 1) / kScanTile; }
-size_t octree_chunks(uint64_t n_geo) { return (n_geo + kChunk - 1) / kChunk; }
+// Scan tiles: every 64-byte chunk up to the one holding word n_words (whose P4 entry is the
+// total), 256 chunks per tile.
+size_t octree_scan_tiles(uint64_t n_geo) { return (((n_geo + 3) / 4) / 16 + 1 + 255) / 256; }
+size_t octree_words(uint64_t n_geo) { return (n_geo + 3) / 4; }
 
 }  // namespace sgs

@@ -50,11 +50,11 @@ struct GeoPlan {
 // Scratch carve-out of one scene decode (device pointers).
 struct Scratch {
     uint8_t *geo_bytes;     // n_geo (rANS geometry only)
-    uint32_t *chunk_prefix; // n_chunks + 1 popcount prefix per 64-byte chunk
+    uint32_t *p4;           // popcount prefix at every 4-byte word of the tokens (+ total)
     uint64_t *scan_flags;   // look-back tile status
     uint32_t *ticket;       // tile ticket counter (zeroed)
-    uint64_t *codes[3];     // packed (x:21 | y:21 | z:21) coordinates: ping-pong for the
-                            // per-level kernels, then every level of the subtree walk
+    uint64_t *codes[2];     // packed (x:21 | y:21 | z:21) coordinates of the levels that
+                            // start a fused expansion group (ping-pong)
     uint8_t *tables;        // expanded static tables
     uint32_t *dup_prefix;   // n_dup + 1
     uint8_t *learned;       // learned-mode per-scene work area
