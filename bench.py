@@ -4,7 +4,7 @@ A step is one whole scene decode (octree geometry -> positions, attribute tokens
 structure of arrays) of a synthetic paper-shaped scene already resident in HBM.  Default
 workload: 1,000,000 Gaussians (900,000 after pruning), depth-16 octree, channel-wise
 fixed-length attributes with per-channel widths drawn from 4..10 bits.  Other workloads:
---workload static (same scene, channel-wise static rANS, 65,536 lanes), learned (same scene,
+--workload static (same scene, channel-wise static rANS, 151,552 lanes), learned (same scene,
 learned context model, 4,096 lanes), small (20,000 Gaussians, depth 12, static rANS, 32 lanes).
 
 Prints one JSON line.  --impl reference times the CPU oracle on the same workload instead.
@@ -31,9 +31,9 @@ WORKLOADS = {
     "fixed": dict(n=1_000_000, seed=1000, depth=16, mode=0, geo_mode=0, lanes=0,
                   desc="fixed-length scene decode: N=1,000,000 Gaussians (900,000 after pruning), "
                        "depth-16 octree (raw tokens), 56 channels at 4..10 bits"),
-    "static": dict(n=1_000_000, seed=1000, depth=16, mode=1, geo_mode=1, lanes=65536,
+    "static": dict(n=1_000_000, seed=1000, depth=16, mode=1, geo_mode=1, lanes=151552,
                    desc="channel-wise static rANS scene decode: N=1,000,000 (900,000 kept), depth 16, "
-                        "8-bit tokens, 65,536 lanes, rANS-coded octree levels"),
+                        "8-bit tokens, 151,552 lanes (one 32-warp CTA per SM), rANS-coded octree levels"),
     "learned": dict(n=1_000_000, seed=2000, depth=16, mode=2, geo_mode=1, lanes=4096,
                     desc="learned-model scene decode: N=1,000,000 (900,000 kept), depth 16, 8-bit "
                          "tokens, 4,096 lanes, context MLP 4->64->64->256"),

@@ -8,7 +8,8 @@
 // every 4-byte word of B, so any node's children follow from two loads: P4[x / 4] plus the
 // popcount of the bytes of its word below x.  Expansion is then a map with no block-wide
 // synchronisation: a thread takes one node and walks its subtree depth first through up to
-// kMaxFuse levels (a small stack of child iterators in shared memory), writing the packed
+// kMaxFuse levels (a small stack of child iterators in shared memory; more levels per thread
+// would chain too many dependent loads, so each launch covers a few levels), writing the packed
 // coordinates (x:21 | y:21 | z:21) of the nodes at the end of its levels or, at the last
 // level, the voxel-centre positions of the leaf rows.  The few small top levels are
 // expanded by one CTA, concurrently with the scan.
@@ -25,7 +26,7 @@ constexpr uint32_t kSpinLimit = 1u << 22;          // bounded look-back wait
 constexpr int kTopThreads = 1024;
 constexpr uint32_t kTopCap = 2048;                 // levels the top kernel keeps in smem
 constexpr int kExpThreads = 128;
-constexpr int kMaxFuse = 12;                       // levels one expansion thread walks
+constexpr int kMaxFuse = 3;                        // levels one expansion thread walks
 constexpr uint64_t kM21 = (1ull << 21) - 1;
 
 struct LeafOut {

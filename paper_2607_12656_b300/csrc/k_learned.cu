@@ -117,6 +117,7 @@ struct LSmem2 {
     int32_t red_idx[8][32];
     uint32_t red_sum[8][32];
     uint32_t red_T[8][32];
+    uint32_t R[32];
     uint32_t nrows[32];
     uint64_t row0[32];
     float step[kNChan], offset[kNChan];
@@ -301,14 +302,15 @@ __device__ __forceinline__ void produce_step(LSmem2 &S, uint32_t i, int c, int b
         if (t == 0) { S.red_sum[cs][rA] = sA; S.red_sum[cs][rB] = sB; }
     }
     producer_sync();
-    uint32_t RA, RB;
-    {
-        uint64_t EA = 0, EB = 0;
+    // R = floor(65280 * 2^32 / E) once per row (32 threads), then shared
+    if (tid < 32) {
+        uint64_t E = 0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) { EA += S.red_sum[q][rA]; EB += S.red_sum[q][rB]; }
-        RA = (uint32_t)((65280ull << 32) / EA);
-        RB = (uint32_t)((65280ull << 32) / EB);
+        for (int q = 0; q < 8; ++q) E += S.red_sum[q][tid];
+        S.R[tid] = (uint32_t)((65280ull << 32) / E);
     }
+    producer_sync();
+    const uint32_t RA = S.R[rA], RB = S.R[rB];
     // (c) floor terms and per-slice sums
     {
         uint32_t TA = 0, TB = 0;

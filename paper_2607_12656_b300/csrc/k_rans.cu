@@ -80,7 +80,7 @@ struct AttrParams {
     int *status;
 };
 
-constexpr int kAttrWarps = 8;
+constexpr int kAttrWarps = 32;  // one CTA per SM shares one copy of the 56 tables
 constexpr size_t kAttrTabSmem = kNChan * kTabCdfWords * 4 + kNChan * 256 + 2 * kNChan * 4;
 constexpr size_t kAttrSmem = kAttrTabSmem + kAttrWarps * kWinWords * 2;
 static_assert(kAttrTabSmem % 16 == 0, "window must be 16-byte aligned");

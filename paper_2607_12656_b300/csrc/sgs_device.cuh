@@ -80,7 +80,7 @@ __device__ __forceinline__ uint32_t rans_sym(uint32_t &x, const uint32_t *cdf,
 
 // Word stream of one group of up to 32 lanes, read through a shared-memory window of
 // kWinWords words that the warp refills with coalesced 16-byte loads.
-constexpr uint32_t kWinWords = 2048;
+constexpr uint32_t kWinWords = 1024;
 
 struct GroupStream {
     const uint8_t *w;   // group stream (16-byte aligned)
