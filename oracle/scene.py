@@ -197,14 +197,15 @@ def lane_bounds(n: int, lanes: int) -> np.ndarray:
 
 
 def static_row_order(n: int, lanes: int) -> tuple[np.ndarray, np.ndarray]:
-    """Row order of channel-wise static coding and its lane boundaries.
+    """Item order of static-table coding (attribute rows, or octree tokens) and its lane
+    boundaries.
 
-    Group g of 32 lanes owns the rows that its lanes would own as contiguous chunks
-    (rows [floor(32 g n / L), floor(min(32 g + 32, L) n / L))), and deals them round robin to
-    its n_g lanes: lane j of the group codes rows R_g + j, R_g + j + n_g, ...  Static coding
-    has no context between rows, so this changes no code length; it only makes the 32 lanes
-    of a group hold 32 consecutive rows at every step.  Returns (perm, lane_start): the rows in
-    lane-major coding order and the offsets of each lane's rows in perm."""
+    Group g of 32 lanes owns the items that its lanes would own as contiguous chunks
+    (items [floor(32 g n / L), floor(min(32 g + 32, L) n / L))), and deals them round robin to
+    its n_g lanes: lane j of the group codes items R_g + j, R_g + j + n_g, ...  Static coding
+    has no context between items, so this changes no code length; it only makes the 32 lanes
+    of a group hold 32 consecutive items at every step.  Returns (perm, lane_start): the items
+    in lane-major coding order and the offsets of each lane's items in perm."""
     perm = np.empty(n, np.int64)
     lane_start = np.zeros(lanes + 1, np.int64)
     lb = lane_bounds(n, lanes)
@@ -470,8 +471,9 @@ def encode(pos: np.ndarray, attr: np.ndarray, *, mode: int, depth: int, bits=8, 
         geo_tab = b"".join(table_bytes(t) for t in tabs)
         syms = np.concatenate(coded_syms)
         tab_id = np.concatenate([np.full(len(b), i, np.uint8) for i, b in enumerate(coded_syms)])
-        f, c = static_fc(syms, tab_id, tabs)
-        geo_pay, goff, gw = rans_encode(lane_bounds(n_coded, Lg), f, c)
+        gperm, gstart = static_row_order(n_coded, Lg)
+        f, c = static_fc(syms[gperm], tab_id[gperm], tabs)
+        geo_pay, goff, gw = rans_encode(gstart, f, c)
         geo_grp = group_table_bytes(goff, gw)
     # attributes
     L = 0
@@ -602,7 +604,10 @@ def decode(buf: bytes) -> dict:
         gw = np.frombuffer(buf, "<u4", G, h["off_geo_grp"] + 8 * (G + 1))
         tab_id = np.concatenate([np.full(int(n_level[l]), i, np.uint8) for i, l in enumerate(cl)])
         pay = buf[h["off_geo_pay"]:h["off_attr_tab"]]
-        syms = rans_decode_static(lane_bounds(n_coded, Lg), tab_id, tabs, pay, goff, gw)
+        gperm, gstart = static_row_order(n_coded, Lg)
+        dec = rans_decode_static(gstart, tab_id[gperm], tabs, pay, goff, gw)
+        syms = np.zeros(n_coded, np.uint8)
+        syms[gperm] = dec
         q0 = 0
         for l in cl:
             levels[l] = syms[q0:q0 + int(n_level[l])]

@@ -23,9 +23,10 @@ struct sgs_ctx {
     int n_marks;
     cudaEvent_t marks[kMaxStages + 1];  // caller's stream: start, tokens, octree, end
     cudaEvent_t amarks[2];              // attribute stream: start, end
-    cudaStream_t aux;                   // attribute decode runs here, forked from the caller
-    cudaStream_t aux2;                  // octree top levels, concurrent with the scan
-    cudaEvent_t fork, join, top_fork, top_join;
+    cudaStream_t aux;                   // attribute decode (lowest priority), forked from the caller
+    cudaStream_t geo;                   // geometry chain (highest priority)
+    cudaStream_t aux2;                  // octree top levels (highest priority), beside the scan
+    cudaEvent_t fork, join, gjoin, top_fork, top_join;
 };
 
 namespace sgs {
@@ -135,10 +136,16 @@ extern "C" int sgs_create(sgs_ctx **out, int device, size_t scratch_bytes) {
     c->n_marks = 0;
     for (int i = 0; i <= kMaxStages; ++i) cudaEventCreate(&c->marks[i]);
     for (int i = 0; i < 2; ++i) cudaEventCreate(&c->amarks[i]);
-    if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->aux2, cudaStreamNonBlocking) != cudaSuccess ||
+    // the latency-bound geometry chain outranks the bandwidth-bound attribute kernels, so its
+    // small launches get SMs as soon as attribute CTAs retire
+    int prio_low = 0, prio_high = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    if (cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_low) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->geo, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->aux2, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->gjoin, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->top_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->top_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaFree(c->status_dev);
@@ -183,6 +190,8 @@ extern "C" void sgs_destroy(sgs_ctx *c) {
     for (int i = 0; i < 2; ++i) cudaEventDestroy(c->amarks[i]);
     cudaEventDestroy(c->fork);
     cudaEventDestroy(c->join);
+    cudaEventDestroy(c->gjoin);
+    cudaStreamDestroy(c->geo);
     cudaEventDestroy(c->top_fork);
     cudaEventDestroy(c->top_join);
     cudaStreamDestroy(c->aux);
@@ -345,8 +354,9 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
         if (e != cudaSuccess) return SGS_E_CUDA;
     }
     uint8_t *attr_tables = s.tables + (size_t)plan.n_coded_levels * kTabBytes;
-    // fork: attributes on the attribute stream
-    if (cudaEventRecord(c->fork, st) != cudaSuccess || cudaStreamWaitEvent(c->aux, c->fork, 0) != cudaSuccess)
+    // fork: attributes on the attribute stream, geometry on the geometry stream
+    if (cudaEventRecord(c->fork, st) != cudaSuccess || cudaStreamWaitEvent(c->aux, c->fork, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(c->geo, c->fork, 0) != cudaSuccess)
         return SGS_E_CUDA;
     if (c->profile) cudaEventRecord(c->amarks[0], c->aux);
     if (info.n_rows) c->launches += 1;
@@ -358,23 +368,25 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
     if (e != cudaSuccess) return SGS_E_CUDA;
     if (c->profile) cudaEventRecord(c->amarks[1], c->aux);
     if (cudaEventRecord(c->join, c->aux) != cudaSuccess) return SGS_E_CUDA;
-    // geometry on the caller's stream
+    cudaStream_t gs = c->geo;
     const uint8_t *B = bits + info.off[S_GEO_RAW];
     if (info.geo_mode == SGS_GEO_RANS && info.n_geo) {
-        if ((e = launch_geo_copy_raw(bits, info, plan, s.geo_bytes, st)) != cudaSuccess) return SGS_E_CUDA;
-        if ((e = launch_rans_static_geo(bits, info, plan, s.tables, s.geo_bytes, status, st)) != cudaSuccess)
+        if ((e = launch_geo_copy_raw(bits, info, plan, s.geo_bytes, gs)) != cudaSuccess) return SGS_E_CUDA;
+        if ((e = launch_rans_static_geo(bits, info, plan, s.tables, s.geo_bytes, status, gs)) != cudaSuccess)
             return SGS_E_CUDA;
         B = s.geo_bytes;
         c->launches += 2;
     }
-    mark();
-    if ((e = launch_octree(B, info, plan, bits, s, out, status, st, c->aux2, c->top_fork, c->top_join)) !=
+    if (c->profile && c->n_marks <= kMaxStages) cudaEventRecord(c->marks[c->n_marks++], gs);
+    if ((e = launch_octree(B, info, plan, bits, s, out, status, gs, c->aux2, c->top_fork, c->top_join)) !=
         cudaSuccess)
         return SGS_E_CUDA;
     if (info.n_rows) c->launches += octree_launches(info, plan);
-    mark();
+    if (c->profile && c->n_marks <= kMaxStages) cudaEventRecord(c->marks[c->n_marks++], gs);
     // join
-    if (cudaStreamWaitEvent(st, c->join, 0) != cudaSuccess) return SGS_E_CUDA;
+    if (cudaEventRecord(c->gjoin, gs) != cudaSuccess || cudaStreamWaitEvent(st, c->join, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(st, c->gjoin, 0) != cudaSuccess)
+        return SGS_E_CUDA;
     mark();
     return SGS_OK;
 }

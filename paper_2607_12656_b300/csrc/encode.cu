@@ -230,10 +230,10 @@ void rans_encode(const std::vector<uint64_t> &lane_start, const uint32_t *sym_f,
     while (grp.size() % 16) grp.push_back(0);
 }
 
-// Channel-wise static coding: group g of 32 lanes owns the rows its lanes would own as
-// contiguous chunks and deals them round robin to its lanes (lane j: rows R_g + j + k n_g),
-// so the 32 lanes of a group always hold 32 consecutive rows.  Returns the rows in
-// lane-major coding order and each lane's start offset (in rows).
+// Static-table coding (attribute rows, octree tokens): group g of 32 lanes owns the items
+// its lanes would own as contiguous chunks and deals them round robin to its lanes (lane j:
+// items R_g + j + k n_g), so the 32 lanes of a group always hold 32 consecutive items.
+// Returns the items in lane-major coding order and each lane's start offset.
 void static_row_order(uint64_t n, uint64_t L, std::vector<uint32_t> &perm, std::vector<uint64_t> &start) {
     perm.resize(n);
     start.assign(L + 1, 0);
@@ -343,7 +343,7 @@ extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, u
     uint32_t Lg = 0;
     if (n_coded) {
         Lg = prm->geo_lanes ? prm->geo_lanes : default_geo_lanes(n_coded);
-        std::vector<uint32_t> sf(n_coded), scu(n_coded);
+        std::vector<uint32_t> tf(n_coded), tcu(n_coded);  // in token order
         uint64_t p = 0;
         for (int l : coded_levels) {
             uint64_t h[kNSym] = {0};
@@ -353,9 +353,14 @@ extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, u
             put_table(s_gtab, f);
             uint32_t acc = 0;
             for (int s = 0; s < kNSym; ++s) { cu[s] = acc; acc += f[s]; }
-            for (uint8_t b : P.levels[l]) { sf[p] = f[b]; scu[p] = cu[b]; ++p; }
+            for (uint8_t b : P.levels[l]) { tf[p] = f[b]; tcu[p] = cu[b]; ++p; }
         }
-        rans_encode(lane_bounds(n_coded, Lg, 1), sf.data(), scu.data(), s_ggrp, s_gpay);
+        // tokens dealt round robin to the lanes of each group, as for static attributes
+        std::vector<uint32_t> perm, sf(n_coded), scu(n_coded);
+        std::vector<uint64_t> gstart;
+        static_row_order(n_coded, Lg, perm, gstart);
+        for (uint64_t i = 0; i < n_coded; ++i) { sf[i] = tf[perm[i]]; scu[i] = tcu[perm[i]]; }
+        rans_encode(gstart, sf.data(), scu.data(), s_ggrp, s_gpay);
     }
     for (size_t i = 0; i < P.dups.size(); ++i) put<uint32_t>(s_dup, P.dups[i]);
     for (int c = 0; c < kNChan; ++c) put<float>(s_chan, P.step[c]);

@@ -8,10 +8,9 @@
 // every 4-byte word of B, so any node's children follow from two loads: P4[x / 4] plus the
 // popcount of the bytes of its word below x.  Expansion is then a map with no block-wide
 // synchronisation: a thread takes one node and walks its subtree depth first through up to
-// kMaxFuse levels (a small stack of child iterators in shared memory; more levels per thread
-// would chain too many dependent loads, so each launch covers a few levels), writing the packed
-// coordinates (x:21 | y:21 | z:21) of the nodes at the end of its levels or, at the last
-// level, the voxel-centre positions of the leaf rows.  The few small top levels are
+// kMaxFuse chain-like levels (a small stack of child iterators in shared memory), writing the
+// packed coordinates (x:21 | y:21 | z:21) of the nodes at the end of its levels or, at the
+// last level, the voxel-centre positions of the leaf rows.  The few small top levels are
 // expanded by one CTA, concurrently with the scan.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -26,7 +25,7 @@ constexpr uint32_t kSpinLimit = 1u << 22;          // bounded look-back wait
 constexpr int kTopThreads = 1024;
 constexpr uint32_t kTopCap = 2048;                 // levels the top kernel keeps in smem
 constexpr int kExpThreads = 128;
-constexpr int kMaxFuse = 3;                        // levels one expansion thread walks
+constexpr int kMaxFuse = 8;                        // levels one expansion thread walks
 constexpr uint64_t kM21 = (1ull << 21) - 1;
 
 struct LeafOut {
@@ -366,15 +365,17 @@ int octree_top_level(const GeoPlan &plan) {
     return l1;
 }
 
-// Level groups [ls, le) of the fused expansion: extend while the frontier stays within 4x of
-// the group's start and the group holds at most kMaxFuse levels.
+// Level groups [ls, le) of the fused expansion.  A thread's levels run one after another, so
+// only chain-like levels are fused: extend while the frontier grows by at most 1/10 over the
+// group (branching subtrees would leave a warp waiting for its widest lane), and the group
+// holds at most kMaxFuse levels.
 int octree_groups(const GeoPlan &plan, int *starts) {
     const int D = plan.depth;
     int n = 0;
     int ls = octree_top_level(plan);
     while (ls < D) {
         int le = ls + 1;
-        while (le < D && le - ls < kMaxFuse && (uint64_t)plan.n_level[le] <= 4ull * plan.n_level[ls]) ++le;
+        while (le < D && le - ls < kMaxFuse && (uint64_t)plan.n_level[le] * 10 <= 11ull * plan.n_level[ls]) ++le;
         starts[n++] = ls;
         ls = le;
     }

@@ -184,21 +184,18 @@ __global__ void __launch_bounds__(32 * kGeoWarps) k_rans_geo(GeoParams p) {
     const int lane = threadIdx.x & 31;
     const uint32_t g = blockIdx.x * kGeoWarps + (threadIdx.x >> 5);
     if (g >= p.G) return;
-    const uint32_t j = g * 32 + lane;
+    // the group's tokens, dealt round robin to its lanes: lane j holds tokens I0 + j + k nl
     const int nl = (int)min(32u, p.L - g * 32);
-    uint64_t i0 = 0, i1 = 0;
-    if (lane < nl) {
-        i0 = (uint64_t)j * p.n_coded / p.L;
-        i1 = (uint64_t)(j + 1) * p.n_coded / p.L;
-    }
-    const uint64_t n = i1 - i0;
+    const uint64_t I0 = (uint64_t)g * 32 * p.n_coded / p.L;
+    const uint64_t I1 = (uint64_t)(g * 32 + nl) * p.n_coded / p.L;
+    const uint64_t n = (lane < nl && I0 + lane < I1) ? (I1 - I0 - lane + nl - 1) / nl : 0;
     GroupStream gs;
     uint32_t x;
     group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, g, nl, lane, gs, x, s_win);
     const uint64_t maxn = warp_max_u64(n);
-    int k = 0;  // coded level of symbol i0
-    while (k + 1 < nt && p.plan.coded_start[k + 1] <= i0) ++k;
-    uint64_t i = i0;
+    uint64_t i = I0 + lane;
+    int k = 0;  // coded level of token i
+    while (k + 1 < nt && p.plan.coded_start[k + 1] <= i) ++k;
     for (uint64_t t = 0; t < maxn; ++t) {
         const bool active = t < n;
         if (active) {
@@ -206,7 +203,7 @@ __global__ void __launch_bounds__(32 * kGeoWarps) k_rans_geo(GeoParams p) {
             const uint32_t s = rans_sym(x, s_cdf + k * kTabCdfWords, s_bucket + k * 256);
             const uint64_t dst = p.plan.level_off[p.plan.coded_level[k]] + (i - p.plan.coded_start[k]);
             p.geo_bytes[dst] = (uint8_t)s;
-            ++i;
+            i += nl;
         }
         group_refill(gs, x, active);
     }
