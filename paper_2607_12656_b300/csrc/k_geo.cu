@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kScanThreads) k_octree_scan(const uint8_t *B, 
 
 // Node x of B: its token and P(x) from the word prefix.
 __device__ __forceinline__ void node_at(const uint8_t *B, uint64_t n, const uint32_t *P4,
-                                        uint64_t x, uint32_t &byte, uint32_t &p) {
+                                        uint32_t x, uint32_t &byte, uint32_t &p) {
     const uint32_t w = word_at(B, n, x >> 2);
     const uint32_t sh = 8u * (uint32_t)(x & 3);
     byte = (w >> sh) & 0xFFu;
@@ -309,27 +309,44 @@ __global__ void __launch_bounds__(kExpThreads) k_octree_expand(ExpandParams p) {
     __shared__ uint32_t s_p[kMaxFuse][kExpThreads];
     __shared__ uint32_t s_it[kMaxFuse][kExpThreads];  // remaining mask | taken << 8
     __shared__ uint64_t s_code[kMaxFuse][kExpThreads];
+    __shared__ uint32_t s_off[SGS_MAX_DEPTH + 2];      // level offsets (node indices < 2^32)
     const int tid = threadIdx.x;
+    if (tid <= p.depth + 1) s_off[tid] = (uint32_t)p.level_off[tid];
+    __syncthreads();
     if (p.check && blockIdx.x == 0 && tid < p.depth) {
         // sum of the popcounts of level l = nodes of level l+1, and the first child of the
         // level's first node is the next level's first node
         const int l = tid;
         uint32_t b0, p0, b1, p1;
-        node_at(p.B, p.n_geo, p.P4, p.level_off[l], b0, p0);
-        node_at(p.B, p.n_geo, p.P4, p.level_off[l + 1], b1, p1);
-        if (1ull + p0 != p.level_off[l + 1] || (uint64_t)(p1 - p0) != p.level_off[l + 2] - p.level_off[l + 1])
+        node_at(p.B, p.n_geo, p.P4, s_off[l], b0, p0);
+        node_at(p.B, p.n_geo, p.P4, s_off[l + 1], b1, p1);
+        if (1u + p0 != s_off[l + 1] || p1 - p0 != s_off[l + 2] - s_off[l + 1])
             set_status(p.status, SGS_E_CORRUPT);
     }
-    const uint64_t lo = p.level_off[p.ls];
-    const uint64_t x = lo + (uint64_t)blockIdx.x * kExpThreads + tid;
-    if (x >= p.level_off[p.ls + 1]) return;
+    const uint32_t lo = s_off[p.ls];
+    const uint32_t x = lo + blockIdx.x * kExpThreads + tid;
+    if (x >= s_off[p.ls + 1]) return;
     uint32_t byte, px;
     node_at(p.B, p.n_geo, p.P4, x, byte, px);
+    uint64_t code = p.codes_in[x - lo];
+    const uint32_t leaf_base = s_off[p.depth];
+    int lvl = p.ls;  // level of the current node
+    // chains: follow single children without the stack
+    while (lvl + 1 < p.le && __popc(byte) == 1) {
+        const uint32_t child = 1u + px;
+        ++lvl;
+        if (child < s_off[lvl] || child >= s_off[lvl + 1]) {
+            set_status(p.status, SGS_E_CORRUPT);
+            return;
+        }
+        code = child_code(code, __ffs(byte) - 1);
+        node_at(p.B, p.n_geo, p.P4, child, byte, px);
+    }
+    // depth first through the remaining levels lvl .. le-1
     s_p[0][tid] = px;
     s_it[0][tid] = byte;
-    s_code[0][tid] = p.codes_in[x - lo];
-    const int K = p.le - p.ls;
-    const uint64_t leaf_base = p.level_off[p.depth];
+    s_code[0][tid] = code;
+    const int K = p.le - lvl;
     int d = 0;
     while (d >= 0) {
         const uint32_t it = s_it[d][tid];
@@ -338,16 +355,16 @@ __global__ void __launch_bounds__(kExpThreads) k_octree_expand(ExpandParams p) {
         const uint32_t k = __ffs(mask) - 1;
         const uint32_t taken = it >> 8;
         s_it[d][tid] = (mask & (mask - 1)) | ((taken + 1) << 8);
-        const uint64_t child = 1ull + s_p[d][tid] + taken;
-        const int lc = p.ls + d + 1;  // level of the child
-        if (child < p.level_off[lc] || child >= p.level_off[lc + 1]) {
+        const uint32_t child = 1u + s_p[d][tid] + taken;
+        const int lc = lvl + d + 1;  // level of the child
+        if (child < s_off[lc] || child >= s_off[lc + 1]) {
             set_status(p.status, SGS_E_CORRUPT);
             return;
         }
         const uint64_t cc = child_code(s_code[d][tid], k);
         if (d + 1 == K) {
-            if (lc == p.depth) write_leaf(p.leaf, (uint32_t)(child - leaf_base), cc, p.status);
-            else p.codes_out[child - p.level_off[lc]] = cc;
+            if (lc == p.depth) write_leaf(p.leaf, child - leaf_base, cc, p.status);
+            else p.codes_out[child - s_off[lc]] = cc;
         } else {
             uint32_t cb, cp;
             node_at(p.B, p.n_geo, p.P4, child, cb, cp);

@@ -47,7 +47,9 @@ __global__ void __launch_bounds__(256) k_tables(const uint8_t *bits, TableOffset
     uint32_t *out_cdf = reinterpret_cast<uint32_t *>(tables + (size_t)t * kTabBytes);
     uint8_t *out_bucket = tables + (size_t)t * kTabBytes + kTabCdfWords * 4;
     out_cdf[s] = cdf[s];
-    if (s == 0) out_cdf[256] = cdf[256];
+    // cdf[256] = 2^16 always (a corrupt table was flagged above): every slot < 2^16 then
+    // finds its symbol at or below 255 without a bound check in the decoders
+    if (s == 0) out_cdf[256] = 65536u;
     // bucket[b]: largest symbol whose cdf <= b * 256 (a lower bound for any slot >= b*256)
     const uint32_t key = (uint32_t)s << 8;
     int lo = 0, hi = 255;
@@ -85,6 +87,7 @@ constexpr size_t kAttrTabSmem = kNChan * kTabCdfWords * 4 + kNChan * 256 + 2 * k
 constexpr size_t kAttrSmem = kAttrTabSmem + kAttrWarps * kWinWords * 2;
 static_assert(kAttrTabSmem % 16 == 0, "window must be 16-byte aligned");
 
+template <bool IDX>
 __global__ void __launch_bounds__(32 * kAttrWarps) k_rans_attr(AttrParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *s_cdf = (uint32_t *)smem;                          // [56][257]
@@ -102,28 +105,52 @@ __global__ void __launch_bounds__(32 * kAttrWarps) k_rans_attr(AttrParams p) {
     const uint32_t g = blockIdx.x * kAttrWarps + (threadIdx.x >> 5);
     if (g >= p.G) return;
     // the group's rows, dealt round robin to its lanes: lane j holds rows R0 + j + k nl
-    const int nl = (int)min(32u, p.L - g * 32);
-    const uint64_t R0 = (uint64_t)g * 32 * p.n_rows / p.L;
-    const uint64_t R1 = (uint64_t)(g * 32 + nl) * p.n_rows / p.L;
-    const uint64_t my_rows = (lane < nl && R0 + lane < R1) ? (R1 - R0 - lane + nl - 1) / nl : 0;
-    const uint64_t n = my_rows * kNChan;
+    const uint32_t nl = min(32u, p.L - g * 32);
+    const uint32_t R0 = (uint32_t)((uint64_t)g * 32 * p.n_rows / p.L);
+    const uint32_t R1 = (uint32_t)((uint64_t)(g * 32 + nl) * p.n_rows / p.L);
+    const uint32_t my_rows = ((uint32_t)lane < nl && R0 + lane < R1) ? (R1 - R0 - lane + nl - 1) / nl : 0;
+    const uint32_t n = my_rows * kNChan;
     GroupStream gs;
     uint32_t x;
-    group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, g, nl, lane, gs, x, s_win);
-    const uint64_t maxn = warp_max_u64(n);
-    uint64_t row = R0 + lane;
+    group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, g, (int)nl, lane, gs, x, s_win);
+    uint32_t maxn = n;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxn = max(maxn, __shfl_xor_sync(0xffffffffu, maxn, o));
+    // per-channel state advanced incrementally: tables, constants, output pointer
+    uint32_t row = R0 + lane;
+    const uint32_t *cdf = s_cdf;
+    const uint8_t *bkt = s_bucket;
     int c = 0;
-    for (uint64_t t = 0; t < maxn; ++t) {
+    float *orow = p.out + row;  // channel 0 of the current row (no out_index)
+    float *o = orow;
+    for (uint32_t t = 0; t < maxn; ++t) {
         const bool active = t < n;
         if (active) {
-            const uint32_t s = rans_sym(x, s_cdf + c * kTabCdfWords, s_bucket + c * 256);
-            const uint64_t col = p.out_index ? (uint64_t)p.out_index[row] : row;
-            p.out[(uint64_t)c * p.n_rows + col] = dequant(s, s_step[c], s_off[c]);
-            if (++c == kNChan) { c = 0; row += nl; }
+            const uint32_t slot = x & 0xFFFFu;
+            uint32_t sym = bkt[slot >> 8];
+            uint32_t hi = cdf[sym + 1];
+            while (hi <= slot) hi = cdf[++sym + 1];  // cdf[256] = 2^16 > slot ends the walk
+            const uint32_t lo = cdf[sym];
+            x = (hi - lo) * (x >> 16) + slot - lo;
+            const float v = dequant(sym, s_step[c], s_off[c]);
+            if (IDX) p.out[(size_t)c * p.n_rows + p.out_index[row]] = v;
+            else *o = v;
+            if (++c == kNChan) {
+                c = 0;
+                cdf = s_cdf;
+                bkt = s_bucket;
+                row += nl;
+                orow += nl;
+                o = orow;
+            } else {
+                cdf += kTabCdfWords;
+                bkt += 256;
+                o += p.n_rows;
+            }
         }
         group_refill(gs, x, active);
     }
-    const bool bad = gs.bad || (lane < nl && x != 0x10000u) || (gs.ptr != gs.n_words);
+    const bool bad = gs.bad || (lane < (int)nl && x != 0x10000u) || (gs.ptr != gs.n_words);
     if (bad) set_status(p.status, SGS_E_CORRUPT);
 }
 
@@ -146,13 +173,17 @@ cudaError_t launch_rans_static_attr(const uint8_t *bits, const sgs_scene_info &i
     p.status = status;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_rans_attr, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_rans_attr<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kAttrSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_rans_attr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kAttrSmem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const unsigned grid = (p.G + kAttrWarps - 1) / kAttrWarps;
-    k_rans_attr<<<grid, 32 * kAttrWarps, kAttrSmem, st>>>(p);
+    if (p.out_index) k_rans_attr<true><<<grid, 32 * kAttrWarps, kAttrSmem, st>>>(p);
+    else k_rans_attr<false><<<grid, 32 * kAttrWarps, kAttrSmem, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -179,30 +210,54 @@ __global__ void __launch_bounds__(32 * kGeoWarps) k_rans_geo(GeoParams p) {
     uint32_t *s_cdf = (uint32_t *)smem;
     uint8_t *s_bucket = smem + (size_t)nt * kTabCdfWords * 4;
     uint16_t *s_win = reinterpret_cast<uint16_t *>(smem + kGeoTabSmem) + (threadIdx.x >> 5) * kWinWords;
+    __shared__ uint32_t s_start[SGS_MAX_DEPTH + 1];  // first coded token of each coded level
+    __shared__ uint32_t s_dbase[SGS_MAX_DEPTH];      // BFS offset of its tokens minus that
     load_tables_smem(p.tables, nt, s_cdf, s_bucket);
+    if (threadIdx.x <= (unsigned)nt) s_start[threadIdx.x] = (uint32_t)p.plan.coded_start[threadIdx.x];
+    if (threadIdx.x < (unsigned)nt)
+        s_dbase[threadIdx.x] = (uint32_t)(p.plan.level_off[p.plan.coded_level[threadIdx.x]] -
+                                          p.plan.coded_start[threadIdx.x]);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const uint32_t g = blockIdx.x * kGeoWarps + (threadIdx.x >> 5);
     if (g >= p.G) return;
     // the group's tokens, dealt round robin to its lanes: lane j holds tokens I0 + j + k nl
     const int nl = (int)min(32u, p.L - g * 32);
-    const uint64_t I0 = (uint64_t)g * 32 * p.n_coded / p.L;
-    const uint64_t I1 = (uint64_t)(g * 32 + nl) * p.n_coded / p.L;
-    const uint64_t n = (lane < nl && I0 + lane < I1) ? (I1 - I0 - lane + nl - 1) / nl : 0;
+    const uint32_t I0 = (uint32_t)((uint64_t)g * 32 * p.n_coded / p.L);
+    const uint32_t I1 = (uint32_t)((uint64_t)(g * 32 + nl) * p.n_coded / p.L);
+    const uint32_t n = (lane < nl && I0 + lane < I1) ? (I1 - I0 - lane + nl - 1) / nl : 0;
     GroupStream gs;
     uint32_t x;
     group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, g, nl, lane, gs, x, s_win);
-    const uint64_t maxn = warp_max_u64(n);
-    uint64_t i = I0 + lane;
-    int k = 0;  // coded level of token i
-    while (k + 1 < nt && p.plan.coded_start[k + 1] <= i) ++k;
-    for (uint64_t t = 0; t < maxn; ++t) {
+    uint32_t maxn = n;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxn = max(maxn, __shfl_xor_sync(0xffffffffu, maxn, o));
+    uint32_t i = I0 + lane;
+    // coded level k of token i: its table, the token's offset into the level, and where the
+    // next coded level starts
+    int k = 0;
+    while (k + 1 < nt && s_start[k + 1] <= i) ++k;
+    const uint32_t *cdf = s_cdf + k * kTabCdfWords;
+    const uint8_t *bkt = s_bucket + k * 256;
+    uint32_t next = s_start[k + 1];
+    uint32_t dbase = s_dbase[k];
+    for (uint32_t t = 0; t < maxn; ++t) {
         const bool active = t < n;
         if (active) {
-            while (k + 1 < nt && p.plan.coded_start[k + 1] <= i) ++k;
-            const uint32_t s = rans_sym(x, s_cdf + k * kTabCdfWords, s_bucket + k * 256);
-            const uint64_t dst = p.plan.level_off[p.plan.coded_level[k]] + (i - p.plan.coded_start[k]);
-            p.geo_bytes[dst] = (uint8_t)s;
+            while (i >= next && k + 1 < nt) {
+                ++k;
+                cdf += kTabCdfWords;
+                bkt += 256;
+                next = s_start[k + 1];
+                dbase = s_dbase[k];
+            }
+            const uint32_t slot = x & 0xFFFFu;
+            uint32_t sym = bkt[slot >> 8];
+            uint32_t hi = cdf[sym + 1];
+            while (hi <= slot) hi = cdf[++sym + 1];
+            const uint32_t lo = cdf[sym];
+            x = (hi - lo) * (x >> 16) + slot - lo;
+            p.geo_bytes[dbase + i] = (uint8_t)sym;
             i += nl;
         }
         group_refill(gs, x, active);

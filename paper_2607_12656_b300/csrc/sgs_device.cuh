@@ -87,6 +87,7 @@ struct GroupStream {
     uint32_t n_words;
     uint32_t ptr;       // next word to read
     uint32_t wbase;     // first word held in the window
+    uint32_t wlimit;    // refill once ptr passes this (wbase + kWinWords - 32)
     uint16_t *win;      // this warp's window
     bool bad;
 };
@@ -95,6 +96,7 @@ struct GroupStream {
 __device__ __forceinline__ void window_fill(GroupStream &gs, uint32_t base) {
     const int lane = threadIdx.x & 31;
     gs.wbase = base;
+    gs.wlimit = base + kWinWords - 32;
     const uint4 *src = reinterpret_cast<const uint4 *>(gs.w) + (base >> 3);
     uint4 *dst = reinterpret_cast<uint4 *>(gs.win);
     const uint32_t n16 = (gs.n_words + 7) >> 3;  // 16-byte units holding stream words
@@ -140,7 +142,7 @@ __device__ __forceinline__ void group_refill(GroupStream &gs, uint32_t &x, bool 
     const bool need = active && x < 0x10000u;
     const uint32_t mask = __ballot_sync(0xffffffffu, need);
     if (mask == 0) return;
-    if (gs.ptr + 32 > gs.wbase + kWinWords) window_fill(gs, gs.ptr & ~7u);
+    if (gs.ptr > gs.wlimit) window_fill(gs, gs.ptr & ~7u);
     if (need) {
         const uint32_t idx = gs.ptr + __popc(mask & ((1u << (threadIdx.x & 31)) - 1u));
         uint32_t w = 0;
