@@ -376,6 +376,116 @@ __global__ void __launch_bounds__(kExpThreads) k_octree_expand(ExpandParams p) {
     }
 }
 
+// Chain-like level groups: each thread advances kIlp independent nodes (x, x + T, ...) one
+// level at a time, issuing all their loads before using any, so a resident grid keeps many
+// dependent load chains in flight.  A node with several children (rare below the cut) is
+// finished by the depth-first walk of expand_from.
+constexpr int kIlp = 4;
+
+// Depth-first expansion of one node (byte b, P value pp, code) at level lvl down to level le.
+__device__ __noinline__ void expand_from(const ExpandParams &p, const uint32_t *s_off, int lvl,
+                                         uint32_t b, uint32_t pp, uint64_t code) {
+    uint32_t st_p[kMaxFuse], st_it[kMaxFuse];
+    uint64_t st_code[kMaxFuse];
+    st_p[0] = pp;
+    st_it[0] = b;
+    st_code[0] = code;
+    const int K = p.le - lvl;
+    const uint32_t leaf_base = s_off[p.depth];
+    int d = 0;
+    while (d >= 0) {
+        const uint32_t it = st_it[d];
+        const uint32_t mask = it & 0xFFu;
+        if (!mask) { --d; continue; }
+        const uint32_t k = __ffs(mask) - 1;
+        const uint32_t taken = it >> 8;
+        st_it[d] = (mask & (mask - 1)) | ((taken + 1) << 8);
+        const uint32_t child = 1u + st_p[d] + taken;
+        const int lc = lvl + d + 1;
+        if (child < s_off[lc] || child >= s_off[lc + 1]) {
+            set_status(p.status, SGS_E_CORRUPT);
+            return;
+        }
+        const uint64_t cc = child_code(st_code[d], k);
+        if (d + 1 == K) {
+            if (lc == p.depth) write_leaf(p.leaf, child - leaf_base, cc, p.status);
+            else p.codes_out[child - s_off[lc]] = cc;
+        } else {
+            uint32_t cb, cp;
+            node_at(p.B, p.n_geo, p.P4, child, cb, cp);
+            ++d;
+            st_p[d] = cp;
+            st_it[d] = cb;
+            st_code[d] = cc;
+        }
+    }
+}
+
+// Level-count check (CTA 0 of the first expansion launch): the popcounts of level l sum to
+// the node count of level l+1, and level l's first node has level l+1's first node as child.
+__device__ __forceinline__ void check_levels(const ExpandParams &p, const uint32_t *s_off) {
+    const int l = threadIdx.x;
+    if (!p.check || blockIdx.x != 0 || l >= p.depth) return;
+    uint32_t b0, p0, b1, p1;
+    node_at(p.B, p.n_geo, p.P4, s_off[l], b0, p0);
+    node_at(p.B, p.n_geo, p.P4, s_off[l + 1], b1, p1);
+    if (1u + p0 != s_off[l + 1] || p1 - p0 != s_off[l + 2] - s_off[l + 1])
+        set_status(p.status, SGS_E_CORRUPT);
+}
+
+__global__ void __launch_bounds__(kExpThreads) k_octree_chain(ExpandParams p) {
+    __shared__ uint32_t s_off[SGS_MAX_DEPTH + 2];
+    const int tid = threadIdx.x;
+    if (tid <= p.depth + 1) s_off[tid] = (uint32_t)p.level_off[tid];
+    __syncthreads();
+    check_levels(p, s_off);
+    const uint32_t lo = s_off[p.ls], hi = s_off[p.ls + 1];
+    const uint32_t T = gridDim.x * kExpThreads;
+    const uint32_t x0 = lo + blockIdx.x * kExpThreads + tid;
+    uint32_t node[kIlp], byte[kIlp], pp[kIlp];
+    uint64_t code[kIlp];
+    bool live[kIlp];
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        node[j] = x0 + j * T;
+        live[j] = node[j] < hi;
+        byte[j] = 0;
+        pp[j] = 0;
+        code[j] = 0;
+        if (live[j]) {
+            node_at(p.B, p.n_geo, p.P4, node[j], byte[j], pp[j]);
+            code[j] = p.codes_in[node[j] - lo];
+        }
+    }
+    int lvl = p.ls;
+    // all live nodes single-child: step every chain down one level together
+    while (lvl + 1 < p.le) {
+        bool all_single = true;
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) all_single &= !live[j] || __popc(byte[j]) == 1;
+        if (!all_single) break;
+        ++lvl;
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            if (!live[j]) continue;
+            const uint32_t child = 1u + pp[j];
+            if (child < s_off[lvl] || child >= s_off[lvl + 1]) {
+                set_status(p.status, SGS_E_CORRUPT);
+                live[j] = false;
+                continue;
+            }
+            code[j] = child_code(code[j], __ffs(byte[j]) - 1);
+            node[j] = child;
+        }
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j)
+            if (live[j]) node_at(p.B, p.n_geo, p.P4, node[j], byte[j], pp[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j)
+        if (live[j]) expand_from(p, s_off, lvl, byte[j], pp[j], code[j]);
+}
+
 int octree_top_level(const GeoPlan &plan) {
     int l1 = 1;
     while (l1 < plan.depth && plan.n_level[l1] <= kTopCap) ++l1;
@@ -467,8 +577,14 @@ cudaError_t launch_octree(const uint8_t *B, const sgs_scene_info &info, const Ge
         ep.codes_in = s.codes[gi & 1];
         ep.codes_out = ep.le < D ? s.codes[(gi + 1) & 1] : nullptr;
         ep.check = gi == 0;
-        const unsigned grid = (unsigned)((plan.n_level[ep.ls] + kExpThreads - 1) / kExpThreads);
-        k_octree_expand<<<grid, kExpThreads, 0, st>>>(ep);
+        if (ep.le - ep.ls > 1) {
+            const uint64_t per = (uint64_t)kExpThreads * kIlp;
+            const unsigned grid = (unsigned)((plan.n_level[ep.ls] + per - 1) / per);
+            k_octree_chain<<<grid, kExpThreads, 0, st>>>(ep);
+        } else {
+            const unsigned grid = (unsigned)((plan.n_level[ep.ls] + kExpThreads - 1) / kExpThreads);
+            k_octree_expand<<<grid, kExpThreads, 0, st>>>(ep);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
