@@ -457,13 +457,23 @@ __global__ void __launch_bounds__(kExpThreads) k_octree_chain(ExpandParams p) {
             code[j] = p.codes_in[node[j] - lo];
         }
     }
+    // step every single-child chain down one level together; a chain that branches leaves
+    // the group with its own level and is finished depth first afterwards
     int lvl = p.ls;
-    // all live nodes single-child: step every chain down one level together
-    while (lvl + 1 < p.le) {
-        bool all_single = true;
+    int dlvl[kIlp];
 #pragma unroll
-        for (int j = 0; j < kIlp; ++j) all_single &= !live[j] || __popc(byte[j]) == 1;
-        if (!all_single) break;
+    for (int j = 0; j < kIlp; ++j) dlvl[j] = -1;
+    while (lvl + 1 < p.le) {
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            if (live[j] && __popc(byte[j]) != 1) {
+                live[j] = false;
+                dlvl[j] = lvl;
+            }
+            any |= live[j];
+        }
+        if (!any) break;
         ++lvl;
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
@@ -482,8 +492,10 @@ __global__ void __launch_bounds__(kExpThreads) k_octree_chain(ExpandParams p) {
             if (live[j]) node_at(p.B, p.n_geo, p.P4, node[j], byte[j], pp[j]);
     }
 #pragma unroll
-    for (int j = 0; j < kIlp; ++j)
+    for (int j = 0; j < kIlp; ++j) {
         if (live[j]) expand_from(p, s_off, lvl, byte[j], pp[j], code[j]);
+        else if (dlvl[j] >= 0) expand_from(p, s_off, dlvl[j], byte[j], pp[j], code[j]);
+    }
 }
 
 int octree_top_level(const GeoPlan &plan) {
