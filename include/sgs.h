@@ -190,16 +190,55 @@ int scene_decode(sgs_ctx *ctx, const uint8_t *bits_dev, const sgs_scene_info *in
 int scene_decode_noalloc(const uint8_t *bits_dev, const sgs_scene_info *info,
                          const sgs_scene_out *out, sgs_stream stream);
 
-/* One batch item for scene_decode_batch. */
+/* One scene of a batch: its bitstream (device, 16-byte aligned), its scene_query result and
+ * its caller-allocated outputs (as for scene_decode). */
 typedef struct {
     const uint8_t *bits_dev;
     sgs_scene_info info;
     sgs_scene_out out;
 } sgs_batch_item;
 
-/* Decodes n scenes of any modes and sizes with one launch per pipeline stage covering all
- * scenes (a work list over every scene's lanes, groups and octree tiles).  Scratch need =
- * the sum over items of info.scratch_bytes.  Same errors as scene_decode.                  */
+/* Batched decode (no counterpart in the paper, which decodes one scene at a time; the scenes
+ * are independent, and Sec. 3.4.2's parallelism over groups extends across them).  Every
+ * pipeline stage of all n scenes runs as ONE persistent launch: its CTAs take work items
+ * (the lanes' groups, table expansions, scan tiles, octree node blocks of every scene) from
+ * a shared counter.  The octree expansion takes one launch per level-group index, so a run
+ * is about 10 + (deepest scene's expansion groups) launches whatever n is.
+ *
+ * A plan binds the items' buffers (bitstreams, outputs) and holds, in one device block, every
+ * scene's scratch, the per-stage work lists and per-scene status words. */
+typedef struct sgs_batch sgs_batch;
+
+/* Device bytes of a plan for these items (the scratch of every scene plus the work lists).
+ * Errors: SGS_E_INVALID (NULL, misaligned bitstream, missing outputs, info not produced by
+ * scene_query), SGS_E_UNSUPPORTED (more than 2^31 work items in a stage). */
+int scene_batch_bytes(const sgs_batch_item *items, int n, size_t *bytes);
+
+/* Builds a plan on ctx's device: allocates its device block (cudaMalloc) and uploads the
+ * work lists (synchronously).  The items array may be freed afterwards; the buffers it
+ * points to must stay valid while the plan is used.  Errors: as scene_batch_bytes, plus
+ * SGS_E_NOMEM, SGS_E_CUDA. */
+int scene_batch_plan(sgs_ctx *ctx, const sgs_batch_item *items, int n, sgs_batch **plan);
+
+/* Enqueues one decode of every scene of the plan on `stream` (the context's internal
+ * streams fork from it and join back).  Allocates nothing and does not wait for the device,
+ * so the call can be captured in a CUDA graph and replayed; every run re-decodes the bound
+ * bitstreams into the bound outputs.  A run's status goes to the context (sgs_sync) and per
+ * scene to scene_batch_status.  Runs of one plan, or of plans sharing the context, must be
+ * ordered on one stream.  Errors: SGS_E_INVALID (plan of another device), SGS_E_CUDA. */
+int scene_batch_run(sgs_ctx *ctx, sgs_batch *plan, sgs_stream stream);
+
+/* Copies the per-scene status words of the plan's last completed run (n = the plan's
+ * scene count) to host memory; call after the run's stream has finished.  Blocking. */
+int scene_batch_status(const sgs_batch *plan, int *status, int n);
+
+/* Frees the plan's device block (after its runs have finished). */
+void scene_batch_free(sgs_batch *plan);
+
+/* One-shot batched decode with the context's scratch as the plan's device block: needs
+ * scene_batch_bytes(items, n) <= the context's scratch (else SGS_E_NOMEM, nothing enqueued).
+ * Asynchronous; the work lists are copied to the scratch in `stream` order, so calls that
+ * share the context must use one stream.  Status via sgs_sync.  Same errors as scene_decode. */
 int scene_decode_batch(sgs_ctx *ctx, const sgs_batch_item *items, int n, sgs_stream stream);
 
 /* ------------------------------------------------------------------ encode */

@@ -8,26 +8,8 @@
 #include <algorithm>
 #include <new>
 
+#include "sgs_ctx.h"
 #include "sgs_internal.h"
-
-constexpr int kMaxStages = 8;
-
-struct sgs_ctx {
-    int device;
-    uint8_t *scratch;
-    size_t scratch_bytes;
-    int *status_dev;
-    int *status_host;  // pinned
-    uint64_t launches; // kernels launched by decode calls on this context
-    int profile;       // record stage events in decode calls
-    int n_marks;
-    cudaEvent_t marks[kMaxStages + 1];  // caller's stream: start, tokens, octree, end
-    cudaEvent_t amarks[2];              // attribute stream: start, end
-    cudaStream_t aux;                   // attribute decode (lowest priority), forked from the caller
-    cudaStream_t geo;                   // geometry chain (highest priority)
-    cudaStream_t aux2;                  // octree top levels (highest priority), beside the scan
-    cudaEvent_t fork, join, gjoin, top_fork, top_join;
-};
 
 namespace sgs {
 
@@ -369,16 +351,14 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
     if (c->profile) cudaEventRecord(c->amarks[1], c->aux);
     if (cudaEventRecord(c->join, c->aux) != cudaSuccess) return SGS_E_CUDA;
     cudaStream_t gs = c->geo;
-    const uint8_t *B = bits + info.off[S_GEO_RAW];
     if (info.geo_mode == SGS_GEO_RANS && info.n_geo) {
         if ((e = launch_geo_copy_raw(bits, info, plan, s.geo_bytes, gs)) != cudaSuccess) return SGS_E_CUDA;
         if ((e = launch_rans_static_geo(bits, info, plan, s.tables, s.geo_bytes, status, gs)) != cudaSuccess)
             return SGS_E_CUDA;
-        B = s.geo_bytes;
         c->launches += 2;
     }
     if (c->profile && c->n_marks <= kMaxStages) cudaEventRecord(c->marks[c->n_marks++], gs);
-    if ((e = launch_octree(B, info, plan, bits, s, out, status, gs, c->aux2, c->top_fork, c->top_join)) !=
+    if ((e = launch_octree(info, plan, bits, s, out, status, gs, c->aux2, c->top_fork, c->top_join)) !=
         cudaSuccess)
         return SGS_E_CUDA;
     if (info.n_rows) c->launches += octree_launches(info, plan);
@@ -399,25 +379,4 @@ extern "C" int scene_decode(sgs_ctx *c, const uint8_t *bits, const sgs_scene_inf
     if (info->scratch_bytes > c->scratch_bytes) return SGS_E_NOMEM;
     if (cudaSetDevice(c->device) != cudaSuccess) return SGS_E_CUDA;
     return decode_one(c, bits, *info, *out, c->scratch, (cudaStream_t)stream);
-}
-
-extern "C" int scene_decode_batch(sgs_ctx *c, const sgs_batch_item *items, int n,
-                                  sgs_stream stream) {
-    if (!c || (!items && n) || n < 0) return SGS_E_INVALID;
-    uint64_t need = 0;
-    for (int i = 0; i < n; ++i) {
-        if (!items[i].bits_dev || ((uintptr_t)items[i].bits_dev & 15)) return SGS_E_INVALID;
-        if (items[i].info.n_rows && (!items[i].out.attr || !items[i].out.pos)) return SGS_E_INVALID;
-        need += a256(items[i].info.scratch_bytes);
-    }
-    if (need > c->scratch_bytes) return SGS_E_NOMEM;
-    if (cudaSetDevice(c->device) != cudaSuccess) return SGS_E_CUDA;
-    uint64_t off = 0;
-    for (int i = 0; i < n; ++i) {
-        int r = decode_one(c, items[i].bits_dev, items[i].info, items[i].out, c->scratch + off,
-                           (cudaStream_t)stream);
-        if (r != SGS_OK) return r;
-        off += a256(items[i].info.scratch_bytes);
-    }
-    return SGS_OK;
 }

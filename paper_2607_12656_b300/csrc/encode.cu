@@ -122,6 +122,7 @@ int prepare(const float *pos, const float *attr, uint32_t n, uint32_t D, const u
     // per-channel quantization
     const uint32_t R = P.rows();
     P.q16.assign((size_t)R * kNChan, 0);
+#pragma omp parallel for schedule(dynamic, 1)
     for (int c = 0; c < kNChan; ++c) {
         const float *v = attr + (uint64_t)c * n;
         if (R == 0) {
@@ -186,17 +187,16 @@ void put_table(std::vector<uint8_t> &o, const uint32_t *f) {
 // sym_f / sym_c: frequency and cumulative of every token, lane-major (lane_start offsets).
 void rans_encode(const std::vector<uint64_t> &lane_start, const uint32_t *sym_f,
                  const uint32_t *sym_c, std::vector<uint8_t> &grp, std::vector<uint8_t> &pay) {
-    const uint64_t L = lane_start.size() - 1;
-    const uint64_t G = (L + 31) / 32;
-    std::vector<uint64_t> goff(G + 1, 0);
-    std::vector<uint32_t> gw(G, 0);
-    std::vector<uint16_t> w;
-    for (uint64_t g = 0; g < G; ++g) {
-        const uint64_t j0 = 32 * g, j1 = std::min(L, j0 + 32);
+    const int64_t L = (int64_t)lane_start.size() - 1;
+    const int64_t G = (L + 31) / 32;
+    std::vector<std::vector<uint16_t>> words(G);  // each group's stream, in emission order
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t g = 0; g < G; ++g) {
+        const int64_t j0 = 32 * g, j1 = std::min(L, j0 + 32);
         const int nl = (int)(j1 - j0);
         uint64_t maxn = 0;
-        for (uint64_t j = j0; j < j1; ++j) maxn = std::max(maxn, lane_start[j + 1] - lane_start[j]);
-        w.clear();
+        for (int64_t j = j0; j < j1; ++j) maxn = std::max(maxn, lane_start[j + 1] - lane_start[j]);
+        std::vector<uint16_t> &w = words[g];
         uint32_t x[32];
         for (int j = 0; j < nl; ++j) x[j] = kM;
         for (uint64_t tt = maxn; tt-- > 0;) {
@@ -216,14 +216,26 @@ void rans_encode(const std::vector<uint64_t> &lane_start, const uint32_t *sym_f,
             w.push_back((uint16_t)(x[j] & 0xFFFFu));
             w.push_back((uint16_t)(x[j] >> 16));
         }
-        gw[g] = (uint32_t)w.size();
-        for (size_t k = w.size(); k-- > 0;) {
-            pay.push_back((uint8_t)(w[k] & 0xFF));
-            pay.push_back((uint8_t)(w[k] >> 8));
-        }
-        while (pay.size() % 16) pay.push_back(0);
-        goff[g + 1] = pay.size();
     }
+    // assemble: each group's words reversed, little endian, padded to 16 bytes
+    std::vector<uint64_t> goff(G + 1, 0);
+    std::vector<uint32_t> gw(G, 0);
+    for (int64_t g = 0; g < G; ++g) {
+        gw[g] = (uint32_t)words[g].size();
+        goff[g + 1] = goff[g] + ((2ull * gw[g] + 15) & ~15ull);
+    }
+    const size_t base = pay.size();
+    pay.resize(base + goff[G], 0);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t g = 0; g < G; ++g) {
+        uint8_t *o = pay.data() + base + goff[g];
+        const std::vector<uint16_t> &w = words[g];
+        for (size_t k = w.size(), i = 0; k-- > 0; ++i) {
+            o[2 * i] = (uint8_t)(w[k] & 0xFF);
+            o[2 * i + 1] = (uint8_t)(w[k] >> 8);
+        }
+    }
+    for (int64_t g = 0; g <= G; ++g) goff[g] += base;
     grp.resize(8 * (G + 1) + 4 * G);
     memcpy(grp.data(), goff.data(), 8 * (G + 1));
     memcpy(grp.data() + 8 * (G + 1), gw.data(), 4 * G);
@@ -387,12 +399,14 @@ extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, u
             std::vector<uint64_t> rstart;
             static_row_order(R, L, perm, rstart);
             for (uint64_t j = 0; j <= L; ++j) starts[j] = rstart[j] * kNChan;
+            std::vector<uint32_t> ftab((size_t)kNChan * kNSym);
+#pragma omp parallel for schedule(dynamic, 1)
             for (int c = 0; c < kNChan; ++c) {
                 uint64_t h[kNSym] = {0};
                 for (uint32_t rr = 0; rr < R; ++rr) h[P.q16[(size_t)rr * kNChan + c]]++;
-                uint32_t f[kNSym], cu[kNSym];
+                uint32_t *f = &ftab[(size_t)c * kNSym];
+                uint32_t cu[kNSym];
                 normalize(h, f);
-                put_table(s_atab, f);
                 uint32_t acc = 0;
                 for (int s = 0; s < kNSym; ++s) { cu[s] = acc; acc += f[s]; }
                 for (uint64_t p = 0; p < R; ++p) {
@@ -401,6 +415,7 @@ extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, u
                     scu[p * kNChan + c] = cu[q];
                 }
             }
+            for (int c = 0; c < kNChan; ++c) put_table(s_atab, &ftab[(size_t)c * kNSym]);
         } else {
             const uint8_t *m = static_cast<const uint8_t *>(prm->model);
             s_atab.assign(m, m + SGS_MODEL_BYTES);

@@ -9,6 +9,7 @@
 // reads sum(b_c)/8 bytes and writes 224.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "sgs_device.cuh"
 #include "sgs_internal.h"
@@ -32,10 +33,10 @@ struct FixedParams {
 // VEC: every channel's output base is 16-byte aligned and there is no out_index, so lane j
 // writes rows 4j..4j+3 (+128 k) with one 16-byte store; otherwise one 4-byte store per row.
 template <bool VEC>
-__global__ void __launch_bounds__(32 * kFixWarps) k_fixed(FixedParams p) {
+__device__ __forceinline__ void fixed_body(const FixedParams &p, uint32_t vb) {
     __shared__ uint32_t s_words[kFixWarps][32 * kFixMaxBits + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint64_t item = (uint64_t)blockIdx.x * kFixWarps + warp;
+    const uint64_t item = (uint64_t)vb * kFixWarps + warp;
     const uint32_t c = (uint32_t)(item / p.n_items_per_chan);
     if (c >= (uint32_t)kNChan) return;
     const uint32_t blk = (uint32_t)(item - (uint64_t)c * p.n_items_per_chan);
@@ -95,10 +96,20 @@ __global__ void __launch_bounds__(32 * kFixWarps) k_fixed(FixedParams p) {
     }
 }
 
-cudaError_t launch_fixed(const uint8_t *bits, const sgs_scene_info &info,
-                         const sgs_scene_out &out, int *status, cudaStream_t st) {
-    if (info.n_rows == 0) return cudaSuccess;
-    FixedParams p;
+template <bool VEC>
+__global__ void __launch_bounds__(32 * kFixWarps) k_fixed(FixedParams p) { fixed_body<VEC>(p, blockIdx.x); }
+
+template <bool VEC>
+__global__ void __launch_bounds__(32 * kFixWarps) k_fixed_multi(MultiArgs m) {
+    run_items<FixedParams>(m, [](const FixedParams &p, uint32_t vb, uint32_t, bool) { fixed_body<VEC>(p, vb); });
+}
+
+// Parameters of one scene; returns its CTAs (0: nothing to do) and whether it takes the
+// vector-store variant.
+uint32_t make_fixed(const uint8_t *bits, const sgs_scene_info &info, const sgs_scene_out &out,
+                    int *status, FixedParams *pp, bool *vec) {
+    FixedParams &p = *pp;
+    memset(&p, 0, sizeof(p));
     p.bits = bits;
     p.chan_off = info.off[S_CHAN];
     p.tab_off = info.off[S_ATTR_TAB];
@@ -109,12 +120,39 @@ cudaError_t launch_fixed(const uint8_t *bits, const sgs_scene_info &info,
     p.out = out.attr;
     p.out_index = out.out_index;
     p.status = status;
+    *vec = !out.out_index && (info.n_rows % 4 == 0) && (((uintptr_t)out.attr & 15) == 0);
+    if (info.n_rows == 0) return 0;
     const uint64_t items = (uint64_t)p.n_items_per_chan * kNChan;
-    const unsigned grid = (unsigned)((items + kFixWarps - 1) / kFixWarps);
-    const bool vec = !out.out_index && (info.n_rows % 4 == 0) && (((uintptr_t)out.attr & 15) == 0);
+    return (uint32_t)((items + kFixWarps - 1) / kFixWarps);
+}
+
+cudaError_t launch_fixed(const uint8_t *bits, const sgs_scene_info &info,
+                         const sgs_scene_out &out, int *status, cudaStream_t st) {
+    FixedParams p;
+    bool vec;
+    const uint32_t grid = make_fixed(bits, info, out, status, &p, &vec);
+    if (grid == 0) return cudaSuccess;
     if (vec) k_fixed<true><<<grid, 32 * kFixWarps, 0, st>>>(p);
     else k_fixed<false><<<grid, 32 * kFixWarps, 0, st>>>(p);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ batched stage
+
+uint32_t stage_fixed(const SceneRef &r, bool vec_variant, void *par) {
+    FixedParams p;
+    bool vec;
+    const uint32_t n = make_fixed(r.bits, *r.info, *r.out, r.status, &p, &vec);
+    if (vec != vec_variant) return 0;
+    memcpy(par, &p, sizeof(p));
+    return n;
+}
+
+size_t stage_fixed_bytes() { return sizeof(FixedParams); }
+
+cudaError_t launch_fixed_multi(bool vec, const MultiArgs &m, cudaStream_t st) {
+    if (vec) return launch_persistent(k_fixed_multi<true>, 32 * kFixWarps, 0, m, st);
+    return launch_persistent(k_fixed_multi<false>, 32 * kFixWarps, 0, m, st);
 }
 
 }  // namespace sgs

@@ -14,6 +14,7 @@
 // expanded by one CTA, concurrently with the scan.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "sgs_device.cuh"
 #include "sgs_internal.h"
@@ -88,15 +89,26 @@ __device__ __forceinline__ uint32_t word_at(const uint8_t *B, uint64_t n, uint64
 }
 
 // P4[k] = popcount of B[0, 4k) for k = 0 .. ceil(n/4).  Tile = 256 threads x 64 bytes.
-__global__ void __launch_bounds__(kScanThreads) k_octree_scan(const uint8_t *B, uint64_t n,
-                                                              uint32_t *P4, uint64_t n_words,
-                                                              uint64_t *flags, uint32_t *ticket,
-                                                              int *status) {
+// Tiles must start in increasing order: a tile's look-back waits only on tiles that started
+// before it (the single-scene kernel draws tiles from a ticket, the batched one claims items
+// in order).
+struct ScanParams {
+    const uint8_t *B;
+    uint64_t n, n_words;
+    uint32_t *P4;
+    uint64_t *flags;
+    uint32_t *ticket;
+    int *status;
+};
+
+__device__ __forceinline__ void scan_body(const ScanParams &sp, uint32_t tile) {
     __shared__ uint32_t sm[8];
-    __shared__ uint32_t s_tile, s_prefix;
-    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
+    __shared__ uint32_t s_prefix;
+    const uint8_t *B = sp.B;
+    const uint64_t n = sp.n, n_words = sp.n_words;
+    uint32_t *P4 = sp.P4;
+    uint64_t *flags = sp.flags;
+    int *status = sp.status;
     const uint64_t k = (uint64_t)tile * kScanThreads + threadIdx.x;  // 64-byte chunk
     const uint64_t w0 = 16 * k;                                      // its first word
     uint32_t cnt[16];
@@ -168,6 +180,17 @@ __global__ void __launch_bounds__(kScanThreads) k_octree_scan(const uint8_t *B, 
     }
 }
 
+__global__ void __launch_bounds__(kScanThreads) k_octree_scan(ScanParams p) {
+    __shared__ uint32_t s_tile;
+    if (threadIdx.x == 0) s_tile = atomicAdd(p.ticket, 1u);
+    __syncthreads();
+    scan_body(p, s_tile);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_octree_scan_multi(MultiArgs m) {
+    run_items<ScanParams>(m, [](const ScanParams &p, uint32_t vb, uint32_t, bool) { scan_body(p, vb); });
+}
+
 // Node x of B: its token and P(x) from the word prefix.
 __device__ __forceinline__ void node_at(const uint8_t *B, uint64_t n, const uint32_t *P4,
                                         uint32_t x, uint32_t &byte, uint32_t &p) {
@@ -179,10 +202,18 @@ __device__ __forceinline__ void node_at(const uint8_t *B, uint64_t n, const uint
 
 // ------------------------------------------------------------------ duplicates
 
-__global__ void __launch_bounds__(256) k_dup_prefix(const uint32_t *dup, uint32_t n_dup,
-                                                    uint32_t n_leaves, uint32_t n_rows,
-                                                    uint32_t *dup_prefix, int *status) {
+struct DupParams {
+    const uint32_t *dup;
+    uint32_t n_dup, n_leaves, n_rows;
+    uint32_t *dup_prefix;
+    int *status;
+};
+
+__device__ __forceinline__ void dup_body(const DupParams &p) {
     __shared__ uint32_t sm[8];
+    const uint32_t *dup = p.dup;
+    const uint32_t n_dup = p.n_dup, n_leaves = p.n_leaves, n_rows = p.n_rows;
+    uint32_t *dup_prefix = p.dup_prefix;
     uint32_t carry = 0;
     bool bad = false;
     for (uint32_t base = 0; base < n_dup; base += 256) {
@@ -202,7 +233,13 @@ __global__ void __launch_bounds__(256) k_dup_prefix(const uint32_t *dup, uint32_
         dup_prefix[n_dup] = carry;
         if ((uint64_t)carry + n_leaves != n_rows) bad = true;
     }
-    if (bad) set_status(status, SGS_E_CORRUPT);
+    if (bad) set_status(p.status, SGS_E_CORRUPT);
+}
+
+__global__ void __launch_bounds__(256) k_dup_prefix(DupParams p) { dup_body(p); }
+
+__global__ void __launch_bounds__(256) k_dup_multi(MultiArgs m) {
+    run_items<DupParams>(m, [](const DupParams &p, uint32_t, uint32_t, bool) { dup_body(p); });
 }
 
 // ------------------------------------------------------------------ top levels (one CTA)
@@ -218,7 +255,7 @@ struct TopParams {
 
 constexpr uint32_t kTopStage = 8192;  // top-level tokens staged in shared memory
 
-__global__ void __launch_bounds__(kTopThreads) k_octree_top(TopParams p) {
+__device__ __forceinline__ void top_body(const TopParams &p) {
     __shared__ uint64_t codes[2][kTopCap];
     __shared__ uint8_t stage[kTopStage];
     __shared__ uint32_t wsum[32];
@@ -287,6 +324,12 @@ __global__ void __launch_bounds__(kTopThreads) k_octree_top(TopParams p) {
     }
 }
 
+__global__ void __launch_bounds__(kTopThreads) k_octree_top(TopParams p) { top_body(p); }
+
+__global__ void __launch_bounds__(kTopThreads) k_octree_top_multi(MultiArgs m) {
+    run_items<TopParams>(m, [](const TopParams &p, uint32_t, uint32_t, bool) { top_body(p); });
+}
+
 // ------------------------------------------------------------------ fused levels
 
 // Thread per node x of level ls: depth-first through levels ls .. le-1, emitting the nodes of
@@ -305,7 +348,7 @@ struct ExpandParams {
     int *status;
 };
 
-__global__ void __launch_bounds__(kExpThreads) k_octree_expand(ExpandParams p) {
+__device__ __forceinline__ void expand_body(const ExpandParams &p, uint32_t vb) {
     __shared__ uint32_t s_p[kMaxFuse][kExpThreads];
     __shared__ uint32_t s_it[kMaxFuse][kExpThreads];  // remaining mask | taken << 8
     __shared__ uint64_t s_code[kMaxFuse][kExpThreads];
@@ -313,7 +356,7 @@ __global__ void __launch_bounds__(kExpThreads) k_octree_expand(ExpandParams p) {
     const int tid = threadIdx.x;
     if (tid <= p.depth + 1) s_off[tid] = (uint32_t)p.level_off[tid];
     __syncthreads();
-    if (p.check && blockIdx.x == 0 && tid < p.depth) {
+    if (p.check && vb == 0 && tid < p.depth) {
         // sum of the popcounts of level l = nodes of level l+1, and the first child of the
         // level's first node is the next level's first node
         const int l = tid;
@@ -324,7 +367,7 @@ __global__ void __launch_bounds__(kExpThreads) k_octree_expand(ExpandParams p) {
             set_status(p.status, SGS_E_CORRUPT);
     }
     const uint32_t lo = s_off[p.ls];
-    const uint32_t x = lo + blockIdx.x * kExpThreads + tid;
+    const uint32_t x = lo + vb * kExpThreads + tid;
     if (x >= s_off[p.ls + 1]) return;
     uint32_t byte, px;
     node_at(p.B, p.n_geo, p.P4, x, byte, px);
@@ -376,126 +419,10 @@ __global__ void __launch_bounds__(kExpThreads) k_octree_expand(ExpandParams p) {
     }
 }
 
-// Chain-like level groups: each thread advances kIlp independent nodes (x, x + T, ...) one
-// level at a time, issuing all their loads before using any, so a resident grid keeps many
-// dependent load chains in flight.  A node with several children (rare below the cut) is
-// finished by the depth-first walk of expand_from.
-constexpr int kIlp = 4;
+__global__ void __launch_bounds__(kExpThreads) k_octree_expand(ExpandParams p) { expand_body(p, blockIdx.x); }
 
-// Depth-first expansion of one node (byte b, P value pp, code) at level lvl down to level le.
-__device__ __noinline__ void expand_from(const ExpandParams &p, const uint32_t *s_off, int lvl,
-                                         uint32_t b, uint32_t pp, uint64_t code) {
-    uint32_t st_p[kMaxFuse], st_it[kMaxFuse];
-    uint64_t st_code[kMaxFuse];
-    st_p[0] = pp;
-    st_it[0] = b;
-    st_code[0] = code;
-    const int K = p.le - lvl;
-    const uint32_t leaf_base = s_off[p.depth];
-    int d = 0;
-    while (d >= 0) {
-        const uint32_t it = st_it[d];
-        const uint32_t mask = it & 0xFFu;
-        if (!mask) { --d; continue; }
-        const uint32_t k = __ffs(mask) - 1;
-        const uint32_t taken = it >> 8;
-        st_it[d] = (mask & (mask - 1)) | ((taken + 1) << 8);
-        const uint32_t child = 1u + st_p[d] + taken;
-        const int lc = lvl + d + 1;
-        if (child < s_off[lc] || child >= s_off[lc + 1]) {
-            set_status(p.status, SGS_E_CORRUPT);
-            return;
-        }
-        const uint64_t cc = child_code(st_code[d], k);
-        if (d + 1 == K) {
-            if (lc == p.depth) write_leaf(p.leaf, child - leaf_base, cc, p.status);
-            else p.codes_out[child - s_off[lc]] = cc;
-        } else {
-            uint32_t cb, cp;
-            node_at(p.B, p.n_geo, p.P4, child, cb, cp);
-            ++d;
-            st_p[d] = cp;
-            st_it[d] = cb;
-            st_code[d] = cc;
-        }
-    }
-}
-
-// Level-count check (CTA 0 of the first expansion launch): the popcounts of level l sum to
-// the node count of level l+1, and level l's first node has level l+1's first node as child.
-__device__ __forceinline__ void check_levels(const ExpandParams &p, const uint32_t *s_off) {
-    const int l = threadIdx.x;
-    if (!p.check || blockIdx.x != 0 || l >= p.depth) return;
-    uint32_t b0, p0, b1, p1;
-    node_at(p.B, p.n_geo, p.P4, s_off[l], b0, p0);
-    node_at(p.B, p.n_geo, p.P4, s_off[l + 1], b1, p1);
-    if (1u + p0 != s_off[l + 1] || p1 - p0 != s_off[l + 2] - s_off[l + 1])
-        set_status(p.status, SGS_E_CORRUPT);
-}
-
-__global__ void __launch_bounds__(kExpThreads) k_octree_chain(ExpandParams p) {
-    __shared__ uint32_t s_off[SGS_MAX_DEPTH + 2];
-    const int tid = threadIdx.x;
-    if (tid <= p.depth + 1) s_off[tid] = (uint32_t)p.level_off[tid];
-    __syncthreads();
-    check_levels(p, s_off);
-    const uint32_t lo = s_off[p.ls], hi = s_off[p.ls + 1];
-    const uint32_t T = gridDim.x * kExpThreads;
-    const uint32_t x0 = lo + blockIdx.x * kExpThreads + tid;
-    uint32_t node[kIlp], byte[kIlp], pp[kIlp];
-    uint64_t code[kIlp];
-    bool live[kIlp];
-#pragma unroll
-    for (int j = 0; j < kIlp; ++j) {
-        node[j] = x0 + j * T;
-        live[j] = node[j] < hi;
-        byte[j] = 0;
-        pp[j] = 0;
-        code[j] = 0;
-        if (live[j]) {
-            node_at(p.B, p.n_geo, p.P4, node[j], byte[j], pp[j]);
-            code[j] = p.codes_in[node[j] - lo];
-        }
-    }
-    // step every single-child chain down one level together; a chain that branches leaves
-    // the group with its own level and is finished depth first afterwards
-    int lvl = p.ls;
-    int dlvl[kIlp];
-#pragma unroll
-    for (int j = 0; j < kIlp; ++j) dlvl[j] = -1;
-    while (lvl + 1 < p.le) {
-        bool any = false;
-#pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
-            if (live[j] && __popc(byte[j]) != 1) {
-                live[j] = false;
-                dlvl[j] = lvl;
-            }
-            any |= live[j];
-        }
-        if (!any) break;
-        ++lvl;
-#pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
-            if (!live[j]) continue;
-            const uint32_t child = 1u + pp[j];
-            if (child < s_off[lvl] || child >= s_off[lvl + 1]) {
-                set_status(p.status, SGS_E_CORRUPT);
-                live[j] = false;
-                continue;
-            }
-            code[j] = child_code(code[j], __ffs(byte[j]) - 1);
-            node[j] = child;
-        }
-#pragma unroll
-        for (int j = 0; j < kIlp; ++j)
-            if (live[j]) node_at(p.B, p.n_geo, p.P4, node[j], byte[j], pp[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < kIlp; ++j) {
-        if (live[j]) expand_from(p, s_off, lvl, byte[j], pp[j], code[j]);
-        else if (dlvl[j] >= 0) expand_from(p, s_off, dlvl[j], byte[j], pp[j], code[j]);
-    }
+__global__ void __launch_bounds__(kExpThreads) k_octree_expand_multi(MultiArgs m) {
+    run_items<ExpandParams>(m, [](const ExpandParams &p, uint32_t vb, uint32_t, bool) { expand_body(p, vb); });
 }
 
 int octree_top_level(const GeoPlan &plan) {
@@ -522,17 +449,18 @@ int octree_groups(const GeoPlan &plan, int *starts) {
     return n;
 }
 
-size_t octree_scan_tiles(uint64_t n_geo);
+// ------------------------------------------------------------------ parameters
 
-// ------------------------------------------------------------------ launcher
+// The token array the octree kernels read: the stream's raw section, or the scratch copy
+// the geometry decoder filled when levels are rANS-coded.
+static const uint8_t *geo_tokens(const uint8_t *bits, const sgs_scene_info &info, const Scratch &s) {
+    return (info.geo_mode == SGS_GEO_RANS && info.n_geo) ? s.geo_bytes : bits + info.off[S_GEO_RAW];
+}
 
-cudaError_t launch_octree(const uint8_t *B, const sgs_scene_info &info, const GeoPlan &plan,
-                          const uint8_t *bits, const Scratch &s, const sgs_scene_out &out,
-                          int *status, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_a,
-                          cudaEvent_t ev_b) {
-    if (info.n_rows == 0 || info.n_leaves == 0) return cudaSuccess;
-    const int D = plan.depth;
+static LeafOut make_leaf(const uint8_t *bits, const sgs_scene_info &info, const Scratch &s,
+                         const sgs_scene_out &out) {
     LeafOut lo;
+    memset(&lo, 0, sizeof(lo));
     lo.pos = out.pos;
     lo.coord = out.coord;
     lo.out_index = out.out_index;
@@ -544,62 +472,165 @@ cudaError_t launch_octree(const uint8_t *B, const sgs_scene_info &info, const Ge
     lo.dup_prefix = s.dup_prefix;
     lo.scale = ldexpf(1.0f, -(int)info.depth);
     lo.half = ldexpf(1.0f, -(int)info.depth - 1);
-    cudaError_t e;
-    if (info.n_dup) {
-        k_dup_prefix<<<1, 256, 0, st>>>(lo.dup, info.n_dup, info.n_leaves, info.n_rows,
-                                        s.dup_prefix, status);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    const uint64_t n_words = (info.n_geo + 3) / 4;
-    const uint64_t n_tiles = octree_scan_tiles(info.n_geo);
+    return lo;
+}
+
+static bool octree_work(const sgs_scene_info &info) { return info.n_rows != 0 && info.n_leaves != 0; }
+
+static uint32_t make_dup(const uint8_t *bits, const sgs_scene_info &info, const Scratch &s, int *status,
+                         DupParams *pp) {
+    DupParams &p = *pp;
+    memset(&p, 0, sizeof(p));
+    p.dup = reinterpret_cast<const uint32_t *>(bits + info.off[S_DUP]);
+    p.n_dup = info.n_dup;
+    p.n_leaves = info.n_leaves;
+    p.n_rows = info.n_rows;
+    p.dup_prefix = s.dup_prefix;
+    p.status = status;
+    return (octree_work(info) && info.n_dup) ? 1 : 0;
+}
+
+static uint32_t make_scan(const uint8_t *bits, const sgs_scene_info &info, const Scratch &s, int *status,
+                          ScanParams *pp) {
+    ScanParams &p = *pp;
+    memset(&p, 0, sizeof(p));
+    p.B = geo_tokens(bits, info, s);
+    p.n = info.n_geo;
+    p.n_words = (info.n_geo + 3) / 4;
+    p.P4 = s.p4;
+    p.flags = s.scan_flags;
+    p.ticket = s.ticket;
+    p.status = status;
+    return octree_work(info) ? (uint32_t)octree_scan_tiles(info.n_geo) : 0;
+}
+
+static uint32_t make_top(const uint8_t *bits, const sgs_scene_info &info, const GeoPlan &plan,
+                         const Scratch &s, const sgs_scene_out &out, int *status, TopParams *pp) {
+    TopParams &p = *pp;
+    memset(&p, 0, sizeof(p));
+    const int l1 = octree_top_level(plan);
+    p.B = geo_tokens(bits, info, s);
+    p.plan = plan;
+    p.l1 = l1;
+    p.codes_out = (l1 < plan.depth) ? s.codes[0] : nullptr;
+    p.leaf = make_leaf(bits, info, s, out);
+    p.status = status;
+    return octree_work(info) ? 1 : 0;
+}
+
+// Expansion group gi (levels starts[gi] .. starts[gi+1]).
+static uint32_t make_expand(const uint8_t *bits, const sgs_scene_info &info, const GeoPlan &plan,
+                            const Scratch &s, const sgs_scene_out &out, int *status, int gi,
+                            ExpandParams *pp) {
+    ExpandParams &ep = *pp;
+    memset(&ep, 0, sizeof(ep));
     int starts[SGS_MAX_DEPTH + 2];
     const int n_groups = octree_groups(plan, starts);
-    const int l1 = octree_top_level(plan);
+    if (!octree_work(info) || gi >= n_groups) return 0;
+    const int D = plan.depth;
+    ep.B = geo_tokens(bits, info, s);
+    ep.n_geo = info.n_geo;
+    ep.P4 = s.p4;
+    ep.depth = D;
+    for (int l = 0; l <= D; ++l) ep.level_off[l] = plan.level_off[l];
+    ep.level_off[D + 1] = plan.level_off[D] + plan.n_level[D];
+    ep.leaf = make_leaf(bits, info, s, out);
+    ep.status = status;
+    ep.ls = starts[gi];
+    ep.le = starts[gi + 1];
+    ep.codes_in = s.codes[gi & 1];
+    ep.codes_out = ep.le < D ? s.codes[(gi + 1) & 1] : nullptr;
+    ep.check = gi == 0;
+    return (uint32_t)((plan.n_level[ep.ls] + kExpThreads - 1) / kExpThreads);
+}
+
+// ------------------------------------------------------------------ launcher
+
+cudaError_t launch_octree(const sgs_scene_info &info, const GeoPlan &plan,
+                          const uint8_t *bits, const Scratch &s, const sgs_scene_out &out,
+                          int *status, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_a,
+                          cudaEvent_t ev_b) {
+    if (!octree_work(info)) return cudaSuccess;
+    cudaError_t e;
+    DupParams dp;
+    if (make_dup(bits, info, s, status, &dp)) {
+        k_dup_prefix<<<1, 256, 0, st>>>(dp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     // the top levels need no prefix: they run on st2 while the scan runs on st
     if (st2 != st) {
         if (cudaEventRecord(ev_a, st) != cudaSuccess || cudaStreamWaitEvent(st2, ev_a, 0) != cudaSuccess)
             return cudaErrorUnknown;
     }
     TopParams tp;
-    tp.B = B;
-    tp.plan = plan;
-    tp.l1 = l1;
-    tp.codes_out = (l1 < D) ? s.codes[0] : nullptr;
-    tp.leaf = lo;
-    tp.status = status;
+    make_top(bits, info, plan, s, out, status, &tp);
     k_octree_top<<<1, kTopThreads, 0, st2>>>(tp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (st2 != st && cudaEventRecord(ev_b, st2) != cudaSuccess) return cudaErrorUnknown;
-    k_octree_scan<<<(unsigned)n_tiles, kScanThreads, 0, st>>>(B, info.n_geo, s.p4, n_words,
-                                                              s.scan_flags, s.ticket, status);
+    ScanParams sp;
+    const uint32_t tiles = make_scan(bits, info, s, status, &sp);
+    k_octree_scan<<<tiles, kScanThreads, 0, st>>>(sp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (st2 != st && cudaStreamWaitEvent(st, ev_b, 0) != cudaSuccess) return cudaErrorUnknown;
     ExpandParams ep;
-    ep.B = B;
-    ep.n_geo = info.n_geo;
-    ep.P4 = s.p4;
-    ep.depth = D;
-    for (int l = 0; l <= D; ++l) ep.level_off[l] = plan.level_off[l];
-    ep.level_off[D + 1] = plan.level_off[D] + plan.n_level[D];
-    ep.leaf = lo;
-    ep.status = status;
-    for (int gi = 0; gi < n_groups; ++gi) {
-        ep.ls = starts[gi];
-        ep.le = starts[gi + 1];
-        ep.codes_in = s.codes[gi & 1];
-        ep.codes_out = ep.le < D ? s.codes[(gi + 1) & 1] : nullptr;
-        ep.check = gi == 0;
-        if (ep.le - ep.ls > 1) {
-            const uint64_t per = (uint64_t)kExpThreads * kIlp;
-            const unsigned grid = (unsigned)((plan.n_level[ep.ls] + per - 1) / per);
-            k_octree_chain<<<grid, kExpThreads, 0, st>>>(ep);
-        } else {
-            const unsigned grid = (unsigned)((plan.n_level[ep.ls] + kExpThreads - 1) / kExpThreads);
-            k_octree_expand<<<grid, kExpThreads, 0, st>>>(ep);
-        }
+    for (int gi = 0;; ++gi) {
+        const uint32_t grid = make_expand(bits, info, plan, s, out, status, gi, &ep);
+        if (grid == 0) break;
+        k_octree_expand<<<grid, kExpThreads, 0, st>>>(ep);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// ------------------------------------------------------------------ batched stages
+
+uint32_t stage_dup(const SceneRef &r, void *par) {
+    DupParams p;
+    const uint32_t n = make_dup(r.bits, *r.info, *r.s, r.status, &p);
+    memcpy(par, &p, sizeof(p));
+    return n;
+}
+size_t stage_dup_bytes() { return sizeof(DupParams); }
+cudaError_t launch_dup_multi(const MultiArgs &m, cudaStream_t st) {
+    return launch_persistent(k_dup_multi, 256, 0, m, st);
+}
+
+uint32_t stage_scan(const SceneRef &r, void *par) {
+    ScanParams p;
+    const uint32_t n = make_scan(r.bits, *r.info, *r.s, r.status, &p);
+    memcpy(par, &p, sizeof(p));
+    return n;
+}
+size_t stage_scan_bytes() { return sizeof(ScanParams); }
+cudaError_t launch_scan_multi(const MultiArgs &m, cudaStream_t st) {
+    return launch_persistent(k_octree_scan_multi, kScanThreads, 0, m, st);
+}
+
+uint32_t stage_top(const SceneRef &r, void *par) {
+    TopParams p;
+    const uint32_t n = make_top(r.bits, *r.info, *r.plan, *r.s, *r.out, r.status, &p);
+    memcpy(par, &p, sizeof(p));
+    return n;
+}
+size_t stage_top_bytes() { return sizeof(TopParams); }
+cudaError_t launch_top_multi(const MultiArgs &m, cudaStream_t st) {
+    return launch_persistent(k_octree_top_multi, kTopThreads, 0, m, st);
+}
+
+uint32_t stage_expand(const SceneRef &r, int group, void *par) {
+    ExpandParams p;
+    const uint32_t n = make_expand(r.bits, *r.info, *r.plan, *r.s, *r.out, r.status, group, &p);
+    memcpy(par, &p, sizeof(p));
+    return n;
+}
+size_t stage_expand_bytes() { return sizeof(ExpandParams); }
+cudaError_t launch_expand_multi(const MultiArgs &m, cudaStream_t st) {
+    return launch_persistent(k_octree_expand_multi, kExpThreads, 0, m, st);
+}
+
+int octree_group_count(const sgs_scene_info &info, const GeoPlan &plan) {
+    int starts[SGS_MAX_DEPTH + 2];
+    return octree_work(info) ? octree_groups(plan, starts) : 0;
 }
 
 // Scratch of the octree stage: bytes of each ping-pong code buffer (the widest level that

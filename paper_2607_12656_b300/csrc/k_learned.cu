@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <string.h>
 #include <cuda_bf16.h>
 
 #include <vector>
@@ -362,13 +363,68 @@ __device__ __forceinline__ void produce_step(LSmem2 &S, uint32_t i, int c, int b
     }
 }
 
-__global__ void __launch_bounds__(kLT, 1) k_learned_decode(LearnedParams p) {
+// The consumer warp: the group's 32 rANS chains over K steps.
+__device__ __forceinline__ void consume(const LearnedParams &p, LSmem2 &S, uint32_t grp, int nl,
+                                        uint32_t K, volatile int *abort_) {
+    const int lane = threadIdx.x & 31;
+    GroupStream gs;
+    uint32_t x = 0x10000u;
+    group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, grp, nl, lane, gs, x, S.win);
+    bool aborted = false;
+    for (uint32_t k = 0; k < K; ++k) {
+        const int b = (int)(k % kNB);
+        // every lane acquires the producers' release of buffer b
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&S.full[b], (k / kNB) & 1, abort_));
+        if (!ok) {
+            if (lane == 0) { *abort_ = 1; set_status(p.status, SGS_E_TIMEOUT); }
+            aborted = true;
+            break;
+        }
+        const uint32_t i = k / kNChan;
+        const int c = (int)(k - i * kNChan);
+        const bool live = lane < nl && i < S.nrows[lane];
+        if (live) {
+            const uint32_t slot = x & 0xFFFFu;
+            const uint16_t *cdf = S.cdf[b][lane];
+            uint32_t s = 0;
+#pragma unroll
+            for (uint32_t st = 128; st > 0; st >>= 1)
+                if (cdf[s + st] <= slot) s += st;
+            const uint32_t lo = cdf[s];
+            const uint32_t hi = s < 255 ? cdf[s + 1] : 65536u;
+            x = (hi - lo) * (x >> 16) + slot - lo;
+            S.ctx[(lane * 4 + (i & 3)) * kNChan + c] = (uint8_t)s;
+            const uint64_t row = S.row0[lane] + i;
+            const uint64_t col = p.out_index ? (uint64_t)p.out_index[row] : row;
+            p.out[(uint64_t)c * p.n_rows + col] = dequant(s, S.step[c], S.offset[c]);
+        }
+        group_refill(gs, x, live);
+        __syncwarp();
+        if (lane == 0 && k + kNB < K) mbar_arrive(&S.empty[b]);
+    }
+    if (!aborted) {
+        const bool bad = gs.bad || (lane < nl && x != 0x10000u) || (gs.ptr != gs.n_words);
+        if (bad) set_status(p.status, SGS_E_CORRUPT);
+    }
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// One group of 32 lanes.  reload = false: the CTA's previous group was of the same scene,
+// whose model is still in shared memory (S.bad records whether it was refused).
+__device__ __forceinline__ void learned_body(const LearnedParams &p, uint32_t grp, bool reload) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     LSmem2 &S = *reinterpret_cast<LSmem2 *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t grp = blockIdx.x;
     const int nl = (int)min(32u, p.L - grp * 32);
-    if (!load_model2(S, p.bits + p.model_off, p.status)) return;
+    if (reload) {
+        if (!load_model2(S, p.bits + p.model_off, p.status)) return;
+    } else {
+        if (S.bad) return;
+        if (tid == 0) S.abort_ = 0;
+    }
     if (tid < kNChan) {
         S.step[tid] = ld_f32(p.bits + p.chan_off + 4 * tid);
         S.offset[tid] = ld_f32(p.bits + p.chan_off + 4 * (kNChan + tid));
@@ -413,56 +469,33 @@ __global__ void __launch_bounds__(kLT, 1) k_learned_decode(LearnedParams p) {
             __syncwarp();
             if (lane == 0) mbar_arrive(&S.full[b]);
         }
-        return;
+    } else {
+        consume(p, S, grp, nl, K, abort_);
     }
-    // ---------------- consumer: the 32 rANS chains
-    GroupStream gs;
-    uint32_t x = 0x10000u;
-    group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, grp, nl, lane, gs, x, S.win);
-    bool aborted = false;
-    for (uint32_t k = 0; k < K; ++k) {
-        const int b = (int)(k % kNB);
-        // every lane acquires the producers' release of buffer b
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(&S.full[b], (k / kNB) & 1, abort_));
-        if (!ok) {
-            if (lane == 0) { *abort_ = 1; set_status(p.status, SGS_E_TIMEOUT); }
-            aborted = true;
-            break;
+    // every hand-off is over: retire the barriers (a persistent CTA initialises them again)
+    __syncthreads();
+    if (tid == 0)
+        for (int b = 0; b < kNB; ++b) {
+            mbar_inval(&S.full[b]);
+            mbar_inval(&S.empty[b]);
         }
-        const uint32_t i = k / kNChan;
-        const int c = (int)(k - i * kNChan);
-        const bool live = lane < nl && i < S.nrows[lane];
-        if (live) {
-            const uint32_t slot = x & 0xFFFFu;
-            const uint16_t *cdf = S.cdf[b][lane];
-            uint32_t s = 0;
-#pragma unroll
-            for (uint32_t st = 128; st > 0; st >>= 1)
-                if (cdf[s + st] <= slot) s += st;
-            const uint32_t lo = cdf[s];
-            const uint32_t hi = s < 255 ? cdf[s + 1] : 65536u;
-            x = (hi - lo) * (x >> 16) + slot - lo;
-            S.ctx[(lane * 4 + (i & 3)) * kNChan + c] = (uint8_t)s;
-            const uint64_t row = S.row0[lane] + i;
-            const uint64_t col = p.out_index ? (uint64_t)p.out_index[row] : row;
-            p.out[(uint64_t)c * p.n_rows + col] = dequant(s, S.step[c], S.offset[c]);
-        }
-        group_refill(gs, x, live);
-        __syncwarp();
-        if (lane == 0 && k + kNB < K) mbar_arrive(&S.empty[b]);
-    }
-    if (!aborted) {
-        const bool bad = gs.bad || (lane < nl && x != 0x10000u) || (gs.ptr != gs.n_words);
-        if (bad) set_status(p.status, SGS_E_CORRUPT);
-    }
+}
+
+__global__ void __launch_bounds__(kLT, 1) k_learned_decode(LearnedParams p) { learned_body(p, blockIdx.x, true); }
+
+__global__ void __launch_bounds__(kLT, 1) k_learned_multi(MultiArgs m) {
+    run_items<LearnedParams>(m, [](const LearnedParams &p, uint32_t vb, uint32_t, bool same) {
+        learned_body(p, vb, !same);
+    });
 }
 
 size_t learned_work_bytes(const sgs_scene_info &) { return 0; }
 
-cudaError_t launch_learned_decode(const uint8_t *bits, const sgs_scene_info &info,
-                                  const sgs_scene_out &out, uint8_t *, int *status, cudaStream_t st) {
-    if (info.n_rows == 0) return cudaSuccess;
-    LearnedParams p;
+
+static uint32_t make_learned(const uint8_t *bits, const sgs_scene_info &info, const sgs_scene_out &out,
+                             int *status, LearnedParams *pp) {
+    LearnedParams &p = *pp;
+    memset(&p, 0, sizeof(p));
     p.bits = bits;
     p.model_off = info.off[S_ATTR_TAB];
     p.chan_off = info.off[S_CHAN];
@@ -475,16 +508,41 @@ cudaError_t launch_learned_decode(const uint8_t *bits, const sgs_scene_info &inf
     p.out = out.attr;
     p.out_index = out.out_index;
     p.status = status;
-    const size_t smem = sizeof(LSmem2);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_learned_decode, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    k_learned_decode<<<p.G, kLT, smem, st>>>(p);
+    return info.n_rows ? p.G : 0;
+}
+
+static cudaError_t learned_smem_limit(const void *kernel, bool *done) {
+    if (*done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LSmem2));
+    if (e == cudaSuccess) *done = true;
+    return e;
+}
+
+cudaError_t launch_learned_decode(const uint8_t *bits, const sgs_scene_info &info,
+                                  const sgs_scene_out &out, uint8_t *, int *status, cudaStream_t st) {
+    LearnedParams p;
+    const uint32_t grid = make_learned(bits, info, out, status, &p);
+    if (grid == 0) return cudaSuccess;
+    static bool set = false;
+    cudaError_t e = learned_smem_limit(reinterpret_cast<const void *>(k_learned_decode), &set);
+    if (e != cudaSuccess) return e;
+    k_learned_decode<<<grid, kLT, sizeof(LSmem2), st>>>(p);
     return cudaGetLastError();
+}
+
+uint32_t stage_learned(const SceneRef &r, void *par) {
+    if (r.info->mode != SGS_MODE_LEARNED) return 0;
+    LearnedParams p;
+    const uint32_t n = make_learned(r.bits, *r.info, *r.out, r.status, &p);
+    memcpy(par, &p, sizeof(p));
+    return n;
+}
+size_t stage_learned_bytes() { return sizeof(LearnedParams); }
+cudaError_t launch_learned_multi(const MultiArgs &m, cudaStream_t st) {
+    static bool set = false;
+    cudaError_t e = learned_smem_limit(reinterpret_cast<const void *>(k_learned_multi), &set);
+    if (e != cudaSuccess) return e;
+    return launch_persistent(k_learned_multi, kLT, sizeof(LSmem2), m, st);
 }
 
 // ------------------------------------------------------------------ encoder side

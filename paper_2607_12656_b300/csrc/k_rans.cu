@@ -10,6 +10,7 @@
 // Tables live in shared memory as cdf[257] plus a 256-bucket index on the top 8 slot bits.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "sgs_internal.h"
 #include "sgs_device.cuh"
@@ -24,13 +25,20 @@ struct TableOffsets {
     uint32_t off[kMaxTables];
 };
 
-__global__ void __launch_bounds__(256) k_tables(const uint8_t *bits, TableOffsets to,
-                                                uint8_t *tables, int n_geo_tables,
-                                                int allow_empty_attr, int *status) {
+struct TableParams {
+    const uint8_t *bits;
+    TableOffsets to;
+    uint8_t *tables;
+    int n_geo_tables, allow_empty_attr;
+    int *status;
+};
+
+__device__ __forceinline__ void tables_body(const TableParams &p, uint32_t t) {
     __shared__ uint32_t sm[8];
     __shared__ uint32_t cdf[kTabCdfWords];
-    const int s = threadIdx.x, t = blockIdx.x;
-    const uint64_t off = to.off[t];
+    const int s = threadIdx.x;
+    const uint8_t *bits = p.bits;
+    const uint64_t off = p.to.off[t];
     const uint32_t present = (bits[off + (s >> 3)] >> (s & 7)) & 1u;
     uint32_t K;
     const uint32_t rank = block_excl_scan_256(present, &K, sm);
@@ -40,12 +48,12 @@ __global__ void __launch_bounds__(256) k_tables(const uint8_t *bits, TableOffset
     cdf[s] = c;
     if (s == 0) {
         cdf[256] = tot;
-        const bool empty_ok = allow_empty_attr && t >= n_geo_tables && tot == 0;
-        if (!(tot == 65536u || empty_ok)) set_status(status, SGS_E_CORRUPT);
+        const bool empty_ok = p.allow_empty_attr && (int)t >= p.n_geo_tables && tot == 0;
+        if (!(tot == 65536u || empty_ok)) set_status(p.status, SGS_E_CORRUPT);
     }
     __syncthreads();
-    uint32_t *out_cdf = reinterpret_cast<uint32_t *>(tables + (size_t)t * kTabBytes);
-    uint8_t *out_bucket = tables + (size_t)t * kTabBytes + kTabCdfWords * 4;
+    uint32_t *out_cdf = reinterpret_cast<uint32_t *>(p.tables + (size_t)t * kTabBytes);
+    uint8_t *out_bucket = p.tables + (size_t)t * kTabBytes + kTabCdfWords * 4;
     out_cdf[s] = cdf[s];
     // cdf[256] = 2^16 always (a corrupt table was flagged above): every slot < 2^16 then
     // finds its symbol at or below 255 without a bound check in the decoders
@@ -60,12 +68,31 @@ __global__ void __launch_bounds__(256) k_tables(const uint8_t *bits, TableOffset
     out_bucket[s] = (uint8_t)lo;
 }
 
+__global__ void __launch_bounds__(256) k_tables(TableParams p) { tables_body(p, blockIdx.x); }
+
+__global__ void __launch_bounds__(256) k_tables_multi(MultiArgs m) {
+    run_items<TableParams>(m, [](const TableParams &p, uint32_t vb, uint32_t, bool) { tables_body(p, vb); });
+}
+
+static uint32_t make_tables(const uint8_t *bits, const sgs_scene_info &info, int n_geo_tables,
+                            uint8_t *tables, int *status, TableParams *pp) {
+    TableParams &p = *pp;
+    memset(&p, 0, sizeof(p));
+    p.bits = bits;
+    for (uint32_t i = 0; i < info.n_tables; ++i) p.to.off[i] = info.table_off[i];
+    p.tables = tables;
+    p.n_geo_tables = n_geo_tables;
+    p.allow_empty_attr = info.n_rows == 0;
+    p.status = status;
+    return info.n_tables;
+}
+
 cudaError_t launch_tables(const uint8_t *bits, const sgs_scene_info &info, int n_geo_tables,
                           uint8_t *tables, int *status, cudaStream_t st) {
-    if (info.n_tables == 0) return cudaSuccess;
-    TableOffsets to;
-    for (uint32_t i = 0; i < info.n_tables; ++i) to.off[i] = info.table_off[i];
-    k_tables<<<info.n_tables, 256, 0, st>>>(bits, to, tables, n_geo_tables, info.n_rows == 0, status);
+    TableParams p;
+    const uint32_t grid = make_tables(bits, info, n_geo_tables, tables, status, &p);
+    if (grid == 0) return cudaSuccess;
+    k_tables<<<grid, 256, 0, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -88,21 +115,23 @@ constexpr size_t kAttrSmem = kAttrTabSmem + kAttrWarps * kWinWords * 2;
 static_assert(kAttrTabSmem % 16 == 0, "window must be 16-byte aligned");
 
 template <bool IDX>
-__global__ void __launch_bounds__(32 * kAttrWarps) k_rans_attr(AttrParams p) {
+__device__ __forceinline__ void rans_attr_body(const AttrParams &p, uint32_t vb, bool reload) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *s_cdf = (uint32_t *)smem;                          // [56][257]
     uint8_t *s_bucket = smem + kNChan * kTabCdfWords * 4;         // [56][256]
     float *s_step = (float *)(s_bucket + kNChan * 256);           // [56]
     float *s_off = s_step + kNChan;                               // [56]
     uint16_t *s_win = reinterpret_cast<uint16_t *>(smem + kAttrTabSmem) + (threadIdx.x >> 5) * kWinWords;
-    load_tables_smem(p.tables, kNChan, s_cdf, s_bucket);
-    if (threadIdx.x < kNChan) {
-        s_step[threadIdx.x] = ld_f32(p.bits + p.chan_off + 4 * threadIdx.x);
-        s_off[threadIdx.x] = ld_f32(p.bits + p.chan_off + 4 * (kNChan + threadIdx.x));
+    if (reload) {  // (a CTA's next item of the same scene finds the tables in place)
+        load_tables_smem(p.tables, kNChan, s_cdf, s_bucket);
+        if (threadIdx.x < kNChan) {
+            s_step[threadIdx.x] = ld_f32(p.bits + p.chan_off + 4 * threadIdx.x);
+            s_off[threadIdx.x] = ld_f32(p.bits + p.chan_off + 4 * (kNChan + threadIdx.x));
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const int lane = threadIdx.x & 31;
-    const uint32_t g = blockIdx.x * kAttrWarps + (threadIdx.x >> 5);
+    const uint32_t g = vb * kAttrWarps + (threadIdx.x >> 5);
     if (g >= p.G) return;
     // the group's rows, dealt round robin to its lanes: lane j holds rows R0 + j + k nl
     const uint32_t nl = min(32u, p.L - g * 32);
@@ -154,11 +183,20 @@ __global__ void __launch_bounds__(32 * kAttrWarps) k_rans_attr(AttrParams p) {
     if (bad) set_status(p.status, SGS_E_CORRUPT);
 }
 
-cudaError_t launch_rans_static_attr(const uint8_t *bits, const sgs_scene_info &info,
-                                    const uint8_t *tables, const sgs_scene_out &out, int *status,
-                                    cudaStream_t st) {
-    if (info.n_rows == 0) return cudaSuccess;
-    AttrParams p;
+template <bool IDX>
+__global__ void __launch_bounds__(32 * kAttrWarps) k_rans_attr(AttrParams p) { rans_attr_body<IDX>(p, blockIdx.x, true); }
+
+template <bool IDX>
+__global__ void __launch_bounds__(32 * kAttrWarps) k_rans_attr_multi(MultiArgs m) {
+    run_items<AttrParams>(m, [](const AttrParams &p, uint32_t vb, uint32_t, bool same) {
+        rans_attr_body<IDX>(p, vb, !same);
+    });
+}
+
+static uint32_t make_rans_attr(const uint8_t *bits, const sgs_scene_info &info, const uint8_t *tables,
+                               const sgs_scene_out &out, int *status, AttrParams *pp) {
+    AttrParams &p = *pp;
+    memset(&p, 0, sizeof(p));
     p.bits = bits;
     p.tables = tables;
     p.chan_off = info.off[S_CHAN];
@@ -171,17 +209,29 @@ cudaError_t launch_rans_static_attr(const uint8_t *bits, const sgs_scene_info &i
     p.out = out.attr;
     p.out_index = out.out_index;
     p.status = status;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_rans_attr<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kAttrSmem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_rans_attr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kAttrSmem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    const unsigned grid = (p.G + kAttrWarps - 1) / kAttrWarps;
+    if (info.n_rows == 0) return 0;
+    return (p.G + kAttrWarps - 1) / kAttrWarps;
+}
+
+// Raises the dynamic shared memory limit of `kernel` once.
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t bytes, bool *done) {
+    if (*done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) *done = true;
+    return e;
+}
+
+cudaError_t launch_rans_static_attr(const uint8_t *bits, const sgs_scene_info &info,
+                                    const uint8_t *tables, const sgs_scene_out &out, int *status,
+                                    cudaStream_t st) {
+    AttrParams p;
+    const uint32_t grid = make_rans_attr(bits, info, tables, out, status, &p);
+    if (grid == 0) return cudaSuccess;
+    static bool set0 = false, set1 = false;
+    cudaError_t e = allow_smem(k_rans_attr<false>, kAttrSmem, &set0);
+    if (e == cudaSuccess) e = allow_smem(k_rans_attr<true>, kAttrSmem, &set1);
+    if (e != cudaSuccess) return e;
     if (p.out_index) k_rans_attr<true><<<grid, 32 * kAttrWarps, kAttrSmem, st>>>(p);
     else k_rans_attr<false><<<grid, 32 * kAttrWarps, kAttrSmem, st>>>(p);
     return cudaGetLastError();
@@ -204,7 +254,7 @@ constexpr int kGeoWarps = 8;
 constexpr size_t kGeoTabSmem = (SGS_MAX_DEPTH * (kTabCdfWords * 4 + 256) + 15) & ~size_t(15);
 static_assert(kGeoTabSmem % 16 == 0, "window must be 16-byte aligned");
 
-__global__ void __launch_bounds__(32 * kGeoWarps) k_rans_geo(GeoParams p) {
+__device__ __forceinline__ void rans_geo_body(const GeoParams &p, uint32_t vb) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int nt = p.plan.n_coded_levels;
     uint32_t *s_cdf = (uint32_t *)smem;
@@ -219,7 +269,7 @@ __global__ void __launch_bounds__(32 * kGeoWarps) k_rans_geo(GeoParams p) {
                                           p.plan.coded_start[threadIdx.x]);
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const uint32_t g = blockIdx.x * kGeoWarps + (threadIdx.x >> 5);
+    const uint32_t g = vb * kGeoWarps + (threadIdx.x >> 5);
     if (g >= p.G) return;
     // the group's tokens, dealt round robin to its lanes: lane j holds tokens I0 + j + k nl
     const int nl = (int)min(32u, p.L - g * 32);
@@ -266,11 +316,18 @@ __global__ void __launch_bounds__(32 * kGeoWarps) k_rans_geo(GeoParams p) {
     if (bad) set_status(p.status, SGS_E_CORRUPT);
 }
 
-cudaError_t launch_rans_static_geo(const uint8_t *bits, const sgs_scene_info &info,
-                                   const GeoPlan &plan, const uint8_t *tables, uint8_t *geo_bytes,
-                                   int *status, cudaStream_t st) {
-    if (info.n_geo_coded == 0) return cudaSuccess;
-    GeoParams p;
+constexpr size_t kGeoSmem = kGeoTabSmem + kGeoWarps * kWinWords * 2;
+
+__global__ void __launch_bounds__(32 * kGeoWarps) k_rans_geo(GeoParams p) { rans_geo_body(p, blockIdx.x); }
+
+__global__ void __launch_bounds__(32 * kGeoWarps) k_rans_geo_multi(MultiArgs m) {
+    run_items<GeoParams>(m, [](const GeoParams &p, uint32_t vb, uint32_t, bool) { rans_geo_body(p, vb); });
+}
+
+static uint32_t make_rans_geo(const uint8_t *bits, const sgs_scene_info &info, const GeoPlan &plan,
+                              const uint8_t *tables, uint8_t *geo_bytes, int *status, GeoParams *pp) {
+    GeoParams &p = *pp;
+    memset(&p, 0, sizeof(p));
     p.bits = bits;
     p.tables = tables;
     p.grp_sec = info.off[S_GEO_GRP];
@@ -282,16 +339,20 @@ cudaError_t launch_rans_static_geo(const uint8_t *bits, const sgs_scene_info &in
     p.plan = plan;
     p.geo_bytes = geo_bytes;
     p.status = status;
-    const size_t smem = kGeoTabSmem + kGeoWarps * kWinWords * 2;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_rans_geo, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    const unsigned grid = (p.G + kGeoWarps - 1) / kGeoWarps;
-    k_rans_geo<<<grid, 32 * kGeoWarps, smem, st>>>(p);
+    if (info.n_geo_coded == 0) return 0;
+    return (p.G + kGeoWarps - 1) / kGeoWarps;
+}
+
+cudaError_t launch_rans_static_geo(const uint8_t *bits, const sgs_scene_info &info,
+                                   const GeoPlan &plan, const uint8_t *tables, uint8_t *geo_bytes,
+                                   int *status, cudaStream_t st) {
+    GeoParams p;
+    const uint32_t grid = make_rans_geo(bits, info, plan, tables, geo_bytes, status, &p);
+    if (grid == 0) return cudaSuccess;
+    static bool set = false;
+    cudaError_t e = allow_smem(k_rans_geo, kGeoSmem, &set);
+    if (e != cudaSuccess) return e;
+    k_rans_geo<<<grid, 32 * kGeoWarps, kGeoSmem, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -303,19 +364,35 @@ struct RawCopy {
     uint64_t dst[SGS_MAX_DEPTH];
 };
 
-__global__ void k_geo_copy_raw(const uint8_t *raw, RawCopy rc, uint8_t *geo_bytes) {
-    const uint64_t total = rc.src[rc.n];
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
-         i += (uint64_t)gridDim.x * blockDim.x) {
+struct CopyParams {
+    const uint8_t *raw;
+    RawCopy rc;
+    uint8_t *geo_bytes;
+};
+
+constexpr uint32_t kCopyBytes = 256 * 16;  // bytes one CTA copies
+
+__device__ __forceinline__ void geo_copy_body(const CopyParams &p, uint32_t vb) {
+    const uint64_t total = p.rc.src[p.rc.n];
+    const uint64_t end = min(total, (uint64_t)(vb + 1) * kCopyBytes);
+    for (uint64_t i = (uint64_t)vb * kCopyBytes + threadIdx.x; i < end; i += 256) {
         int k = 0;
-        while (k + 1 < rc.n && rc.src[k + 1] <= i) ++k;
-        geo_bytes[rc.dst[k] + (i - rc.src[k])] = raw[i];
+        while (k + 1 < p.rc.n && p.rc.src[k + 1] <= i) ++k;
+        p.geo_bytes[p.rc.dst[k] + (i - p.rc.src[k])] = p.raw[i];
     }
 }
 
-cudaError_t launch_geo_copy_raw(const uint8_t *bits, const sgs_scene_info &info,
-                                const GeoPlan &plan, uint8_t *geo_bytes, cudaStream_t st) {
-    RawCopy rc;
+__global__ void __launch_bounds__(256) k_geo_copy_raw(CopyParams p) { geo_copy_body(p, blockIdx.x); }
+
+__global__ void __launch_bounds__(256) k_geo_copy_multi(MultiArgs m) {
+    run_items<CopyParams>(m, [](const CopyParams &p, uint32_t vb, uint32_t, bool) { geo_copy_body(p, vb); });
+}
+
+static uint32_t make_geo_copy(const uint8_t *bits, const sgs_scene_info &info, const GeoPlan &plan,
+                              uint8_t *geo_bytes, CopyParams *pp) {
+    CopyParams &p = *pp;
+    memset(&p, 0, sizeof(p));
+    RawCopy &rc = p.rc;
     rc.n = 0;
     rc.src[0] = 0;
     for (int l = 0; l < plan.depth; ++l) {
@@ -326,12 +403,78 @@ cudaError_t launch_geo_copy_raw(const uint8_t *bits, const sgs_scene_info &info,
         rc.src[rc.n + 1] = rc.src[rc.n] + plan.n_level[l];
         ++rc.n;
     }
-    if (rc.n == 0 || rc.src[rc.n] == 0) return cudaSuccess;
-    const uint64_t total = rc.src[rc.n];
-    const uint64_t want = (total + 255) / 256;
-    const unsigned grid = (unsigned)(want < 4096 ? want : 4096);
-    k_geo_copy_raw<<<grid, 256, 0, st>>>(bits + info.off[S_GEO_RAW], rc, geo_bytes);
+    p.raw = bits + info.off[S_GEO_RAW];
+    p.geo_bytes = geo_bytes;
+    if (info.geo_mode != SGS_GEO_RANS || info.n_geo == 0 || rc.n == 0 || rc.src[rc.n] == 0) return 0;
+    return (uint32_t)((rc.src[rc.n] + kCopyBytes - 1) / kCopyBytes);
+}
+
+cudaError_t launch_geo_copy_raw(const uint8_t *bits, const sgs_scene_info &info,
+                                const GeoPlan &plan, uint8_t *geo_bytes, cudaStream_t st) {
+    CopyParams p;
+    const uint32_t grid = make_geo_copy(bits, info, plan, geo_bytes, &p);
+    if (grid == 0) return cudaSuccess;
+    k_geo_copy_raw<<<grid, 256, 0, st>>>(p);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ batched stages
+
+uint32_t stage_tables(const SceneRef &r, void *par) {
+    TableParams p;
+    const uint32_t n = make_tables(r.bits, *r.info, r.plan->n_coded_levels, r.s->tables, r.status, &p);
+    memcpy(par, &p, sizeof(p));
+    return n;
+}
+size_t stage_tables_bytes() { return sizeof(TableParams); }
+cudaError_t launch_tables_multi(const MultiArgs &m, cudaStream_t st) {
+    return launch_persistent(k_tables_multi, 256, 0, m, st);
+}
+
+uint32_t stage_rans_attr(const SceneRef &r, bool idx_variant, void *par) {
+    if (r.info->mode != SGS_MODE_STATIC || (r.out->out_index != nullptr) != idx_variant) return 0;
+    AttrParams p;
+    const uint8_t *attr_tables = r.s->tables + (size_t)r.plan->n_coded_levels * kTabBytes;
+    const uint32_t n = make_rans_attr(r.bits, *r.info, attr_tables, *r.out, r.status, &p);
+    memcpy(par, &p, sizeof(p));
+    return n;
+}
+size_t stage_rans_attr_bytes() { return sizeof(AttrParams); }
+cudaError_t launch_rans_attr_multi(bool idx, const MultiArgs &m, cudaStream_t st) {
+    static bool set0 = false, set1 = false;
+    if (idx) {
+        cudaError_t e = allow_smem(k_rans_attr_multi<true>, kAttrSmem, &set1);
+        if (e != cudaSuccess) return e;
+        return launch_persistent(k_rans_attr_multi<true>, 32 * kAttrWarps, kAttrSmem, m, st);
+    }
+    cudaError_t e = allow_smem(k_rans_attr_multi<false>, kAttrSmem, &set0);
+    if (e != cudaSuccess) return e;
+    return launch_persistent(k_rans_attr_multi<false>, 32 * kAttrWarps, kAttrSmem, m, st);
+}
+
+uint32_t stage_rans_geo(const SceneRef &r, void *par) {
+    GeoParams p;
+    const uint32_t n = make_rans_geo(r.bits, *r.info, *r.plan, r.s->tables, r.s->geo_bytes, r.status, &p);
+    memcpy(par, &p, sizeof(p));
+    return n;
+}
+size_t stage_rans_geo_bytes() { return sizeof(GeoParams); }
+cudaError_t launch_rans_geo_multi(const MultiArgs &m, cudaStream_t st) {
+    static bool set = false;
+    cudaError_t e = allow_smem(k_rans_geo_multi, kGeoSmem, &set);
+    if (e != cudaSuccess) return e;
+    return launch_persistent(k_rans_geo_multi, 32 * kGeoWarps, kGeoSmem, m, st);
+}
+
+uint32_t stage_geo_copy(const SceneRef &r, void *par) {
+    CopyParams p;
+    const uint32_t n = make_geo_copy(r.bits, *r.info, *r.plan, r.s->geo_bytes, &p);
+    memcpy(par, &p, sizeof(p));
+    return n;
+}
+size_t stage_geo_copy_bytes() { return sizeof(CopyParams); }
+cudaError_t launch_geo_copy_multi(const MultiArgs &m, cudaStream_t st) {
+    return launch_persistent(k_geo_copy_multi, 256, 0, m, st);
 }
 
 }  // namespace sgs

@@ -87,14 +87,12 @@ extern "C" int scene_decode_noalloc(const uint8_t *bits, const sgs_scene_info *i
         default: e = launch_learned_decode(bits, *info, *out, s.learned, status, st); break;
     }
     if (e != cudaSuccess) return SGS_E_CUDA;
-    const uint8_t *B = bits + info->off[S_GEO_RAW];
     if (info->geo_mode == SGS_GEO_RANS && info->n_geo) {
         if (launch_geo_copy_raw(bits, *info, plan, s.geo_bytes, st) != cudaSuccess) return SGS_E_CUDA;
         if (launch_rans_static_geo(bits, *info, plan, s.tables, s.geo_bytes, status, st) != cudaSuccess)
             return SGS_E_CUDA;
-        B = s.geo_bytes;
     }
-    if (launch_octree(B, *info, plan, bits, s, *out, status, st, st, nullptr, nullptr) != cudaSuccess)
+    if (launch_octree(*info, plan, bits, s, *out, status, st, st, nullptr, nullptr) != cudaSuccess)
         return SGS_E_CUDA;
     int host_status = SGS_OK;
     if (cudaMemcpyAsync(&host_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)

@@ -1,0 +1,26 @@
+// The decode context (internal): scratch, status word, streams and events of the decode
+// pipeline.  Shared by the single-scene and batched decode entry points.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sgs.h"
+
+constexpr int kMaxStages = 8;
+
+struct sgs_ctx {
+    int device;
+    uint8_t *scratch;
+    size_t scratch_bytes;
+    int *status_dev;
+    int *status_host;  // pinned
+    uint64_t launches; // kernels launched by decode calls on this context
+    int profile;       // record stage events in decode calls
+    int n_marks;
+    cudaEvent_t marks[kMaxStages + 1];  // caller's stream: start, tokens, octree, end
+    cudaEvent_t amarks[2];              // attribute stream: start, end
+    cudaStream_t aux;                   // attribute decode (lowest priority), forked from the caller
+    cudaStream_t geo;                   // geometry chain (highest priority)
+    cudaStream_t aux2;                  // octree top levels (highest priority), beside the scan
+    cudaEvent_t fork, join, gjoin, top_fork, top_join;
+};

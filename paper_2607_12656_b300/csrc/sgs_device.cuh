@@ -152,4 +152,44 @@ __device__ __forceinline__ void group_refill(GroupStream &gs, uint32_t &x, bool 
     gs.ptr += __popc(mask);
 }
 
+// ------------------------------------------------------------------ batched stages
+
+// Persistent loop: each CTA claims items in increasing order with an atomic counter, finds
+// the owning scene by binary search, copies its parameters to shared memory and runs
+// body(params, item within the scene, items of the scene, same), where `same` says that this
+// CTA's previous item belonged to the same scene (shared-memory state the body derived from
+// the scene's parameters is still there).
+template <typename P, typename Body>
+__device__ __forceinline__ void run_items(const MultiArgs &m, Body body) {
+    __shared__ uint32_t s_item;
+    __shared__ int s_scene;
+    __shared__ __align__(16) uint8_t s_par[(sizeof(P) + 15) & ~size_t(15)];
+    int prev = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t item = atomicAdd(m.counter, 1u);
+            int lo = 0, hi = m.n - 1;  // last scene whose first item <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (m.prefix[mid] <= item) lo = mid; else hi = mid - 1;
+            }
+            s_item = item;
+            s_scene = lo;
+        }
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= m.total) break;
+        const int sc = s_scene;
+        const bool same = sc == prev;
+        prev = sc;
+        const uint4 *src = reinterpret_cast<const uint4 *>(m.params + (size_t)sc * m.stride);
+        uint4 *dst = reinterpret_cast<uint4 *>(s_par);
+        if (!same)
+            for (uint32_t i = threadIdx.x; i < sizeof(s_par) / 16; i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+        body(*reinterpret_cast<const P *>(s_par), item - m.prefix[sc], m.prefix[sc + 1] - m.prefix[sc], same);
+        __syncthreads();
+    }
+}
+
 }  // namespace sgs

@@ -61,6 +61,7 @@ struct Scratch {
 };
 
 size_t scratch_need(const sgs_scene_info &info, Scratch *layout, uint8_t *base);
+size_t octree_scan_tiles(uint64_t n_geo);
 
 // Device status: kernels record the most severe error with atomicMin (codes are negative).
 __device__ __forceinline__ void set_status(int *status, int code) {
@@ -78,9 +79,10 @@ cudaError_t launch_rans_static_geo(const uint8_t *bits, const sgs_scene_info &in
                                    int *status, cudaStream_t st);
 cudaError_t launch_geo_copy_raw(const uint8_t *bits, const sgs_scene_info &info,
                                 const GeoPlan &plan, uint8_t *geo_bytes, cudaStream_t st);
-// The top levels run on st2 (forked from st with ev_a, joined with ev_b) concurrently with
-// the popcount scan; pass st2 == st to run everything on one stream.
-cudaError_t launch_octree(const uint8_t *geo, const sgs_scene_info &info, const GeoPlan &plan,
+// The octree reads the raw token section, or the scratch copy of the geometry decoder when
+// levels are rANS-coded.  The top levels run on st2 (forked from st with ev_a, joined with
+// ev_b) concurrently with the popcount scan; pass st2 == st to run everything on one stream.
+cudaError_t launch_octree(const sgs_scene_info &info, const GeoPlan &plan,
                           const uint8_t *bits, const Scratch &s, const sgs_scene_out &out,
                           int *status, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_a,
                           cudaEvent_t ev_b);
@@ -97,5 +99,79 @@ cudaError_t launch_learned_fc(const uint8_t *model_dev, const uint8_t *tokens_de
                               uint32_t *cum_dev, cudaStream_t st);
 
 void make_geo_plan(const sgs_scene_info &info, GeoPlan *plan);
+
+// ------------------------------------------------------------------ batched stages
+// A batched decode runs each pipeline stage of many scenes as one persistent launch: CTAs
+// claim work items (the single-scene kernel's CTAs, "virtual blocks") in increasing order
+// from an atomic counter and look up the owning scene.  Scene s of a stage owns items
+// [prefix[s], prefix[s+1]) and the parameter block at params + s * stride.
+struct MultiArgs {
+    const uint8_t *params;
+    uint32_t stride;          // multiple of 16
+    const uint32_t *prefix;   // n + 1 entries, strictly increasing
+    int n;
+    uint32_t total;           // prefix[n]
+    uint32_t *counter;        // zero before the launch
+};
+
+// One scene as the stage builders see it (device pointers; the scratch already carved).
+struct SceneRef {
+    const uint8_t *bits;
+    const sgs_scene_info *info;
+    const sgs_scene_out *out;
+    const Scratch *s;
+    const GeoPlan *plan;
+    int *status;
+};
+
+// CTAs of `kernel` resident on the whole current device (cached per kernel and device).
+int resident_ctas(const void *kernel, int threads, size_t smem);
+
+// Launches a persistent grid (at most one wave of resident CTAs).  With m.total = 0 it only
+// fills the occupancy cache.
+template <typename K>
+cudaError_t launch_persistent(K kernel, int threads, size_t smem, const MultiArgs &m, cudaStream_t st) {
+    const int r = resident_ctas(reinterpret_cast<const void *>(kernel), threads, smem);
+    if (r <= 0) return cudaErrorInvalidConfiguration;
+    if (m.total == 0) return cudaSuccess;
+    const unsigned grid = m.total < (uint32_t)r ? m.total : (unsigned)r;
+    kernel<<<grid, threads, smem, st>>>(m);
+    return cudaGetLastError();
+}
+
+// Stage builders: write one scene's parameter block to `par` (at most the stage's
+// *_bytes()) and return its items, 0 when the scene has no work in the stage.
+uint32_t stage_fixed(const SceneRef &r, bool vec_variant, void *par);
+size_t stage_fixed_bytes();
+cudaError_t launch_fixed_multi(bool vec, const MultiArgs &m, cudaStream_t st);
+uint32_t stage_tables(const SceneRef &r, void *par);
+size_t stage_tables_bytes();
+cudaError_t launch_tables_multi(const MultiArgs &m, cudaStream_t st);
+uint32_t stage_rans_attr(const SceneRef &r, bool idx_variant, void *par);
+size_t stage_rans_attr_bytes();
+cudaError_t launch_rans_attr_multi(bool idx, const MultiArgs &m, cudaStream_t st);
+uint32_t stage_rans_geo(const SceneRef &r, void *par);
+size_t stage_rans_geo_bytes();
+cudaError_t launch_rans_geo_multi(const MultiArgs &m, cudaStream_t st);
+uint32_t stage_geo_copy(const SceneRef &r, void *par);
+size_t stage_geo_copy_bytes();
+cudaError_t launch_geo_copy_multi(const MultiArgs &m, cudaStream_t st);
+uint32_t stage_learned(const SceneRef &r, void *par);
+size_t stage_learned_bytes();
+cudaError_t launch_learned_multi(const MultiArgs &m, cudaStream_t st);
+// octree: duplicates, popcount scan, top levels, then expansion group k (k = 0, 1, ...)
+uint32_t stage_dup(const SceneRef &r, void *par);
+size_t stage_dup_bytes();
+cudaError_t launch_dup_multi(const MultiArgs &m, cudaStream_t st);
+uint32_t stage_scan(const SceneRef &r, void *par);
+size_t stage_scan_bytes();
+cudaError_t launch_scan_multi(const MultiArgs &m, cudaStream_t st);
+uint32_t stage_top(const SceneRef &r, void *par);
+size_t stage_top_bytes();
+cudaError_t launch_top_multi(const MultiArgs &m, cudaStream_t st);
+uint32_t stage_expand(const SceneRef &r, int group, void *par);
+size_t stage_expand_bytes();
+cudaError_t launch_expand_multi(const MultiArgs &m, cudaStream_t st);
+int octree_group_count(const sgs_scene_info &info, const GeoPlan &plan);
 
 }  // namespace sgs

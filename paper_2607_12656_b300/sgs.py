@@ -74,6 +74,12 @@ def lib() -> ctypes.CDLL:
         L.scene_query.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(SceneInfo)]
         L.scene_decode.argtypes = [P, P, ctypes.POINTER(SceneInfo), ctypes.POINTER(SceneOut), P]
         L.scene_decode_batch.argtypes = [P, ctypes.POINTER(BatchItem), i32, P]
+        L.scene_batch_bytes.argtypes = [ctypes.POINTER(BatchItem), i32, ctypes.POINTER(ctypes.c_size_t)]
+        L.scene_batch_plan.argtypes = [P, ctypes.POINTER(BatchItem), i32, ctypes.POINTER(P)]
+        L.scene_batch_run.argtypes = [P, P, P]
+        L.scene_batch_status.argtypes = [P, ctypes.POINTER(i32), i32]
+        L.scene_batch_free.argtypes = [P]
+        L.scene_batch_free.restype = None
         L.scene_encode.argtypes = [P, P, P, u32, ctypes.POINTER(EncodeParams), P, ctypes.c_size_t,
                                    ctypes.POINTER(ctypes.c_size_t)]
         L.scene_tokens.argtypes = [P, P, u32, u32, P, ctypes.c_size_t, ctypes.POINTER(u32)]
@@ -207,8 +213,8 @@ def scene_decode_noalloc(bits_dev, info: SceneInfo, attr, pos, coord=None, out_i
     return code
 
 
-def scene_decode_batch(ctx: Context, items: list, stream=None) -> None:
-    """items: (bits_dev, info, attr, pos[, coord[, out_index]]) tuples."""
+def _batch_items(items: list):
+    """items: (bits_dev, info, attr, pos[, coord[, out_index]]) tuples -> a BatchItem array."""
     arr = (BatchItem * max(len(items), 1))()
     for i, it in enumerate(items):
         bits_dev, info, attr, pos = it[:4]
@@ -217,7 +223,53 @@ def scene_decode_batch(ctx: Context, items: list, stream=None) -> None:
         arr[i].bits_dev = _ptr(bits_dev)
         arr[i].info = info
         arr[i].out = _out(attr, pos, coord, oidx)
-    _check(lib().scene_decode_batch(ctx.handle, arr, len(items), _stream(stream)), "scene_decode_batch")
+    return arr
+
+
+def scene_batch_bytes(items: list) -> int:
+    """Device bytes of a batch plan (every scene's scratch plus the work lists)."""
+    n = ctypes.c_size_t(0)
+    _check(lib().scene_batch_bytes(_batch_items(items), len(items), ctypes.byref(n)), "scene_batch_bytes")
+    return n.value
+
+
+def scene_decode_batch(ctx: Context, items: list, stream=None) -> None:
+    """One-shot batched decode in the context's scratch (needs scene_batch_bytes(items))."""
+    _check(lib().scene_decode_batch(ctx.handle, _batch_items(items), len(items), _stream(stream)),
+           "scene_decode_batch")
+
+
+class BatchPlan:
+    """A batched decode plan: binds the items' buffers; run() enqueues one decode of all of
+    them (no allocation, no host wait: capturable in a CUDA graph)."""
+
+    def __init__(self, ctx: Context, items: list):
+        h = P()
+        _check(lib().scene_batch_plan(ctx.handle, _batch_items(items), len(items), ctypes.byref(h)),
+               "scene_batch_plan")
+        self.handle = h
+        self.ctx = ctx
+        self.n = len(items)
+        self.items = items  # keep the bound buffers alive
+
+    def run(self, stream=None) -> None:
+        _check(lib().scene_batch_run(self.ctx.handle, self.handle, _stream(stream)), "scene_batch_run")
+
+    def status(self) -> list[int]:
+        arr = (i32 * max(self.n, 1))()
+        _check(lib().scene_batch_status(self.handle, arr, self.n), "scene_batch_status")
+        return list(arr[:self.n])
+
+    def close(self) -> None:
+        if self.handle:
+            lib().scene_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ----------------------------------------------------------------------------- encode
@@ -241,14 +293,17 @@ def scene_encode(pos: np.ndarray, attr: np.ndarray, *, mode: int, depth: int, la
         prm.model = mbuf.ctypes.data
     need = ctypes.c_size_t(0)
     h = ctx.handle if ctx is not None else None
-    code = lib().scene_encode(h, pos.ctypes.data, attr.ctypes.data, n, ctypes.byref(prm), None, 0,
-                              ctypes.byref(need))
-    if code not in (OK, E_INVALID) or need.value == 0:
-        _check(code, "scene_encode")
-    out = np.zeros(need.value, np.uint8)
-    _check(lib().scene_encode(h, pos.ctypes.data, attr.ctypes.data, n, ctypes.byref(prm),
-                              out.ctypes.data, out.size, ctypes.byref(need)), "scene_encode")
-    return out.tobytes()
+    # one pass in the common case: room for 2 bytes per token plus tables and headers
+    cap = (1 << 20) + n * (2 * NCHAN + 16) + 64 * (lanes + geo_lanes)
+    out = np.empty(cap, np.uint8)
+    code = lib().scene_encode(h, pos.ctypes.data, attr.ctypes.data, n, ctypes.byref(prm), out.ctypes.data,
+                              out.size, ctypes.byref(need))
+    if code == E_INVALID and need.value > cap:
+        out = np.empty(need.value, np.uint8)
+        code = lib().scene_encode(h, pos.ctypes.data, attr.ctypes.data, n, ctypes.byref(prm),
+                                  out.ctypes.data, out.size, ctypes.byref(need))
+    _check(code, "scene_encode")
+    return out[: need.value].tobytes()
 
 
 def scene_tokens(pos: np.ndarray, attr: np.ndarray, depth: int) -> np.ndarray:

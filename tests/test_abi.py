@@ -110,3 +110,29 @@ def test_freeze_matches_oracle(small_scene):
         want = S.model_bytes(M.freeze(w, q, S.lane_bounds(P.n_rows, lanes), seed))
         got = sgs.sgs_freeze(sgs.pack_weights(w), q, lanes, seed)
         assert got == want
+
+
+def test_batch_bytes_host_side(small_scene):
+    """scene_batch_bytes lays a batch out on the host only: it covers every scene's scratch,
+    grows with the batch, and refuses infos that scene_query did not produce or misaligned
+    bitstreams (the pointers are never dereferenced here)."""
+    bufs = [S.encode(small_scene.pos, small_scene.attr, mode=m, depth=12, lanes=64, bits=8)
+            for m in (S.MODE_FIXED, S.MODE_STATIC)]
+    infos = [sgs.scene_query(b) for b in bufs]
+    fake = 1 << 24  # 16-byte aligned stand-ins for device addresses
+
+    def items(k):
+        return [(fake, infos[j % 2], fake, fake) for j in range(k)]
+
+    one, four = sgs.scene_batch_bytes(items(1)), sgs.scene_batch_bytes(items(4))
+    assert one >= (infos[0].scratch_bytes + 255) // 256 * 256
+    assert four > 2 * one
+    assert sgs.scene_batch_bytes([]) >= 0
+    bad = sgs.SceneInfo.from_buffer_copy(infos[0])
+    bad.scratch_bytes += 16
+    with pytest.raises(sgs.SgsError) as e:
+        sgs.scene_batch_bytes([(fake, bad, fake, fake)])
+    assert e.value.code == sgs.E_INVALID
+    with pytest.raises(sgs.SgsError) as e:
+        sgs.scene_batch_bytes([(fake + 8, infos[0], fake, fake)])
+    assert e.value.code == sgs.E_INVALID

@@ -51,21 +51,116 @@ def test_pool_alone_matches_oracle(ctx, pool):
         assert st == sgs.OK and same_bits(attr, P.attr) and same_bits(pos, P.pos)
 
 
-def test_batch_decode_matches_alone(pool):
-    infos = [sgs.scene_query(b) for b, _ in pool]
-    need = sum((i.scratch_bytes + 255) // 256 * 256 for i in infos)
-    c = sgs.Context(0, need)
-    items, outs = [], []
-    for (buf, P), info in zip(pool, infos):
+def _batch_items(pool, with_index=()):
+    """Device buffers for every pool scene; scenes listed in with_index also get coordinates
+    and a permuted out_index (the scatter variants of every stage)."""
+    items, refs = [], []
+    for j, (buf, P) in enumerate(pool):
+        info = sgs.scene_query(buf)
+        n = info.n_rows
         bits = torch.frombuffer(bytearray(buf), dtype=torch.uint8).cuda()
-        attr = torch.full((56, info.n_rows), float("nan"), device="cuda")
-        pos = torch.full((3, info.n_rows), float("nan"), device="cuda")
-        items.append((bits, info, attr, pos))
-        outs.append((attr, pos, P))
+        attr = torch.full((56, n), float("nan"), device="cuda")
+        pos = torch.full((3, n), float("nan"), device="cuda")
+        if j in with_index:
+            perm = np.random.default_rng(j).permutation(n).astype(np.int32)
+            crd = torch.full((3, n), -1, dtype=torch.int32, device="cuda")
+            items.append((bits, info, attr, pos, crd, torch.from_numpy(perm).cuda()))
+            refs.append((P, perm))
+        else:
+            items.append((bits, info, attr, pos))
+            refs.append((P, None))
+    return items, refs
+
+
+def _check_outputs(items, refs, skip=()):
+    for j, (it, (P, perm)) in enumerate(zip(items, refs)):
+        if j in skip:
+            continue
+        attr, pos = it[2].cpu().numpy(), it[3].cpu().numpy()
+        if perm is None:
+            assert same_bits(attr, P.attr) and same_bits(pos, P.pos), j
+        else:
+            assert same_bits(attr[:, perm], P.attr) and same_bits(pos[:, perm], P.pos), j
+            assert np.array_equal(it[4].cpu().numpy()[:, perm].view(np.uint32), P.coord), j
+
+
+def _reset(items):
+    for it in items:
+        it[2].fill_(float("nan"))
+        it[3].fill_(float("nan"))
+
+
+def test_batch_decode_matches_alone(pool):
+    items, refs = _batch_items(pool)
+    need = sgs.scene_batch_bytes(items)
+    assert need >= sum((it[1].scratch_bytes + 255) // 256 * 256 for it in items)
+    c = sgs.Context(0, need)
     sgs.scene_decode_batch(c, items)
     assert c.sync() == sgs.OK
-    for attr, pos, P in outs:
-        assert same_bits(attr.cpu().numpy(), P.attr) and same_bits(pos.cpu().numpy(), P.pos)
+    _check_outputs(items, refs)
+    # a smaller scratch is refused before anything runs
+    c2 = sgs.Context(0, need - 256)
+    with pytest.raises(sgs.SgsError) as e:
+        sgs.scene_decode_batch(c2, items)
+    assert e.value.code == sgs.E_NOMEM
+    c2.close()
+    c.close()
+
+
+def test_batch_plan_runs_again_and_replays_in_a_graph(pool):
+    items, refs = _batch_items(pool, with_index=(1, 2, 3, 4))
+    c = sgs.Context(0, 0)
+    plan = sgs.BatchPlan(c, items)
+    before = c.launch_count()
+    plan.run()
+    assert c.sync() == sgs.OK
+    launches = c.launch_count() - before
+    assert launches <= 16 + 17  # one launch per stage, whatever the number of scenes
+    assert plan.status() == [sgs.OK] * len(items)
+    _check_outputs(items, refs)
+    _reset(items)
+    plan.run()  # the work lists are reused: counters and flags are cleared by the run itself
+    assert c.sync() == sgs.OK
+    _check_outputs(items, refs)
+    # captured once, replayed twice
+    _reset(items)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.run(s)
+    g.replay()
+    torch.cuda.synchronize()
+    _check_outputs(items, refs)
+    _reset(items)
+    g.replay()
+    torch.cuda.synchronize()
+    assert c.sync() == sgs.OK and plan.status() == [sgs.OK] * len(items)
+    _check_outputs(items, refs)
+    del g
+    plan.close()
+    c.close()
+
+
+def test_batch_status_isolates_a_corrupt_scene(pool):
+    """A scene whose payload was damaged reports its own status; the others decode intact."""
+    bad = 4  # a static-mode scene of the pool
+    assert S.parse_header(pool[bad][0])["mode"] == S.MODE_STATIC
+    damaged = list(pool)
+    buf = bytearray(pool[bad][0])
+    h = S.parse_header(bytes(buf))
+    lo = h["off_attr_pay"]
+    for k in range(lo, min(lo + 64, h["total"])):
+        buf[k] ^= 0x5A
+    damaged[bad] = (bytes(buf), pool[bad][1])
+    items, refs = _batch_items(damaged)
+    c = sgs.Context(0, 0)
+    plan = sgs.BatchPlan(c, items)
+    plan.run()
+    st = plan.status()
+    assert c.sync() == sgs.E_CORRUPT
+    assert st[bad] == sgs.E_CORRUPT and all(v == sgs.OK for j, v in enumerate(st) if j != bad)
+    _check_outputs(items, refs, skip=(bad,))
+    plan.close()
     c.close()
 
 
