@@ -43,6 +43,102 @@ WORKLOADS = {
 METRIC = "decoded Gaussians/s"
 
 
+BATCH = dict(n_scenes=64, lo=50_000, hi=3_000_000, size_seed=3000, depth_lo=14, depth_hi=17,
+             desc="batched decode of 64 scenes: N log-uniform 50k..3M (seeded), depth U{14..17}, "
+                  "even scenes learned-model rANS (W ~ 220 rows per lane), odd scenes channel-wise "
+                  "static rANS (W ~ 32 rows per lane), rANS-coded octree levels; one persistent "
+                  "launch per stage over all scenes")
+
+
+def batch_specs(n_scenes: int) -> list:
+    """(index, N, seed, depth, mode, lanes) of every scene of the batched workload."""
+    from paper_2607_12656_b300.scenegen import loguniform_sizes
+    b = BATCH
+    sizes = loguniform_sizes(b["size_seed"], n_scenes, b["lo"], b["hi"])
+    rng = np.random.Generator(np.random.PCG64(b["size_seed"] + 1))
+    depths = rng.integers(b["depth_lo"], b["depth_hi"] + 1, size=n_scenes)
+    out = []
+    for j in range(n_scenes):
+        n = int(sizes[j])
+        kept = n - n // 10
+        learned = j % 2 == 0
+        w = 220 if learned else 32
+        lanes = max(32, -(-kept // w))
+        out.append((j, n, 3000 + j, int(depths[j]), 2 if learned else 1, lanes))
+    return out
+
+
+SERVE = dict(pool_per_mode=6, lo=100_000, hi=6_000_000, size_seed=4000, depth=16, rates=(20, 50, 100, 200, 400),
+             requests=400, arrival_seed=4999, budget=120 << 30, slots=8,
+             desc="continuous-batching decode server: a pool of 3 modes x 6 scenes (N log-uniform "
+                  "100k..6M, depth 16), requests draw a mode then a scene uniformly, Poisson arrivals, "
+                  "admission by HBM footprint within 120 GB, 8 concurrent decode slots")
+
+
+def serve_specs(per_mode: int) -> list:
+    """(index, N, seed, depth, mode, lanes) of every pool scene: fixed, static, learned."""
+    from paper_2607_12656_b300.scenegen import loguniform_sizes
+    c = SERVE
+    sizes = loguniform_sizes(c["size_seed"], 3 * per_mode, c["lo"], c["hi"])
+    out = []
+    for j in range(3 * per_mode):
+        mode = j // per_mode
+        n = int(sizes[j])
+        kept = n - n // 10
+        lanes = 0 if mode == 0 else max(32, -(-kept // (220 if mode == 2 else 32)))
+        out.append((j, n, 4000 + j, c["depth"], mode, lanes))
+    return out
+
+
+_worker_ctx = None
+
+
+def encode_scene(spec, model=None) -> bytes:
+    """Generates and encodes one scene (runs in a worker process)."""
+    global _worker_ctx
+    from paper_2607_12656_b300 import sgs
+    from paper_2607_12656_b300.scenegen import make_scene
+    j, n, seed, depth, mode, lanes = spec
+    sc = make_scene(n, seed)
+    if mode == 0:
+        from paper_2607_12656_b300.scenegen import fixed_bits
+        return sgs.scene_encode(sc.pos, sc.attr, mode=0, depth=depth, bits=fixed_bits(seed), geo_mode=0)
+    kw = dict(mode=mode, depth=depth, lanes=lanes, geo_mode=1)
+    if mode == 2:
+        if _worker_ctx is None:
+            _worker_ctx = sgs.Context(0, 0)
+        kw.update(model=model, ctx=_worker_ctx)
+    return sgs.scene_encode(sc.pos, sc.attr, **kw)
+
+
+def build_batch(n_scenes: int, train_steps: int, specs=None):
+    """All bitstreams of a multi-scene workload: scenes are generated and encoded by a pool of
+    spawned workers; one context model, trained on the first learned scene, serves every
+    learned scene."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    specs = batch_specs(n_scenes) if specs is None else specs
+    workers = max(1, min(32, (os.cpu_count() or 1)))
+    os.environ.setdefault("OMP_NUM_THREADS", str(max(1, (os.cpu_count() or 1) // workers)))
+    bufs = [None] * len(specs)
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as pool:
+        futs = {pool.submit(encode_scene, s): s[0] for s in specs if s[4] != 2}
+        learned = [s for s in specs if s[4] == 2]
+        model = None
+        if learned:
+            from paper_2607_12656_b300 import learned as L, sgs
+            from paper_2607_12656_b300.scenegen import make_scene
+            j, n, seed, depth, mode, lanes = learned[0]
+            ctx = sgs.Context(0, 0)
+            model = L.train_and_freeze(ctx, make_scene(n, seed), depth, lanes, steps=train_steps,
+                                       batch=65536, seed=1)
+            ctx.close()
+            futs.update({pool.submit(encode_scene, s, model): s[0] for s in learned})
+        for f in cf.as_completed(futs):
+            bufs[futs[f]] = f.result()
+    return specs, bufs
+
+
 def peaks() -> dict:
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -284,6 +380,192 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """The batched workload: every scene's bitstream resident in HBM, one plan run per step."""
+    import torch
+    import torch.distributed as dist
+    from paper_2607_12656_b300 import sgs
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    specs, bufs = build_batch(args.scenes, args.train_steps or 300)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    ctx = sgs.Context(local, 0)
+    infos = [sgs.scene_query(b) for b in bufs]
+    rows = sum(int(i.n_rows) for i in infos)
+    host_bits = [torch.frombuffer(bytearray(b), dtype=torch.uint8).pin_memory() for b in bufs]
+    dev_bits = [h.to(dev) for h in host_bits]
+    outs = [(torch.empty((56, i.n_rows), device=dev), torch.empty((3, i.n_rows), device=dev)) for i in infos]
+    items = [(dev_bits[j], infos[j], outs[j][0], outs[j][1]) for j in range(len(infos))]
+    plan = sgs.BatchPlan(ctx, items)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.run(stream)
+    if ctx.sync(stream) != sgs.OK or plan.status() != [sgs.OK] * len(items):
+        raise RuntimeError("batch decode status %s" % plan.status())
+    launches0 = ctx.launch_count()
+    times = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.run(stream)
+            b.record(stream)
+            stream.synchronize()
+            times.append(a.elapsed_time(b))
+        torch.cuda.synchronize()
+    launches = ctx.launch_count() - launches0
+    if ctx.sync(stream) != sgs.OK:
+        raise RuntimeError("batch decode failed")
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / args.steps
+    # the same scenes decoded one after another (one scene_decode call each)
+    ctx.reserve(max(int(i.scratch_bytes) for i in infos))
+    seq = []
+    for k in range(min(args.steps, 10)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for j in range(len(items)):
+            sgs.scene_decode(ctx, dev_bits[j], infos[j], outs[j][0], outs[j][1], None, None, stream)
+        b.record(stream)
+        stream.synchronize()
+        seq.append(a.elapsed_time(b))
+    # one plan run captured in a CUDA graph and replayed
+    graph = []
+    try:
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream()
+        cap.wait_stream(stream)
+        with torch.cuda.graph(g, stream=cap):
+            plan.run(cap)
+        torch.cuda.synchronize()
+        for k in range(min(args.steps, 20)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+            stream.synchronize()
+            graph.append(a.elapsed_time(b))
+    except Exception as exc:
+        print("graph capture failed: %s" % exc, file=sys.stderr)
+    # end to end: bitstreams from pinned host memory, decode, outputs back to pinned host memory
+    host_out = [(torch.empty(o[0].shape, pin_memory=True), torch.empty(o[1].shape, pin_memory=True)) for o in outs]
+    e2e = []
+    for k in range(min(args.steps, 5)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for h, d in zip(host_bits, dev_bits):
+            d.copy_(h, non_blocking=True)
+        plan.run(stream)
+        for (ha, hp), (da, dp) in zip(host_out, outs):
+            ha.copy_(da, non_blocking=True)
+            hp.copy_(dp, non_blocking=True)
+        b.record(stream)
+        stream.synchronize()
+        e2e.append(a.elapsed_time(b))
+    if ctx.sync(stream) != sgs.OK:
+        raise RuntimeError("batch decode failed")
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    in_bytes = sum(len(b) for b in bufs)
+    out_bytes = 4 * 59 * rows
+    line = {"metric": METRIC, "value": rows * world / (ms / 1e3), "unit": "Gaussians/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32->f32", "data": "synthetic",
+            "config": {"workload": BATCH["desc"] + " [%d scenes]" % len(items), "n_rows": rows,
+                       "scenes": len(items), "learned_scenes": sum(1 for s in specs if s[4] == 2),
+                       "bitstream_bytes": in_bytes, "output_bytes": out_bytes,
+                       "l2": "flushed (256 MiB write) before every timed step; outputs exceed L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
+                           "min": min(times), "max": max(times), "note": "whole-batch makespan per step"},
+            "sequential": {"ms_per_step": float(np.mean(seq)), "value": rows / (np.mean(seq) / 1e3),
+                           "note": "same scenes, one scene_decode call after another"},
+            "gpu_launches": launches // args.steps,
+            "roofline": {"kernel": "whole batch (dominated by the learned decoder)", "bound": "hbm",
+                         "achieved": (in_bytes + out_bytes) / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": (in_bytes + out_bytes) / (ms / 1e3) / 1e9 / hbm if hbm else None,
+                         "traffic": None,
+                         "note": "compressed bytes read + fp32 outputs written over the makespan"},
+            "e2e": {"value": rows / (np.mean(e2e) / 1e3), "unit": "Gaussians/s", "h2d_bytes_per_step": in_bytes,
+                    "d2h_bytes_per_step": out_bytes, "ms_per_step": float(np.mean(e2e))},
+            "clocks": clk.summary()}
+    if graph:
+        line["graph"] = {"ms_per_step": float(np.mean(graph)), "value": rows / (np.mean(graph) / 1e3),
+                         "note": "one plan run captured in a CUDA graph and replayed"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_serve(args):
+    """Serving: Poisson request streams at several rates against the decode server."""
+    import torch
+    from paper_2607_12656_b300 import serve, sgs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    c = SERVE
+    specs = serve_specs(c["pool_per_mode"])
+    specs, bufs = build_batch(len(specs), args.train_steps or 300, specs)
+    torch.cuda.set_device(local)
+    scenes = [serve.Scene(b) for b in bufs]
+    modes = {name: [s[0] for s in specs if s[4] == m] for m, name in enumerate(("fixed", "static", "learned"))}
+    srv = serve.DecodeServer(scenes, slots=c["slots"], hbm_budget=c["budget"], device=local)
+    # warm-up: every scene once
+    warm = srv.run([(0.0, j) for j in range(len(scenes))] * max(1, args.warmup // 3))
+    if any(r.status != sgs.OK for r in warm):
+        raise RuntimeError("serving warm-up failed")
+    rates = [float(r) for r in (args.rates.split(",") if args.rates else c["rates"])]
+    per_rate = []
+    with ClockSampler(local) as clk:
+        for k, lam in enumerate(rates):
+            reqs = serve.poisson_arrivals_modes(lam, args.requests or c["requests"], modes,
+                                                seed=c["arrival_seed"] + k)
+            res = srv.run(reqs)
+            summ = serve.summarize(res, scenes, modes)
+            summ["rate_req_s"] = lam
+            per_rate.append(summ)
+    srv.close()
+    best = max(per_rate, key=lambda d: d["gaussians_per_s"])
+    line = {"metric": METRIC, "value": best["gaussians_per_s"] * world, "unit": "Gaussians/s", "n_gpus": world,
+            "steps": len(rates), "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32->f32", "data": "synthetic",
+            "config": {"workload": c["desc"], "requests_per_rate": args.requests or c["requests"],
+                       "rates_req_s": rates, "pool_scenes": len(scenes),
+                       "pool_gaussians": int(sum(s.n_rows for s in scenes)),
+                       "l2": "not flushed: serving traffic (bitstream upload + outputs) far exceeds L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "latency_ms": {"p50": best["p50_ms"], "p99": best["p99_ms"],
+                           "note": "arrival to completion, at the rate with the highest throughput"},
+            "per_rate": per_rate,
+            "e2e": {"value": best["gaussians_per_s"] * world, "unit": "Gaussians/s",
+                    "h2d_bytes_per_step": None, "d2h_bytes_per_step": 0,
+                    "note": "every request uploads its bitstream from pinned host memory inside its latency"},
+            "gpu_launches": None, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(w: dict, buf: bytes, budget_s: float) -> dict:
     """The CPU oracle, as it stands, decoding the same bitstream (or a bounded part of it)."""
     from oracle import scene as S
@@ -336,7 +618,10 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fixed", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="fixed", choices=sorted(WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--scenes", type=int, default=BATCH["n_scenes"], help="scenes of the batch workload")
+    ap.add_argument("--rates", default=None, help="serve workload: comma-separated request rates (req/s)")
+    ap.add_argument("--requests", type=int, default=None, help="serve workload: requests per rate")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     ap.add_argument("--traffic", type=float, default=None,
@@ -345,6 +630,13 @@ def main():
     ap.add_argument("--lanes", type=int, default=None, help="override the workload's rANS lanes")
     ap.add_argument("--train-steps", type=int, default=None, help="override the learned model's steps")
     args = ap.parse_args()
+    if args.workload in ("batch", "serve"):
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the %s workload is timed on the GPU only; "
+                              "the oracle arm runs the single-scene workloads" % args.workload}))
+            return
+        (run_batch if args.workload == "batch" else run_serve)(args)
+        return
     w = dict(WORKLOADS[args.workload])
     if args.n is not None:
         w["n"] = args.n

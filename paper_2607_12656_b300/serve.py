@@ -146,6 +146,20 @@ def poisson_arrivals(rate: float, n: int, n_scenes: int, seed: int) -> list[tupl
     return [(float(a), int(b)) for a, b in zip(t, which)]
 
 
+def poisson_arrivals_modes(rate: float, n: int, modes: dict, seed: int) -> list[tuple[float, int]]:
+    """Poisson arrivals; each request draws a coding mode uniformly, then a scene of that mode
+    uniformly (scene ids from modes: name -> list of ids)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    groups = [ids for ids in modes.values() if ids]
+    m = rng.integers(0, len(groups), size=n)
+    out = []
+    for a, g in zip(t, m):
+        ids = groups[int(g)]
+        out.append((float(a), int(ids[int(rng.integers(0, len(ids)))])))
+    return out
+
+
 def summarize(results: list[Result], scenes: list[Scene], modes: dict | None = None) -> dict:
     lat = np.array([r.latency for r in results]) * 1e3
     span = max(r.done for r in results) - min(r.arrival for r in results)
