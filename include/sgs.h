@@ -93,7 +93,7 @@ typedef struct {
     uint32_t geo_mode;        /* SGS_GEO_*                                                */
     uint32_t depth;           /* 1..21                                                    */
     uint32_t lanes;           /* attribute rANS lanes (entropy-coded modes), >= 1          */
-    uint32_t geo_lanes;       /* geometry rANS lanes, 0 = about 512 tokens per lane        */
+    uint32_t geo_lanes;       /* geometry rANS lanes, 0 = about 128 tokens per lane        */
     uint32_t bits[SGS_NCHAN]; /* fixed-length bit widths 1..16 (8 is forced for rANS modes)*/
     const void *model;        /* learned mode: SGS_MODEL_BYTES of frozen model, else NULL  */
 } sgs_encode_params;
@@ -201,9 +201,8 @@ typedef struct {
 /* Batched decode (no counterpart in the paper, which decodes one scene at a time; the scenes
  * are independent, and Sec. 3.4.2's parallelism over groups extends across them).  Every
  * pipeline stage of all n scenes runs as ONE persistent launch: its CTAs take work items
- * (the lanes' groups, table expansions, scan tiles, octree node blocks of every scene) from
- * a shared counter.  The octree expansion takes one launch per level-group index, so a run
- * is about 10 + (deepest scene's expansion groups) launches whatever n is.
+ * (the lanes' groups, table expansions, scan tiles, blocks of octree leaves of every scene)
+ * from a shared counter, so a run is at most 11 launches whatever n is.
  *
  * A plan binds the items' buffers (bitstreams, outputs) and holds, in one device block, every
  * scene's scratch, the per-stage work lists and per-scene status words. */
@@ -257,6 +256,40 @@ int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, uint32_t n,
  * the context model on the scene's own tokens.  cap in bytes.                               */
 int scene_tokens(const float *pos, const float *attr, uint32_t n, uint32_t depth,
                  uint8_t *tokens, size_t cap, uint32_t *n_rows);
+
+/* ------------------------------------------------------------------ autotuning */
+
+/* Lane-count tuning: the paper's complexity knob is the group size W, Gaussians per
+ * autoregressive group (Sec. 4, implementation details: W = 256 for the main model, 32 for
+ * the fast one); here lanes = ceil(N' / W).  sgs_autotune encodes the given scene at every
+ * candidate W, decodes each bitstream on the context's device `reps` times (CUDA events,
+ * median), and picks the smallest bitstream whose decode time is at most max_ms (the fastest
+ * one if max_ms <= 0 or none qualifies). */
+#define SGS_TUNE_MAX_CAND 16
+typedef struct {
+    const float *pos, *attr;  /* host scene, as for scene_encode                           */
+    uint32_t n;
+    uint32_t mode;            /* SGS_MODE_STATIC or SGS_MODE_LEARNED                      */
+    uint32_t depth;
+    uint32_t geo_mode;
+    const void *model;        /* learned mode: the frozen model                           */
+    uint32_t n_cand;          /* 1 .. SGS_TUNE_MAX_CAND                                   */
+    uint32_t rows_per_lane[SGS_TUNE_MAX_CAND];  /* candidate W values, >= 1              */
+    float max_ms;             /* decode-time target, <= 0: fastest                         */
+    uint32_t reps;            /* timed decodes per candidate (>= 1)                       */
+} sgs_tune_request;
+
+typedef struct {
+    uint32_t best;            /* index of the chosen candidate                            */
+    uint32_t lanes[SGS_TUNE_MAX_CAND];
+    uint64_t bytes[SGS_TUNE_MAX_CAND];   /* bitstream size                                */
+    float ms[SGS_TUNE_MAX_CAND];         /* median decode time                            */
+} sgs_tune_result;
+
+/* Allocates device memory for the trial bitstreams and outputs (freed before returning)
+ * and may grow the context's scratch.  Synchronous.  Errors: SGS_E_INVALID (bad request),
+ * SGS_E_NOMEM, SGS_E_CUDA, or the status of a failed trial decode. */
+int sgs_autotune(sgs_ctx *ctx, const sgs_tune_request *req, sgs_tune_result *res);
 
 /* ------------------------------------------------------------------ learned part */
 

@@ -16,7 +16,6 @@ namespace sgs {
 size_t octree_scan_tiles(uint64_t n_geo);
 int octree_launches(const sgs_scene_info &info, const GeoPlan &plan);
 size_t octree_words(uint64_t n_geo);
-void octree_code_buffers(const sgs_scene_info &info, const GeoPlan &plan, uint64_t *pingpong);
 
 static inline uint64_t a256(uint64_t x) { return (x + 255) & ~255ull; }
 
@@ -67,10 +66,7 @@ size_t scratch_need(const sgs_scene_info &info, Scratch *s, uint8_t *base) {
     t.p4 = reinterpret_cast<uint32_t *>(take(4 * (octree_words(info.n_geo) + 16)));
     t.scan_flags = reinterpret_cast<uint64_t *>(take(8 * (octree_scan_tiles(info.n_geo) + 1)));
     t.ticket = reinterpret_cast<uint32_t *>(take(256));
-    uint64_t pp;
-    octree_code_buffers(info, plan, &pp);
-    t.codes[0] = reinterpret_cast<uint64_t *>(take(pp));
-    t.codes[1] = reinterpret_cast<uint64_t *>(take(pp));
+    t.par = reinterpret_cast<uint32_t *>(take(info.n_rows ? 4ull * (info.n_geo + info.n_leaves) : 0));
     const int n_tab = plan.n_coded_levels + (info.mode == SGS_MODE_STATIC ? kNChan : 0);
     t.tables = take((uint64_t)n_tab * kTabBytes);
     t.dup_prefix = reinterpret_cast<uint32_t *>(take(4ull * (info.n_dup + 1)));
@@ -124,12 +120,9 @@ extern "C" int sgs_create(sgs_ctx **out, int device, size_t scratch_bytes) {
     cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
     if (cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_low) != cudaSuccess ||
         cudaStreamCreateWithPriority(&c->geo, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&c->aux2, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->gjoin, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->top_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->top_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->gjoin, cudaEventDisableTiming) != cudaSuccess) {
         cudaFree(c->status_dev);
         cudaFreeHost(c->status_host);
         delete c;
@@ -174,10 +167,7 @@ extern "C" void sgs_destroy(sgs_ctx *c) {
     cudaEventDestroy(c->join);
     cudaEventDestroy(c->gjoin);
     cudaStreamDestroy(c->geo);
-    cudaEventDestroy(c->top_fork);
-    cudaEventDestroy(c->top_join);
     cudaStreamDestroy(c->aux);
-    cudaStreamDestroy(c->aux2);
     cudaFree(c->status_dev);
     cudaFreeHost(c->status_host);
     delete c;
@@ -265,6 +255,7 @@ extern "C" int scene_query(const uint8_t *b, size_t len, sgs_scene_info *info) {
             info->n_leaves < info->n_level[D - 1] || (uint64_t)info->n_leaves > 8ull * info->n_level[D - 1])
             return SGS_E_INVALID;
         if (info->n_geo + info->n_leaves >= (1ull << 32)) return SGS_E_INVALID;
+        if (info->n_geo > (1ull << 29)) return SGS_E_UNSUPPORTED;  // parent index in 29 bits
         if (info->n_dup > info->n_leaves) return SGS_E_INVALID;
     }
     // geometry sections
@@ -358,9 +349,7 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
         c->launches += 2;
     }
     if (c->profile && c->n_marks <= kMaxStages) cudaEventRecord(c->marks[c->n_marks++], gs);
-    if ((e = launch_octree(info, plan, bits, s, out, status, gs, c->aux2, c->top_fork, c->top_join)) !=
-        cudaSuccess)
-        return SGS_E_CUDA;
+    if ((e = launch_octree(info, plan, bits, s, out, status, gs)) != cudaSuccess) return SGS_E_CUDA;
     if (info.n_rows) c->launches += octree_launches(info, plan);
     if (c->profile && c->n_marks <= kMaxStages) cudaEventRecord(c->marks[c->n_marks++], gs);
     // join

@@ -6,9 +6,9 @@
 // the parameter block of each scene that has work in the stage and the prefix sums of the
 // scenes' item counts (an item is one CTA of the single-scene kernel).  The lists go to
 // device memory once.  Run: a fixed number of launches -- static tables; attributes per
-// coding mode; raw geometry copy, geometry tokens, duplicate prefix; popcount scan beside
-// the top levels; one launch per octree expansion group index -- enqueued without
-// allocation or host synchronisation, so a run can be captured in a CUDA graph.  Each launch
+// coding mode; raw geometry copy, geometry tokens, duplicate prefix; popcount scan with the
+// parent scatter; leaf walk -- enqueued without allocation or host synchronisation, so a
+// run can be captured in a CUDA graph.  Each launch
 // is a grid of resident CTAs that claim items from an atomic counter in increasing order
 // (which keeps the scan's look-back waiting only on tiles that already started).
 #include <cuda_runtime.h>
@@ -49,8 +49,8 @@ namespace {
 
 constexpr int kMaxLaunches = 16 + SGS_MAX_DEPTH;
 
-enum Kind { K_TABLES, K_FIXED, K_ATTR, K_LEARNED, K_COPY, K_GEO, K_DUP, K_SCAN, K_TOP, K_EXPAND };
-enum Role { R_MAIN, R_ATTR, R_GEO, R_TOP };
+enum Kind { K_TABLES, K_FIXED, K_ATTR, K_LEARNED, K_COPY, K_GEO, K_DUP, K_SCAN, K_WALK };
+enum Role { R_MAIN, R_ATTR, R_GEO };
 
 struct LaunchRec {
     Kind kind;
@@ -75,8 +75,7 @@ size_t stage_bytes(Kind k) {
         case K_GEO: return stage_rans_geo_bytes();
         case K_DUP: return stage_dup_bytes();
         case K_SCAN: return stage_scan_bytes();
-        case K_TOP: return stage_top_bytes();
-        default: return stage_expand_bytes();
+        default: return stage_walk_bytes();
     }
 }
 
@@ -90,8 +89,7 @@ uint32_t stage_items(Kind k, int variant, const SceneRef &r, void *par) {
         case K_GEO: return stage_rans_geo(r, par);
         case K_DUP: return stage_dup(r, par);
         case K_SCAN: return stage_scan(r, par);
-        case K_TOP: return stage_top(r, par);
-        default: return stage_expand(r, variant, par);
+        default: return stage_walk(r, par);
     }
 }
 
@@ -105,8 +103,7 @@ cudaError_t launch_kind(Kind k, int variant, const MultiArgs &m, cudaStream_t st
         case K_GEO: return launch_rans_geo_multi(m, st);
         case K_DUP: return launch_dup_multi(m, st);
         case K_SCAN: return launch_scan_multi(m, st);
-        case K_TOP: return launch_top_multi(m, st);
-        default: return launch_expand_multi(m, st);
+        default: return launch_walk_multi(m, st);
     }
 }
 
@@ -129,7 +126,6 @@ struct BatchLayout {
     std::vector<LaunchRec> launches;
     std::vector<uint8_t> lists;  // prefix and parameter lists, uploaded to lists_off
     uint64_t zero_off, zero_bytes, status_off, lists_off, total;
-    int n_groups_max;
 };
 
 static int build_layout(const sgs_batch_item *items, int n, uint8_t *base, BatchLayout *L) {
@@ -207,16 +203,9 @@ static int build_layout(const sgs_batch_item *items, int n, uint8_t *base, Batch
     if (rc == SGS_OK) rc = add(K_COPY, 0, R_GEO);
     if (rc == SGS_OK) rc = add(K_GEO, 0, R_GEO);
     if (rc == SGS_OK) rc = add(K_DUP, 0, R_GEO);
-    if (rc == SGS_OK) rc = add(K_TOP, 0, R_TOP);
     if (rc == SGS_OK) rc = add(K_SCAN, 0, R_GEO);
-    int gmax = 0;
-    for (int i = 0; i < n; ++i) {
-        const int g = octree_group_count(items[i].info, L->plans[i]);
-        gmax = g > gmax ? g : gmax;
-    }
-    for (int g = 0; g < gmax && rc == SGS_OK; ++g) rc = add(K_EXPAND, g, R_GEO);
+    if (rc == SGS_OK) rc = add(K_WALK, 0, R_GEO);
     if (rc != SGS_OK) return rc;
-    L->n_groups_max = gmax;
     L->total = a256(L->lists_off + L->lists.size());
     return SGS_OK;
 }
@@ -271,37 +260,24 @@ int batch_init(sgs_ctx *c, const sgs_batch_item *items, int n, uint8_t *base, sg
 int batch_run(sgs_ctx *c, sgs_batch *b, cudaStream_t st) {
     const BatchLayout &L = b->L;
     if (cudaMemsetAsync(b->base + L.zero_off, 0, L.zero_bytes, st) != cudaSuccess) return SGS_E_CUDA;
-    cudaStream_t role_stream[4] = {st, c->aux, c->geo, c->aux2};
-    if (cudaEventRecord(c->fork, st) != cudaSuccess || cudaStreamWaitEvent(c->aux, c->fork, 0) != cudaSuccess ||
-        cudaStreamWaitEvent(c->geo, c->fork, 0) != cudaSuccess || cudaStreamWaitEvent(c->aux2, c->fork, 0) != cudaSuccess)
-        return SGS_E_CUDA;
-    // the tables feed both halves: run them first on the caller's stream, then fork again
-    bool forked_after_tables = false;
+    cudaStream_t role_stream[3] = {st, c->aux, c->geo};
+    // the tables feed both halves: run them first on the caller's stream, then fork
+    bool forked = false;
     for (size_t i = 0; i < L.launches.size(); ++i) {
         const LaunchRec &r = L.launches[i];
-        if (r.kind != K_TABLES && !forked_after_tables) {
+        if (r.kind != K_TABLES && !forked) {
             if (cudaEventRecord(c->fork, st) != cudaSuccess || cudaStreamWaitEvent(c->aux, c->fork, 0) != cudaSuccess ||
                 cudaStreamWaitEvent(c->geo, c->fork, 0) != cudaSuccess)
                 return SGS_E_CUDA;
-            forked_after_tables = true;
-        }
-        if (r.kind == K_TOP) {  // beside the scan: fork from the geometry stream
-            if (cudaEventRecord(c->top_fork, c->geo) != cudaSuccess ||
-                cudaStreamWaitEvent(c->aux2, c->top_fork, 0) != cudaSuccess)
-                return SGS_E_CUDA;
-        }
-        if (r.kind == K_EXPAND && r.variant == 0) {  // expansion needs the top levels
-            if (cudaEventRecord(c->top_join, c->aux2) != cudaSuccess ||
-                cudaStreamWaitEvent(c->geo, c->top_join, 0) != cudaSuccess)
-                return SGS_E_CUDA;
+            forked = true;
         }
         if (launch_kind(r.kind, r.variant, multi_args(*b, r, (int)i), role_stream[r.role]) != cudaSuccess)
             return SGS_E_CUDA;
         c->launches += 1;
     }
-    if (cudaEventRecord(c->join, c->aux) != cudaSuccess || cudaEventRecord(c->gjoin, c->geo) != cudaSuccess ||
-        cudaEventRecord(c->top_join, c->aux2) != cudaSuccess || cudaStreamWaitEvent(st, c->join, 0) != cudaSuccess ||
-        cudaStreamWaitEvent(st, c->gjoin, 0) != cudaSuccess || cudaStreamWaitEvent(st, c->top_join, 0) != cudaSuccess)
+    if (forked && (cudaEventRecord(c->join, c->aux) != cudaSuccess || cudaEventRecord(c->gjoin, c->geo) != cudaSuccess ||
+                   cudaStreamWaitEvent(st, c->join, 0) != cudaSuccess ||
+                   cudaStreamWaitEvent(st, c->gjoin, 0) != cudaSuccess))
         return SGS_E_CUDA;
     if (b->n) {
         k_status_fold<<<1, 256, 0, st>>>(reinterpret_cast<const int *>(b->base + L.status_off), b->n, c->status_dev);

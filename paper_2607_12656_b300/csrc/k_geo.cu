@@ -1,17 +1,17 @@
-// Sparse-octree expansion on sm_103a (Sec. 3.4, "Geometry Occupancy Coding": occupancy
+// Sparse-octree decoding on sm_103a (Sec. 3.4, "Geometry Occupancy Coding": occupancy
 // tokens, one per internal node, level by level; one position per voxel plus duplicate
 // counts as metadata).
 //
 // The tokens of all levels form one breadth-first array B.  With P(x) = sum of popc(B[h])
-// for h < x, the children of node x are the nodes 1 + P(x) + j (j < popc(B[x])), leaves
-// numbered after the internal nodes.  One device-wide scan (decoupled look-back) writes P at
-// every 4-byte word of B, so any node's children follow from two loads: P4[x / 4] plus the
-// popcount of the bytes of its word below x.  Expansion is then a map with no block-wide
-// synchronisation: a thread takes one node and walks its subtree depth first through up to
-// kMaxFuse chain-like levels (a small stack of child iterators in shared memory), writing the
-// packed coordinates (x:21 | y:21 | z:21) of the nodes at the end of its levels or, at the
-// last level, the voxel-centre positions of the leaf rows.  The few small top levels are
-// expanded by one CTA, concurrently with the scan.
+// for h < x, the children of node x are the nodes 1 + P(x) + j (j < popc(B[x])), the j-th
+// taking child index k = the j-th set bit of B[x]; leaves are numbered after the internal
+// nodes.  Two launches decode the tree without any level-by-level synchronisation:
+//   1. a device-wide scan of popcounts (decoupled look-back) that, as soon as a tile knows
+//      P(x), writes every child's parent entry par[1 + P(x) + j] = x << 3 | k;
+//   2. a walk from every leaf up to the root (D dependent loads of par), assembling the
+//      leaf's coordinates one bit per level, then writing its position rows.
+// The level counts in the header are checked against P (the children of each level are
+// exactly the next level), so every parent entry is written once per decode.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -23,10 +23,9 @@ namespace sgs {
 
 constexpr int kScanThreads = 256;
 constexpr uint32_t kSpinLimit = 1u << 22;          // bounded look-back wait
-constexpr int kTopThreads = 1024;
-constexpr uint32_t kTopCap = 2048;                 // levels the top kernel keeps in smem
-constexpr int kExpThreads = 128;
-constexpr int kMaxFuse = 8;                        // levels one expansion thread walks
+constexpr int kWalkThreads = 256;
+constexpr int kWalkIlp = 8;                        // leaves a thread walks together
+constexpr uint32_t kWalkLeaves = kWalkThreads * kWalkIlp;  // leaves per CTA
 constexpr uint64_t kM21 = (1ull << 21) - 1;
 
 struct LeafOut {
@@ -96,14 +95,20 @@ struct ScanParams {
     const uint8_t *B;
     uint64_t n, n_words;
     uint32_t *P4;
+    uint32_t *par;             // parent entries x << 3 | k of nodes 1 .. total-1
     uint64_t *flags;
     uint32_t *ticket;
     int *status;
+    int depth;
+    uint32_t level_off[SGS_MAX_DEPTH + 2];  // [D + 1] = total node count
 };
 
 __device__ __forceinline__ void scan_body(const ScanParams &sp, uint32_t tile) {
     __shared__ uint32_t sm[8];
     __shared__ uint32_t s_prefix;
+    // the tile's token words and P at each, word w at w + w / 16 (padded: conflict-free)
+    __shared__ uint32_t sm_words[kScanThreads * 17];
+    __shared__ uint32_t sm_pref[kScanThreads * 17];
     const uint8_t *B = sp.B;
     const uint64_t n = sp.n, n_words = sp.n_words;
     uint32_t *P4 = sp.P4;
@@ -111,24 +116,24 @@ __device__ __forceinline__ void scan_body(const ScanParams &sp, uint32_t tile) {
     int *status = sp.status;
     const uint64_t k = (uint64_t)tile * kScanThreads + threadIdx.x;  // 64-byte chunk
     const uint64_t w0 = 16 * k;                                      // its first word
-    uint32_t cnt[16];
+    uint32_t wd[16];  // the chunk's words (bytes at or past n cleared)
     uint32_t sum = 0;
     if (64 * k + 64 <= n) {
         const uint4 *p = reinterpret_cast<const uint4 *>(B + 64 * k);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const uint4 v = p[i];
-            cnt[4 * i] = __popc(v.x);
-            cnt[4 * i + 1] = __popc(v.y);
-            cnt[4 * i + 2] = __popc(v.z);
-            cnt[4 * i + 3] = __popc(v.w);
+            wd[4 * i] = v.x;
+            wd[4 * i + 1] = v.y;
+            wd[4 * i + 2] = v.z;
+            wd[4 * i + 3] = v.w;
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) cnt[i] = (w0 + i) * 4 < n ? __popc(word_at(B, n, w0 + i)) : 0u;
+        for (int i = 0; i < 16; ++i) wd[i] = (w0 + i) * 4 < n ? word_at(B, n, w0 + i) : 0u;
     }
 #pragma unroll
-    for (int i = 0; i < 16; ++i) sum += cnt[i];
+    for (int i = 0; i < 16; ++i) sum += __popc(wd[i]);
     uint32_t agg;
     const uint32_t local = block_excl_scan_256(sum, &agg, sm);
     // decoupled look-back, 32 predecessors per step (flag 1 = aggregate, 2 = inclusive prefix)
@@ -172,11 +177,49 @@ __device__ __forceinline__ void scan_body(const ScanParams &sp, uint32_t tile) {
         }
     }
     __syncthreads();
-    uint32_t run = s_prefix + local;
+    const uint32_t base = s_prefix + local;  // P(4 w0)
+    uint32_t run = base;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         if (w0 + i <= n_words) P4[w0 + i] = run;  // P4[n_words] = total
-        run += cnt[i];
+        run += __popc(wd[i]);
+    }
+    // parent entries of the children of the tile's nodes, written in rounds where lane i
+    // takes node base + 256 r + i, so a warp's children entries are contiguous: the words
+    // and their prefixes go through shared memory
+    {
+        uint32_t r = base;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            sm_words[17 * threadIdx.x + i] = wd[i];
+            sm_pref[17 * threadIdx.x + i] = r;
+            r += __popc(wd[i]);
+        }
+    }
+    __syncthreads();
+    const uint64_t tile_x = (uint64_t)tile * kScanThreads * 64;  // first node of the tile
+    if (tile_x >= n) return;
+    uint64_t x = tile_x + threadIdx.x;
+    int l = 0;
+    while (l < sp.depth && sp.level_off[l + 1] <= x) ++l;
+    for (int r = 0; r < 64; ++r, x += kScanThreads) {
+        if (x >= n) break;
+        while (l < sp.depth && sp.level_off[l + 1] <= x) ++l;
+        const uint32_t xl = (uint32_t)(x - tile_x), wi = (xl >> 2) + (xl >> 6);
+        const uint32_t w = sm_words[wi], sh = 8u * (xl & 3u);
+        uint32_t byte = (w >> sh) & 0xFFu;
+        uint32_t y = 1u + sm_pref[wi] + __popc(w & ((1u << sh) - 1u));
+        const uint32_t lo = sp.level_off[l + 1], hi = sp.level_off[l + 2];
+        while (byte) {
+            const uint32_t kc = __ffs(byte) - 1;
+            byte &= byte - 1;
+            if (y < lo || y >= hi) {
+                set_status(status, SGS_E_CORRUPT);
+                break;
+            }
+            sp.par[y] = ((uint32_t)x << 3) | kc;
+            ++y;
+        }
     }
 }
 
@@ -242,211 +285,84 @@ __global__ void __launch_bounds__(256) k_dup_multi(MultiArgs m) {
     run_items<DupParams>(m, [](const DupParams &p, uint32_t, uint32_t, bool) { dup_body(p); });
 }
 
-// ------------------------------------------------------------------ top levels (one CTA)
+// ------------------------------------------------------------------ leaf walk
 
-struct TopParams {
-    const uint8_t *B;
-    GeoPlan plan;
-    int l1;               // first level not held in shared memory (or D)
-    uint64_t *codes_out;  // codes of level l1 (if l1 < D)
-    LeafOut leaf;
-    int *status;
-};
-
-constexpr uint32_t kTopStage = 8192;  // top-level tokens staged in shared memory
-
-__device__ __forceinline__ void top_body(const TopParams &p) {
-    __shared__ uint64_t codes[2][kTopCap];
-    __shared__ uint8_t stage[kTopStage];
-    __shared__ uint32_t wsum[32];
-    __shared__ uint32_t s_carry;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) codes[0][0] = 0;
-    // all top-level tokens in one coalesced pass (they are contiguous from BFS index 0)
-    const uint64_t n_top = p.plan.level_off[p.l1];
-    const bool staged = n_top <= kTopStage;
-    if (staged)
-        for (uint32_t i = threadIdx.x; i < n_top; i += kTopThreads) stage[i] = p.B[i];
-    __syncthreads();
-    int cur = 0;
-    for (int l = 0; l < p.l1; ++l) {
-        const uint32_t n = p.plan.n_level[l];
-        const uint32_t n_next = p.plan.n_level[l + 1];
-        const bool to_leaves = (l + 1 == p.plan.depth);
-        const bool to_global = (l + 1 == p.l1) && !to_leaves;
-        const uint8_t *Bl = (staged ? stage : p.B) + p.plan.level_off[l];
-        if (threadIdx.x == 0) s_carry = 0;
-        __syncthreads();
-        for (uint32_t base = 0; base < n; base += kTopThreads) {
-            const uint32_t i = base + threadIdx.x;
-            const uint32_t byte = i < n ? Bl[i] : 0u;
-            const uint32_t cnt = __popc(byte);
-            uint32_t incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            if (lane == 31) wsum[warp] = incl;
-            __syncthreads();
-            if (warp == 0) {
-                uint32_t v = wsum[lane], iv = v;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    uint32_t t = __shfl_up_sync(0xffffffffu, iv, o);
-                    if (lane >= o) iv += t;
-                }
-                wsum[lane] = iv - v;  // exclusive warp offsets
-            }
-            __syncthreads();
-            uint32_t idx = s_carry + wsum[warp] + incl - cnt;
-            if (i < n) {
-                const uint64_t pc = codes[cur][i];
-                uint32_t b = byte;
-                while (b) {
-                    const uint32_t k = __ffs(b) - 1;
-                    b &= b - 1;
-                    const uint64_t cc = child_code(pc, k);
-                    if (idx >= n_next) { set_status(p.status, SGS_E_CORRUPT); break; }
-                    if (to_leaves) write_leaf(p.leaf, idx, cc, p.status);
-                    else if (to_global) p.codes_out[idx] = cc;
-                    else codes[cur ^ 1][idx] = cc;
-                    ++idx;
-                }
-            }
-            __syncthreads();
-            if (threadIdx.x == kTopThreads - 1) s_carry += wsum[31] + incl;
-            __syncthreads();
-        }
-        if (threadIdx.x == 0 && s_carry != n_next) set_status(p.status, SGS_E_CORRUPT);
-        cur ^= 1;
-        __syncthreads();
-    }
+// Level-count check: the popcounts of level l sum to the node count of level l+1, and level
+// l's first node has level l+1's first node as its first child.
+__device__ __forceinline__ void check_levels(const uint8_t *B, uint64_t n_geo, const uint32_t *P4,
+                                             const uint32_t *off, int depth, int *status) {
+    const int l = threadIdx.x;
+    if (l >= depth) return;
+    uint32_t b0, p0, b1, p1;
+    node_at(B, n_geo, P4, off[l], b0, p0);
+    node_at(B, n_geo, P4, off[l + 1], b1, p1);
+    if (1u + p0 != off[l + 1] || p1 - p0 != off[l + 2] - off[l + 1]) set_status(status, SGS_E_CORRUPT);
 }
 
-__global__ void __launch_bounds__(kTopThreads) k_octree_top(TopParams p) { top_body(p); }
-
-__global__ void __launch_bounds__(kTopThreads) k_octree_top_multi(MultiArgs m) {
-    run_items<TopParams>(m, [](const TopParams &p, uint32_t, uint32_t, bool) { top_body(p); });
-}
-
-// ------------------------------------------------------------------ fused levels
-
-// Thread per node x of level ls: depth-first through levels ls .. le-1, emitting the nodes of
-// level le (codes) or, when le = D, the leaf rows.  The stack holds one child iterator per
-// level (P of the node, remaining child mask, children taken, packed coordinates).
-struct ExpandParams {
+struct WalkParams {
     const uint8_t *B;
     uint64_t n_geo;
     const uint32_t *P4;
-    int ls, le, depth;
-    uint64_t level_off[SGS_MAX_DEPTH + 2];  // BFS offset of each level, [D+1] = end of leaves
-    const uint64_t *codes_in;               // level ls, indexed by x - level_off[ls]
-    uint64_t *codes_out;                    // level le (NULL when le = D)
+    const uint32_t *par;
+    uint32_t leaf_lo, n_leaves;  // first leaf's node index, leaf count
+    int depth, check;            // CTA 0 of the walk verifies the level counts
     LeafOut leaf;
-    int check;                              // CTA 0 verifies the level counts
+    uint32_t level_off[SGS_MAX_DEPTH + 2];
     int *status;
 };
 
-__device__ __forceinline__ void expand_body(const ExpandParams &p, uint32_t vb) {
-    __shared__ uint32_t s_p[kMaxFuse][kExpThreads];
-    __shared__ uint32_t s_it[kMaxFuse][kExpThreads];  // remaining mask | taken << 8
-    __shared__ uint64_t s_code[kMaxFuse][kExpThreads];
-    __shared__ uint32_t s_off[SGS_MAX_DEPTH + 2];      // level offsets (node indices < 2^32)
-    const int tid = threadIdx.x;
-    if (tid <= p.depth + 1) s_off[tid] = (uint32_t)p.level_off[tid];
-    __syncthreads();
-    if (p.check && vb == 0 && tid < p.depth) {
-        // sum of the popcounts of level l = nodes of level l+1, and the first child of the
-        // level's first node is the next level's first node
-        const int l = tid;
-        uint32_t b0, p0, b1, p1;
-        node_at(p.B, p.n_geo, p.P4, s_off[l], b0, p0);
-        node_at(p.B, p.n_geo, p.P4, s_off[l + 1], b1, p1);
-        if (1u + p0 != s_off[l + 1] || p1 - p0 != s_off[l + 2] - s_off[l + 1])
-            set_status(p.status, SGS_E_CORRUPT);
+// Leaves vb * kWalkLeaves + j * kWalkThreads + threadIdx.x, j < kWalkIlp: the D steps of
+// the kWalkIlp walks are interleaved so their loads are in flight together.  Step s reads
+// the parent entry of the current node: its child index k gives bit s of the coordinates
+// (x, y, z) = (bit 2, bit 1, bit 0 of k), its parent index the next node.  Each step must go
+// to a smaller index and the walk must end at the root after exactly D steps (D <= 21, so
+// bit s stays inside its 21-bit field).
+__device__ __forceinline__ void walk_body(const WalkParams &p, uint32_t vb) {
+    if (p.check && vb == 0) check_levels(p.B, p.n_geo, p.P4, p.level_off, p.depth, p.status);
+    uint32_t y[kWalkIlp];
+    uint64_t code[kWalkIlp];  // packed x:21 | y:21 | z:21
+    bool on[kWalkIlp];
+#pragma unroll
+    for (int j = 0; j < kWalkIlp; ++j) {
+        const uint32_t u = vb * kWalkLeaves + j * kWalkThreads + threadIdx.x;
+        on[j] = u < p.n_leaves;
+        y[j] = p.leaf_lo + (on[j] ? u : 0u);
+        code[j] = 0;
     }
-    const uint32_t lo = s_off[p.ls];
-    const uint32_t x = lo + vb * kExpThreads + tid;
-    if (x >= s_off[p.ls + 1]) return;
-    uint32_t byte, px;
-    node_at(p.B, p.n_geo, p.P4, x, byte, px);
-    uint64_t code = p.codes_in[x - lo];
-    const uint32_t leaf_base = s_off[p.depth];
-    int lvl = p.ls;  // level of the current node
-    // chains: follow single children without the stack
-    while (lvl + 1 < p.le && __popc(byte) == 1) {
-        const uint32_t child = 1u + px;
-        ++lvl;
-        if (child < s_off[lvl] || child >= s_off[lvl + 1]) {
-            set_status(p.status, SGS_E_CORRUPT);
-            return;
-        }
-        code = child_code(code, __ffs(byte) - 1);
-        node_at(p.B, p.n_geo, p.P4, child, byte, px);
-    }
-    // depth first through the remaining levels lvl .. le-1
-    s_p[0][tid] = px;
-    s_it[0][tid] = byte;
-    s_code[0][tid] = code;
-    const int K = p.le - lvl;
-    int d = 0;
-    while (d >= 0) {
-        const uint32_t it = s_it[d][tid];
-        const uint32_t mask = it & 0xFFu;
-        if (!mask) { --d; continue; }
-        const uint32_t k = __ffs(mask) - 1;
-        const uint32_t taken = it >> 8;
-        s_it[d][tid] = (mask & (mask - 1)) | ((taken + 1) << 8);
-        const uint32_t child = 1u + s_p[d][tid] + taken;
-        const int lc = lvl + d + 1;  // level of the child
-        if (child < s_off[lc] || child >= s_off[lc + 1]) {
-            set_status(p.status, SGS_E_CORRUPT);
-            return;
-        }
-        const uint64_t cc = child_code(s_code[d][tid], k);
-        if (d + 1 == K) {
-            if (lc == p.depth) write_leaf(p.leaf, child - leaf_base, cc, p.status);
-            else p.codes_out[child - s_off[lc]] = cc;
-        } else {
-            uint32_t cb, cp;
-            node_at(p.B, p.n_geo, p.P4, child, cb, cp);
-            ++d;
-            s_p[d][tid] = cp;
-            s_it[d][tid] = cb;
-            s_code[d][tid] = cc;
+    bool bad = false;
+    for (int st = 0; st < p.depth; ++st) {
+        uint32_t e[kWalkIlp];
+#pragma unroll
+        for (int j = 0; j < kWalkIlp; ++j) e[j] = on[j] ? p.par[y[j]] : 0u;
+#pragma unroll
+        for (int j = 0; j < kWalkIlp; ++j) {
+            if (!on[j]) continue;
+            const uint32_t up = e[j] >> 3, k = e[j] & 7u;
+            if (up >= y[j]) {
+                bad = true;
+                on[j] = false;
+                continue;
+            }
+            code[j] |= (((uint64_t)((k >> 2) & 1u) << 42) | ((uint64_t)((k >> 1) & 1u) << 21) | (k & 1u)) << st;
+            y[j] = up;
         }
     }
-}
-
-__global__ void __launch_bounds__(kExpThreads) k_octree_expand(ExpandParams p) { expand_body(p, blockIdx.x); }
-
-__global__ void __launch_bounds__(kExpThreads) k_octree_expand_multi(MultiArgs m) {
-    run_items<ExpandParams>(m, [](const ExpandParams &p, uint32_t vb, uint32_t, bool) { expand_body(p, vb); });
-}
-
-int octree_top_level(const GeoPlan &plan) {
-    int l1 = 1;
-    while (l1 < plan.depth && plan.n_level[l1] <= kTopCap) ++l1;
-    return l1;
-}
-
-// Level groups [ls, le) of the fused expansion.  A thread's levels run one after another, so
-// only chain-like levels are fused: extend while the frontier grows by at most 1/10 over the
-// group (branching subtrees would leave a warp waiting for its widest lane), and the group
-// holds at most kMaxFuse levels.
-int octree_groups(const GeoPlan &plan, int *starts) {
-    const int D = plan.depth;
-    int n = 0;
-    int ls = octree_top_level(plan);
-    while (ls < D) {
-        int le = ls + 1;
-        while (le < D && le - ls < kMaxFuse && (uint64_t)plan.n_level[le] * 10 <= 11ull * plan.n_level[ls]) ++le;
-        starts[n++] = ls;
-        ls = le;
+#pragma unroll
+    for (int j = 0; j < kWalkIlp; ++j) {
+        if (!on[j]) continue;
+        if (y[j] != 0) {
+            bad = true;
+            continue;
+        }
+        write_leaf(p.leaf, vb * kWalkLeaves + j * kWalkThreads + threadIdx.x, code[j], p.status);
     }
-    starts[n] = D;
-    return n;
+    if (bad) set_status(p.status, SGS_E_CORRUPT);
+}
+
+__global__ void __launch_bounds__(kWalkThreads) k_octree_walk(WalkParams p) { walk_body(p, blockIdx.x); }
+
+__global__ void __launch_bounds__(kWalkThreads) k_octree_walk_multi(MultiArgs m) {
+    run_items<WalkParams>(m, [](const WalkParams &p, uint32_t vb, uint32_t, bool) { walk_body(p, vb); });
 }
 
 // ------------------------------------------------------------------ parameters
@@ -490,66 +406,50 @@ static uint32_t make_dup(const uint8_t *bits, const sgs_scene_info &info, const 
     return (octree_work(info) && info.n_dup) ? 1 : 0;
 }
 
-static uint32_t make_scan(const uint8_t *bits, const sgs_scene_info &info, const Scratch &s, int *status,
-                          ScanParams *pp) {
+static void level_offsets(const sgs_scene_info &info, const GeoPlan &plan, uint32_t *off) {
+    for (int k = 0; k <= plan.depth; ++k) off[k] = (uint32_t)plan.level_off[k];
+    off[plan.depth + 1] = (uint32_t)(info.n_geo + info.n_leaves);
+}
+
+static uint32_t make_scan(const uint8_t *bits, const sgs_scene_info &info, const GeoPlan &plan,
+                          const Scratch &s, int *status, ScanParams *pp) {
     ScanParams &p = *pp;
     memset(&p, 0, sizeof(p));
     p.B = geo_tokens(bits, info, s);
     p.n = info.n_geo;
     p.n_words = (info.n_geo + 3) / 4;
     p.P4 = s.p4;
+    p.par = s.par;
     p.flags = s.scan_flags;
     p.ticket = s.ticket;
     p.status = status;
+    p.depth = plan.depth;
+    level_offsets(info, plan, p.level_off);
     return octree_work(info) ? (uint32_t)octree_scan_tiles(info.n_geo) : 0;
 }
 
-static uint32_t make_top(const uint8_t *bits, const sgs_scene_info &info, const GeoPlan &plan,
-                         const Scratch &s, const sgs_scene_out &out, int *status, TopParams *pp) {
-    TopParams &p = *pp;
+static uint32_t make_walk(const uint8_t *bits, const sgs_scene_info &info, const GeoPlan &plan,
+                          const Scratch &s, const sgs_scene_out &out, int *status, WalkParams *pp) {
+    WalkParams &p = *pp;
     memset(&p, 0, sizeof(p));
-    const int l1 = octree_top_level(plan);
     p.B = geo_tokens(bits, info, s);
-    p.plan = plan;
-    p.l1 = l1;
-    p.codes_out = (l1 < plan.depth) ? s.codes[0] : nullptr;
+    p.n_geo = info.n_geo;
+    p.P4 = s.p4;
+    p.par = s.par;
+    p.leaf_lo = (uint32_t)info.n_geo;
+    p.n_leaves = info.n_leaves;
+    p.depth = plan.depth;
+    p.check = 1;
     p.leaf = make_leaf(bits, info, s, out);
+    level_offsets(info, plan, p.level_off);
     p.status = status;
-    return octree_work(info) ? 1 : 0;
-}
-
-// Expansion group gi (levels starts[gi] .. starts[gi+1]).
-static uint32_t make_expand(const uint8_t *bits, const sgs_scene_info &info, const GeoPlan &plan,
-                            const Scratch &s, const sgs_scene_out &out, int *status, int gi,
-                            ExpandParams *pp) {
-    ExpandParams &ep = *pp;
-    memset(&ep, 0, sizeof(ep));
-    int starts[SGS_MAX_DEPTH + 2];
-    const int n_groups = octree_groups(plan, starts);
-    if (!octree_work(info) || gi >= n_groups) return 0;
-    const int D = plan.depth;
-    ep.B = geo_tokens(bits, info, s);
-    ep.n_geo = info.n_geo;
-    ep.P4 = s.p4;
-    ep.depth = D;
-    for (int l = 0; l <= D; ++l) ep.level_off[l] = plan.level_off[l];
-    ep.level_off[D + 1] = plan.level_off[D] + plan.n_level[D];
-    ep.leaf = make_leaf(bits, info, s, out);
-    ep.status = status;
-    ep.ls = starts[gi];
-    ep.le = starts[gi + 1];
-    ep.codes_in = s.codes[gi & 1];
-    ep.codes_out = ep.le < D ? s.codes[(gi + 1) & 1] : nullptr;
-    ep.check = gi == 0;
-    return (uint32_t)((plan.n_level[ep.ls] + kExpThreads - 1) / kExpThreads);
+    return octree_work(info) ? (info.n_leaves + kWalkLeaves - 1) / kWalkLeaves : 0;
 }
 
 // ------------------------------------------------------------------ launcher
 
-cudaError_t launch_octree(const sgs_scene_info &info, const GeoPlan &plan,
-                          const uint8_t *bits, const Scratch &s, const sgs_scene_out &out,
-                          int *status, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_a,
-                          cudaEvent_t ev_b) {
+cudaError_t launch_octree(const sgs_scene_info &info, const GeoPlan &plan, const uint8_t *bits,
+                          const Scratch &s, const sgs_scene_out &out, int *status, cudaStream_t st) {
     if (!octree_work(info)) return cudaSuccess;
     cudaError_t e;
     DupParams dp;
@@ -557,29 +457,14 @@ cudaError_t launch_octree(const sgs_scene_info &info, const GeoPlan &plan,
         k_dup_prefix<<<1, 256, 0, st>>>(dp);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    // the top levels need no prefix: they run on st2 while the scan runs on st
-    if (st2 != st) {
-        if (cudaEventRecord(ev_a, st) != cudaSuccess || cudaStreamWaitEvent(st2, ev_a, 0) != cudaSuccess)
-            return cudaErrorUnknown;
-    }
-    TopParams tp;
-    make_top(bits, info, plan, s, out, status, &tp);
-    k_octree_top<<<1, kTopThreads, 0, st2>>>(tp);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (st2 != st && cudaEventRecord(ev_b, st2) != cudaSuccess) return cudaErrorUnknown;
     ScanParams sp;
-    const uint32_t tiles = make_scan(bits, info, s, status, &sp);
+    const uint32_t tiles = make_scan(bits, info, plan, s, status, &sp);
     k_octree_scan<<<tiles, kScanThreads, 0, st>>>(sp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (st2 != st && cudaStreamWaitEvent(st, ev_b, 0) != cudaSuccess) return cudaErrorUnknown;
-    ExpandParams ep;
-    for (int gi = 0;; ++gi) {
-        const uint32_t grid = make_expand(bits, info, plan, s, out, status, gi, &ep);
-        if (grid == 0) break;
-        k_octree_expand<<<grid, kExpThreads, 0, st>>>(ep);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    WalkParams wp;
+    const uint32_t blocks = make_walk(bits, info, plan, s, out, status, &wp);
+    k_octree_walk<<<blocks, kWalkThreads, 0, st>>>(wp);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ batched stages
@@ -597,7 +482,7 @@ cudaError_t launch_dup_multi(const MultiArgs &m, cudaStream_t st) {
 
 uint32_t stage_scan(const SceneRef &r, void *par) {
     ScanParams p;
-    const uint32_t n = make_scan(r.bits, *r.info, *r.s, r.status, &p);
+    const uint32_t n = make_scan(r.bits, *r.info, *r.plan, *r.s, r.status, &p);
     memcpy(par, &p, sizeof(p));
     return n;
 }
@@ -606,49 +491,19 @@ cudaError_t launch_scan_multi(const MultiArgs &m, cudaStream_t st) {
     return launch_persistent(k_octree_scan_multi, kScanThreads, 0, m, st);
 }
 
-uint32_t stage_top(const SceneRef &r, void *par) {
-    TopParams p;
-    const uint32_t n = make_top(r.bits, *r.info, *r.plan, *r.s, *r.out, r.status, &p);
+uint32_t stage_walk(const SceneRef &r, void *par) {
+    WalkParams p;
+    const uint32_t n = make_walk(r.bits, *r.info, *r.plan, *r.s, *r.out, r.status, &p);
     memcpy(par, &p, sizeof(p));
     return n;
 }
-size_t stage_top_bytes() { return sizeof(TopParams); }
-cudaError_t launch_top_multi(const MultiArgs &m, cudaStream_t st) {
-    return launch_persistent(k_octree_top_multi, kTopThreads, 0, m, st);
-}
-
-uint32_t stage_expand(const SceneRef &r, int group, void *par) {
-    ExpandParams p;
-    const uint32_t n = make_expand(r.bits, *r.info, *r.plan, *r.s, *r.out, r.status, group, &p);
-    memcpy(par, &p, sizeof(p));
-    return n;
-}
-size_t stage_expand_bytes() { return sizeof(ExpandParams); }
-cudaError_t launch_expand_multi(const MultiArgs &m, cudaStream_t st) {
-    return launch_persistent(k_octree_expand_multi, kExpThreads, 0, m, st);
-}
-
-int octree_group_count(const sgs_scene_info &info, const GeoPlan &plan) {
-    int starts[SGS_MAX_DEPTH + 2];
-    return octree_work(info) ? octree_groups(plan, starts) : 0;
-}
-
-// Scratch of the octree stage: bytes of each ping-pong code buffer (the widest level that
-// starts a fused group, or level l1 written by the top kernel).
-void octree_code_buffers(const sgs_scene_info &info, const GeoPlan &plan, uint64_t *pingpong) {
-    int starts[SGS_MAX_DEPTH + 2];
-    const int n = octree_groups(plan, starts);
-    uint64_t m = 1;
-    for (int i = 0; i < n; ++i) m = m > plan.n_level[starts[i]] ? m : plan.n_level[starts[i]];
-    if (info.n_rows == 0) m = 1;
-    *pingpong = 8 * m;
+size_t stage_walk_bytes() { return sizeof(WalkParams); }
+cudaError_t launch_walk_multi(const MultiArgs &m, cudaStream_t st) {
+    return launch_persistent(k_octree_walk_multi, kWalkThreads, 0, m, st);
 }
 
 // Kernels launch_octree enqueues for a non-empty scene.
-int octree_launches(const sgs_scene_info &info, const GeoPlan &plan) {
-    int starts[SGS_MAX_DEPTH + 2];
-    return (info.n_dup ? 1 : 0) + 2 + octree_groups(plan, starts);
-}
+int octree_launches(const sgs_scene_info &info, const GeoPlan &) { return (info.n_dup ? 1 : 0) + 2; }
 
 // Scan tiles: every 64-byte chunk up to the one holding word n_words (whose P4 entry is the
 // total), 256 chunks per tile.

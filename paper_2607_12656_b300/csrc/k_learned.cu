@@ -59,26 +59,25 @@ __device__ __forceinline__ uint32_t lds32(const __nv_bfloat16 *p) {
     return *reinterpret_cast<const uint32_t *>(p);
 }
 
-// acc(16 x 8 tile at rows r0.., cols n0..) += A[r0.., 0..63] * W[n0.., 0..63]^T, both bf16
-// rows of stride kBS in shared memory; returns the exact integer sums.
-__device__ __forceinline__ void tile_16x8x64(int32_t (&out)[4], const __nv_bfloat16 *A, int r0,
-                                             const __nv_bfloat16 *W, int n0, int g, int t) {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int kk = 0; kk < 64; kk += 16) {
-        const uint32_t a0 = lds32(A + (r0 + g) * kBS + kk + 2 * t);
-        const uint32_t a1 = lds32(A + (r0 + g + 8) * kBS + kk + 2 * t);
-        const uint32_t a2 = lds32(A + (r0 + g) * kBS + kk + 8 + 2 * t);
-        const uint32_t a3 = lds32(A + (r0 + g + 8) * kBS + kk + 8 + 2 * t);
-        const uint32_t b0 = lds32(W + (n0 + g) * kBS + kk + 2 * t);
-        const uint32_t b1 = lds32(W + (n0 + g) * kBS + kk + 8 + 2 * t);
-        mma_bf16(acc, a0, a1, a2, a3, b0, b1);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) out[i] = __float2int_rn(acc[i]);
+// The four A fragments of one m16n8k16 tile (16 x 16 bf16, row-major, rows kBS apart) with
+// one ldmatrix: lane L gives the address of row (L & 7) + 8 ((L >> 3) & 1), columns
+// 8 (L >> 4) .. +7, of the tile starting at A.
+__device__ __forceinline__ void ldsm_a(const __nv_bfloat16 *A, uint32_t &a0, uint32_t &a1, uint32_t &a2,
+                                       uint32_t &a3) {
+    const int lane = threadIdx.x & 31;
+    const __nv_bfloat16 *p = A + ((lane & 7) + 8 * ((lane >> 3) & 1)) * kBS + 8 * (lane >> 4);
+    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
+                 : "r"(addr));
 }
 
 __device__ __forceinline__ __nv_bfloat16 bf(int v) { return __int2bfloat16_rn(v); }
+// Two small integers as a bf16 pair, the first in the low half.
+__device__ __forceinline__ uint32_t pack_bf16(int lo, int hi) {
+    __nv_bfloat162 h = __halves2bfloat162(bf(lo), bf(hi));
+    return *reinterpret_cast<uint32_t *>(&h);
+}
 
 struct LearnedParams {
     const uint8_t *bits;
@@ -89,17 +88,24 @@ struct LearnedParams {
     int *status;
 };
 
-// Pipelined decoder: 16 producer warps compute, step by step (Gaussian i, channel c), the
-// 32 lanes' frequency tables -- layer 1 on the ALU, layers 2-3 as int8 mma.sync, the
-// integer softmax -- and store them as u16 cumulative tables in a ring of kNB buffers; one
-// consumer warp runs the 32 rANS chains, binary-searching its lane's table.  Only the search
-// is on the sequential chain; the context of step (i+1, c) needs only (i, c), 56 steps back,
-// so producers run up to kNB steps ahead.  Hand-offs use mbarriers with bounded waits.
-constexpr int kPW = 16;                  // producer warps
+// Pipelined decoder: 16 producer warps compute the frequency tables of the steps (Gaussian i,
+// channel c) ahead of one consumer warp that runs the group's 32 rANS chains.  Each producer
+// warp owns 8 of a step's 32 contexts and computes them end to end on its own -- layer 1 on
+// the ALU, layers 2-3 as bf16 mma.sync with the contexts as the N dimension, the integer
+// softmax reduced with shuffles among the 8 lanes that share a context -- so producers never
+// synchronise with each other.  Four warps make one step; the 16 warps work on 4 steps at
+// once, writing u16 cumulative tables into a ring of kNB steps.  The context of step (i, c)
+// needs only (i-1 .. i-4, c), at least 56 steps back, so the ring's release by the consumer
+// also publishes the tokens a producer reads.  Hand-offs are mbarriers with bounded waits.
+constexpr int kPW = 12;                  // producer warps
 constexpr int kPT = 32 * kPW;            // producer threads
 constexpr int kLT = kPT + 32;            // + consumer warp
-constexpr int kNB = 4;                   // pipeline depth (steps)
+constexpr int kNB = 8;                   // ring depth (steps)
+constexpr int kQW = 4;                   // warps per step (8 contexts each)
+constexpr int kSW = kPW / kQW;           // steps in flight
 constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr int kCS = 264;                 // cdf row stride (u16): rows 528 B apart spread the banks
+static_assert(kNB >= kSW && kNB <= kNChan, "ring");
 
 struct LSmem2 {
     int8_t w1[64 * 4];
@@ -109,16 +115,10 @@ struct LSmem2 {
     alignas(16) __nv_bfloat16 w3[256 * kBS];
     int32_t b3[256];
     uint32_t exp2q[256];
-    alignas(16) __nv_bfloat16 h1[32 * kBS];
-    alignas(16) __nv_bfloat16 h2[32 * kBS];
-    uint8_t ctx[32 * 4 * kNChan];            // [lane][ring row][channel]
-    alignas(16) uint16_t cdf[kNB][32][256];  // cumulative frequency of each symbol
-    alignas(16) uint16_t win[kWinWords];     // consumer's word-stream window
-    int32_t red_max[8][32];
-    int32_t red_idx[8][32];
-    uint32_t red_sum[8][32];
-    uint32_t red_T[8][32];
-    uint32_t R[32];
+    alignas(16) __nv_bfloat16 h2t[kPW][8 * kBS];  // per warp: layer-2 output, [context][unit]
+    uint8_t ctx[32 * 4 * kNChan];               // [lane][ring row][channel]
+    alignas(16) uint16_t cdf[kNB][32][kCS];     // cumulative frequency of each symbol
+    alignas(16) uint16_t win[kWinWords];        // consumer's word-stream window
     uint32_t nrows[32];
     uint64_t row0[32];
     float step[kNChan], offset[kNChan];
@@ -128,7 +128,9 @@ struct LSmem2 {
     int bad;
     int abort_;
 };
-static_assert(offsetof(LSmem2, cdf) % 16 == 0 && offsetof(LSmem2, win) % 16 == 0, "alignment");
+static_assert(offsetof(LSmem2, cdf) % 16 == 0 && offsetof(LSmem2, win) % 16 == 0 &&
+              offsetof(LSmem2, h2t) % 16 == 0, "alignment");
+static_assert(sizeof(LSmem2) <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -158,10 +160,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
     }
     return false;
 }
-__device__ __forceinline__ void producer_sync() {
-    asm volatile("bar.sync 1, %0;" ::"r"(kPT) : "memory");
-}
-
 __device__ bool load_model2(LSmem2 &S, const uint8_t *m, int *status) {
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -202,163 +200,188 @@ __device__ bool load_model2(LSmem2 &S, const uint8_t *m, int *status) {
     return true;
 }
 
-// One producer step: frequency tables of the 32 lanes' rows for (i, c) into cdf[b].
-__device__ __forceinline__ void produce_step(LSmem2 &S, uint32_t i, int c, int b) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// One warp's share of step (i, c): the frequency tables of lanes 8q .. 8q+7 into cdf[b].
+// mma.sync m16n8k16 fragments: lane = 4 g + t; A rows g, g+8, B column g, D rows g, g+8 x
+// columns 2t, 2t+1.  Layers 2 and 3 compute W h^T, so the 8 contexts are the columns.
+__device__ __forceinline__ void produce_pass(LSmem2 &S, uint32_t i, int c, int b, int q) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    // layer 1 (ALU): row r = tid >> 4, outputs 4 (tid & 15) .. +3
+    // ---- layer 1 for context g: the 16 units this lane feeds into layer 2's B fragments
+    uint32_t bf2[4][2];
     {
-        const int r = tid >> 4, o0 = (tid & 15) * 4;
-        int32_t u[4];
+        const int L = 8 * q + g;
+        // u_j = token_{i-j} - 128 as packed int8 (0 before the lane's first row)
+        uint32_t up = 0;
 #pragma unroll
-        for (int j = 1; j <= 4; ++j)
-            u[j - 1] = (i >= (uint32_t)j) ? (int32_t)S.ctx[(r * 4 + ((i - j) & 3)) * kNChan + c] - 128 : 0;
+        for (int j = 1; j <= 4; ++j) {
+            const uint32_t tok = (i >= (uint32_t)j) ? S.ctx[(L * 4 + ((i - j) & 3)) * kNChan + c] : 128u;
+            up |= (tok ^ 0x80u) << (8 * (j - 1));
+        }
+        const int32_t *b1 = S.b1 + c * 64;
+        const int32_t *w1 = reinterpret_cast<const int32_t *>(S.w1);  // row o: 4 int8 weights
+        const int32_t m1 = S.m1, sh1 = S.sh1;
 #pragma unroll
-        for (int o = o0; o < o0 + 4; ++o) {
-            int32_t acc = S.b1[c * 64 + o];
+        for (int kt = 0; kt < 4; ++kt)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc += (int32_t)S.w1[o * 4 + j] * u[j];
-            S.h1[r * kBS + o] = bf(requant(acc, S.m1, S.sh1));
+            for (int h = 0; h < 2; ++h) {
+                int32_t v[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int o = 16 * kt + 8 * h + 2 * t + e;
+                    v[e] = requant(__dp4a(w1[o], (int32_t)up, b1[o]), m1, sh1);
+                }
+                bf2[kt][h] = pack_bf16(v[0], v[1]);
+            }
+    }
+    // ---- layer 2: D[unit][context] = W2 h1^T; requantised into this warp's transpose buffer
+    __nv_bfloat16 *h2t = S.h2t[warp];
+    {
+        const int32_t m2 = S.m2, sh2 = S.sh2;
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kt = 0; kt < 4; ++kt) {
+                uint32_t a0, a1, a2, a3;
+                ldsm_a(S.w2 + 16 * mt * kBS + 16 * kt, a0, a1, a2, a3);
+                mma_bf16(acc, a0, a1, a2, a3, bf2[kt][0], bf2[kt][1]);
+            }
+            const int r0 = 16 * mt + g, r1 = r0 + 8;
+            h2t[(2 * t) * kBS + r0] = bf(requant(__float2int_rn(acc[0]) + S.b2[r0], m2, sh2));
+            h2t[(2 * t + 1) * kBS + r0] = bf(requant(__float2int_rn(acc[1]) + S.b2[r0], m2, sh2));
+            h2t[(2 * t) * kBS + r1] = bf(requant(__float2int_rn(acc[2]) + S.b2[r1], m2, sh2));
+            h2t[(2 * t + 1) * kBS + r1] = bf(requant(__float2int_rn(acc[3]) + S.b2[r1], m2, sh2));
         }
     }
-    producer_sync();
-    // layer 2: warp -> rows 16 (warp & 1), cols 8 (warp >> 1)
-    {
-        const int r0 = (warp & 1) * 16, n0 = (warp >> 1) * 8;
-        int32_t acc[4] = {0, 0, 0, 0};
-        tile_16x8x64(acc, S.h1, r0, S.w2, n0, g, t);
-        const int col = n0 + 2 * t;
-        S.h2[(r0 + g) * kBS + col] = bf(requant(acc[0] + S.b2[col], S.m2, S.sh2));
-        S.h2[(r0 + g) * kBS + col + 1] = bf(requant(acc[1] + S.b2[col + 1], S.m2, S.sh2));
-        S.h2[(r0 + g + 8) * kBS + col] = bf(requant(acc[2] + S.b2[col], S.m2, S.sh2));
-        S.h2[(r0 + g + 8) * kBS + col + 1] = bf(requant(acc[3] + S.b2[col + 1], S.m2, S.sh2));
+    __syncwarp();
+    uint32_t bf3[4][2];
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+        bf3[kt][0] = lds32(h2t + g * kBS + 16 * kt + 2 * t);
+        bf3[kt][1] = lds32(h2t + g * kBS + 16 * kt + 2 * t + 8);
     }
-    producer_sync();
-    // layer 3: warp -> rows 16 (warp & 1), column slice cs = warp >> 1 (32 columns)
-    const int r0 = (warp & 1) * 16, cs = warp >> 1;
-    const int rA = r0 + g, rB = r0 + g + 8;
-    int32_t z[4][4];
+    // ---- layer 3: z[symbol][context]; this lane holds symbols 16 mt + g (+8) of contexts
+    //      2t (z[mt][0], z[mt][2]) and 2t+1 (z[mt][1], z[mt][3])
+    int32_t z[16][4];
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-        const int n0 = cs * 32 + nt * 8;
-        z[nt][0] = z[nt][1] = z[nt][2] = z[nt][3] = 0;
-        tile_16x8x64(z[nt], S.h2, r0, S.w3, n0, g, t);
-        const int col = n0 + 2 * t;
-        z[nt][0] += S.b3[col];
-        z[nt][1] += S.b3[col + 1];
-        z[nt][2] += S.b3[col];
-        z[nt][3] += S.b3[col + 1];
+    for (int mt = 0; mt < 16; ++mt) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+            uint32_t a0, a1, a2, a3;
+            ldsm_a(S.w3 + 16 * mt * kBS + 16 * kt, a0, a1, a2, a3);
+            mma_bf16(acc, a0, a1, a2, a3, bf3[kt][0], bf3[kt][1]);
+        }
+        const int32_t b30 = S.b3[16 * mt + g], b31 = S.b3[16 * mt + g + 8];
+        z[mt][0] = __float2int_rn(acc[0]) + b30;
+        z[mt][1] = __float2int_rn(acc[1]) + b30;
+        z[mt][2] = __float2int_rn(acc[2]) + b31;
+        z[mt][3] = __float2int_rn(acc[3]) + b31;
     }
-    // (a) row max, lowest argmax
-    {
-        int32_t mA = z[0][0], mB = z[0][2];
-        int32_t iA = cs * 32 + 2 * t, iB = iA;
+    // ---- integer softmax of contexts 2t (e = 0) and 2t+1 (e = 1); the 8 lanes g = 0..7 with
+    //      this t hold all 256 symbols of both
+    int32_t zmax[2], amax[2];
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
+    for (int e = 0; e < 2; ++e) {
+        zmax[e] = z[0][e];
+        amax[e] = g;
 #pragma unroll
-            for (int v = 0; v < 2; ++v) {
-                const int32_t col = cs * 32 + nt * 8 + 2 * t + v;
-                if (z[nt][v] > mA) { mA = z[nt][v]; iA = col; }
-                if (z[nt][2 + v] > mB) { mB = z[nt][2 + v]; iB = col; }
+        for (int mt = 0; mt < 16; ++mt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int32_t v = z[mt][2 * h + e];
+                const int32_t k = 16 * mt + 8 * h + g;  // ascending over (mt, h): strict > keeps the lowest
+                if (v > zmax[e]) { zmax[e] = v; amax[e] = k; }
             }
 #pragma unroll
-        for (int o = 1; o <= 2; o <<= 1) {
-            const int32_t omA = __shfl_xor_sync(0xffffffffu, mA, o), oiA = __shfl_xor_sync(0xffffffffu, iA, o);
-            const int32_t omB = __shfl_xor_sync(0xffffffffu, mB, o), oiB = __shfl_xor_sync(0xffffffffu, iB, o);
-            if (omA > mA || (omA == mA && oiA < iA)) { mA = omA; iA = oiA; }
-            if (omB > mB || (omB == mB && oiB < iB)) { mB = omB; iB = oiB; }
-        }
-        if (t == 0) {
-            S.red_max[cs][rA] = mA; S.red_idx[cs][rA] = iA;
-            S.red_max[cs][rB] = mB; S.red_idx[cs][rB] = iB;
+        for (int o = 4; o < 32; o <<= 1) {
+            const int32_t om = __shfl_xor_sync(0xffffffffu, zmax[e], o);
+            const int32_t oa = __shfl_xor_sync(0xffffffffu, amax[e], o);
+            if (om > zmax[e] || (om == zmax[e] && oa < amax[e])) { zmax[e] = om; amax[e] = oa; }
         }
     }
-    producer_sync();
-    int32_t zmA = S.red_max[0][rA], amA = S.red_idx[0][rA];
-    int32_t zmB = S.red_max[0][rB], amB = S.red_idx[0][rB];
+    // e_k = EXP2Q[t_k & 255] >> (t_k >> 8), t_k = min((d_k ms) >> ss, 6144); z is overwritten
+    const uint32_t ms = S.ms, ss = S.ss;
+    uint32_t E[2] = {0u, 0u};
 #pragma unroll
-    for (int q = 1; q < 8; ++q) {
-        if (S.red_max[q][rA] > zmA) { zmA = S.red_max[q][rA]; amA = S.red_idx[q][rA]; }
-        if (S.red_max[q][rB] > zmB) { zmB = S.red_max[q][rB]; amB = S.red_idx[q][rB]; }
+    for (int mt = 0; mt < 16; ++mt)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int e = v & 1;
+            const uint32_t d = (uint32_t)(zmax[e] - z[mt][v]);
+            const uint64_t tt = ((uint64_t)d * ms) >> ss;
+            const uint32_t tk = tt > 6144u ? 6144u : (uint32_t)tt;
+            const uint32_t ek = S.exp2q[tk & 255] >> (tk >> 8);
+            z[mt][v] = (int32_t)ek;
+            E[e] += ek;
+        }
+    uint32_t R[2], Tf[2] = {0u, 0u};
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) E[e] += __shfl_xor_sync(0xffffffffu, E[e], o);
+        R[e] = (uint32_t)((65280ull << 32) / E[e]);
     }
-    // (b) e_k and partial sums
-    {
-        uint32_t sA = 0, sB = 0;
-        const uint32_t ms = S.ms, ss = S.ss;
+    // floor terms floor(e_k R / 2^32) and their sum
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
+    for (int mt = 0; mt < 16; ++mt)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const uint32_t d = (uint32_t)((v < 2 ? zmA : zmB) - z[nt][v]);
-                const uint64_t tt = ((uint64_t)d * ms) >> ss;
-                const uint32_t tk = tt > 6144 ? 6144u : (uint32_t)tt;
-                const uint32_t e = S.exp2q[tk & 255] >> (tk >> 8);
-                z[nt][v] = (int32_t)e;
-                if (v < 2) sA += e; else sB += e;
+        for (int v = 0; v < 4; ++v) {
+            const uint32_t fl = __umulhi((uint32_t)z[mt][v], R[v & 1]);
+            z[mt][v] = (int32_t)fl;
+            Tf[v & 1] += fl;
+        }
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) Tf[e] += __shfl_xor_sync(0xffffffffu, Tf[e], o);
+    // f_k = 1 + floor term, the remainder at the argmax; frequencies in symbol order, then an
+    // in-place exclusive prefix turns them into the cumulative table
+    uint16_t *cdfw = &S.cdf[b][8 * q][0];  // this warp's 8 contexts, rows kCS apart
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const uint32_t rem = 65536u - 256u - Tf[e];
+        uint16_t *row = cdfw + (2 * t + e) * kCS;
+#pragma unroll
+        for (int mt = 0; mt < 16; ++mt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = 16 * mt + 8 * h + g;
+                const uint32_t f = 1u + (uint32_t)z[mt][2 * h + e] + (k == amax[e] ? rem : 0u);
+                row[k] = (uint16_t)f;  // f <= 65281
             }
-        sA += __shfl_xor_sync(0xffffffffu, sA, 1);
-        sA += __shfl_xor_sync(0xffffffffu, sA, 2);
-        sB += __shfl_xor_sync(0xffffffffu, sB, 1);
-        sB += __shfl_xor_sync(0xffffffffu, sB, 2);
-        if (t == 0) { S.red_sum[cs][rA] = sA; S.red_sum[cs][rB] = sB; }
     }
-    producer_sync();
-    // R = floor(65280 * 2^32 / E) once per row (32 threads), then shared
-    if (tid < 32) {
-        uint64_t E = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) E += S.red_sum[q][tid];
-        S.R[tid] = (uint32_t)((65280ull << 32) / E);
-    }
-    producer_sync();
-    const uint32_t RA = S.R[rA], RB = S.R[rB];
-    // (c) floor terms and per-slice sums
+    __syncwarp();
     {
-        uint32_t TA = 0, TB = 0;
+        // lane -> context lane & 7, quarter lane >> 3 (64 symbols, 8 uint4); the 8 lanes of a
+        // quarter-warp touch 8 rows at the same column: 528-byte rows put them in 8 bank groups
+        const int n = lane & 7, qq = lane >> 3;
+        uint16_t *seg = cdfw + n * kCS + qq * 64;
+        uint4 w[8];
+        uint32_t sum = 0;
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
+        for (int j = 0; j < 8; ++j) {
+            w[j] = reinterpret_cast<const uint4 *>(seg)[j];
+            const uint32_t *h = reinterpret_cast<const uint32_t *>(&w[j]);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const uint32_t fl = __umulhi((uint32_t)z[nt][v], v < 2 ? RA : RB);
-                z[nt][v] = (int32_t)fl;
-                if (v < 2) TA += fl; else TB += fl;
+            for (int k = 0; k < 4; ++k) sum += (h[k] & 0xFFFFu) + (h[k] >> 16);
+        }
+        uint32_t incl = sum;  // scan over the 4 quarters of context n (lanes n, n+8, n+16, n+24)
+        const uint32_t n1 = __shfl_up_sync(0xffffffffu, incl, 8);
+        if (qq >= 1) incl += n1;
+        const uint32_t n2 = __shfl_up_sync(0xffffffffu, incl, 16);
+        if (qq >= 2) incl += n2;
+        uint32_t run = incl - sum;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            uint32_t *h = reinterpret_cast<uint32_t *>(&w[j]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t f0 = h[k] & 0xFFFFu, f1 = h[k] >> 16;
+                h[k] = (run & 0xFFFFu) | ((run + f0) << 16);
+                run += f0 + f1;
             }
-        TA += __shfl_xor_sync(0xffffffffu, TA, 1);
-        TA += __shfl_xor_sync(0xffffffffu, TA, 2);
-        TB += __shfl_xor_sync(0xffffffffu, TB, 1);
-        TB += __shfl_xor_sync(0xffffffffu, TB, 2);
-        if (t == 0) { S.red_T[cs][rA] = TA; S.red_T[cs][rB] = TB; }
-    }
-    producer_sync();
-    // (d) cumulative frequencies: f_k = 1 + floor term (+ remainder at the argmax)
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        const int r = half ? rB : rA;
-        const int32_t am = half ? amB : amA;
-        uint32_t T[8], Tsum = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) { T[q] = S.red_T[q][r]; Tsum += T[q]; }
-        const uint32_t rem = 65536u - 256u - Tsum;
-        uint32_t cum = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (q < cs) cum += 32u + T[q] + ((am >> 5) == q ? rem : 0u);
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const int k0 = cs * 32 + nt * 8 + 2 * t;
-            const uint32_t f0 = 1u + (uint32_t)z[nt][2 * half] + (k0 == am ? rem : 0u);
-            const uint32_t f1 = 1u + (uint32_t)z[nt][2 * half + 1] + (k0 + 1 == am ? rem : 0u);
-            const uint32_t mine = f0 + f1;
-            uint32_t incl = mine;
-            const uint32_t n1 = __shfl_up_sync(0xffffffffu, incl, 1, 4);
-            if (t >= 1) incl += n1;
-            const uint32_t n2 = __shfl_up_sync(0xffffffffu, incl, 2, 4);
-            if (t >= 2) incl += n2;
-            const uint32_t tsum = __shfl_sync(0xffffffffu, incl, 3, 4);
-            const uint32_t start = cum + incl - mine;
-            // cdf[k] <= 65535 for every k <= 255 since every f >= 1
-            *reinterpret_cast<uint32_t *>(&S.cdf[b][r][k0]) = (start & 0xFFFFu) | ((start + f0) << 16);
-            cum += tsum;
+            reinterpret_cast<uint4 *>(seg)[j] = w[j];
         }
     }
 }
@@ -399,8 +422,7 @@ __device__ __forceinline__ void consume(const LearnedParams &p, LSmem2 &S, uint3
             p.out[(uint64_t)c * p.n_rows + col] = dequant(s, S.step[c], S.offset[c]);
         }
         group_refill(gs, x, live);
-        __syncwarp();
-        if (lane == 0 && k + kNB < K) mbar_arrive(&S.empty[b]);
+        if (k + kNB < K) mbar_arrive(&S.empty[b]);
     }
     if (!aborted) {
         const bool bad = gs.bad || (lane < nl && x != 0x10000u) || (gs.ptr != gs.n_words);
@@ -442,8 +464,8 @@ __device__ __forceinline__ void learned_body(const LearnedParams &p, uint32_t gr
     for (int i = tid; i < 32 * 4 * kNChan; i += kLT) S.ctx[i] = 0;
     if (tid == 0) {
         for (int b = 0; b < kNB; ++b) {
-            mbar_init(&S.full[b], kPW);
-            mbar_init(&S.empty[b], 1);
+            mbar_init(&S.full[b], 32 * kQW);  // every lane of the step's producer warps
+            mbar_init(&S.empty[b], 32);       // every consumer lane
         }
     }
     __syncthreads();
@@ -453,21 +475,20 @@ __device__ __forceinline__ void learned_body(const LearnedParams &p, uint32_t gr
     volatile int *abort_ = &S.abort_;
 
     if (warp < kPW) {
-        // ---------------- producers
-        for (uint32_t k = 0; k < K; ++k) {
+        // ---------------- producers: warp w makes contexts 8 (w % 4) .. +7 of steps w / 4 + 4 j
+        const int q = warp % kQW;
+        for (uint32_t k = warp / kQW; k < K; k += kSW) {
             const int b = (int)(k % kNB);
-            // every producer thread acquires the consumer's release of buffer b (and with it
-            // the tokens the consumer wrote into the context ring)
-            if (k >= (uint32_t)kNB && !mbar_wait(&S.empty[b], ((k / kNB) - 1) & 1, abort_)) {
-                *abort_ = 1;
-                if (tid == 0) set_status(p.status, SGS_E_TIMEOUT);
+            // every lane acquires the consumer's release of buffer b (and with it the tokens
+            // the consumer wrote into the context ring)
+            const bool ok = k < (uint32_t)kNB || mbar_wait(&S.empty[b], ((k / kNB) - 1) & 1, abort_);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) { *abort_ = 1; set_status(p.status, SGS_E_TIMEOUT); }
+                break;
             }
-            producer_sync();  // uniform exit: every producer sees the same abort flag
-            if (*abort_) break;
             const uint32_t i = k / kNChan;
-            produce_step(S, i, (int)(k - i * kNChan), b);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&S.full[b]);
+            produce_pass(S, i, (int)(k - i * kNChan), b, q);
+            mbar_arrive(&S.full[b]);
         }
     } else {
         consume(p, S, grp, nl, K, abort_);

@@ -7,7 +7,7 @@
 // Sec. 3.4.2, decoded in parallel).  The 32 lanes of a group share one word stream; at each
 // step every lane decodes one symbol and the lanes whose state dropped below 2^16 take the
 // next words in lane order -- their word index is the popcount of the ballot below them.
-// Tables live in shared memory as cdf[257] plus a 256-bucket index on the top 8 slot bits.
+// Tables live in shared memory as cdf[257]; a symbol is found by an 8-step binary search.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -18,9 +18,9 @@
 namespace sgs {
 
 // Expands static tables (32-byte presence mask, then (f-1) as u16 per present symbol; each
-// table's offset and size were validated by scene_query) into cdf[257] + bucket[256]; one
-// CTA per table.  A table whose frequencies do not sum to 2^16 marks the stream corrupt (an
-// all-zero attribute table is allowed for an empty scene).
+// table's offset and size were validated by scene_query) into cdf[257]; one CTA per table.  A
+// table whose frequencies do not sum to 2^16 marks the stream corrupt (an all-zero attribute
+// table is allowed for an empty scene).
 struct TableOffsets {
     uint32_t off[kMaxTables];
 };
@@ -35,7 +35,6 @@ struct TableParams {
 
 __device__ __forceinline__ void tables_body(const TableParams &p, uint32_t t) {
     __shared__ uint32_t sm[8];
-    __shared__ uint32_t cdf[kTabCdfWords];
     const int s = threadIdx.x;
     const uint8_t *bits = p.bits;
     const uint64_t off = p.to.off[t];
@@ -45,27 +44,15 @@ __device__ __forceinline__ void tables_body(const TableParams &p, uint32_t t) {
     const uint32_t f = present ? ld_u16(bits + off + 32 + 2ull * rank) + 1u : 0u;
     uint32_t tot;
     const uint32_t c = block_excl_scan_256(f, &tot, sm);
-    cdf[s] = c;
+    uint32_t *out_cdf = reinterpret_cast<uint32_t *>(p.tables + (size_t)t * kTabBytes);
+    out_cdf[s] = c;
     if (s == 0) {
-        cdf[256] = tot;
         const bool empty_ok = p.allow_empty_attr && (int)t >= p.n_geo_tables && tot == 0;
         if (!(tot == 65536u || empty_ok)) set_status(p.status, SGS_E_CORRUPT);
+        // cdf[256] = 2^16 always (a corrupt table was flagged above): every slot < 2^16 then
+        // finds its symbol at or below 255 without a bound check in the decoders
+        out_cdf[256] = 65536u;
     }
-    __syncthreads();
-    uint32_t *out_cdf = reinterpret_cast<uint32_t *>(p.tables + (size_t)t * kTabBytes);
-    uint8_t *out_bucket = p.tables + (size_t)t * kTabBytes + kTabCdfWords * 4;
-    out_cdf[s] = cdf[s];
-    // cdf[256] = 2^16 always (a corrupt table was flagged above): every slot < 2^16 then
-    // finds its symbol at or below 255 without a bound check in the decoders
-    if (s == 0) out_cdf[256] = 65536u;
-    // bucket[b]: largest symbol whose cdf <= b * 256 (a lower bound for any slot >= b*256)
-    const uint32_t key = (uint32_t)s << 8;
-    int lo = 0, hi = 255;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (cdf[mid] <= key) lo = mid; else hi = mid - 1;
-    }
-    out_bucket[s] = (uint8_t)lo;
 }
 
 __global__ void __launch_bounds__(256) k_tables(TableParams p) { tables_body(p, blockIdx.x); }
@@ -110,7 +97,7 @@ struct AttrParams {
 };
 
 constexpr int kAttrWarps = 32;  // one CTA per SM shares one copy of the 56 tables
-constexpr size_t kAttrTabSmem = kNChan * kTabCdfWords * 4 + kNChan * 256 + 2 * kNChan * 4;
+constexpr size_t kAttrTabSmem = kNChan * kTabCdfWords * 4 + 2 * kNChan * 4;
 constexpr size_t kAttrSmem = kAttrTabSmem + kAttrWarps * kWinWords * 2;
 static_assert(kAttrTabSmem % 16 == 0, "window must be 16-byte aligned");
 
@@ -118,12 +105,11 @@ template <bool IDX>
 __device__ __forceinline__ void rans_attr_body(const AttrParams &p, uint32_t vb, bool reload) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *s_cdf = (uint32_t *)smem;                          // [56][257]
-    uint8_t *s_bucket = smem + kNChan * kTabCdfWords * 4;         // [56][256]
-    float *s_step = (float *)(s_bucket + kNChan * 256);           // [56]
+    float *s_step = (float *)(smem + kNChan * kTabCdfWords * 4);  // [56]
     float *s_off = s_step + kNChan;                               // [56]
     uint16_t *s_win = reinterpret_cast<uint16_t *>(smem + kAttrTabSmem) + (threadIdx.x >> 5) * kWinWords;
     if (reload) {  // (a CTA's next item of the same scene finds the tables in place)
-        load_tables_smem(p.tables, kNChan, s_cdf, s_bucket);
+        load_cdf_smem(p.tables, kNChan, s_cdf);
         if (threadIdx.x < kNChan) {
             s_step[threadIdx.x] = ld_f32(p.bits + p.chan_off + 4 * threadIdx.x);
             s_off[threadIdx.x] = ld_f32(p.bits + p.chan_off + 4 * (kNChan + threadIdx.x));
@@ -148,7 +134,6 @@ __device__ __forceinline__ void rans_attr_body(const AttrParams &p, uint32_t vb,
     // per-channel state advanced incrementally: tables, constants, output pointer
     uint32_t row = R0 + lane;
     const uint32_t *cdf = s_cdf;
-    const uint8_t *bkt = s_bucket;
     int c = 0;
     float *orow = p.out + row;  // channel 0 of the current row (no out_index)
     float *o = orow;
@@ -156,10 +141,8 @@ __device__ __forceinline__ void rans_attr_body(const AttrParams &p, uint32_t vb,
         const bool active = t < n;
         if (active) {
             const uint32_t slot = x & 0xFFFFu;
-            uint32_t sym = bkt[slot >> 8];
-            uint32_t hi = cdf[sym + 1];
-            while (hi <= slot) hi = cdf[++sym + 1];  // cdf[256] = 2^16 > slot ends the walk
-            const uint32_t lo = cdf[sym];
+            const uint32_t sym = cdf_search(cdf, slot);
+            const uint32_t lo = cdf[sym], hi = cdf[sym + 1];
             x = (hi - lo) * (x >> 16) + slot - lo;
             const float v = dequant(sym, s_step[c], s_off[c]);
             if (IDX) p.out[(size_t)c * p.n_rows + p.out_index[row]] = v;
@@ -167,13 +150,11 @@ __device__ __forceinline__ void rans_attr_body(const AttrParams &p, uint32_t vb,
             if (++c == kNChan) {
                 c = 0;
                 cdf = s_cdf;
-                bkt = s_bucket;
                 row += nl;
                 orow += nl;
                 o = orow;
             } else {
                 cdf += kTabCdfWords;
-                bkt += 256;
                 o += p.n_rows;
             }
         }
@@ -251,18 +232,17 @@ struct GeoParams {
 };
 
 constexpr int kGeoWarps = 8;
-constexpr size_t kGeoTabSmem = (SGS_MAX_DEPTH * (kTabCdfWords * 4 + 256) + 15) & ~size_t(15);
+constexpr size_t kGeoTabSmem = (SGS_MAX_DEPTH * kTabCdfWords * 4 + 15) & ~size_t(15);
 static_assert(kGeoTabSmem % 16 == 0, "window must be 16-byte aligned");
 
 __device__ __forceinline__ void rans_geo_body(const GeoParams &p, uint32_t vb) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int nt = p.plan.n_coded_levels;
     uint32_t *s_cdf = (uint32_t *)smem;
-    uint8_t *s_bucket = smem + (size_t)nt * kTabCdfWords * 4;
     uint16_t *s_win = reinterpret_cast<uint16_t *>(smem + kGeoTabSmem) + (threadIdx.x >> 5) * kWinWords;
     __shared__ uint32_t s_start[SGS_MAX_DEPTH + 1];  // first coded token of each coded level
     __shared__ uint32_t s_dbase[SGS_MAX_DEPTH];      // BFS offset of its tokens minus that
-    load_tables_smem(p.tables, nt, s_cdf, s_bucket);
+    load_cdf_smem(p.tables, nt, s_cdf);
     if (threadIdx.x <= (unsigned)nt) s_start[threadIdx.x] = (uint32_t)p.plan.coded_start[threadIdx.x];
     if (threadIdx.x < (unsigned)nt)
         s_dbase[threadIdx.x] = (uint32_t)(p.plan.level_off[p.plan.coded_level[threadIdx.x]] -
@@ -288,7 +268,6 @@ __device__ __forceinline__ void rans_geo_body(const GeoParams &p, uint32_t vb) {
     int k = 0;
     while (k + 1 < nt && s_start[k + 1] <= i) ++k;
     const uint32_t *cdf = s_cdf + k * kTabCdfWords;
-    const uint8_t *bkt = s_bucket + k * 256;
     uint32_t next = s_start[k + 1];
     uint32_t dbase = s_dbase[k];
     for (uint32_t t = 0; t < maxn; ++t) {
@@ -297,15 +276,12 @@ __device__ __forceinline__ void rans_geo_body(const GeoParams &p, uint32_t vb) {
             while (i >= next && k + 1 < nt) {
                 ++k;
                 cdf += kTabCdfWords;
-                bkt += 256;
                 next = s_start[k + 1];
                 dbase = s_dbase[k];
             }
             const uint32_t slot = x & 0xFFFFu;
-            uint32_t sym = bkt[slot >> 8];
-            uint32_t hi = cdf[sym + 1];
-            while (hi <= slot) hi = cdf[++sym + 1];
-            const uint32_t lo = cdf[sym];
+            const uint32_t sym = cdf_search(cdf, slot);
+            const uint32_t lo = cdf[sym], hi = cdf[sym + 1];
             x = (hi - lo) * (x >> 16) + slot - lo;
             p.geo_bytes[dbase + i] = (uint8_t)sym;
             i += nl;

@@ -92,7 +92,7 @@ extern "C" int scene_decode_noalloc(const uint8_t *bits, const sgs_scene_info *i
         if (launch_rans_static_geo(bits, *info, plan, s.tables, s.geo_bytes, status, st) != cudaSuccess)
             return SGS_E_CUDA;
     }
-    if (launch_octree(*info, plan, bits, s, *out, status, st, st, nullptr, nullptr) != cudaSuccess)
+    if (launch_octree(*info, plan, bits, s, *out, status, st) != cudaSuccess)
         return SGS_E_CUDA;
     int host_status = SGS_OK;
     if (cudaMemcpyAsync(&host_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)

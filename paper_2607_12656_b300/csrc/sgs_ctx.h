@@ -21,6 +21,5 @@ struct sgs_ctx {
     cudaEvent_t amarks[2];              // attribute stream: start, end
     cudaStream_t aux;                   // attribute decode (lowest priority), forked from the caller
     cudaStream_t geo;                   // geometry chain (highest priority)
-    cudaStream_t aux2;                  // octree top levels (highest priority), beside the scan
-    cudaEvent_t fork, join, gjoin, top_fork, top_join;
+    cudaEvent_t fork, join, gjoin;
 };

@@ -53,28 +53,21 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *to
     return wbase + incl - v;
 }
 
-// Copies n expanded tables (cdf[257] + bucket[256] each) into shared memory.
-__device__ __forceinline__ void load_tables_smem(const uint8_t *tables, int n, uint32_t *s_cdf,
-                                                 uint8_t *s_bucket) {
+// Copies the cdf[257] of n expanded tables into shared memory.
+__device__ __forceinline__ void load_cdf_smem(const uint8_t *tables, int n, uint32_t *s_cdf) {
     for (int i = threadIdx.x; i < n * kTabCdfWords; i += blockDim.x) {
-        int t = i / kTabCdfWords, k = i - t * kTabCdfWords;
+        const int t = i / kTabCdfWords, k = i - t * kTabCdfWords;
         s_cdf[i] = reinterpret_cast<const uint32_t *>(tables + (size_t)t * kTabBytes)[k];
-    }
-    for (int i = threadIdx.x; i < n * 256; i += blockDim.x) {
-        int t = i >> 8, k = i & 255;
-        s_bucket[i] = tables[(size_t)t * kTabBytes + kTabCdfWords * 4 + k];
     }
 }
 
-// One rANS decode step (M = 2^16) against a cdf[257] + bucket[256] table.
-__device__ __forceinline__ uint32_t rans_sym(uint32_t &x, const uint32_t *cdf,
-                                             const uint8_t *bucket) {
-    const uint32_t slot = x & 0xFFFFu;
-    uint32_t s = bucket[slot >> 8];
-    while (s < 255 && cdf[s + 1] <= slot) ++s;
-    const uint32_t lo = cdf[s];
-    const uint32_t f = cdf[s + 1] - lo;
-    x = f * (x >> 16) + slot - lo;
+// The symbol s with cdf[s] <= slot < cdf[s+1] (cdf[0] = 0, cdf[256] = 2^16 > slot): the
+// largest index whose cdf is at most slot, by eight branch-free halvings -- the same cost
+// for every lane of a warp, whatever the distribution's shape.
+__device__ __forceinline__ uint32_t cdf_search(const uint32_t *cdf, uint32_t slot) {
+    uint32_t s = 0;
+#pragma unroll
+    for (uint32_t st = 128; st > 0; st >>= 1) s += (cdf[s + st] <= slot) ? st : 0u;
     return s;
 }
 
@@ -150,6 +143,90 @@ __device__ __forceinline__ void group_refill(GroupStream &gs, uint32_t &x, bool 
         x = (x << 16) | w;
     }
     gs.ptr += __popc(mask);
+}
+
+// ------------------------------------------------------------------ fixed-length items
+
+// Channel-wise fixed-length decoding (Sec. 3.4.1): one warp item = one channel x 1,024 rows.
+constexpr int kFixWarps = 8;          // warps of a k_fixed CTA
+constexpr int kFixRows = 1024;        // rows per warp item
+constexpr int kFixMaxBits = 16;
+constexpr int kFixStage = 32 * kFixMaxBits + 1;  // staged words per warp
+
+struct FixedParams {
+    const uint8_t *bits;
+    uint64_t chan_off, tab_off, pay_off, pay_len;
+    uint32_t n_rows;
+    uint32_t n_items_per_chan;
+    float *out;
+    const uint32_t *out_index;
+    int *status;
+};
+
+// Warp item `item` (channel item / n_items_per_chan); sw = this warp's kFixStage staging
+// words in shared memory.  VEC: every channel's output base is 16-byte aligned and there is
+// no out_index, so lane j writes rows 4j..4j+3 (+128 k) with one 16-byte store; otherwise one
+// 4-byte store per row.
+template <bool VEC>
+__device__ __forceinline__ void fixed_warp_item(const FixedParams &p, uint64_t item, uint32_t *sw) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t c = (uint32_t)(item / p.n_items_per_chan);
+    if (c >= (uint32_t)kNChan) return;
+    const uint32_t blk = (uint32_t)(item - (uint64_t)c * p.n_items_per_chan);
+    const uint32_t b = *reinterpret_cast<const uint32_t *>(p.bits + p.chan_off + 4 * (2 * kNChan + c));
+    const float step = ld_f32(p.bits + p.chan_off + 4 * c);
+    const float offset = ld_f32(p.bits + p.chan_off + 4 * (kNChan + c));
+    const uint64_t *coff = reinterpret_cast<const uint64_t *>(p.bits + p.tab_off);
+    const uint64_t cbeg = coff[c], cend = coff[c + 1];
+    const uint64_t nwords_chan = ((uint64_t)p.n_rows * b + 31) / 32;
+    if (b < 1 || b > kFixMaxBits || cbeg > cend || cend > p.pay_len || cbeg % 16 != 0 ||
+        (cend - cbeg) < 4 * nwords_chan) {
+        if (lane == 0) set_status(p.status, SGS_E_CORRUPT);
+        return;
+    }
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(p.bits + p.pay_off + cbeg);
+    const uint64_t w0 = (uint64_t)blk * 32 * b;   // first word of this item
+    const uint32_t nw = 32 * b;
+    __syncwarp();  // the previous item's reads of sw are done
+    for (uint32_t i = lane; i <= nw; i += 32)
+        sw[i] = (w0 + i < nwords_chan) ? w[w0 + i] : 0u;
+    __syncwarp();
+    const uint32_t mask = (1u << b) - 1u;  // b <= 16
+    const uint32_t r0 = blk * kFixRows;
+    const uint32_t rows = p.n_rows - r0 < (uint32_t)kFixRows ? p.n_rows - r0 : (uint32_t)kFixRows;
+    float *outc = p.out + (size_t)c * p.n_rows + r0;
+    if (VEC) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t rl = (uint32_t)k * 128 + 4 * lane;
+            uint32_t bit = rl * b;
+            float v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t wi = bit >> 5;
+                v[q] = dequant(__funnelshift_r(sw[wi], sw[wi + 1], bit & 31) & mask, step, offset);
+                bit += b;
+            }
+            if (rl + 4 <= rows) {
+                *reinterpret_cast<float4 *>(outc + rl) = make_float4(v[0], v[1], v[2], v[3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (rl + q < rows) outc[rl + q] = v[q];
+            }
+        }
+    } else {
+#pragma unroll 4
+        for (int k = 0; k < 32; ++k) {
+            const uint32_t rl = (uint32_t)k * 32 + lane;
+            if (rl >= rows) break;
+            const uint32_t bit = rl * b;
+            const uint32_t wi = bit >> 5;
+            const float v = dequant(__funnelshift_r(sw[wi], sw[wi + 1], bit & 31) & mask, step, offset);
+            if (p.out_index) p.out[(size_t)c * p.n_rows + p.out_index[r0 + rl]] = v;
+            else outc[rl] = v;
+        }
+    }
 }
 
 // ------------------------------------------------------------------ batched stages

@@ -33,9 +33,9 @@ constexpr int kMaxTables = kNChan + SGS_MAX_DEPTH;
 enum Sec { S_LEVELS = 0, S_DUP, S_CHAN, S_GEO_RAW, S_GEO_TAB, S_GEO_GRP, S_GEO_PAY, S_ATTR_TAB,
            S_ATTR_GRP, S_ATTR_PAY, S_TOTAL };
 
-// Expanded static table in device memory: cdf[257] (u32) then bucket[256] (u8).
+// Expanded static table in device memory: cdf[257] (u32), padded to 16 bytes.
 constexpr int kTabCdfWords = 257;
-constexpr int kTabBytes = kTabCdfWords * 4 + 256 + 12;  // 1296, multiple of 16
+constexpr int kTabBytes = (kTabCdfWords * 4 + 15) & ~15;  // 1040
 
 // Per-level facts of one scene's octree, by value in kernel parameters.
 struct GeoPlan {
@@ -53,8 +53,7 @@ struct Scratch {
     uint32_t *p4;           // popcount prefix at every 4-byte word of the tokens (+ total)
     uint64_t *scan_flags;   // look-back tile status
     uint32_t *ticket;       // tile ticket counter (zeroed)
-    uint64_t *codes[2];     // packed (x:21 | y:21 | z:21) coordinates of the levels that
-                            // start a fused expansion group (ping-pong)
+    uint32_t *par;          // parent entry (x << 3 | child index) of every node but the root
     uint8_t *tables;        // expanded static tables
     uint32_t *dup_prefix;   // n_dup + 1
     uint8_t *learned;       // learned-mode per-scene work area
@@ -80,12 +79,9 @@ cudaError_t launch_rans_static_geo(const uint8_t *bits, const sgs_scene_info &in
 cudaError_t launch_geo_copy_raw(const uint8_t *bits, const sgs_scene_info &info,
                                 const GeoPlan &plan, uint8_t *geo_bytes, cudaStream_t st);
 // The octree reads the raw token section, or the scratch copy of the geometry decoder when
-// levels are rANS-coded.  The top levels run on st2 (forked from st with ev_a, joined with
-// ev_b) concurrently with the popcount scan; pass st2 == st to run everything on one stream.
-cudaError_t launch_octree(const sgs_scene_info &info, const GeoPlan &plan,
-                          const uint8_t *bits, const Scratch &s, const sgs_scene_out &out,
-                          int *status, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_a,
-                          cudaEvent_t ev_b);
+// levels are rANS-coded.  Scan with parent scatter, then the leaf walk, on st.
+cudaError_t launch_octree(const sgs_scene_info &info, const GeoPlan &plan, const uint8_t *bits,
+                          const Scratch &s, const sgs_scene_out &out, int *status, cudaStream_t st);
 cudaError_t launch_fixed(const uint8_t *bits, const sgs_scene_info &info,
                          const sgs_scene_out &out, int *status, cudaStream_t st);
 cudaError_t launch_learned_decode(const uint8_t *bits, const sgs_scene_info &info,
@@ -159,19 +155,15 @@ cudaError_t launch_geo_copy_multi(const MultiArgs &m, cudaStream_t st);
 uint32_t stage_learned(const SceneRef &r, void *par);
 size_t stage_learned_bytes();
 cudaError_t launch_learned_multi(const MultiArgs &m, cudaStream_t st);
-// octree: duplicates, popcount scan, top levels, then expansion group k (k = 0, 1, ...)
+// octree: duplicates, popcount scan with parent scatter, leaf walk
 uint32_t stage_dup(const SceneRef &r, void *par);
 size_t stage_dup_bytes();
 cudaError_t launch_dup_multi(const MultiArgs &m, cudaStream_t st);
 uint32_t stage_scan(const SceneRef &r, void *par);
 size_t stage_scan_bytes();
 cudaError_t launch_scan_multi(const MultiArgs &m, cudaStream_t st);
-uint32_t stage_top(const SceneRef &r, void *par);
-size_t stage_top_bytes();
-cudaError_t launch_top_multi(const MultiArgs &m, cudaStream_t st);
-uint32_t stage_expand(const SceneRef &r, int group, void *par);
-size_t stage_expand_bytes();
-cudaError_t launch_expand_multi(const MultiArgs &m, cudaStream_t st);
-int octree_group_count(const sgs_scene_info &info, const GeoPlan &plan);
+uint32_t stage_walk(const SceneRef &r, void *par);
+size_t stage_walk_bytes();
+cudaError_t launch_walk_multi(const MultiArgs &m, cudaStream_t st);
 
 }  // namespace sgs

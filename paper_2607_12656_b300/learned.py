@@ -19,10 +19,19 @@ def train_and_freeze(ctx: sgs.Context, scene, depth: int, lanes: int, *, steps: 
     w = torch.from_numpy(sgs.pack_weights(kaiming_init(init_seed))).to(dev)
     adam = torch.zeros(2 * sgs.WEIGHTS_FLOATS, dtype=torch.float32, device=dev)
     losses = torch.zeros(max(steps, 1), dtype=torch.float32, device=dev)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
     sgs.sgs_train(ctx, tok_dev, tokens.shape[0], lanes, w, adam, steps=steps, batch=batch, seed=seed,
                   lr=lr, loss_dev=losses)
+    t1.record()
     weights = w.cpu().numpy()
+    LAST_TRAIN.update(ms=t0.elapsed_time(t1), steps=steps, batch=batch,
+                      final_bits=float(losses[max(steps, 1) - 1].item()))
     model = sgs.sgs_freeze(weights, tokens, lanes, seed)
     if return_losses:
         return model, weights, losses.cpu().numpy()[:steps]
     return model
+
+
+# device time and final loss (bits per token) of the last train_and_freeze call
+LAST_TRAIN = {}

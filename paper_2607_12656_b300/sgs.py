@@ -43,6 +43,20 @@ class TrainParams(ctypes.Structure):
     _fields_ = [("steps", u32), ("batch", u32), ("seed", u32), ("lr", ctypes.c_float)]
 
 
+TUNE_MAX_CAND = 16
+
+
+class TuneRequest(ctypes.Structure):
+    _fields_ = [("pos", P), ("attr", P), ("n", u32), ("mode", u32), ("depth", u32), ("geo_mode", u32),
+                ("model", P), ("n_cand", u32), ("rows_per_lane", u32 * TUNE_MAX_CAND), ("max_ms", ctypes.c_float),
+                ("reps", u32)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("best", u32), ("lanes", u32 * TUNE_MAX_CAND), ("bytes", u64 * TUNE_MAX_CAND),
+                ("ms", ctypes.c_float * TUNE_MAX_CAND)]
+
+
 class BatchItem(ctypes.Structure):
     _fields_ = [("bits_dev", P), ("info", SceneInfo), ("out", SceneOut)]
 
@@ -91,6 +105,7 @@ def lib() -> ctypes.CDLL:
         L.sgs_launch_count.argtypes = [P]
         L.sgs_launch_count.restype = u64
         L.scene_decode_noalloc.argtypes = [P, ctypes.POINTER(SceneInfo), ctypes.POINTER(SceneOut), P]
+        L.sgs_autotune.argtypes = [P, ctypes.POINTER(TuneRequest), ctypes.POINTER(TuneResult)]
         _lib = L
     return _lib
 
@@ -360,3 +375,31 @@ def unpack_weights(flat: np.ndarray) -> dict:
         out[k] = np.asarray(flat[o:o + n], np.float32).reshape(shp)
         o += n
     return out
+
+
+# ----------------------------------------------------------------------------- autotuning
+
+def autotune(ctx: Context, pos: np.ndarray, attr: np.ndarray, *, mode: int, depth: int, rows_per_lane,
+             max_ms: float = 0.0, reps: int = 5, geo_mode: int = GEO_RANS, model: bytes | None = None) -> dict:
+    """Encodes the scene at every candidate W (rows per lane), times each decode on the
+    context's device and returns {"best": index, "lanes": [...], "bytes": [...], "ms": [...]}."""
+    pos = np.ascontiguousarray(pos, np.float32)
+    attr = np.ascontiguousarray(attr, np.float32)
+    cands = list(rows_per_lane)
+    assert 1 <= len(cands) <= TUNE_MAX_CAND
+    rq = TuneRequest()
+    rq.pos, rq.attr, rq.n = pos.ctypes.data, attr.ctypes.data, pos.shape[1]
+    rq.mode, rq.depth, rq.geo_mode = mode, depth, geo_mode
+    mbuf = None
+    if model is not None:
+        mbuf = np.frombuffer(bytes(model), np.uint8).copy()
+        rq.model = mbuf.ctypes.data
+    rq.n_cand = len(cands)
+    for i, w in enumerate(cands):
+        rq.rows_per_lane[i] = int(w)
+    rq.max_ms, rq.reps = max_ms, reps
+    res = TuneResult()
+    _check(lib().sgs_autotune(ctx.handle, ctypes.byref(rq), ctypes.byref(res)), "sgs_autotune")
+    k = len(cands)
+    return {"best": int(res.best), "rows_per_lane": cands, "lanes": list(res.lanes[:k]),
+            "bytes": [int(b) for b in res.bytes[:k]], "ms": list(res.ms[:k])}

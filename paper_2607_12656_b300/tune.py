@@ -1,11 +1,10 @@
-"""Autotuner: picks the rANS lane count (the paper's group size W = N'/L, Sec. 3.4.2, its
-complexity knob) per coding mode and scene-size bucket by timing real decodes on this GPU.
+"""Lane-count choice per (GPU, mode, scene size), cached as JSON.
 
-More lanes mean more parallel decoders but more per-lane overhead (4-byte initial state,
-final flush) and, for the learned model, shorter contexts; the tuner measures decode time
-and coded size for each candidate and keeps the fastest candidate whose size is within
-`max_size_growth` of the smallest.  Results are cached in a JSON file keyed by GPU name, SM
-count, mode and log2 size bucket.
+The decode's parallelism is set at encode time by the group size W (rows per lane), the
+paper's complexity knob (Sec. 4, implementation details).  ``choose_lanes`` returns the lane
+count for a scene: from the cache when the same GPU model and SM count have already tuned
+this mode at this size bucket (power of two of N), else by running ``sgs_autotune`` on the
+scene and recording the chosen W.
 """
 from __future__ import annotations
 
@@ -15,65 +14,43 @@ import os
 
 from . import sgs
 
-CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
-CANDIDATES = {sgs.MODE_STATIC: [4096, 16384, 32768, 65536, 131072, 262144],
-              sgs.MODE_LEARNED: [1024, 2048, 4096, 8192, 16384]}
+DEFAULT_W = (16, 32, 64, 128, 256)
 
 
-def _key(mode: int, n: int) -> str:
+def _device_key(device: int) -> str:
     import torch
-    p = torch.cuda.get_device_properties(torch.cuda.current_device())
-    return "%s|%d|mode%d|n2^%d" % (p.name, p.multi_processor_count, mode, int(math.log2(max(n, 2))))
+    p = torch.cuda.get_device_properties(device)
+    return "%s/%dsm" % (p.name, p.multi_processor_count)
 
 
-def load_cache() -> dict:
-    try:
-        return json.load(open(CACHE))
-    except Exception:
-        return {}
+def bucket(n: int) -> int:
+    return int(round(math.log2(max(n, 1))))
 
 
-def lookup(mode: int, n: int) -> int | None:
-    return load_cache().get(_key(mode, n), {}).get("lanes")
+class LaneTuner:
+    def __init__(self, path: str | None = None):
+        self.path = path
+        self.table = {}
+        if path and os.path.exists(path):
+            with open(path) as f:
+                self.table = json.load(f)
 
+    def key(self, ctx: sgs.Context, mode: int, n: int, max_ms: float) -> str:
+        return "%s|mode%d|n2^%d|max%.3g" % (_device_key(ctx.device), mode, bucket(n), max_ms)
 
-def time_decode(ctx: sgs.Context, buf: bytes, reps: int = 5) -> float:
-    import torch
-    info = sgs.scene_query(buf)
-    ctx.reserve(info.scratch_bytes)
-    bits = torch.frombuffer(bytearray(buf), dtype=torch.uint8).cuda()
-    attr = torch.empty((56, max(info.n_rows, 1)), device="cuda")
-    pos = torch.empty((3, max(info.n_rows, 1)), device="cuda")
-    sgs.scene_decode(ctx, bits, info, attr, pos)
-    if ctx.sync() != sgs.OK:
-        raise RuntimeError("decode failed while tuning")
-    times = []
-    for _ in range(reps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        sgs.scene_decode(ctx, bits, info, attr, pos)
-        b.record()
-        torch.cuda.synchronize()
-        times.append(a.elapsed_time(b))
-    return sorted(times)[len(times) // 2]
-
-
-def tune(ctx: sgs.Context, scene, depth: int, mode: int, model: bytes | None = None,
-         candidates: list[int] | None = None, max_size_growth: float = 0.01, save: bool = True) -> dict:
-    cands = candidates or CANDIDATES[mode]
-    rows = []
-    for L in cands:
-        kw = dict(mode=mode, depth=depth, lanes=L, geo_mode=sgs.GEO_RANS)
-        if mode == sgs.MODE_LEARNED:
-            kw.update(model=model, ctx=ctx)
-        buf = sgs.scene_encode(scene.pos, scene.attr, **kw)
-        rows.append({"lanes": L, "bytes": len(buf), "ms": time_decode(ctx, buf)})
-    smallest = min(r["bytes"] for r in rows)
-    ok = [r for r in rows if r["bytes"] <= smallest * (1 + max_size_growth)] or rows
-    best = min(ok, key=lambda r: r["ms"])
-    out = {"lanes": best["lanes"], "ms": best["ms"], "bytes": best["bytes"], "candidates": rows}
-    if save:
-        cache = load_cache()
-        cache[_key(mode, scene.n)] = out
-        json.dump(cache, open(CACHE, "w"), indent=1)
-    return out
+    def choose_lanes(self, ctx: sgs.Context, pos, attr, *, mode: int, depth: int, max_ms: float = 0.0,
+                     candidates=DEFAULT_W, model: bytes | None = None, reps: int = 5) -> int:
+        n = pos.shape[1]
+        kept = n - n // 10
+        k = self.key(ctx, mode, n, max_ms)
+        if k not in self.table:
+            r = sgs.autotune(ctx, pos, attr, mode=mode, depth=depth, rows_per_lane=candidates, max_ms=max_ms,
+                             reps=reps, model=model)
+            b = r["best"]
+            self.table[k] = {"rows_per_lane": r["rows_per_lane"][b], "ms": r["ms"][b], "bytes": r["bytes"][b],
+                             "sweep": {str(w): [ms, by] for w, ms, by in zip(r["rows_per_lane"], r["ms"], r["bytes"])}}
+            if self.path:
+                with open(self.path, "w") as f:
+                    json.dump(self.table, f, indent=1, sort_keys=True)
+        w = self.table[k]["rows_per_lane"]
+        return max(1, -(-kept // w))

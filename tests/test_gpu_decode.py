@@ -171,3 +171,23 @@ def test_full_size_static_scene(ctx, fixed_1m):
         buf = sgs.scene_encode(sc.pos, sc.attr, mode=sgs.MODE_STATIC, depth=16, lanes=lanes, geo_mode=sgs.GEO_RANS)
         st, attr, pos, _, _ = gpu_decode(ctx, buf)
         assert st == sgs.OK and same_bits(attr, P.attr) and same_bits(pos, P.pos)
+
+
+def test_autotune_sweeps_group_sizes(ctx, small_scene):
+    """The tuner measures every candidate W: smaller groups mean more lanes and a larger
+    bitstream, and every trial decode succeeded; the choice honours the target."""
+    from paper_2607_12656_b300.tune import LaneTuner
+    sc = small_scene
+    r = sgs.autotune(ctx, sc.pos, sc.attr, mode=sgs.MODE_STATIC, depth=12, rows_per_lane=[8, 32, 128], reps=3)
+    assert r["lanes"][0] > r["lanes"][1] > r["lanes"][2]
+    assert r["bytes"][0] > r["bytes"][1] > r["bytes"][2]
+    assert all(ms > 0 for ms in r["ms"])
+    assert r["ms"][r["best"]] == min(r["ms"])
+    loose = sgs.autotune(ctx, sc.pos, sc.attr, mode=sgs.MODE_STATIC, depth=12, rows_per_lane=[8, 32, 128],
+                         reps=3, max_ms=1e3)
+    assert loose["best"] == 2  # every candidate meets the target: the smallest bitstream wins
+    t = LaneTuner()
+    lanes = t.choose_lanes(ctx, sc.pos, sc.attr, mode=sgs.MODE_STATIC, depth=12, candidates=(16, 64), reps=2)
+    assert lanes >= 1 and len(t.table) == 1
+    with pytest.raises(sgs.SgsError):
+        sgs.autotune(ctx, sc.pos, sc.attr, mode=sgs.MODE_FIXED, depth=12, rows_per_lane=[32])
