@@ -64,8 +64,7 @@ size_t scratch_need(const sgs_scene_info &info, Scratch *s, uint8_t *base) {
     Scratch t;
     t.geo_bytes = take(info.geo_mode == SGS_GEO_RANS ? info.n_geo : 0);
     t.p4 = reinterpret_cast<uint32_t *>(take(4 * (octree_words(info.n_geo) + 16)));
-    t.scan_flags = reinterpret_cast<uint64_t *>(take(8 * (octree_scan_tiles(info.n_geo) + 1)));
-    t.ticket = reinterpret_cast<uint32_t *>(take(256));
+    t.tile_sums = reinterpret_cast<uint32_t *>(take(4 * (octree_scan_tiles(info.n_geo) + 1)));
     t.par = reinterpret_cast<uint32_t *>(take(info.n_rows ? 4ull * (info.n_geo + info.n_leaves) : 0));
     const int n_tab = plan.n_coded_levels + (info.mode == SGS_MODE_STATIC ? kNChan : 0);
     t.tables = take((uint64_t)n_tab * kTabBytes);
@@ -318,9 +317,6 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
         if (c->profile && c->n_marks <= kMaxStages) cudaEventRecord(c->marks[c->n_marks++], st);
     };
     mark();
-    // zero the look-back flags and ticket (adjacent regions)
-    const size_t zbytes = (uint8_t *)s.ticket + 256 - (uint8_t *)s.scan_flags;
-    if ((e = cudaMemsetAsync(s.scan_flags, 0, zbytes, st)) != cudaSuccess) return SGS_E_CUDA;
     if (info.n_tables) {
         c->launches += 1;
         e = launch_tables(bits, info, plan.n_coded_levels, s.tables, status, st);

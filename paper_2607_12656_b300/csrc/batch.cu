@@ -9,8 +9,7 @@
 // coding mode; raw geometry copy, geometry tokens, duplicate prefix; popcount scan with the
 // parent scatter; leaf walk -- enqueued without allocation or host synchronisation, so a
 // run can be captured in a CUDA graph.  Each launch
-// is a grid of resident CTAs that claim items from an atomic counter in increasing order
-// (which keeps the scan's look-back waiting only on tiles that already started).
+// is a grid of resident CTAs that claim items from an atomic counter in increasing order.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -88,7 +87,7 @@ uint32_t stage_items(Kind k, int variant, const SceneRef &r, void *par) {
         case K_COPY: return stage_geo_copy(r, par);
         case K_GEO: return stage_rans_geo(r, par);
         case K_DUP: return stage_dup(r, par);
-        case K_SCAN: return stage_scan(r, par);
+        case K_SCAN: return stage_scan(r, variant, par);
         default: return stage_walk(r, par);
     }
 }
@@ -102,7 +101,7 @@ cudaError_t launch_kind(Kind k, int variant, const MultiArgs &m, cudaStream_t st
         case K_COPY: return launch_geo_copy_multi(m, st);
         case K_GEO: return launch_rans_geo_multi(m, st);
         case K_DUP: return launch_dup_multi(m, st);
-        case K_SCAN: return launch_scan_multi(m, st);
+        case K_SCAN: return launch_scan_multi(variant, m, st);
         default: return launch_walk_multi(m, st);
     }
 }
@@ -117,9 +116,9 @@ __global__ void k_status_fold(const int *status, int n, int *out) {
 }  // namespace
 
 // Device layout of a plan, from `base`:
-//   scene scratch (each a256) | counters[kMaxLaunches] | status[n] | scan flags of every scene
-//   | prefix lists | parameter lists
-// The span from the counters to the end of the flags is zeroed by every run.
+//   scene scratch (each a256) | counters[kMaxLaunches] | status[n] | prefix lists | parameter
+//   lists
+// The counters and status words are zeroed by every run.
 struct BatchLayout {
     std::vector<Scratch> scratch;
     std::vector<GeoPlan> plans;
@@ -148,10 +147,6 @@ static int build_layout(const sgs_batch_item *items, int n, uint8_t *base, Batch
     off += a256(4ull * kMaxLaunches);
     L->status_off = off;
     off += a256(4ull * (n > 0 ? n : 1));
-    for (int i = 0; i < n; ++i) {  // look-back flags of every scene, in the zeroed span
-        L->scratch[i].scan_flags = reinterpret_cast<uint64_t *>(base ? base + off : nullptr);
-        off += a256(8 * (octree_scan_tiles(items[i].info.n_geo) + 1));
-    }
     L->zero_bytes = off - L->zero_off;
     L->lists_off = off;
     std::vector<SceneRef> refs(n);
@@ -203,7 +198,9 @@ static int build_layout(const sgs_batch_item *items, int n, uint8_t *base, Batch
     if (rc == SGS_OK) rc = add(K_COPY, 0, R_GEO);
     if (rc == SGS_OK) rc = add(K_GEO, 0, R_GEO);
     if (rc == SGS_OK) rc = add(K_DUP, 0, R_GEO);
-    if (rc == SGS_OK) rc = add(K_SCAN, 0, R_GEO);
+    if (rc == SGS_OK) rc = add(K_SCAN, 1, R_GEO);  // tile sums
+    if (rc == SGS_OK) rc = add(K_SCAN, 0, R_GEO);  // prefixes
+    if (rc == SGS_OK) rc = add(K_SCAN, 2, R_GEO);  // parent entries
     if (rc == SGS_OK) rc = add(K_WALK, 0, R_GEO);
     if (rc != SGS_OK) return rc;
     L->total = a256(L->lists_off + L->lists.size());

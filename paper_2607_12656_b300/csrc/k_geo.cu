@@ -6,8 +6,8 @@
 // for h < x, the children of node x are the nodes 1 + P(x) + j (j < popc(B[x])), the j-th
 // taking child index k = the j-th set bit of B[x]; leaves are numbered after the internal
 // nodes.  Two launches decode the tree without any level-by-level synchronisation:
-//   1. a device-wide scan of popcounts (decoupled look-back) that, as soon as a tile knows
-//      P(x), writes every child's parent entry par[1 + P(x) + j] = x << 3 | k;
+//   1. a device-wide scan of popcounts (reduce, then scan), then a map over the nodes that
+//      writes every child's parent entry par[1 + P(x) + j] = x << 3 | k;
 //   2. a walk from every leaf up to the root (D dependent loads of par), assembling the
 //      leaf's coordinates one bit per level, then writing its position rows.
 // The level counts in the header are checked against P (the children of each level are
@@ -22,7 +22,6 @@
 namespace sgs {
 
 constexpr int kScanThreads = 256;
-constexpr uint32_t kSpinLimit = 1u << 22;          // bounded look-back wait
 constexpr int kWalkThreads = 256;
 constexpr int kWalkIlp = 8;                        // leaves a thread walks together
 constexpr uint32_t kWalkLeaves = kWalkThreads * kWalkIlp;  // leaves per CTA
@@ -87,37 +86,24 @@ __device__ __forceinline__ uint32_t word_at(const uint8_t *B, uint64_t n, uint64
     return w;
 }
 
-// P4[k] = popcount of B[0, 4k) for k = 0 .. ceil(n/4).  Tile = 256 threads x 64 bytes.
-// Tiles must start in increasing order: a tile's look-back waits only on tiles that started
-// before it (the single-scene kernel draws tiles from a ticket, the batched one claims items
-// in order).
+// P4[k] = popcount of B[0, 4k) for k = 0 .. ceil(n/4), as a reduce-then-scan over tiles of
+// 256 threads x 64 bytes: k_octree_reduce writes each tile's popcount sum, then
+// k_octree_scan gives each tile the sum of the tiles before it (a block-wide sum of their
+// sums) and scans inside the tile to write P4.  No tile ever waits on another.
 struct ScanParams {
     const uint8_t *B;
     uint64_t n, n_words;
     uint32_t *P4;
     uint32_t *par;             // parent entries x << 3 | k of nodes 1 .. total-1
-    uint64_t *flags;
-    uint32_t *ticket;
+    uint32_t *tile_sums;       // one popcount sum per tile
     int *status;
     int depth;
     uint32_t level_off[SGS_MAX_DEPTH + 2];  // [D + 1] = total node count
 };
 
-__device__ __forceinline__ void scan_body(const ScanParams &sp, uint32_t tile) {
-    __shared__ uint32_t sm[8];
-    __shared__ uint32_t s_prefix;
-    // the tile's token words and P at each, word w at w + w / 16 (padded: conflict-free)
-    __shared__ uint32_t sm_words[kScanThreads * 17];
-    __shared__ uint32_t sm_pref[kScanThreads * 17];
-    const uint8_t *B = sp.B;
-    const uint64_t n = sp.n, n_words = sp.n_words;
-    uint32_t *P4 = sp.P4;
-    uint64_t *flags = sp.flags;
-    int *status = sp.status;
-    const uint64_t k = (uint64_t)tile * kScanThreads + threadIdx.x;  // 64-byte chunk
-    const uint64_t w0 = 16 * k;                                      // its first word
-    uint32_t wd[16];  // the chunk's words (bytes at or past n cleared)
-    uint32_t sum = 0;
+// The tile's 16 words per thread (bytes at or past n cleared).
+__device__ __forceinline__ void tile_words(const uint8_t *B, uint64_t n, uint64_t k, uint32_t (&wd)[16]) {
+    const uint64_t w0 = 16 * k;
     if (64 * k + 64 <= n) {
         const uint4 *p = reinterpret_cast<const uint4 *>(B + 64 * k);
 #pragma unroll
@@ -132,102 +118,59 @@ __device__ __forceinline__ void scan_body(const ScanParams &sp, uint32_t tile) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) wd[i] = (w0 + i) * 4 < n ? word_at(B, n, w0 + i) : 0u;
     }
+}
+
+__device__ __forceinline__ void reduce_body(const ScanParams &sp, uint32_t tile) {
+    __shared__ uint32_t sm[8];
+    uint32_t wd[16];
+    tile_words(sp.B, sp.n, (uint64_t)tile * kScanThreads + threadIdx.x, wd);
+    uint32_t sum = 0;
 #pragma unroll
     for (int i = 0; i < 16; ++i) sum += __popc(wd[i]);
+    uint32_t tot;
+    block_excl_scan_256(sum, &tot, sm);
+    if (threadIdx.x == 0) sp.tile_sums[tile] = tot;
+}
+
+__device__ __forceinline__ void scan_body(const ScanParams &sp, uint32_t tile) {
+    __shared__ uint32_t sm[8];
+    __shared__ uint32_t sm_p4[kScanThreads * 17];
+    const uint64_t n = sp.n, n_words = sp.n_words;
+    const uint64_t k = (uint64_t)tile * kScanThreads + threadIdx.x;  // 64-byte chunk
+    uint32_t wd[16];
+    tile_words(sp.B, n, k, wd);
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) sum += __popc(wd[i]);
+    // tiles before this one
+    uint32_t before = 0;
+    for (uint32_t t = threadIdx.x; t < tile; t += kScanThreads) before += sp.tile_sums[t];
+    uint32_t prefix;
+    block_excl_scan_256(before, &prefix, sm);
     uint32_t agg;
     const uint32_t local = block_excl_scan_256(sum, &agg, sm);
-    // decoupled look-back, 32 predecessors per step (flag 1 = aggregate, 2 = inclusive prefix)
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        volatile unsigned long long *vf = reinterpret_cast<volatile unsigned long long *>(flags);
-        if (lane == 0) {
-            vf[tile] = ((tile == 0 ? 2ull : 1ull) << 32) | agg;
-            __threadfence();
-        }
-        uint32_t prefix = 0;
-        int64_t hi = (int64_t)tile - 1;  // newest predecessor not yet summed
-        uint32_t spins = 0;
-        while (hi >= 0) {
-            const int64_t idx = hi - lane;
-            unsigned long long v = idx >= 0 ? vf[idx] : (2ull << 32);
-            while (__any_sync(0xffffffffu, (v >> 32) == 0)) {
-                if (++spins > kSpinLimit) break;
-                __nanosleep(32);
-                if ((v >> 32) == 0) v = vf[idx];
-            }
-            if (spins > kSpinLimit) {
-                if (lane == 0) set_status(status, SGS_E_TIMEOUT);
-                break;
-            }
-            const uint32_t incl = __ballot_sync(0xffffffffu, (v >> 32) == 2);
-            const int stop = incl ? __ffs(incl) - 1 : 31;  // lanes 0..stop contribute
-            uint32_t val = (lane <= stop) ? (uint32_t)v : 0u;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
-            prefix += val;
-            if (incl) break;
-            hi -= 32;
-        }
-        if (lane == 0) {
-            if (tile != 0) {
-                __threadfence();
-                vf[tile] = (2ull << 32) | (uint64_t)(prefix + agg);
-            }
-            s_prefix = prefix;
-        }
-    }
-    __syncthreads();
-    const uint32_t base = s_prefix + local;  // P(4 w0)
+    const uint32_t base = prefix + local;  // P at this thread's first word
+    // P4 of the tile's 4096 words through shared memory (word w at w + w / 16: conflict-free),
+    // then written out contiguously
     uint32_t run = base;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        if (w0 + i <= n_words) P4[w0 + i] = run;  // P4[n_words] = total
+        sm_p4[17 * threadIdx.x + i] = run;
         run += __popc(wd[i]);
     }
-    // parent entries of the children of the tile's nodes, written in rounds where lane i
-    // takes node base + 256 r + i, so a warp's children entries are contiguous: the words
-    // and their prefixes go through shared memory
-    {
-        uint32_t r = base;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            sm_words[17 * threadIdx.x + i] = wd[i];
-            sm_pref[17 * threadIdx.x + i] = r;
-            r += __popc(wd[i]);
-        }
-    }
     __syncthreads();
-    const uint64_t tile_x = (uint64_t)tile * kScanThreads * 64;  // first node of the tile
-    if (tile_x >= n) return;
-    uint64_t x = tile_x + threadIdx.x;
-    int l = 0;
-    while (l < sp.depth && sp.level_off[l + 1] <= x) ++l;
-    for (int r = 0; r < 64; ++r, x += kScanThreads) {
-        if (x >= n) break;
-        while (l < sp.depth && sp.level_off[l + 1] <= x) ++l;
-        const uint32_t xl = (uint32_t)(x - tile_x), wi = (xl >> 2) + (xl >> 6);
-        const uint32_t w = sm_words[wi], sh = 8u * (xl & 3u);
-        uint32_t byte = (w >> sh) & 0xFFu;
-        uint32_t y = 1u + sm_pref[wi] + __popc(w & ((1u << sh) - 1u));
-        const uint32_t lo = sp.level_off[l + 1], hi = sp.level_off[l + 2];
-        while (byte) {
-            const uint32_t kc = __ffs(byte) - 1;
-            byte &= byte - 1;
-            if (y < lo || y >= hi) {
-                set_status(status, SGS_E_CORRUPT);
-                break;
-            }
-            sp.par[y] = ((uint32_t)x << 3) | kc;
-            ++y;
-        }
-    }
+    const uint64_t tw = (uint64_t)tile * kScanThreads * 16;  // the tile's first word
+#pragma unroll 4
+    for (uint32_t j = threadIdx.x; j < kScanThreads * 16; j += kScanThreads)
+        if (tw + j <= n_words) sp.P4[tw + j] = sm_p4[j + (j >> 4)];  // P4[n_words] = total
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_octree_scan(ScanParams p) {
-    __shared__ uint32_t s_tile;
-    if (threadIdx.x == 0) s_tile = atomicAdd(p.ticket, 1u);
-    __syncthreads();
-    scan_body(p, s_tile);
+__global__ void __launch_bounds__(kScanThreads) k_octree_reduce(ScanParams p) { reduce_body(p, blockIdx.x); }
+
+__global__ void __launch_bounds__(kScanThreads) k_octree_scan(ScanParams p) { scan_body(p, blockIdx.x); }
+
+__global__ void __launch_bounds__(kScanThreads) k_octree_reduce_multi(MultiArgs m) {
+    run_items<ScanParams>(m, [](const ScanParams &p, uint32_t vb, uint32_t, bool) { reduce_body(p, vb); });
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_octree_scan_multi(MultiArgs m) {
@@ -241,6 +184,50 @@ __device__ __forceinline__ void node_at(const uint8_t *B, uint64_t n, const uint
     const uint32_t sh = 8u * (uint32_t)(x & 3);
     byte = (w >> sh) & 0xFFu;
     p = P4[x >> 2] + __popc(w & ((1u << sh) - 1u));
+}
+
+// Parent entries: node x's j-th child (child index k = the j-th set bit of B[x]) is node
+// 1 + P(x) + j, and gets par = x << 3 | k.  A map over the nodes, kScatterIlp per thread with
+// their loads issued first; consecutive threads take consecutive nodes, whose children are
+// consecutive, so the stores coalesce.  A child index past the last node marks the stream
+// corrupt; that each level's children are exactly the next level is checked by the walk.
+constexpr int kScatterIlp = 4;
+constexpr uint32_t kScatterNodes = kScanThreads * kScatterIlp;
+
+__device__ __forceinline__ void scatter_body(const ScanParams &sp, uint32_t vb) {
+    const uint32_t total = sp.level_off[sp.depth + 1];
+    uint32_t byte[kScatterIlp], y[kScatterIlp];
+#pragma unroll
+    for (int q = 0; q < kScatterIlp; ++q) {
+        const uint32_t x = vb * kScatterNodes + q * kScanThreads + threadIdx.x;
+        byte[q] = 0;
+        y[q] = 0;
+        if (x < sp.n) {
+            node_at(sp.B, sp.n, sp.P4, x, byte[q], y[q]);
+            ++y[q];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kScatterIlp; ++q) {
+        const uint32_t x = vb * kScatterNodes + q * kScanThreads + threadIdx.x;
+        uint32_t b = byte[q], yy = y[q];
+        while (b) {
+            const uint32_t kc = __ffs(b) - 1;
+            b &= b - 1;
+            if (yy >= total) {
+                set_status(sp.status, SGS_E_CORRUPT);
+                break;
+            }
+            sp.par[yy] = (x << 3) | kc;
+            ++yy;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_octree_scatter(ScanParams p) { scatter_body(p, blockIdx.x); }
+
+__global__ void __launch_bounds__(kScanThreads) k_octree_scatter_multi(MultiArgs m) {
+    run_items<ScanParams>(m, [](const ScanParams &p, uint32_t vb, uint32_t, bool) { scatter_body(p, vb); });
 }
 
 // ------------------------------------------------------------------ duplicates
@@ -420,12 +407,15 @@ static uint32_t make_scan(const uint8_t *bits, const sgs_scene_info &info, const
     p.n_words = (info.n_geo + 3) / 4;
     p.P4 = s.p4;
     p.par = s.par;
-    p.flags = s.scan_flags;
-    p.ticket = s.ticket;
+    p.tile_sums = s.tile_sums;
     p.status = status;
     p.depth = plan.depth;
     level_offsets(info, plan, p.level_off);
     return octree_work(info) ? (uint32_t)octree_scan_tiles(info.n_geo) : 0;
+}
+
+static uint32_t scatter_blocks(const sgs_scene_info &info) {
+    return (uint32_t)((info.n_geo + kScatterNodes - 1) / kScatterNodes);
 }
 
 static uint32_t make_walk(const uint8_t *bits, const sgs_scene_info &info, const GeoPlan &plan,
@@ -459,7 +449,11 @@ cudaError_t launch_octree(const sgs_scene_info &info, const GeoPlan &plan, const
     }
     ScanParams sp;
     const uint32_t tiles = make_scan(bits, info, plan, s, status, &sp);
+    k_octree_reduce<<<tiles, kScanThreads, 0, st>>>(sp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_octree_scan<<<tiles, kScanThreads, 0, st>>>(sp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_octree_scatter<<<scatter_blocks(info), kScanThreads, 0, st>>>(sp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     WalkParams wp;
     const uint32_t blocks = make_walk(bits, info, plan, s, out, status, &wp);
@@ -480,14 +474,16 @@ cudaError_t launch_dup_multi(const MultiArgs &m, cudaStream_t st) {
     return launch_persistent(k_dup_multi, 256, 0, m, st);
 }
 
-uint32_t stage_scan(const SceneRef &r, void *par) {
+uint32_t stage_scan(const SceneRef &r, int variant, void *par) {
     ScanParams p;
     const uint32_t n = make_scan(r.bits, *r.info, *r.plan, *r.s, r.status, &p);
     memcpy(par, &p, sizeof(p));
-    return n;
+    return (variant == 2 && n) ? scatter_blocks(*r.info) : n;
 }
 size_t stage_scan_bytes() { return sizeof(ScanParams); }
-cudaError_t launch_scan_multi(const MultiArgs &m, cudaStream_t st) {
+cudaError_t launch_scan_multi(int variant, const MultiArgs &m, cudaStream_t st) {
+    if (variant == 1) return launch_persistent(k_octree_reduce_multi, kScanThreads, 0, m, st);
+    if (variant == 2) return launch_persistent(k_octree_scatter_multi, kScanThreads, 0, m, st);
     return launch_persistent(k_octree_scan_multi, kScanThreads, 0, m, st);
 }
 
@@ -503,7 +499,7 @@ cudaError_t launch_walk_multi(const MultiArgs &m, cudaStream_t st) {
 }
 
 // Kernels launch_octree enqueues for a non-empty scene.
-int octree_launches(const sgs_scene_info &info, const GeoPlan &) { return (info.n_dup ? 1 : 0) + 2; }
+int octree_launches(const sgs_scene_info &info, const GeoPlan &) { return (info.n_dup ? 1 : 0) + 4; }
 
 // Scan tiles: every 64-byte chunk up to the one holding word n_words (whose P4 entry is the
 // total), 256 chunks per tile.

@@ -73,10 +73,9 @@ extern "C" int scene_decode_noalloc(const uint8_t *bits, const sgs_scene_info *i
     scratch_need(*info, &s, base);
     GeoPlan plan;
     make_geo_plan(*info, &plan);
-    // the array keeps the previous call's contents: clear the status, look-back flags, ticket
+    // the array keeps the previous call's contents: clear the status word (nothing else
+    // needs to start at zero)
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return SGS_E_CUDA;
-    const size_t zbytes = (uint8_t *)s.ticket + 256 - (uint8_t *)s.scan_flags;
-    if (cudaMemsetAsync(s.scan_flags, 0, zbytes, st) != cudaSuccess) return SGS_E_CUDA;
     if (launch_tables(bits, *info, plan.n_coded_levels, s.tables, status, st) != cudaSuccess)
         return SGS_E_CUDA;
     uint8_t *attr_tables = s.tables + (size_t)plan.n_coded_levels * kTabBytes;

@@ -51,8 +51,7 @@ struct GeoPlan {
 struct Scratch {
     uint8_t *geo_bytes;     // n_geo (rANS geometry only)
     uint32_t *p4;           // popcount prefix at every 4-byte word of the tokens (+ total)
-    uint64_t *scan_flags;   // look-back tile status
-    uint32_t *ticket;       // tile ticket counter (zeroed)
+    uint32_t *tile_sums;    // popcount sum of each scan tile
     uint32_t *par;          // parent entry (x << 3 | child index) of every node but the root
     uint8_t *tables;        // expanded static tables
     uint32_t *dup_prefix;   // n_dup + 1
@@ -159,9 +158,9 @@ cudaError_t launch_learned_multi(const MultiArgs &m, cudaStream_t st);
 uint32_t stage_dup(const SceneRef &r, void *par);
 size_t stage_dup_bytes();
 cudaError_t launch_dup_multi(const MultiArgs &m, cudaStream_t st);
-uint32_t stage_scan(const SceneRef &r, void *par);
+uint32_t stage_scan(const SceneRef &r, int variant, void *par);  // 0 scan, 1 reduce, 2 scatter
 size_t stage_scan_bytes();
-cudaError_t launch_scan_multi(const MultiArgs &m, cudaStream_t st);
+cudaError_t launch_scan_multi(int variant, const MultiArgs &m, cudaStream_t st);
 uint32_t stage_walk(const SceneRef &r, void *par);
 size_t stage_walk_bytes();
 cudaError_t launch_walk_multi(const MultiArgs &m, cudaStream_t st);

@@ -74,9 +74,11 @@ def lib() -> ctypes.CDLL:
     """Loads libsgs.so (building it first if the sources are newer).  Raises if it cannot."""
     global _lib
     if _lib is None:
-        path = _build.LIB
-        if not os.path.exists(path) or _build.needs_build():
-            path = _build.build()
+        path = os.environ.get("SGS_LIBRARY")  # an alternative build of the same library
+        if not path:
+            path = _build.LIB
+            if not os.path.exists(path) or _build.needs_build():
+                path = _build.build()
         L = ctypes.CDLL(path)
         L.sgs_strerror.restype = ctypes.c_char_p
         L.sgs_strerror.argtypes = [i32]
