@@ -31,9 +31,10 @@ WORKLOADS = {
     "fixed": dict(n=1_000_000, seed=1000, depth=16, mode=0, geo_mode=0, lanes=0,
                   desc="fixed-length scene decode: N=1,000,000 Gaussians (900,000 after pruning), "
                        "depth-16 octree (raw tokens), 56 channels at 4..10 bits"),
-    "static": dict(n=1_000_000, seed=1000, depth=16, mode=1, geo_mode=1, lanes=151552,
+    "static": dict(n=1_000_000, seed=1000, depth=16, mode=1, geo_mode=1, lanes=151552, geo_w=32,
                    desc="channel-wise static rANS scene decode: N=1,000,000 (900,000 kept), depth 16, "
-                        "8-bit tokens, 151,552 lanes (one 32-warp CTA per SM), rANS-coded octree levels"),
+                        "8-bit tokens, 151,552 lanes (one 32-warp CTA per SM), rANS-coded octree levels "
+                        "at about 32 tokens per geometry lane"),
     "learned": dict(n=1_000_000, seed=2000, depth=16, mode=2, geo_mode=1, lanes=4096,
                     desc="learned-model scene decode: N=1,000,000 (900,000 kept), depth 16, 8-bit "
                          "tokens, 4,096 lanes, context MLP 4->64->64->256"),
@@ -41,6 +42,12 @@ WORKLOADS = {
                   desc="small static scene decode: N=20,000 (18,000 kept), depth 12, 32 lanes"),
 }
 METRIC = "decoded Gaussians/s"
+WORKLOADS_DEFAULT = None  # the default workload's dict, set in main()
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_fixed launch on the
+# default workload, from an ncu --set full capture of the present kernel: 43.92 MB read +
+# 141.73 MB written (part of the 201.6 MB of output is still in L2 when the kernel ends).
+K_FIXED_TRAFFIC = 43_916_288 + 141_727_744
 
 
 BATCH = dict(n_scenes=64, lo=50_000, hi=3_000_000, size_seed=3000, depth_lo=14, depth_hi=17,
@@ -210,6 +217,8 @@ def make_bitstream(w: dict, ctx=None):
         kw["bits"] = fixed_bits(w["seed"])
     else:
         kw["lanes"] = w["lanes"]
+    if w.get("geo_w"):  # geometry lanes for throughput: about geo_w coded tokens per lane
+        kw["geo_lanes"] = geo_lanes_for(sc, w)
     model = None
     if w["mode"] == 2:
         from paper_2607_12656_b300 import learned
@@ -218,6 +227,16 @@ def make_bitstream(w: dict, ctx=None):
         kw["model"] = model
         kw["ctx"] = ctx
     return sc, sgs.scene_encode(sc.pos, sc.attr, **kw)
+
+
+def geo_lanes_for(sc, w) -> int:
+    """Geometry lanes giving about w["geo_w"] rANS-coded octree tokens per lane (a multiple
+    of 32): the coded token count is read back from a first encode's header."""
+    from paper_2607_12656_b300 import sgs
+    probe = sgs.scene_encode(sc.pos, sc.attr, mode=0, depth=w["depth"], bits=4, geo_mode=1)
+    n_coded = int(sgs.scene_query(probe).n_geo_coded)
+    per = w["geo_w"] * 32
+    return max(32, -(-n_coded // per) * 32)
 
 
 def fixed_algorithmic_bytes(info, bits_np) -> int:
@@ -368,7 +387,9 @@ def run_ours(args, w):
         line["roofline"] = {"kernel": "k_fixed (fixed-length unpack + dequant + SoA store)", "bound": "hbm",
                             "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm if hbm else None,
                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else "fallback 6400",
-                            "algorithmic_bytes": alg, "traffic": args.traffic}
+                            "algorithmic_bytes": alg,
+                            "traffic": args.traffic if args.traffic is not None else
+                            (K_FIXED_TRAFFIC if w is WORKLOADS_DEFAULT else None)}
         geo_alg = info.n_geo + 12 * n
         line["roofline_octree"] = {"bound": "hbm", "algorithmic_bytes": geo_alg,
                                    "achieved": geo_alg / (line["stage_ms"]["octree_positions"] / 1e3) / 1e9,
@@ -604,7 +625,12 @@ def run_reference(args, w):
         kw["bits"] = fixed_bits(w["seed"])
     else:
         kw["lanes"] = w["lanes"]
-    buf = S.encode(sc.pos, sc.attr, **kw)
+    P = S.prepare(sc.pos, sc.attr, w["depth"], kw.get("bits", 8))
+    if w.get("geo_w"):  # the same geometry lanes as the GPU arm
+        coded = S.geo_plan(P.levels, w["geo_mode"])
+        n_coded = sum(len(P.levels[l]) for l in range(w["depth"]) if coded[l])
+        kw["geo_lanes"] = max(32, -(-n_coded // (w["geo_w"] * 32)) * 32)
+    buf = S.encode(sc.pos, sc.attr, prep=P, **kw)
     for _ in range(args.warmup):
         S.decode(buf)
     times = []
@@ -651,6 +677,9 @@ def main():
         (run_batch if args.workload == "batch" else run_serve)(args)
         return
     w = dict(WORKLOADS[args.workload])
+    if args.workload == "fixed" and args.n is None:
+        global WORKLOADS_DEFAULT
+        WORKLOADS_DEFAULT = w
     if args.n is not None:
         w["n"] = args.n
         w["desc"] += " [resized: N=%d]" % args.n

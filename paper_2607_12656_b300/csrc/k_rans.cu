@@ -97,6 +97,7 @@ struct AttrParams {
 };
 
 constexpr int kAttrWarps = 32;  // one CTA per SM shares one copy of the 56 tables
+static_assert(kNChan % 8 == 0, "channels are decoded 8 at a time");
 constexpr size_t kAttrTabSmem = kNChan * kTabCdfWords * 4 + 2 * kNChan * 4;
 constexpr size_t kAttrSmem = kAttrTabSmem + kAttrWarps * kWinWords * 2;
 static_assert(kAttrTabSmem % 16 == 0, "window must be 16-byte aligned");
@@ -131,34 +132,29 @@ __device__ __forceinline__ void rans_attr_body(const AttrParams &p, uint32_t vb,
     uint32_t maxn = n;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) maxn = max(maxn, __shfl_xor_sync(0xffffffffu, maxn, o));
-    // per-channel state advanced incrementally: tables, constants, output pointer
+    // row by row, the 56 channels of a row in order (the coding order); channels unrolled by
+    // 8 so table and constant offsets are immediates
+    const uint32_t maxr = (maxn + kNChan - 1) / kNChan;
     uint32_t row = R0 + lane;
-    const uint32_t *cdf = s_cdf;
-    int c = 0;
-    float *orow = p.out + row;  // channel 0 of the current row (no out_index)
-    float *o = orow;
-    for (uint32_t t = 0; t < maxn; ++t) {
-        const bool active = t < n;
-        if (active) {
-            const uint32_t slot = x & 0xFFFFu;
-            const uint32_t sym = cdf_search(cdf, slot);
-            const uint32_t lo = cdf[sym], hi = cdf[sym + 1];
-            x = (hi - lo) * (x >> 16) + slot - lo;
-            const float v = dequant(sym, s_step[c], s_off[c]);
-            if (IDX) p.out[(size_t)c * p.n_rows + p.out_index[row]] = v;
-            else *o = v;
-            if (++c == kNChan) {
-                c = 0;
-                cdf = s_cdf;
-                row += nl;
-                orow += nl;
-                o = orow;
-            } else {
-                cdf += kTabCdfWords;
-                o += p.n_rows;
+    for (uint32_t rr = 0; rr < maxr; ++rr, row += nl) {
+        const bool active = rr < my_rows;
+        float *o = p.out + (IDX ? (active ? p.out_index[row] : 0u) : row);
+        const uint32_t *cdf = s_cdf;
+        for (int c0 = 0; c0 < kNChan; c0 += 8) {
+#pragma unroll
+            for (int c = c0; c < c0 + 8; ++c) {
+                if (active) {
+                    const uint32_t *tc = cdf + (c - c0) * kTabCdfWords;
+                    const uint32_t slot = x & 0xFFFFu;
+                    const uint32_t sym = cdf_search(tc, slot);
+                    const uint32_t lo = tc[sym], hi = tc[sym + 1];
+                    x = (hi - lo) * (x >> 16) + slot - lo;
+                    o[(size_t)c * p.n_rows] = dequant(sym, s_step[c], s_off[c]);
+                }
+                group_refill(gs, x, active);
             }
+            cdf += 8 * kTabCdfWords;
         }
-        group_refill(gs, x, active);
     }
     const bool bad = gs.bad || (lane < (int)nl && x != 0x10000u) || (gs.ptr != gs.n_words);
     if (bad) set_status(p.status, SGS_E_CORRUPT);
