@@ -331,11 +331,8 @@ def run_ours(args, w):
     except Exception as exc:  # graph capture unavailable: report eager numbers only
         print("graph capture failed: %s" % exc, file=sys.stderr)
         graph_times = []
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    from paper_2607_12656_b300 import replicas
+    total_ms = replicas.max_over_ranks(sum(times), dev)  # the slowest replica sets the time
     ms_per_step = total_ms / args.steps
     value = n * world * args.steps / (total_ms / 1e3)
 
@@ -420,10 +417,12 @@ def run_batch(args):
     import torch.distributed as dist
     from paper_2607_12656_b300 import sgs
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    specs, bufs = build_batch(args.scenes, args.train_steps or 300)
+    from paper_2607_12656_b300 import replicas
+    rank, world, local = replicas.rank_info()
+    # scenes are independent: rank r decodes its share of the batch, no exchange
+    all_specs = batch_specs(args.scenes)
+    specs, bufs = build_batch(args.scenes, args.train_steps or 300,
+                              [all_specs[i] for i in replicas.shard(len(all_specs), rank, world)])
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
@@ -460,11 +459,8 @@ def run_batch(args):
     launches = ctx.launch_count() - launches0
     if ctx.sync(stream) != sgs.OK:
         raise RuntimeError("batch decode failed")
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replicas.max_over_ranks(sum(times), dev)
+    rows_all = int(replicas.sum_over_ranks(rows, dev))  # Gaussians decoded by all ranks per step
     ms = total_ms / args.steps
     # the same scenes decoded one after another (one scene_decode call each)
     ctx.reserve(max(int(i.scratch_bytes) for i in infos))
@@ -518,14 +514,16 @@ def run_batch(args):
     hbm = pk.get("hbm_gbs")
     in_bytes = sum(len(b) for b in bufs)
     out_bytes = 4 * 59 * rows
-    line = {"metric": METRIC, "value": rows * world / (ms / 1e3), "unit": "Gaussians/s", "n_gpus": world,
+    line = {"metric": METRIC, "value": rows_all / (ms / 1e3), "unit": "Gaussians/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32->f32", "data": "synthetic",
-            "config": {"workload": BATCH["desc"] + " [%d scenes]" % len(items), "n_rows": rows,
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "u32->f32",
+            "data": "synthetic",
+            "config": {"workload": BATCH["desc"] + " [%d scenes, split by scene over %d GPU(s)]" % (args.scenes, world),
+                       "n_rows": rows_all,
                        "scenes": len(items), "learned_scenes": sum(1 for s in specs if s[4] == 2),
                        "bitstream_bytes": in_bytes, "output_bytes": out_bytes,
                        "l2": "flushed (256 MiB write) before every timed step; outputs exceed L2",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "scenes split across GPUs" if world > 1 else "single GPU"},
             "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
                            "min": min(times), "max": max(times), "note": "whole-batch makespan per step"},
             "sequential": {"ms_per_step": float(np.mean(seq)), "value": rows / (np.mean(seq) / 1e3),
@@ -600,6 +598,43 @@ def run_serve(args):
         print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """Group-size sweep: for W (rows per lane, the paper's complexity knob) in 16..256, the
+    bitstream size and the decode time of the 1M-Gaussian scene, static and learned modes,
+    measured by sgs_autotune (encode at each W, median of timed decodes)."""
+    import torch
+    from paper_2607_12656_b300 import learned, sgs
+    from paper_2607_12656_b300.scenegen import make_scene
+    from paper_2607_12656_b300.replicas import rank_info
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    ctx = sgs.Context(local, 0)
+    ws = [16, 32, 64, 128, 256]
+    curves = {}
+    for mode, name, seed in ((1, "static", 1000), (2, "learned", 2000)):
+        sc = make_scene(1_000_000, seed)
+        model = None
+        if mode == 2:
+            model = learned.train_and_freeze(ctx, sc, 16, 4096, steps=args.train_steps or 2000, batch=65536, seed=1)
+        r = sgs.autotune(ctx, sc.pos, sc.attr, mode=mode, depth=16, rows_per_lane=ws, reps=5 if mode == 1 else 3,
+                         model=model)
+        kept = 900_000
+        curves[name] = [{"rows_per_lane": w, "lanes": l, "bytes": b, "bits_per_gaussian": 8.0 * b / kept,
+                         "decode_ms": ms, "gaussians_per_s": kept / (ms / 1e3)}
+                        for w, l, b, ms in zip(r["rows_per_lane"], r["lanes"], r["bytes"], r["ms"])]
+    ctx.close()
+    best = max((c for v in curves.values() for c in v), key=lambda c: c["gaussians_per_s"])
+    line = {"metric": METRIC, "value": best["gaussians_per_s"], "unit": "Gaussians/s", "n_gpus": 1,
+            "steps": 5, "warmup": 1, "ms_per_step": best["decode_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32->f32", "data": "synthetic",
+            "config": {"workload": "group-size sweep: 1M-Gaussian scene (900,000 kept), depth 16, W = rows per "
+                                   "lane in 16..256, static and learned attribute coding; decode median of timed runs "
+                                   "(sgs_autotune), L2 not flushed", "rows_per_lane": ws},
+            "curves": curves}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(w: dict, buf: bytes, budget_s: float) -> dict:
     """The CPU oracle, as it stands, decoding the same bitstream (or a bounded part of it)."""
     from oracle import scene as S
@@ -657,7 +692,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fixed", choices=sorted(WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--workload", default="fixed", choices=sorted(WORKLOADS) + ["batch", "serve", "sweep"])
     ap.add_argument("--scenes", type=int, default=BATCH["n_scenes"], help="scenes of the batch workload")
     ap.add_argument("--rates", default=None, help="serve workload: comma-separated request rates (req/s)")
     ap.add_argument("--requests", type=int, default=None, help="serve workload: requests per rate")
@@ -669,12 +704,12 @@ def main():
     ap.add_argument("--lanes", type=int, default=None, help="override the workload's rANS lanes")
     ap.add_argument("--train-steps", type=int, default=None, help="override the learned model's steps")
     args = ap.parse_args()
-    if args.workload in ("batch", "serve"):
+    if args.workload in ("batch", "serve", "sweep"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the %s workload is timed on the GPU only; "
                               "the oracle arm runs the single-scene workloads" % args.workload}))
             return
-        (run_batch if args.workload == "batch" else run_serve)(args)
+        {"batch": run_batch, "serve": run_serve, "sweep": run_sweep}[args.workload](args)
         return
     w = dict(WORKLOADS[args.workload])
     if args.workload == "fixed" and args.n is None:
