@@ -611,6 +611,7 @@ def run_sweep(args):
     ctx = sgs.Context(local, 0)
     ws = [16, 32, 64, 128, 256]
     curves = {}
+    encode_s = {}
     for mode, name, seed in ((1, "static", 1000), (2, "learned", 2000)):
         sc = make_scene(1_000_000, seed)
         model = None
@@ -618,6 +619,14 @@ def run_sweep(args):
             model = learned.train_and_freeze(ctx, sc, 16, 4096, steps=args.train_steps or 2000, batch=65536, seed=1)
         r = sgs.autotune(ctx, sc.pos, sc.attr, mode=mode, depth=16, rows_per_lane=ws, reps=5 if mode == 1 else 3,
                          model=model)
+        # whole scene_encode (prepare on the host, attribute coding on the device or host), W = 32
+        lanes = -(-900_000 // 32)
+        for where, c in (("device", ctx), ("host", None)):
+            if mode == 2 and c is None:
+                continue  # learned coding needs the device for the model's frequencies
+            t0 = time.perf_counter()
+            sgs.scene_encode(sc.pos, sc.attr, mode=mode, depth=16, lanes=lanes, model=model, ctx=c)
+            encode_s["%s_%s" % (name, where)] = time.perf_counter() - t0
         kept = 900_000
         curves[name] = [{"rows_per_lane": w, "lanes": l, "bytes": b, "bits_per_gaussian": 8.0 * b / kept,
                          "decode_ms": ms, "gaussians_per_s": kept / (ms / 1e3)}
@@ -630,7 +639,10 @@ def run_sweep(args):
             "config": {"workload": "group-size sweep: 1M-Gaussian scene (900,000 kept), depth 16, W = rows per "
                                    "lane in 16..256, static and learned attribute coding; decode median of timed runs "
                                    "(sgs_autotune), L2 not flushed", "rows_per_lane": ws},
-            "curves": curves}
+            "curves": curves,
+            "encode": {"seconds": encode_s, "gaussians": 1_000_000, "threads": os.cpu_count(),
+                       "note": "whole scene_encode of the 1M scene at W = 32: prepare (prune, Morton sort, octree, "
+                               "quantize) on the host cores, attribute rANS coding on the device or on the host"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

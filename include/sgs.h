@@ -245,8 +245,10 @@ int scene_decode_batch(sgs_ctx *ctx, const sgs_batch_item *items, int n, sgs_str
 /* Encodes a scene given as host arrays pos[3][n] (in [0,1)) and attr[56][n] (finite):
  * prune floor(n/10) of lowest opacity, voxelize, Morton sort, octree, per-channel quantize,
  * then code (Sec. 3.3-3.4).  Writes at most `cap` bytes to `out` (host) and sets *out_len.
- * If cap is too small returns SGS_E_INVALID with *out_len = the size needed.  ctx may be
- * NULL except in learned mode (the context model's frequencies are computed on its device).
+ * If cap is too small returns SGS_E_INVALID with *out_len = the size needed.  With a ctx the
+ * attribute streams' interleaved rANS coding (static and learned) runs on its device; ctx may
+ * be NULL except in learned mode, and then static coding runs on the host.  Either way the
+ * bytes are the same.
  * Errors: SGS_E_INVALID, SGS_E_NOMEM, SGS_E_CUDA.                                            */
 int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, uint32_t n,
                  const sgs_encode_params *params, uint8_t *out, size_t cap, size_t *out_len);

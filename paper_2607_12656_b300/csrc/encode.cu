@@ -16,6 +16,7 @@
 #include <numeric>
 #include <vector>
 
+#include "sgs_ctx.h"
 #include "sgs_internal.h"
 
 namespace sgs {
@@ -301,10 +302,14 @@ uint32_t default_geo_lanes(uint64_t n) {
 
 }  // namespace
 
-// Computes on the device the frequency and cumulative of every token under the frozen
-// model; defined with the learned decoder.
-int learned_token_fc(sgs_ctx *c, const uint8_t *model, const uint8_t *tokens, uint32_t n_rows,
-                     uint32_t lanes, std::vector<uint32_t> &f, std::vector<uint32_t> &cum);
+// Interleaved rANS coding of the attribute streams on the device (k_encode.cu; the learned
+// model's frequencies in k_learned.cu), byte for byte as rans_encode above.
+int rans_encode_static_device(const uint8_t *tok_lane_major, uint64_t nsym, const uint32_t *ftab,
+                              const std::vector<uint64_t> &lane_start, std::vector<uint8_t> &grp,
+                              std::vector<uint8_t> &pay);
+int learned_encode_device(const uint8_t *model, const uint8_t *tokens, uint32_t n_rows, uint32_t lanes,
+                          const std::vector<uint64_t> &lane_start, std::vector<uint8_t> &grp,
+                          std::vector<uint8_t> &pay);
 
 }  // namespace sgs
 
@@ -392,7 +397,11 @@ extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, u
     } else {
         L = prm->lanes;
         const uint64_t nsym = (uint64_t)R * kNChan;
-        std::vector<uint32_t> sf(nsym), scu(nsym);
+        std::vector<uint32_t> sf, scu;  // host coding only
+        if (!ctx) {
+            sf.resize(nsym);
+            scu.resize(nsym);
+        }
         std::vector<uint64_t> starts = lane_bounds(R, L, kNChan);
         if (prm->mode == SGS_MODE_STATIC) {
             std::vector<uint32_t> perm;
@@ -409,22 +418,34 @@ extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, u
                 normalize(h, f);
                 uint32_t acc = 0;
                 for (int s = 0; s < kNSym; ++s) { cu[s] = acc; acc += f[s]; }
-                for (uint64_t p = 0; p < R; ++p) {
-                    const uint32_t q = P.q16[(size_t)perm[p] * kNChan + c];
-                    sf[p * kNChan + c] = f[q];
-                    scu[p * kNChan + c] = cu[q];
-                }
+                if (!ctx)
+                    for (uint64_t p = 0; p < R; ++p) {
+                        const uint32_t q = P.q16[(size_t)perm[p] * kNChan + c];
+                        sf[p * kNChan + c] = f[q];
+                        scu[p * kNChan + c] = cu[q];
+                    }
             }
             for (int c = 0; c < kNChan; ++c) put_table(s_atab, &ftab[(size_t)c * kNSym]);
+            if (ctx) {  // the interleaved rANS coding on the context's device
+                std::vector<uint8_t> tok(nsym);
+#pragma omp parallel for schedule(static)
+                for (int64_t p = 0; p < (int64_t)R; ++p)
+                    for (int c = 0; c < kNChan; ++c) tok[(size_t)p * kNChan + c] = (uint8_t)P.q16[(size_t)perm[p] * kNChan + c];
+                if (cudaSetDevice(ctx->device) != cudaSuccess) return SGS_E_CUDA;
+                r = rans_encode_static_device(tok.data(), nsym, ftab.data(), starts, s_agrp, s_apay);
+                if (r) return r;
+            } else {
+                rans_encode(starts, sf.data(), scu.data(), s_agrp, s_apay);
+            }
         } else {
             const uint8_t *m = static_cast<const uint8_t *>(prm->model);
             s_atab.assign(m, m + SGS_MODEL_BYTES);
             std::vector<uint8_t> tok(nsym);
             for (uint64_t i = 0; i < nsym; ++i) tok[i] = (uint8_t)P.q16[i];
-            r = learned_token_fc(ctx, m, tok.data(), R, L, sf, scu);
+            if (cudaSetDevice(ctx->device) != cudaSuccess) return SGS_E_CUDA;
+            r = learned_encode_device(m, tok.data(), R, L, starts, s_agrp, s_apay);
             if (r) return r;
         }
-        rans_encode(starts, sf.data(), scu.data(), s_agrp, s_apay);
     }
     // assemble
     std::vector<uint8_t> *secs[10] = {&s_levels, &s_dup, &s_chan, &s_graw, &s_gtab,

@@ -669,28 +669,31 @@ __global__ void __launch_bounds__(256) k_learned_fc(const uint8_t *model, const 
     }
 }
 
-int learned_token_fc(sgs_ctx *, const uint8_t *model, const uint8_t *tokens, uint32_t n_rows,
-                     uint32_t lanes, std::vector<uint32_t> &f, std::vector<uint32_t> &cum) {
+int rans_encode_device(const uint32_t *f, const uint32_t *cum, const std::vector<uint64_t> &lane_start,
+                       std::vector<uint8_t> &grp, std::vector<uint8_t> &pay);
+
+// Learned attribute coding on the device: the frozen model's f and cum of every token stay on
+// the device for the interleaved rANS encoder.
+int learned_encode_device(const uint8_t *model, const uint8_t *tokens, uint32_t n_rows, uint32_t lanes,
+                          const std::vector<uint64_t> &lane_start, std::vector<uint8_t> &grp,
+                          std::vector<uint8_t> &pay) {
     const uint64_t n = (uint64_t)n_rows * kNChan;
-    f.assign(n, 0);
-    cum.assign(n, 0);
-    if (n == 0) return SGS_OK;
     uint8_t *dm = nullptr, *dt = nullptr;
     uint32_t *df = nullptr, *dc = nullptr;
     int rc = SGS_OK;
-    if (cudaMalloc(&dm, SGS_MODEL_BYTES) != cudaSuccess || cudaMalloc(&dt, n) != cudaSuccess ||
-        cudaMalloc(&df, 4 * n) != cudaSuccess || cudaMalloc(&dc, 4 * n) != cudaSuccess) {
+    if (cudaMalloc(&dm, SGS_MODEL_BYTES) != cudaSuccess || cudaMalloc(&dt, n ? n : 1) != cudaSuccess ||
+        cudaMalloc(&df, 4 * (n ? n : 1)) != cudaSuccess || cudaMalloc(&dc, 4 * (n ? n : 1)) != cudaSuccess) {
         rc = SGS_E_NOMEM;
+    } else if (cudaMemcpy(dm, model, SGS_MODEL_BYTES, cudaMemcpyHostToDevice) != cudaSuccess ||
+               (n && cudaMemcpy(dt, tokens, n, cudaMemcpyHostToDevice) != cudaSuccess)) {
+        rc = SGS_E_CUDA;
     } else {
-        cudaMemcpy(dm, model, SGS_MODEL_BYTES, cudaMemcpyHostToDevice);
-        cudaMemcpy(dt, tokens, n, cudaMemcpyHostToDevice);
-        const uint64_t blocks = (n + 255) / 256;
-        k_learned_fc<<<(unsigned)(blocks < 148 * 64 ? blocks : 148 * 64), 256>>>(dm, dt, n_rows, lanes, df, dc);
-        if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) rc = SGS_E_CUDA;
-        else {
-            cudaMemcpy(f.data(), df, 4 * n, cudaMemcpyDeviceToHost);
-            cudaMemcpy(cum.data(), dc, 4 * n, cudaMemcpyDeviceToHost);
+        if (n) {
+            const uint64_t blocks = (n + 255) / 256;
+            k_learned_fc<<<(unsigned)(blocks < 148 * 64 ? blocks : 148 * 64), 256>>>(dm, dt, n_rows, lanes, df, dc);
+            if (cudaGetLastError() != cudaSuccess) rc = SGS_E_CUDA;
         }
+        if (rc == SGS_OK) rc = rans_encode_device(df, dc, lane_start, grp, pay);
     }
     cudaFree(dm);
     cudaFree(dt);

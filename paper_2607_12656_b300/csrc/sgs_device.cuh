@@ -188,8 +188,10 @@ __device__ __forceinline__ void fixed_warp_item(const FixedParams &p, uint64_t i
     const uint64_t w0 = (uint64_t)blk * 32 * b;   // first word of this item
     const uint32_t nw = 32 * b;
     __syncwarp();  // the previous item's reads of sw are done
+    // packed words and outputs are touched once: streaming (evict-first) accesses keep them
+    // from displacing the octree's working set in L2 while the two halves run together
     for (uint32_t i = lane; i <= nw; i += 32)
-        sw[i] = (w0 + i < nwords_chan) ? w[w0 + i] : 0u;
+        sw[i] = (w0 + i < nwords_chan) ? __ldcs(w + w0 + i) : 0u;
     __syncwarp();
     const uint32_t mask = (1u << b) - 1u;  // b <= 16
     const uint32_t r0 = blk * kFixRows;
@@ -208,11 +210,11 @@ __device__ __forceinline__ void fixed_warp_item(const FixedParams &p, uint64_t i
                 bit += b;
             }
             if (rl + 4 <= rows) {
-                *reinterpret_cast<float4 *>(outc + rl) = make_float4(v[0], v[1], v[2], v[3]);
+                __stcs(reinterpret_cast<float4 *>(outc + rl), make_float4(v[0], v[1], v[2], v[3]));
             } else {
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    if (rl + q < rows) outc[rl + q] = v[q];
+                    if (rl + q < rows) __stcs(outc + rl + q, v[q]);
             }
         }
     } else {
@@ -223,8 +225,8 @@ __device__ __forceinline__ void fixed_warp_item(const FixedParams &p, uint64_t i
             const uint32_t bit = rl * b;
             const uint32_t wi = bit >> 5;
             const float v = dequant(__funnelshift_r(sw[wi], sw[wi + 1], bit & 31) & mask, step, offset);
-            if (p.out_index) p.out[(size_t)c * p.n_rows + p.out_index[r0 + rl]] = v;
-            else outc[rl] = v;
+            if (p.out_index) __stcs(p.out + (size_t)c * p.n_rows + p.out_index[r0 + rl], v);
+            else __stcs(outc + rl, v);
         }
     }
 }

@@ -191,3 +191,15 @@ def test_autotune_sweeps_group_sizes(ctx, small_scene):
     assert lanes >= 1 and len(t.table) == 1
     with pytest.raises(sgs.SgsError):
         sgs.autotune(ctx, sc.pos, sc.attr, mode=sgs.MODE_FIXED, depth=12, rows_per_lane=[32])
+
+
+@pytest.mark.parametrize("n,lanes", [(20_000, 40), (60_000, 2048), (30_000, 33), (5_000, 1)])
+def test_device_static_encoder_matches_oracle_and_host(ctx, n, lanes):
+    """The attribute rANS coding on the device (with a context) writes the oracle's bytes, and
+    the host coding (no context) the same; lane counts include ragged last groups."""
+    sc = make_scene(n, 71)
+    P = S.prepare(sc.pos, sc.attr, 13, 8)
+    want = S.encode(None, None, mode=S.MODE_STATIC, depth=13, lanes=lanes, prep=P)
+    dev = sgs.scene_encode(sc.pos, sc.attr, mode=sgs.MODE_STATIC, depth=13, lanes=lanes, ctx=ctx)
+    host = sgs.scene_encode(sc.pos, sc.attr, mode=sgs.MODE_STATIC, depth=13, lanes=lanes)
+    assert dev == want and host == want
