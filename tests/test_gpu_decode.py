@@ -203,3 +203,47 @@ def test_device_static_encoder_matches_oracle_and_host(ctx, n, lanes):
     dev = sgs.scene_encode(sc.pos, sc.attr, mode=sgs.MODE_STATIC, depth=13, lanes=lanes, ctx=ctx)
     host = sgs.scene_encode(sc.pos, sc.attr, mode=sgs.MODE_STATIC, depth=13, lanes=lanes)
     assert dev == want and host == want
+
+
+@pytest.mark.parametrize("n,depth", [(1, 21), (3, 21), (5000, 21), (5000, 20), (20000, 17)])
+def test_deep_octrees(ctx, n, depth):
+    """Deep trees (up to the 21-bit coordinate limit): every leaf walks depth levels up to the
+    root; a single Gaussian is one chain of 21 nodes."""
+    sc = make_scene(n, 300 + depth)
+    check(ctx, sc, depth, mode=S.MODE_FIXED, bits=fixed_bits(depth), geo_mode=S.GEO_RAW)
+    check(ctx, sc, depth, mode=S.MODE_STATIC, lanes=7, geo_mode=S.GEO_RANS)
+
+
+def test_duplicates_with_scatter_and_coords(ctx):
+    """Many Gaussians per voxel at a shallow depth, rows scattered by out_index, with voxel
+    coordinates: each leaf writes all its rows."""
+    sc = make_scene(9000, 6)
+    P = S.prepare(sc.pos, sc.attr, 4, 8)
+    assert len(P.dups) > 20
+    buf = S.encode(None, None, mode=S.MODE_STATIC, depth=4, lanes=50, geo_mode=S.GEO_RAW, prep=P)
+    perm = np.random.default_rng(6).permutation(P.n_rows)
+    st, attr, pos, crd, _ = gpu_decode(ctx, buf, out_index=perm)
+    assert st == sgs.OK
+    assert same_bits(attr[:, perm], P.attr) and same_bits(pos[:, perm], P.pos)
+    assert np.array_equal(crd[:, perm], P.coord)
+
+
+def test_corrupt_raw_geometry_detected(ctx, small_scene):
+    """Flipped bits in raw occupancy tokens (fixed-length scene): the level counts no longer
+    match the tokens, and the decoder reports CORRUPT (or decodes other positions) without
+    reading or writing out of bounds."""
+    P = S.prepare(small_scene.pos, small_scene.attr, 12, fixed_bits(4))
+    buf = S.encode(None, None, mode=S.MODE_FIXED, depth=12, bits=fixed_bits(4), geo_mode=S.GEO_RAW, prep=P)
+    h = S.parse_header(buf)
+    rng = np.random.default_rng(3)
+    flagged = 0
+    for trial in range(12):
+        b = bytearray(buf)
+        k = int(rng.integers(h["off_geo_raw"], h["off_geo_raw"] + h["n_geo"]))
+        b[k] ^= 1 << int(rng.integers(0, 8))
+        st, attr, pos, _, _ = gpu_decode(ctx, bytes(b))
+        if st == sgs.E_CORRUPT:
+            flagged += 1
+        else:
+            assert st == sgs.OK and not same_bits(pos, P.pos)
+    assert flagged >= 10
