@@ -430,6 +430,22 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
+def scene_latency(samples: list, modes: list) -> dict:
+    """p50/p99 of the per-scene completion times of the timed batch runs, overall and per
+    coding mode (completion flags: the device's global timer from the run's first kernel to
+    the end of the scene's last work item)."""
+    names = {0: "fixed", 1: "static", 2: "learned"}
+    out = {"note": "per-scene completion time inside a batch run (completion flags, device global timer)"}
+    groups = {"all": [v for run in samples for v in run if v >= 0]}
+    for m in sorted(set(modes)):
+        groups[names.get(m, str(m))] = [run[j] for run in samples for j in range(len(run)) if modes[j] == m and run[j] >= 0]
+    for k, v in groups.items():
+        if v:
+            out[k] = {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99)), "max": float(max(v)),
+                      "samples": len(v)}
+    return out
+
+
 def run_batch(args):
     """The batched workload: every scene's bitstream resident in HBM, one plan run per step."""
     import torch
@@ -461,7 +477,7 @@ def run_batch(args):
     if ctx.sync(stream) != sgs.OK or plan.status() != [sgs.OK] * len(items):
         raise RuntimeError("batch decode status %s" % plan.status())
     launches0 = ctx.launch_count()
-    times = []
+    times, scene_ms = [], []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -474,6 +490,7 @@ def run_batch(args):
             b.record(stream)
             stream.synchronize()
             times.append(a.elapsed_time(b))
+            scene_ms.append(plan.times_ms())  # read after the step's stop event
         torch.cuda.synchronize()
     launches = ctx.launch_count() - launches0
     if ctx.sync(stream) != sgs.OK:
@@ -545,6 +562,7 @@ def run_batch(args):
                        "parallelism": "scenes split across GPUs" if world > 1 else "single GPU"},
             "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
                            "min": min(times), "max": max(times), "note": "whole-batch makespan per step"},
+            "scene_latency_ms": scene_latency(scene_ms, [s[4] for s in specs]),
             "sequential": {"ms_per_step": float(np.mean(seq)), "value": rows / (np.mean(seq) / 1e3),
                            "note": "same scenes, one scene_decode call after another"},
             "gpu_launches": launches // args.steps,

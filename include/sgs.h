@@ -202,7 +202,8 @@ typedef struct {
  * are independent, and Sec. 3.4.2's parallelism over groups extends across them).  Every
  * pipeline stage of all n scenes runs as ONE persistent launch: its CTAs take work items
  * (the lanes' groups, table expansions, scan tiles, blocks of octree leaves of every scene)
- * from a shared counter, so a run is at most 13 launches whatever n is.
+ * from a shared counter, so a run is at most 13 stage launches whatever n is (plus one
+ * kernel that starts the run and one that folds the scenes' status words).
  *
  * A plan binds the items' buffers (bitstreams, outputs) and holds, in one device block, every
  * scene's scratch, the per-stage work lists and per-scene status words. */
@@ -230,6 +231,14 @@ int scene_batch_run(sgs_ctx *ctx, sgs_batch *plan, sgs_stream stream);
 /* Copies the per-scene status words of the plan's last completed run (n = the plan's
  * scene count) to host memory; call after the run's stream has finished.  Blocking. */
 int scene_batch_status(const sgs_batch *plan, int *status, int n);
+
+/* Per-scene completion times of the plan's last completed run (n = the plan's scene count),
+ * in milliseconds: from the run's first kernel to the end of the scene's last work item over
+ * all of the run's launches, both read from the device's global nanosecond timer.  Each
+ * scene keeps a completion count that every finished work item increments; the item that
+ * completes it stamps the time.  A scene without work items gets -1.  Blocking; call after
+ * the run's stream has finished. */
+int scene_batch_times(const sgs_batch *plan, double *ms, int n);
 
 /* Frees the plan's device block (after its runs have finished). */
 void scene_batch_free(sgs_batch *plan);

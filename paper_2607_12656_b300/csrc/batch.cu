@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "sgs_ctx.h"
+#include "sgs_device.cuh"
 #include "sgs_internal.h"
 
 namespace sgs {
@@ -55,7 +56,7 @@ struct LaunchRec {
     Kind kind;
     int variant;   // vector / out_index variant
     Role role;
-    uint64_t prefix_off, param_off;  // byte offsets in the plan's list area
+    uint64_t prefix_off, param_off, scene_off;  // byte offsets in the plan's list area
     uint32_t stride;
     int n;
     uint32_t total;
@@ -106,6 +107,14 @@ cudaError_t launch_kind(Kind k, int variant, const MultiArgs &m, cudaStream_t st
     }
 }
 
+// First kernel of a run: zeroes the counters, status words, completion counts and times
+// (n16 16-byte units) and stamps the run's start on the device global timer.
+__global__ void k_run_begin(uint4 *zero, uint32_t n16, unsigned long long *t_start) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += gridDim.x * blockDim.x)
+        zero[i] = make_uint4(0, 0, 0, 0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *t_start = globaltimer_ns();
+}
+
 __global__ void k_status_fold(const int *status, int n, int *out) {
     int worst = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) worst = min(worst, status[i]);
@@ -116,15 +125,16 @@ __global__ void k_status_fold(const int *status, int n, int *out) {
 }  // namespace
 
 // Device layout of a plan, from `base`:
-//   scene scratch (each a256) | counters[kMaxLaunches] | status[n] | prefix lists | parameter
-//   lists
-// The counters and status words are zeroed by every run.
+//   scene scratch (each a256) | counters[kMaxLaunches] | status[n] | done[n] | t_done[n] |
+//   t_start | lists (per launch: prefix, scene ids, parameters; then need[n])
+// Every run zeroes the span from the counters to t_done.
 struct BatchLayout {
     std::vector<Scratch> scratch;
     std::vector<GeoPlan> plans;
     std::vector<LaunchRec> launches;
-    std::vector<uint8_t> lists;  // prefix and parameter lists, uploaded to lists_off
-    uint64_t zero_off, zero_bytes, status_off, lists_off, total;
+    std::vector<uint8_t> lists;  // uploaded to lists_off
+    std::vector<uint32_t> need;  // work items of each scene over all launches
+    uint64_t zero_off, zero_bytes, status_off, done_off, times_off, start_off, need_off, lists_off, total;
 };
 
 static int build_layout(const sgs_batch_item *items, int n, uint8_t *base, BatchLayout *L) {
@@ -147,8 +157,15 @@ static int build_layout(const sgs_batch_item *items, int n, uint8_t *base, Batch
     off += a256(4ull * kMaxLaunches);
     L->status_off = off;
     off += a256(4ull * (n > 0 ? n : 1));
+    L->done_off = off;
+    off += a256(4ull * (n > 0 ? n : 1));
+    L->times_off = off;
+    off += a256(8ull * (n > 0 ? n : 1));
     L->zero_bytes = off - L->zero_off;
+    L->start_off = off;
+    off += 256;
     L->lists_off = off;
+    L->need.assign(n, 0);
     std::vector<SceneRef> refs(n);
     for (int i = 0; i < n; ++i) {
         refs[i].bits = items[i].bits_dev;
@@ -167,15 +184,17 @@ static int build_layout(const sgs_batch_item *items, int n, uint8_t *base, Batch
         rec.variant = variant;
         rec.role = role;
         rec.stride = (uint32_t)a16(bytes);
-        std::vector<uint32_t> prefix(1, 0);
+        std::vector<uint32_t> prefix(1, 0), scene;
         std::vector<uint8_t> params;
         for (int i = 0; i < n; ++i) {
             memset(par, 0, sizeof(par));
             const uint32_t c = stage_items(k, variant, refs[i], par);
             if (!c) continue;
             if ((uint64_t)prefix.back() + c >= (1ull << 31)) return SGS_E_UNSUPPORTED;
+            if ((uint64_t)L->need[i] + c >= (1ull << 31)) return SGS_E_UNSUPPORTED;
             params.insert(params.end(), par, par + rec.stride);
             prefix.push_back(prefix.back() + c);
+            scene.push_back((uint32_t)i);
         }
         rec.n = (int)prefix.size() - 1;
         rec.total = prefix.back();
@@ -186,8 +205,13 @@ static int build_layout(const sgs_batch_item *items, int n, uint8_t *base, Batch
         L->lists.insert(L->lists.end(), reinterpret_cast<uint8_t *>(prefix.data()),
                         reinterpret_cast<uint8_t *>(prefix.data() + prefix.size()));
         L->lists.resize(a16(L->lists.size()));
+        rec.scene_off = L->lists.size();
+        L->lists.insert(L->lists.end(), reinterpret_cast<uint8_t *>(scene.data()),
+                        reinterpret_cast<uint8_t *>(scene.data() + scene.size()));
+        L->lists.resize(a16(L->lists.size()));
         rec.param_off = L->lists.size();
         L->lists.insert(L->lists.end(), params.begin(), params.end());
+        for (size_t j = 0; j < scene.size(); ++j) L->need[scene[j]] += prefix[j + 1] - prefix[j];
         L->launches.push_back(rec);
         return SGS_OK;
     };
@@ -203,6 +227,10 @@ static int build_layout(const sgs_batch_item *items, int n, uint8_t *base, Batch
     if (rc == SGS_OK) rc = add(K_SCAN, 2, R_GEO);  // parent entries
     if (rc == SGS_OK) rc = add(K_WALK, 0, R_GEO);
     if (rc != SGS_OK) return rc;
+    L->lists.resize(a16(L->lists.size()));
+    L->need_off = L->lists.size();
+    L->lists.insert(L->lists.end(), reinterpret_cast<uint8_t *>(L->need.data()),
+                    reinterpret_cast<uint8_t *>(L->need.data() + L->need.size()));
     L->total = a256(L->lists_off + L->lists.size());
     return SGS_OK;
 }
@@ -231,6 +259,10 @@ MultiArgs multi_args(const sgs_batch &b, const LaunchRec &r, int idx) {
     m.n = r.n;
     m.total = r.total;
     m.counter = reinterpret_cast<uint32_t *>(b.base + b.L.zero_off) + idx;
+    m.scene_id = reinterpret_cast<const uint32_t *>(lists + r.scene_off);
+    m.done = reinterpret_cast<uint32_t *>(b.base + b.L.done_off);
+    m.need = reinterpret_cast<const uint32_t *>(lists + b.L.need_off);
+    m.t_done = reinterpret_cast<unsigned long long *>(b.base + b.L.times_off);
     return m;
 }
 
@@ -256,11 +288,24 @@ int batch_init(sgs_ctx *c, const sgs_batch_item *items, int n, uint8_t *base, sg
 
 int batch_run(sgs_ctx *c, sgs_batch *b, cudaStream_t st) {
     const BatchLayout &L = b->L;
-    if (cudaMemsetAsync(b->base + L.zero_off, 0, L.zero_bytes, st) != cudaSuccess) return SGS_E_CUDA;
+    {
+        const uint32_t n16 = (uint32_t)(L.zero_bytes / 16);
+        k_run_begin<<<(n16 + 255) / 256 < 64 ? (n16 + 255) / 256 : 64, 256, 0, st>>>(
+            reinterpret_cast<uint4 *>(b->base + L.zero_off), n16,
+            reinterpret_cast<unsigned long long *>(b->base + L.start_off));
+        if (cudaGetLastError() != cudaSuccess) return SGS_E_CUDA;
+        c->launches += 1;
+    }
     cudaStream_t role_stream[3] = {st, c->aux, c->geo};
-    // the tables feed both halves: run them first on the caller's stream, then fork
+    // The tables feed both halves: they run first on the caller's stream, then the attribute
+    // and geometry streams fork.  The learned-model launch goes last on the attribute
+    // stream, after the whole geometry chain: its persistent CTAs fill every SM (one per SM)
+    // for most of the run, so a geometry stage queued behind them would wait for the whole
+    // learned decode, and with it every scene's completion.  Fixed-length and static
+    // scenes thus complete while the learned decode has not started.
     bool forked = false;
-    for (size_t i = 0; i < L.launches.size(); ++i) {
+    int learned = -1;
+    auto launch = [&](size_t i) -> int {
         const LaunchRec &r = L.launches[i];
         if (r.kind != K_TABLES && !forked) {
             if (cudaEventRecord(c->fork, st) != cudaSuccess || cudaStreamWaitEvent(c->aux, c->fork, 0) != cudaSuccess ||
@@ -271,6 +316,20 @@ int batch_run(sgs_ctx *c, sgs_batch *b, cudaStream_t st) {
         if (launch_kind(r.kind, r.variant, multi_args(*b, r, (int)i), role_stream[r.role]) != cudaSuccess)
             return SGS_E_CUDA;
         c->launches += 1;
+        return SGS_OK;
+    };
+    for (size_t i = 0; i < L.launches.size(); ++i) {
+        if (L.launches[i].kind == K_LEARNED) {
+            learned = (int)i;
+            continue;
+        }
+        if (launch(i) != SGS_OK) return SGS_E_CUDA;
+    }
+    if (learned >= 0) {
+        if (forked && (cudaEventRecord(c->gjoin, c->geo) != cudaSuccess ||
+                       cudaStreamWaitEvent(c->aux, c->gjoin, 0) != cudaSuccess))
+            return SGS_E_CUDA;
+        if (launch((size_t)learned) != SGS_OK) return SGS_E_CUDA;
     }
     if (forked && (cudaEventRecord(c->join, c->aux) != cudaSuccess || cudaEventRecord(c->gjoin, c->geo) != cudaSuccess ||
                    cudaStreamWaitEvent(st, c->join, 0) != cudaSuccess ||
@@ -338,6 +397,20 @@ extern "C" int scene_batch_status(const sgs_batch *b, int *status, int n) {
     if (cudaSetDevice(b->device) != cudaSuccess) return SGS_E_CUDA;
     if (cudaMemcpy(status, b->base + b->L.status_off, 4ull * n, cudaMemcpyDeviceToHost) != cudaSuccess)
         return SGS_E_CUDA;
+    return SGS_OK;
+}
+
+extern "C" int scene_batch_times(const sgs_batch *b, double *ms, int n) {
+    if (!b || (!ms && n) || n != b->n) return SGS_E_INVALID;
+    if (n == 0) return SGS_OK;
+    if (cudaSetDevice(b->device) != cudaSuccess) return SGS_E_CUDA;
+    std::vector<unsigned long long> t(n);
+    unsigned long long t0 = 0;
+    if (cudaMemcpy(t.data(), b->base + b->L.times_off, 8ull * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&t0, b->base + b->L.start_off, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SGS_E_CUDA;
+    for (int i = 0; i < n; ++i)
+        ms[i] = (b->L.need[i] && t[i] >= t0) ? (double)(t[i] - t0) * 1e-6 : -1.0;
     return SGS_OK;
 }
 

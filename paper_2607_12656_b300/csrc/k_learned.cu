@@ -7,12 +7,10 @@
 //   t_k = min(((zmax - z_k) ms) >> ss, 6144),  e_k = EXP2Q[t_k & 255] >> (t_k >> 8),
 //   R = floor(65280 * 2^32 / sum e),  f_k = 1 + floor(e_k R / 2^32),  remainder to argmax z.
 //
-// Decoder: one CTA of 8 warps per group of 32 lanes; it walks the group's tokens in stream
-// order (Gaussian i, channel c).  Per (i, c) step the 32 lanes' rows go through layer 1 on
-// the ALU, layers 2-3 as int8 mma.sync m16n8k32 with exact int32 accumulation (sm_103a has
-// no tcgen05 int8 kind), the softmax reductions across the 4 column quarters, a CDF search
-// restricted to the quarter holding each lane's slot, and finally warp 0 advances the 32
-// rANS states and refills them from the group's shared word stream.
+// Decoder: one CTA per group of 32 lanes, walking the group's tokens in stream order
+// (Gaussian i, channel c): 12 producer warps compute the steps' cumulative tables ahead of
+// one consumer warp that advances the 32 rANS states and refills them from the group's
+// shared word stream (details at the pipeline's constants below).
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -88,13 +86,13 @@ struct LearnedParams {
     int *status;
 };
 
-// Pipelined decoder: 16 producer warps compute the frequency tables of the steps (Gaussian i,
+// Pipelined decoder: kPW producer warps compute the frequency tables of the steps (Gaussian i,
 // channel c) ahead of one consumer warp that runs the group's 32 rANS chains.  Each producer
 // warp owns 8 of a step's 32 contexts and computes them end to end on its own -- layer 1 on
 // the ALU, layers 2-3 as bf16 mma.sync with the contexts as the N dimension, the integer
 // softmax reduced with shuffles among the 8 lanes that share a context -- so producers never
-// synchronise with each other.  Four warps make one step; the 16 warps work on 4 steps at
-// once, writing u16 cumulative tables into a ring of kNB steps.  The context of step (i, c)
+// synchronise with each other.  Four warps make one step; the kPW warps work on kSW steps
+// at once, writing u16 cumulative tables into a ring of kNB steps.  The context of step (i, c)
 // needs only (i-1 .. i-4, c), at least 56 steps back, so the ring's release by the consumer
 // also publishes the tokens a producer reads.  Hand-offs are mbarriers with bounded waits.
 constexpr int kPW = 12;                  // producer warps

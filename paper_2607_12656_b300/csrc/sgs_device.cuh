@@ -233,6 +233,13 @@ __device__ __forceinline__ void fixed_warp_item(const FixedParams &p, uint64_t i
 
 // ------------------------------------------------------------------ batched stages
 
+// The device's global nanosecond timer (PTX special register %globaltimer).
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Persistent loop: each CTA claims items in increasing order with an atomic counter, finds
 // the owning scene by binary search, copies its parameters to shared memory and runs
 // body(params, item within the scene, items of the scene, same), where `same` says that this
@@ -268,6 +275,13 @@ __device__ __forceinline__ void run_items(const MultiArgs &m, Body body) {
         __syncthreads();
         body(*reinterpret_cast<const P *>(s_par), item - m.prefix[sc], m.prefix[sc + 1] - m.prefix[sc], same);
         __syncthreads();
+        if (m.done && threadIdx.x == 0) {
+            // the CTA's writes for this item precede the count: the last item of the scene
+            // to finish is the one whose increment reaches need
+            __threadfence();
+            const uint32_t g = m.scene_id[sc];
+            if (atomicAdd(m.done + g, 1u) + 1u == m.need[g]) m.t_done[g] = globaltimer_ns();
+        }
     }
 }
 

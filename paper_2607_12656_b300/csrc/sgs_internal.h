@@ -107,6 +107,14 @@ struct MultiArgs {
     int n;
     uint32_t total;           // prefix[n]
     uint32_t *counter;        // zero before the launch
+    // Completion flags (all NULL when unused): list entry s is scene scene_id[s] of the
+    // batch; done[g] counts the finished items of scene g over all launches of a run
+    // (zero before the run), need[g] is their number, and the CTA that finishes the last
+    // one stamps the device global timer (ns) into t_done[g].
+    const uint32_t *scene_id;
+    uint32_t *done;
+    const uint32_t *need;
+    unsigned long long *t_done;
 };
 
 // One scene as the stage builders see it (device pointers; the scratch already carved).

@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
         L.scene_batch_plan.argtypes = [P, ctypes.POINTER(BatchItem), i32, ctypes.POINTER(P)]
         L.scene_batch_run.argtypes = [P, P, P]
         L.scene_batch_status.argtypes = [P, ctypes.POINTER(i32), i32]
+        L.scene_batch_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), i32]
         L.scene_batch_free.argtypes = [P]
         L.scene_batch_free.restype = None
         L.scene_encode.argtypes = [P, P, P, u32, ctypes.POINTER(EncodeParams), P, ctypes.c_size_t,
@@ -275,6 +276,13 @@ class BatchPlan:
     def status(self) -> list[int]:
         arr = (i32 * max(self.n, 1))()
         _check(lib().scene_batch_status(self.handle, arr, self.n), "scene_batch_status")
+        return list(arr[:self.n])
+
+    def times_ms(self) -> list[float]:
+        """Per-scene completion times (ms from the start of the last finished run; -1 for a
+        scene without work)."""
+        arr = (ctypes.c_double * max(self.n, 1))()
+        _check(lib().scene_batch_times(self.handle, arr, self.n), "scene_batch_times")
         return list(arr[:self.n])
 
     def close(self) -> None:

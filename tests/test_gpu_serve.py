@@ -141,6 +141,39 @@ def test_batch_plan_runs_again_and_replays_in_a_graph(pool):
     c.close()
 
 
+def test_batch_completion_times(pool):
+    """Every scene's completion time (completion flags, device global timer) lies inside the
+    run as the caller's stream events see it, and a graph replay stamps new ones."""
+    items, refs = _batch_items(pool)
+    c = sgs.Context(0, 0)
+    plan = sgs.BatchPlan(c, items)
+    plan.run()  # warm
+    assert c.sync() == sgs.OK
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.run(torch.cuda.current_stream())
+    e1.record()
+    torch.cuda.synchronize()
+    span = e0.elapsed_time(e1)
+    t = plan.times_ms()
+    assert len(t) == len(items)
+    assert all(0.0 <= v <= span + 0.01 for v in t), (t, span)
+    assert max(t) > 0.5 * span  # the last scene ends near the end of the run
+    _check_outputs(items, refs)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.run(s)
+    plan.times_ms()  # nothing ran during the capture; the last run's times stay
+    g.replay()
+    torch.cuda.synchronize()
+    t2 = plan.times_ms()
+    assert all(v >= 0.0 for v in t2) and max(t2) > 0.0
+    del g
+    plan.close()
+    c.close()
+
+
 def test_batch_status_isolates_a_corrupt_scene(pool):
     """A scene whose payload was damaged reports its own status; the others decode intact."""
     bad = 4  # a static-mode scene of the pool
