@@ -47,6 +47,30 @@ def model_struct(m: dict) -> Model:
     return s
 
 
+class PeModel(ctypes.Structure):
+    """Frozen position-aware model, field for field as the C struct or_pe_model."""
+    _fields_ = [
+        ("s1", ctypes.c_float), ("s2", ctypes.c_float), ("smu", ctypes.c_float), ("slr", ctypes.c_float),
+        ("b1", ctypes.c_int32 * (NCHAN * HID)),
+        ("b2", ctypes.c_int32 * HID),
+        ("b3", ctypes.c_int32 * 2),
+        ("w1", ctypes.c_int8 * (HID * 80)),
+        ("w2", ctypes.c_int8 * (HID * HID)),
+        ("w3", ctypes.c_int8 * (2 * HID)),
+    ]
+
+
+def pe_model_struct(m: dict) -> PeModel:
+    s = PeModel()
+    for k, dt in (("b1", np.int32), ("b2", np.int32), ("b3", np.int32), ("w1", np.int8), ("w2", np.int8),
+                  ("w3", np.int8)):
+        arr = np.ascontiguousarray(np.asarray(m[k]).astype(dt)).ravel()
+        ctypes.memmove(ctypes.addressof(getattr(s, k)), arr.ctypes.data, arr.nbytes)
+    for k in ("s1", "s2", "smu", "slr"):
+        setattr(s, k, float(m[k]))
+    return s
+
+
 _lib = None
 
 
@@ -73,6 +97,16 @@ def lib():
         L.or_calib_max.restype = None
         L.or_calib_max.argtypes = [P, P, i32, i32, P, P, P, P, P, P, i64, P, P]
         L.or_model_size.restype = ctypes.c_int
+        L.or_pe_model_size.restype = ctypes.c_int
+        assert L.or_pe_model_size() == ctypes.sizeof(PeModel)
+        L.or_pe_phi.restype = None
+        L.or_pe_phi.argtypes = [P, ctypes.c_int, P, P]
+        L.or_pe_head.restype = None
+        L.or_pe_head.argtypes = [P, P, ctypes.c_int, P, P, P]
+        L.or_pe_cdf.restype = u32
+        L.or_pe_cdf.argtypes = [i32, i32, ctypes.c_int, P]
+        L.or_rans_decode_pe.restype = ctypes.c_int
+        L.or_rans_decode_pe.argtypes = [P, P, P, P, i64, ctypes.c_int, P, i64, P, i64, P, P, P]
         assert L.or_model_size() == ctypes.sizeof(Model)
         _lib = L
     return _lib

@@ -13,13 +13,19 @@
  *     frequency table (the learned CDF of Sec. 3.4 "Autoregressive Prediction Coding",
  *     made integer so encoder and decoder agree bit for bit), and the learned decoder.
  *
- * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no floating point is used here).
+ *   - the position-aware model (Fourier positional embedding, Laplace head) and its decoder:
+ *     integer sums, fp32 requantisation with one multiply and round-half-to-even, and the
+ *     integer Laplace CDF.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (the only floating point is the fp32
+ * requantisation of the position-aware model: single multiplies, never fused).
  *
  * Stream format of one group of up to 32 lanes (words are uint16, little endian):
  *   32 initial states, lane j ascending, each as (hi word, lo word);
  *   then for step t = 0, 1, ...: for each lane j ascending that still has a symbol t:
  *   decode symbol t, and if the state fell below 2^16 read one word into its low half.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -379,4 +385,143 @@ void or_calib_max(const int8_t *w1, const int32_t *b1, int32_t m1, int32_t sh1,
     }
     *max1 = a1max;
     *max2 = a2max;
+}
+
+/* ---------------------------------------------------------------- position-aware model */
+
+#define OR_NPHI 75
+#define OR_KIN 80
+#define OR_BANDS 12
+
+typedef struct {
+    float s1, s2, smu, slr;           /* requant scales and head multipliers */
+    int32_t b1[OR_NCHAN * OR_HID];    /* [56][64], embedding and projection bias folded in */
+    int32_t b2[OR_HID];
+    int32_t b3[2];
+    int8_t w1[OR_HID * OR_KIN];       /* [64][80]: u (4), phi (75), 0 */
+    int8_t w2[OR_HID * OR_HID];
+    int8_t w3[2 * OR_HID];
+} or_pe_model;
+
+int or_pe_model_size(void) { return (int)sizeof(or_pe_model); }
+
+/* Embedding inputs of a voxel v (3 coordinates) at depth D: floor(128 mu) per axis, then
+ * for band k the sines and then the cosines of 2 pi 2^k mu on a 256-step phase grid. */
+void or_pe_phi(const uint32_t *v, int depth, const int8_t *sin8, int32_t *phi)
+{
+    for (int a = 0; a < 3; ++a) {
+        uint64_t two = 2ull * v[a] + 1ull;
+        phi[a] = (int32_t)((two << 6) >> depth);
+        for (int k = 0; k < OR_BANDS; ++k) {
+            uint32_t th = (uint32_t)(((two << (k + 8)) >> (depth + 1)) & 255u);
+            phi[3 + 3 * k + a] = sin8[th];
+            phi[3 + 3 * OR_BANDS + 3 * k + a] = sin8[(th + 64u) & 255u];
+        }
+    }
+}
+
+static int32_t or_rq_f32(int32_t acc, float s)
+{
+    float v = rintf((float)acc * s);
+    if (v < 0.0f) v = 0.0f;
+    if (v > 127.0f) v = 127.0f;
+    return (int32_t)v;
+}
+
+/* Head parameters (mean in 1/256 symbol, n = 4096 + log2-rate in 1/256) of channel c. */
+void or_pe_head(const or_pe_model *M, const int32_t *u, int c, const int32_t *phi,
+                int32_t *mu8, int32_t *n)
+{
+    int32_t x[OR_KIN], h1[OR_HID], h2[OR_HID];
+    for (int j = 0; j < OR_CTX; ++j) x[j] = u[j];
+    for (int k = 0; k < OR_NPHI; ++k) x[OR_CTX + k] = phi[k];
+    x[OR_KIN - 1] = 0;
+    for (int o = 0; o < OR_HID; ++o) {
+        int32_t acc = M->b1[c * OR_HID + o];
+        for (int k = 0; k < OR_KIN; ++k) acc += (int32_t)M->w1[o * OR_KIN + k] * x[k];
+        h1[o] = or_rq_f32(acc, M->s1);
+    }
+    for (int o = 0; o < OR_HID; ++o) {
+        int32_t acc = M->b2[o];
+        for (int k = 0; k < OR_HID; ++k) acc += (int32_t)M->w2[o * OR_HID + k] * h1[k];
+        h2[o] = or_rq_f32(acc, M->s2);
+    }
+    int32_t z[2];
+    for (int o = 0; o < 2; ++o) {
+        int32_t acc = M->b3[o];
+        for (int k = 0; k < OR_HID; ++k) acc += (int32_t)M->w3[o * OR_HID + k] * h2[k];
+        z[o] = acc;
+    }
+    float vm = rintf((float)z[0] * M->smu);
+    if (vm < -32640.0f) vm = -32640.0f;
+    if (vm > 32640.0f) vm = 32640.0f;
+    float vl = rintf((float)z[1] * M->slr);
+    if (vl < -2048.0f) vl = -2048.0f;
+    if (vl > 1536.0f) vl = 1536.0f;
+    *mu8 = 32640 + (int32_t)vm;
+    *n = 4096 + (int32_t)vl;
+}
+
+/* Cumulative count below symbol s (0..256) of the integer Laplace with (mu8, n). */
+uint32_t or_pe_cdf(int32_t mu8, int32_t n, int s, const uint32_t *exp2q)
+{
+    if (s <= 0) return 0;
+    if (s >= OR_NSYM) return OR_M;
+    int q = (n + 255) >> 8;
+    uint64_t R = exp2q[(uint32_t)(-n) & 255u] >> (23 - q);
+    int64_t d = 256 * (int64_t)s - 128 - mu8;
+    uint64_t ad = (uint64_t)(d < 0 ? -d : d);
+    uint64_t t = (ad * R) >> 16;
+    if (t > 6144) t = 6144;
+    uint64_t e = exp2q[t & 255] >> (t >> 8);
+    uint64_t F = d < 0 ? (e >> 1) : ((1ull << 23) - (e >> 1));
+    return (uint32_t)s + (uint32_t)((F * 65280ull) >> 23);
+}
+
+/* Decodes lanes [0, n_lanes) coded with the position-aware model: the stream order and the
+ * group format are those of the plain learned decoder; token (row, c) is found by walking
+ * the CDF upwards from symbol 0.  coord: uint32 [3][n_rows] voxel coordinates of the rows. */
+int or_rans_decode_pe(const or_pe_model *M, const uint32_t *exp2q, const int8_t *sin8,
+                      const uint32_t *coord, int64_t n_rows, int depth, const int64_t *lane_row,
+                      int64_t n_lanes, const uint8_t *payload, int64_t pay_len,
+                      const uint64_t *grp_off, const uint32_t *grp_words, uint8_t *syms)
+{
+    int64_t g = 0;
+    for (int64_t j0 = 0; j0 < n_lanes; j0 += 32, ++g) {
+        int64_t j1 = j0 + 32 < n_lanes ? j0 + 32 : n_lanes;
+        int nl = (int)(j1 - j0);
+        or_reader r;
+        uint32_t x[32];
+        if (or_group_setup(&r, x, nl, payload, pay_len, grp_off[g], grp_words[g])) return -1;
+        int64_t maxn = 0;
+        for (int j = 0; j < nl; ++j) {
+            int64_t n = (lane_row[j0 + j + 1] - lane_row[j0 + j]) * OR_NCHAN;
+            if (n > maxn) maxn = n;
+        }
+        for (int64_t t = 0; t < maxn; ++t) {
+            for (int j = 0; j < nl; ++j) {
+                int64_t row0 = lane_row[j0 + j];
+                int64_t n = (lane_row[j0 + j + 1] - row0) * OR_NCHAN;
+                if (t >= n) continue;
+                int64_t row = row0 + t / OR_NCHAN;
+                int c = (int)(t % OR_NCHAN);
+                int32_t u[OR_CTX], phi[OR_NPHI], mu8, nn;
+                uint32_t v[3] = {coord[row], coord[n_rows + row], coord[2 * n_rows + row]};
+                or_context(syms, row, row0, c, u);
+                or_pe_phi(v, depth, sin8, phi);
+                or_pe_head(M, u, c, phi, &mu8, &nn);
+                uint32_t slot = x[j] & (OR_M - 1);
+                int s = 0;
+                while (s < OR_NSYM - 1 && or_pe_cdf(mu8, nn, s + 1, exp2q) <= slot) ++s;
+                uint32_t cs = or_pe_cdf(mu8, nn, s, exp2q);
+                uint32_t fs = or_pe_cdf(mu8, nn, s + 1, exp2q) - cs;
+                syms[row * OR_NCHAN + c] = (uint8_t)s;
+                x[j] = fs * (x[j] >> OR_PROB_BITS) + slot - cs;
+                if (x[j] < OR_L) x[j] = (x[j] << 16) | or_read(&r);
+            }
+            if (r.bad) return -1;
+        }
+        if (or_group_finish(&r, x, nl)) return -1;
+    }
+    return 0;
 }

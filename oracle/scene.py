@@ -17,7 +17,9 @@ Steps (the decoded values are fixed by steps 1-5 alone: the coders change only t
   5. dequantize: v' = fl32(fl32(q * step) + offset), two roundings, no fused multiply-add;
   6. code the tokens: channel-wise fixed-length (Sec. 3.4.1, "UltraFast"), channel-wise
      static-frequency rANS, or rANS driven by the learned local autoregressive model
-     (Sec. 3.4.2, groups of W Gaussians decoded in parallel = rANS lanes).
+     (Sec. 3.4.2, groups of W Gaussians decoded in parallel = rANS lanes), either the plain
+     model (softmax over 256 symbols) or the position-aware one (Fourier positional
+     embedding of the decoded voxel and a Laplace head, oracle/model_pe.py).
 """
 from __future__ import annotations
 
@@ -26,12 +28,12 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import native
+from . import model_pe, native
 from .exp2q import exp2q_table
 
 MAGIC = 0x31534753  # "SGS1"
 VERSION = 1
-MODE_FIXED, MODE_STATIC, MODE_LEARNED = 0, 1, 2
+MODE_FIXED, MODE_STATIC, MODE_LEARNED, MODE_LEARNED_PE = 0, 1, 2, 3
 GEO_RAW, GEO_RANS = 0, 1
 NCHAN = 56
 NSYM = 256
@@ -382,6 +384,37 @@ def rans_decode_learned(model, lane_row, lane_lo, lane_hi, payload, goff, gw, n_
     return syms[:n_rows]
 
 
+def rans_decode_pe(model: dict, coord: np.ndarray, depth: int, lane_row: np.ndarray, payload, goff, gw) -> np.ndarray:
+    """Position-aware learned decode of every lane; row-major symbols [n_rows, 56]."""
+    L = native.lib()
+    ms = native.pe_model_struct(model)
+    n_rows = int(lane_row[-1])
+    syms = np.zeros((max(n_rows, 1), NCHAN), np.uint8)
+    pay = np.frombuffer(payload, np.uint8).copy() if len(payload) else np.zeros(1, np.uint8)
+    crd = np.ascontiguousarray(coord if n_rows else np.zeros((3, 1)), np.uint32)
+    lr = np.ascontiguousarray(lane_row, np.int64)
+    go = np.ascontiguousarray(goff, np.uint64)
+    gwa = np.ascontiguousarray(gw if len(gw) else np.zeros(1), np.uint32)
+    ex = _exp2q_arr()
+    s8 = _sin8_arr()
+    rc = L.or_rans_decode_pe(native.ctypes.byref(ms), native.ptr(ex), native.ptr(s8), native.ptr(crd), n_rows,
+                             depth, native.ptr(lr), len(lane_row) - 1, native.ptr(pay), len(payload),
+                             native.ptr(go), native.ptr(gwa), native.ptr(syms))
+    if rc != 0:
+        raise ValueError("corrupt rANS stream")
+    return syms[:n_rows]
+
+
+_SIN8 = None
+
+
+def _sin8_arr() -> np.ndarray:
+    global _SIN8
+    if _SIN8 is None:
+        _SIN8 = model_pe.sin8_table().astype(np.int8)
+    return _SIN8
+
+
 # ----------------------------------------------------------------------------- the pipeline
 
 @dataclass
@@ -448,7 +481,7 @@ def encode(pos: np.ndarray, attr: np.ndarray, *, mode: int, depth: int, bits=8, 
            geo_mode: int = GEO_RANS, geo_lanes: int = 0, model: dict | None = None,
            prep: Prepared | None = None) -> bytes:
     """Scene -> bitstream (layout documented in the design notes and in include/sgs.h)."""
-    if mode in (MODE_STATIC, MODE_LEARNED):
+    if mode in (MODE_STATIC, MODE_LEARNED, MODE_LEARNED_PE):
         bits = 8
     P = prep if prep is not None else prepare(pos, attr, depth, bits)
     if mode != MODE_FIXED and np.any(P.bits != 8):
@@ -497,12 +530,18 @@ def encode(pos: np.ndarray, attr: np.ndarray, *, mode: int, depth: int, bits=8, 
             tab_id = np.tile(np.arange(NCHAN, dtype=np.uint8), nr)
             perm, rows_start = static_row_order(nr, L)
             f, cc = static_fc(syms[perm].ravel(), tab_id, tabs) if nr else (np.zeros(0), np.zeros(0))
-        else:
+        elif mode == MODE_LEARNED:
             if model is None:
                 raise ValueError("learned mode needs a model")
             validate_model(_model_arrays(model))
             attr_tab = model_bytes(model)
             f, cc = learned_fc(model, syms, lane_row, 0, L)
+        else:
+            if model is None:
+                raise ValueError("learned mode needs a model")
+            model_pe.validate(model)
+            attr_tab = model_pe.model_bytes(model)
+            f, cc = model_pe.token_fc(model, syms, lane_row, P.coord, depth)
         starts = rows_start * NCHAN if mode == MODE_STATIC else lane_row * NCHAN
         attr_pay, goff, gw = rans_encode(starts, f, cc)
         attr_grp = group_table_bytes(goff, gw)
@@ -642,8 +681,11 @@ def decode(buf: bytes) -> dict:
             syms = rans_decode_static(rows_start * NCHAN, tab_id, tabs, pay, goff, gw)
             q = np.zeros((nr, NCHAN), np.uint32)
             q[perm] = syms.reshape(nr, NCHAN)
-        else:
+        elif mode == MODE_LEARNED:
             model = parse_model(buf, h["off_attr_tab"])
             q = rans_decode_learned(model, lane_row, 0, L, pay, goff, gw, nr).astype(np.uint32)
+        else:
+            model = model_pe.parse_model(buf, h["off_attr_tab"])
+            q = rans_decode_pe(model, coord, D, lane_row, pay, goff, gw).astype(np.uint32)
     attr = np.stack([dequantize(q[:, c], step[c], offset[c]) for c in range(NCHAN)]) if nr else np.zeros((NCHAN, 0), np.float32)
     return {"attr": attr, "pos": position(coord, D), "coord": coord, "q": q, "header": h}

@@ -156,6 +156,27 @@ def kaiming_init(seed: int, n_ctx: int = 4, n_emb: int = 16, hidden: int = 64, n
     }
 
 
+def kaiming_init_pe(seed: int, n_chan: int = N_CHAN) -> dict:
+    """Seeded initial float weights of the position-aware model: the projection of the 75
+    embedding inputs to 32, layer 1 over [context (4), channel embedding (16), projection
+    (32)], layer 2, and the 2-output head (Kaiming-uniform, head scaled by 0.1 so that the
+    initial Laplace sits near the middle of the token range; biases zero, embedding N(0, 1)).
+    Passed as inputs to both trainers."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def ku(fan_out, fan_in, scale=1.0):
+        bound = math.sqrt(6.0 / fan_in)
+        return (scale * rng.uniform(-bound, bound, size=(fan_out, fan_in))).astype(np.float32)
+
+    return {
+        "emb": rng.standard_normal((n_chan, 16)).astype(np.float32),
+        "wp": ku(32, 75), "bp": np.zeros(32, np.float32),
+        "w1": ku(64, 52), "b1": np.zeros(64, np.float32),
+        "w2": ku(64, 64), "b2": np.zeros(64, np.float32),
+        "w3": ku(2, 64, 0.1), "b3": np.zeros(2, np.float32),
+    }
+
+
 # Workload recipes (sizes of the paper-shaped configurations)
 SMALL = dict(n=20_000, seed=0, depth=12, lanes=32)            # static channel-wise, 8-bit
 FIXED_1M = dict(n=1_000_000, seed=1000, depth=16)             # fixed-length 4..10 bits
