@@ -48,6 +48,9 @@ extern "C" {
 #define SGS_MODE_FIXED 0      /* channel-wise fixed-length codes (Sec. 3.4.1)            */
 #define SGS_MODE_STATIC 1     /* channel-wise static-frequency rANS                       */
 #define SGS_MODE_LEARNED 2    /* rANS with the learned context model (Sec. 3.4.2)        */
+#define SGS_MODE_LEARNED_PE 3 /* rANS with the position-aware learned model: the Fourier
+                                 positional embedding of Sec. 3.4.2 (L = 12 bands, d = 32)
+                                 and a conditional Laplace head (Sec. 3.2)                  */
 #define SGS_GEO_RAW 0         /* occupancy tokens stored as bytes                         */
 #define SGS_GEO_RANS 1        /* levels of >= 4096 nodes coded with per-level rANS tables */
 
@@ -95,10 +98,22 @@ typedef struct {
     uint32_t lanes;           /* attribute rANS lanes (entropy-coded modes), >= 1          */
     uint32_t geo_lanes;       /* geometry rANS lanes, 0 = about 128 tokens per lane        */
     uint32_t bits[SGS_NCHAN]; /* fixed-length bit widths 1..16 (8 is forced for rANS modes)*/
-    const void *model;        /* learned mode: SGS_MODEL_BYTES of frozen model, else NULL  */
+    const void *model;        /* learned modes: the frozen model (SGS_MODEL_BYTES, or
+                                 SGS_MODEL_PE_BYTES for SGS_MODE_LEARNED_PE), else NULL    */
 } sgs_encode_params;
 
 #define SGS_MODEL_BYTES 36384
+
+/* Frozen position-aware model (the model section of SGS_MODE_LEARNED_PE), little endian:
+ *   f32 s1, s2 (requantisation scales, in (0, 127]), smu, slr (head multipliers, > 0);
+ *   16 zero bytes; i32 B1[56][64] (channel embedding and projection bias folded in);
+ *   i32 b2[64]; i32 b3[2] + 8 zero bytes; i8 W1[64][80] over [u (4); phi (75); 0]
+ *   (the projection folded in); i8 W2[64][64]; i8 W3[2][64].  Biases below 2^23 in
+ *   magnitude.  Inference: h = clamp(rint(fl32(acc * s)), 0, 127) per layer; mean
+ *   mu8 = 32640 + clamp(rint(z0 * smu), +-32640) (1/256 symbol); n = 4096 +
+ *   clamp(rint(z1 * slr), -2048, 1536) (log2 rate in 1/256, plus 16); token CDF
+ *   cdf(s) = s + floor(65280 F(s - 1/2) / 2^23), F the Laplace CDF through EXP2Q.        */
+#define SGS_MODEL_PE_BYTES 23984
 
 /* Training parameters of the context model (the learned part, Sec. 3.4.2). */
 typedef struct {
@@ -111,6 +126,13 @@ typedef struct {
 /* Float weights of the context model, all fp32, row-major:
  *   emb[56][16], w1[64][20], b1[64], w2[64][64], b2[64], w3[256][64], b3[256].             */
 #define SGS_WEIGHTS_FLOATS (56 * 16 + 64 * 20 + 64 + 64 * 64 + 64 + 256 * 64 + 256)
+
+/* Float weights of the position-aware model, all fp32, row-major:
+ *   emb[56][16], wp[32][75], bp[32] (the projection PE = wp phi + bp of Sec. 3.4.2),
+ *   w1[64][52] over [u / 128 (4), emb (16), PE (32)], b1[64], w2[64][64], b2[64],
+ *   w3[2][64], b3[2] (mean 127.5 + 64 z0 clipped to [0, 255], log2 rate z1 clipped to
+ *   [-8, 6]).                                                                            */
+#define SGS_WEIGHTS_PE_FLOATS (56 * 16 + 32 * 75 + 32 + 64 * 52 + 64 + 64 * 64 + 64 + 2 * 64 + 2)
 
 /* ------------------------------------------------------------------ context */
 

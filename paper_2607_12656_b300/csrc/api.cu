@@ -70,8 +70,15 @@ size_t scratch_need(const sgs_scene_info &info, Scratch *s, uint8_t *base) {
     t.tables = take((uint64_t)n_tab * kTabBytes);
     t.dup_prefix = reinterpret_cast<uint32_t *>(take(4ull * (info.n_dup + 1)));
     t.learned = take(info.mode == SGS_MODE_LEARNED ? learned_work_bytes(info) : 0);
+    t.coord = reinterpret_cast<uint32_t *>(take(info.mode == SGS_MODE_LEARNED_PE ? 12ull * info.n_rows : 0));
     if (s) *s = t;
     return off;
+}
+
+sgs_scene_out effective_out(const sgs_scene_info &info, const sgs_scene_out &out, const Scratch &s) {
+    sgs_scene_out o = out;
+    if (info.mode == SGS_MODE_LEARNED_PE && !o.coord) o.coord = s.coord;
+    return o;
 }
 
 }  // namespace sgs
@@ -224,7 +231,7 @@ extern "C" int scene_query(const uint8_t *b, size_t len, sgs_scene_info *info) {
     info->n_geo_coded = rd64(b + 56);
     for (int i = 0; i < 11; ++i) info->off[i] = rd64(b + 64 + 8 * i);
     info->total_len = info->off[S_TOTAL];
-    if (n_chan != (uint32_t)kNChan || info->mode > 2 || info->geo_mode > 1) return SGS_E_INVALID;
+    if (n_chan != (uint32_t)kNChan || info->mode > SGS_MODE_LEARNED_PE || info->geo_mode > 1) return SGS_E_INVALID;
     if (info->depth < 1 || info->depth > SGS_MAX_DEPTH) return SGS_E_INVALID;
     if (info->total_len != len) return SGS_E_INVALID;
     if (info->off[0] != (uint64_t)kHeaderBytes) return SGS_E_INVALID;
@@ -276,6 +283,8 @@ extern "C" int scene_query(const uint8_t *b, size_t len, sgs_scene_info *info) {
         if (sec(S_ATTR_GRP) < 8 * (G + 1) + 4 * G) return SGS_E_INVALID;
         if (info->mode == SGS_MODE_LEARNED && sec(S_ATTR_TAB) < (uint64_t)SGS_MODEL_BYTES)
             return SGS_E_INVALID;
+        if (info->mode == SGS_MODE_LEARNED_PE && sec(S_ATTR_TAB) < (uint64_t)SGS_MODEL_PE_BYTES)
+            return SGS_E_INVALID;
     }
     // static tables: walk the variable-size tables once (presence mask, then (f-1) per
     // present symbol, padded to 16 bytes) and record where each one starts
@@ -303,11 +312,15 @@ extern "C" int scene_query(const uint8_t *b, size_t len, sgs_scene_info *info) {
 
 // Enqueues every stage of one scene's decode using scratch `base`.  The attribute decode is
 // forked onto the context's attribute stream (it does not depend on the geometry) and joined
-// back into `st` at the end, so the two halves overlap on the device.
+// back into `st` at the end, so the two halves overlap on the device.  The position-aware
+// model reads the decoded voxels (attributes are coded upon the decoded geometry, Sec. 3.4),
+// so its decode follows the octree on the geometry stream.
 static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &info,
-                      const sgs_scene_out &out, uint8_t *base, cudaStream_t st) {
+                      const sgs_scene_out &user_out, uint8_t *base, cudaStream_t st) {
     Scratch s;
     scratch_need(info, &s, base);
+    const sgs_scene_out out = effective_out(info, user_out, s);
+    const bool after_geo = info.mode == SGS_MODE_LEARNED_PE;
     GeoPlan plan;
     make_geo_plan(info, &plan);
     int *status = c->status_dev;
@@ -327,15 +340,17 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
     if (cudaEventRecord(c->fork, st) != cudaSuccess || cudaStreamWaitEvent(c->aux, c->fork, 0) != cudaSuccess ||
         cudaStreamWaitEvent(c->geo, c->fork, 0) != cudaSuccess)
         return SGS_E_CUDA;
-    if (c->profile) cudaEventRecord(c->amarks[0], c->aux);
-    if (info.n_rows) c->launches += 1;
-    switch (info.mode) {
-        case SGS_MODE_FIXED: e = launch_fixed(bits, info, out, status, c->aux); break;
-        case SGS_MODE_STATIC: e = launch_rans_static_attr(bits, info, attr_tables, out, status, c->aux); break;
-        default: e = launch_learned_decode(bits, info, out, s.learned, status, c->aux); break;
+    if (!after_geo) {
+        if (c->profile) cudaEventRecord(c->amarks[0], c->aux);
+        if (info.n_rows) c->launches += 1;
+        switch (info.mode) {
+            case SGS_MODE_FIXED: e = launch_fixed(bits, info, out, status, c->aux); break;
+            case SGS_MODE_STATIC: e = launch_rans_static_attr(bits, info, attr_tables, out, status, c->aux); break;
+            default: e = launch_learned_decode(bits, info, out, s.learned, status, c->aux); break;
+        }
+        if (e != cudaSuccess) return SGS_E_CUDA;
+        if (c->profile) cudaEventRecord(c->amarks[1], c->aux);
     }
-    if (e != cudaSuccess) return SGS_E_CUDA;
-    if (c->profile) cudaEventRecord(c->amarks[1], c->aux);
     if (cudaEventRecord(c->join, c->aux) != cudaSuccess) return SGS_E_CUDA;
     cudaStream_t gs = c->geo;
     if (info.geo_mode == SGS_GEO_RANS && info.n_geo) {
@@ -348,6 +363,12 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
     if ((e = launch_octree(info, plan, bits, s, out, status, gs)) != cudaSuccess) return SGS_E_CUDA;
     if (info.n_rows) c->launches += octree_launches(info, plan);
     if (c->profile && c->n_marks <= kMaxStages) cudaEventRecord(c->marks[c->n_marks++], gs);
+    if (after_geo) {
+        if (c->profile) cudaEventRecord(c->amarks[0], gs);
+        if ((e = launch_learned_pe_decode(bits, info, out, out.coord, status, gs)) != cudaSuccess) return SGS_E_CUDA;
+        if (info.n_rows) c->launches += 1;
+        if (c->profile) cudaEventRecord(c->amarks[1], gs);
+    }
     // join
     if (cudaEventRecord(c->gjoin, gs) != cudaSuccess || cudaStreamWaitEvent(st, c->join, 0) != cudaSuccess ||
         cudaStreamWaitEvent(st, c->gjoin, 0) != cudaSuccess)

@@ -49,7 +49,7 @@ namespace {
 
 constexpr int kMaxLaunches = 16 + SGS_MAX_DEPTH;
 
-enum Kind { K_TABLES, K_FIXED, K_ATTR, K_LEARNED, K_COPY, K_GEO, K_DUP, K_SCAN, K_WALK };
+enum Kind { K_TABLES, K_FIXED, K_ATTR, K_LEARNED, K_COPY, K_GEO, K_DUP, K_SCAN, K_WALK, K_LEARNED_PE };
 enum Role { R_MAIN, R_ATTR, R_GEO };
 
 struct LaunchRec {
@@ -75,6 +75,7 @@ size_t stage_bytes(Kind k) {
         case K_GEO: return stage_rans_geo_bytes();
         case K_DUP: return stage_dup_bytes();
         case K_SCAN: return stage_scan_bytes();
+        case K_LEARNED_PE: return stage_learned_pe_bytes();
         default: return stage_walk_bytes();
     }
 }
@@ -89,6 +90,7 @@ uint32_t stage_items(Kind k, int variant, const SceneRef &r, void *par) {
         case K_GEO: return stage_rans_geo(r, par);
         case K_DUP: return stage_dup(r, par);
         case K_SCAN: return stage_scan(r, variant, par);
+        case K_LEARNED_PE: return stage_learned_pe(r, par);
         default: return stage_walk(r, par);
     }
 }
@@ -103,6 +105,7 @@ cudaError_t launch_kind(Kind k, int variant, const MultiArgs &m, cudaStream_t st
         case K_GEO: return launch_rans_geo_multi(m, st);
         case K_DUP: return launch_dup_multi(m, st);
         case K_SCAN: return launch_scan_multi(variant, m, st);
+        case K_LEARNED_PE: return launch_learned_pe_multi(m, st);
         default: return launch_walk_multi(m, st);
     }
 }
@@ -134,12 +137,14 @@ struct BatchLayout {
     std::vector<LaunchRec> launches;
     std::vector<uint8_t> lists;  // uploaded to lists_off
     std::vector<uint32_t> need;  // work items of each scene over all launches
+    std::vector<sgs_scene_out> outs;  // each scene's outputs as the stages see them
     uint64_t zero_off, zero_bytes, status_off, done_off, times_off, start_off, need_off, lists_off, total;
 };
 
 static int build_layout(const sgs_batch_item *items, int n, uint8_t *base, BatchLayout *L) {
     L->scratch.assign(n, Scratch());
     L->plans.assign(n, GeoPlan());
+    L->outs.assign(n, sgs_scene_out());
     L->launches.clear();
     L->lists.clear();
     uint64_t off = 0;
@@ -150,6 +155,7 @@ static int build_layout(const sgs_batch_item *items, int n, uint8_t *base, Batch
         const size_t need = scratch_need(it.info, nullptr, nullptr);
         if (need != it.info.scratch_bytes) return SGS_E_INVALID;  // info not from scene_query
         scratch_need(it.info, &L->scratch[i], base ? base + off : nullptr);
+        L->outs[i] = effective_out(it.info, it.out, L->scratch[i]);
         make_geo_plan(it.info, &L->plans[i]);
         off += a256(need);
     }
@@ -170,7 +176,7 @@ static int build_layout(const sgs_batch_item *items, int n, uint8_t *base, Batch
     for (int i = 0; i < n; ++i) {
         refs[i].bits = items[i].bits_dev;
         refs[i].info = &items[i].info;
-        refs[i].out = &items[i].out;
+        refs[i].out = &L->outs[i];
         refs[i].s = &L->scratch[i];
         refs[i].plan = &L->plans[i];
         refs[i].status = reinterpret_cast<int *>(base ? base + L->status_off + 4ull * i : nullptr);
@@ -226,6 +232,8 @@ static int build_layout(const sgs_batch_item *items, int n, uint8_t *base, Batch
     if (rc == SGS_OK) rc = add(K_SCAN, 0, R_GEO);  // prefixes
     if (rc == SGS_OK) rc = add(K_SCAN, 2, R_GEO);  // parent entries
     if (rc == SGS_OK) rc = add(K_WALK, 0, R_GEO);
+    // the position-aware model reads the voxels the walk wrote: after it, on its stream
+    if (rc == SGS_OK) rc = add(K_LEARNED_PE, 0, R_GEO);
     if (rc != SGS_OK) return rc;
     L->lists.resize(a16(L->lists.size()));
     L->need_off = L->lists.size();

@@ -4,7 +4,8 @@
 //   depth D -> sort rows by (Morton code, original index) -> sparse-octree occupancy tokens
 //   per level, duplicate counts as metadata -> per-channel uniform quantization
 //   (offset = min, step = fl32((max-min)/(2^b-1)), q = clamp(rint((v-offset)/step))) ->
-//   channel-wise fixed-length packing, static-frequency rANS, or learned-model rANS.
+//   channel-wise fixed-length packing, static-frequency rANS, or learned-model rANS (the
+//   plain model or the position-aware one).
 // The output bytes are fully determined by the inputs (all tie-breaks fixed), so any two
 // correct encoders produce identical bitstreams.
 #include <cuda_runtime.h>
@@ -33,6 +34,7 @@ struct Prepared {
     uint32_t bits[kNChan];
     std::vector<uint8_t> q8;             // [rows][56] when every width <= 8
     std::vector<uint16_t> q16;           // [rows][56]
+    std::vector<uint32_t> coord;         // [3][rows] voxel coordinates of the rows
     float step[kNChan], offset[kNChan];
     uint32_t rows() const { return (uint32_t)keep.size(); }
 };
@@ -87,9 +89,13 @@ int prepare(const float *pos, const float *attr, uint32_t n, uint32_t D, const u
     });
     P.keep.resize(keep.size());
     std::vector<uint64_t> sc(keep.size());
+    P.coord.assign(3 * keep.size(), 0);
     for (size_t r = 0; r < ord.size(); ++r) {
         P.keep[r] = keep[ord[r]];
         sc[r] = code[ord[r]];
+        for (uint32_t b = 0; b < D; ++b)
+            for (int k = 0; k < 3; ++k)
+                P.coord[k * keep.size() + r] |= (uint32_t)((sc[r] >> (3 * b + 2 - k)) & 1u) << b;
     }
     // unique voxels and duplicate counts
     for (size_t r = 0; r < sc.size();) {
@@ -310,6 +316,10 @@ int rans_encode_static_device(const uint8_t *tok_lane_major, uint64_t nsym, cons
 int learned_encode_device(const uint8_t *model, const uint8_t *tokens, uint32_t n_rows, uint32_t lanes,
                           const std::vector<uint64_t> &lane_start, std::vector<uint8_t> &grp,
                           std::vector<uint8_t> &pay);
+bool pe_model_valid(const uint8_t *model);
+int learned_pe_encode_device(const uint8_t *model, const uint8_t *tokens, const uint32_t *coord, uint32_t depth,
+                             uint32_t n_rows, uint32_t lanes, const std::vector<uint64_t> &lane_start,
+                             std::vector<uint8_t> &grp, std::vector<uint8_t> &pay);
 
 }  // namespace sgs
 
@@ -333,11 +343,14 @@ extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, u
                             const sgs_encode_params *prm, uint8_t *out, size_t cap,
                             size_t *out_len) {
     if (!prm || !out_len || (n && (!pos || !attr))) return SGS_E_INVALID;
-    if (prm->mode > 2 || prm->geo_mode > 1) return SGS_E_INVALID;
+    if (prm->mode > SGS_MODE_LEARNED_PE || prm->geo_mode > 1) return SGS_E_INVALID;
     uint32_t bits[kNChan];
     for (int c = 0; c < kNChan; ++c) bits[c] = prm->mode == SGS_MODE_FIXED ? prm->bits[c] : 8u;
     if (prm->mode != SGS_MODE_FIXED && prm->lanes < 1) return SGS_E_INVALID;
     if (prm->mode == SGS_MODE_LEARNED && (!prm->model || !ctx)) return SGS_E_INVALID;
+    if (prm->mode == SGS_MODE_LEARNED_PE &&
+        (!prm->model || !ctx || !pe_model_valid(static_cast<const uint8_t *>(prm->model))))
+        return SGS_E_INVALID;
     Prepared P;
     int r = prepare(pos, attr, n, prm->depth, bits, P);
     if (r) return r;
@@ -437,13 +450,21 @@ extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, u
             } else {
                 rans_encode(starts, sf.data(), scu.data(), s_agrp, s_apay);
             }
-        } else {
+        } else if (prm->mode == SGS_MODE_LEARNED) {
             const uint8_t *m = static_cast<const uint8_t *>(prm->model);
             s_atab.assign(m, m + SGS_MODEL_BYTES);
             std::vector<uint8_t> tok(nsym);
             for (uint64_t i = 0; i < nsym; ++i) tok[i] = (uint8_t)P.q16[i];
             if (cudaSetDevice(ctx->device) != cudaSuccess) return SGS_E_CUDA;
             r = learned_encode_device(m, tok.data(), R, L, starts, s_agrp, s_apay);
+            if (r) return r;
+        } else {
+            const uint8_t *m = static_cast<const uint8_t *>(prm->model);
+            s_atab.assign(m, m + SGS_MODEL_PE_BYTES);
+            std::vector<uint8_t> tok(nsym);
+            for (uint64_t i = 0; i < nsym; ++i) tok[i] = (uint8_t)P.q16[i];
+            if (cudaSetDevice(ctx->device) != cudaSuccess) return SGS_E_CUDA;
+            r = learned_pe_encode_device(m, tok.data(), P.coord.data(), D, R, L, starts, s_agrp, s_apay);
             if (r) return r;
         }
     }

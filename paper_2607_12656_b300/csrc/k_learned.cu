@@ -21,6 +21,7 @@
 
 #include "exp2q_table.h"
 #include "sgs_device.cuh"
+#include "sgs_mma.cuh"
 #include "sgs_internal.h"
 
 namespace sgs {
@@ -44,15 +45,6 @@ __device__ __forceinline__ int32_t requant(int32_t acc, int32_t m, int32_t sh) {
 // int8 kind and a far slower int8 mma path.)
 constexpr int kBS = 72;  // smem row stride in bf16 elements (64 used): conflict-free fragments
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
 __device__ __forceinline__ uint32_t lds32(const __nv_bfloat16 *p) {
     return *reinterpret_cast<const uint32_t *>(p);
 }
@@ -68,13 +60,6 @@ __device__ __forceinline__ void ldsm_a(const __nv_bfloat16 *A, uint32_t &a0, uin
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
                  : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
                  : "r"(addr));
-}
-
-__device__ __forceinline__ __nv_bfloat16 bf(int v) { return __int2bfloat16_rn(v); }
-// Two small integers as a bf16 pair, the first in the low half.
-__device__ __forceinline__ uint32_t pack_bf16(int lo, int hi) {
-    __nv_bfloat162 h = __halves2bfloat162(bf(lo), bf(hi));
-    return *reinterpret_cast<uint32_t *>(&h);
 }
 
 struct LearnedParams {

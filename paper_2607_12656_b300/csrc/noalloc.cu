@@ -79,11 +79,13 @@ extern "C" int scene_decode_noalloc(const uint8_t *bits, const sgs_scene_info *i
     if (launch_tables(bits, *info, plan.n_coded_levels, s.tables, status, st) != cudaSuccess)
         return SGS_E_CUDA;
     uint8_t *attr_tables = s.tables + (size_t)plan.n_coded_levels * kTabBytes;
+    const sgs_scene_out o = effective_out(*info, *out, s);
     cudaError_t e = cudaSuccess;
     switch (info->mode) {
-        case SGS_MODE_FIXED: e = launch_fixed(bits, *info, *out, status, st); break;
-        case SGS_MODE_STATIC: e = launch_rans_static_attr(bits, *info, attr_tables, *out, status, st); break;
-        default: e = launch_learned_decode(bits, *info, *out, s.learned, status, st); break;
+        case SGS_MODE_FIXED: e = launch_fixed(bits, *info, o, status, st); break;
+        case SGS_MODE_STATIC: e = launch_rans_static_attr(bits, *info, attr_tables, o, status, st); break;
+        case SGS_MODE_LEARNED: e = launch_learned_decode(bits, *info, o, s.learned, status, st); break;
+        default: break;  // the position-aware model follows the octree
     }
     if (e != cudaSuccess) return SGS_E_CUDA;
     if (info->geo_mode == SGS_GEO_RANS && info->n_geo) {
@@ -91,7 +93,10 @@ extern "C" int scene_decode_noalloc(const uint8_t *bits, const sgs_scene_info *i
         if (launch_rans_static_geo(bits, *info, plan, s.tables, s.geo_bytes, status, st) != cudaSuccess)
             return SGS_E_CUDA;
     }
-    if (launch_octree(*info, plan, bits, s, *out, status, st) != cudaSuccess)
+    if (launch_octree(*info, plan, bits, s, o, status, st) != cudaSuccess)
+        return SGS_E_CUDA;
+    if (info->mode == SGS_MODE_LEARNED_PE &&
+        launch_learned_pe_decode(bits, *info, o, o.coord, status, st) != cudaSuccess)
         return SGS_E_CUDA;
     int host_status = SGS_OK;
     if (cudaMemcpyAsync(&host_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)

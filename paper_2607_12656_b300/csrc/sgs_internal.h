@@ -12,7 +12,8 @@
 //   geo_grp  u64 group_off[G+1] (bytes from geo_pay), u32 group_words[G]   (G = ceil(Lg/32))
 //   geo_pay  rANS group streams
 //   attr_tab fixed: u64 chan_off[57] (bytes from attr_pay); static: 56 tables as geo_tab;
-//            learned: the frozen model (SGS_MODEL_BYTES)
+//            learned: the frozen model (SGS_MODEL_BYTES); position-aware learned: the
+//            frozen model (SGS_MODEL_PE_BYTES)
 //   attr_grp as geo_grp with G = ceil(L/32)
 //   attr_pay payload
 #pragma once
@@ -56,6 +57,8 @@ struct Scratch {
     uint8_t *tables;        // expanded static tables
     uint32_t *dup_prefix;   // n_dup + 1
     uint8_t *learned;       // learned-mode per-scene work area
+    uint32_t *coord;        // position-aware mode: voxel coordinates [3][n_rows] when the
+                            // caller asks for none (the attribute model reads them)
 };
 
 size_t scratch_need(const sgs_scene_info &info, Scratch *layout, uint8_t *base);
@@ -87,6 +90,18 @@ cudaError_t launch_learned_decode(const uint8_t *bits, const sgs_scene_info &inf
                                   const sgs_scene_out &out, uint8_t *work, int *status,
                                   cudaStream_t st);
 size_t learned_work_bytes(const sgs_scene_info &info);
+// Position-aware learned decode: reads the rows' voxel coordinates coord [3][n_rows]
+// (written by the octree walk before it, in stream order).
+cudaError_t launch_learned_pe_decode(const uint8_t *bits, const sgs_scene_info &info,
+                                     const sgs_scene_out &out, const uint32_t *coord, int *status,
+                                     cudaStream_t st);
+// Encoder helper: f and cum of every token under a frozen position-aware model (device).
+cudaError_t launch_pe_fc(const uint8_t *model_dev, const uint8_t *tok_dev, const uint32_t *coord_dev,
+                         int depth, uint32_t n_rows, uint32_t lanes, uint32_t *f_dev,
+                         uint32_t *cum_dev, int *status, cudaStream_t st);
+// The outputs a decode works with: the caller's, with the coordinates redirected to
+// scratch when the position-aware model needs them and the caller passed none.
+sgs_scene_out effective_out(const sgs_scene_info &info, const sgs_scene_out &out, const Scratch &s);
 
 // Encoder helper: f and cum of every token under a frozen model (device arrays).
 cudaError_t launch_learned_fc(const uint8_t *model_dev, const uint8_t *tokens_dev,
@@ -162,6 +177,9 @@ cudaError_t launch_geo_copy_multi(const MultiArgs &m, cudaStream_t st);
 uint32_t stage_learned(const SceneRef &r, void *par);
 size_t stage_learned_bytes();
 cudaError_t launch_learned_multi(const MultiArgs &m, cudaStream_t st);
+uint32_t stage_learned_pe(const SceneRef &r, void *par);
+size_t stage_learned_pe_bytes();
+cudaError_t launch_learned_pe_multi(const MultiArgs &m, cudaStream_t st);
 // octree: duplicates, popcount scan with parent scatter, leaf walk
 uint32_t stage_dup(const SceneRef &r, void *par);
 size_t stage_dup_bytes();

@@ -12,12 +12,14 @@ import numpy as np
 from . import build as _build
 
 OK, E_INVALID, E_CORRUPT, E_NOMEM, E_CUDA, E_TIMEOUT, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
-MODE_FIXED, MODE_STATIC, MODE_LEARNED = 0, 1, 2
+MODE_FIXED, MODE_STATIC, MODE_LEARNED, MODE_LEARNED_PE = 0, 1, 2, 3
 GEO_RAW, GEO_RANS = 0, 1
 NCHAN = 56
 MAX_DEPTH = 21
 MODEL_BYTES = 36384
+MODEL_PE_BYTES = 23984
 WEIGHTS_FLOATS = 56 * 16 + 64 * 20 + 64 + 64 * 64 + 64 + 256 * 64 + 256
+WEIGHTS_PE_FLOATS = 56 * 16 + 32 * 75 + 32 + 64 * 52 + 64 + 64 * 64 + 64 + 2 * 64 + 2
 
 u32, u64, i32, P = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
 
@@ -314,7 +316,7 @@ def scene_encode(pos: np.ndarray, attr: np.ndarray, *, mode: int, depth: int, la
     mbuf = None
     if model is not None:
         mbuf = np.frombuffer(bytes(model), np.uint8).copy()
-        assert mbuf.size == MODEL_BYTES
+        assert mbuf.size == (MODEL_PE_BYTES if mode == MODE_LEARNED_PE else MODEL_BYTES)
         prm.model = mbuf.ctypes.data
     need = ctypes.c_size_t(0)
     h = ctx.handle if ctx is not None else None
