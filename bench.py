@@ -38,6 +38,11 @@ WORKLOADS = {
     "learned": dict(n=1_000_000, seed=2000, depth=16, mode=2, geo_mode=1, lanes=4096,
                     desc="learned-model scene decode: N=1,000,000 (900,000 kept), depth 16, 8-bit "
                          "tokens, 4,096 lanes, context MLP 4->64->64->256"),
+    "learned_pe": dict(n=1_000_000, seed=2000, depth=16, mode=3, geo_mode=1, lanes=28125,
+                       desc="position-aware learned scene decode: N=1,000,000 (900,000 kept), depth 16, "
+                            "8-bit tokens, 28,125 lanes (W = 32 rows per lane, the paper's fast group size), "
+                            "context MLP over 4 previous tokens + Fourier positional embedding of the decoded "
+                            "voxel (12 bands, 75 -> 32), Laplace head"),
     "small": dict(n=20_000, seed=0, depth=12, mode=1, geo_mode=1, lanes=32,
                   desc="small static scene decode: N=20,000 (18,000 kept), depth 12, 32 lanes"),
 }
@@ -220,10 +225,10 @@ def make_bitstream(w: dict, ctx=None):
     if w.get("geo_w"):  # geometry lanes for throughput: about geo_w coded tokens per lane
         kw["geo_lanes"] = geo_lanes_for(sc, w)
     model = None
-    if w["mode"] == 2:
+    if w["mode"] in (2, 3):
         from paper_2607_12656_b300 import learned
-        model = learned.train_and_freeze(ctx, sc, w["depth"], w["lanes"], steps=w.get("train_steps", 2000),
-                                         batch=65536, seed=1)
+        train = learned.train_and_freeze if w["mode"] == 2 else learned.train_and_freeze_pe
+        model = train(ctx, sc, w["depth"], w["lanes"], steps=w.get("train_steps", 2000), batch=65536, seed=1)
         kw["model"] = model
         kw["ctx"] = ctx
     return sc, sgs.scene_encode(sc.pos, sc.attr, **kw)
@@ -405,7 +410,9 @@ def run_ours(args, w):
         line["roofline_octree"] = {"bound": "hbm", "algorithmic_bytes": geo_alg,
                                    "achieved": geo_alg / (line["stage_ms"]["octree_positions"] / 1e3) / 1e9,
                                    "unit": "GB/s"}
-    if w["mode"] == 2:
+    if w["mode"] != 0:
+        line["config"]["attr_bits_per_gaussian"] = 8.0 * (info.total_len - info.off[7]) / n
+    if w["mode"] in (2, 3):
         from paper_2607_12656_b300 import learned
         tr = learned.LAST_TRAIN
         line["training"] = {"steps": tr["steps"], "batch": tr["batch"], "device_ms": tr["ms"],

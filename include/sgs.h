@@ -290,6 +290,12 @@ int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, uint32_t n,
 int scene_tokens(const float *pos, const float *attr, uint32_t n, uint32_t depth,
                  uint8_t *tokens, size_t cap, uint32_t *n_rows);
 
+/* As scene_tokens, plus the rows' voxel coordinates (host uint32 [3][n_rows], the decoder's
+ * coord output), the inputs of the position-aware model's training and freeze.  cap: rows
+ * the caller's arrays hold.                                                                  */
+int scene_rows(const float *pos, const float *attr, uint32_t n, uint32_t depth, uint8_t *tokens,
+               uint32_t *coord, uint32_t cap, uint32_t *n_rows);
+
 /* ------------------------------------------------------------------ autotuning */
 
 /* Lane-count tuning: the paper's complexity knob is the group size W, Gaussians per
@@ -349,6 +355,21 @@ int sgs_train_grad(sgs_ctx *ctx, const uint8_t *tokens_dev, uint32_t n_rows, uin
  * tokens (host uint8 [n_rows][56]) drawn with `seed`.  Errors: SGS_E_INVALID.              */
 int sgs_freeze(const float *weights, const uint8_t *tokens, uint32_t n_rows, uint32_t lanes,
                uint32_t seed, uint8_t *model_out);
+
+/* The position-aware model (SGS_MODE_LEARNED_PE; float layout SGS_WEIGHTS_PE_FLOATS): as
+ * sgs_train / sgs_train_grad / sgs_freeze with the rows' voxel coordinates (coord_dev device,
+ * coord host: uint32 [3][n_rows], from scene_rows) at octree depth `depth`.  Loss = code
+ * length in bits under the discretised Laplace (Sec. 3.2) with the coder's one-count floor,
+ * p(s) = (1 + 65280 P(s)) / 65536.  The freeze folds the embedding projection into layer 1
+ * and writes SGS_MODEL_PE_BYTES.  Errors: SGS_E_INVALID, SGS_E_NOMEM, SGS_E_CUDA.          */
+int sgs_train_pe(sgs_ctx *ctx, const uint8_t *tokens_dev, const uint32_t *coord_dev, uint32_t depth,
+                 uint32_t n_rows, uint32_t lanes, const sgs_train_params *params, uint32_t step0,
+                 float *weights_dev, float *adam_dev, float *loss_dev);
+int sgs_train_pe_grad(sgs_ctx *ctx, const uint8_t *tokens_dev, const uint32_t *coord_dev, uint32_t depth,
+                      uint32_t n_rows, uint32_t lanes, const int64_t *pos_dev, uint32_t batch,
+                      const float *weights_dev, float *grad_dev, float *loss_host);
+int sgs_freeze_pe(const float *weights, const uint8_t *tokens, const uint32_t *coord, uint32_t depth,
+                  uint32_t n_rows, uint32_t lanes, uint32_t seed, uint8_t *model_out);
 
 #ifdef __cplusplus
 }

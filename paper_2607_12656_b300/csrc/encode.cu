@@ -339,6 +339,22 @@ extern "C" int scene_tokens(const float *pos, const float *attr, uint32_t n, uin
     return SGS_OK;
 }
 
+extern "C" int scene_rows(const float *pos, const float *attr, uint32_t n, uint32_t depth, uint8_t *tokens,
+                          uint32_t *coord, uint32_t cap, uint32_t *n_rows) {
+    if (!pos || !attr || !n_rows) return SGS_E_INVALID;
+    uint32_t bits[kNChan];
+    for (int c = 0; c < kNChan; ++c) bits[c] = 8;
+    Prepared P;
+    int r = prepare(pos, attr, n, depth, bits, P);
+    if (r) return r;
+    const uint32_t R = P.rows();
+    *n_rows = R;
+    if (cap < R || ((!tokens || !coord) && R)) return SGS_E_INVALID;
+    for (size_t i = 0; i < (size_t)R * kNChan; ++i) tokens[i] = (uint8_t)P.q16[i];
+    for (int k = 0; k < 3; ++k) memcpy(coord + (size_t)k * R, P.coord.data() + (size_t)k * R, 4ull * R);
+    return SGS_OK;
+}
+
 extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, uint32_t n,
                             const sgs_encode_params *prm, uint8_t *out, size_t cap,
                             size_t *out_len) {

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "sgs_internal.h"
+#include "sgs_train.cuh"
 
 namespace sgs {
 
@@ -27,26 +28,6 @@ namespace sgs {
 constexpr int kW_EMB = 0, kW_W1 = 896, kW_B1 = 2176, kW_W2 = 2240, kW_B2 = 6336, kW_W3 = 6400,
               kW_B3 = 22784, kW_TOTAL = 23040;
 static_assert(kW_TOTAL == SGS_WEIGHTS_FLOATS, "weight layout");
-
-__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
-    uint64_t z = x + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-// Token position of sample k of a step: hi32(splitmix64(seed<<40 ^ step<<20 ^ k)) * n >> 32.
-__host__ __device__ __forceinline__ uint64_t sample_pos(uint32_t seed, uint32_t step, uint32_t k,
-                                                        uint64_t n_total) {
-    const uint64_t key = ((uint64_t)seed << 40) ^ ((uint64_t)step << 20) ^ (uint64_t)k;
-    return ((splitmix64(key) >> 32) * n_total) >> 32;
-}
-
-// First row of the lane holding `row` (lanes own rows [floor(j n / L), floor((j+1) n / L))).
-__host__ __device__ __forceinline__ uint64_t lane_row0(uint64_t row, uint64_t n, uint64_t L) {
-    const uint64_t j = ((row + 1) * L + n - 1) / n - 1;
-    return j * n / L;
-}
 
 constexpr int kTR = 128;  // tokens per CTA in k_train_rows
 
@@ -186,7 +167,7 @@ __global__ void __launch_bounds__(kTR) k_train_rows(RowParams p) {
 
 // part[split][m][n] = sum over b in split of A[m][b] * Bm[n][b]; column n == N is the bias
 // (Bm = 1).  If onehot, A[m][b] = (cidx[b] == m).  CTA: 32 x 32 outputs, 256 threads.
-constexpr int kOT = 32, kOK = 64, kSplits = 16;
+constexpr int kOT = 32, kOK = 64, kSplits = kTrainSplits;
 
 struct OuterParams {
     const float *A;
@@ -255,10 +236,10 @@ __global__ void k_reduce(const float *part, int M, int N, int bias, float *grad,
     else grad[b_off + m] = s;
 }
 
-__global__ void k_adam(float *w, float *mom, const float *g, float lr, float bc1, float bc2) {
+__global__ void k_adam(float *w, float *mom, const float *g, int n, float lr, float bc1, float bc2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= kW_TOTAL) return;
-    float *m = mom, *v = mom + kW_TOTAL;
+    if (i >= n) return;
+    float *m = mom, *v = mom + n;
     const float gi = g[i];
     m[i] = 0.9f * m[i] + 0.1f * gi;
     v[i] = 0.999f * v[i] + 0.001f * gi * gi;
@@ -303,15 +284,30 @@ static int train_alloc(TrainBufs &t, uint32_t B) {
     return SGS_OK;
 }
 
-static cudaError_t outer_and_reduce(const TrainBufs &t, const float *A, const int32_t *cidx,
-                                    const float *Bm, int M, int N, int bias, int w_off, int b_off,
-                                    cudaStream_t st) {
-    OuterParams op{A, cidx, Bm, M, N, bias, t.B, t.ws.part};
+cudaError_t train_outer_reduce(const float *A, const int32_t *cidx, const float *Bm, int M, int N, int bias,
+                               uint32_t B, float *part, float *grad, int w_off, int b_off, cudaStream_t st) {
+    OuterParams op{A, cidx, Bm, M, N, bias, B, part};
     dim3 grid((M + kOT - 1) / kOT, (N + bias + kOT - 1) / kOT, kSplits);
     k_outer<<<grid, 256, 0, st>>>(op);
     const int n = M * (N + bias);
-    k_reduce<<<(n + 255) / 256, 256, 0, st>>>(t.ws.part, M, N, bias, t.ws.grad, w_off, b_off);
+    k_reduce<<<(n + 255) / 256, 256, 0, st>>>(part, M, N, bias, grad, w_off, b_off);
     return cudaGetLastError();
+}
+
+cudaError_t train_adam(float *w, float *mom, const float *g, int n, float lr, float bc1, float bc2, cudaStream_t st) {
+    k_adam<<<(n + 255) / 256, 256, 0, st>>>(w, mom, g, n, lr, bc1, bc2);
+    return cudaGetLastError();
+}
+
+cudaError_t train_loss(const float *part, int n, uint32_t B, float *out, cudaStream_t st) {
+    k_loss<<<1, 32, 0, st>>>(part, n, B, out);
+    return cudaGetLastError();
+}
+
+static cudaError_t outer_and_reduce(const TrainBufs &t, const float *A, const int32_t *cidx,
+                                    const float *Bm, int M, int N, int bias, int w_off, int b_off,
+                                    cudaStream_t st) {
+    return train_outer_reduce(A, cidx, Bm, M, N, bias, t.B, t.ws.part, t.ws.grad, w_off, b_off, st);
 }
 
 // One forward/backward: gradients into t.ws.grad, mean loss into *loss_dev (if non-null).
@@ -338,7 +334,7 @@ static cudaError_t train_grad_step(const TrainBufs &t, const uint8_t *tok, uint3
 
 // ------------------------------------------------------------------ freeze (host)
 
-static void q8(const float *w, int n, int stride, int cols, std::vector<int8_t> &q, double &s) {
+void q8(const float *w, int n, int stride, int cols, std::vector<int8_t> &q, double &s) {
     double mx = 0.0;
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < cols; ++j) mx = std::max(mx, fabs((double)w[i * stride + j]));
@@ -353,7 +349,7 @@ static void q8(const float *w, int n, int stride, int cols, std::vector<int8_t> 
         }
 }
 
-static int32_t clamp24(double v) {
+int32_t clamp24(double v) {
     const double lim = (double)((1 << 24) - 1);
     return (int32_t)std::min(lim, std::max(-lim, v));
 }
@@ -495,7 +491,7 @@ extern "C" int sgs_train(sgs_ctx *ctx, const uint8_t *tok, uint32_t n_rows, uint
         if (e != cudaSuccess) break;
         const double tt = (double)step + 1.0;
         const float bc1 = (float)(1.0 - pow(0.9, tt)), bc2 = (float)(1.0 - pow(0.999, tt));
-        k_adam<<<(kW_TOTAL + 255) / 256, 256, 0, st>>>(w, adam, t.ws.grad, prm->lr, bc1, bc2);
+        k_adam<<<(kW_TOTAL + 255) / 256, 256, 0, st>>>(w, adam, t.ws.grad, kW_TOTAL, prm->lr, bc1, bc2);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -102,6 +102,10 @@ def lib() -> ctypes.CDLL:
         L.scene_encode.argtypes = [P, P, P, u32, ctypes.POINTER(EncodeParams), P, ctypes.c_size_t,
                                    ctypes.POINTER(ctypes.c_size_t)]
         L.scene_tokens.argtypes = [P, P, u32, u32, P, ctypes.c_size_t, ctypes.POINTER(u32)]
+        L.scene_rows.argtypes = [P, P, u32, u32, P, P, u32, ctypes.POINTER(u32)]
+        L.sgs_train_pe.argtypes = [P, P, P, u32, u32, u32, ctypes.POINTER(TrainParams), u32, P, P, P]
+        L.sgs_train_pe_grad.argtypes = [P, P, P, u32, u32, u32, P, u32, P, P, ctypes.POINTER(ctypes.c_float)]
+        L.sgs_freeze_pe.argtypes = [P, P, P, u32, u32, u32, u32, P]
         L.sgs_train.argtypes = [P, P, u32, u32, ctypes.POINTER(TrainParams), u32, P, P, P]
         L.sgs_train_grad.argtypes = [P, P, u32, u32, P, u32, P, P, ctypes.POINTER(ctypes.c_float)]
         L.sgs_freeze.argtypes = [P, P, u32, u32, u32, P]
@@ -345,6 +349,21 @@ def scene_tokens(pos: np.ndarray, attr: np.ndarray, depth: int) -> np.ndarray:
     return tok[: nr.value].copy()
 
 
+def scene_rows(pos: np.ndarray, attr: np.ndarray, depth: int):
+    """(tokens uint8 [n_rows, 56], voxel coordinates uint32 [3, n_rows]) as the encoder sees
+    the rows."""
+    pos = np.ascontiguousarray(pos, np.float32)
+    attr = np.ascontiguousarray(attr, np.float32)
+    n = pos.shape[1]
+    tok = np.zeros((max(n, 1), NCHAN), np.uint8)
+    crd = np.zeros(3 * max(n, 1), np.uint32)
+    nr = u32(0)
+    _check(lib().scene_rows(pos.ctypes.data, attr.ctypes.data, n, depth, tok.ctypes.data, crd.ctypes.data,
+                            max(n, 1), ctypes.byref(nr)), "scene_rows")
+    r = nr.value
+    return tok[:r].copy(), crd[:3 * r].reshape(3, r).copy()
+
+
 # ----------------------------------------------------------------------------- learned part
 
 def sgs_train(ctx: Context, tokens_dev, n_rows: int, lanes: int, weights_dev, adam_dev, *, steps: int,
@@ -370,6 +389,55 @@ def sgs_freeze(weights: np.ndarray, tokens: np.ndarray, lanes: int, seed: int) -
     _check(lib().sgs_freeze(w.ctypes.data, t.ctypes.data, t.shape[0], lanes, seed, out.ctypes.data),
            "sgs_freeze")
     return out.tobytes()
+
+
+def sgs_train_pe(ctx: Context, tokens_dev, coord_dev, depth: int, n_rows: int, lanes: int, weights_dev, adam_dev,
+                 *, steps: int, batch: int = 65536, seed: int = 0, lr: float = 1e-3, step0: int = 0,
+                 loss_dev=None) -> None:
+    prm = TrainParams(steps, batch, seed, lr)
+    _check(lib().sgs_train_pe(ctx.handle, _ptr(tokens_dev), _ptr(coord_dev), depth, n_rows, lanes,
+                              ctypes.byref(prm), step0, _ptr(weights_dev), _ptr(adam_dev), _ptr(loss_dev)),
+           "sgs_train_pe")
+
+
+def sgs_train_pe_grad(ctx: Context, tokens_dev, coord_dev, depth: int, n_rows: int, lanes: int, pos_dev,
+                      weights_dev, grad_dev) -> float:
+    loss = ctypes.c_float(0)
+    n = int(pos_dev.numel())
+    _check(lib().sgs_train_pe_grad(ctx.handle, _ptr(tokens_dev), _ptr(coord_dev), depth, n_rows, lanes,
+                                   _ptr(pos_dev), n, _ptr(weights_dev), _ptr(grad_dev), ctypes.byref(loss)),
+           "sgs_train_pe_grad")
+    return float(loss.value)
+
+
+def sgs_freeze_pe(weights: np.ndarray, tokens: np.ndarray, coord: np.ndarray, depth: int, lanes: int,
+                  seed: int) -> bytes:
+    w = np.ascontiguousarray(weights, np.float32)
+    assert w.size == WEIGHTS_PE_FLOATS
+    t = np.ascontiguousarray(tokens, np.uint8)
+    c = np.ascontiguousarray(coord, np.uint32)
+    assert c.shape == (3, t.shape[0])
+    out = np.zeros(MODEL_PE_BYTES, np.uint8)
+    _check(lib().sgs_freeze_pe(w.ctypes.data, t.ctypes.data, c.ctypes.data, depth, t.shape[0], lanes, seed,
+                               out.ctypes.data), "sgs_freeze_pe")
+    return out.tobytes()
+
+
+WEIGHT_PE_SHAPES = [("emb", (56, 16)), ("wp", (32, 75)), ("bp", (32,)), ("w1", (64, 52)), ("b1", (64,)),
+                    ("w2", (64, 64)), ("b2", (64,)), ("w3", (2, 64)), ("b3", (2,))]
+
+
+def pack_weights_pe(d: dict) -> np.ndarray:
+    return np.concatenate([np.asarray(d[k], np.float32).reshape(-1) for k, _ in WEIGHT_PE_SHAPES])
+
+
+def unpack_weights_pe(flat: np.ndarray) -> dict:
+    out, o = {}, 0
+    for k, shp in WEIGHT_PE_SHAPES:
+        n = int(np.prod(shp))
+        out[k] = np.asarray(flat[o:o + n], np.float32).reshape(shp)
+        o += n
+    return out
 
 
 WEIGHT_SHAPES = [("emb", (56, 16)), ("w1", (64, 20)), ("b1", (64,)), ("w2", (64, 64)), ("b2", (64,)),

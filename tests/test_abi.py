@@ -112,6 +112,29 @@ def test_freeze_matches_oracle(small_scene):
         assert got == want
 
 
+def test_scene_rows_match_oracle(small_scene):
+    """Tokens and voxel coordinates of the rows, as the oracle prepares them."""
+    P = S.prepare(small_scene.pos, small_scene.attr, 12, 8)
+    tok, crd = sgs.scene_rows(small_scene.pos, small_scene.attr, 12)
+    assert np.array_equal(tok, P.q.astype(np.uint8)) and np.array_equal(crd, P.coord)
+
+
+def test_freeze_pe_matches_oracle(small_scene):
+    """Given the same fp32 weights, rows and voxels, the library's freeze of the
+    position-aware model emits the oracle's model byte for byte."""
+    from oracle import model_pe as E
+    from paper_2607_12656_b300.scenegen import kaiming_init_pe
+    for depth, lanes, seed, wseed in ((12, 32, 3, 1), (9, 7, 11, 2), (16, 4096, 5, 3)):
+        P = S.prepare(small_scene.pos, small_scene.attr, depth, 8)
+        q = P.q.astype(np.uint8)
+        w = kaiming_init_pe(wseed)
+        rng = np.random.default_rng(wseed)
+        w = {k: (v + 0.05 * rng.standard_normal(v.shape)).astype(np.float32) for k, v in w.items()}
+        want = E.model_bytes(E.freeze(w, q, S.lane_bounds(P.n_rows, lanes), P.coord, depth, seed))
+        got = sgs.sgs_freeze_pe(sgs.pack_weights_pe(w), q, P.coord, depth, lanes, seed)
+        assert got == want
+
+
 def test_batch_bytes_host_side(small_scene):
     """scene_batch_bytes lays a batch out on the host only: it covers every scene's scratch,
     grows with the batch, and refuses infos that scene_query did not produce or misaligned
