@@ -17,7 +17,8 @@
 // Decoder: one warp per group of 32 lanes.  For each row step i the warp first runs the model
 // for all 56 channels of its 32 lanes -- 112 tiles of 16 contexts, each three bf16 mma.sync
 // layers with the contexts as M, so a layer's accumulator fragments are the next layer's A
-// fragments without any data movement -- and keeps each (mean, rate) in shared memory; then
+// fragments without any data movement; layer 1's embedding part depends on the row only and
+// is computed once per row -- and keeps each (mean, rate) in shared memory; then
 // it decodes the row's 56 tokens, each lane searching its CDF with 8 evaluations.  The
 // context of (i, c) needs only rows i-1 .. i-4, so the whole row's model runs before its
 // tokens are decoded.  The encoder's frequency kernel runs the same tile code with 32
@@ -194,21 +195,39 @@ __device__ __forceinline__ void pe_model_row(const PeSmem &S, const uint32_t *hi
                        a2 = __shfl_sync(0xffffffffu, v2, ga);
         const uint32_t c0 = __shfl_sync(0xffffffffu, v0, gb), c1 = __shfl_sync(0xffffffffu, v1, gb),
                        c2 = __shfl_sync(0xffffffffu, v2, gb);
-        uint32_t A[5][4];
+        // Layer 1 splits into the embedding part, which depends on the row only, and the
+        // context part (columns 0-3, the tokens u): the embedding part P of the tile's 16
+        // contexts is computed once per row (k tiles 0-4 with the u columns zero) and reused
+        // for all 56 channels.  Every partial sum is an integer below 2^24: exact in fp32.
+        float P[8][4];
+        {
+            uint32_t A[5][4];
 #pragma unroll
-        for (int kt = 0; kt < 5; ++kt) {
-            const int k = 16 * kt + 2 * t;
-            A[kt][0] = pack_bf16f(pe_x(S.sin8, a0, a1, a2, D, k), pe_x(S.sin8, a0, a1, a2, D, k + 1));
-            A[kt][1] = pack_bf16f(pe_x(S.sin8, c0, c1, c2, D, k), pe_x(S.sin8, c0, c1, c2, D, k + 1));
-            A[kt][2] = pack_bf16f(pe_x(S.sin8, a0, a1, a2, D, k + 8), pe_x(S.sin8, a0, a1, a2, D, k + 9));
-            A[kt][3] = pack_bf16f(pe_x(S.sin8, c0, c1, c2, D, k + 8), pe_x(S.sin8, c0, c1, c2, D, k + 9));
+            for (int kt = 0; kt < 5; ++kt) {
+                const int k = 16 * kt + 2 * t;
+                A[kt][0] = pack_bf16f(pe_x(S.sin8, a0, a1, a2, D, k), pe_x(S.sin8, a0, a1, a2, D, k + 1));
+                A[kt][1] = pack_bf16f(pe_x(S.sin8, c0, c1, c2, D, k), pe_x(S.sin8, c0, c1, c2, D, k + 1));
+                A[kt][2] = pack_bf16f(pe_x(S.sin8, a0, a1, a2, D, k + 8), pe_x(S.sin8, a0, a1, a2, D, k + 9));
+                A[kt][3] = pack_bf16f(pe_x(S.sin8, c0, c1, c2, D, k + 8), pe_x(S.sin8, c0, c1, c2, D, k + 9));
+            }
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                P[nt][0] = P[nt][1] = P[nt][2] = P[nt][3] = 0.0f;
+#pragma unroll
+                for (int kt = 0; kt < 5; ++kt) {
+                    const uint2 b = S.w1f[kt * 8 + nt][lane];
+                    mma_bf16(P[nt], A[kt][0], A[kt][1], A[kt][2], A[kt][3], b.x, b.y);
+                }
+            }
         }
 #pragma unroll 1
         for (int c = 0; c < kNChan; ++c) {
-            if (t < 2) {  // columns 2t, 2t + 1 of k tile 0 are the context tokens u_2t, u_2t+1
+            // context part: columns 2t, 2t + 1 (t < 2) of k tile 0 are the tokens u_2t, u_2t+1
+            uint32_t u0 = 0u, u1 = 0u;
+            if (t < 2) {
                 const uint32_t ha = hist[c * 32 + ga] >> (16 * t), hb = hist[c * 32 + gb] >> (16 * t);
-                A[0][0] = pack_bf16((int)(ha & 255u) - 128, (int)((ha >> 8) & 255u) - 128);
-                A[0][1] = pack_bf16((int)(hb & 255u) - 128, (int)((hb >> 8) & 255u) - 128);
+                u0 = pack_bf16((int)(ha & 255u) - 128, (int)((ha >> 8) & 255u) - 128);
+                u1 = pack_bf16((int)(hb & 255u) - 128, (int)((hb >> 8) & 255u) - 128);
             }
             uint32_t H[4][4];
             {
@@ -216,19 +235,18 @@ __device__ __forceinline__ void pe_model_row(const PeSmem &S, const uint32_t *hi
 #pragma unroll
                 for (int nt = 0; nt < 8; ++nt) {
                     d[nt][0] = d[nt][1] = d[nt][2] = d[nt][3] = 0.0f;
-#pragma unroll
-                    for (int kt = 0; kt < 5; ++kt) {
-                        const uint2 b = S.w1f[kt * 8 + nt][lane];
-                        mma_bf16(d[nt], A[kt][0], A[kt][1], A[kt][2], A[kt][3], b.x, b.y);
-                    }
+                    const uint2 b = S.w1f[nt][lane];
+                    mma_bf16(d[nt], u0, u1, 0u, 0u, b.x, b.y);
                 }
                 const float *b1 = S.b1 + c * 64;
 #pragma unroll
                 for (int nt = 0; nt < 8; ++nt) {
                     const float2 bb = *reinterpret_cast<const float2 *>(b1 + 8 * nt + 2 * t);
                     const int j = (nt & 1) * 2;
-                    H[nt >> 1][j] = pack_bf16f(pe_rq(d[nt][0] + bb.x, S.s1), pe_rq(d[nt][1] + bb.y, S.s1));
-                    H[nt >> 1][j + 1] = pack_bf16f(pe_rq(d[nt][2] + bb.x, S.s1), pe_rq(d[nt][3] + bb.y, S.s1));
+                    H[nt >> 1][j] = pack_bf16f(pe_rq(d[nt][0] + (P[nt][0] + bb.x), S.s1),
+                                               pe_rq(d[nt][1] + (P[nt][1] + bb.y), S.s1));
+                    H[nt >> 1][j + 1] = pack_bf16f(pe_rq(d[nt][2] + (P[nt][2] + bb.x), S.s1),
+                                                   pe_rq(d[nt][3] + (P[nt][3] + bb.y), S.s1));
                 }
             }
             uint32_t H2[4][4];
