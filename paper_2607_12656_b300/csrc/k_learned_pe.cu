@@ -14,12 +14,13 @@
 //   n = 4096 + clamp(rint(z1 * slr), -2048, 1536) (log2 of the rate in 1/256, plus 16);
 //   cdf(s) = s + floor(65280 F(s - 1/2) / 2^23), F from EXP2Q (pe_cdf below).
 //
-// Decoder: one warp per group of 32 lanes.  For each row step i the warp first runs the model
-// for all 56 channels of its 32 lanes -- 112 tiles of 16 contexts, each three bf16 mma.sync
+// Decoder: a team of two warps per group of 32 lanes.  For each row step i the team first runs
+// the model for all 56 channels of its 32 lanes, each warp one half -- 112 tiles of 16
+// contexts, each three bf16 mma.sync
 // layers with the contexts as M, so a layer's accumulator fragments are the next layer's A
 // fragments without any data movement; layer 1's embedding part depends on the row only and
 // is computed once per row -- and keeps each (mean, rate) in shared memory; then
-// it decodes the row's 56 tokens, each lane searching its CDF with 8 evaluations.  The
+// one warp decodes the row's 56 tokens, each lane searching its CDF with 8 evaluations.  The
 // context of (i, c) needs only rows i-1 .. i-4, so the whole row's model runs before its
 // tokens are decoded.  The encoder's frequency kernel runs the same tile code with 32
 // consecutive rows as its contexts.
@@ -47,13 +48,14 @@ __constant__ int8_t kPeSin8[256] = {SGS_SIN8_VALUES};
 constexpr int kPB_B1 = 32, kPB_B2 = 14368, kPB_B3 = 14624, kPB_W1 = 14640, kPB_W2 = 19760, kPB_W3 = 23856;
 static_assert(kPB_W3 + 128 == SGS_MODEL_PE_BYTES, "model layout");
 constexpr int kKin = 80;      // layer-1 inputs
-constexpr int kPeWarps = 8;   // groups (warps) per CTA
-constexpr int kPeThreads = 32 * kPeWarps;
+constexpr int kPeGroups = 3;  // groups per CTA
+constexpr int kPeTeam = 2;    // warps per group: each runs one 16-lane half of the model tiles
+constexpr int kPeThreads = 32 * kPeGroups * kPeTeam;
 
 struct PeSmem {
-    alignas(16) uint16_t win[kPeWarps][kWinWords];  // group stream windows (filled by 16-byte stores)
-    uint2 w1f[40][32];   // layer-1 B fragments [k tile * 8 + n tile][lane] (W1 transposed)
-    uint2 w2f[32][32];   // layer-2 B fragments
+    alignas(16) uint16_t win[kPeGroups][kWinWords];  // group stream windows (filled by 16-byte stores)
+    uint4 w1f[5][4][32];  // layer-1 B fragments (W1 transposed) [k tile][n tile pair][lane]: n tiles 2p, 2p + 1
+    uint4 w2f[4][4][32];  // layer-2 B fragments, likewise
     uint2 w3f[4][32];    // layer-3 B fragments (outputs 0, 1; the other six columns zero)
     float b1[kNChan * 64];
     float b2[64];
@@ -62,12 +64,12 @@ struct PeSmem {
     float step[kNChan], offset[kNChan];
     float b3[2], s1, s2, smu, slr;
     int bad;
-    uint32_t hist[kPeWarps][kNChan * 32];  // per channel and lane: s_{i-1} .. s_{i-4}, one byte each
-    uint32_t par[kPeWarps][kNChan * 32];   // per channel and lane: mu8 | n << 16
+    uint32_t hist[kPeGroups][kNChan * 32];  // per channel and lane: s_{i-1} .. s_{i-4}, one byte each
+    uint32_t par[kPeGroups][kNChan * 32];   // per channel and lane: mu8 | n << 16
 };
 static_assert(offsetof(PeSmem, win) % 16 == 0 && sizeof(PeSmem::win[0]) % 16 == 0, "16-byte window stores");
 static_assert(offsetof(PeSmem, b1) % 8 == 0 && offsetof(PeSmem, b2) % 8 == 0, "float2 bias loads");
-static_assert(offsetof(PeSmem, w1f) % 8 == 0, "8-byte fragment loads");
+static_assert(offsetof(PeSmem, w1f) % 16 == 0 && offsetof(PeSmem, w2f) % 16 == 0, "16-byte fragment loads");
 
 __device__ __forceinline__ int32_t ld_i32(const uint8_t *p) { return *reinterpret_cast<const int32_t *>(p); }
 
@@ -102,17 +104,22 @@ __device__ bool pe_load_model(PeSmem &S, const uint8_t *m) {
     const int8_t *w1 = reinterpret_cast<const int8_t *>(m + kPB_W1);
     const int8_t *w2 = reinterpret_cast<const int8_t *>(m + kPB_W2);
     const int8_t *w3 = reinterpret_cast<const int8_t *>(m + kPB_W3);
-    for (int f = tid; f < 40 * 32; f += blockDim.x) {
-        const int fi = f >> 5, ln = f & 31, g = ln >> 2, t = ln & 3;
-        const int kt = fi >> 3, nt = fi & 7, n = 8 * nt + g, k0 = 16 * kt + 2 * t;
-        const int8_t *r = w1 + n * kKin;
-        S.w1f[fi][ln] = make_uint2(pack_bf16(r[k0], r[k0 + 1]), pack_bf16(r[k0 + 8], r[k0 + 9]));
+    // B fragment of n tile nt, k tile kt for lane (g, t): rows k0, k0 + 1 and k0 + 8, k0 + 9 of
+    // column n = 8 nt + g of W^T, i.e. row n of W
+    auto frag = [](const int8_t *w, int ld, int kt, int nt, int ln) {
+        const int8_t *r = w + (8 * nt + (ln >> 2)) * ld;
+        const int k0 = 16 * kt + 2 * (ln & 3);
+        return make_uint2(pack_bf16(r[k0], r[k0 + 1]), pack_bf16(r[k0 + 8], r[k0 + 9]));
+    };
+    for (int f = tid; f < 5 * 4 * 32; f += blockDim.x) {
+        const int kt = f >> 7, np = (f >> 5) & 3, ln = f & 31;
+        const uint2 a = frag(w1, kKin, kt, 2 * np, ln), b = frag(w1, kKin, kt, 2 * np + 1, ln);
+        S.w1f[kt][np][ln] = make_uint4(a.x, a.y, b.x, b.y);
     }
-    for (int f = tid; f < 32 * 32; f += blockDim.x) {
-        const int fi = f >> 5, ln = f & 31, g = ln >> 2, t = ln & 3;
-        const int kt = fi >> 3, nt = fi & 7, n = 8 * nt + g, k0 = 16 * kt + 2 * t;
-        const int8_t *r = w2 + n * 64;
-        S.w2f[fi][ln] = make_uint2(pack_bf16(r[k0], r[k0 + 1]), pack_bf16(r[k0 + 8], r[k0 + 9]));
+    for (int f = tid; f < 4 * 4 * 32; f += blockDim.x) {
+        const int kt = f >> 7, np = (f >> 5) & 3, ln = f & 31;
+        const uint2 a = frag(w2, 64, kt, 2 * np, ln), b = frag(w2, 64, kt, 2 * np + 1, ln);
+        S.w2f[kt][np][ln] = make_uint4(a.x, a.y, b.x, b.y);
     }
     for (int f = tid; f < 4 * 32; f += blockDim.x) {
         const int kt = f >> 5, ln = f & 31, g = ln >> 2, t = ln & 3, k0 = 16 * kt + 2 * t;
@@ -150,8 +157,13 @@ __device__ __forceinline__ float pe_x(const int8_t *sin8, uint32_t v0, uint32_t 
     return (float)sin8[th];
 }
 
-__device__ __forceinline__ float pe_rq(float acc, float s) {
-    return fminf(fmaxf(rintf(__fmul_rn(acc, s)), 0.0f), 127.0f);
+// Two activations clamp(rint(fl32(acc * s)), 0, 127) packed as a bf16 pair (a in the low
+// half): rint and the upper clamp in fp32, the clamp at 0 by the conversion's relu.
+__device__ __forceinline__ uint32_t pe_rq2(float a, float b, float s) {
+    const float ra = fminf(rintf(__fmul_rn(a, s)), 127.0f), rb = fminf(rintf(__fmul_rn(b, s)), 127.0f);
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(rb), "f"(ra));
+    return d;
 }
 
 __device__ __forceinline__ uint32_t pe_head(float zm, float zl, float smu, float slr) {
@@ -175,11 +187,11 @@ __device__ __forceinline__ uint32_t pe_rate(const uint32_t *exq, uint32_t n) {
     return exq[(0u - n) & 255u] >> (23u - q);
 }
 
-// The model for the 32 contexts of one warp (context = lane) and all 56 channels: hist holds
-// each context's packed history per channel, (v0, v1, v2) the lane's voxel; writes
-// par[c * 32 + lane].  Runs the 16-context tiles of lanes 0-15 and 16-31.
-__device__ __forceinline__ void pe_model_row(const PeSmem &S, const uint32_t *hist, uint32_t *par, uint32_t v0,
-                                             uint32_t v1, uint32_t v2, int D) {
+// The model for 16 of a group's 32 contexts (context = lane; half h: lanes 16h .. 16h + 15)
+// and all 56 channels: hist holds each context's packed history per channel, (v0, v1, v2)
+// the calling lane's voxel; writes par[c * 32 + context].
+__device__ __forceinline__ void pe_model_half(const PeSmem &S, const uint32_t *hist, uint32_t *par, uint32_t v0,
+                                              uint32_t v1, uint32_t v2, int D, int h) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     uint32_t w3b[4][2];
 #pragma unroll
@@ -188,8 +200,7 @@ __device__ __forceinline__ void pe_model_row(const PeSmem &S, const uint32_t *hi
         w3b[kt][0] = b.x;
         w3b[kt][1] = b.y;
     }
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
+    {
         const int ga = 16 * h + g, gb = ga + 8;  // the tile's rows g and g + 8
         const uint32_t a0 = __shfl_sync(0xffffffffu, v0, ga), a1 = __shfl_sync(0xffffffffu, v1, ga),
                        a2 = __shfl_sync(0xffffffffu, v2, ga);
@@ -211,14 +222,15 @@ __device__ __forceinline__ void pe_model_row(const PeSmem &S, const uint32_t *hi
                 A[kt][3] = pack_bf16f(pe_x(S.sin8, c0, c1, c2, D, k + 8), pe_x(S.sin8, c0, c1, c2, D, k + 9));
             }
 #pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                P[nt][0] = P[nt][1] = P[nt][2] = P[nt][3] = 0.0f;
+            for (int nt = 0; nt < 8; ++nt) P[nt][0] = P[nt][1] = P[nt][2] = P[nt][3] = 0.0f;
 #pragma unroll
-                for (int kt = 0; kt < 5; ++kt) {
-                    const uint2 b = S.w1f[kt * 8 + nt][lane];
-                    mma_bf16(P[nt], A[kt][0], A[kt][1], A[kt][2], A[kt][3], b.x, b.y);
+            for (int kt = 0; kt < 5; ++kt)
+#pragma unroll
+                for (int np = 0; np < 4; ++np) {
+                    const uint4 b = S.w1f[kt][np][lane];
+                    mma_bf16(P[2 * np], A[kt][0], A[kt][1], A[kt][2], A[kt][3], b.x, b.y);
+                    mma_bf16(P[2 * np + 1], A[kt][0], A[kt][1], A[kt][2], A[kt][3], b.z, b.w);
                 }
-            }
         }
 #pragma unroll 1
         for (int c = 0; c < kNChan; ++c) {
@@ -232,41 +244,41 @@ __device__ __forceinline__ void pe_model_row(const PeSmem &S, const uint32_t *hi
             uint32_t H[4][4];
             {
                 float d[8][4];
+                // the embedding part enters as the accumulator: every partial sum stays below 2^22
 #pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
-                    d[nt][0] = d[nt][1] = d[nt][2] = d[nt][3] = 0.0f;
-                    const uint2 b = S.w1f[nt][lane];
-                    mma_bf16(d[nt], u0, u1, 0u, 0u, b.x, b.y);
+                for (int np = 0; np < 4; ++np) {
+                    const uint4 b = S.w1f[0][np][lane];
+                    mma_bf16_c(d[2 * np], P[2 * np], u0, u1, 0u, 0u, b.x, b.y);
+                    mma_bf16_c(d[2 * np + 1], P[2 * np + 1], u0, u1, 0u, 0u, b.z, b.w);
                 }
                 const float *b1 = S.b1 + c * 64;
 #pragma unroll
                 for (int nt = 0; nt < 8; ++nt) {
                     const float2 bb = *reinterpret_cast<const float2 *>(b1 + 8 * nt + 2 * t);
                     const int j = (nt & 1) * 2;
-                    H[nt >> 1][j] = pack_bf16f(pe_rq(d[nt][0] + (P[nt][0] + bb.x), S.s1),
-                                               pe_rq(d[nt][1] + (P[nt][1] + bb.y), S.s1));
-                    H[nt >> 1][j + 1] = pack_bf16f(pe_rq(d[nt][2] + (P[nt][2] + bb.x), S.s1),
-                                                   pe_rq(d[nt][3] + (P[nt][3] + bb.y), S.s1));
+                    H[nt >> 1][j] = pe_rq2(d[nt][0] + bb.x, d[nt][1] + bb.y, S.s1);
+                    H[nt >> 1][j + 1] = pe_rq2(d[nt][2] + bb.x, d[nt][3] + bb.y, S.s1);
                 }
             }
             uint32_t H2[4][4];
             {
                 float d[8][4];
 #pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
-                    d[nt][0] = d[nt][1] = d[nt][2] = d[nt][3] = 0.0f;
+                for (int nt = 0; nt < 8; ++nt) d[nt][0] = d[nt][1] = d[nt][2] = d[nt][3] = 0.0f;
 #pragma unroll
-                    for (int kt = 0; kt < 4; ++kt) {
-                        const uint2 b = S.w2f[kt * 8 + nt][lane];
-                        mma_bf16(d[nt], H[kt][0], H[kt][1], H[kt][2], H[kt][3], b.x, b.y);
+                for (int kt = 0; kt < 4; ++kt)
+#pragma unroll
+                    for (int np = 0; np < 4; ++np) {
+                        const uint4 b = S.w2f[kt][np][lane];
+                        mma_bf16(d[2 * np], H[kt][0], H[kt][1], H[kt][2], H[kt][3], b.x, b.y);
+                        mma_bf16(d[2 * np + 1], H[kt][0], H[kt][1], H[kt][2], H[kt][3], b.z, b.w);
                     }
-                }
 #pragma unroll
                 for (int nt = 0; nt < 8; ++nt) {
                     const float2 bb = *reinterpret_cast<const float2 *>(S.b2 + 8 * nt + 2 * t);
                     const int j = (nt & 1) * 2;
-                    H2[nt >> 1][j] = pack_bf16f(pe_rq(d[nt][0] + bb.x, S.s2), pe_rq(d[nt][1] + bb.y, S.s2));
-                    H2[nt >> 1][j + 1] = pack_bf16f(pe_rq(d[nt][2] + bb.x, S.s2), pe_rq(d[nt][3] + bb.y, S.s2));
+                    H2[nt >> 1][j] = pe_rq2(d[nt][0] + bb.x, d[nt][1] + bb.y, S.s2);
+                    H2[nt >> 1][j + 1] = pe_rq2(d[nt][2] + bb.x, d[nt][3] + bb.y, S.s2);
                 }
             }
             float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -291,10 +303,21 @@ struct PeParams {
     int *status;
 };
 
-// One group of 32 lanes, decoded by one warp.
-__device__ void pe_group(const PeParams &p, PeSmem &S, uint32_t grp) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *hist = S.hist[warp], *par = S.par[warp];
+// The two warps of a group's team synchronise on a named barrier of their own (ids 1..3;
+// __syncthreads uses 0).  Both execute the same sequence of barriers.
+__device__ __forceinline__ void team_sync(int slot) {
+    static_assert(kPeGroups == 3 && kPeTeam == 2, "one barrier id per team, 64 threads each");
+    if (slot == 0) asm volatile("bar.sync 1, 64;" ::: "memory");
+    else if (slot == 1) asm volatile("bar.sync 2, 64;" ::: "memory");
+    else asm volatile("bar.sync 3, 64;" ::: "memory");
+}
+
+// One group of 32 lanes, decoded by a team of two warps: per row step each warp runs the
+// model for one half of the lanes, then member 0 decodes the row's tokens (the group's word
+// stream is read by one warp, in lane order).
+__device__ void pe_group(const PeParams &p, PeSmem &S, uint32_t grp, int slot, int member) {
+    const int lane = threadIdx.x & 31;
+    uint32_t *hist = S.hist[slot], *par = S.par[slot];
     const int nl = (int)min(32u, p.L - grp * 32);
     uint64_t r0 = 0, r1 = 0;
     if (lane < nl) {
@@ -306,10 +329,13 @@ __device__ void pe_group(const PeParams &p, PeSmem &S, uint32_t grp) {
     uint32_t maxrows = nrows;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) maxrows = max(maxrows, __shfl_xor_sync(0xffffffffu, maxrows, o));
-    for (int c = 0; c < kNChan; ++c) hist[c * 32 + lane] = 0x80808080u;
     GroupStream gs;
     uint32_t x = 0x10000u;
-    group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, grp, nl, lane, gs, x, S.win[warp]);
+    if (member == 0) {
+        for (int c = 0; c < kNChan; ++c) hist[c * 32 + lane] = 0x80808080u;
+        group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, grp, nl, lane, gs, x, S.win[slot]);
+    }
+    team_sync(slot);
     const int D = (int)p.depth;
     for (uint32_t i = 0; i < maxrows; ++i) {
         const bool live = lane < nl && i < nrows;
@@ -322,33 +348,43 @@ __device__ void pe_group(const PeParams &p, PeSmem &S, uint32_t grp) {
             v1 = p.coord[(uint64_t)p.n_rows + col];
             v2 = p.coord[2ull * p.n_rows + col];
         }
-        __syncwarp();
-        pe_model_row(S, hist, par, v0, v1, v2, D);
-        __syncwarp();
-        for (int c = 0; c < kNChan; ++c) {
-            if (live) {
-                const uint32_t pr = par[c * 32 + lane];
-                const int mu8 = (int)(pr & 0xFFFFu);
-                const uint32_t R = pe_rate(S.exq, pr >> 16);
-                const uint32_t slot = x & 0xFFFFu;
-                uint32_t s = 0, lo = 0, hi = 65536u;
+        pe_model_half(S, hist, par, v0, v1, v2, D, member);
+        team_sync(slot);  // both halves of the row's (mean, rate) are in par
+        if (member == 0) {
+            for (int c = 0; c < kNChan; ++c) {
+                if (live) {
+                    const uint32_t pr = par[c * 32 + lane];
+                    const int mu8 = (int)(pr & 0xFFFFu);
+                    const uint32_t R = pe_rate(S.exq, pr >> 16);
+                    const uint32_t slot_ = x & 0xFFFFu;
+                    // 4-ary search: cdf(s) = lo <= slot < hi = cdf(s + 4 st); three independent
+                    // evaluations per level, four levels
+                    uint32_t s = 0, lo = 0, hi = 65536u;
 #pragma unroll
-                for (uint32_t st = 128; st > 0; st >>= 1) {
-                    const uint32_t cm = pe_cdf(S.exq, mu8, R, s + st);
-                    if (cm <= slot) { s += st; lo = cm; } else { hi = cm; }
+                    for (uint32_t st = 64; st > 0; st >>= 2) {
+                        const uint32_t c1 = pe_cdf(S.exq, mu8, R, s + st), c2 = pe_cdf(S.exq, mu8, R, s + 2 * st),
+                                       c3 = pe_cdf(S.exq, mu8, R, s + 3 * st);
+                        if (c3 <= slot_) { s += 3 * st; lo = c3; }
+                        else if (c2 <= slot_) { s += 2 * st; lo = c2; hi = c3; }
+                        else if (c1 <= slot_) { s += st; lo = c1; hi = c2; }
+                        else { hi = c1; }
+                    }
+                    x = (hi - lo) * (x >> 16) + slot_ - lo;
+                    hist[c * 32 + lane] = (hist[c * 32 + lane] << 8) | s;
+                    p.out[(uint64_t)c * p.n_rows + col] = dequant(s, S.step[c], S.offset[c]);
                 }
-                x = (hi - lo) * (x >> 16) + slot - lo;
-                hist[c * 32 + lane] = (hist[c * 32 + lane] << 8) | s;
-                p.out[(uint64_t)c * p.n_rows + col] = dequant(s, S.step[c], S.offset[c]);
+                group_refill(gs, x, live);
             }
-            group_refill(gs, x, live);
         }
+        team_sync(slot);  // the row's tokens are in hist before the next row's model
     }
-    const bool bad = gs.bad || (lane < nl && x != 0x10000u) || (gs.ptr != gs.n_words);
-    if (bad) set_status(p.status, SGS_E_CORRUPT);
+    if (member == 0) {
+        const bool bad = gs.bad || (lane < nl && x != 0x10000u) || (gs.ptr != gs.n_words);
+        if (bad) set_status(p.status, SGS_E_CORRUPT);
+    }
 }
 
-// CTA work unit: groups [vb * kPeWarps, +kPeWarps), one per warp.
+// CTA work unit: groups [vb * kPeGroups, +kPeGroups), one team of two warps each.
 __device__ __forceinline__ void pe_body(const PeParams &p, uint32_t vb, bool reload) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     PeSmem &S = *reinterpret_cast<PeSmem *>(smem_raw);
@@ -365,21 +401,23 @@ __device__ __forceinline__ void pe_body(const PeParams &p, uint32_t vb, bool rel
     } else if (S.bad) {
         return;
     }
-    const uint32_t grp = vb * kPeWarps + (threadIdx.x >> 5);
-    if (grp < p.G) pe_group(p, S, grp);
+    const int warp = threadIdx.x >> 5, slot = warp / kPeTeam;
+    const uint32_t grp = vb * kPeGroups + slot;
+    if (grp < p.G) pe_group(p, S, grp, slot, warp % kPeTeam);
 }
 
-__global__ void __launch_bounds__(kPeThreads, 1) k_learned_pe(PeParams p) { pe_body(p, blockIdx.x, true); }
+__global__ void __launch_bounds__(kPeThreads, 2) k_learned_pe(PeParams p) { pe_body(p, blockIdx.x, true); }
 
-__global__ void __launch_bounds__(kPeThreads, 1) k_learned_pe_multi(MultiArgs m) {
+__global__ void __launch_bounds__(kPeThreads, 2) k_learned_pe_multi(MultiArgs m) {
     run_items<PeParams>(m, [](const PeParams &p, uint32_t vb, uint32_t, bool same) { pe_body(p, vb, !same); });
 }
 
 // ------------------------------------------------------------------ encoder side
 
-// f and cum of every token (row-major = lane-major order): one warp per 32 consecutive rows,
-// each row a context of the model tile.  A token's context restarts at its lane's first row.
-__global__ void __launch_bounds__(kPeThreads, 1) k_pe_fc(const uint8_t *model, const uint8_t *tok,
+// f and cum of every token (row-major = lane-major order): one team of two warps per 32
+// consecutive rows, each row a context of the model tiles.  A token's context restarts at
+// its lane's first row.
+__global__ void __launch_bounds__(kPeThreads, 2) k_pe_fc(const uint8_t *model, const uint8_t *tok,
                                                          const uint32_t *coord, int D, uint32_t n_rows,
                                                          uint32_t L, uint32_t *f, uint32_t *cum, int *status) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -389,18 +427,18 @@ __global__ void __launch_bounds__(kPeThreads, 1) k_pe_fc(const uint8_t *model, c
         return;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *hist = S.hist[warp], *par = S.par[warp];
-    const uint64_t row = ((uint64_t)blockIdx.x * kPeWarps + warp) * 32 + lane;
-    const uint64_t first = ((uint64_t)blockIdx.x * kPeWarps + warp) * 32;
-    if (first >= n_rows) return;  // whole warp
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, slot = warp / kPeTeam, member = warp % kPeTeam;
+    uint32_t *hist = S.hist[slot], *par = S.par[slot];
+    const uint64_t first = ((uint64_t)blockIdx.x * kPeGroups + slot) * 32;
+    if (first >= n_rows) return;  // the whole team
+    const uint64_t row = first + lane;
     const bool live = row < n_rows;
     uint64_t row0 = 0;
     if (live) {
         const uint64_t j = ((row + 1) * L + n_rows - 1) / n_rows - 1;  // the lane holding row
         row0 = j * n_rows / L;
     }
-    for (int c = 0; c < kNChan; ++c) {
+    for (int c = member; c < kNChan; c += kPeTeam) {
         uint32_t h = 0x80808080u;
         if (live)
             for (int j = 4; j >= 1; --j)
@@ -413,11 +451,11 @@ __global__ void __launch_bounds__(kPeThreads, 1) k_pe_fc(const uint8_t *model, c
         v1 = coord[(uint64_t)n_rows + row];
         v2 = coord[2ull * n_rows + row];
     }
-    __syncwarp();
-    pe_model_row(S, hist, par, v0, v1, v2, D);
-    __syncwarp();
+    team_sync(slot);
+    pe_model_half(S, hist, par, v0, v1, v2, D, member);
+    team_sync(slot);
     if (!live) return;
-    for (int c = 0; c < kNChan; ++c) {
+    for (int c = member; c < kNChan; c += kPeTeam) {
         const uint32_t pr = par[c * 32 + lane];
         const int mu8 = (int)(pr & 0xFFFFu);
         const uint32_t R = pe_rate(S.exq, pr >> 16);
@@ -447,7 +485,7 @@ uint32_t make_pe(const uint8_t *bits, const sgs_scene_info &info, const sgs_scen
     p.out = out.attr;
     p.out_index = out.out_index;
     p.status = status;
-    return info.n_rows ? (p.G + kPeWarps - 1) / kPeWarps : 0;
+    return info.n_rows ? (p.G + kPeGroups - 1) / kPeGroups : 0;
 }
 
 cudaError_t pe_smem_limit(const void *kernel, bool *done) {
@@ -493,8 +531,8 @@ cudaError_t launch_pe_fc(const uint8_t *model_dev, const uint8_t *tok_dev, const
     static bool set = false;
     cudaError_t e = pe_smem_limit(reinterpret_cast<const void *>(k_pe_fc), &set);
     if (e != cudaSuccess) return e;
-    const uint32_t warps = (n_rows + 31) / 32;
-    k_pe_fc<<<(warps + kPeWarps - 1) / kPeWarps, kPeThreads, sizeof(PeSmem), st>>>(
+    const uint32_t teams = (n_rows + 31) / 32;
+    k_pe_fc<<<(teams + kPeGroups - 1) / kPeGroups, kPeThreads, sizeof(PeSmem), st>>>(
         model_dev, tok_dev, coord_dev, depth, n_rows, lanes, f_dev, cum_dev, status);
     return cudaGetLastError();
 }
