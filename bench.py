@@ -644,7 +644,7 @@ def run_serve(args):
 
 def run_sweep(args):
     """Group-size sweep: for W (rows per lane, the paper's complexity knob) in 16..256, the
-    bitstream size and the decode time of the 1M-Gaussian scene, static and learned modes,
+    bitstream size and the decode time of the 1M-Gaussian scene, static and both learned modes,
     measured by sgs_autotune (encode at each W, median of timed decodes)."""
     import torch
     from paper_2607_12656_b300 import learned, sgs
@@ -656,17 +656,20 @@ def run_sweep(args):
     ws = [16, 32, 64, 128, 256]
     curves = {}
     encode_s = {}
-    for mode, name, seed in ((1, "static", 1000), (2, "learned", 2000)):
+    for mode, name, seed in ((1, "static", 1000), (2, "learned", 2000), (3, "learned_pe", 2000)):
         sc = make_scene(1_000_000, seed)
         model = None
         if mode == 2:
             model = learned.train_and_freeze(ctx, sc, 16, 4096, steps=args.train_steps or 2000, batch=65536, seed=1)
+        if mode == 3:  # trained at W = 32, the paper's fast group size
+            model = learned.train_and_freeze_pe(ctx, sc, 16, 28125, steps=args.train_steps or 2000, batch=65536,
+                                                seed=1)
         r = sgs.autotune(ctx, sc.pos, sc.attr, mode=mode, depth=16, rows_per_lane=ws, reps=5 if mode == 1 else 3,
                          model=model)
         # whole scene_encode (prepare on the host, attribute coding on the device or host), W = 32
         lanes = -(-900_000 // 32)
         for where, c in (("device", ctx), ("host", None)):
-            if mode == 2 and c is None:
+            if mode != 1 and c is None:
                 continue  # learned coding needs the device for the model's frequencies
             t0 = time.perf_counter()
             sgs.scene_encode(sc.pos, sc.attr, mode=mode, depth=16, lanes=lanes, model=model, ctx=c)
@@ -681,7 +684,7 @@ def run_sweep(args):
             "steps": 5, "warmup": 1, "ms_per_step": best["decode_ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32->f32", "data": "synthetic",
             "config": {"workload": "group-size sweep: 1M-Gaussian scene (900,000 kept), depth 16, W = rows per "
-                                   "lane in 16..256, static and learned attribute coding; decode median of timed runs "
+                                   "lane in 16..256, static, learned and position-aware learned attribute coding; decode median of timed runs "
                                    "(sgs_autotune), L2 not flushed", "rows_per_lane": ws},
             "curves": curves,
             "encode": {"seconds": encode_s, "gaussians": 1_000_000, "threads": os.cpu_count(),

@@ -308,10 +308,10 @@ int scene_rows(const float *pos, const float *attr, uint32_t n, uint32_t depth, 
 typedef struct {
     const float *pos, *attr;  /* host scene, as for scene_encode                           */
     uint32_t n;
-    uint32_t mode;            /* SGS_MODE_STATIC or SGS_MODE_LEARNED                      */
+    uint32_t mode;            /* SGS_MODE_STATIC, SGS_MODE_LEARNED or SGS_MODE_LEARNED_PE */
     uint32_t depth;
     uint32_t geo_mode;
-    const void *model;        /* learned mode: the frozen model                           */
+    const void *model;        /* learned modes: the frozen model                          */
     uint32_t n_cand;          /* 1 .. SGS_TUNE_MAX_CAND                                   */
     uint32_t rows_per_lane[SGS_TUNE_MAX_CAND];  /* candidate W values, >= 1              */
     float max_ms;             /* decode-time target, <= 0: fastest                         */

@@ -26,8 +26,9 @@ struct DevBuf {
 
 extern "C" int sgs_autotune(sgs_ctx *c, const sgs_tune_request *rq, sgs_tune_result *res) {
     if (!c || !rq || !res || !rq->pos || !rq->attr || rq->n == 0) return SGS_E_INVALID;
-    if (rq->mode != SGS_MODE_STATIC && rq->mode != SGS_MODE_LEARNED) return SGS_E_INVALID;
-    if (rq->mode == SGS_MODE_LEARNED && !rq->model) return SGS_E_INVALID;
+    if (rq->mode != SGS_MODE_STATIC && rq->mode != SGS_MODE_LEARNED && rq->mode != SGS_MODE_LEARNED_PE)
+        return SGS_E_INVALID;
+    if ((rq->mode == SGS_MODE_LEARNED || rq->mode == SGS_MODE_LEARNED_PE) && !rq->model) return SGS_E_INVALID;
     if (rq->n_cand < 1 || rq->n_cand > SGS_TUNE_MAX_CAND || rq->reps < 1) return SGS_E_INVALID;
     for (uint32_t k = 0; k < rq->n_cand; ++k)
         if (rq->rows_per_lane[k] < 1) return SGS_E_INVALID;
