@@ -203,3 +203,60 @@ def freeze(w: dict, q: np.ndarray, lane_row: np.ndarray, seed: int, n_calib: int
     ms = int(np.clip(np.rint(s_z * LOG2E * 256.0 * 65536.0), 1, (1 << 24) - 1))
     return dict(w1=w1q, b1=B1, m1=m1, sh1=sh1, w2=w2q, b2=b2q, m2=m2, sh2=sh2,
                 w3=w3q, b3=b3q, ms=ms, ss=16)
+
+
+# ----------------------------------------------------------------------------- explicit contexts
+
+def train_ctx(init: dict, U: np.ndarray, C: np.ndarray, S: np.ndarray, steps: int, batch: int, seed: int,
+              lr: float = 1e-3):
+    """fp64 training on an explicit sample set: sample k of a step is entry
+    sample_positions(seed, step, batch, n) of (U [n, 4], C [n], S [n])."""
+    p = {k: np.asarray(init[k], np.float64).copy() for k in PARAMS}
+    m = {k: np.zeros_like(p[k]) for k in PARAMS}
+    v = {k: np.zeros_like(p[k]) for k in PARAMS}
+    n = len(S)
+    losses = []
+    for t in range(steps):
+        idx = sample_positions(seed, t, batch, n)
+        loss, g = forward_backward(p, U[idx].astype(np.int64), C[idx].astype(np.int64), S[idx].astype(np.int64))
+        adam_step(p, g, m, v, t + 1, lr)
+        losses.append(loss)
+    return p, losses
+
+
+def freeze_ctx(w: dict, U: np.ndarray, C: np.ndarray, seed: int, n_calib: int = 65536) -> dict:
+    """As freeze, with the calibration contexts drawn from an explicit sample set (entry
+    sample_positions(seed, 2^20 - 1, n_calib, n) of (U, C)); the arithmetic is freeze's."""
+    p = {k: np.asarray(w[k], np.float32).astype(np.float64) for k in PARAMS}
+    s_u = 1.0 / 128.0
+    w1q, s_w1 = _q8(p["w1"][:, :CTX])
+    s_a1 = s_u * s_w1
+    b1f = np.empty((NCHAN, HID), np.float64)
+    for c in range(NCHAN):
+        for o in range(HID):
+            t = p["b1"][o]
+            for e in range(EMB):
+                t = t + p["w1"][o, CTX + e] * p["emb"][c, e]
+            b1f[c, o] = t
+    B1 = _clamp24(np.rint(b1f / s_a1))
+    w2q, s_w2 = _q8(p["w2"])
+    w3q, s_w3 = _q8(p["w3"])
+    idx = sample_positions(seed, CALIB_STEP, n_calib, len(C))
+    u = U[idx].astype(np.int64)
+    c = C[idx].astype(np.int64)
+    a1 = u @ w1q.astype(np.int64).T + B1[c].astype(np.int64)
+    A1 = max(int(a1.max()), 1)
+    m1, sh1 = _requant_params(A1)
+    s_h1 = s_a1 * A1 / 127.0
+    s_a2 = s_h1 * s_w2
+    b2q = _clamp24(np.rint(p["b2"] / s_a2))
+    h1 = np.clip((a1 * m1 + (1 << (sh1 - 1))) >> sh1, 0, 127)
+    a2 = h1 @ w2q.astype(np.int64).T + b2q.astype(np.int64)
+    A2 = max(int(a2.max()), 1)
+    m2, sh2 = _requant_params(A2)
+    s_h2 = s_a2 * A2 / 127.0
+    s_z = s_h2 * s_w3
+    b3q = _clamp24(np.rint(p["b3"] / s_z))
+    ms = int(np.clip(np.rint(s_z * LOG2E * 256.0 * 65536.0), 1, (1 << 24) - 1))
+    return dict(w1=w1q, b1=B1, m1=m1, sh1=sh1, w2=w2q, b2=b2q, m2=m2, sh2=sh2,
+                w3=w3q, b3=b3q, ms=ms, ss=16)

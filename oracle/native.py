@@ -84,6 +84,8 @@ def lib():
         L.or_rans_encode.argtypes = [i64, i64, P, P, P, P, i64, P, P]
         L.or_rans_decode_static.restype = ctypes.c_int
         L.or_rans_decode_static.argtypes = [i64, P, P, P, ctypes.c_int, P, i64, P, P, P]
+        L.or_rans_decode_static16.restype = ctypes.c_int
+        L.or_rans_decode_static16.argtypes = [i64, P, P, P, ctypes.c_int, P, i64, P, P, P]
         L.or_model_logits.restype = None
         L.or_model_logits.argtypes = [P, P, ctypes.c_int, P]
         L.or_logits_to_freq.restype = None

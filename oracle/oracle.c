@@ -199,6 +199,46 @@ int or_rans_decode_static(int64_t n_lanes, const int64_t *lane_start, const uint
     return 0;
 }
 
+/* As or_rans_decode_static with 16-bit table ids (the context tables of a learned octree
+ * level: one table per distinct (parent byte, child index)). */
+int or_rans_decode_static16(int64_t n_lanes, const int64_t *lane_start, const uint16_t *tab_id,
+                          const uint32_t *freq, int n_tab, const uint8_t *payload,
+                          int64_t pay_len, const uint64_t *grp_off, const uint32_t *grp_words,
+                          uint8_t *syms)
+{
+    int64_t g = 0;
+    for (int64_t j0 = 0; j0 < n_lanes; j0 += 32, ++g) {
+        int64_t j1 = j0 + 32 < n_lanes ? j0 + 32 : n_lanes;
+        int nl = (int)(j1 - j0);
+        or_reader r;
+        uint32_t x[32];
+        if (or_group_setup(&r, x, nl, payload, pay_len, grp_off[g], grp_words[g])) return -1;
+        int64_t maxn = 0;
+        for (int j = 0; j < nl; ++j) {
+            int64_t n = lane_start[j0 + j + 1] - lane_start[j0 + j];
+            if (n > maxn) maxn = n;
+        }
+        for (int64_t t = 0; t < maxn; ++t) {
+            for (int j = 0; j < nl; ++j) {
+                int64_t n = lane_start[j0 + j + 1] - lane_start[j0 + j];
+                if (t >= n) continue;
+                int64_t p = lane_start[j0 + j] + t;
+                if (tab_id[p] >= n_tab) return -1;
+                const uint32_t *tab = freq + (size_t)tab_id[p] * OR_NSYM;
+                uint32_t slot = x[j] & (OR_M - 1), fs, cs;
+                int s = or_find(tab, slot, &fs, &cs);
+                if (s < 0) return -1;
+                syms[p] = (uint8_t)s;
+                x[j] = fs * (x[j] >> OR_PROB_BITS) + slot - cs;
+                if (x[j] < OR_L) x[j] = (x[j] << 16) | or_read(&r);
+            }
+            if (r.bad) return -1;
+        }
+        if (or_group_finish(&r, x, nl)) return -1;
+    }
+    return 0;
+}
+
 /* ------------------------------------------------- integer context model (learned) */
 
 typedef struct {

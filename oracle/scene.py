@@ -34,7 +34,7 @@ from .exp2q import exp2q_table
 MAGIC = 0x31534753  # "SGS1"
 VERSION = 1
 MODE_FIXED, MODE_STATIC, MODE_LEARNED, MODE_LEARNED_PE = 0, 1, 2, 3
-GEO_RAW, GEO_RANS = 0, 1
+GEO_RAW, GEO_RANS, GEO_LEARNED = 0, 1, 2
 NCHAN = 56
 NSYM = 256
 GEO_RANS_MIN_LEVEL = 4096   # octree levels with fewer nodes are stored raw
@@ -265,6 +265,25 @@ def rans_decode_static(lane_start, tab_id, tables, payload, goff, gw) -> np.ndar
     return syms[:nsym]
 
 
+def rans_decode_static16(lane_start, tab_id, tables, payload, goff, gw) -> np.ndarray:
+    """As rans_decode_static with up to 65,535 tables (16-bit table ids)."""
+    L = native.lib()
+    ls = np.ascontiguousarray(lane_start, dtype=np.int64)
+    nsym = int(ls[-1])
+    syms = np.zeros(max(nsym, 1), np.uint8)
+    freq = np.ascontiguousarray(np.stack(tables) if len(tables) else np.zeros((1, NSYM)), dtype=np.uint32)
+    pay = np.frombuffer(payload, np.uint8).copy() if len(payload) else np.zeros(1, np.uint8)
+    tid = np.ascontiguousarray(tab_id, dtype=np.uint16) if nsym else np.zeros(1, np.uint16)
+    go = np.ascontiguousarray(goff, np.uint64)
+    gwa = np.ascontiguousarray(gw if len(gw) else np.zeros(1), np.uint32)
+    rc = L.or_rans_decode_static16(len(ls) - 1, native.ptr(ls), native.ptr(tid), native.ptr(freq),
+                                   len(tables), native.ptr(pay), len(payload), native.ptr(go),
+                                   native.ptr(gwa), native.ptr(syms))
+    if rc != 0:
+        raise ValueError("corrupt rANS stream")
+    return syms[:nsym]
+
+
 def static_fc(syms: np.ndarray, tab_id: np.ndarray, tables: list[np.ndarray]):
     F = np.stack(tables)
     C = np.stack([cum_of(t) for t in tables])
@@ -473,13 +492,65 @@ def prepare(pos: np.ndarray, attr: np.ndarray, depth: int, bits) -> Prepared:
 
 
 def geo_plan(levels: list[np.ndarray], geo_mode: int):
-    coded = [geo_mode == GEO_RANS and len(b) >= GEO_RANS_MIN_LEVEL for b in levels]
+    coded = [geo_mode != GEO_RAW and len(b) >= GEO_RANS_MIN_LEVEL for b in levels]
     return coded
+
+
+# ----------------------------------------------------------------------------- learned geometry
+
+_POPCOUNT8 = np.array([bin(b).count("1") for b in range(256)], np.int64)
+
+
+def geo_children_ctx(parent: np.ndarray) -> np.ndarray:
+    """Context id 8 b + k of every node of a level, given the level above it: node order is
+    the parents in order and, within a parent with byte b, its set bits k ascending (the
+    breadth-first serialization of Sec. 3.4, "Geometry Occupancy Coding"); the parent level
+    conditions the children, as Eq. 8's p(t_l | t_<l)."""
+    b = np.asarray(parent, np.int64)
+    bits = (b[:, None] >> np.arange(8)) & 1
+    pi, k = np.nonzero(bits)
+    return 8 * b[pi] + k
+
+
+def geo_ctx_inputs(ctx: np.ndarray) -> np.ndarray:
+    """Model inputs u [n, 4] of context ids: the parent byte, the child index, the parent's
+    occupied-child count and the child's rank among them, each mapped into [-128, 127]."""
+    ctx = np.asarray(ctx, np.int64)
+    b, k = ctx >> 3, ctx & 7
+    rank = _POPCOUNT8[b & ((1 << k) - 1)]
+    return np.stack([b - 128, 32 * k - 112, 16 * _POPCOUNT8[b] - 64, 32 * rank - 112], axis=1)
+
+
+def geo_samples(levels: list[np.ndarray], geo_mode: int = GEO_LEARNED):
+    """Training samples (U [n, 4], C [n] = level, S [n] = token) of every coded level."""
+    coded = geo_plan(levels, geo_mode)
+    U, C, S = [], [], []
+    for l in range(1, len(levels)):
+        if not coded[l]:
+            continue
+        U.append(geo_ctx_inputs(geo_children_ctx(levels[l - 1])))
+        C.append(np.full(len(levels[l]), l, np.int64))
+        S.append(np.asarray(levels[l], np.int64))
+    if not U:
+        return np.zeros((0, 4), np.int64), np.zeros(0, np.int64), np.zeros(0, np.int64)
+    return np.concatenate(U), np.concatenate(C), np.concatenate(S)
+
+
+def geo_level_tables(model: dict, level: int, ctx: np.ndarray):
+    """(distinct context ids, their frequency tables [k][256], each token's table index)."""
+    ids, tab = np.unique(ctx, return_inverse=True)
+    U = geo_ctx_inputs(ids)
+    tables = [learned_freq(model, U[i], level) for i in range(len(ids))]
+    return ids, tables, tab.astype(np.uint16)
+
+
+def geo_lanes_for_level(n: int) -> int:
+    return default_geo_lanes(n)
 
 
 def encode(pos: np.ndarray, attr: np.ndarray, *, mode: int, depth: int, bits=8, lanes: int = 32,
            geo_mode: int = GEO_RANS, geo_lanes: int = 0, model: dict | None = None,
-           prep: Prepared | None = None) -> bytes:
+           prep: Prepared | None = None, geo_model: dict | None = None) -> bytes:
     """Scene -> bitstream (layout documented in the design notes and in include/sgs.h)."""
     if mode in (MODE_STATIC, MODE_LEARNED, MODE_LEARNED_PE):
         bits = 8
@@ -498,7 +569,25 @@ def encode(pos: np.ndarray, attr: np.ndarray, *, mode: int, depth: int, bits=8, 
     geo_grp = b""
     geo_pay = b""
     Lg = 0
-    if n_coded:
+    if n_coded and geo_mode == GEO_LEARNED:
+        # learned geometry: one model (geo_tab); each coded level's tokens in lanes of
+        # contiguous chunks, coded with the context tables of the level above it
+        if geo_model is None:
+            raise ValueError("learned geometry needs a model")
+        validate_model(_model_arrays(geo_model))
+        geo_tab = model_bytes(geo_model)
+        for l in range(depth):
+            if not coded[l]:
+                continue
+            ctx = geo_children_ctx(P.levels[l - 1])
+            _, tables, tab = geo_level_tables(geo_model, l, ctx)
+            f, cc = static_fc(P.levels[l], tab, tables)
+            Ll = geo_lanes_for_level(len(P.levels[l]))
+            Lg += Ll
+            pay, goff, gw = rans_encode(lane_bounds(len(P.levels[l]), Ll), f, cc)
+            geo_grp += group_table_bytes(np.asarray(goff, np.uint64) + np.uint64(len(geo_pay)), gw)
+            geo_pay += pay
+    elif n_coded:
         Lg = geo_lanes if geo_lanes > 0 else default_geo_lanes(n_coded)
         tabs = [normalize_freq(np.bincount(b, minlength=NSYM)) for b in coded_syms]
         geo_tab = b"".join(table_bytes(t) for t in tabs)
@@ -634,7 +723,25 @@ def decode(buf: bytes) -> dict:
             levels[l] = np.frombuffer(buf, np.uint8, int(n_level[l]), p)
             p += int(n_level[l])
     n_coded = h["n_geo_coded"]
-    if n_coded:
+    if n_coded and h["geo_mode"] == GEO_LEARNED:
+        geo_model = parse_model(buf, h["off_geo_tab"])
+        pay = buf[h["off_geo_pay"]:h["off_attr_tab"]]
+        gp = h["off_geo_grp"]
+        for l in range(D):
+            if not coded[l]:
+                continue
+            n_l = int(n_level[l])
+            Ll = geo_lanes_for_level(n_l)
+            G = (Ll + 31) // 32
+            goff = np.frombuffer(buf, "<u8", G + 1, gp)
+            gw = np.frombuffer(buf, "<u4", G, gp + 8 * (G + 1))
+            gp += _align16(8 * (G + 1) + 4 * G)
+            ctx = geo_children_ctx(levels[l - 1])
+            if len(ctx) != n_l:
+                raise ValueError("corrupt octree level")
+            _, tables, tab = geo_level_tables(geo_model, l, ctx)
+            levels[l] = rans_decode_static16(lane_bounds(n_l, Ll), tab, tables, pay, goff, gw)
+    elif n_coded:
         cl = [l for l in range(D) if coded[l]]
         tabs, _ = parse_tables(buf, h["off_geo_tab"], len(cl))
         Lg = h["geo_lanes"]
