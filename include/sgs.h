@@ -296,6 +296,34 @@ int scene_tokens(const float *pos, const float *attr, uint32_t n, uint32_t depth
 int scene_rows(const float *pos, const float *attr, uint32_t n, uint32_t depth, uint8_t *tokens,
                uint32_t *coord, uint32_t cap, uint32_t *n_rows);
 
+/* ------------------------------------------------------------------ rendering */
+
+/* A pinhole camera: world point p maps to camera space t = rot (p - origin) (rot row-major,
+ * camera axes x right, y down, z forward) and to pixel (fx t_x / t_z + cx, fy t_y / t_z + cy);
+ * pixel (x, y) is sampled at its integer coordinates. */
+typedef struct {
+    float rot[9];
+    float origin[3];
+    float fx, fy, cx, cy;
+    uint32_t width, height;   /* 1 .. 16384 */
+} sgs_camera;
+
+/* Renders n decoded Gaussians (device attr [56][n] and pos [3][n], as scene_decode writes
+ * them) into image_dev (device float [3][height][width], background 0) with tile splatting,
+ * the 3DGS forward pass the paper's decoded scenes are drawn with (no counterpart in the
+ * paper's coder; its tables' rendering column): per Gaussian the projected 2D covariance
+ * (+0.3 I), radius ceil(3 sqrt(lambda_max)) and the 16 x 16-pixel tiles it touches, colour
+ * from the degree-3 spherical harmonics (channels 0-47) along the view ray, opacity
+ * sigmoid(channel 48), scales exp(channels 49-51), rotation the quaternion (w, x, y, z) of
+ * channels 52-55; per pixel the tile's Gaussians front to back (depth, then index), alpha =
+ * min(0.99, opacity exp(-0.5 d^T Sigma'^-1 d)) skipped below 1/255, compositing stopped
+ * before the transmittance falls below 1e-4; Gaussians with camera depth <= 0.2 are culled.
+ * Synchronous: reads back the number of (tile, Gaussian) pairs to size the sort.  The
+ * context keeps a workspace for it (grown with cudaMalloc when a frame needs more, freed
+ * by sgs_destroy).  Errors: SGS_E_INVALID, SGS_E_NOMEM, SGS_E_CUDA. */
+int sgs_render(sgs_ctx *ctx, const float *attr_dev, const float *pos_dev, uint32_t n, const sgs_camera *camera,
+               float *image_dev, sgs_stream stream);
+
 /* ------------------------------------------------------------------ autotuning */
 
 /* Lane-count tuning: the paper's complexity knob is the group size W, Gaussians per

@@ -167,6 +167,7 @@ extern "C" void sgs_destroy(sgs_ctx *c) {
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     if (c->scratch) cudaFree(c->scratch);
+    if (c->rws) cudaFree(c->rws);
     for (int i = 0; i <= kMaxStages; ++i) cudaEventDestroy(c->marks[i]);
     for (int i = 0; i < 2; ++i) cudaEventDestroy(c->amarks[i]);
     cudaEventDestroy(c->fork);

@@ -22,4 +22,6 @@ struct sgs_ctx {
     cudaStream_t aux;                   // attribute decode (lowest priority), forked from the caller
     cudaStream_t geo;                   // geometry chain (highest priority)
     cudaEvent_t fork, join, gjoin;
+    uint8_t *rws;                       // sgs_render workspace (grown on demand)
+    size_t rws_bytes;
 };

@@ -63,6 +63,12 @@ class BatchItem(ctypes.Structure):
     _fields_ = [("bits_dev", P), ("info", SceneInfo), ("out", SceneOut)]
 
 
+class Camera(ctypes.Structure):
+    _fields_ = [("rot", ctypes.c_float * 9), ("origin", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("width", u32),
+                ("height", u32)]
+
+
 class SgsError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__("%s: %s (%d)" % (what, lib().sgs_strerror(code).decode(), code))
@@ -103,6 +109,7 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(ctypes.c_size_t)]
         L.scene_tokens.argtypes = [P, P, u32, u32, P, ctypes.c_size_t, ctypes.POINTER(u32)]
         L.scene_rows.argtypes = [P, P, u32, u32, P, P, u32, ctypes.POINTER(u32)]
+        L.sgs_render.argtypes = [P, P, P, u32, ctypes.POINTER(Camera), P, P]
         L.sgs_train_pe.argtypes = [P, P, P, u32, u32, u32, ctypes.POINTER(TrainParams), u32, P, P, P]
         L.sgs_train_pe_grad.argtypes = [P, P, P, u32, u32, u32, P, u32, P, P, ctypes.POINTER(ctypes.c_float)]
         L.sgs_freeze_pe.argtypes = [P, P, P, u32, u32, u32, u32, P]
@@ -362,6 +369,22 @@ def scene_rows(pos: np.ndarray, attr: np.ndarray, depth: int):
                             max(n, 1), ctypes.byref(nr)), "scene_rows")
     r = nr.value
     return tok[:r].copy(), crd[:3 * r].reshape(3, r).copy()
+
+
+def camera(rot, origin, fx: float, fy: float, cx: float, cy: float, width: int, height: int) -> Camera:
+    c = Camera()
+    for i, v in enumerate(np.asarray(rot, np.float32).ravel()):
+        c.rot[i] = float(v)
+    for i, v in enumerate(np.asarray(origin, np.float32).ravel()):
+        c.origin[i] = float(v)
+    c.fx, c.fy, c.cx, c.cy, c.width, c.height = fx, fy, cx, cy, width, height
+    return c
+
+
+def render(ctx: Context, attr_dev, pos_dev, n: int, cam: Camera, image_dev, stream=None) -> None:
+    """Splats n decoded Gaussians into image_dev (device float [3, height, width])."""
+    _check(lib().sgs_render(ctx.handle, _ptr(attr_dev), _ptr(pos_dev), n, ctypes.byref(cam), _ptr(image_dev),
+                            _stream(stream)), "sgs_render")
 
 
 # ----------------------------------------------------------------------------- learned part
