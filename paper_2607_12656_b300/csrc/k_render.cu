@@ -424,6 +424,7 @@ extern "C" int sgs_render(sgs_ctx *ctx, const float *attr, const float *pos, uin
     uint2 *ranges = reinterpret_cast<uint2 *>(b + o_rng);
     if (cudaMemsetAsync(ranges, 0, 8ull * n_tiles, st) != cudaSuccess) return SGS_E_CUDA;
     int cur = 0;
+    ctx->launches += n ? 4 : 0;  // preprocess + scan
     if (E) {
         k_rs_emit<<<(n + 255) / 256, 256, 0, st>>>(n, P, offs, c.tx, keys[0], vals[0]);
         int tile_bits = 0;
@@ -438,7 +439,9 @@ extern "C" int sgs_render(sgs_ctx *ctx, const float *attr, const float *pos, uin
             cur ^= 1;
         }
         k_rs_ranges<<<(E + 255) / 256, 256, 0, st>>>(keys[cur], E, ranges);
+        ctx->launches += 2 + 5 * passes;  // emit, ranges; per pass count, scan (3), scatter
     }
+    ctx->launches += 1;
     k_rs_render<<<n_tiles, kTile * kTile, 0, st>>>(ranges, vals[cur], P, c, image);
     if (cudaGetLastError() != cudaSuccess) return SGS_E_CUDA;
     return SGS_OK;

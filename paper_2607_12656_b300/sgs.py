@@ -381,6 +381,19 @@ def camera(rot, origin, fx: float, fy: float, cx: float, cy: float, width: int, 
     return c
 
 
+def look_at(origin, target, up, width: int, height: int, fov_y_deg: float) -> Camera:
+    """A pinhole camera at `origin` looking at `target`, vertical field of view fov_y_deg
+    (camera axes: x right, y down, z forward)."""
+    o = np.asarray(origin, np.float64)
+    z = np.asarray(target, np.float64) - o
+    z /= np.linalg.norm(z)
+    x = np.cross(z, np.asarray(up, np.float64))
+    x /= np.linalg.norm(x)
+    y = np.cross(z, x)
+    f = 0.5 * height / np.tan(np.radians(fov_y_deg) / 2)
+    return camera(np.stack([x, y, z]), o, f, f, width / 2.0, height / 2.0, width, height)
+
+
 def render(ctx: Context, attr_dev, pos_dev, n: int, cam: Camera, image_dev, stream=None) -> None:
     """Splats n decoded Gaussians into image_dev (device float [3, height, width])."""
     _check(lib().sgs_render(ctx.handle, _ptr(attr_dev), _ptr(pos_dev), n, ctypes.byref(cam), _ptr(image_dev),
