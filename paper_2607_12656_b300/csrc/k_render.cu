@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include "sgs_ctx.h"
+#include "sgs_device.cuh"
 #include "sgs_internal.h"
 
 namespace sgs {
@@ -69,6 +70,7 @@ __global__ void k_rs_pre(const float *attr, const float *pos, uint32_t n, Cam c,
     const float ty = c.r[3] * qx + c.r[4] * qy + c.r[5] * qz;
     const float tz = c.r[6] * qx + c.r[7] * qy + c.r[8] * qz;
     P.count[i] = 0;
+    P.depth[i] = 0.0f;
     if (!(tz > 0.2f)) return;
     const float s0 = expf(attr[49ull * n + i]), s1 = expf(attr[50ull * n + i]), s2 = expf(attr[51ull * n + i]);
     float w = attr[52ull * n + i], x = attr[53ull * n + i], y = attr[54ull * n + i], z = attr[55ull * n + i];
@@ -184,25 +186,44 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_apply(const uint32_t *in, u
 
 // ------------------------------------------------------------------ entries and sort
 
-__global__ void k_rs_emit(uint32_t n, Pre P, const uint32_t *off, int tiles_x, uint64_t *keys, uint32_t *vals) {
+// Gaussians in depth order: sidx[k] is the k-th nearest (ties by index), cnt_s[k] its tile
+// count; depth keys are the positive floats' bits, which order as the floats.
+__global__ void k_rs_depth_keys(uint32_t n, Pre P, uint32_t *keys, uint32_t *vals) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || P.count[i] == 0) return;
-    const uint2 r = P.rect[i];
-    const uint32_t x0 = r.x & 0xFFFFu, y0 = r.x >> 16, x1 = r.y & 0xFFFFu, y1 = r.y >> 16;
-    const uint64_t d = __float_as_uint(P.depth[i]);  // positive floats order as their bits
-    uint32_t k = off[i];
-    for (uint32_t y = y0; y < y1; ++y)
-        for (uint32_t x = x0; x < x1; ++x) {
-            keys[k] = ((uint64_t)(y * tiles_x + x) << 32) | d;
-            vals[k] = i;
-            ++k;
-        }
+    if (i >= n) return;
+    keys[i] = __float_as_uint(P.depth[i]);
+    vals[i] = i;
 }
 
-__device__ __forceinline__ uint32_t digit_of(uint64_t key, int shift) { return (uint32_t)(key >> shift) & 255u; }
+__global__ void k_rs_gather_counts(uint32_t n, const uint32_t *sidx, const uint32_t *count, uint32_t *cnt_s) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) cnt_s[k] = count[sidx[k]];
+}
+
+// One warp per Gaussian, in depth order: its entries (tile id, Gaussian), tiles in row-major
+// order of its rectangle, written by the warp's lanes together.  A stable sort on the tile
+// then leaves each tile's Gaussians in depth order.
+__global__ void k_rs_emit(uint32_t n, Pre P, const uint32_t *sidx, const uint32_t *off, int tiles_x, uint32_t *keys,
+                          uint32_t *vals) {
+    const uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31;
+    if (k >= n) return;
+    const uint32_t i = sidx[k];
+    const uint32_t cnt = P.count[i];
+    if (cnt == 0) return;
+    const uint2 r = P.rect[i];
+    const uint32_t x0 = r.x & 0xFFFFu, y0 = r.x >> 16, w = (r.y & 0xFFFFu) - x0;
+    const uint32_t base = off[k];
+    for (uint32_t j = lane; j < cnt; j += 32) {
+        keys[base + j] = (y0 + j / w) * (uint32_t)tiles_x + x0 + j % w;
+        vals[base + j] = i;
+    }
+}
+
+__device__ __forceinline__ uint32_t digit_of(uint32_t key, int shift) { return (key >> shift) & 255u; }
 
 // counts[d * nb + b] = items of block b with digit d
-__global__ void __launch_bounds__(kSortThreads) k_sort_count(const uint64_t *keys, uint32_t n, int shift, uint32_t nb,
+__global__ void __launch_bounds__(kSortThreads) k_sort_count(const uint32_t *keys, uint32_t n, int shift, uint32_t nb,
                                                               uint32_t *counts) {
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
@@ -217,32 +238,36 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_count(const uint64_t *key
 }
 
 // Stable scatter: item order within a block is round-major, lanes in order; ranks among equal
-// digits come from match_any inside a warp and a per-digit prefix over the warps.
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t *keys, const uint32_t *vals, uint32_t n,
+// digits come from match_any inside a warp and a per-digit prefix over the warps.  The block
+// first places its items in shared memory in block-sorted order, then writes each digit's
+// run to its global place, so consecutive threads store to consecutive addresses.
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t *keys, const uint32_t *vals, uint32_t n,
                                                                 int shift, uint32_t nb, const uint32_t *offs,
-                                                                uint64_t *keys_out, uint32_t *vals_out) {
+                                                                uint32_t *keys_out, uint32_t *vals_out) {
     __shared__ uint32_t cnt[kSortThreads / 32][256];
-    __shared__ uint32_t run[256];
+    __shared__ uint32_t run[256], lbase[256], goff[256], scan_sm[8];
+    __shared__ uint32_t sk[kSortChunk];
+    __shared__ uint32_t sv[kSortChunk];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    run[threadIdx.x] = offs[(size_t)threadIdx.x * nb + blockIdx.x];
+    run[threadIdx.x] = 0;
+    goff[threadIdx.x] = offs[(size_t)threadIdx.x * nb + blockIdx.x];
     const uint64_t base = (uint64_t)blockIdx.x * kSortChunk;
+    uint32_t key[kSortRounds];
+    uint32_t val[kSortRounds], dig[kSortRounds], lrank[kSortRounds];
+#pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
         for (int w = 0; w < kSortThreads / 32; ++w) cnt[w][threadIdx.x] = 0;
         __syncthreads();
         const uint64_t i = base + (uint64_t)r * kSortThreads + threadIdx.x;
         const bool live = i < n;
-        uint64_t key = 0;
-        uint32_t val = 0, d = 256u;  // no digit: matches no real one
-        if (live) {
-            key = keys[i];
-            val = vals[i];
-            d = digit_of(key, shift);
-        }
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        key[r] = live ? keys[i] : 0u;
+        val[r] = live ? vals[i] : 0u;
+        dig[r] = live ? digit_of(key[r], shift) : 256u;  // no digit: matches no real one
+        const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
         const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-        if (live && rank == 0) cnt[warp][d] = __popc(peers);
+        if (live && rank == 0) cnt[warp][dig[r]] = __popc(peers);
         __syncthreads();
-        {   // thread t: prefix of digit t over the warps, continuing the block's running offset
+        {   // thread t: prefix of digit t over the warps, continuing the block's running count
             uint32_t acc = run[threadIdx.x];
             for (int w = 0; w < kSortThreads / 32; ++w) {
                 const uint32_t c = cnt[w][threadIdx.x];
@@ -252,21 +277,36 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t *k
             run[threadIdx.x] = acc;
         }
         __syncthreads();
-        if (live) {
-            const uint32_t p = cnt[warp][d] + rank;
-            keys_out[p] = key;
-            vals_out[p] = val;
-        }
+        lrank[r] = live ? cnt[warp][dig[r]] + rank : 0u;
         __syncthreads();
+    }
+    uint32_t total;
+    lbase[threadIdx.x] = block_excl_scan_256(run[threadIdx.x], &total, scan_sm);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r)
+        if (dig[r] < 256u) {
+            const uint32_t p = lbase[dig[r]] + lrank[r];
+            sk[p] = key[r];
+            sv[p] = val[r];
+        }
+    __syncthreads();
+    const uint32_t m = (uint32_t)min((uint64_t)kSortChunk, (uint64_t)n - base);
+    for (uint32_t k = threadIdx.x; k < m; k += kSortThreads) {
+        const uint32_t kk = sk[k];
+        const uint32_t d = digit_of(kk, shift);
+        const uint32_t g = goff[d] + (k - lbase[d]);
+        keys_out[g] = kk;
+        vals_out[g] = sv[k];
     }
 }
 
-__global__ void k_rs_ranges(const uint64_t *keys, uint32_t n, uint2 *ranges) {
+__global__ void k_rs_ranges(const uint32_t *keys, uint32_t n, uint2 *ranges) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint32_t t = (uint32_t)(keys[i] >> 32);
-    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = i;
-    if (i + 1 == n || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = i + 1;
+    const uint32_t t = keys[i];
+    if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
+    if (i + 1 == n || keys[i + 1] != t) ranges[t].y = i + 1;
 }
 
 __global__ void __launch_bounds__(kTile * kTile) k_rs_render(const uint2 *ranges, const uint32_t *vals, Pre P, Cam c,
@@ -365,16 +405,18 @@ extern "C" int sgs_render(sgs_ctx *ctx, const float *attr, const float *pos, uin
     c.w = (int)cam->width; c.h = (int)cam->height;
     c.tx = (c.w + kTile - 1) / kTile; c.ty = (c.h + kTile - 1) / kTile;
     const uint32_t n_tiles = (uint32_t)(c.tx * c.ty);
-    // per-Gaussian arrays, scan sums, tile ranges
+    // per-Gaussian arrays and their depth sort, scan sums, tile ranges
     const uint64_t nn = n ? n : 1;
     const uint32_t nsb = (uint32_t)((nn + kScanBlock - 1) / kScanBlock);
+    const uint32_t gnb = (uint32_t)((nn + kSortChunk - 1) / kSortChunk);
     uint64_t off = 0;
     auto take = [&](uint64_t bytes) { const uint64_t o = off; off = a256(off + bytes); return o; };
     const uint64_t o_uv = take(8 * nn), o_co = take(16 * nn), o_col = take(16 * nn), o_dep = take(4 * nn),
                    o_rect = take(8 * nn), o_cnt = take(4 * nn), o_off = take(4 * nn), o_sums = take(4ull * (nsb + 1)),
-                   o_rng = take(8ull * n_tiles);
-    const uint64_t fixed = off;
-    int rc = ensure_ws(ctx, fixed);
+                   o_rng = take(8ull * n_tiles), o_gk0 = take(4 * nn), o_gk1 = take(4 * nn), o_gv0 = take(4 * nn),
+                   o_gv1 = take(4 * nn), o_gc = take(4ull * 256 * gnb), o_gco = take(4ull * 256 * gnb),
+                   o_gcs = take(4ull * ((256ull * gnb + kScanBlock - 1) / kScanBlock + 1)), o_cs = take(4 * nn);
+    int rc = ensure_ws(ctx, off);
     if (rc) return rc;
     uint8_t *b = ctx->rws;
     Pre P;
@@ -386,24 +428,61 @@ extern "C" int sgs_render(sgs_ctx *ctx, const float *attr, const float *pos, uin
     P.count = reinterpret_cast<uint32_t *>(b + o_cnt);
     uint32_t *offs = reinterpret_cast<uint32_t *>(b + o_off);
     uint32_t *sums = reinterpret_cast<uint32_t *>(b + o_sums);
+    uint32_t *gk[2] = {reinterpret_cast<uint32_t *>(b + o_gk0), reinterpret_cast<uint32_t *>(b + o_gk1)};
+    uint32_t *gv[2] = {reinterpret_cast<uint32_t *>(b + o_gv0), reinterpret_cast<uint32_t *>(b + o_gv1)};
+    uint32_t *cnt_s = reinterpret_cast<uint32_t *>(b + o_cs);
+    auto radix = [&](uint32_t **k2, uint32_t **v2, uint32_t count, int bits, uint32_t *cnt, uint32_t *cnt_off,
+                     uint32_t *csums) -> int {
+        const uint32_t nb = (count + kSortChunk - 1) / kSortChunk;
+        int cur = 0;
+        for (int sh = 0; sh < bits; sh += 8) {
+            k_sort_count<<<nb, kSortThreads, 0, st>>>(k2[cur], count, sh, nb, cnt);
+            if (scan_u32(cnt, 256ull * nb, csums, cnt_off, st) != cudaSuccess) return -1;
+            k_sort_scatter<<<nb, kSortThreads, 0, st>>>(k2[cur], v2[cur], count, sh, nb, cnt_off, k2[cur ^ 1],
+                                                        v2[cur ^ 1]);
+            cur ^= 1;
+            ctx->launches += 5;
+        }
+        return cur;
+    };
     uint32_t E = 0;
+    int gcur = 0;
     if (n) {
         k_rs_pre<<<(n + 255) / 256, 256, 0, st>>>(attr, pos, n, c, P);
-        if (scan_u32(P.count, n, sums, offs, st) != cudaSuccess) return SGS_E_CUDA;
+        k_rs_depth_keys<<<(n + 255) / 256, 256, 0, st>>>(n, P, gk[0], gv[0]);
+        gcur = radix(gk, gv, n, 32, reinterpret_cast<uint32_t *>(b + o_gc), reinterpret_cast<uint32_t *>(b + o_gco),
+                     reinterpret_cast<uint32_t *>(b + o_gcs));
+        if (gcur < 0) return SGS_E_CUDA;
+        k_rs_gather_counts<<<(n + 255) / 256, 256, 0, st>>>(n, gv[gcur], P.count, cnt_s);
+        if (scan_u32(cnt_s, n, sums, offs, st) != cudaSuccess) return SGS_E_CUDA;
+        ctx->launches += 6;
         if (cudaMemcpyAsync(&E, sums + nsb, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return SGS_E_CUDA;
     }
-    // entries (double-buffered keys and values) and the sort's digit counts
+    // entries (double-buffered tile keys and Gaussian indices) and the sort's digit counts;
+    // the per-Gaussian results live below `fixed`, kept when the workspace grows
+    const uint64_t fixed = off;
     const uint64_t ne = E ? E : 1;
     const uint32_t nb = (uint32_t)((ne + kSortChunk - 1) / kSortChunk);
     const uint32_t ncnt = 256u * nb, ncsb = (ncnt + kScanBlock - 1) / kScanBlock;
-    const uint64_t o_k0 = take(8 * ne), o_k1 = take(8 * ne), o_v0 = take(4 * ne), o_v1 = take(4 * ne),
-                   o_c = take(4ull * ncnt), o_co2 = take(4ull * ncnt), o_cs = take(4ull * (ncsb + 1));
+    const uint64_t o_k0 = take(4 * ne), o_k1 = take(4 * ne), o_v0 = take(4 * ne), o_v1 = take(4 * ne),
+                   o_c = take(4ull * ncnt), o_co2 = take(4ull * ncnt), o_cs2 = take(4ull * (ncsb + 1));
     if (off > ctx->rws_bytes) {
-        // grow, keeping nothing: the per-Gaussian results are recomputed below
-        if ((rc = ensure_ws(ctx, off))) return rc;
-        b = ctx->rws;
+        uint8_t *nbuf = nullptr;
+        if (cudaMalloc(&nbuf, off) != cudaSuccess) {
+            cudaGetLastError();
+            return SGS_E_NOMEM;
+        }
+        if (cudaMemcpyAsync(nbuf, ctx->rws, fixed, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            cudaFree(nbuf);
+            return SGS_E_CUDA;
+        }
+        cudaFree(ctx->rws);
+        ctx->rws = nbuf;
+        ctx->rws_bytes = off;
+        b = nbuf;
         P.uv = reinterpret_cast<float2 *>(b + o_uv);
         P.conic_op = reinterpret_cast<float4 *>(b + o_co);
         P.colour = reinterpret_cast<float4 *>(b + o_col);
@@ -411,35 +490,23 @@ extern "C" int sgs_render(sgs_ctx *ctx, const float *attr, const float *pos, uin
         P.rect = reinterpret_cast<uint2 *>(b + o_rect);
         P.count = reinterpret_cast<uint32_t *>(b + o_cnt);
         offs = reinterpret_cast<uint32_t *>(b + o_off);
-        sums = reinterpret_cast<uint32_t *>(b + o_sums);
-        if (n) {
-            k_rs_pre<<<(n + 255) / 256, 256, 0, st>>>(attr, pos, n, c, P);
-            if (scan_u32(P.count, n, sums, offs, st) != cudaSuccess) return SGS_E_CUDA;
-        }
+        gv[0] = reinterpret_cast<uint32_t *>(b + o_gv0);
+        gv[1] = reinterpret_cast<uint32_t *>(b + o_gv1);
     }
-    uint64_t *keys[2] = {reinterpret_cast<uint64_t *>(b + o_k0), reinterpret_cast<uint64_t *>(b + o_k1)};
+    uint32_t *keys[2] = {reinterpret_cast<uint32_t *>(b + o_k0), reinterpret_cast<uint32_t *>(b + o_k1)};
     uint32_t *vals[2] = {reinterpret_cast<uint32_t *>(b + o_v0), reinterpret_cast<uint32_t *>(b + o_v1)};
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(b + o_c), *cnt_off = reinterpret_cast<uint32_t *>(b + o_co2),
-             *csums = reinterpret_cast<uint32_t *>(b + o_cs);
     uint2 *ranges = reinterpret_cast<uint2 *>(b + o_rng);
     if (cudaMemsetAsync(ranges, 0, 8ull * n_tiles, st) != cudaSuccess) return SGS_E_CUDA;
     int cur = 0;
-    ctx->launches += n ? 4 : 0;  // preprocess + scan
     if (E) {
-        k_rs_emit<<<(n + 255) / 256, 256, 0, st>>>(n, P, offs, c.tx, keys[0], vals[0]);
+        k_rs_emit<<<(uint32_t)((32ull * n + 255) / 256), 256, 0, st>>>(n, P, gv[gcur], offs, c.tx, keys[0], vals[0]);
         int tile_bits = 0;
         while ((1u << tile_bits) < n_tiles) ++tile_bits;
-        const int passes = 4 + (tile_bits + 7) / 8;
-        for (int pass = 0; pass < passes; ++pass) {
-            const int shift = 8 * pass;
-            k_sort_count<<<nb, kSortThreads, 0, st>>>(keys[cur], E, shift, nb, cnt);
-            if (scan_u32(cnt, ncnt, csums, cnt_off, st) != cudaSuccess) return SGS_E_CUDA;
-            k_sort_scatter<<<nb, kSortThreads, 0, st>>>(keys[cur], vals[cur], E, shift, nb, cnt_off, keys[cur ^ 1],
-                                                        vals[cur ^ 1]);
-            cur ^= 1;
-        }
+        cur = radix(keys, vals, E, tile_bits, reinterpret_cast<uint32_t *>(b + o_c),
+                    reinterpret_cast<uint32_t *>(b + o_co2), reinterpret_cast<uint32_t *>(b + o_cs2));
+        if (cur < 0) return SGS_E_CUDA;
         k_rs_ranges<<<(E + 255) / 256, 256, 0, st>>>(keys[cur], E, ranges);
-        ctx->launches += 2 + 5 * passes;  // emit, ranges; per pass count, scan (3), scatter
+        ctx->launches += 2;
     }
     ctx->launches += 1;
     k_rs_render<<<n_tiles, kTile * kTile, 0, st>>>(ranges, vals[cur], P, c, image);
