@@ -224,7 +224,7 @@ typedef struct {
  * are independent, and Sec. 3.4.2's parallelism over groups extends across them).  Every
  * pipeline stage of all n scenes runs as ONE persistent launch: its CTAs take work items
  * (the lanes' groups, table expansions, scan tiles, blocks of octree leaves of every scene)
- * from a shared counter, so a run is at most 13 stage launches whatever n is (plus one
+ * from a shared counter, so a run is at most 14 stage launches whatever n is (plus one
  * kernel that starts the run and one that folds the scenes' status words).
  *
  * A plan binds the items' buffers (bitstreams, outputs) and holds, in one device block, every
