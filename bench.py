@@ -57,13 +57,14 @@ K_FIXED_TRAFFIC = 43_916_288 + 141_727_744
 
 BATCH = dict(n_scenes=64, lo=50_000, hi=3_000_000, size_seed=3000, depth_lo=14, depth_hi=17,
              desc="batched decode of 64 scenes: N log-uniform 50k..3M (seeded), depth U{14..17}, "
-                  "even scenes learned-model rANS (W ~ 220 rows per lane), odd scenes channel-wise "
-                  "static rANS (W ~ 32 rows per lane), rANS-coded octree levels; one persistent "
-                  "launch per stage over all scenes")
+                  "even scenes learned-model rANS, odd scenes channel-wise static rANS, rows per lane "
+                  "per mode chosen by the lane tuner, rANS-coded octree levels; one persistent launch "
+                  "per stage over all scenes")
 
 
-def batch_specs(n_scenes: int) -> list:
-    """(index, N, seed, depth, mode, lanes) of every scene of the batched workload."""
+def batch_specs(n_scenes: int, w_learned: int = 220, w_static: int = 32) -> list:
+    """(index, N, seed, depth, mode, lanes) of every scene of the batched workload, at W rows
+    per lane per coding mode."""
     from paper_2607_12656_b300.scenegen import loguniform_sizes
     b = BATCH
     sizes = loguniform_sizes(b["size_seed"], n_scenes, b["lo"], b["hi"])
@@ -74,7 +75,7 @@ def batch_specs(n_scenes: int) -> list:
         n = int(sizes[j])
         kept = n - n // 10
         learned = j % 2 == 0
-        w = 220 if learned else 32
+        w = w_learned if learned else w_static
         lanes = max(32, -(-kept // w))
         out.append((j, n, 3000 + j, int(depths[j]), 2 if learned else 1, lanes))
     return out
@@ -123,10 +124,15 @@ def encode_scene(spec, model=None) -> bytes:
     return sgs.scene_encode(sc.pos, sc.attr, **kw)
 
 
-def build_batch(n_scenes: int, train_steps: int, specs=None):
+TUNED = {}  # rows per lane chosen by the tuner for the batched workload, per coding mode
+
+
+def build_batch(n_scenes: int, train_steps: int, specs=None, tune: bool = False):
     """All bitstreams of a multi-scene workload: scenes are generated and encoded by a pool of
     spawned workers; one context model, trained on the first learned scene, serves every
-    learned scene."""
+    learned scene.  With `tune`, the rows per lane of each coding mode are chosen by the
+    lane tuner (sgs_autotune: the fastest decode over W in 16..256) on that mode's
+    median-size scene, and every scene of the mode is encoded at that W."""
     import concurrent.futures as cf
     import multiprocessing as mp
     specs = batch_specs(n_scenes) if specs is None else specs
@@ -134,18 +140,36 @@ def build_batch(n_scenes: int, train_steps: int, specs=None):
     os.environ.setdefault("OMP_NUM_THREADS", str(max(1, (os.cpu_count() or 1) // workers)))
     bufs = [None] * len(specs)
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as pool:
-        futs = {pool.submit(encode_scene, s): s[0] for s in specs if s[4] != 2}
         learned = [s for s in specs if s[4] == 2]
         model = None
+        from paper_2607_12656_b300 import sgs
+        from paper_2607_12656_b300.scenegen import make_scene
         if learned:
-            from paper_2607_12656_b300 import learned as L, sgs
-            from paper_2607_12656_b300.scenegen import make_scene
+            from paper_2607_12656_b300 import learned as L
             j, n, seed, depth, mode, lanes = learned[0]
             ctx = sgs.Context(0, 0)
             model = L.train_and_freeze(ctx, make_scene(n, seed), depth, lanes, steps=train_steps,
                                        batch=65536, seed=1)
             ctx.close()
-            futs.update({pool.submit(encode_scene, s, model): s[0] for s in learned})
+        if tune:
+            from paper_2607_12656_b300.tune import LaneTuner
+            tuner = LaneTuner()
+            ctx = sgs.Context(0, 0)
+            w_of = {}
+            for mode in sorted({s[4] for s in specs if s[4] != 0}):
+                mine = sorted((s for s in specs if s[4] == mode), key=lambda s: s[1])
+                j, n, seed, depth, _, _ = mine[len(mine) // 2]
+                sc = make_scene(n, seed)
+                lanes = tuner.choose_lanes(ctx, sc.pos, sc.attr, mode=mode, depth=depth, reps=3,
+                                           model=model if mode == 2 else None)
+                w_of[mode] = -(-(n - n // 10) // lanes)
+            ctx.close()
+            TUNED.update({{1: "static", 2: "learned"}[m]: w for m, w in w_of.items()})
+            specs = [(j, n, seed, depth, mode, max(32, -(-(n - n // 10) // w_of[mode])) if mode in w_of else lanes)
+                     for j, n, seed, depth, mode, lanes in specs]
+            learned = [s for s in specs if s[4] == 2]
+        futs = {pool.submit(encode_scene, s): s[0] for s in specs if s[4] != 2}
+        futs.update({pool.submit(encode_scene, s, model): s[0] for s in learned})
         for f in cf.as_completed(futs):
             bufs[futs[f]] = f.result()
     return specs, bufs
@@ -464,7 +488,7 @@ def run_batch(args):
     # scenes are independent: rank r decodes its share of the batch, no exchange
     all_specs = batch_specs(args.scenes)
     specs, bufs = build_batch(args.scenes, args.train_steps or 300,
-                              [all_specs[i] for i in replicas.shard(len(all_specs), rank, world)])
+                              [all_specs[i] for i in replicas.shard(len(all_specs), rank, world)], tune=True)
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
@@ -564,6 +588,8 @@ def run_batch(args):
             "config": {"workload": BATCH["desc"] + " [%d scenes, split by scene over %d GPU(s)]" % (args.scenes, world),
                        "n_rows": rows_all,
                        "scenes": len(items), "learned_scenes": sum(1 for s in specs if s[4] == 2),
+                       "rows_per_lane": dict(TUNED), "tuning": "lane tuner (sgs_autotune, fastest decode over W "
+                                                               "in 16..256) on each mode's median scene",
                        "bitstream_bytes": in_bytes, "output_bytes": out_bytes,
                        "l2": "flushed (256 MiB write) before every timed step; outputs exceed L2",
                        "parallelism": "scenes split across GPUs" if world > 1 else "single GPU"},
