@@ -159,3 +159,15 @@ def test_batch_bytes_host_side(small_scene):
     with pytest.raises(sgs.SgsError) as e:
         sgs.scene_batch_bytes([(fake + 8, infos[0], fake, fake)])
     assert e.value.code == sgs.E_INVALID
+
+
+def test_look_at_camera():
+    """The binding's camera: an orthonormal world-to-camera rotation whose z axis points at
+    the target, which projects to the image centre; the focal length gives the field of view."""
+    import math
+    cam = sgs.look_at([0.2, -0.4, -1.0], [0.5, 0.5, 0.5], [0, -1, 0], 640, 480, 60.0)
+    R = np.array(cam.rot[:], np.float64).reshape(3, 3)
+    assert np.allclose(R @ R.T, np.eye(3), atol=1e-6)
+    t = R @ (np.array([0.5, 0.5, 0.5]) - np.array(cam.origin[:]))
+    assert abs(t[0]) < 1e-5 and abs(t[1]) < 1e-5 and t[2] > 0
+    assert abs(cam.fy - 240.0 / math.tan(math.radians(30.0))) < 1e-3 and cam.cx == 320.0 and cam.cy == 240.0
