@@ -250,13 +250,15 @@ def pe_cdf(mu8, n, s):
     return np.where(s <= 0, 0, np.where(s >= 256, 65536, cdf))
 
 
-def token_fc(m: dict, syms_rows: np.ndarray, lane_row: np.ndarray, coord: np.ndarray, depth: int):
-    """f and cum of every token in lane-major order (lane by lane, row by row, channel by
-    channel), the order of the attribute rANS streams."""
+def token_fc(m: dict, syms_rows: np.ndarray, lane_row: np.ndarray, coord: np.ndarray, depth: int,
+             row_lo: int = 0, row_hi: int | None = None):
+    """f and cum of the tokens of rows [row_lo, row_hi) (all by default) in lane-major order
+    (lane by lane, row by row, channel by channel), the order of the attribute rANS streams."""
     n_rows = syms_rows.shape[0]
-    if n_rows == 0:
+    row_hi = n_rows if row_hi is None else row_hi
+    if row_hi <= row_lo:
         return np.zeros(0, np.uint32), np.zeros(0, np.uint32)
-    pos = np.arange(n_rows * NCHAN, dtype=np.int64)   # row-major = lane-major (lanes own row ranges)
+    pos = np.arange(row_lo * NCHAN, row_hi * NCHAN, dtype=np.int64)  # row-major = lane-major
     u, c, s, row, _ = M.contexts(syms_rows, lane_row, pos)
     phi = phi_q(coord, depth)[row]
     mu8, n = forward_int(m, u, c, phi)

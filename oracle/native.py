@@ -108,7 +108,7 @@ def lib():
         L.or_pe_cdf.restype = u32
         L.or_pe_cdf.argtypes = [i32, i32, ctypes.c_int, P]
         L.or_rans_decode_pe.restype = ctypes.c_int
-        L.or_rans_decode_pe.argtypes = [P, P, P, P, i64, ctypes.c_int, P, i64, P, i64, P, P, P]
+        L.or_rans_decode_pe.argtypes = [P, P, P, P, i64, ctypes.c_int, P, i64, i64, P, i64, P, P, P]
         assert L.or_model_size() == ctypes.sizeof(Model)
         _lib = L
     return _lib

@@ -518,17 +518,18 @@ uint32_t or_pe_cdf(int32_t mu8, int32_t n, int s, const uint32_t *exp2q)
     return (uint32_t)s + (uint32_t)((F * 65280ull) >> 23);
 }
 
-/* Decodes lanes [0, n_lanes) coded with the position-aware model: the stream order and the
- * group format are those of the plain learned decoder; token (row, c) is found by walking
+/* Decodes lanes [lane_lo, lane_hi) (lane_lo a multiple of 32) coded with the position-aware
+ * model: the stream order and the group format are those of the plain learned decoder; token (row, c) is found by walking
  * the CDF upwards from symbol 0.  coord: uint32 [3][n_rows] voxel coordinates of the rows. */
 int or_rans_decode_pe(const or_pe_model *M, const uint32_t *exp2q, const int8_t *sin8,
                       const uint32_t *coord, int64_t n_rows, int depth, const int64_t *lane_row,
-                      int64_t n_lanes, const uint8_t *payload, int64_t pay_len,
+                      int64_t lane_lo, int64_t lane_hi, const uint8_t *payload, int64_t pay_len,
                       const uint64_t *grp_off, const uint32_t *grp_words, uint8_t *syms)
 {
-    int64_t g = 0;
-    for (int64_t j0 = 0; j0 < n_lanes; j0 += 32, ++g) {
-        int64_t j1 = j0 + 32 < n_lanes ? j0 + 32 : n_lanes;
+    if (lane_lo % 32 != 0) return -1;
+    int64_t g = lane_lo / 32;
+    for (int64_t j0 = lane_lo; j0 < lane_hi; j0 += 32, ++g) {
+        int64_t j1 = j0 + 32 < lane_hi ? j0 + 32 : lane_hi;
         int nl = (int)(j1 - j0);
         or_reader r;
         uint32_t x[32];

@@ -403,8 +403,10 @@ def rans_decode_learned(model, lane_row, lane_lo, lane_hi, payload, goff, gw, n_
     return syms[:n_rows]
 
 
-def rans_decode_pe(model: dict, coord: np.ndarray, depth: int, lane_row: np.ndarray, payload, goff, gw) -> np.ndarray:
-    """Position-aware learned decode of every lane; row-major symbols [n_rows, 56]."""
+def rans_decode_pe(model: dict, coord: np.ndarray, depth: int, lane_row: np.ndarray, payload, goff, gw,
+                   lane_lo: int = 0, lane_hi: int | None = None) -> np.ndarray:
+    """Position-aware learned decode of lanes [lane_lo, lane_hi) (all by default); row-major
+    symbols [n_rows, 56] (rows of other lanes stay 0)."""
     L = native.lib()
     ms = native.pe_model_struct(model)
     n_rows = int(lane_row[-1])
@@ -416,8 +418,9 @@ def rans_decode_pe(model: dict, coord: np.ndarray, depth: int, lane_row: np.ndar
     gwa = np.ascontiguousarray(gw if len(gw) else np.zeros(1), np.uint32)
     ex = _exp2q_arr()
     s8 = _sin8_arr()
+    lane_hi = len(lane_row) - 1 if lane_hi is None else lane_hi
     rc = L.or_rans_decode_pe(native.ctypes.byref(ms), native.ptr(ex), native.ptr(s8), native.ptr(crd), n_rows,
-                             depth, native.ptr(lr), len(lane_row) - 1, native.ptr(pay), len(payload),
+                             depth, native.ptr(lr), lane_lo, lane_hi, native.ptr(pay), len(payload),
                              native.ptr(go), native.ptr(gwa), native.ptr(syms))
     if rc != 0:
         raise ValueError("corrupt rANS stream")

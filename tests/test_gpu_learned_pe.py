@@ -219,3 +219,33 @@ def test_trained_model_codes_better_than_channel_wise(ctx):
     P = S.prepare(sc.pos, sc.attr, 14, 8)
     st, attr, pos, crd, _ = gpu_decode(ctx, pb)
     assert st == sgs.OK and same_bits(attr, P.attr) and np.array_equal(crd, P.coord)
+
+
+def test_full_size_scene(ctx):
+    """The bench's configuration: 1M Gaussians, depth 16, 28,125 lanes (W = 32), model trained
+    2,000 steps of 65,536 tokens on the device; every decoded value equals the oracle's;
+    sampled groups' bytes equal the oracle encoder's and the oracle decodes them to the same
+    tokens."""
+    from paper_2607_12656_b300 import learned
+    sc = make_scene(1_000_000, 2000)
+    lanes = 28125
+    model = learned.train_and_freeze_pe(ctx, sc, 16, lanes, steps=2000, batch=65536, seed=1)
+    buf = sgs.scene_encode(sc.pos, sc.attr, mode=sgs.MODE_LEARNED_PE, depth=16, lanes=lanes, model=model, ctx=ctx)
+    P = S.prepare(sc.pos, sc.attr, 16, 8)
+    st, attr, pos, crd, _ = gpu_decode(ctx, buf)
+    assert st == sgs.OK and same_bits(attr, P.attr) and same_bits(pos, P.pos) and np.array_equal(crd, P.coord)
+    h = S.parse_header(buf)
+    m = E.parse_model(buf, h["off_attr_tab"])
+    G = (lanes + 31) // 32
+    goff = np.frombuffer(buf, "<u8", G + 1, h["off_attr_grp"])
+    gw = np.frombuffer(buf, "<u4", G, h["off_attr_grp"] + 8 * (G + 1))
+    pay = buf[h["off_attr_pay"]:]
+    lr = S.lane_bounds(P.n_rows, lanes)
+    q = P.q.astype(np.uint8)
+    for g in (0, 411, G - 1):
+        lo, hi = 32 * g, min(lanes, 32 * g + 32)
+        f, c = E.token_fc(m, q, lr, P.coord, 16, int(lr[lo]), int(lr[hi]))
+        want, _, _ = S.rans_encode((lr[lo:hi + 1] - lr[lo]) * 56, f, c)
+        assert pay[int(goff[g]):int(goff[g + 1])] == want
+        dec = S.rans_decode_pe(m, P.coord, 16, lr, pay, goff, gw, lo, hi)
+        assert np.array_equal(dec[lr[lo]:lr[hi]], q[lr[lo]:lr[hi]])
