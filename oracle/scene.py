@@ -708,8 +708,10 @@ def parse_header(buf: bytes) -> dict:
     return h
 
 
-def decode(buf: bytes) -> dict:
-    """Bitstream -> {attr [56][n], pos [3][n], coord [3][n], q [n][56]} (rows in Morton order)."""
+def decode(buf: bytes, attr_groups: int | None = None) -> dict:
+    """Bitstream -> {attr [56][n], pos [3][n], coord [3][n], q [n][56]} (rows in Morton order).
+    attr_groups = k limits a learned-model decode to the attribute lanes of the first k groups
+    of 32 (rows of the other lanes stay 0): a bounded sample for timing."""
     h = parse_header(buf)
     D, nr, U = h["depth"], h["n_rows"], h["n_leaves"]
     n_level = np.frombuffer(buf, "<u4", D, h["off_levels"]).astype(np.int64)
@@ -793,9 +795,11 @@ def decode(buf: bytes) -> dict:
             q[perm] = syms.reshape(nr, NCHAN)
         elif mode == MODE_LEARNED:
             model = parse_model(buf, h["off_attr_tab"])
-            q = rans_decode_learned(model, lane_row, 0, L, pay, goff, gw, nr).astype(np.uint32)
+            hi = L if attr_groups is None else min(L, 32 * attr_groups)
+            q = rans_decode_learned(model, lane_row, 0, hi, pay, goff, gw, nr).astype(np.uint32)
         else:
             model = model_pe.parse_model(buf, h["off_attr_tab"])
-            q = rans_decode_pe(model, coord, D, lane_row, pay, goff, gw).astype(np.uint32)
+            hi = L if attr_groups is None else min(L, 32 * attr_groups)
+            q = rans_decode_pe(model, coord, D, lane_row, pay, goff, gw, 0, hi).astype(np.uint32)
     attr = np.stack([dequantize(q[:, c], step[c], offset[c]) for c in range(NCHAN)]) if nr else np.zeros((NCHAN, 0), np.float32)
     return {"attr": attr, "pos": position(coord, D), "coord": coord, "q": q, "header": h}

@@ -28,6 +28,19 @@ namespace sgs {
 
 __constant__ uint32_t kExp2Q[256] = {SGS_EXP2Q_VALUES};
 
+// The decoder expands e(t) = EXP2Q[t & 255] >> (t >> 8) into one table over t = 0 .. kETop:
+// e(t) = 0 for every t >= kETop (EXP2Q[0] = 2^23 is the only entry that survives a shift by
+// 23, and nothing survives 24), so clamping t at kETop instead of 6144 leaves every e_k as
+// it is and turns the lookup into a single load.
+constexpr int kETop = 23 * 256 + 1;
+constexpr uint32_t kExp2QHost[256] = {SGS_EXP2Q_VALUES};
+constexpr bool exp_tail_zero() {
+    for (int t = kETop; t <= 6144; ++t)
+        if ((kExp2QHost[t & 255] >> (t >> 8)) != 0u) return false;
+    return (kExp2QHost[0] >> 23) == 1u;
+}
+static_assert(exp_tail_zero(), "EXP2Q vanishes from 23 * 256 + 1 on");
+
 
 // Frozen model blob offsets (bytes).
 constexpr int kMB_B1 = 32, kMB_B2 = 14368, kMB_B3 = 14624, kMB_W1 = 15648, kMB_W2 = 15904,
@@ -83,7 +96,7 @@ struct LearnedParams {
 constexpr int kPW = 12;                  // producer warps
 constexpr int kPT = 32 * kPW;            // producer threads
 constexpr int kLT = kPT + 32;            // + consumer warp
-constexpr int kNB = 8;                   // ring depth (steps)
+constexpr int kNB = 7;                   // ring depth (steps)
 constexpr int kQW = 4;                   // warps per step (8 contexts each)
 constexpr int kSW = kPW / kQW;           // steps in flight
 constexpr uint32_t kWaitLimit = 1u << 24;
@@ -96,8 +109,8 @@ struct LSmem2 {
     alignas(16) __nv_bfloat16 w2[64 * kBS];
     int32_t b2[64];
     alignas(16) __nv_bfloat16 w3[256 * kBS];
-    int32_t b3[256];
-    uint32_t exp2q[256];
+    int32_t b3m[256];                           // b3 - 0x4B400000 (see layer 3)
+    uint32_t etab[kETop + 1];                   // e(t), t = 0 .. kETop
     alignas(16) __nv_bfloat16 h2t[kPW][8 * kBS];  // per warp: layer-2 output, [context][unit]
     uint8_t ctx[32 * 4 * kNChan];               // [lane][ring row][channel]
     alignas(16) uint16_t cdf[kNB][32][kCS];     // cumulative frequency of each symbol
@@ -108,6 +121,7 @@ struct LSmem2 {
     alignas(8) uint64_t full[kNB], empty[kNB];
     int32_t m1, sh1, m2, sh2;
     uint32_t ms, ss;
+    uint32_t dcap;  // smallest d with (d ms) >> ss >= kETop, saturated at 2^32 - 1
     int bad;
     int abort_;
 };
@@ -151,6 +165,10 @@ __device__ bool load_model2(LSmem2 &S, const uint8_t *m, int *status) {
         S.ms = (uint32_t)h[4]; S.ss = (uint32_t)h[5];
         S.bad = !(S.sh1 >= 1 && S.sh1 <= 47 && S.sh2 >= 1 && S.sh2 <= 47 && S.m1 >= 0 && S.m2 >= 0 &&
                   S.ms >= 1 && S.ms < (1u << 24) && S.ss <= 24);
+        if (!S.bad) {
+            const uint64_t dc = (((uint64_t)kETop << S.ss) + S.ms - 1) / S.ms;
+            S.dcap = dc > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)dc;
+        }
         S.abort_ = 0;
     }
     const int32_t *b1 = reinterpret_cast<const int32_t *>(m + kMB_B1);
@@ -166,11 +184,11 @@ __device__ bool load_model2(LSmem2 &S, const uint8_t *m, int *status) {
         badb |= (b2[i] >= (1 << 24) || b2[i] <= -(1 << 24));
     }
     for (int i = tid; i < 256; i += kLT) {
-        S.b3[i] = b3[i];
+        S.b3m[i] = b3[i] - 0x4B400000;
         badb |= (b3[i] >= (1 << 24) || b3[i] <= -(1 << 24));
-        S.exp2q[i] = kExp2Q[i];
         S.w1[i] = (int8_t)m[kMB_W1 + i];
     }
+    for (int t = tid; t <= kETop; t += kLT) S.etab[t] = kExp2Q[t & 255] >> (t >> 8);
     for (int i = tid; i < 64 * 64; i += kLT) S.w2[(i >> 6) * kBS + (i & 63)] = bf((int8_t)m[kMB_W2 + i]);
     for (int i = tid; i < 256 * 64; i += kLT) S.w3[(i >> 6) * kBS + (i & 63)] = bf((int8_t)m[kMB_W3 + i]);
     __syncthreads();
@@ -255,11 +273,12 @@ __device__ __forceinline__ void produce_pass(LSmem2 &S, uint32_t i, int c, int b
             ldsm_a(S.w3 + 16 * mt * kBS + 16 * kt, a0, a1, a2, a3);
             mma_bf16(acc, a0, a1, a2, a3, bf3[kt][0], bf3[kt][1]);
         }
-        const int32_t b30 = S.b3[16 * mt + g], b31 = S.b3[16 * mt + g + 8];
-        z[mt][0] = __float2int_rn(acc[0]) + b30;
-        z[mt][1] = __float2int_rn(acc[1]) + b30;
-        z[mt][2] = __float2int_rn(acc[2]) + b31;
-        z[mt][3] = __float2int_rn(acc[3]) + b31;
+        // acc is an integer of magnitude below 2^21, so acc + 1.5 2^23 is exact and its bit
+        // pattern is 0x4B400000 + acc: the conversion is one full-rate add
+        const int32_t b30 = S.b3m[16 * mt + g], b31 = S.b3m[16 * mt + g + 8];
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            z[mt][v] = __float_as_int(__fadd_rn(acc[v], 12582912.0f)) + (v < 2 ? b30 : b31);
     }
     // ---- integer softmax of contexts 2t (e = 0) and 2t+1 (e = 1); the 8 lanes g = 0..7 with
     //      this t hold all 256 symbols of both
@@ -283,18 +302,19 @@ __device__ __forceinline__ void produce_pass(LSmem2 &S, uint32_t i, int c, int b
             if (om > zmax[e] || (om == zmax[e] && oa < amax[e])) { zmax[e] = om; amax[e] = oa; }
         }
     }
-    // e_k = EXP2Q[t_k & 255] >> (t_k >> 8), t_k = min((d_k ms) >> ss, 6144); z is overwritten
-    const uint32_t ms = S.ms, ss = S.ss;
+    // e_k = etab[min((min(d_k, dcap) ms) >> ss, kETop)]: for d_k >= dcap both t_k and the
+    // clamped t are at least kETop, where e vanishes; below dcap the product shifted by ss is
+    // under 2^32 and the clamp does nothing.  z is overwritten with e_k.
+    const uint32_t ms = S.ms, ss = S.ss, dcap = S.dcap;
     uint32_t E[2] = {0u, 0u};
 #pragma unroll
     for (int mt = 0; mt < 16; ++mt)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int e = v & 1;
-            const uint32_t d = (uint32_t)(zmax[e] - z[mt][v]);
-            const uint64_t tt = ((uint64_t)d * ms) >> ss;
-            const uint32_t tk = tt > 6144u ? 6144u : (uint32_t)tt;
-            const uint32_t ek = S.exp2q[tk & 255] >> (tk >> 8);
+            const uint32_t d = min((uint32_t)(zmax[e] - z[mt][v]), dcap);
+            const uint32_t tt = (uint32_t)(((uint64_t)d * ms) >> ss);
+            const uint32_t ek = S.etab[min(tt, (uint32_t)kETop)];
             z[mt][v] = (int32_t)ek;
             E[e] += ek;
         }
@@ -305,34 +325,38 @@ __device__ __forceinline__ void produce_pass(LSmem2 &S, uint32_t i, int c, int b
         for (int o = 4; o < 32; o <<= 1) E[e] += __shfl_xor_sync(0xffffffffu, E[e], o);
         R[e] = (uint32_t)((65280ull << 32) / E[e]);
     }
-    // floor terms floor(e_k R / 2^32) and their sum
-#pragma unroll
-    for (int mt = 0; mt < 16; ++mt)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const uint32_t fl = __umulhi((uint32_t)z[mt][v], R[v & 1]);
-            z[mt][v] = (int32_t)fl;
-            Tf[v & 1] += fl;
-        }
-#pragma unroll
-    for (int e = 0; e < 2; ++e)
-#pragma unroll
-        for (int o = 4; o < 32; o <<= 1) Tf[e] += __shfl_xor_sync(0xffffffffu, Tf[e], o);
-    // f_k = 1 + floor term, the remainder at the argmax; frequencies in symbol order, then an
-    // in-place exclusive prefix turns them into the cumulative table
+    // f_k = 1 + floor(e_k R / 2^32) stored in symbol order; their sum gives the remainder,
+    // which one lane per context then adds at the argmax
     uint16_t *cdfw = &S.cdf[b][8 * q][0];  // this warp's 8 contexts, rows kCS apart
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-        const uint32_t rem = 65536u - 256u - Tf[e];
         uint16_t *row = cdfw + (2 * t + e) * kCS;
 #pragma unroll
         for (int mt = 0; mt < 16; ++mt)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int k = 16 * mt + 8 * h + g;
-                const uint32_t f = 1u + (uint32_t)z[mt][2 * h + e] + (k == amax[e] ? rem : 0u);
-                row[k] = (uint16_t)f;  // f <= 65281
+                const uint32_t f = __umulhi((uint32_t)z[mt][2 * h + e], R[e]) + 1u;
+                Tf[e] += f;
+                row[16 * mt + 8 * h + g] = (uint16_t)f;
             }
+    }
+    uint32_t pk[2];  // (remainder << 8) | argmax of context 2t + e
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) Tf[e] += __shfl_xor_sync(0xffffffffu, Tf[e], o);
+        pk[e] = ((65536u - Tf[e]) << 8) | (uint32_t)amax[e];
+    }
+    {
+        // context n = lane (lanes 0..7) is held by the lanes with t = n / 2, component n % 2
+        const uint32_t p0 = __shfl_sync(0xffffffffu, pk[0], (lane & 7) >> 1);
+        const uint32_t p1 = __shfl_sync(0xffffffffu, pk[1], (lane & 7) >> 1);
+        const uint32_t p = (lane & 1) ? p1 : p0;
+        __syncwarp();
+        if (lane < 8) {
+            uint16_t *fa = cdfw + lane * kCS + (p & 255u);
+            *fa = (uint16_t)(*fa + (p >> 8));  // f <= 65281
+        }
     }
     __syncwarp();
     {

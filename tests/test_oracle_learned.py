@@ -153,6 +153,21 @@ def test_learned_round_trip(trained_toy):
     assert np.array_equal(d["pos"], P.pos)
 
 
+def test_sampled_decode_is_the_full_decode_on_its_groups(trained_toy):
+    """decode(attr_groups=k) decodes the rows of the first k groups of 32 lanes exactly as the
+    full decode does and leaves every other row 0 (the bounded sample timed as a baseline)."""
+    sc, P, q, lr, p, _ = trained_toy
+    m = M.freeze({k: v.astype(np.float32) for k, v in p.items()}, q, lr, seed=3)
+    L = 80
+    buf = S.encode(None, None, mode=S.MODE_LEARNED, depth=10, lanes=L, model=m, prep=P)
+    rows = S.lane_bounds(P.n_rows, L)
+    for k in (0, 1, 2, 5):
+        d = S.decode(buf, attr_groups=k)
+        cut = int(rows[min(L, 32 * k)])
+        assert np.array_equal(d["q"][:cut], P.q[:cut]) and not d["q"][cut:].any()
+        assert np.array_equal(d["coord"], P.coord)
+
+
 def _gain(rho):
     from paper_2607_12656_b300.scenegen import make_scene, kaiming_init
     sc = make_scene(20000, 2, rho)
