@@ -364,15 +364,17 @@ __device__ __forceinline__ void produce_pass(LSmem2 &S, uint32_t i, int c, int b
         // quarter-warp touch 8 rows at the same column: 528-byte rows put them in 8 bank groups
         const int n = lane & 7, qq = lane >> 3;
         uint16_t *seg = cdfw + n * kCS + qq * 64;
+        // Every f >= 1 and a context's f sum to 2^16, so the even and the odd halves of a
+        // segment each sum below 2^16: the words add without carries between the halves, and
+        // so do the two halves of one word (f0 + f1 < 2^16).
         uint4 w[8];
-        uint32_t sum = 0;
+        uint32_t sw = 0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             w[j] = reinterpret_cast<const uint4 *>(seg)[j];
-            const uint32_t *h = reinterpret_cast<const uint32_t *>(&w[j]);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) sum += (h[k] & 0xFFFFu) + (h[k] >> 16);
+            sw += (w[j].x + w[j].y) + (w[j].z + w[j].w);
         }
+        const uint32_t sum = (sw & 0xFFFFu) + (sw >> 16);
         uint32_t incl = sum;  // scan over the 4 quarters of context n (lanes n, n+8, n+16, n+24)
         const uint32_t n1 = __shfl_up_sync(0xffffffffu, incl, 8);
         if (qq >= 1) incl += n1;
@@ -384,9 +386,10 @@ __device__ __forceinline__ void produce_pass(LSmem2 &S, uint32_t i, int c, int b
             uint32_t *h = reinterpret_cast<uint32_t *>(&w[j]);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const uint32_t f0 = h[k] & 0xFFFFu, f1 = h[k] >> 16;
-                h[k] = (run & 0xFFFFu) | ((run + f0) << 16);
-                run += f0 + f1;
+                // (run, run + f0) with run + f0 <= 65535 below symbol 256; then run += f0 + f1
+                const uint32_t hv = h[k];
+                h[k] = run * 0x10001u + (hv << 16);
+                run += (hv * 0x10001u) >> 16;
             }
             reinterpret_cast<uint4 *>(seg)[j] = w[j];
         }
