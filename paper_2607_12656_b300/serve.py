@@ -2,7 +2,9 @@
 
 Requests (scene bitstreams with arrival times) are admitted as soon as a slot and HBM budget
 are free: admission charges each request its device footprint (bitstream + decoded outputs +
-decode scratch) against the budget.  Each slot owns a CUDA stream and a library context (its
+decode scratch) against the budget, in arrival order.  A request whose footprint alone
+exceeds the budget can never be admitted; it is answered at once with E_NOMEM instead of
+holding up the queue.  Each slot owns a CUDA stream and a library context (its
 own scratch and status word), so admitted decodes overlap on the device while the host loop
 keeps admitting and retiring.  Latency = completion event time - arrival time.
 
@@ -69,18 +71,20 @@ class _Slot:
 class DecodeServer:
     def __init__(self, scenes: list[Scene], *, slots: int = 8, hbm_budget: int = 120 << 30,
                  device: int = 0, keep_outputs: bool = False):
-        import torch
-        self.torch = torch
         self.scenes = scenes
         self.device = device
         self.budget = hbm_budget
         self.keep = keep_outputs
         scratch = max(s.info.scratch_bytes for s in scenes)
-        self.slots = [_Slot(device, scratch) for _ in range(slots)]
+        self.slots = self._make_slots(slots, scratch)
         self.in_use = 0
 
+    # ---- device side: one stream and one library context per slot
+    def _make_slots(self, n: int, scratch: int) -> list:
+        return [_Slot(self.device, scratch) for _ in range(n)]
+
     def _launch(self, slot: _Slot, req: int, sid: int, arrival: float, now: float):
-        torch = self.torch
+        import torch
         sc = self.scenes[sid]
         dev = torch.device("cuda", self.device)
         with torch.cuda.stream(slot.stream):
@@ -94,8 +98,20 @@ class DecodeServer:
             sgs.scene_decode(slot.ctx, bits, sc.info, attr, pos, None, None, slot.stream)
             ev1.record(slot.stream)
         slot.busy = (req, sid, arrival, now, ev0, ev1, (bits, attr, pos))
-        self.in_use += sc.footprint()
 
+    def _finished(self, slot: _Slot) -> bool:
+        return slot.busy[5].query()
+
+    def _retire(self, slot: _Slot, t0: float) -> Result:
+        req, sid, arr, adm, ev0, ev1, bufs = slot.busy
+        st = slot.ctx.sync(slot.stream)
+        r = Result(req, sid, arr, adm, time.perf_counter() - t0, st)
+        if self.keep:
+            n = self.scenes[sid].n_rows
+            r.attr, r.pos = bufs[1][:, :n].cpu(), bufs[2][:, :n].cpu()
+        return r
+
+    # ---- host loop: arrivals, retirement, admission
     def run(self, requests: list[tuple[float, int]]) -> list[Result]:
         """requests: (arrival offset in s, scene index), sorted by arrival.  Returns results in
         completion order."""
@@ -107,25 +123,26 @@ class DecodeServer:
             now = time.perf_counter() - t0
             while pending and pending[0][1] <= now:
                 queue.append(pending.popleft())
-            # retire finished decodes
             for sl in self.slots:
-                if sl.busy and sl.busy[5].query():
-                    req, sid, arr, adm, ev0, ev1, bufs = sl.busy
-                    st = sl.ctx.sync(sl.stream)
-                    done = time.perf_counter() - t0
-                    r = Result(req, sid, arr, adm, done, st)
-                    if self.keep:
-                        r.attr, r.pos = bufs[1][:, :self.scenes[sid].n_rows].cpu(), bufs[2][:, :self.scenes[sid].n_rows].cpu()
-                    results.append(r)
+                if sl.busy and self._finished(sl):
+                    sid = sl.busy[1]
+                    results.append(self._retire(sl, t0))
                     self.in_use -= self.scenes[sid].footprint()
                     sl.busy = None
             # admit in arrival order while a slot and memory are free
             while queue:
-                free = [sl for sl in self.slots if sl.busy is None]
                 req, arr, sid = queue[0]
-                if not free or self.in_use + self.scenes[sid].footprint() > self.budget:
+                fp = self.scenes[sid].footprint()
+                if fp > self.budget:  # can never fit: answer now rather than block the queue
+                    queue.popleft()
+                    t = time.perf_counter() - t0
+                    results.append(Result(req, sid, arr, t, t, sgs.E_NOMEM))
+                    continue
+                free = [sl for sl in self.slots if sl.busy is None]
+                if not free or self.in_use + fp > self.budget:
                     break
                 queue.popleft()
+                self.in_use += fp
                 self._launch(free[0], req, sid, arr, time.perf_counter() - t0)
             if not queue and pending:
                 wait = pending[0][1] - (time.perf_counter() - t0)
