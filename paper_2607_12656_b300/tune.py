@@ -49,8 +49,10 @@ class LaneTuner:
             b = r["best"]
             self.table[k] = {"rows_per_lane": r["rows_per_lane"][b], "ms": r["ms"][b], "bytes": r["bytes"][b],
                              "sweep": {str(w): [ms, by] for w, ms, by in zip(r["rows_per_lane"], r["ms"], r["bytes"])}}
-            if self.path:
-                with open(self.path, "w") as f:
+            if self.path:  # written whole, then renamed: a reader never sees half a file
+                tmp = self.path + ".tmp"
+                with open(tmp, "w") as f:
                     json.dump(self.table, f, indent=1, sort_keys=True)
+                os.replace(tmp, self.path)
         w = self.table[k]["rows_per_lane"]
         return max(1, -(-kept // w))
