@@ -825,9 +825,12 @@ def run_reference(args, w):
     from paper_2607_12656_b300.scenegen import fixed_bits, make_scene
     # each step decodes a bounded sample of the workload: a scene of the same recipe (seed,
     # depth, coding, rows per lane) with fewer Gaussians, so that the whole run stays within
-    # about two minutes of host time at the oracle's measured rate (~0.36 M Gaussians/s)
-    budget_s, rate = 120.0, 3.6e5
-    n = int(min(w["n"], max(20_000, budget_s * rate / max(1, args.steps + args.warmup))))
+    # about two minutes of host time at the oracle's measured rate per coding mode (Gaussians/s
+    # on one core: fixed-length 3.3e5, static 1.4e5, learned 1.8e3, position-aware 3.2e3)
+    budget_s = 120.0
+    rate = {0: 3.3e5, 1: 1.4e5, 2: 1.8e3, 3: 3.2e3}[w["mode"]]
+    floor = 20_000 if w["mode"] < 2 else 256
+    n = int(min(w["n"], max(floor, budget_s * rate / max(1, args.steps + args.warmup))))
     frac = n / w["n"]
     sc = make_scene(n, w["seed"])
     kw = dict(mode=w["mode"], depth=w["depth"], geo_mode=w["geo_mode"])
@@ -840,6 +843,23 @@ def run_reference(args, w):
         coded = S.geo_plan(P.levels, w["geo_mode"])
         n_coded = sum(len(P.levels[l]) for l in range(w["depth"]) if coded[l])
         kw["geo_lanes"] = max(32, -(-n_coded // (w["geo_w"] * 32)) * 32)
+    note = ""
+    if w["mode"] in (2, 3):
+        # a model from a short oracle training run: the decode's work per token does not
+        # depend on the weights
+        from paper_2607_12656_b300.scenegen import kaiming_init, kaiming_init_pe
+        q = P.q.astype(np.uint8)
+        lr = S.lane_bounds(P.n_rows, kw["lanes"])
+        if w["mode"] == 2:
+            from oracle import model as M
+            p, _ = M.train(kaiming_init(1), q, lr, 30, 4096, seed=1, lr=3e-3)
+            kw["model"] = M.freeze({k: v.astype(np.float32) for k, v in p.items()}, q, lr, seed=1)
+        else:
+            from oracle import model_pe as E
+            p, _ = E.train(kaiming_init_pe(1), q, lr, P.coord, w["depth"], 30, 4096, seed=1, lr=3e-3)
+            kw["model"] = E.freeze({k: v.astype(np.float32) for k, v in p.items()}, q, lr, P.coord, w["depth"],
+                                   seed=1)
+        note = "; model from 30 oracle training steps of 4,096 tokens"
     buf = S.encode(sc.pos, sc.attr, prep=P, **kw)
     for _ in range(args.warmup):
         S.decode(buf)
@@ -851,7 +871,7 @@ def run_reference(args, w):
     rows = S.parse_header(buf)["n_rows"]
     value = rows * len(times) / sum(times)
     sample = ("one oracle decode per step of a %d-Gaussian scene (%d rows) of the workload's recipe "
-              "(%s), single thread" % (n, rows, "full size" if n == w["n"] else "bounded sample"))
+              "(%s), single thread%s" % (n, rows, "full size" if n == w["n"] else "bounded sample", note))
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": "Gaussians/s",
                       "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
