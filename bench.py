@@ -268,6 +268,51 @@ def geo_lanes_for(sc, w) -> int:
     return max(32, -(-n_coded // per) * 32)
 
 
+SMS = 148  # B300: 2 dies x 74 SMs
+
+
+def attr_roofline(mode: int, n: int, attr_bytes: int, attr_ms: float, pk: dict) -> dict:
+    """Roofline of the attribute decoder of a coded mode over its stage time (CUDA events on the
+    attribute stream).  Algorithmic work per decoded symbol (56 per Gaussian):
+      static rANS: the coded attribute section read once + 4 B written (HBM);
+      learned: the integer softmax and cumulative table, 10 integer operations for each of the
+        256 entries (ALU; peak = 148 SMs x 4 warp instructions x 32 lanes per clock at the
+        maximum SM clock), with the 20,480 tensor-core MACs of layers 2-3 beside it;
+      position-aware: 4 x 64 + 64 x 64 + 2 x 64 MACs per symbol and 75 x 64 per row (tensor)."""
+    sec = attr_ms / 1e3
+    syms = 56 * n
+    bf16 = pk.get("bf16_tflops")
+    bf16_src = "MEASURED_PEAKS.json bf16_tflops (measured, burst)" if bf16 else "fallback 1800"
+    bf16 = bf16 or 1800.0
+    if mode == 1:
+        hbm = pk.get("hbm_gbs")
+        src = "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else "fallback 6400"
+        hbm = hbm or 6400.0
+        alg = attr_bytes + 4 * syms
+        ach = alg / sec / 1e9
+        return {"kernel": "k_rans_attr (static rANS + dequant + SoA store)", "bound": "hbm", "achieved": ach,
+                "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": src, "algorithmic_bytes": alg,
+                "traffic": None, "note": "issue-bound in practice: a dependent integer chain per symbol"}
+    if mode == 2:
+        mhz = pk.get("sm_max_mhz") or 2032.0
+        peak = SMS * 4 * 32 * mhz * 1e6 / 1e9
+        ops = 10 * 256 * syms
+        ach = ops / sec / 1e9
+        tf = 2 * 20480 * syms / sec / 1e12
+        return {"kernel": "k_learned_decode (context MLP + integer softmax + rANS)", "bound": "alu",
+                "achieved": ach, "peak": peak, "unit": "Gop/s", "frac": ach / peak,
+                "peak_source": "derived: 148 SMs x 4 warp instructions x 32 lanes per clock at %.0f MHz" % mhz,
+                "algorithmic_ops": ops, "traffic": None,
+                "tensor": {"achieved": tf, "peak": bf16, "unit": "TFLOP/s", "frac": tf / bf16,
+                           "peak_source": bf16_src}}
+    flops = 2 * (4 * 64 + 64 * 64 + 2 * 64) * syms + 2 * 75 * 64 * n
+    ach = flops / sec / 1e12
+    return {"kernel": "k_learned_pe (position-aware context MLP + Laplace CDF search + rANS)", "bound": "tensor",
+            "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16, "peak_source": bf16_src,
+            "algorithmic_flops": flops, "traffic": None,
+            "note": "latency-bound in practice: dependent mma and requantisation chains per row step"}
+
+
 def fixed_algorithmic_bytes(info, bits_np) -> int:
     n = info.n_rows
     read = sum(4 * ((n * int(b) + 31) // 32) for b in bits_np)
@@ -436,6 +481,10 @@ def run_ours(args, w):
                                    "unit": "GB/s"}
     if w["mode"] != 0:
         line["config"]["attr_bits_per_gaussian"] = 8.0 * (info.total_len - info.off[7]) / n
+        rl = attr_roofline(w["mode"], n, info.total_len - info.off[7], line["stage_ms"]["attributes"], pk)
+        # the learned decoders dominate their decode; static attributes run beside a longer
+        # geometry-token decode, so theirs is reported under its own key
+        line["roofline" if w["mode"] in (2, 3) else "roofline_attributes"] = rl
     if w["mode"] in (2, 3):
         from paper_2607_12656_b300 import learned
         tr = learned.LAST_TRAIN
