@@ -38,3 +38,22 @@ def test_position_aware_tensor(bench):
     assert r["algorithmic_flops"] == 2 * 4480 * 56_000 + 2 * 4800 * 1000
     assert r["unit"] == "TFLOP/s" and r["frac"] == pytest.approx(r["achieved"] / 1800)
     assert bench.attr_roofline(3, 1000, 0, 1.0, {})["peak_source"] == "fallback 1800"
+
+
+def test_reference_arm_line_contract():
+    """bench.py --impl reference prints one JSON line with the contract's keys: the oracle's
+    throughput, its cpu_baseline description and an e2e block with no host-device bytes."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "small",
+                          "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "Gaussians/s" and d["value"] > 0
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "Gaussians/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["n_rows"] == 18_000
