@@ -228,3 +228,17 @@ def test_learned_pe_round_trip(trained_toy):
     assert np.array_equal(d["pos"], P.pos)
     # the model bytes survive a parse
     assert E.model_bytes(E.parse_model(buf, h["off_attr_tab"])) == E.model_bytes(m)
+
+
+def test_sampled_decode_is_the_full_decode_on_its_groups(trained_toy):
+    """decode(attr_groups=k) decodes the rows of the first k groups of 32 lanes exactly as the
+    full decode does and leaves every other row 0."""
+    sc, P, q, lr, p, _ = trained_toy
+    m = E.freeze({k: v.astype(np.float32) for k, v in p.items()}, q, lr, P.coord, 10, seed=3)
+    L = 70
+    buf = S.encode(None, None, mode=S.MODE_LEARNED_PE, depth=10, lanes=L, model=m, prep=P)
+    rows = S.lane_bounds(P.n_rows, L)
+    for k in (0, 1, 3):
+        d = S.decode(buf, attr_groups=k)
+        cut = int(rows[min(L, 32 * k)])
+        assert np.array_equal(d["q"][:cut], P.q[:cut]) and not d["q"][cut:].any()
