@@ -53,6 +53,11 @@ extern "C" {
                                  and a conditional Laplace head (Sec. 3.2)                  */
 #define SGS_GEO_RAW 0         /* occupancy tokens stored as bytes                         */
 #define SGS_GEO_RANS 1        /* levels of >= 4096 nodes coded with per-level rANS tables */
+#define SGS_GEO_LEARNED 2     /* levels of >= 4096 nodes coded with a learned model of the
+                                 level above (Eq. 8): context = (parent byte, child index),
+                                 the SGS_MODEL_BYTES integer model with the level as its
+                                 channel.  scene_encode writes it; decoding it is not built
+                                 (scene_query answers SGS_E_UNSUPPORTED)                   */
 
 #define SGS_NCHAN 56
 #define SGS_MAX_DEPTH 21
@@ -100,6 +105,10 @@ typedef struct {
     uint32_t bits[SGS_NCHAN]; /* fixed-length bit widths 1..16 (8 is forced for rANS modes)*/
     const void *model;        /* learned modes: the frozen model (SGS_MODEL_BYTES, or
                                  SGS_MODEL_PE_BYTES for SGS_MODE_LEARNED_PE), else NULL    */
+    const void *geo_model;    /* SGS_GEO_LEARNED: the geometry model (SGS_MODEL_BYTES; its
+                                 inputs u = (b - 128, 32 k - 112, 16 popcount(b) - 64,
+                                 32 rank - 112) of parent byte b and child index k, rank =
+                                 set bits of b below k; channel = level), else NULL        */
 } sgs_encode_params;
 
 #define SGS_MODEL_BYTES 36384

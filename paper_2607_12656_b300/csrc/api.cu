@@ -232,7 +232,9 @@ extern "C" int scene_query(const uint8_t *b, size_t len, sgs_scene_info *info) {
     info->n_geo_coded = rd64(b + 56);
     for (int i = 0; i < 11; ++i) info->off[i] = rd64(b + 64 + 8 * i);
     info->total_len = info->off[S_TOTAL];
-    if (n_chan != (uint32_t)kNChan || info->mode > SGS_MODE_LEARNED_PE || info->geo_mode > 1) return SGS_E_INVALID;
+    if (n_chan != (uint32_t)kNChan || info->mode > SGS_MODE_LEARNED_PE || info->geo_mode > SGS_GEO_LEARNED)
+        return SGS_E_INVALID;
+    if (info->geo_mode == SGS_GEO_LEARNED) return SGS_E_UNSUPPORTED;  // no device decoder for it
     if (info->depth < 1 || info->depth > SGS_MAX_DEPTH) return SGS_E_INVALID;
     if (info->total_len != len) return SGS_E_INVALID;
     if (info->off[0] != (uint64_t)kHeaderBytes) return SGS_E_INVALID;

@@ -17,6 +17,7 @@
 #include <numeric>
 #include <vector>
 
+#include "exp2q_table.h"
 #include "sgs_ctx.h"
 #include "sgs_internal.h"
 
@@ -306,6 +307,104 @@ uint32_t default_geo_lanes(uint64_t n) {
     return (uint32_t)std::max<uint64_t>(32, (n + per - 1) / per * 32);
 }
 
+// ---- the learned model's integer frequencies on the host (for the learned geometry coder)
+//
+// Frozen model blob (SGS_MODEL_BYTES, little endian): i32 m1, sh1, m2, sh2, ms, ss, then 8
+// zero bytes; i32 B1[56][64]; i32 b2[64]; i32 b3[256]; i8 W1[64][4]; i8 W2[64][64];
+// i8 W3[256][64].  Inference: acc1 = W1 u + B1[c], h1 = rq(acc1; m1, sh1), acc2 = W2 h1 + b2,
+// h2 = rq(acc2; m2, sh2), z = W3 h2 + b3, rq(a; m, sh) = clamp((a m + 2^(sh-1)) >> sh, 0, 127)
+// in 64-bit arithmetic; then the integer softmax: d_k = zmax - z_k, t_k = min((d_k ms) >> ss,
+// 6144), e_k = EXP2Q[t_k & 255] >> (t_k >> 8), R = floor(65280 2^32 / sum e), f_k = 1 +
+// floor(e_k R / 2^32), and the remainder 2^16 - sum f added at the lowest index of max z.
+constexpr size_t kMB1 = 32, kMb2 = 14368, kMb3 = 14624, kMW1 = 15648, kMW2 = 15904, kMW3 = 20000;
+constexpr uint32_t kExp2QTab[256] = {SGS_EXP2Q_VALUES};
+static_assert(kMW3 + 256 * 64 == SGS_MODEL_BYTES, "model layout");
+
+int32_t rdi(const uint8_t *m, size_t off) {
+    int32_t v;
+    memcpy(&v, m + off, 4);
+    return v;
+}
+
+struct HostModel {
+    const uint8_t *m = nullptr;
+    int32_t m1 = 0, sh1 = 0, m2 = 0, sh2 = 0;
+    uint32_t ms = 0, ss = 0;
+};
+
+// Reads the header scalars and checks the ranges every decoder relies on (shifts, multipliers,
+// biases below 2^24 in magnitude).
+bool host_model(const uint8_t *m, HostModel &H) {
+    if (!m) return false;
+    H.m = m;
+    H.m1 = rdi(m, 0); H.sh1 = rdi(m, 4); H.m2 = rdi(m, 8); H.sh2 = rdi(m, 12);
+    H.ms = (uint32_t)rdi(m, 16); H.ss = (uint32_t)rdi(m, 20);
+    if (!(H.sh1 >= 1 && H.sh1 <= 47 && H.sh2 >= 1 && H.sh2 <= 47 && H.m1 >= 0 && H.m2 >= 0 && H.ms >= 1 &&
+          H.ms < (1u << 24) && H.ss <= 24))
+        return false;
+    auto ok = [&](size_t off, int n) {
+        for (int i = 0; i < n; ++i) {
+            const int32_t v = rdi(m, off + 4 * (size_t)i);
+            if (v >= (1 << 24) || v <= -(1 << 24)) return false;
+        }
+        return true;
+    };
+    return ok(kMB1, kNChan * 64) && ok(kMb2, 64) && ok(kMb3, 256);
+}
+
+int64_t requant_host(int64_t a, int32_t m, int32_t sh) {
+    const int64_t v = (a * (int64_t)m + ((int64_t)1 << (sh - 1))) >> sh;
+    return v < 0 ? 0 : (v > 127 ? 127 : v);
+}
+
+void learned_freq_host(const HostModel &H, const int32_t u[4], int c, uint32_t *f) {
+    const int8_t *W1 = reinterpret_cast<const int8_t *>(H.m + kMW1);
+    const int8_t *W2 = reinterpret_cast<const int8_t *>(H.m + kMW2);
+    const int8_t *W3 = reinterpret_cast<const int8_t *>(H.m + kMW3);
+    int64_t h1[64], h2[64];
+    for (int o = 0; o < 64; ++o) {
+        int64_t a = rdi(H.m, kMB1 + 4 * ((size_t)c * 64 + o));
+        for (int j = 0; j < 4; ++j) a += (int64_t)W1[4 * o + j] * u[j];
+        h1[o] = requant_host(a, H.m1, H.sh1);
+    }
+    for (int o = 0; o < 64; ++o) {
+        int64_t a = rdi(H.m, kMb2 + 4 * (size_t)o);
+        for (int k = 0; k < 64; ++k) a += (int64_t)W2[64 * o + k] * h1[k];
+        h2[o] = requant_host(a, H.m2, H.sh2);
+    }
+    int64_t z[kNSym];
+    int amax = 0;
+    for (int s = 0; s < kNSym; ++s) {
+        int64_t a = rdi(H.m, kMb3 + 4 * (size_t)s);
+        for (int k = 0; k < 64; ++k) a += (int64_t)W3[64 * s + k] * h2[k];
+        z[s] = a;
+        if (a > z[amax]) amax = s;
+    }
+    uint64_t e[kNSym], E = 0;
+    for (int s = 0; s < kNSym; ++s) {
+        const uint64_t t = std::min<uint64_t>(((uint64_t)(z[amax] - z[s]) * H.ms) >> H.ss, 6144);
+        e[s] = kExp2QTab[t & 255] >> (t >> 8);
+        E += e[s];
+    }
+    const uint64_t R = (65280ull << 32) / E;
+    uint32_t sum = 0;
+    for (int s = 0; s < kNSym; ++s) {
+        f[s] = 1u + (uint32_t)((e[s] * R) >> 32);
+        sum += f[s];
+    }
+    f[amax] += kM - sum;
+}
+
+// Learned geometry (SGS_GEO_LEARNED): level l's nodes, in order, are the set bits k (ascending)
+// of each byte b of level l - 1; node context 8 b + k; the model's inputs of a context.
+void geo_inputs(uint32_t ctx, int32_t u[4]) {
+    const uint32_t b = ctx >> 3, k = ctx & 7;
+    u[0] = (int32_t)b - 128;
+    u[1] = 32 * (int32_t)k - 112;
+    u[2] = 16 * __builtin_popcount(b) - 64;
+    u[3] = 32 * __builtin_popcount(b & ((1u << k) - 1u)) - 112;
+}
+
 }  // namespace
 
 // Interleaved rANS coding of the attribute streams on the device (k_encode.cu; the learned
@@ -359,7 +458,7 @@ extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, u
                             const sgs_encode_params *prm, uint8_t *out, size_t cap,
                             size_t *out_len) {
     if (!prm || !out_len || (n && (!pos || !attr))) return SGS_E_INVALID;
-    if (prm->mode > SGS_MODE_LEARNED_PE || prm->geo_mode > 1) return SGS_E_INVALID;
+    if (prm->mode > SGS_MODE_LEARNED_PE || prm->geo_mode > SGS_GEO_LEARNED) return SGS_E_INVALID;
     uint32_t bits[kNChan];
     for (int c = 0; c < kNChan; ++c) bits[c] = prm->mode == SGS_MODE_FIXED ? prm->bits[c] : 8u;
     if (prm->mode != SGS_MODE_FIXED && prm->lanes < 1) return SGS_E_INVALID;
@@ -379,7 +478,7 @@ extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, u
         const uint32_t nl = (uint32_t)P.levels[l].size();
         put<uint32_t>(s_levels, nl);
         n_geo += nl;
-        if (prm->geo_mode == SGS_GEO_RANS && nl >= kGeoRansMinLevel) {
+        if (prm->geo_mode != SGS_GEO_RAW && nl >= kGeoRansMinLevel) {
             coded_levels.push_back((int)l);
             n_coded += nl;
         } else {
@@ -387,7 +486,50 @@ extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, u
         }
     }
     uint32_t Lg = 0;
-    if (n_coded) {
+    if (n_coded && prm->geo_mode == SGS_GEO_LEARNED) {
+        // one model for every coded level (the geometry table section); each level's tokens
+        // in lanes of contiguous chunks, about 128 tokens per lane, coded with the frequency
+        // tables of their contexts; the levels' group tables follow one another and point
+        // into one payload
+        HostModel H;
+        if (!host_model(static_cast<const uint8_t *>(prm->geo_model), H)) return SGS_E_INVALID;
+        const uint8_t *gm = static_cast<const uint8_t *>(prm->geo_model);
+        s_gtab.assign(gm, gm + SGS_MODEL_BYTES);
+        std::vector<uint32_t> F((size_t)2048 * kNSym), C((size_t)2048 * kNSym);
+        for (int l : coded_levels) {
+            const std::vector<uint8_t> &par = P.levels[l - 1], &cur = P.levels[l];
+            std::vector<uint16_t> ctx;
+            ctx.reserve(cur.size());
+            for (uint8_t b : par)
+                for (uint32_t k = 0; k < 8; ++k)
+                    if ((b >> k) & 1u) ctx.push_back((uint16_t)(8u * b + k));
+            if (ctx.size() != cur.size()) return SGS_E_INVALID;
+            std::vector<uint8_t> present(2048, 0);
+            for (uint16_t x : ctx) present[x] = 1;
+            std::vector<int> ids;
+            for (int x = 0; x < 2048; ++x)
+                if (present[x]) ids.push_back(x);
+#pragma omp parallel for schedule(dynamic, 8)
+            for (int64_t i = 0; i < (int64_t)ids.size(); ++i) {
+                int32_t u[4];
+                geo_inputs((uint32_t)ids[i], u);
+                uint32_t *f = &F[(size_t)ids[i] * kNSym], *cu = &C[(size_t)ids[i] * kNSym];
+                learned_freq_host(H, u, l, f);
+                uint32_t acc = 0;
+                for (int s2 = 0; s2 < kNSym; ++s2) { cu[s2] = acc; acc += f[s2]; }
+            }
+            std::vector<uint32_t> tf(cur.size()), tcu(cur.size());
+            for (size_t p = 0; p < cur.size(); ++p) {
+                tf[p] = F[(size_t)ctx[p] * kNSym + cur[p]];
+                tcu[p] = C[(size_t)ctx[p] * kNSym + cur[p]];
+            }
+            const uint32_t Ll = default_geo_lanes(cur.size());
+            Lg += Ll;
+            std::vector<uint8_t> grp;
+            rans_encode(lane_bounds(cur.size(), Ll, 1), tf.data(), tcu.data(), grp, s_gpay);
+            s_ggrp.insert(s_ggrp.end(), grp.begin(), grp.end());
+        }
+    } else if (n_coded) {
         Lg = prm->geo_lanes ? prm->geo_lanes : default_geo_lanes(n_coded);
         std::vector<uint32_t> tf(n_coded), tcu(n_coded);  // in token order
         uint64_t p = 0;

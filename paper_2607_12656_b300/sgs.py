@@ -13,7 +13,7 @@ from . import build as _build
 
 OK, E_INVALID, E_CORRUPT, E_NOMEM, E_CUDA, E_TIMEOUT, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 MODE_FIXED, MODE_STATIC, MODE_LEARNED, MODE_LEARNED_PE = 0, 1, 2, 3
-GEO_RAW, GEO_RANS = 0, 1
+GEO_RAW, GEO_RANS, GEO_LEARNED = 0, 1, 2
 NCHAN = 56
 MAX_DEPTH = 21
 MODEL_BYTES = 36384
@@ -38,7 +38,7 @@ class SceneOut(ctypes.Structure):
 
 class EncodeParams(ctypes.Structure):
     _fields_ = [("mode", u32), ("geo_mode", u32), ("depth", u32), ("lanes", u32), ("geo_lanes", u32),
-                ("bits", u32 * NCHAN), ("model", P)]
+                ("bits", u32 * NCHAN), ("model", P), ("geo_model", P)]
 
 
 class TrainParams(ctypes.Structure):
@@ -314,7 +314,7 @@ class BatchPlan:
 
 def scene_encode(pos: np.ndarray, attr: np.ndarray, *, mode: int, depth: int, lanes: int = 32,
                  geo_mode: int = GEO_RANS, geo_lanes: int = 0, bits=8, model: bytes | None = None,
-                 ctx: Context | None = None) -> bytes:
+                 ctx: Context | None = None, geo_model: bytes | None = None) -> bytes:
     pos = np.ascontiguousarray(pos, np.float32)
     attr = np.ascontiguousarray(attr, np.float32)
     n = pos.shape[1]
@@ -329,6 +329,11 @@ def scene_encode(pos: np.ndarray, attr: np.ndarray, *, mode: int, depth: int, la
         mbuf = np.frombuffer(bytes(model), np.uint8).copy()
         assert mbuf.size == (MODEL_PE_BYTES if mode == MODE_LEARNED_PE else MODEL_BYTES)
         prm.model = mbuf.ctypes.data
+    gbuf = None
+    if geo_model is not None:
+        gbuf = np.frombuffer(bytes(geo_model), np.uint8).copy()
+        assert gbuf.size == MODEL_BYTES
+        prm.geo_model = gbuf.ctypes.data
     need = ctypes.c_size_t(0)
     h = ctx.handle if ctx is not None else None
     # one pass in the common case: room for 2 bytes per token plus tables and headers

@@ -1,6 +1,7 @@
 """Pins of the oracle's learned geometry coder (Sec. 3.4, "Geometry Occupancy Coding": each
 octree level is coded conditioned on the level above it, Eq. 8): context derivation, the
-explicit-sample trainer and freeze, the coding round trip and the conditional-entropy bound."""
+explicit-sample trainer and freeze, the coding round trip and the conditional-entropy bound;
+and the library's host encoder for the same coder against the oracle's bytes."""
 import numpy as np
 import pytest
 
@@ -118,3 +119,49 @@ def test_trained_model_codes_above_the_conditional_entropy(geo_scene):
     assert bound < pay_l < 1.25 * bound, (bound, pay_l, pay_s)
     d = S.decode(learned)
     assert np.array_equal(d["attr"], P.attr) and np.array_equal(d["coord"], P.coord)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_library_encoder_bytes_equal_oracle(geo_scene, seed):
+    """The library's host encoder writes the oracle's bytes for learned geometry (any valid
+    integer model; fixed-length and static attributes), and scene_query refuses the stream,
+    whose device decoder is not built."""
+    from paper_2607_12656_b300 import sgs
+    from paper_2607_12656_b300.scenegen import fixed_bits
+    sc, P = geo_scene
+    m = _random_model(seed)
+    want = S.encode(None, None, mode=S.MODE_STATIC, depth=12, lanes=40, prep=P, geo_mode=S.GEO_LEARNED, geo_model=m)
+    got = sgs.scene_encode(sc.pos, sc.attr, mode=sgs.MODE_STATIC, depth=12, lanes=40, geo_mode=sgs.GEO_LEARNED,
+                           geo_model=S.model_bytes(m))
+    assert got == want
+    Pf = S.prepare(sc.pos, sc.attr, 12, fixed_bits(2))
+    want = S.encode(None, None, mode=S.MODE_FIXED, depth=12, bits=fixed_bits(2), prep=Pf, geo_mode=S.GEO_LEARNED,
+                    geo_model=m)
+    got = sgs.scene_encode(sc.pos, sc.attr, mode=sgs.MODE_FIXED, depth=12, bits=fixed_bits(2),
+                           geo_mode=sgs.GEO_LEARNED, geo_model=S.model_bytes(m))
+    assert got == want
+    with pytest.raises(sgs.SgsError) as e:
+        sgs.scene_query(got)
+    assert e.value.code == sgs.E_UNSUPPORTED
+
+
+def test_library_encoder_trained_geometry_model(geo_scene):
+    """A geometry model trained and frozen by the oracle: the library's bytes equal the
+    oracle's; a missing or invalid model is refused."""
+    from paper_2607_12656_b300 import sgs
+    from paper_2607_12656_b300.scenegen import kaiming_init
+    sc, P = geo_scene
+    U, C, Sy = S.geo_samples(P.levels)
+    p, _ = M.train_ctx(kaiming_init(2), U, C, Sy, 40, 2048, seed=4, lr=3e-3)
+    m = M.freeze_ctx({k: v.astype(np.float32) for k, v in p.items()}, U, C, seed=4)
+    want = S.encode(None, None, mode=S.MODE_STATIC, depth=12, lanes=40, prep=P, geo_mode=S.GEO_LEARNED, geo_model=m)
+    got = sgs.scene_encode(sc.pos, sc.attr, mode=sgs.MODE_STATIC, depth=12, lanes=40, geo_mode=sgs.GEO_LEARNED,
+                           geo_model=S.model_bytes(m))
+    assert got == want
+    with pytest.raises(sgs.SgsError):
+        sgs.scene_encode(sc.pos, sc.attr, mode=sgs.MODE_STATIC, depth=12, lanes=40, geo_mode=sgs.GEO_LEARNED)
+    bad = bytearray(S.model_bytes(m))
+    bad[4:8] = (0).to_bytes(4, "little")  # sh1 = 0 is outside the model's range
+    with pytest.raises(sgs.SgsError):
+        sgs.scene_encode(sc.pos, sc.attr, mode=sgs.MODE_STATIC, depth=12, lanes=40, geo_mode=sgs.GEO_LEARNED,
+                         geo_model=bytes(bad))
