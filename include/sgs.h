@@ -393,6 +393,15 @@ int sgs_train_grad(sgs_ctx *ctx, const uint8_t *tokens_dev, uint32_t n_rows, uin
 int sgs_freeze(const float *weights, const uint8_t *tokens, uint32_t n_rows, uint32_t lanes,
                uint32_t seed, uint8_t *model_out);
 
+/* As sgs_freeze, for a model whose contexts are an explicit sample set rather than the
+ * previous tokens of a row (the learned geometry coder's (parent byte, child index) inputs,
+ * SGS_GEO_LEARNED): u host int32 [n][4] in [-128, 127], chan host uint32 [n] below
+ * SGS_NCHAN; calibration sample k is entry sample_pos(seed, 2^20 - 1, k, n) of the set, with
+ * the trainer's counter-based sampler.  Writes SGS_MODEL_BYTES.  Errors: SGS_E_INVALID
+ * (missing arrays, n = 0, non-finite weights, inputs out of range).                        */
+int sgs_freeze_samples(const float *weights, const int32_t *u, const uint32_t *chan, uint64_t n,
+                       uint32_t seed, uint8_t *model_out);
+
 /* The position-aware model (SGS_MODE_LEARNED_PE; float layout SGS_WEIGHTS_PE_FLOATS): as
  * sgs_train / sgs_train_grad / sgs_freeze with the rows' voxel coordinates (coord_dev device,
  * coord host: uint32 [3][n_rows], from scene_rows) at octree depth `depth`.  Loss = code

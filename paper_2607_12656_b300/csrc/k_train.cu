@@ -373,13 +373,17 @@ static int32_t rq_host(int32_t acc, int32_t m, int32_t sh) {
 
 using namespace sgs;
 
-extern "C" int sgs_freeze(const float *w, const uint8_t *tok, uint32_t n_rows, uint32_t lanes,
-                          uint32_t seed, uint8_t *out) {
-    if (!w || !out || !tok || n_rows == 0 || lanes == 0) return SGS_E_INVALID;
+namespace sgs {
+namespace {
+
+// The freeze's arithmetic (fp64, fixed operation order): per-tensor int8 weights, the channel
+// embedding folded into the layer-1 bias, requantisation multipliers from the layer maxima
+// over the n_cal calibration contexts (u [n_cal][4], channel cc [n_cal]), biases at the
+// layers' scales, the softmax multiplier; then the model blob.
+void freeze_common(const float *w, const std::vector<int32_t> &u, const std::vector<int> &cc, uint8_t *out) {
     const float *emb = w + kW_EMB, *W1 = w + kW_W1, *b1 = w + kW_B1, *W2 = w + kW_W2, *b2 = w + kW_B2,
                 *W3 = w + kW_W3, *b3 = w + kW_B3;
-    for (int i = 0; i < kW_TOTAL; ++i)
-        if (!isfinite(w[i])) return SGS_E_INVALID;
+    const int n_cal = (int)cc.size();
     const double s_u = 1.0 / 128.0;
     std::vector<int8_t> w1q, w2q, w3q;
     double s_w1, s_w2, s_w3;
@@ -394,20 +398,6 @@ extern "C" int sgs_freeze(const float *w, const uint8_t *tok, uint32_t n_rows, u
         }
     q8(W2, 64, 64, 64, w2q, s_w2);
     q8(W3, 256, 64, 64, w3q, s_w3);
-    // integer calibration over 65,536 tokens drawn at step 2^20 - 1
-    const uint64_t n_total = (uint64_t)n_rows * kNChan;
-    const int n_cal = 65536;
-    std::vector<int32_t> u(4 * n_cal);
-    std::vector<int> cc(n_cal);
-    for (int k = 0; k < n_cal; ++k) {
-        const uint64_t pos = sample_pos(seed, (1u << 20) - 1, (uint32_t)k, n_total);
-        const uint64_t row = pos / kNChan;
-        const int c = (int)(pos % kNChan);
-        const uint64_t row0 = lane_row0(row, n_rows, lanes);
-        cc[k] = c;
-        for (int q = 1; q <= 4; ++q)
-            u[4 * k + q - 1] = (row >= row0 + q) ? (int32_t)tok[(row - q) * kNChan + c] - 128 : 0;
-    }
     auto acc1 = [&](int k, int o) {
         int32_t a = B1[cc[k] * 64 + o];
         for (int j = 0; j < 4; ++j) a += (int32_t)w1q[o * 4 + j] * u[4 * k + j];
@@ -450,6 +440,58 @@ extern "C" int sgs_freeze(const float *w, const uint8_t *tok, uint32_t n_rows, u
     memcpy(out + 15648, w1q.data(), 256);
     memcpy(out + 15904, w2q.data(), 4096);
     memcpy(out + 20000, w3q.data(), 16384);
+}
+
+bool weights_finite(const float *w) {
+    for (int i = 0; i < kW_TOTAL; ++i)
+        if (!isfinite(w[i])) return false;
+    return true;
+}
+
+}  // namespace
+}  // namespace sgs
+
+extern "C" int sgs_freeze(const float *w, const uint8_t *tok, uint32_t n_rows, uint32_t lanes,
+                          uint32_t seed, uint8_t *out) {
+    if (!w || !out || !tok || n_rows == 0 || lanes == 0) return SGS_E_INVALID;
+    if (!weights_finite(w)) return SGS_E_INVALID;
+    // integer calibration over 65,536 tokens drawn at step 2^20 - 1
+    const uint64_t n_total = (uint64_t)n_rows * kNChan;
+    const int n_cal = 65536;
+    std::vector<int32_t> u(4 * n_cal);
+    std::vector<int> cc(n_cal);
+    for (int k = 0; k < n_cal; ++k) {
+        const uint64_t pos = sample_pos(seed, (1u << 20) - 1, (uint32_t)k, n_total);
+        const uint64_t row = pos / kNChan;
+        const int c = (int)(pos % kNChan);
+        const uint64_t row0 = lane_row0(row, n_rows, lanes);
+        cc[k] = c;
+        for (int q = 1; q <= 4; ++q)
+            u[4 * k + q - 1] = (row >= row0 + q) ? (int32_t)tok[(row - q) * kNChan + c] - 128 : 0;
+    }
+    freeze_common(w, u, cc, out);
+    return SGS_OK;
+}
+
+extern "C" int sgs_freeze_samples(const float *w, const int32_t *u_in, const uint32_t *chan, uint64_t n,
+                                  uint32_t seed, uint8_t *out) {
+    if (!w || !out || !u_in || !chan || n == 0) return SGS_E_INVALID;
+    if (!weights_finite(w)) return SGS_E_INVALID;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (chan[i] >= (uint32_t)kNChan) return SGS_E_INVALID;
+        for (int j = 0; j < 4; ++j)
+            if (u_in[4 * i + j] < -128 || u_in[4 * i + j] > 127) return SGS_E_INVALID;
+    }
+    // calibration sample k = entry sample_pos(seed, 2^20 - 1, k, n) of the set
+    const int n_cal = 65536;
+    std::vector<int32_t> u(4 * n_cal);
+    std::vector<int> cc(n_cal);
+    for (int k = 0; k < n_cal; ++k) {
+        const uint64_t i = sample_pos(seed, (1u << 20) - 1, (uint32_t)k, n);
+        cc[k] = (int)chan[i];
+        for (int j = 0; j < 4; ++j) u[4 * k + j] = u_in[4 * i + j];
+    }
+    freeze_common(w, u, cc, out);
     return SGS_OK;
 }
 

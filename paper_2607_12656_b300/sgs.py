@@ -116,6 +116,7 @@ def lib() -> ctypes.CDLL:
         L.sgs_train.argtypes = [P, P, u32, u32, ctypes.POINTER(TrainParams), u32, P, P, P]
         L.sgs_train_grad.argtypes = [P, P, u32, u32, P, u32, P, P, ctypes.POINTER(ctypes.c_float)]
         L.sgs_freeze.argtypes = [P, P, u32, u32, u32, P]
+        L.sgs_freeze_samples.argtypes = [P, P, P, u64, u32, P]
         L.sgs_profile.argtypes = [P, i32]
         L.sgs_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_float), i32]
         L.sgs_launch_count.argtypes = [P]
@@ -429,6 +430,20 @@ def sgs_freeze(weights: np.ndarray, tokens: np.ndarray, lanes: int, seed: int) -
     out = np.zeros(MODEL_BYTES, np.uint8)
     _check(lib().sgs_freeze(w.ctypes.data, t.ctypes.data, t.shape[0], lanes, seed, out.ctypes.data),
            "sgs_freeze")
+    return out.tobytes()
+
+
+def sgs_freeze_samples(weights: np.ndarray, u: np.ndarray, chan: np.ndarray, seed: int) -> bytes:
+    """Frozen integer model (SGS_MODEL_BYTES) from fp32 weights and an explicit sample set of
+    contexts u [n, 4] (int, in [-128, 127]) and channels chan [n]."""
+    w = np.ascontiguousarray(weights, np.float32)
+    assert w.size == WEIGHTS_FLOATS
+    uu = np.ascontiguousarray(u, np.int32)
+    cc = np.ascontiguousarray(chan, np.uint32)
+    assert uu.ndim == 2 and uu.shape[1] == 4 and cc.shape == (uu.shape[0],)
+    out = np.zeros(MODEL_BYTES, np.uint8)
+    _check(lib().sgs_freeze_samples(w.ctypes.data, uu.ctypes.data, cc.ctypes.data, cc.size, seed, out.ctypes.data),
+           "sgs_freeze_samples")
     return out.tobytes()
 
 

@@ -165,3 +165,22 @@ def test_library_encoder_trained_geometry_model(geo_scene):
     with pytest.raises(sgs.SgsError):
         sgs.scene_encode(sc.pos, sc.attr, mode=sgs.MODE_STATIC, depth=12, lanes=40, geo_mode=sgs.GEO_LEARNED,
                          geo_model=bytes(bad))
+
+
+def test_library_freeze_over_samples_equals_oracle(geo_scene):
+    """sgs_freeze_samples writes the oracle's freeze_ctx model byte for byte (same weights,
+    samples and seed); it refuses inputs out of range."""
+    from paper_2607_12656_b300 import sgs
+    from paper_2607_12656_b300.scenegen import kaiming_init
+    sc, P = geo_scene
+    U, C, Sy = S.geo_samples(P.levels)
+    p, _ = M.train_ctx(kaiming_init(3), U, C, Sy, 20, 2048, seed=6, lr=3e-3)
+    w = {k: v.astype(np.float32) for k, v in p.items()}
+    for seed in (6, 9):
+        want = S.model_bytes(M.freeze_ctx(w, U, C, seed=seed))
+        got = sgs.sgs_freeze_samples(sgs.pack_weights(w), U, C, seed)
+        assert got == want
+    with pytest.raises(sgs.SgsError):
+        sgs.sgs_freeze_samples(sgs.pack_weights(w), U + 200, C, 6)
+    with pytest.raises(sgs.SgsError):
+        sgs.sgs_freeze_samples(sgs.pack_weights(w), U, C + 56, 6)
