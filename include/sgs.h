@@ -182,7 +182,8 @@ uint64_t sgs_launch_count(sgs_ctx *ctx);
 /* Parses and validates the header of a bitstream (host bytes `bits`, `len` bytes, at least
  * the header and the level table; the section offsets are checked against total_len).
  * Definition of the fields: Sec. 3.4 split into geometry and attribute streams.
- * Errors: SGS_E_INVALID (short buffer, bad magic/version/sizes/offsets).                   */
+ * Errors: SGS_E_INVALID (short buffer, bad magic/version/sizes/offsets), SGS_E_UNSUPPORTED
+ * (geometry coded with SGS_GEO_LEARNED, which no device decoder reads yet).                */
 int scene_query(const uint8_t *bits, size_t len, sgs_scene_info *info);
 
 /* Decodes one scene: occupancy tokens -> octree expansion (Sec. 3.4, Geometry Occupancy
