@@ -300,6 +300,14 @@ int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, uint32_t n,
 int scene_tokens(const float *pos, const float *attr, uint32_t n, uint32_t depth,
                  uint8_t *tokens, size_t cap, uint32_t *n_rows);
 
+/* Training samples of the learned geometry coder (SGS_GEO_LEARNED): for every node of each
+ * level of >= 4096 nodes (levels 1..depth-1, in order, nodes in order), its context inputs
+ * u [4] (of its parent byte b and child index k, as sgs_encode_params.geo_model), its level
+ * as the channel and its occupancy byte as the symbol: host int32 u [cap][4], uint32
+ * chan [cap], uint8 sym [cap]; *n_samples set; SGS_E_INVALID if cap is too small.          */
+int scene_geo_samples(const float *pos, const float *attr, uint32_t n, uint32_t depth, int32_t *u,
+                      uint32_t *chan, uint8_t *sym, uint64_t cap, uint64_t *n_samples);
+
 /* As scene_tokens, plus the rows' voxel coordinates (host uint32 [3][n_rows], the decoder's
  * coord output), the inputs of the position-aware model's training and freeze.  cap: rows
  * the caller's arrays hold.                                                                  */

@@ -454,6 +454,38 @@ extern "C" int scene_rows(const float *pos, const float *attr, uint32_t n, uint3
     return SGS_OK;
 }
 
+extern "C" int scene_geo_samples(const float *pos, const float *attr, uint32_t n, uint32_t depth, int32_t *u,
+                                 uint32_t *chan, uint8_t *sym, uint64_t cap, uint64_t *n_samples) {
+    if (!pos || !attr || !n_samples) return SGS_E_INVALID;
+    uint32_t bits[kNChan];
+    for (int c = 0; c < kNChan; ++c) bits[c] = 8;
+    Prepared P;
+    int r = prepare(pos, attr, n, depth, bits, P);
+    if (r) return r;
+    uint64_t total = 0;
+    for (uint32_t l = 1; l < depth; ++l)
+        if (P.levels[l].size() >= kGeoRansMinLevel) total += P.levels[l].size();
+    *n_samples = total;
+    if (cap < total || ((!u || !chan || !sym) && total)) return SGS_E_INVALID;
+    uint64_t k = 0;
+    for (uint32_t l = 1; l < depth; ++l) {
+        if (P.levels[l].size() < kGeoRansMinLevel) continue;
+        uint64_t j = 0;
+        for (uint8_t b : P.levels[l - 1])
+            for (uint32_t kk = 0; kk < 8; ++kk)
+                if ((b >> kk) & 1u) {
+                    if (j >= P.levels[l].size()) return SGS_E_INVALID;
+                    geo_inputs(8u * b + kk, u + 4 * (k + j));
+                    chan[k + j] = l;
+                    sym[k + j] = P.levels[l][j];
+                    ++j;
+                }
+        if (j != P.levels[l].size()) return SGS_E_INVALID;
+        k += j;
+    }
+    return SGS_OK;
+}
+
 extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, uint32_t n,
                             const sgs_encode_params *prm, uint8_t *out, size_t cap,
                             size_t *out_len) {

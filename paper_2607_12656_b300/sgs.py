@@ -109,6 +109,7 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(ctypes.c_size_t)]
         L.scene_tokens.argtypes = [P, P, u32, u32, P, ctypes.c_size_t, ctypes.POINTER(u32)]
         L.scene_rows.argtypes = [P, P, u32, u32, P, P, u32, ctypes.POINTER(u32)]
+        L.scene_geo_samples.argtypes = [P, P, u32, u32, P, P, P, u64, ctypes.POINTER(u64)]
         L.sgs_render.argtypes = [P, P, P, u32, ctypes.POINTER(Camera), P, P]
         L.sgs_train_pe.argtypes = [P, P, P, u32, u32, u32, ctypes.POINTER(TrainParams), u32, P, P, P]
         L.sgs_train_pe_grad.argtypes = [P, P, P, u32, u32, u32, P, u32, P, P, ctypes.POINTER(ctypes.c_float)]
@@ -360,6 +361,26 @@ def scene_tokens(pos: np.ndarray, attr: np.ndarray, depth: int) -> np.ndarray:
     _check(lib().scene_tokens(pos.ctypes.data, attr.ctypes.data, n, depth, tok.ctypes.data, tok.size,
                               ctypes.byref(nr)), "scene_tokens")
     return tok[: nr.value].copy()
+
+
+def scene_geo_samples(pos: np.ndarray, attr: np.ndarray, depth: int):
+    """The learned geometry coder's training samples: (u int32 [n, 4], chan uint32 [n],
+    sym uint8 [n]) over the nodes of every coded octree level."""
+    pos = np.ascontiguousarray(pos, np.float32)
+    attr = np.ascontiguousarray(attr, np.float32)
+    n = pos.shape[1]
+    need = u64(0)
+    code = lib().scene_geo_samples(pos.ctypes.data, attr.ctypes.data, n, depth, None, None, None, 0,
+                                   ctypes.byref(need))
+    if code != OK and not (code == E_INVALID and need.value > 0):
+        _check(code, "scene_geo_samples")
+    k = need.value
+    uu = np.zeros((max(k, 1), 4), np.int32)
+    cc = np.zeros(max(k, 1), np.uint32)
+    ss = np.zeros(max(k, 1), np.uint8)
+    _check(lib().scene_geo_samples(pos.ctypes.data, attr.ctypes.data, n, depth, uu.ctypes.data, cc.ctypes.data,
+                                   ss.ctypes.data, k, ctypes.byref(need)), "scene_geo_samples")
+    return uu[:k], cc[:k], ss[:k]
 
 
 def scene_rows(pos: np.ndarray, attr: np.ndarray, depth: int):

@@ -184,3 +184,17 @@ def test_library_freeze_over_samples_equals_oracle(geo_scene):
         sgs.sgs_freeze_samples(sgs.pack_weights(w), U + 200, C, 6)
     with pytest.raises(sgs.SgsError):
         sgs.sgs_freeze_samples(sgs.pack_weights(w), U, C + 56, 6)
+
+
+def test_library_geometry_samples_equal_oracle(geo_scene):
+    """scene_geo_samples gives the oracle's training samples (inputs, level, token) in order;
+    a scene with no coded level has none."""
+    from paper_2607_12656_b300 import sgs
+    sc, P = geo_scene
+    U, C, Sy = S.geo_samples(P.levels)
+    u, c, s = sgs.scene_geo_samples(sc.pos, sc.attr, 12)
+    assert np.array_equal(u, U) and np.array_equal(c, C) and np.array_equal(s, Sy)
+    from paper_2607_12656_b300.scenegen import make_scene
+    small = make_scene(300, 2)
+    u, c, s = sgs.scene_geo_samples(small.pos, small.attr, 8)
+    assert len(u) == len(c) == len(s) == 0
