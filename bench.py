@@ -7,7 +7,12 @@ fixed-length attributes with per-channel widths drawn from 4..10 bits.  Other wo
 --workload static (same scene, channel-wise static rANS, 151,552 lanes), learned (same scene,
 learned context model, 4,096 lanes), small (20,000 Gaussians, depth 12, static rANS, 32 lanes).
 
-Prints one JSON line.  --impl reference times the CPU oracle on the same workload instead.
+With no --workload the run decodes the default scene in every coding mode: the fixed-length
+decode is the headline line, and static rANS (4,096 and 151,552 lanes), the learned model
+(4,096 lanes), the position-aware model and the small plain-method scene are sub-objects
+("modes") with the same measurements, all but the small one on the same scene.
+
+Prints one JSON line.  --impl reference times the CPU oracle on the headline workload instead.
 Multi-GPU (torchrun): scenes are independent, so each rank decodes its own replica with no
 collective; value = Gaussians decoded by all ranks / max time over ranks.
 """
@@ -35,10 +40,11 @@ WORKLOADS = {
                    desc="channel-wise static rANS scene decode: N=1,000,000 (900,000 kept), depth 16, "
                         "8-bit tokens, 151,552 lanes (one 32-warp CTA per SM), rANS-coded octree levels "
                         "at about 32 tokens per geometry lane"),
-    "learned": dict(n=1_000_000, seed=2000, depth=16, mode=2, geo_mode=1, lanes=4096,
+    "learned": dict(n=1_000_000, seed=1000, depth=16, mode=2, geo_mode=1, lanes=4096,
                     desc="learned-model scene decode: N=1,000,000 (900,000 kept), depth 16, 8-bit "
-                         "tokens, 4,096 lanes, context MLP 4->64->64->256"),
-    "learned_pe": dict(n=1_000_000, seed=2000, depth=16, mode=3, geo_mode=1, lanes=28125,
+                         "tokens, 4,096 lanes, context MLP 4->64->64->256 trained 2,000 steps x 65,536 "
+                         "tokens on the scene's own tokens"),
+    "learned_pe": dict(n=1_000_000, seed=1000, depth=16, mode=3, geo_mode=1, lanes=28125,
                        desc="position-aware learned scene decode: N=1,000,000 (900,000 kept), depth 16, "
                             "8-bit tokens, 28,125 lanes (W = 32 rows per lane, the paper's fast group size), "
                             "context MLP over 4 previous tokens + Fourier positional embedding of the decoded "
@@ -55,124 +61,50 @@ WORKLOADS_DEFAULT = None  # the default workload's dict, set in main()
 K_FIXED_TRAFFIC = 43_916_288 + 141_727_744
 
 
-BATCH = dict(n_scenes=64, lo=50_000, hi=3_000_000, size_seed=3000, depth_lo=14, depth_hi=17,
-             desc="batched decode of 64 scenes: N log-uniform 50k..3M (seeded), depth U{14..17}, "
-                  "even scenes learned-model rANS, odd scenes channel-wise static rANS, rows per lane "
-                  "per mode chosen by the lane tuner, rANS-coded octree levels; one persistent launch "
-                  "per stage over all scenes")
+from paper_2607_12656_b300.workloads import BATCH, SERVE  # noqa: E402
 
 
 def batch_specs(n_scenes: int, w_learned: int = 220, w_static: int = 32) -> list:
-    """(index, N, seed, depth, mode, lanes) of every scene of the batched workload, at W rows
-    per lane per coding mode."""
-    from paper_2607_12656_b300.scenegen import loguniform_sizes
-    b = BATCH
-    sizes = loguniform_sizes(b["size_seed"], n_scenes, b["lo"], b["hi"])
-    rng = np.random.Generator(np.random.PCG64(b["size_seed"] + 1))
-    depths = rng.integers(b["depth_lo"], b["depth_hi"] + 1, size=n_scenes)
-    out = []
-    for j in range(n_scenes):
-        n = int(sizes[j])
-        kept = n - n // 10
-        learned = j % 2 == 0
-        w = w_learned if learned else w_static
-        lanes = max(32, -(-kept // w))
-        out.append((j, n, 3000 + j, int(depths[j]), 2 if learned else 1, lanes))
-    return out
-
-
-SERVE = dict(pool_per_mode=6, lo=100_000, hi=6_000_000, size_seed=4000, depth=16, rates=(20, 50, 100, 200, 400),
-             requests=400, arrival_seed=4999, budget=120 << 30, slots=8,
-             desc="continuous-batching decode server: a pool of 3 modes x 6 scenes (N log-uniform "
-                  "100k..6M, depth 16), requests draw a mode then a scene uniformly, Poisson arrivals, "
-                  "admission by HBM footprint within 120 GB, 8 concurrent decode slots")
+    from paper_2607_12656_b300 import workloads
+    return workloads.batch_specs(n_scenes, w_learned, w_static)
 
 
 def serve_specs(per_mode: int) -> list:
-    """(index, N, seed, depth, mode, lanes) of every pool scene: fixed, static, learned."""
-    from paper_2607_12656_b300.scenegen import loguniform_sizes
-    c = SERVE
-    sizes = loguniform_sizes(c["size_seed"], 3 * per_mode, c["lo"], c["hi"])
-    out = []
-    for j in range(3 * per_mode):
-        mode = j // per_mode
-        n = int(sizes[j])
-        kept = n - n // 10
-        lanes = 0 if mode == 0 else max(32, -(-kept // (220 if mode == 2 else 32)))
-        out.append((j, n, 4000 + j, c["depth"], mode, lanes))
-    return out
-
-
-_worker_ctx = None
-
-
-def encode_scene(spec, model=None) -> bytes:
-    """Generates and encodes one scene (runs in a worker process)."""
-    global _worker_ctx
-    from paper_2607_12656_b300 import sgs
-    from paper_2607_12656_b300.scenegen import make_scene
-    j, n, seed, depth, mode, lanes = spec
-    sc = make_scene(n, seed)
-    if mode == 0:
-        from paper_2607_12656_b300.scenegen import fixed_bits
-        return sgs.scene_encode(sc.pos, sc.attr, mode=0, depth=depth, bits=fixed_bits(seed), geo_mode=0)
-    kw = dict(mode=mode, depth=depth, lanes=lanes, geo_mode=1)
-    if mode == 2:
-        if _worker_ctx is None:
-            _worker_ctx = sgs.Context(0, 0)
-        kw.update(model=model, ctx=_worker_ctx)
-    return sgs.scene_encode(sc.pos, sc.attr, **kw)
+    from paper_2607_12656_b300 import workloads
+    return workloads.serve_specs(per_mode)
 
 
 TUNED = {}  # rows per lane chosen by the tuner for the batched workload, per coding mode
 
 
 def build_batch(n_scenes: int, train_steps: int, specs=None, tune: bool = False):
-    """All bitstreams of a multi-scene workload: scenes are generated and encoded by a pool of
-    spawned workers; one context model, trained on the first learned scene, serves every
-    learned scene.  With `tune`, the rows per lane of each coding mode are chosen by the
-    lane tuner (sgs_autotune: the fastest decode over W in 16..256) on that mode's
-    median-size scene, and every scene of the mode is encoded at that W."""
-    import concurrent.futures as cf
-    import multiprocessing as mp
+    """All bitstreams of a multi-scene workload, generated, trained (every learned scene its
+    own model, on its own tokens) and encoded by a pool of spawned workers.  With `tune`, the
+    rows per lane of each coding mode are first chosen by the lane tuner (sgs_autotune: the
+    fastest decode over W in 16..256) on that mode's median-size scene (a learned one with
+    its own model), and every scene of the mode is encoded at that W."""
+    from paper_2607_12656_b300 import workloads
     specs = batch_specs(n_scenes) if specs is None else specs
-    workers = max(1, min(32, (os.cpu_count() or 1)))
-    os.environ.setdefault("OMP_NUM_THREADS", str(max(1, (os.cpu_count() or 1) // workers)))
-    bufs = [None] * len(specs)
-    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as pool:
-        learned = [s for s in specs if s[4] == 2]
-        model = None
-        from paper_2607_12656_b300 import sgs
+    if tune:
+        from paper_2607_12656_b300 import learned, sgs
         from paper_2607_12656_b300.scenegen import make_scene
-        if learned:
-            from paper_2607_12656_b300 import learned as L
-            j, n, seed, depth, mode, lanes = learned[0]
-            ctx = sgs.Context(0, 0)
-            model = L.train_and_freeze(ctx, make_scene(n, seed), depth, lanes, steps=train_steps,
-                                       batch=65536, seed=1)
-            ctx.close()
-        if tune:
-            from paper_2607_12656_b300.tune import LaneTuner
-            tuner = LaneTuner()
-            ctx = sgs.Context(0, 0)
-            w_of = {}
-            for mode in sorted({s[4] for s in specs if s[4] != 0}):
-                mine = sorted((s for s in specs if s[4] == mode), key=lambda s: s[1])
-                j, n, seed, depth, _, _ = mine[len(mine) // 2]
-                sc = make_scene(n, seed)
-                lanes = tuner.choose_lanes(ctx, sc.pos, sc.attr, mode=mode, depth=depth, reps=3,
-                                           model=model if mode == 2 else None)
-                w_of[mode] = -(-(n - n // 10) // lanes)
-            ctx.close()
-            TUNED.update({{1: "static", 2: "learned"}[m]: w for m, w in w_of.items()})
-            specs = [(j, n, seed, depth, mode, max(32, -(-(n - n // 10) // w_of[mode])) if mode in w_of else lanes)
-                     for j, n, seed, depth, mode, lanes in specs]
-            learned = [s for s in specs if s[4] == 2]
-        futs = {pool.submit(encode_scene, s): s[0] for s in specs if s[4] != 2}
-        futs.update({pool.submit(encode_scene, s, model): s[0] for s in learned})
-        for f in cf.as_completed(futs):
-            bufs[futs[f]] = f.result()
-    return specs, bufs
+        from paper_2607_12656_b300.tune import LaneTuner
+        tuner = LaneTuner()
+        ctx = sgs.Context(0, 0)
+        w_of = {}
+        for mode in sorted({s[4] for s in specs if s[4] != 0}):
+            mine = sorted((s for s in specs if s[4] == mode), key=lambda s: s[1])
+            j, n, seed, depth, _, lanes = mine[len(mine) // 2]
+            sc = make_scene(n, seed)
+            model = (learned.train_and_freeze(ctx, sc, depth, lanes, steps=train_steps, batch=65536, seed=seed)
+                     if mode == 2 else None)
+            lanes = tuner.choose_lanes(ctx, sc.pos, sc.attr, mode=mode, depth=depth, reps=3, model=model)
+            w_of[mode] = -(-(n - n // 10) // lanes)
+        ctx.close()
+        TUNED.update({{1: "static", 2: "learned"}[m]: w for m, w in w_of.items()})
+        specs = [(j, n, seed, depth, mode, workloads.lanes_for(n, w_of[mode]) if mode in w_of else lanes)
+                 for j, n, seed, depth, mode, lanes in specs]
+    return specs, workloads.build(specs, train_steps)
 
 
 def peaks() -> dict:
@@ -237,10 +169,13 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def make_bitstream(w: dict, ctx=None):
+def make_bitstream(w: dict, ctx=None, sc=None):
+    """The workload's scene (or the given one, when it is the same scene) and its bitstream;
+    learned modes train their model on the scene's own tokens on the device first."""
     from paper_2607_12656_b300 import sgs
     from paper_2607_12656_b300.scenegen import fixed_bits, make_scene
-    sc = make_scene(w["n"], w["seed"])
+    if sc is None:
+        sc = make_scene(w["n"], w["seed"])
     kw = dict(mode=w["mode"], depth=w["depth"], geo_mode=w["geo_mode"])
     if w["mode"] == 0:
         kw["bits"] = fixed_bits(w["seed"])
@@ -319,19 +254,21 @@ def fixed_algorithmic_bytes(info, bits_np) -> int:
     return read + 4 * 56 * n
 
 
-def run_ours(args, w):
+def measure(args, w, ctx, sc=None, cpu: bool = True, headline: bool = False) -> dict:
+    """One coding mode of one scene: the timed decode (bitstream resident in HBM, L2 flushed
+    before every step, CUDA events on the caller's stream), latency percentiles, stage split,
+    CUDA-graph replay, the attribute kernel's roofline, the end-to-end figure through the
+    public API (bitstream from pinned host memory, outputs read back), the CPU oracle on the
+    same bitstream, and bits per Gaussian."""
     import torch
-    import torch.distributed as dist
     from paper_2607_12656_b300 import sgs
-
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
-    ctx = sgs.Context(local, 0)
-    sc, buf = make_bitstream(w, ctx)
+    from paper_2607_12656_b300 import replicas
+    rank, world, local = replicas.rank_info()
+    sc, buf = make_bitstream(w, ctx, sc)
+    train = None
+    if w["mode"] in (2, 3):
+        from paper_2607_12656_b300 import learned
+        train = dict(learned.LAST_TRAIN)
     info = sgs.scene_query(buf)
     ctx.reserve(info.scratch_bytes)
     n = info.n_rows
@@ -354,6 +291,7 @@ def run_ours(args, w):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = ctx.launch_count()
     if world > 1:
+        import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
@@ -402,10 +340,10 @@ def run_ours(args, w):
             graph_times.append(a.elapsed_time(b))
         if ctx.sync(stream) != sgs.OK:
             graph_times = []
+        del g
     except Exception as exc:  # graph capture unavailable: report eager numbers only
         print("graph capture failed: %s" % exc, file=sys.stderr)
         graph_times = []
-    from paper_2607_12656_b300 import replicas
     total_ms = replicas.max_over_ranks(sum(times), dev)  # the slowest replica sets the time
     ms_per_step = total_ms / args.steps
     value = n * world * args.steps / (total_ms / 1e3)
@@ -413,8 +351,9 @@ def run_ours(args, w):
     # end to end through the public API: pinned host bitstream -> device, decode, outputs -> host
     host_attr = torch.empty((56, n), dtype=torch.float32).pin_memory()
     host_pos = torch.empty((3, n), dtype=torch.float32).pin_memory()
+    reps = max(3, min(args.steps, 50 if w["mode"] < 2 else 10))
     e2e_times = []
-    for k in range(min(args.steps, 50)):
+    for k in range(reps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -425,10 +364,9 @@ def run_ours(args, w):
         b.record(stream)
         stream.synchronize()
         e2e_times.append(a.elapsed_time(b))
-    e2e_ms = sum(e2e_times) / len(e2e_times)
     # the same with the outputs left on the device for a renderer: upload, decode, status read
     dev_times = []
-    for k in range(min(args.steps, 50)):
+    for k in range(reps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -443,10 +381,9 @@ def run_ours(args, w):
 
     pk = peaks()
     hbm = pk.get("hbm_gbs")
-    line = {"metric": METRIC, "value": value, "unit": "Gaussians/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32->f32", "data": "synthetic",
+    line = {"value": value, "unit": "Gaussians/s", "ms_per_step": ms_per_step,
             "config": {"workload": w["desc"], "n_rows": n, "bitstream_bytes": len(buf),
+                       "bits_per_gaussian": 8.0 * len(buf) / n if n else None,
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
@@ -455,8 +392,8 @@ def run_ours(args, w):
                          "octree_positions": float(np.mean([s[1] for s in stage])),
                          "attributes": float(np.mean([s[2] for s in stage])),
                          "whole_decode": float(np.mean([s[3] for s in stage])),
-                         "note": "attributes run on their own stream, concurrent with geometry; "
-                                 "separate decodes with stage events recorded"},
+                         "note": "attributes run on their own stream, concurrent with geometry (the "
+                                 "position-aware model after it); separate decodes with stage events recorded"},
             "wall_s": wall}
     if graph_times:
         gms = float(np.mean(graph_times))
@@ -474,26 +411,23 @@ def run_ours(args, w):
                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else "fallback 6400",
                             "algorithmic_bytes": alg,
                             "traffic": args.traffic if args.traffic is not None else
-                            (K_FIXED_TRAFFIC if w is WORKLOADS_DEFAULT else None)}
+                            (K_FIXED_TRAFFIC if headline else None)}
         geo_alg = info.n_geo + 12 * n
         line["roofline_octree"] = {"bound": "hbm", "algorithmic_bytes": geo_alg,
                                    "achieved": geo_alg / (line["stage_ms"]["octree_positions"] / 1e3) / 1e9,
                                    "unit": "GB/s"}
-    if w["mode"] != 0:
+    else:
         line["config"]["attr_bits_per_gaussian"] = 8.0 * (info.total_len - info.off[7]) / n
         rl = attr_roofline(w["mode"], n, info.total_len - info.off[7], line["stage_ms"]["attributes"], pk)
-        # the learned decoders dominate their decode; static attributes run beside a longer
-        # geometry-token decode, so theirs is reported under its own key
-        line["roofline" if w["mode"] in (2, 3) else "roofline_attributes"] = rl
-    if w["mode"] in (2, 3):
-        from paper_2607_12656_b300 import learned
-        tr = learned.LAST_TRAIN
-        line["training"] = {"steps": tr["steps"], "batch": tr["batch"], "device_ms": tr["ms"],
-                            "tokens_per_s": tr["steps"] * tr["batch"] / (tr["ms"] / 1e3),
-                            "final_loss_bits_per_token": tr["final_bits"],
+        line["roofline"] = rl
+    if train is not None:
+        line["training"] = {"steps": train["steps"], "batch": train["batch"], "device_ms": train["ms"],
+                            "tokens_per_s": train["steps"] * train["batch"] / (train["ms"] / 1e3),
+                            "final_loss_bits_per_token": train["final_bits"],
                             "note": "context-model training on the GPU before the timed decodes (not timed in value)"}
     line["e2e"] = {"value": n * len(e2e_times) / (sum(e2e_times) / 1e3), "unit": "Gaussians/s",
-                   "h2d_bytes_per_step": len(buf), "d2h_bytes_per_step": 4 * 59 * n, "ms_per_step": e2e_ms,
+                   "h2d_bytes_per_step": len(buf), "d2h_bytes_per_step": 4 * 59 * n,
+                   "ms_per_step": sum(e2e_times) / len(e2e_times),
                    "note": "bitstream uploaded from pinned memory, every decoded fp32 array read back"}
     line["e2e_outputs_on_device"] = {"value": n * len(dev_times) / (sum(dev_times) / 1e3), "unit": "Gaussians/s",
                                      "h2d_bytes_per_step": len(buf), "d2h_bytes_per_step": 4,
@@ -501,10 +435,80 @@ def run_ours(args, w):
                                      "note": "bitstream uploaded, outputs kept on the device, status word read"}
     line["gpu_launches"] = launches
     line["clocks"] = clk.summary()
-    if rank == 0 and not args.no_cpu_baseline:
+    if cpu and rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, buf, args.cpu_budget)
+    return sc, line
+
+
+def _contract(line: dict, args, world: int) -> dict:
+    """The benchmark contract's keys around a measured line."""
+    out = {"metric": METRIC, "value": line["value"], "unit": "Gaussians/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": line["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u32->f32", "data": "synthetic"}
+    out.update({k: v for k, v in line.items() if k not in out})
+    return out
+
+
+def run_ours(args, w):
+    """One workload: its measured line."""
+    import torch
+    import torch.distributed as dist
+    from paper_2607_12656_b300 import sgs
+    from paper_2607_12656_b300 import replicas
+    rank, world, local = replicas.rank_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    ctx = sgs.Context(local, 0)
+    _, line = measure(args, w, ctx, headline=w is WORKLOADS_DEFAULT)
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(_contract(line, args, world)), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# The default run: the 1M-Gaussian scene of the fixed-length workload (seed 1000, depth 16)
+# decoded in every coding mode -- the metric's comparison of learned and channel-wise coding on
+# the same scene -- plus the small static scene of the plain method.  The fixed-length decode
+# is the headline (value); the others are sub-objects with the same measurements.
+DEFAULT_MODES = (("static", "static_4096"), ("static", "static"), ("learned", "learned"),
+                 ("learned_pe", "learned_pe"), ("small", "small"))
+
+
+def run_default(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2607_12656_b300 import sgs
+    from paper_2607_12656_b300 import replicas
+    rank, world, local = replicas.rank_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    ctx = sgs.Context(local, 0)
+    w = WORKLOADS_DEFAULT
+    sc, head = measure(args, w, ctx, headline=True)
+    modes = {}
+    for key, name in DEFAULT_MODES:
+        wm = dict(WORKLOADS[key])
+        if name == "static_4096":
+            wm.update(lanes=4096, geo_w=None,
+                      desc="channel-wise static rANS scene decode of the same scene: N=1,000,000 (900,000 kept), "
+                           "depth 16, 8-bit tokens, 4,096 lanes (the learned workload's lanes and W = 220 rows "
+                           "per lane), rANS-coded octree levels at the default 128 tokens per geometry lane")
+        same = wm["n"] == w["n"] and wm["seed"] == w["seed"]
+        _, line = measure(args, wm, ctx, sc if same else None)
+        modes[name] = line
+        torch.cuda.empty_cache()
+    head["modes"] = modes
+    head["modes_note"] = ("every mode but 'small' decodes the same 1M-Gaussian scene (seed 1000, depth 16, "
+                          "900,000 rows kept): fixed-length (the headline), channel-wise static rANS at "
+                          "4,096 lanes and at 151,552 lanes, the learned context model at 4,096 lanes "
+                          "(trained 2,000 x 65,536 tokens on the device), the position-aware model at "
+                          "28,125 lanes; 'small' is the 20,000-Gaussian plain-method scene (seed 0, "
+                          "depth 12, 32 lanes)")
+    if rank == 0:
+        print(json.dumps(_contract(head, args, world)), flush=True)
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
@@ -746,7 +750,7 @@ def run_serve(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     c = SERVE
-    specs = serve_specs(c["pool_per_mode"])
+    specs = serve_specs(args.pool_per_mode or c["pool_per_mode"])
     specs, bufs = build_batch(len(specs), args.train_steps or 300, specs)
     torch.cuda.set_device(local)
     scenes = [serve.Scene(b) for b in bufs]
@@ -801,7 +805,7 @@ def run_sweep(args):
     ws = [16, 32, 64, 128, 256]
     curves = {}
     encode_s = {}
-    for mode, name, seed in ((1, "static", 1000), (2, "learned", 2000), (3, "learned_pe", 2000)):
+    for mode, name, seed in ((1, "static", 1000), (2, "learned", 1000), (3, "learned_pe", 1000)):
         sc = make_scene(1_000_000, seed)
         model = None
         if mode == 2:
@@ -839,35 +843,117 @@ def run_sweep(args):
         print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(w: dict, buf: bytes, budget_s: float) -> dict:
-    """The CPU oracle, as it stands, decoding the same bitstream (or a bounded part of it)."""
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_seconds(buf: bytes, groups) -> tuple:
+    """Seconds of one oracle decode of buf: the whole decode, or (learned modes, groups = k)
+    the geometry and dequantisation plus the attribute lanes of the first k groups of 32,
+    returned as (base seconds, seconds with k groups)."""
     from oracle import scene as S
-    h = S.parse_header(buf)
-    G = (h["lanes"] + 31) // 32 if h["mode"] in (S.MODE_LEARNED, S.MODE_LEARNED_PE) else 0
-    if G <= 2:
+    if groups is None:
         t0 = time.perf_counter()
         S.decode(buf)
-        dt = time.perf_counter() - t0
-        return {"value": h["n_rows"] / dt, "unit": "Gaussians/s", "cores": 1, "kind": "oracle",
-                "sample": "one full decode of the same bitstream (%d rows) by the numpy + C oracle, "
-                          "single thread, %.2f s" % (h["n_rows"], dt)}
-    # learned models: the oracle's attribute decode costs about a minute per million tokens,
-    # so it decodes the full geometry and the first k of the G equal groups of lanes, and the
-    # attribute time is scaled by G / k
-    def timed(k):
+        return time.perf_counter() - t0, None
+    t0 = time.perf_counter()
+    S.decode(buf, attr_groups=0)
+    t1 = time.perf_counter()
+    S.decode(buf, attr_groups=groups)
+    return t1 - t0, time.perf_counter() - t1
+
+
+def _oracle_worker(path: str, groups):
+    with open(path, "rb") as f:
+        buf = f.read()
+    return _oracle_seconds(buf, groups)
+
+
+def cpu_baseline(w: dict, buf: bytes, budget_s: float) -> dict:
+    """The CPU oracle, as it stands, decoding the same bitstream (or a bounded part of it):
+    one host thread, then the same sample on every available core at once (one oracle
+    process per core, each decoding its own copy: the throughput of the host's cores on
+    independent scenes)."""
+    from oracle import scene as S
+    h = S.parse_header(buf)
+    rows = h["n_rows"]
+    G = (h["lanes"] + 31) // 32 if h["mode"] in (S.MODE_LEARNED, S.MODE_LEARNED_PE) else 0
+    if G <= 2:
+        dt, _ = _oracle_seconds(buf, None)
+        k, est = None, dt
+        sample = "one full decode of the same bitstream (%d rows) by the numpy + C oracle, %.2f s" % (rows, dt)
+    else:
+        # learned models: the oracle's attribute decode costs about a minute per million tokens,
+        # so it decodes the full geometry and the first k of the G equal groups of lanes, and the
+        # attribute time is scaled by G / k
+        t_base, t_one = _oracle_seconds(buf, 1)
+        t_one = max(1e-3, t_one - t_base)
+        k = int(min(G, max(1, (budget_s - t_base) / t_one)))
+        t_base, t_k = _oracle_seconds(buf, k)
+        t_k = max(1e-6, t_k - t_base)
+        est = t_base + t_k * G / k
+        sample = ("the numpy + C oracle on the same bitstream (%d rows): full geometry and dequantisation "
+                  "(%.2f s) plus the attribute decode of %d of the %d groups of 32 lanes (%.2f s), scaled to "
+                  "all groups: %.1f s per decode" % (rows, t_base, k, G, t_k, est))
+    out = {"value": rows / est, "unit": "Gaussians/s", "cores": 1, "kind": "oracle", "sample": sample,
+           "cpu_model": cpu_model(), "nproc": host_cores()}
+    out["all_cores"] = cpu_baseline_all_cores(buf, k, G, rows)
+    return out
+
+
+def cpu_baseline_all_cores(buf: bytes, k, G: int, rows: int) -> dict:
+    """Every usable core runs the single-thread sample at once, in its own spawned oracle
+    process (numpy and BLAS limited to one thread each); value = decodes completed per second
+    over the slowest process, times the rows of a decode."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import tempfile
+    cores = host_cores()
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        avail = 0
+    # each oracle decode of a 1M-Gaussian scene holds a few GB of numpy temporaries
+    per = max(1 << 30, 60 * len(buf))
+    n = max(1, min(cores, int(avail // per) if avail else cores))
+    env = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    with tempfile.NamedTemporaryFile(suffix=".sgs", delete=False) as f:
+        f.write(buf)
+        path = f.name
+    try:
+        for v in env:
+            os.environ[v] = "1"
         t0 = time.perf_counter()
-        S.decode(buf, attr_groups=k)
-        return time.perf_counter() - t0
-    t_base = timed(0)
-    t_one = max(1e-3, timed(1) - t_base)
-    k = int(min(G, max(1, (budget_s - t_base) / t_one)))
-    t_k = max(1e-6, timed(k) - t_base)
-    est = t_base + t_k * G / k
-    return {"value": h["n_rows"] / est, "unit": "Gaussians/s", "cores": 1, "kind": "oracle",
-            "sample": "the numpy + C oracle, single thread, on the same bitstream (%d rows): full geometry "
-                      "and dequantisation (%.2f s) plus the attribute decode of %d of the %d groups of 32 "
-                      "lanes (%.2f s), scaled to all groups: %.1f s per decode"
-                      % (h["n_rows"], t_base, k, G, t_k, est)}
+        with cf.ProcessPoolExecutor(max_workers=n, mp_context=mp.get_context("spawn")) as pool:
+            res = [f.result() for f in [pool.submit(_oracle_worker, path, k) for _ in range(n)]]
+        wall = time.perf_counter() - t0
+    finally:
+        for v, old in env.items():
+            if old is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = old
+        os.unlink(path)
+    if k is None:
+        est = max(r[0] for r in res)
+    else:
+        est = max(b + max(1e-6, t - b) * G / k for b, t in res)
+    return {"value": n * rows / est, "unit": "Gaussians/s", "cores": n, "kind": "oracle",
+            "sample": "%d oracle processes at once, each decoding the single-thread sample of its own copy "
+                      "(slowest %.1f s per full decode, %.1f s wall with process start-up)" % (n, est, wall)}
 
 
 def run_reference(args, w):
@@ -942,10 +1028,12 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fixed", choices=sorted(WORKLOADS) + ["batch", "serve", "sweep", "render"])
+    ap.add_argument("--workload", default="default",
+                    choices=["default"] + sorted(WORKLOADS) + ["batch", "serve", "sweep", "render"])
     ap.add_argument("--scenes", type=int, default=BATCH["n_scenes"], help="scenes of the batch workload")
     ap.add_argument("--rates", default=None, help="serve workload: comma-separated request rates (req/s)")
     ap.add_argument("--requests", type=int, default=None, help="serve workload: requests per rate")
+    ap.add_argument("--pool-per-mode", type=int, default=None, help="serve workload: pool scenes per coding mode")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     ap.add_argument("--traffic", type=float, default=None,
@@ -961,9 +1049,16 @@ def main():
             return
         {"batch": run_batch, "serve": run_serve, "sweep": run_sweep, "render": run_render}[args.workload](args)
         return
+    global WORKLOADS_DEFAULT
+    if args.workload == "default":
+        WORKLOADS_DEFAULT = dict(WORKLOADS["fixed"])
+        if args.impl == "reference":
+            run_reference(args, WORKLOADS_DEFAULT)
+        else:
+            run_default(args)
+        return
     w = dict(WORKLOADS[args.workload])
     if args.workload == "fixed" and args.n is None:
-        global WORKLOADS_DEFAULT
         WORKLOADS_DEFAULT = w
     if args.n is not None:
         w["n"] = args.n

@@ -177,6 +177,16 @@ int sgs_profile_read(sgs_ctx *ctx, float *ms, int cap);
 /* Number of CUDA kernels enqueued by decode calls on this context since its creation. */
 uint64_t sgs_launch_count(sgs_ctx *ctx);
 
+/* Poll budget of the device-side waits of this context's learned-model decodes (the
+ * hand-offs between the decoder's producer and consumer warps, Sec. 3.4.2's per-group
+ * decode).  Each wait polls at most `polls` times (with a short sleep between polls) and
+ * then gives up: the decode's status becomes SGS_E_TIMEOUT (read with sgs_sync), every warp
+ * of the CTA leaves its loop and the context stays usable.  polls = 0 restores the default,
+ * 2^24 polls (seconds, far beyond any legitimate wait).  Failure detection without a GPU
+ * fault: a budget of 1 makes the first wait that is not already satisfied give up.
+ * Applies to scene_decode calls made after it.  Errors: SGS_E_INVALID (NULL ctx).          */
+int sgs_set_wait_limit(sgs_ctx *ctx, uint32_t polls);
+
 /* ------------------------------------------------------------------ decode */
 
 /* Parses and validates the header of a bitstream (host bytes `bits`, `len` bytes, at least

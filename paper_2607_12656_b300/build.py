@@ -1,6 +1,12 @@
-"""Builds libsgs.so (all CUDA sources of csrc/) in-tree for sm_103a with nvcc."""
+"""Builds libsgs.so (all CUDA sources of csrc/) in-tree for sm_103a with nvcc.
+
+Each source compiles to its own object (in parallel, under _build/, recompiled only when the
+source or a header is newer than the object); the objects are then linked into the shared
+library.  No source references another's device code, so whole-translation-unit compilation
+needs no device linking."""
 from __future__ import annotations
 
+import concurrent.futures as cf
 import glob
 import os
 import subprocess
@@ -9,30 +15,55 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsgs.so")
+OBJ = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC,-ffp-contract=off,-fopenmp",
-         "-Xptxas", "-O3"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-fopenmp", "-Xptxas", "-O3"]
 
 
 def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def headers() -> list[str]:
+    return (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+            [os.path.join(HERE, "..", "include", "sgs.h")])
+
+
+def _obj(src: str) -> str:
+    return os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+
+
+def _stale(src: str, newest_header: float) -> bool:
+    o = _obj(src)
+    return not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(src), newest_header)
+
+
 def needs_build() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
-    deps.append(os.path.join(HERE, "..", "include", "sgs.h"))
-    return any(os.path.getmtime(p) > t for p in deps)
+    return any(os.path.getmtime(p) > t for p in sources() + headers())
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not needs_build():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc, *ARCH, *FLAGS, "-I", os.path.join(HERE, "..", "include"), "-o", LIB + ".tmp",
-           *sources(), "-lcuda", "-lgomp"]
+    os.makedirs(OBJ, exist_ok=True)
+    newest = max(os.path.getmtime(h) for h in headers())
+    todo = [s for s in sources() if force or _stale(s, newest)]
+
+    def compile_one(src: str) -> None:
+        cmd = [nvcc, *ARCH, *FLAGS, "-I", os.path.join(HERE, "..", "include"), "-c", "-o", _obj(src) + ".tmp", src]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        subprocess.check_call(cmd)
+        os.replace(_obj(src) + ".tmp", _obj(src))
+
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(todo), os.cpu_count() or 1))) as pool:
+        for f in [pool.submit(compile_one, s) for s in todo]:
+            f.result()
+    cmd = [nvcc, *ARCH, "-shared", "-o", LIB + ".tmp", *[_obj(s) for s in sources()], "-lcuda", "-lgomp"]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.check_call(cmd)

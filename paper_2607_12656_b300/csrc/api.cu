@@ -117,6 +117,7 @@ extern "C" int sgs_create(sgs_ctx **out, int device, size_t scratch_bytes) {
     cudaMemset(c->status_dev, 0, 256);
     c->launches = 0;
     c->profile = 0;
+    c->wait_limit = kDefaultWaitPolls;
     c->n_marks = 0;
     for (int i = 0; i <= kMaxStages; ++i) cudaEventCreate(&c->marks[i]);
     for (int i = 0; i < 2; ++i) cudaEventCreate(&c->amarks[i]);
@@ -200,6 +201,12 @@ extern "C" int sgs_profile_read(sgs_ctx *c, float *ms, int cap) {
 }
 
 extern "C" uint64_t sgs_launch_count(sgs_ctx *c) { return c ? c->launches : 0; }
+
+extern "C" int sgs_set_wait_limit(sgs_ctx *c, uint32_t polls) {
+    if (!c) return SGS_E_INVALID;
+    c->wait_limit = polls ? polls : kDefaultWaitPolls;
+    return SGS_OK;
+}
 
 extern "C" int sgs_sync(sgs_ctx *c, sgs_stream stream) {
     if (!c) return SGS_E_INVALID;
@@ -349,7 +356,7 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
         switch (info.mode) {
             case SGS_MODE_FIXED: e = launch_fixed(bits, info, out, status, c->aux); break;
             case SGS_MODE_STATIC: e = launch_rans_static_attr(bits, info, attr_tables, out, status, c->aux); break;
-            default: e = launch_learned_decode(bits, info, out, s.learned, status, c->aux); break;
+            default: e = launch_learned_decode(bits, info, out, s.learned, status, c->aux, c->wait_limit); break;
         }
         if (e != cudaSuccess) return SGS_E_CUDA;
         if (c->profile) cudaEventRecord(c->amarks[1], c->aux);

@@ -82,6 +82,7 @@ struct LearnedParams {
     float *out;
     const uint32_t *out_index;
     int *status;
+    uint32_t wait_limit;  // polls of each bounded mbarrier wait before it gives up
 };
 
 // Pipelined decoder: kPW producer warps compute the frequency tables of the steps (Gaussian i,
@@ -99,7 +100,7 @@ constexpr int kLT = kPT + 32;            // + consumer warp
 constexpr int kNB = 7;                   // ring depth (steps)
 constexpr int kQW = 4;                   // warps per step (8 contexts each)
 constexpr int kSW = kPW / kQW;           // steps in flight
-constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr uint32_t kWaitLimit = kDefaultWaitPolls;
 constexpr int kCS = 264;                 // cdf row stride (u16): rows 528 B apart spread the banks
 static_assert(kNB >= kSW && kNB <= kNChan, "ring");
 
@@ -148,9 +149,11 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase of `parity` to complete; false on timeout or abort.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_) {
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+// Bounded wait for the phase of `parity` to complete: at most `limit` polls; false on
+// timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_,
+                                          uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it) {
         if (mbar_test(bar, parity)) return true;
         if (*abort_) return false;
         if (it > 64) __nanosleep(64);
@@ -407,7 +410,7 @@ __device__ __forceinline__ void consume(const LearnedParams &p, LSmem2 &S, uint3
     for (uint32_t k = 0; k < K; ++k) {
         const int b = (int)(k % kNB);
         // every lane acquires the producers' release of buffer b
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(&S.full[b], (k / kNB) & 1, abort_));
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&S.full[b], (k / kNB) & 1, abort_, p.wait_limit));
         if (!ok) {
             if (lane == 0) { *abort_ = 1; set_status(p.status, SGS_E_TIMEOUT); }
             aborted = true;
@@ -491,7 +494,7 @@ __device__ __forceinline__ void learned_body(const LearnedParams &p, uint32_t gr
             const int b = (int)(k % kNB);
             // every lane acquires the consumer's release of buffer b (and with it the tokens
             // the consumer wrote into the context ring)
-            const bool ok = k < (uint32_t)kNB || mbar_wait(&S.empty[b], ((k / kNB) - 1) & 1, abort_);
+            const bool ok = k < (uint32_t)kNB || mbar_wait(&S.empty[b], ((k / kNB) - 1) & 1, abort_, p.wait_limit);
             if (!__all_sync(0xffffffffu, ok)) {
                 if (lane == 0) { *abort_ = 1; set_status(p.status, SGS_E_TIMEOUT); }
                 break;
@@ -524,9 +527,10 @@ size_t learned_work_bytes(const sgs_scene_info &) { return 0; }
 
 
 static uint32_t make_learned(const uint8_t *bits, const sgs_scene_info &info, const sgs_scene_out &out,
-                             int *status, LearnedParams *pp) {
+                             int *status, LearnedParams *pp, uint32_t wait_limit = kWaitLimit) {
     LearnedParams &p = *pp;
     memset(&p, 0, sizeof(p));
+    p.wait_limit = wait_limit ? wait_limit : kWaitLimit;
     p.bits = bits;
     p.model_off = info.off[S_ATTR_TAB];
     p.chan_off = info.off[S_CHAN];
@@ -550,9 +554,10 @@ static cudaError_t learned_smem_limit(const void *kernel, bool *done) {
 }
 
 cudaError_t launch_learned_decode(const uint8_t *bits, const sgs_scene_info &info,
-                                  const sgs_scene_out &out, uint8_t *, int *status, cudaStream_t st) {
+                                  const sgs_scene_out &out, uint8_t *, int *status, cudaStream_t st,
+                                  uint32_t wait_limit) {
     LearnedParams p;
-    const uint32_t grid = make_learned(bits, info, out, status, &p);
+    const uint32_t grid = make_learned(bits, info, out, status, &p, wait_limit);
     if (grid == 0) return cudaSuccess;
     static bool set = false;
     cudaError_t e = learned_smem_limit(reinterpret_cast<const void *>(k_learned_decode), &set);

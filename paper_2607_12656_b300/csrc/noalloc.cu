@@ -76,8 +76,13 @@ extern "C" int scene_decode_noalloc(const uint8_t *bits, const sgs_scene_info *i
     // the array keeps the previous call's contents: clear the status word (nothing else
     // needs to start at zero)
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return SGS_E_CUDA;
-    if (launch_tables(bits, *info, plan.n_coded_levels, s.tables, status, st) != cudaSuccess)
+    // once a stage is enqueued, an error return first waits for what is already on the
+    // stream, so that no work of this call still uses the shared array afterwards
+    auto fail = [&]() {
+        cudaStreamSynchronize(st);
         return SGS_E_CUDA;
+    };
+    if (launch_tables(bits, *info, plan.n_coded_levels, s.tables, status, st) != cudaSuccess) return fail();
     uint8_t *attr_tables = s.tables + (size_t)plan.n_coded_levels * kTabBytes;
     const sgs_scene_out o = effective_out(*info, *out, s);
     cudaError_t e = cudaSuccess;
@@ -87,20 +92,19 @@ extern "C" int scene_decode_noalloc(const uint8_t *bits, const sgs_scene_info *i
         case SGS_MODE_LEARNED: e = launch_learned_decode(bits, *info, o, s.learned, status, st); break;
         default: break;  // the position-aware model follows the octree
     }
-    if (e != cudaSuccess) return SGS_E_CUDA;
+    if (e != cudaSuccess) return fail();
     if (info->geo_mode == SGS_GEO_RANS && info->n_geo) {
-        if (launch_geo_copy_raw(bits, *info, plan, s.geo_bytes, st) != cudaSuccess) return SGS_E_CUDA;
+        if (launch_geo_copy_raw(bits, *info, plan, s.geo_bytes, st) != cudaSuccess) return fail();
         if (launch_rans_static_geo(bits, *info, plan, s.tables, s.geo_bytes, status, st) != cudaSuccess)
-            return SGS_E_CUDA;
+            return fail();
     }
-    if (launch_octree(*info, plan, bits, s, o, status, st) != cudaSuccess)
-        return SGS_E_CUDA;
+    if (launch_octree(*info, plan, bits, s, o, status, st) != cudaSuccess) return fail();
     if (info->mode == SGS_MODE_LEARNED_PE &&
         launch_learned_pe_decode(bits, *info, o, o.coord, status, st) != cudaSuccess)
-        return SGS_E_CUDA;
+        return fail();
     int host_status = SGS_OK;
     if (cudaMemcpyAsync(&host_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        return SGS_E_CUDA;
+        return fail();
     if (cudaStreamSynchronize(st) != cudaSuccess) return SGS_E_CUDA;
     return host_status;
 }

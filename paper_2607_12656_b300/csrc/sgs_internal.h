@@ -86,9 +86,11 @@ cudaError_t launch_octree(const sgs_scene_info &info, const GeoPlan &plan, const
                           const Scratch &s, const sgs_scene_out &out, int *status, cudaStream_t st);
 cudaError_t launch_fixed(const uint8_t *bits, const sgs_scene_info &info,
                          const sgs_scene_out &out, int *status, cudaStream_t st);
+// Polls of a bounded device wait before it gives up (the default of sgs_set_wait_limit).
+constexpr uint32_t kDefaultWaitPolls = 1u << 24;
 cudaError_t launch_learned_decode(const uint8_t *bits, const sgs_scene_info &info,
                                   const sgs_scene_out &out, uint8_t *work, int *status,
-                                  cudaStream_t st);
+                                  cudaStream_t st, uint32_t wait_limit = kDefaultWaitPolls);
 size_t learned_work_bytes(const sgs_scene_info &info);
 // Position-aware learned decode: reads the rows' voxel coordinates coord [3][n_rows]
 // (written by the octree walk before it, in stream order).

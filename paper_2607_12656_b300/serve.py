@@ -1,12 +1,15 @@
 """Continuous-batching decode server on one GPU.
 
 Requests (scene bitstreams with arrival times) are admitted as soon as a slot and HBM budget
-are free: admission charges each request its device footprint (bitstream + decoded outputs +
-decode scratch) against the budget, in arrival order.  A request whose footprint alone
-exceeds the budget can never be admitted; it is answered at once with E_NOMEM instead of
-holding up the queue.  Each slot owns a CUDA stream and a library context (its
-own scratch and status word), so admitted decodes overlap on the device while the host loop
-keeps admitting and retiring.  Latency = completion event time - arrival time.
+are free.  Each slot owns a CUDA stream and a library context whose decode scratch, sized for
+the pool's largest scene, is allocated once when the server is built; the slots' scratch is
+charged against the HBM budget then, and each request is charged its own device buffers
+(bitstream + decoded outputs) at admission, in arrival order.  A request that cannot fit
+even with every other slot idle is answered at once with E_NOMEM instead of holding up the
+queue.  Admitted decodes overlap on the device while the host loop keeps admitting and
+retiring.  Latency = completion - arrival, with the completion taken from the device: the
+admission time plus the CUDA-event time from the slot's first enqueued operation to the end
+of its decode (the loop's polling delay is not counted).
 
 Only orchestration lives here; every decode runs in the library's kernels through
 ``scene_decode``.
@@ -40,8 +43,13 @@ class Scene:
     def n_rows(self) -> int:
         return int(self.info.n_rows)
 
+    def buffers(self) -> int:
+        """Device bytes a request allocates: the bitstream and the decoded outputs."""
+        return int(self.info.total_len) + 4 * 59 * self.n_rows
+
     def footprint(self) -> int:
-        return int(self.info.total_len) + 4 * 59 * self.n_rows + int(self.info.scratch_bytes)
+        """Device bytes of one decode of this scene: its buffers plus its decode scratch."""
+        return self.buffers() + int(self.info.scratch_bytes)
 
 
 @dataclasses.dataclass
@@ -54,6 +62,7 @@ class Result:
     status: int
     attr: object = None
     pos: object = None
+    digest: tuple = None  # (sha256 of attr bytes, sha256 of pos bytes) with keep_outputs="digest"
 
     @property
     def latency(self) -> float:
@@ -70,14 +79,17 @@ class _Slot:
 
 class DecodeServer:
     def __init__(self, scenes: list[Scene], *, slots: int = 8, hbm_budget: int = 120 << 30,
-                 device: int = 0, keep_outputs: bool = False):
+                 device: int = 0, keep_outputs=False):
+        """keep_outputs: False, True (results carry host copies of the outputs) or "digest"
+        (results carry SHA-256 digests of the outputs' bytes, for scenes too large to keep)."""
         self.scenes = scenes
         self.device = device
         self.budget = hbm_budget
         self.keep = keep_outputs
         scratch = max(s.info.scratch_bytes for s in scenes)
+        self.slot_scratch = slots * int(scratch)  # allocated now, charged once
         self.slots = self._make_slots(slots, scratch)
-        self.in_use = 0
+        self.in_use = self.slot_scratch
 
     # ---- device side: one stream and one library context per slot
     def _make_slots(self, n: int, scratch: int) -> list:
@@ -105,10 +117,16 @@ class DecodeServer:
     def _retire(self, slot: _Slot, t0: float) -> Result:
         req, sid, arr, adm, ev0, ev1, bufs = slot.busy
         st = slot.ctx.sync(slot.stream)
-        r = Result(req, sid, arr, adm, time.perf_counter() - t0, st)
+        r = Result(req, sid, arr, adm, adm + ev0.elapsed_time(ev1) / 1e3, st)
         if self.keep:
             n = self.scenes[sid].n_rows
-            r.attr, r.pos = bufs[1][:, :n].cpu(), bufs[2][:, :n].cpu()
+            a, p = bufs[1][:, :n].cpu(), bufs[2][:, :n].cpu()
+            if self.keep == "digest":
+                import hashlib
+                r.digest = (hashlib.sha256(a.numpy().tobytes()).hexdigest(),
+                            hashlib.sha256(p.numpy().tobytes()).hexdigest())
+            else:
+                r.attr, r.pos = a, p
         return r
 
     # ---- host loop: arrivals, retirement, admission
@@ -127,13 +145,13 @@ class DecodeServer:
                 if sl.busy and self._finished(sl):
                     sid = sl.busy[1]
                     results.append(self._retire(sl, t0))
-                    self.in_use -= self.scenes[sid].footprint()
+                    self.in_use -= self.scenes[sid].buffers()
                     sl.busy = None
             # admit in arrival order while a slot and memory are free
             while queue:
                 req, arr, sid = queue[0]
-                fp = self.scenes[sid].footprint()
-                if fp > self.budget:  # can never fit: answer now rather than block the queue
+                fp = self.scenes[sid].buffers()
+                if fp + self.slot_scratch > self.budget:  # can never fit: answer now, do not block
                     queue.popleft()
                     t = time.perf_counter() - t0
                     results.append(Result(req, sid, arr, t, t, sgs.E_NOMEM))

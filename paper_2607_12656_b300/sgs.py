@@ -122,6 +122,7 @@ def lib() -> ctypes.CDLL:
         L.sgs_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_float), i32]
         L.sgs_launch_count.argtypes = [P]
         L.sgs_launch_count.restype = u64
+        L.sgs_set_wait_limit.argtypes = [P, u32]
         L.scene_decode_noalloc.argtypes = [P, ctypes.POINTER(SceneInfo), ctypes.POINTER(SceneOut), P]
         L.sgs_autotune.argtypes = [P, ctypes.POINTER(TuneRequest), ctypes.POINTER(TuneResult)]
         _lib = L
@@ -190,6 +191,10 @@ class Context:
     def launch_count(self) -> int:
         return int(lib().sgs_launch_count(self.handle))
 
+    def set_wait_limit(self, polls: int) -> None:
+        """Poll budget of the learned decoders' bounded device waits (0 = the default)."""
+        _check(lib().sgs_set_wait_limit(self.handle, polls), "sgs_set_wait_limit")
+
     def close(self) -> None:
         if getattr(self, "handle", None):
             lib().sgs_destroy(self.handle)
@@ -231,7 +236,21 @@ def scene_decode(ctx: Context, bits_dev, info: SceneInfo, attr, pos, coord=None,
                               _stream(stream)), "scene_decode")
 
 
-NOALLOC_SCRATCH_BYTES = 64 << 20
+def _header_constant(name: str) -> int:
+    """An integer #define of the library's C header (include/sgs.h), so that the binding
+    never restates a size the library fixes."""
+    import re
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "sgs.h")
+    m = re.search(r"^#define\s+%s\s+(.+?)\s*(/\*.*)?$" % name, open(hdr).read(), re.M)
+    if not m:
+        raise RuntimeError("%s is not defined in %s" % (name, hdr))
+    expr = re.sub(r"(?<=\d)[uU]?[lL]{0,2}\b", "", m.group(1))
+    if not re.fullmatch(r"[\d\s()<+*-]+", expr):
+        raise RuntimeError("cannot evaluate %s = %s" % (name, m.group(1)))
+    return int(eval(expr, {"__builtins__": {}}))
+
+
+NOALLOC_SCRATCH_BYTES = _header_constant("SGS_NOALLOC_SCRATCH_BYTES")
 
 
 def scene_decode_noalloc(bits_dev, info: SceneInfo, attr, pos, coord=None, out_index=None,

@@ -13,6 +13,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from test_gpu_decode import gpu_decode, same_bits  # noqa: E402
+from tolerance import assert_close  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -83,10 +84,6 @@ def test_learned_corrupt_model_flagged(ctx, toy):
 
 # ----------------------------------------------------------------------------- training
 
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
-
-
 def test_training_gradients_match_fp64(ctx):
     sc = make_scene(5000, 31)
     tokens = sgs.scene_tokens(sc.pos, sc.attr, 11)
@@ -103,7 +100,7 @@ def test_training_gradients_match_fp64(ctx):
     g32 = sgs.unpack_weights(grad.cpu().numpy())
     assert abs(loss32 - loss64) / loss64 < 1e-5
     for k in M.PARAMS:
-        assert _rel(g32[k].astype(np.float64), g64[k]) < 1e-4, k
+        assert_close(g32[k], g64[k], 'gradient ' + k)
 
 
 def test_training_steps_match_fp64(ctx):
@@ -120,7 +117,7 @@ def test_training_steps_match_fp64(ctx):
                   batch=2048, seed=6, lr=1e-3, loss_dev=losses)
     w32 = sgs.unpack_weights(w.cpu().numpy())
     for k in M.PARAMS:
-        assert _rel(w32[k].astype(np.float64), p64[k]) < 1e-4, k
+        assert_close(w32[k], p64[k], 'weights ' + k)
     assert np.allclose(losses.cpu().numpy(), losses64, rtol=1e-4)
 
 
@@ -179,3 +176,48 @@ def test_full_size_learned_scene(ctx):
         assert pay[int(goff[g]):int(goff[g + 1])] == want
         dec = S.rans_decode_learned(m, lr, lo, hi, pay, goff, gw, P.n_rows)
         assert np.array_equal(dec[lr[lo]:lr[hi]], q[lr[lo]:lr[hi]])
+
+
+def test_training_resumes_exactly(ctx):
+    """Checkpoint and resume: 3 steps, then 3 more from the saved weights and Adam moments at
+    step0 = 3, give the same weights, bit for bit, as 6 uninterrupted steps (the sampler and
+    the bias corrections are indexed by the global step), and both agree element-wise with
+    the fp64 oracle's 6 steps."""
+    sc = make_scene(4000, 33)
+    tokens = sgs.scene_tokens(sc.pos, sc.attr, 11)
+    lanes = 8
+    init = kaiming_init(11)
+    dev = torch.device("cuda", 0)
+    tok = torch.from_numpy(tokens).to(dev)
+    whole = torch.from_numpy(sgs.pack_weights(init)).to(dev)
+    adam = torch.zeros(2 * sgs.WEIGHTS_FLOATS, device=dev)
+    sgs.sgs_train(ctx, tok, tokens.shape[0], lanes, whole, adam, steps=6, batch=2048, seed=7, lr=1e-3)
+    part = torch.from_numpy(sgs.pack_weights(init)).to(dev)
+    adam2 = torch.zeros(2 * sgs.WEIGHTS_FLOATS, device=dev)
+    sgs.sgs_train(ctx, tok, tokens.shape[0], lanes, part, adam2, steps=3, batch=2048, seed=7, lr=1e-3)
+    saved_w, saved_adam = part.cpu().clone(), adam2.cpu().clone()  # the checkpoint
+    part, adam2 = saved_w.to(dev), saved_adam.to(dev)
+    sgs.sgs_train(ctx, tok, tokens.shape[0], lanes, part, adam2, steps=3, batch=2048, seed=7, lr=1e-3, step0=3)
+    assert torch.equal(part.view(torch.int32), whole.view(torch.int32))
+    assert torch.equal(adam2.view(torch.int32), adam.view(torch.int32))
+    p64, _ = M.train(init, tokens, S.lane_bounds(tokens.shape[0], lanes), 6, 2048, seed=7, lr=1e-3)
+    w32 = sgs.unpack_weights(part.cpu().numpy())
+    for k in M.PARAMS:
+        assert_close(w32[k], p64[k], 'resumed weights ' + k)
+
+
+def test_bounded_wait_times_out_and_context_recovers(ctx, toy):
+    """Failure detection without a GPU fault: with a poll budget of 1 the decoder's first wait
+    that is not already satisfied gives up, the decode reports SGS_E_TIMEOUT through
+    sgs_sync, every warp leaves, and the same context then decodes the scene bit-exactly
+    with the default budget."""
+    sc, P, model = toy
+    buf = S.encode(None, None, mode=S.MODE_LEARNED, depth=10, lanes=64, model=model, prep=P)
+    ctx.set_wait_limit(1)
+    try:
+        st, _, _, _, _ = gpu_decode(ctx, buf)
+    finally:
+        ctx.set_wait_limit(0)
+    assert st == sgs.E_TIMEOUT, sgs.lib().sgs_strerror(st)
+    st, attr, pos, crd, _ = gpu_decode(ctx, buf)
+    assert st == sgs.OK and same_bits(attr, P.attr) and same_bits(pos, P.pos) and np.array_equal(crd, P.coord)

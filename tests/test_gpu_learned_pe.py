@@ -15,6 +15,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from test_gpu_decode import gpu_decode, same_bits  # noqa: E402
+from tolerance import assert_close  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -161,10 +162,6 @@ def test_batched_and_noalloc_parity(ctx, toy):
 
 # ----------------------------------------------------------------------------- training
 
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
-
-
 def test_training_gradients_match_fp64(ctx):
     sc = make_scene(5000, 31)
     tokens, coord = sgs.scene_rows(sc.pos, sc.attr, 11)
@@ -183,7 +180,7 @@ def test_training_gradients_match_fp64(ctx):
     g32 = sgs.unpack_weights_pe(grad.cpu().numpy())
     assert abs(loss32 - loss64) / loss64 < 1e-5
     for k in E.PARAMS:
-        assert _rel(g32[k].astype(np.float64), g64[k]) < 1e-4, k
+        assert_close(g32[k], g64[k], 'gradient ' + k)
 
 
 def test_training_steps_match_fp64(ctx):
@@ -200,7 +197,7 @@ def test_training_steps_match_fp64(ctx):
                      tokens.shape[0], lanes, w, adam, steps=5, batch=2048, seed=6, lr=1e-3, loss_dev=losses)
     w32 = sgs.unpack_weights_pe(w.cpu().numpy())
     for k in E.PARAMS:
-        assert _rel(w32[k].astype(np.float64), p64[k]) < 1e-4, k
+        assert_close(w32[k], p64[k], 'weights ' + k)
     assert np.allclose(losses.cpu().numpy(), losses64, rtol=1e-4)
 
 
@@ -249,3 +246,31 @@ def test_full_size_scene(ctx):
         assert pay[int(goff[g]):int(goff[g + 1])] == want
         dec = S.rans_decode_pe(m, P.coord, 16, lr, pay, goff, gw, lo, hi)
         assert np.array_equal(dec[lr[lo]:lr[hi]], q[lr[lo]:lr[hi]])
+
+
+def test_training_resumes_exactly(ctx):
+    """Checkpoint and resume of the position-aware model: 3 + 3 steps (step0 = 3 from the
+    saved weights and moments) equal 6 uninterrupted steps bit for bit, and the fp64
+    oracle's 6 steps element-wise."""
+    sc = make_scene(4000, 34)
+    tokens, coord = sgs.scene_rows(sc.pos, sc.attr, 11)
+    lanes = 8
+    init = kaiming_init_pe(12)
+    dev = torch.device("cuda", 0)
+    tok = torch.from_numpy(tokens).to(dev)
+    crd = torch.from_numpy(coord.view(np.int32)).to(dev)
+    args = (ctx, tok, crd, 11, tokens.shape[0], lanes)
+    whole = torch.from_numpy(sgs.pack_weights_pe(init)).to(dev)
+    adam = torch.zeros(2 * sgs.WEIGHTS_PE_FLOATS, device=dev)
+    sgs.sgs_train_pe(*args, whole, adam, steps=6, batch=2048, seed=8, lr=1e-3)
+    part = torch.from_numpy(sgs.pack_weights_pe(init)).to(dev)
+    adam2 = torch.zeros(2 * sgs.WEIGHTS_PE_FLOATS, device=dev)
+    sgs.sgs_train_pe(*args, part, adam2, steps=3, batch=2048, seed=8, lr=1e-3)
+    part, adam2 = part.cpu().clone().to(dev), adam2.cpu().clone().to(dev)
+    sgs.sgs_train_pe(*args, part, adam2, steps=3, batch=2048, seed=8, lr=1e-3, step0=3)
+    assert torch.equal(part.view(torch.int32), whole.view(torch.int32))
+    assert torch.equal(adam2.view(torch.int32), adam.view(torch.int32))
+    p64, _ = E.train(init, tokens, S.lane_bounds(tokens.shape[0], lanes), coord, 11, 6, 2048, seed=8, lr=1e-3)
+    w32 = sgs.unpack_weights_pe(part.cpu().numpy())
+    for k in E.PARAMS:
+        assert_close(w32[k], p64[k], 'resumed weights ' + k)

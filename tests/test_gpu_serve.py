@@ -217,10 +217,12 @@ def test_server_mix_equals_alone(pool):
 def test_server_respects_hbm_budget(pool):
     from paper_2607_12656_b300 import serve
     scenes = [serve.Scene(b) for b, _ in pool]
-    biggest = max(s.footprint() for s in scenes)
-    srv = serve.DecodeServer(scenes, slots=4, hbm_budget=biggest)  # one request at a time
+    biggest = max(s.buffers() for s in scenes)
+    scratch = 4 * max(int(s.info.scratch_bytes) for s in scenes)  # the 4 slots' scratch
+    srv = serve.DecodeServer(scenes, slots=4, hbm_budget=scratch + biggest)  # one request at a time
     res = srv.run(serve.poisson_arrivals(5000.0, 12, len(scenes), seed=8))
     srv.close()
+    assert all(r.status == sgs.OK for r in res)
     res = sorted(res, key=lambda r: r.admitted)
     for a, b in zip(res, res[1:]):
-        assert b.admitted >= a.done - 1e-3 or scenes[a.scene].footprint() + scenes[b.scene].footprint() <= biggest
+        assert b.admitted >= a.done - 1e-3 or scenes[a.scene].buffers() + scenes[b.scene].buffers() <= biggest

@@ -85,3 +85,19 @@ def test_budget_of_one_scene_serialises():
     assert all(u == 6 and b == 1 for _, u, b in srv.log)
     for a, b in zip(res, res[1:]):
         assert b.admitted >= a.done
+
+
+@pytest.mark.timeout(60)
+def test_slot_scratch_is_charged_once():
+    """Every slot's decode scratch (sized for the largest scene) is allocated when the server
+    is built and charged against the budget then; requests are charged their own buffers."""
+    info = lambda n, s: types.SimpleNamespace(n_rows=0, total_len=n, scratch_bytes=s)
+    scenes = [serve.Scene(b"", info=info(n, s), host=object()) for n, s in ((3, 1), (2, 2), (7, 1))]
+    srv = _FakeServer(scenes, dur=[0.002, 0.002, 0.002], slots=2, hbm_budget=10)
+    assert srv.slot_scratch == 4 and srv.in_use == 4
+    res = srv.run([(0.0005 * i, i % 3) for i in range(24)])
+    assert all(u <= 10 for _, u, _ in srv.log)
+    # scene 2 needs 7 + the slots' 4 > 10: refused at once; the others fit one at a time
+    for r in res:
+        assert r.status == (sgs.E_NOMEM if r.scene == 2 else sgs.OK)
+    assert srv.in_use == 4
