@@ -350,6 +350,15 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
     if (cudaEventRecord(c->fork, st) != cudaSuccess || cudaStreamWaitEvent(c->aux, c->fork, 0) != cudaSuccess ||
         cudaStreamWaitEvent(c->geo, c->fork, 0) != cudaSuccess)
         return SGS_E_CUDA;
+    // the geometry tokens are enqueued first: their short CTAs take SMs before the attribute
+    // decoder's long-running ones fill the device
+    cudaStream_t gs = c->geo;
+    if (info.geo_mode == SGS_GEO_RANS && info.n_geo) {
+        if ((e = launch_geo_copy_raw(bits, info, plan, s.geo_bytes, gs)) != cudaSuccess) return SGS_E_CUDA;
+        if ((e = launch_rans_static_geo(bits, info, plan, s.tables, s.geo_bytes, status, gs)) != cudaSuccess)
+            return SGS_E_CUDA;
+        c->launches += 2;
+    }
     if (!after_geo) {
         if (c->profile) cudaEventRecord(c->amarks[0], c->aux);
         if (info.n_rows) c->launches += 1;
@@ -362,13 +371,6 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
         if (c->profile) cudaEventRecord(c->amarks[1], c->aux);
     }
     if (cudaEventRecord(c->join, c->aux) != cudaSuccess) return SGS_E_CUDA;
-    cudaStream_t gs = c->geo;
-    if (info.geo_mode == SGS_GEO_RANS && info.n_geo) {
-        if ((e = launch_geo_copy_raw(bits, info, plan, s.geo_bytes, gs)) != cudaSuccess) return SGS_E_CUDA;
-        if ((e = launch_rans_static_geo(bits, info, plan, s.tables, s.geo_bytes, status, gs)) != cudaSuccess)
-            return SGS_E_CUDA;
-        c->launches += 2;
-    }
     if (c->profile && c->n_marks <= kMaxStages) cudaEventRecord(c->marks[c->n_marks++], gs);
     if ((e = launch_octree(info, plan, bits, s, out, status, gs)) != cudaSuccess) return SGS_E_CUDA;
     if (info.n_rows) c->launches += octree_launches(info, plan);

@@ -7,7 +7,8 @@
 // Sec. 3.4.2, decoded in parallel).  The 32 lanes of a group share one word stream; at each
 // step every lane decodes one symbol and the lanes whose state dropped below 2^16 take the
 // next words in lane order -- their word index is the popcount of the ballot below them.
-// Tables live in shared memory as cdf[257]; a symbol is found by an 8-step binary search.
+// Tables live in shared memory as cdf[257] with a slot lookup of 1,024 buckets; a symbol is
+// the bucket's first symbol or one of the few that start after it inside the bucket.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -35,6 +36,7 @@ struct TableParams {
 
 __device__ __forceinline__ void tables_body(const TableParams &p, uint32_t t) {
     __shared__ uint32_t sm[8];
+    __shared__ uint32_t s_cdf[kTabCdfWords];
     const int s = threadIdx.x;
     const uint8_t *bits = p.bits;
     const uint64_t off = p.to.off[t];
@@ -46,13 +48,19 @@ __device__ __forceinline__ void tables_body(const TableParams &p, uint32_t t) {
     const uint32_t c = block_excl_scan_256(f, &tot, sm);
     uint32_t *out_cdf = reinterpret_cast<uint32_t *>(p.tables + (size_t)t * kTabBytes);
     out_cdf[s] = c;
+    s_cdf[s] = c;
     if (s == 0) {
         const bool empty_ok = p.allow_empty_attr && (int)t >= p.n_geo_tables && tot == 0;
         if (!(tot == 65536u || empty_ok)) set_status(p.status, SGS_E_CORRUPT);
         // cdf[256] = 2^16 always (a corrupt table was flagged above): every slot < 2^16 then
         // finds its symbol at or below 255 without a bound check in the decoders
         out_cdf[256] = 65536u;
+        s_cdf[256] = 65536u;
     }
+    __syncthreads();
+    // slot lookup: the symbol holding the first slot of each bucket
+    uint8_t *lut = p.tables + (size_t)t * kTabBytes + kTabCdfBytes;
+    for (int b = s; b < kLutBuckets; b += 256) lut[b] = (uint8_t)cdf_search(s_cdf, (uint32_t)b << kLutShift);
 }
 
 __global__ void __launch_bounds__(256) k_tables(TableParams p) { tables_body(p, blockIdx.x); }
@@ -98,9 +106,12 @@ struct AttrParams {
 
 constexpr int kAttrWarps = 32;  // one CTA per SM shares one copy of the 56 tables
 static_assert(kNChan % 8 == 0, "channels are decoded 8 at a time");
-constexpr size_t kAttrTabSmem = kNChan * kTabCdfWords * 4 + 2 * kNChan * 4;
-constexpr size_t kAttrSmem = kAttrTabSmem + kAttrWarps * kWinWords * 2;
-static_assert(kAttrTabSmem % 16 == 0, "window must be 16-byte aligned");
+constexpr size_t kAttrCdfSmem = kNChan * kTabCdfWords * 4 + 2 * kNChan * 4;  // cdf, step, offset
+constexpr size_t kAttrTabSmem = kAttrCdfSmem + kNChan * kLutBuckets;
+constexpr size_t attr_smem(int warps) { return kAttrTabSmem + (size_t)warps * kWinWords * 2; }
+constexpr size_t kAttrSmem = attr_smem(kAttrWarps);
+static_assert(kAttrCdfSmem % 16 == 0 && kAttrTabSmem % 16 == 0, "lookup and windows must be 16-byte aligned");
+static_assert(kAttrSmem <= 227 * 1024, "attribute decoder shared memory");
 
 template <bool IDX>
 __device__ __forceinline__ void rans_attr_body(const AttrParams &p, uint32_t vb, bool reload) {
@@ -108,17 +119,18 @@ __device__ __forceinline__ void rans_attr_body(const AttrParams &p, uint32_t vb,
     uint32_t *s_cdf = (uint32_t *)smem;                          // [56][257]
     float *s_step = (float *)(smem + kNChan * kTabCdfWords * 4);  // [56]
     float *s_off = s_step + kNChan;                               // [56]
+    uint8_t *s_lut = smem + kAttrCdfSmem;                         // [56][1024]
     uint16_t *s_win = reinterpret_cast<uint16_t *>(smem + kAttrTabSmem) + (threadIdx.x >> 5) * kWinWords;
     if (reload) {  // (a CTA's next item of the same scene finds the tables in place)
-        load_cdf_smem(p.tables, kNChan, s_cdf);
-        if (threadIdx.x < kNChan) {
-            s_step[threadIdx.x] = ld_f32(p.bits + p.chan_off + 4 * threadIdx.x);
-            s_off[threadIdx.x] = ld_f32(p.bits + p.chan_off + 4 * (kNChan + threadIdx.x));
+        load_cdf_smem(p.tables, kNChan, s_cdf, s_lut);
+        for (int c = threadIdx.x; c < kNChan; c += blockDim.x) {  // (a CTA may be a single warp)
+            s_step[c] = ld_f32(p.bits + p.chan_off + 4 * c);
+            s_off[c] = ld_f32(p.bits + p.chan_off + 4 * (kNChan + c));
         }
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
-    const uint32_t g = vb * kAttrWarps + (threadIdx.x >> 5);
+    const uint32_t g = vb * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (g >= p.G) return;
     // the group's rows, dealt round robin to its lanes: lane j holds rows R0 + j + k nl
     const uint32_t nl = min(32u, p.L - g * 32);
@@ -140,13 +152,14 @@ __device__ __forceinline__ void rans_attr_body(const AttrParams &p, uint32_t vb,
         const bool active = rr < my_rows;
         float *o = p.out + (IDX ? (active ? p.out_index[row] : 0u) : row);
         const uint32_t *cdf = s_cdf;
+        const uint8_t *lut = s_lut;
         for (int c0 = 0; c0 < kNChan; c0 += 8) {
 #pragma unroll
             for (int c = c0; c < c0 + 8; ++c) {
                 if (active) {
                     const uint32_t *tc = cdf + (c - c0) * kTabCdfWords;
                     const uint32_t slot = x & 0xFFFFu;
-                    const uint32_t sym = cdf_search(tc, slot);
+                    const uint32_t sym = lut_search(tc, lut + (c - c0) * kLutBuckets, slot);
                     const uint32_t lo = tc[sym], hi = tc[sym + 1];
                     x = (hi - lo) * (x >> 16) + slot - lo;
                     o[(size_t)c * p.n_rows] = dequant(sym, s_step[c], s_off[c]);
@@ -154,6 +167,7 @@ __device__ __forceinline__ void rans_attr_body(const AttrParams &p, uint32_t vb,
                 group_refill(gs, x, active);
             }
             cdf += 8 * kTabCdfWords;
+            lut += 8 * kLutBuckets;
         }
     }
     const bool bad = gs.bad || (lane < (int)nl && x != 0x10000u) || (gs.ptr != gs.n_words);
@@ -187,7 +201,21 @@ static uint32_t make_rans_attr(const uint8_t *bits, const sgs_scene_info &info, 
     p.out_index = out.out_index;
     p.status = status;
     if (info.n_rows == 0) return 0;
-    return (p.G + kAttrWarps - 1) / kAttrWarps;
+    return p.G;  // groups (warps); the launcher packs them into CTAs
+}
+
+// Warps per CTA of a single-scene static decode: as many as share one copy of the tables
+// (kAttrWarps) when there are groups enough for every SM, fewer so that few groups still
+// spread over the SMs (each decodes its lanes' long chains alone).
+static int attr_warps(uint32_t groups) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 148;
+    }
+    const uint32_t w = (groups + (uint32_t)sms - 1) / (uint32_t)sms;
+    return (int)(w < 1 ? 1 : (w > (uint32_t)kAttrWarps ? (uint32_t)kAttrWarps : w));
 }
 
 // Raises the dynamic shared memory limit of `kernel` once.
@@ -203,14 +231,16 @@ cudaError_t launch_rans_static_attr(const uint8_t *bits, const sgs_scene_info &i
                                     const uint8_t *tables, const sgs_scene_out &out, int *status,
                                     cudaStream_t st) {
     AttrParams p;
-    const uint32_t grid = make_rans_attr(bits, info, tables, out, status, &p);
-    if (grid == 0) return cudaSuccess;
+    const uint32_t groups = make_rans_attr(bits, info, tables, out, status, &p);
+    if (groups == 0) return cudaSuccess;
     static bool set0 = false, set1 = false;
     cudaError_t e = allow_smem(k_rans_attr<false>, kAttrSmem, &set0);
     if (e == cudaSuccess) e = allow_smem(k_rans_attr<true>, kAttrSmem, &set1);
     if (e != cudaSuccess) return e;
-    if (p.out_index) k_rans_attr<true><<<grid, 32 * kAttrWarps, kAttrSmem, st>>>(p);
-    else k_rans_attr<false><<<grid, 32 * kAttrWarps, kAttrSmem, st>>>(p);
+    const int w = attr_warps(groups);
+    const uint32_t grid = (groups + w - 1) / w;
+    if (p.out_index) k_rans_attr<true><<<grid, 32 * w, attr_smem(w), st>>>(p);
+    else k_rans_attr<false><<<grid, 32 * w, attr_smem(w), st>>>(p);
     return cudaGetLastError();
 }
 
@@ -228,17 +258,21 @@ struct GeoParams {
 };
 
 constexpr int kGeoWarps = 8;
-constexpr size_t kGeoTabSmem = (SGS_MAX_DEPTH * kTabCdfWords * 4 + 15) & ~size_t(15);
-static_assert(kGeoTabSmem % 16 == 0, "window must be 16-byte aligned");
+// Shared memory of the geometry decoder for nt coded levels: cdf [nt][257], lookup
+// [nt][1024], then one word-stream window per warp.
+__host__ __device__ constexpr size_t geo_cdf_smem(int nt) { return ((size_t)nt * kTabCdfWords * 4 + 15) & ~size_t(15); }
+__host__ __device__ constexpr size_t geo_tab_smem(int nt) { return geo_cdf_smem(nt) + (size_t)nt * kLutBuckets; }
+constexpr size_t kGeoTabSmem = geo_tab_smem(SGS_MAX_DEPTH);
 
 __device__ __forceinline__ void rans_geo_body(const GeoParams &p, uint32_t vb) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int nt = p.plan.n_coded_levels;
     uint32_t *s_cdf = (uint32_t *)smem;
-    uint16_t *s_win = reinterpret_cast<uint16_t *>(smem + kGeoTabSmem) + (threadIdx.x >> 5) * kWinWords;
+    uint8_t *s_lut = smem + geo_cdf_smem(nt);
+    uint16_t *s_win = reinterpret_cast<uint16_t *>(smem + geo_tab_smem(nt)) + (threadIdx.x >> 5) * kWinWords;
     __shared__ uint32_t s_start[SGS_MAX_DEPTH + 1];  // first coded token of each coded level
     __shared__ uint32_t s_dbase[SGS_MAX_DEPTH];      // BFS offset of its tokens minus that
-    load_cdf_smem(p.tables, nt, s_cdf);
+    load_cdf_smem(p.tables, nt, s_cdf, s_lut);
     if (threadIdx.x <= (unsigned)nt) s_start[threadIdx.x] = (uint32_t)p.plan.coded_start[threadIdx.x];
     if (threadIdx.x < (unsigned)nt)
         s_dbase[threadIdx.x] = (uint32_t)(p.plan.level_off[p.plan.coded_level[threadIdx.x]] -
@@ -264,6 +298,7 @@ __device__ __forceinline__ void rans_geo_body(const GeoParams &p, uint32_t vb) {
     int k = 0;
     while (k + 1 < nt && s_start[k + 1] <= i) ++k;
     const uint32_t *cdf = s_cdf + k * kTabCdfWords;
+    const uint8_t *lut = s_lut + k * kLutBuckets;
     uint32_t next = s_start[k + 1];
     uint32_t dbase = s_dbase[k];
     for (uint32_t t = 0; t < maxn; ++t) {
@@ -272,11 +307,12 @@ __device__ __forceinline__ void rans_geo_body(const GeoParams &p, uint32_t vb) {
             while (i >= next && k + 1 < nt) {
                 ++k;
                 cdf += kTabCdfWords;
+                lut += kLutBuckets;
                 next = s_start[k + 1];
                 dbase = s_dbase[k];
             }
             const uint32_t slot = x & 0xFFFFu;
-            const uint32_t sym = cdf_search(cdf, slot);
+            const uint32_t sym = lut_search(cdf, lut, slot);
             const uint32_t lo = cdf[sym], hi = cdf[sym + 1];
             x = (hi - lo) * (x >> 16) + slot - lo;
             p.geo_bytes[dbase + i] = (uint8_t)sym;
@@ -324,7 +360,8 @@ cudaError_t launch_rans_static_geo(const uint8_t *bits, const sgs_scene_info &in
     static bool set = false;
     cudaError_t e = allow_smem(k_rans_geo, kGeoSmem, &set);
     if (e != cudaSuccess) return e;
-    k_rans_geo<<<grid, 32 * kGeoWarps, kGeoSmem, st>>>(p);
+    const size_t smem = geo_tab_smem(plan.n_coded_levels) + kGeoWarps * kWinWords * 2;
+    k_rans_geo<<<grid, 32 * kGeoWarps, smem, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -407,9 +444,9 @@ uint32_t stage_rans_attr(const SceneRef &r, bool idx_variant, void *par) {
     if (r.info->mode != SGS_MODE_STATIC || (r.out->out_index != nullptr) != idx_variant) return 0;
     AttrParams p;
     const uint8_t *attr_tables = r.s->tables + (size_t)r.plan->n_coded_levels * kTabBytes;
-    const uint32_t n = make_rans_attr(r.bits, *r.info, attr_tables, *r.out, r.status, &p);
+    const uint32_t groups = make_rans_attr(r.bits, *r.info, attr_tables, *r.out, r.status, &p);
     memcpy(par, &p, sizeof(p));
-    return n;
+    return (groups + kAttrWarps - 1) / kAttrWarps;
 }
 size_t stage_rans_attr_bytes() { return sizeof(AttrParams); }
 cudaError_t launch_rans_attr_multi(bool idx, const MultiArgs &m, cudaStream_t st) {

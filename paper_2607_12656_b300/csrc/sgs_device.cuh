@@ -53,12 +53,31 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *to
     return wbase + incl - v;
 }
 
-// Copies the cdf[257] of n expanded tables into shared memory.
-__device__ __forceinline__ void load_cdf_smem(const uint8_t *tables, int n, uint32_t *s_cdf) {
+// Copies the cdf[257] of n expanded tables into shared memory (s_cdf [n][257]), and, if
+// s_lut is not NULL, their slot lookups (s_lut [n][kLutBuckets], 16-byte aligned).
+__device__ __forceinline__ void load_cdf_smem(const uint8_t *tables, int n, uint32_t *s_cdf, uint8_t *s_lut = nullptr) {
     for (int i = threadIdx.x; i < n * kTabCdfWords; i += blockDim.x) {
         const int t = i / kTabCdfWords, k = i - t * kTabCdfWords;
         s_cdf[i] = reinterpret_cast<const uint32_t *>(tables + (size_t)t * kTabBytes)[k];
     }
+    if (s_lut) {
+        constexpr int kV = kLutBuckets / 16;  // uint4 per table
+        for (int i = threadIdx.x; i < n * kV; i += blockDim.x) {
+            const int t = i / kV, k = i - t * kV;
+            reinterpret_cast<uint4 *>(s_lut)[i] =
+                reinterpret_cast<const uint4 *>(tables + (size_t)t * kTabBytes + kTabCdfBytes)[k];
+        }
+    }
+}
+
+// The symbol s with cdf[s] <= slot < cdf[s+1], starting from the bucket's first symbol: at
+// most the symbols that start inside slot's 64-slot bucket are stepped over (absent symbols,
+// whose cdf equals the next one's, included), so the loop ends below symbol 256 (cdf[256] =
+// 2^16 > slot).
+__device__ __forceinline__ uint32_t lut_search(const uint32_t *cdf, const uint8_t *lut, uint32_t slot) {
+    uint32_t s = lut[slot >> kLutShift];
+    while (cdf[s + 1] <= slot) ++s;
+    return s;
 }
 
 // The symbol s with cdf[s] <= slot < cdf[s+1] (cdf[0] = 0, cdf[256] = 2^16 > slot): the

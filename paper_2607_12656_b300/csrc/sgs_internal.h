@@ -34,9 +34,14 @@ constexpr int kMaxTables = kNChan + SGS_MAX_DEPTH;
 enum Sec { S_LEVELS = 0, S_DUP, S_CHAN, S_GEO_RAW, S_GEO_TAB, S_GEO_GRP, S_GEO_PAY, S_ATTR_TAB,
            S_ATTR_GRP, S_ATTR_PAY, S_TOTAL };
 
-// Expanded static table in device memory: cdf[257] (u32), padded to 16 bytes.
+// Expanded static table in device memory: cdf[257] (u32), padded to 16 bytes, then a slot
+// lookup lut[1024] (u8): lut[b] = the symbol whose range holds slot 64 b.  A slot's symbol is
+// lut[slot >> 6] or one of the symbols that start in the same 64-slot bucket after it.
 constexpr int kTabCdfWords = 257;
-constexpr int kTabBytes = (kTabCdfWords * 4 + 15) & ~15;  // 1040
+constexpr int kTabCdfBytes = (kTabCdfWords * 4 + 15) & ~15;  // 1040
+constexpr int kLutShift = 6;
+constexpr int kLutBuckets = 65536 >> kLutShift;              // 1024
+constexpr int kTabBytes = kTabCdfBytes + kLutBuckets;         // 2064
 
 // Per-level facts of one scene's octree, by value in kernel parameters.
 struct GeoPlan {

@@ -214,6 +214,45 @@ def test_deep_octrees(ctx, n, depth):
     check(ctx, sc, depth, mode=S.MODE_STATIC, lanes=7, geo_mode=S.GEO_RANS)
 
 
+def _scene_at(codes, depth, seed):
+    """A scene with one Gaussian at the centre of each voxel of Morton codes `codes` (plus
+    duplicates on a few of them), attributes from the generator."""
+    from paper_2607_12656_b300.scenegen import make_scene as mk
+    coord = S.demorton(np.asarray(codes, np.uint64), depth).astype(np.float64)  # [3][n]
+    rng = np.random.default_rng(seed)
+    extra = rng.integers(0, coord.shape[1], size=max(1, coord.shape[1] // 50))
+    coord = np.concatenate([coord, coord[:, extra]], axis=1)
+    pos = ((coord + 0.5) / float(1 << depth)).astype(np.float32)
+    sc = mk(pos.shape[1], seed)
+    sc.pos = np.ascontiguousarray(pos)
+    return sc
+
+
+def test_octree_dense_cluster_subtree(ctx):
+    """A dense cluster of 60,000 voxels under one node of the split level among 6,000 scattered
+    ones (depth 16): that node's subtree is wider than a CTA's shared memory, so its CTA falls
+    back to parent entries and a climb to the split level; every position still matches."""
+    rng = np.random.default_rng(0)
+    D = 16
+    sparse = rng.integers(0, 8 ** D, size=6000, dtype=np.uint64)
+    base = np.uint64(rng.integers(0, 8 ** 5)) << np.uint64(3 * (D - 5))
+    dense = base + rng.integers(0, 8 ** (D - 5), size=60000, dtype=np.uint64)
+    sc = _scene_at(np.unique(np.concatenate([sparse, dense])), D, 41)
+    check(ctx, sc, D, mode=S.MODE_FIXED, bits=fixed_bits(41), geo_mode=S.GEO_RAW)
+    check(ctx, sc, D, mode=S.MODE_STATIC, lanes=300, geo_mode=S.GEO_RANS)
+
+
+def test_octree_fan_and_chain(ctx):
+    """Depth 21: 40,000 voxels fanning out at level 7 and one isolated 21-level chain; a slab
+    boundary falls between very unequal subtrees."""
+    rng = np.random.default_rng(1)
+    D = 21
+    codes = np.unique(np.concatenate([rng.integers(0, 8 ** 7, size=40000, dtype=np.uint64) << np.uint64(3 * 14),
+                                      np.array([8 ** 21 - 1], np.uint64)]))
+    sc = _scene_at(codes, D, 42)
+    check(ctx, sc, D, mode=S.MODE_FIXED, bits=fixed_bits(42), geo_mode=S.GEO_RAW)
+
+
 def test_duplicates_with_scatter_and_coords(ctx):
     """Many Gaussians per voxel at a shallow depth, rows scattered by out_index, with voxel
     coordinates: each leaf writes all its rows."""
