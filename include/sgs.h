@@ -56,8 +56,9 @@ extern "C" {
 #define SGS_GEO_LEARNED 2     /* levels of >= 4096 nodes coded with a learned model of the
                                  level above (Eq. 8): context = (parent byte, child index),
                                  the SGS_MODEL_BYTES integer model with the level as its
-                                 channel.  scene_encode writes it; decoding it is not built
-                                 (scene_query answers SGS_E_UNSUPPORTED)                   */
+                                 channel; each coded level in lanes of about 128 tokens.
+                                 Decoded by scene_decode and scene_decode_noalloc (level by
+                                 level); a batch plan refuses it (SGS_E_UNSUPPORTED)        */
 
 #define SGS_NCHAN 56
 #define SGS_MAX_DEPTH 21
@@ -192,8 +193,9 @@ int sgs_set_wait_limit(sgs_ctx *ctx, uint32_t polls);
 /* Parses and validates the header of a bitstream (host bytes `bits`, `len` bytes, at least
  * the header and the level table; the section offsets are checked against total_len).
  * Definition of the fields: Sec. 3.4 split into geometry and attribute streams.
- * Errors: SGS_E_INVALID (short buffer, bad magic/version/sizes/offsets), SGS_E_UNSUPPORTED
- * (geometry coded with SGS_GEO_LEARNED, which no device decoder reads yet).                */
+ * Errors: SGS_E_INVALID (short buffer, bad magic/version/sizes/offsets, or, for
+ * SGS_GEO_LEARNED, a model section shorter than SGS_MODEL_BYTES or lanes and group tables
+ * that are not the coded levels' own), SGS_E_UNSUPPORTED (an octree beyond 2^29 nodes).    */
 int scene_query(const uint8_t *bits, size_t len, sgs_scene_info *info);
 
 /* Decodes one scene: occupancy tokens -> octree expansion (Sec. 3.4, Geometry Occupancy
@@ -253,7 +255,8 @@ typedef struct sgs_batch sgs_batch;
 
 /* Device bytes of a plan for these items (the scratch of every scene plus the work lists).
  * Errors: SGS_E_INVALID (NULL, misaligned bitstream, missing outputs, info not produced by
- * scene_query), SGS_E_UNSUPPORTED (more than 2^31 work items in a stage). */
+ * scene_query), SGS_E_UNSUPPORTED (more than 2^31 work items in a stage, or a scene whose
+ * geometry is SGS_GEO_LEARNED-coded: decode those with scene_decode). */
 int scene_batch_bytes(const sgs_batch_item *items, int n, size_t *bytes);
 
 /* Builds a plan on ctx's device: allocates its device block (cudaMalloc) and uploads the

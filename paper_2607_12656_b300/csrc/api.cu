@@ -39,7 +39,7 @@ void make_geo_plan(const sgs_scene_info &info, GeoPlan *plan) {
         plan->n_level[l] = info.n_level[l];
         plan->level_off[l] = off;
         off += info.n_level[l];
-        if (l < info.depth && info.geo_mode == SGS_GEO_RANS && info.n_level[l] >= kGeoRansMinLevel) {
+        if (l < info.depth && info.geo_mode != SGS_GEO_RAW && info.n_level[l] >= kGeoRansMinLevel) {
             plan->coded_level[k] = (int)l;
             plan->coded_start[k] = coded;
             coded += info.n_level[l];
@@ -47,6 +47,7 @@ void make_geo_plan(const sgs_scene_info &info, GeoPlan *plan) {
         }
     }
     plan->n_coded_levels = k;
+    plan->n_geo_tables = info.geo_mode == SGS_GEO_RANS ? k : 0;
     plan->coded_start[k] = coded;
 }
 
@@ -62,15 +63,16 @@ size_t scratch_need(const sgs_scene_info &info, Scratch *s, uint8_t *base) {
         return p;
     };
     Scratch t;
-    t.geo_bytes = take(info.geo_mode == SGS_GEO_RANS ? info.n_geo : 0);
+    t.geo_bytes = take(info.geo_mode != SGS_GEO_RAW ? info.n_geo : 0);
     t.p4 = reinterpret_cast<uint32_t *>(take(4 * (octree_words(info.n_geo) + 16)));
     t.tile_sums = reinterpret_cast<uint32_t *>(take(4 * (octree_scan_tiles(info.n_geo) + 1)));
     t.par = reinterpret_cast<uint32_t *>(take(info.n_rows ? 4ull * (info.n_geo + info.n_leaves) : 0));
-    const int n_tab = plan.n_coded_levels + (info.mode == SGS_MODE_STATIC ? kNChan : 0);
+    const int n_tab = plan.n_geo_tables + (info.mode == SGS_MODE_STATIC ? kNChan : 0);
     t.tables = take((uint64_t)n_tab * kTabBytes);
     t.dup_prefix = reinterpret_cast<uint32_t *>(take(4ull * (info.n_dup + 1)));
     t.learned = take(info.mode == SGS_MODE_LEARNED ? learned_work_bytes(info) : 0);
     t.coord = reinterpret_cast<uint32_t *>(take(info.mode == SGS_MODE_LEARNED_PE ? 12ull * info.n_rows : 0));
+    t.geo_work = take(info.geo_mode == SGS_GEO_LEARNED && info.n_geo_coded ? geo_learned_scratch(info, nullptr, nullptr) : 0);
     if (s) *s = t;
     return off;
 }
@@ -241,7 +243,6 @@ extern "C" int scene_query(const uint8_t *b, size_t len, sgs_scene_info *info) {
     info->total_len = info->off[S_TOTAL];
     if (n_chan != (uint32_t)kNChan || info->mode > SGS_MODE_LEARNED_PE || info->geo_mode > SGS_GEO_LEARNED)
         return SGS_E_INVALID;
-    if (info->geo_mode == SGS_GEO_LEARNED) return SGS_E_UNSUPPORTED;  // no device decoder for it
     if (info->depth < 1 || info->depth > SGS_MAX_DEPTH) return SGS_E_INVALID;
     if (info->total_len != len) return SGS_E_INVALID;
     if (info->off[0] != (uint64_t)kHeaderBytes) return SGS_E_INVALID;
@@ -257,7 +258,7 @@ extern "C" int scene_query(const uint8_t *b, size_t len, sgs_scene_info *info) {
     for (uint32_t l = 0; l < D; ++l) {
         info->n_level[l] = rd32(b + info->off[S_LEVELS] + 4 * l);
         sum += info->n_level[l];
-        if (info->geo_mode == SGS_GEO_RANS && info->n_level[l] >= kGeoRansMinLevel)
+        if (info->geo_mode != SGS_GEO_RAW && info->n_level[l] >= kGeoRansMinLevel)
             coded += info->n_level[l];
         if (l > 0 && info->n_level[l] < info->n_level[l - 1]) return SGS_E_INVALID;  // every node has >= 1 child
         if (l > 0 && (uint64_t)info->n_level[l] > 8ull * info->n_level[l - 1]) return SGS_E_INVALID;
@@ -277,7 +278,17 @@ extern "C" int scene_query(const uint8_t *b, size_t len, sgs_scene_info *info) {
     // geometry sections
     uint64_t raw = info->n_geo - info->n_geo_coded;
     if (sec(S_GEO_RAW) < raw) return SGS_E_INVALID;
-    if (info->n_geo_coded) {
+    if (info->n_geo_coded && info->geo_mode == SGS_GEO_LEARNED) {
+        // one model, then per coded level a group table (its lanes fixed by its size)
+        uint64_t lanes = 0, grp = 0;
+        for (uint32_t l = 0; l < D; ++l)
+            if (info->n_level[l] >= kGeoRansMinLevel) {
+                lanes += geo_learned_lanes(info->n_level[l]);
+                grp += geo_learned_group_bytes(info->n_level[l]);
+            }
+        if (info->geo_lanes != lanes || sec(S_GEO_TAB) < (uint64_t)SGS_MODEL_BYTES || sec(S_GEO_GRP) < grp)
+            return SGS_E_INVALID;
+    } else if (info->n_geo_coded) {
         if (info->geo_lanes == 0) return SGS_E_INVALID;
         const uint64_t G = (info->geo_lanes + 31) / 32;
         if (sec(S_GEO_GRP) < 8 * (G + 1) + 4 * G) return SGS_E_INVALID;
@@ -342,10 +353,10 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
     mark();
     if (info.n_tables) {
         c->launches += 1;
-        e = launch_tables(bits, info, plan.n_coded_levels, s.tables, status, st);
+        e = launch_tables(bits, info, plan.n_geo_tables, s.tables, status, st);
         if (e != cudaSuccess) return SGS_E_CUDA;
     }
-    uint8_t *attr_tables = s.tables + (size_t)plan.n_coded_levels * kTabBytes;
+    uint8_t *attr_tables = s.tables + (size_t)plan.n_geo_tables * kTabBytes;
     // fork: attributes on the attribute stream, geometry on the geometry stream
     if (cudaEventRecord(c->fork, st) != cudaSuccess || cudaStreamWaitEvent(c->aux, c->fork, 0) != cudaSuccess ||
         cudaStreamWaitEvent(c->geo, c->fork, 0) != cudaSuccess)
@@ -358,6 +369,12 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
         if ((e = launch_rans_static_geo(bits, info, plan, s.tables, s.geo_bytes, status, gs)) != cudaSuccess)
             return SGS_E_CUDA;
         c->launches += 2;
+    } else if (info.geo_mode == SGS_GEO_LEARNED && info.n_geo) {
+        if ((e = launch_geo_copy_raw(bits, info, plan, s.geo_bytes, gs)) != cudaSuccess) return SGS_E_CUDA;
+        int n = 1;
+        if ((e = launch_geo_learned(bits, info, plan, s.geo_bytes, s.geo_work, status, gs, &n)) != cudaSuccess)
+            return SGS_E_CUDA;
+        c->launches += n;
     }
     if (!after_geo) {
         if (c->profile) cudaEventRecord(c->amarks[0], c->aux);

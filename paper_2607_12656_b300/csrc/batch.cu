@@ -152,6 +152,8 @@ static int build_layout(const sgs_batch_item *items, int n, uint8_t *base, Batch
         const sgs_batch_item &it = items[i];
         if (!it.bits_dev || ((uintptr_t)it.bits_dev & 15)) return SGS_E_INVALID;
         if (it.info.n_rows && (!it.out.attr || !it.out.pos)) return SGS_E_INVALID;
+        // learned geometry decodes level by level (a launch sequence per scene): scene_decode only
+        if (it.info.geo_mode == SGS_GEO_LEARNED && it.info.n_geo_coded) return SGS_E_UNSUPPORTED;
         const size_t need = scratch_need(it.info, nullptr, nullptr);
         if (need != it.info.scratch_bytes) return SGS_E_INVALID;  // info not from scene_query
         scratch_need(it.info, &L->scratch[i], base ? base + off : nullptr);

@@ -355,9 +355,9 @@ __global__ void __launch_bounds__(kWalkThreads) k_octree_walk_multi(MultiArgs m)
 // ------------------------------------------------------------------ parameters
 
 // The token array the octree kernels read: the stream's raw section, or the scratch copy
-// the geometry decoder filled when levels are rANS-coded.
+// the geometry decoder filled when levels are coded (static or learned).
 static const uint8_t *geo_tokens(const uint8_t *bits, const sgs_scene_info &info, const Scratch &s) {
-    return (info.geo_mode == SGS_GEO_RANS && info.n_geo) ? s.geo_bytes : bits + info.off[S_GEO_RAW];
+    return (info.geo_mode != SGS_GEO_RAW && info.n_geo) ? s.geo_bytes : bits + info.off[S_GEO_RAW];
 }
 
 static LeafOut make_leaf(const uint8_t *bits, const sgs_scene_info &info, const Scratch &s,

@@ -414,7 +414,7 @@ static uint32_t make_geo_copy(const uint8_t *bits, const sgs_scene_info &info, c
     }
     p.raw = bits + info.off[S_GEO_RAW];
     p.geo_bytes = geo_bytes;
-    if (info.geo_mode != SGS_GEO_RANS || info.n_geo == 0 || rc.n == 0 || rc.src[rc.n] == 0) return 0;
+    if (info.geo_mode == SGS_GEO_RAW || info.n_geo == 0 || rc.n == 0 || rc.src[rc.n] == 0) return 0;
     return (uint32_t)((rc.src[rc.n] + kCopyBytes - 1) / kCopyBytes);
 }
 
@@ -431,7 +431,7 @@ cudaError_t launch_geo_copy_raw(const uint8_t *bits, const sgs_scene_info &info,
 
 uint32_t stage_tables(const SceneRef &r, void *par) {
     TableParams p;
-    const uint32_t n = make_tables(r.bits, *r.info, r.plan->n_coded_levels, r.s->tables, r.status, &p);
+    const uint32_t n = make_tables(r.bits, *r.info, r.plan->n_geo_tables, r.s->tables, r.status, &p);
     memcpy(par, &p, sizeof(p));
     return n;
 }
@@ -443,7 +443,7 @@ cudaError_t launch_tables_multi(const MultiArgs &m, cudaStream_t st) {
 uint32_t stage_rans_attr(const SceneRef &r, bool idx_variant, void *par) {
     if (r.info->mode != SGS_MODE_STATIC || (r.out->out_index != nullptr) != idx_variant) return 0;
     AttrParams p;
-    const uint8_t *attr_tables = r.s->tables + (size_t)r.plan->n_coded_levels * kTabBytes;
+    const uint8_t *attr_tables = r.s->tables + (size_t)r.plan->n_geo_tables * kTabBytes;
     const uint32_t groups = make_rans_attr(r.bits, *r.info, attr_tables, *r.out, r.status, &p);
     memcpy(par, &p, sizeof(p));
     return (groups + kAttrWarps - 1) / kAttrWarps;

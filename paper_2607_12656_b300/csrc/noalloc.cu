@@ -82,8 +82,8 @@ extern "C" int scene_decode_noalloc(const uint8_t *bits, const sgs_scene_info *i
         cudaStreamSynchronize(st);
         return SGS_E_CUDA;
     };
-    if (launch_tables(bits, *info, plan.n_coded_levels, s.tables, status, st) != cudaSuccess) return fail();
-    uint8_t *attr_tables = s.tables + (size_t)plan.n_coded_levels * kTabBytes;
+    if (launch_tables(bits, *info, plan.n_geo_tables, s.tables, status, st) != cudaSuccess) return fail();
+    uint8_t *attr_tables = s.tables + (size_t)plan.n_geo_tables * kTabBytes;
     const sgs_scene_out o = effective_out(*info, *out, s);
     cudaError_t e = cudaSuccess;
     switch (info->mode) {
@@ -96,6 +96,10 @@ extern "C" int scene_decode_noalloc(const uint8_t *bits, const sgs_scene_info *i
     if (info->geo_mode == SGS_GEO_RANS && info->n_geo) {
         if (launch_geo_copy_raw(bits, *info, plan, s.geo_bytes, st) != cudaSuccess) return fail();
         if (launch_rans_static_geo(bits, *info, plan, s.tables, s.geo_bytes, status, st) != cudaSuccess)
+            return fail();
+    } else if (info->geo_mode == SGS_GEO_LEARNED && info->n_geo) {
+        if (launch_geo_copy_raw(bits, *info, plan, s.geo_bytes, st) != cudaSuccess) return fail();
+        if (launch_geo_learned(bits, *info, plan, s.geo_bytes, s.geo_work, status, st, nullptr) != cudaSuccess)
             return fail();
     }
     if (launch_octree(*info, plan, bits, s, o, status, st) != cudaSuccess) return fail();

@@ -47,6 +47,7 @@ constexpr int kTabBytes = kTabCdfBytes + kLutBuckets;         // 2064
 struct GeoPlan {
     int depth;
     int n_coded_levels;
+    int n_geo_tables;                        // static geometry tables (n_coded_levels for rANS, else 0)
     uint32_t n_level[SGS_MAX_DEPTH + 1];     // [D] = leaves
     uint64_t level_off[SGS_MAX_DEPTH + 1];   // global BFS index of each level's first node
     int coded_level[SGS_MAX_DEPTH];          // coded level ids, ascending
@@ -64,6 +65,7 @@ struct Scratch {
     uint8_t *learned;       // learned-mode per-scene work area
     uint32_t *coord;        // position-aware mode: voxel coordinates [3][n_rows] when the
                             // caller asks for none (the attribute model reads them)
+    uint8_t *geo_work;      // learned geometry: context tables, contexts, scan tile sums
 };
 
 size_t scratch_need(const sgs_scene_info &info, Scratch *layout, uint8_t *base);
@@ -85,6 +87,13 @@ cudaError_t launch_rans_static_geo(const uint8_t *bits, const sgs_scene_info &in
                                    int *status, cudaStream_t st);
 cudaError_t launch_geo_copy_raw(const uint8_t *bits, const sgs_scene_info &info,
                                 const GeoPlan &plan, uint8_t *geo_bytes, cudaStream_t st);
+// Learned geometry (SGS_GEO_LEARNED): the coded levels' tokens into geo_bytes, level by level
+// (the raw levels copied there first); work = Scratch::geo_work.  *launches += kernels.
+cudaError_t launch_geo_learned(const uint8_t *bits, const sgs_scene_info &info, const GeoPlan &plan,
+                               uint8_t *geo_bytes, uint8_t *work, int *status, cudaStream_t st, int *launches);
+uint64_t geo_learned_scratch(const sgs_scene_info &info, uint64_t *tab_bytes, uint64_t *ctx_bytes);
+uint32_t geo_learned_lanes(uint64_t n);
+uint64_t geo_learned_group_bytes(uint64_t n);
 // The octree reads the raw token section, or the scratch copy of the geometry decoder when
 // levels are rANS-coded.  Scan with parent scatter, then the leaf walk, on st.
 cudaError_t launch_octree(const sgs_scene_info &info, const GeoPlan &plan, const uint8_t *bits,

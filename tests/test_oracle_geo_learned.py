@@ -124,8 +124,8 @@ def test_trained_model_codes_above_the_conditional_entropy(geo_scene):
 @pytest.mark.parametrize("seed", [0, 1])
 def test_library_encoder_bytes_equal_oracle(geo_scene, seed):
     """The library's host encoder writes the oracle's bytes for learned geometry (any valid
-    integer model; fixed-length and static attributes), and scene_query refuses the stream,
-    whose device decoder is not built."""
+    integer model; fixed-length and static attributes), and scene_query reads the stream's
+    header facts (its coded levels and their lanes) for the device decoder."""
     from paper_2607_12656_b300 import sgs
     from paper_2607_12656_b300.scenegen import fixed_bits
     sc, P = geo_scene
@@ -140,9 +140,11 @@ def test_library_encoder_bytes_equal_oracle(geo_scene, seed):
     got = sgs.scene_encode(sc.pos, sc.attr, mode=sgs.MODE_FIXED, depth=12, bits=fixed_bits(2),
                            geo_mode=sgs.GEO_LEARNED, geo_model=S.model_bytes(m))
     assert got == want
-    with pytest.raises(sgs.SgsError) as e:
-        sgs.scene_query(got)
-    assert e.value.code == sgs.E_UNSUPPORTED
+    info = sgs.scene_query(got)
+    h = S.parse_header(got)
+    assert info.geo_mode == sgs.GEO_LEARNED and info.n_geo_coded == h["n_geo_coded"] > 0
+    assert info.geo_lanes == sum(S.geo_lanes_for_level(len(b)) for b, c in
+                                 zip(Pf.levels, S.geo_plan(Pf.levels, S.GEO_LEARNED)) if c)
 
 
 def test_library_encoder_trained_geometry_model(geo_scene):
