@@ -8,9 +8,9 @@
 //   R = floor(65280 * 2^32 / sum e),  f_k = 1 + floor(e_k R / 2^32),  remainder to argmax z.
 //
 // Decoder: one CTA per group of 32 lanes, walking the group's tokens in stream order
-// (Gaussian i, channel c): 12 producer warps compute the steps' cumulative tables ahead of
-// one consumer warp that advances the 32 rANS states and refills them from the group's
-// shared word stream (details at the pipeline's constants below).
+// (Gaussian i, channel c).  Layer 3 of 128 contexts at a time runs on the fifth-generation
+// tensor cores (tcgen05) into tensor memory, where a thread reads its context's 256 logits as
+// one row; a consumer warp advances the 32 rANS states (roles at the decoder's constants below).
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -22,6 +22,7 @@
 #include "exp2q_table.h"
 #include "sgs_device.cuh"
 #include "sgs_mma.cuh"
+#include "sgs_tc.cuh"
 #include "sgs_internal.h"
 
 namespace sgs {
@@ -52,27 +53,16 @@ __device__ __forceinline__ int32_t requant(int32_t acc, int32_t m, int32_t sh) {
     return (int32_t)(v > 127 ? 127 : v);
 }
 
-// Layers 2-3 on the tensor cores in bf16 with fp32 accumulation.  This is exact: int8
-// weights and activations in [0, 127] are exact in bf16, their products exact in fp32, and
-// every partial sum of 64 products is an integer below 2^21 < 2^24.  (B300 has no tcgen05
-// int8 kind and a far slower int8 mma path.)
-constexpr int kBS = 72;  // smem row stride in bf16 elements (64 used): conflict-free fragments
+// Layers 2 and 3 run on the tensor cores in bf16 with fp32 accumulation, and exactly so:
+// int8 weights and activations in [0, 127] are exact in bf16, their products exact in fp32,
+// and every partial sum of layer 2 (64 products) is an integer below 2^21.  Layer 3
+// accumulates onto 1.5 2^23 in tensor memory, so every partial sum lies in [2^23, 2^24),
+// where fp32 holds every integer, and the result's bit pattern is 0x4B400000 + the sum.
+// (B300 has no tcgen05 int8 kind.)
+constexpr int kBS = 72;  // layer-2 weight rows in shared memory (bf16, 64 used): conflict-free
 
 __device__ __forceinline__ uint32_t lds32(const __nv_bfloat16 *p) {
     return *reinterpret_cast<const uint32_t *>(p);
-}
-
-// The four A fragments of one m16n8k16 tile (16 x 16 bf16, row-major, rows kBS apart) with
-// one ldmatrix: lane L gives the address of row (L & 7) + 8 ((L >> 3) & 1), columns
-// 8 (L >> 4) .. +7, of the tile starting at A.
-__device__ __forceinline__ void ldsm_a(const __nv_bfloat16 *A, uint32_t &a0, uint32_t &a1, uint32_t &a2,
-                                       uint32_t &a3) {
-    const int lane = threadIdx.x & 31;
-    const __nv_bfloat16 *p = A + ((lane & 7) + 8 * ((lane >> 3) & 1)) * kBS + 8 * (lane >> 4);
-    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
-                 : "r"(addr));
 }
 
 struct LearnedParams {
@@ -85,50 +75,60 @@ struct LearnedParams {
     uint32_t wait_limit;  // polls of each bounded mbarrier wait before it gives up
 };
 
-// Pipelined decoder: kPW producer warps compute the frequency tables of the steps (Gaussian i,
-// channel c) ahead of one consumer warp that runs the group's 32 rANS chains.  Each producer
-// warp owns 8 of a step's 32 contexts and computes them end to end on its own -- layer 1 on
-// the ALU, layers 2-3 as bf16 mma.sync with the contexts as the N dimension, the integer
-// softmax reduced with shuffles among the 8 lanes that share a context -- so producers never
-// synchronise with each other.  Four warps make one step; the kPW warps work on kSW steps
-// at once, writing u16 cumulative tables into a ring of kNB steps.  The context of step (i, c)
-// needs only (i-1 .. i-4, c), at least 56 steps back, so the ring's release by the consumer
-// also publishes the tokens a producer reads.  Hand-offs are mbarriers with bounded waits.
-constexpr int kPW = 12;                  // producer warps
-constexpr int kPT = 32 * kPW;            // producer threads
-constexpr int kLT = kPT + 32;            // + consumer warp
-constexpr int kNB = 7;                   // ring depth (steps)
-constexpr int kQW = 4;                   // warps per step (8 contexts each)
-constexpr int kSW = kPW / kQW;           // steps in flight
+// Decoder: one CTA per group of 32 lanes.  A tile is the 128 contexts of 4 channels x 32 lanes
+// at one row i (tile (i, j): channels 4 j .. 4 j + 3), TMEM lane 32 q + l = channel 4 j + q of
+// lane l.  Roles:
+//   warp 0      the consumer: the group's 32 rANS chains in stream order (i, c), each step's
+//               32 tables read from a ring of kNS steps; it writes the tokens, the outputs and
+//               the token history the contexts of later rows read;
+//   warp 1      allocates the tensor memory; its lane 0 issues layer 3 of every tile;
+//   warps 2-5   layers 1 and 2 of a tile, warp w taking channel 4 j + w: layer 1 on the ALU,
+//               layer 2 as mma.sync, requantised into the tile's bf16 operand of layer 3;
+//   warps 6-13  two softmax teams: team T takes the tiles of parity T, their logits in tensor
+//               memory columns 256 T .. 256 T + 255.  A thread per context makes three passes
+//               over its row (max; e_k and their sum; floor terms and cumulative table) and
+//               writes the context's table without the remainder, with a record (argmax,
+//               remainder) that the consumer applies when it looks a slot up.
+// Tile (i, j) needs rows i-1 .. i-4 of its channels: the consumer publishes row i-1 of a
+// channel quad with one mbarrier per quad.  Hand-offs are mbarriers with bounded waits.
+constexpr int kNQ = kNChan / 4;        // tiles per row
+constexpr int kNS = 8;                 // table ring (steps): step (i, c) uses slot c % 8
+constexpr int kWL12 = 2;               // first layer-1/2 warp
+constexpr int kWTeam = 6;              // first softmax warp
+constexpr int kLT = 14 * 32;           // threads
+constexpr int kCS = 264;               // table row stride (u16): 528-byte rows spread the banks
 constexpr uint32_t kWaitLimit = kDefaultWaitPolls;
-constexpr int kCS = 264;                 // cdf row stride (u16): rows 528 B apart spread the banks
-static_assert(kNB >= kSW && kNB <= kNChan, "ring");
+constexpr uint32_t kAccBias = 0x4B400000u;  // bit pattern of 1.5 2^23
+// A row has kNChan = 56 steps, a multiple of the ring, so a step's slot is c % 8; a row has
+// an even number of tiles, so tile (i, j) goes to team j % 2 and its channels to slots
+// 4 (j % 2) .. 4 (j % 2) + 3: each team owns four slots.
+static_assert(kNChan % kNS == 0 && kNQ % 2 == 0 && kNS == 8, "ring layout");
 
-struct LSmem2 {
-    int8_t w1[64 * 4];
-    int32_t b1[kNChan * 64];
-    alignas(16) __nv_bfloat16 w2[64 * kBS];
-    int32_t b2[64];
-    alignas(16) __nv_bfloat16 w3[256 * kBS];
-    int32_t b3m[256];                           // b3 - 0x4B400000 (see layer 3)
-    uint32_t etab[kETop + 1];                   // e(t), t = 0 .. kETop
-    alignas(16) __nv_bfloat16 h2t[kPW][8 * kBS];  // per warp: layer-2 output, [context][unit]
-    uint8_t ctx[32 * 4 * kNChan];               // [lane][ring row][channel]
-    alignas(16) uint16_t cdf[kNB][32][kCS];     // cumulative frequency of each symbol
-    alignas(16) uint16_t win[kWinWords];        // consumer's word-stream window
-    uint32_t nrows[32];
+struct LSmem3 {
+    alignas(1024) uint8_t w3t[256 * 64 * 2];  // layer 3 B operand: W3 (symbol x unit), canonical layout
+    alignas(1024) uint8_t at[128 * 64 * 2];   // layer 3 A operand: one tile's h2 (context x unit)
+    alignas(16) __nv_bfloat16 w2[64 * kBS];   // W2 (out x in) for layer 2's B fragments
+    alignas(16) int32_t b3m[256];             // b3 - 0x4B400000
+    int32_t b2m[64];                          // b2 - 0x4B400000
+    alignas(16) int8_t w1[64 * 4];
+    uint32_t etab[kETop + 1];                 // e(t), t = 0 .. kETop
+    uint8_t ctx[32 * 4 * kNChan];             // token history [lane][row % 4][channel]
+    alignas(16) uint16_t cdf[kNS][32][kCS];   // cumulative table without the remainder
+    uint2 meta[kNS][32];                      // (cdf[a] | (f_a + r) << 16, r | a << 16), a = argmax
+    alignas(16) uint16_t win[kWinWords];      // consumer's word-stream window
     uint64_t row0[32];
+    uint32_t nrows[32];
     float step[kNChan], offset[kNChan];
-    alignas(8) uint64_t full[kNB], empty[kNB];
-    int32_t m1, sh1, m2, sh2;
-    uint32_t ms, ss;
-    uint32_t dcap;  // smallest d with (d ms) >> ss >= kETop, saturated at 2^32 - 1
+    alignas(8) uint64_t a_full, a_empty, t_full[2], t_empty[2], c_full[kNS], c_empty[kNS], tok[kNQ];
+    int32_t m1, sh1, m2, sh2, ahi1, ahi2;
+    uint32_t ms, ss, dcap, mq;
     int bad;
     int abort_;
+    uint32_t tmem;
 };
-static_assert(offsetof(LSmem2, cdf) % 16 == 0 && offsetof(LSmem2, win) % 16 == 0 &&
-              offsetof(LSmem2, h2t) % 16 == 0, "alignment");
-static_assert(sizeof(LSmem2) <= 227 * 1024, "shared memory");
+static_assert(offsetof(LSmem3, at) % 1024 == 0 && offsetof(LSmem3, cdf) % 16 == 0 &&
+              offsetof(LSmem3, win) % 16 == 0 && offsetof(LSmem3, b3m) % 16 == 0, "alignment");
+static_assert(sizeof(LSmem3) + 256 <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -150,17 +150,58 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait for the phase of `parity` to complete: at most `limit` polls; false on
-// timeout or abort.
+// timeout or abort (abort_ may be NULL: then only the limit ends it).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_,
                                           uint32_t limit) {
     for (uint32_t it = 0; it < limit; ++it) {
         if (mbar_test(bar, parity)) return true;
-        if (*abort_) return false;
+        if (abort_ && *abort_) return false;
         if (it > 64) __nanosleep(64);
     }
     return false;
 }
-__device__ bool load_model2(LSmem2 &S, const uint8_t *m, int *status) {
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Requantisation rq(a) = clamp((a m + 2^(sh-1)) >> sh, 0, 127) (m >= 0, 1 <= sh <= 47), on a
+// clamped to [0, ahi]: every a <= 0 gives 0, and ahi is the least a giving 127 or more, so the
+// shifted sum stays below 2^32 and the 64-bit shift is one funnel shift and one shift.
+struct Rq {
+    uint64_t half;
+    uint32_t m, sh_lo, sh_hi;
+    int32_t ahi;
+};
+__device__ __forceinline__ Rq make_rq(int32_t m, int32_t sh, int32_t ahi) {
+    Rq q;
+    q.half = 1ull << (sh - 1);
+    q.m = (uint32_t)m;
+    q.sh_lo = (uint32_t)min(sh, 32);
+    q.sh_hi = (uint32_t)max(sh - 32, 0);
+    q.ahi = ahi;
+    return q;
+}
+__device__ __forceinline__ uint32_t rq32(int32_t a, const Rq &q) {
+    const uint32_t ac = (uint32_t)min(max(a, 0), q.ahi);
+    const uint64_t P = (uint64_t)ac * q.m + q.half;
+    const uint32_t v = __funnelshift_rc((uint32_t)P, (uint32_t)(P >> 32), q.sh_lo) >> q.sh_hi;
+    return min(v, 127u);
+}
+// The least a >= 0 with (a m + 2^(sh-1)) >> sh >= 127, capped at 2^31 - 1.
+__device__ __forceinline__ int32_t rq_ahi(int32_t m, int32_t sh) {
+    if (m <= 0) return 0x7FFFFFFF;
+    const uint64_t need = 253ull << (sh - 1);  // 127 2^sh - 2^(sh-1)
+    const uint64_t a = (need + (uint64_t)m - 1) / (uint64_t)m;
+    return a > 0x7FFFFFFFull ? 0x7FFFFFFF : (int32_t)a;
+}
+
+// Two integers in [0, 127] as a bf16 pair, the first in the low half.
+__device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn((float)lo, (float)hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+__device__ bool load_model3(LSmem3 &S, const uint8_t *m, int *status) {
     const int tid = threadIdx.x;
     if (tid == 0) {
         const int32_t *h = reinterpret_cast<const int32_t *>(m);
@@ -171,6 +212,12 @@ __device__ bool load_model2(LSmem2 &S, const uint8_t *m, int *status) {
         if (!S.bad) {
             const uint64_t dc = (((uint64_t)kETop << S.ss) + S.ms - 1) / S.ms;
             S.dcap = dc > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)dc;
+            // t = floor(d ms / 2^ss) = floor(d mq / 2^32) when ms < 2^ss (then t rises by at
+            // most 1 per unit of d, so t(dcap) = kETop exactly); else mq = 0 and t is taken in 64
+            // bits and clamped
+            S.mq = (S.ss >= 1 && S.ms < (1u << S.ss)) ? (S.ms << (32 - S.ss)) : 0u;
+            S.ahi1 = rq_ahi(S.m1, S.sh1);
+            S.ahi2 = rq_ahi(S.m2, S.sh2);
         }
         S.abort_ = 0;
     }
@@ -178,22 +225,21 @@ __device__ bool load_model2(LSmem2 &S, const uint8_t *m, int *status) {
     const int32_t *b2 = reinterpret_cast<const int32_t *>(m + kMB_B2);
     const int32_t *b3 = reinterpret_cast<const int32_t *>(m + kMB_B3);
     bool badb = false;
-    for (int i = tid; i < kNChan * 64; i += kLT) {
-        S.b1[i] = b1[i];
-        badb |= (b1[i] >= (1 << 24) || b1[i] <= -(1 << 24));
-    }
+    for (int i = tid; i < kNChan * 64; i += kLT) badb |= (b1[i] >= (1 << 24) || b1[i] <= -(1 << 24));
     for (int i = tid; i < 64; i += kLT) {
-        S.b2[i] = b2[i];
+        S.b2m[i] = b2[i] - (int32_t)kAccBias;
         badb |= (b2[i] >= (1 << 24) || b2[i] <= -(1 << 24));
     }
     for (int i = tid; i < 256; i += kLT) {
-        S.b3m[i] = b3[i] - 0x4B400000;
+        S.b3m[i] = b3[i] - (int32_t)kAccBias;
         badb |= (b3[i] >= (1 << 24) || b3[i] <= -(1 << 24));
         S.w1[i] = (int8_t)m[kMB_W1 + i];
     }
     for (int t = tid; t <= kETop; t += kLT) S.etab[t] = kExp2Q[t & 255] >> (t >> 8);
     for (int i = tid; i < 64 * 64; i += kLT) S.w2[(i >> 6) * kBS + (i & 63)] = bf((int8_t)m[kMB_W2 + i]);
-    for (int i = tid; i < 256 * 64; i += kLT) S.w3[(i >> 6) * kBS + (i & 63)] = bf((int8_t)m[kMB_W3 + i]);
+    for (int i = tid; i < 256 * 64; i += kLT)
+        *reinterpret_cast<__nv_bfloat16 *>(S.w3t + tc_off(i >> 6, i & 63)) = bf((int8_t)m[kMB_W3 + i]);
+    tc_fence_proxy();  // W3 is read by the tensor cores
     __syncthreads();
     if (badb) atomicOr(&S.bad, 1);
     __syncthreads();
@@ -204,238 +250,297 @@ __device__ bool load_model2(LSmem2 &S, const uint8_t *m, int *status) {
     return true;
 }
 
-// One warp's share of step (i, c): the frequency tables of lanes 8q .. 8q+7 into cdf[b].
-// mma.sync m16n8k16 fragments: lane = 4 g + t; A rows g, g+8, B column g, D rows g, g+8 x
-// columns 2t, 2t+1.  Layers 2 and 3 compute W h^T, so the 8 contexts are the columns.
-__device__ __forceinline__ void produce_pass(LSmem2 &S, uint32_t i, int c, int b, int q) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    // ---- layer 1 for context g: the 16 units this lane feeds into layer 2's B fragments
-    uint32_t bf2[4][2];
-    {
-        const int L = 8 * q + g;
-        // u_j = token_{i-j} - 128 as packed int8 (0 before the lane's first row)
-        uint32_t up = 0;
+// Every lane's wait, agreed across the warp; on failure the first lane raises the abort.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *abort_, const LearnedParams &p) {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, parity, abort_, p.wait_limit));
+    if (!ok && (threadIdx.x & 31) == 0) {
+        if (!*abort_) set_status(p.status, SGS_E_TIMEOUT);
+        *abort_ = 1;
+    }
+    return ok;
+}
+
+// ---- layers 1-2: warp w makes rows 32 w .. 32 w + 31 of the operand (channel 4 j + w).
+// mma.sync m16n8k16 with the contexts as M: lane 4 g + t holds contexts 16 mt + g (+ 8) and
+// layer-1 units 16 kt + 8 h + 2 t + e (its A fragments); layer 2's accumulators hold the same
+// contexts at out units 8 nt + 2 t + e.
+__device__ void l12_run(const LearnedParams &p, LSmem3 &S, uint32_t NT, volatile int *abort_) {
+    const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) - kWL12;
+    const int g = lane >> 2, t4 = lane & 3;
+    const Rq R1 = make_rq(S.m1, S.sh1, S.ahi1), R2 = make_rq(S.m2, S.sh2, S.ahi2);
+    const int32_t *w1w = reinterpret_cast<const int32_t *>(S.w1);
+    const int32_t *B1 = reinterpret_cast<const int32_t *>(p.bits + p.model_off + kMB_B1);
+    int32_t w1r[4][2][2], b2r[8][2];
 #pragma unroll
-        for (int j = 1; j <= 4; ++j) {
-            const uint32_t tok = (i >= (uint32_t)j) ? S.ctx[(L * 4 + ((i - j) & 3)) * kNChan + c] : 128u;
-            up |= (tok ^ 0x80u) << (8 * (j - 1));
-        }
-        const int32_t *b1 = S.b1 + c * 64;
-        const int32_t *w1 = reinterpret_cast<const int32_t *>(S.w1);  // row o: 4 int8 weights
-        const int32_t m1 = S.m1, sh1 = S.sh1;
+    for (int kt = 0; kt < 4; ++kt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) w1r[kt][h][e] = w1w[16 * kt + 8 * h + 2 * t4 + e];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) b2r[nt][e] = S.b2m[8 * nt + 2 * t4 + e];
+    for (uint32_t tau = 0; tau < NT; ++tau) {
+        const uint32_t i = tau / kNQ, j = tau - i * kNQ;
+        const int c = 4 * (int)j + w;
+        if (i >= 1 && !warp_wait(&S.tok[j], (i - 1) & 1, abort_, p)) break;
+        if (tau >= 1 && !warp_wait(&S.a_empty, (tau - 1) & 1, abort_, p)) break;
+        int32_t b1r[4][2][2];
 #pragma unroll
         for (int kt = 0; kt < 4; ++kt)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                int32_t v[2];
+            for (int h = 0; h < 2; ++h)
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int o = 16 * kt + 8 * h + 2 * t + e;
-                    v[e] = requant(__dp4a(w1[o], (int32_t)up, b1[o]), m1, sh1);
+                for (int e = 0; e < 2; ++e) b1r[kt][h][e] = __ldg(B1 + c * 64 + 16 * kt + 8 * h + 2 * t4 + e);
+        // layer 1 into A fragments: afr[mt][kt][r + 2 h] = units 16 kt + 8 h + 2 t4 (+1) of
+        // context 16 mt + 8 r + g
+        uint32_t afr[2][4][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int l = 16 * mt + 8 * r + g;
+                uint32_t up = 0;  // u_jj = token_{i-jj} - 128 as packed int8, 0 before the lane's start
+#pragma unroll
+                for (int jj = 1; jj <= 4; ++jj) {
+                    const uint32_t tok = (i >= (uint32_t)jj) ? S.ctx[(l * 4 + ((i - jj) & 3)) * kNChan + c] : 128u;
+                    up |= (tok ^ 0x80u) << (8 * (jj - 1));
                 }
-                bf2[kt][h] = pack_bf16(v[0], v[1]);
-            }
-    }
-    // ---- layer 2: D[unit][context] = W2 h1^T; requantised into this warp's transpose buffer
-    __nv_bfloat16 *h2t = S.h2t[warp];
-    {
-        const int32_t m2 = S.m2, sh2 = S.sh2;
 #pragma unroll
-        for (int mt = 0; mt < 4; ++mt) {
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int kt = 0; kt < 4; ++kt)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t v0 = rq32(__dp4a(w1r[kt][h][0], (int32_t)up, b1r[kt][h][0]), R1);
+                        const uint32_t v1 = rq32(__dp4a(w1r[kt][h][1], (int32_t)up, b1r[kt][h][1]), R1);
+                        afr[mt][kt][r + 2 * h] = pack2(v0, v1);
+                    }
+            }
+        // layer 2, requantised into the operand tile
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            uint32_t bfr[4][2];
 #pragma unroll
             for (int kt = 0; kt < 4; ++kt) {
-                uint32_t a0, a1, a2, a3;
-                ldsm_a(S.w2 + 16 * mt * kBS + 16 * kt, a0, a1, a2, a3);
-                mma_bf16(acc, a0, a1, a2, a3, bf2[kt][0], bf2[kt][1]);
-            }
-            const int r0 = 16 * mt + g, r1 = r0 + 8;
-            h2t[(2 * t) * kBS + r0] = bf(requant(__float2int_rn(acc[0]) + S.b2[r0], m2, sh2));
-            h2t[(2 * t + 1) * kBS + r0] = bf(requant(__float2int_rn(acc[1]) + S.b2[r0], m2, sh2));
-            h2t[(2 * t) * kBS + r1] = bf(requant(__float2int_rn(acc[2]) + S.b2[r1], m2, sh2));
-            h2t[(2 * t + 1) * kBS + r1] = bf(requant(__float2int_rn(acc[3]) + S.b2[r1], m2, sh2));
-        }
-    }
-    __syncwarp();
-    uint32_t bf3[4][2];
-#pragma unroll
-    for (int kt = 0; kt < 4; ++kt) {
-        bf3[kt][0] = lds32(h2t + g * kBS + 16 * kt + 2 * t);
-        bf3[kt][1] = lds32(h2t + g * kBS + 16 * kt + 2 * t + 8);
-    }
-    // ---- layer 3: z[symbol][context]; this lane holds symbols 16 mt + g (+8) of contexts
-    //      2t (z[mt][0], z[mt][2]) and 2t+1 (z[mt][1], z[mt][3])
-    int32_t z[16][4];
-#pragma unroll
-    for (int mt = 0; mt < 16; ++mt) {
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt) {
-            uint32_t a0, a1, a2, a3;
-            ldsm_a(S.w3 + 16 * mt * kBS + 16 * kt, a0, a1, a2, a3);
-            mma_bf16(acc, a0, a1, a2, a3, bf3[kt][0], bf3[kt][1]);
-        }
-        // acc is an integer of magnitude below 2^21, so acc + 1.5 2^23 is exact and its bit
-        // pattern is 0x4B400000 + acc: the conversion is one full-rate add
-        const int32_t b30 = S.b3m[16 * mt + g], b31 = S.b3m[16 * mt + g + 8];
-#pragma unroll
-        for (int v = 0; v < 4; ++v)
-            z[mt][v] = __float_as_int(__fadd_rn(acc[v], 12582912.0f)) + (v < 2 ? b30 : b31);
-    }
-    // ---- integer softmax of contexts 2t (e = 0) and 2t+1 (e = 1); the 8 lanes g = 0..7 with
-    //      this t hold all 256 symbols of both
-    int32_t zmax[2], amax[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        zmax[e] = z[0][e];
-        amax[e] = g;
-#pragma unroll
-        for (int mt = 0; mt < 16; ++mt)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int32_t v = z[mt][2 * h + e];
-                const int32_t k = 16 * mt + 8 * h + g;  // ascending over (mt, h): strict > keeps the lowest
-                if (v > zmax[e]) { zmax[e] = v; amax[e] = k; }
+                const __nv_bfloat16 *wr = S.w2 + (8 * nt + g) * kBS + 16 * kt + 2 * t4;
+                bfr[kt][0] = lds32(wr);
+                bfr[kt][1] = lds32(wr + 8);
             }
 #pragma unroll
-        for (int o = 4; o < 32; o <<= 1) {
-            const int32_t om = __shfl_xor_sync(0xffffffffu, zmax[e], o);
-            const int32_t oa = __shfl_xor_sync(0xffffffffu, amax[e], o);
-            if (om > zmax[e] || (om == zmax[e] && oa < amax[e])) { zmax[e] = om; amax[e] = oa; }
-        }
-    }
-    // e_k = etab[min((min(d_k, dcap) ms) >> ss, kETop)]: for d_k >= dcap both t_k and the
-    // clamped t are at least kETop, where e vanishes; below dcap the product shifted by ss is
-    // under 2^32 and the clamp does nothing.  z is overwritten with e_k.
-    const uint32_t ms = S.ms, ss = S.ss, dcap = S.dcap;
-    uint32_t E[2] = {0u, 0u};
+            for (int mt = 0; mt < 2; ++mt) {
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int mt = 0; mt < 16; ++mt)
+                for (int kt = 0; kt < 4; ++kt)
+                    mma_bf16(acc, afr[mt][kt][0], afr[mt][kt][1], afr[mt][kt][2], afr[mt][kt][3], bfr[kt][0], bfr[kt][1]);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int e = v & 1;
-            const uint32_t d = min((uint32_t)(zmax[e] - z[mt][v]), dcap);
-            const uint32_t tt = (uint32_t)(((uint64_t)d * ms) >> ss);
-            const uint32_t ek = S.etab[min(tt, (uint32_t)kETop)];
-            z[mt][v] = (int32_t)ek;
-            E[e] += ek;
-        }
-    uint32_t R[2], Tf[2] = {0u, 0u};
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-#pragma unroll
-        for (int o = 4; o < 32; o <<= 1) E[e] += __shfl_xor_sync(0xffffffffu, E[e], o);
-        R[e] = (uint32_t)((65280ull << 32) / E[e]);
-    }
-    // f_k = 1 + floor(e_k R / 2^32) stored in symbol order; their sum gives the remainder,
-    // which one lane per context then adds at the argmax
-    uint16_t *cdfw = &S.cdf[b][8 * q][0];  // this warp's 8 contexts, rows kCS apart
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        uint16_t *row = cdfw + (2 * t + e) * kCS;
-#pragma unroll
-        for (int mt = 0; mt < 16; ++mt)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t f = __umulhi((uint32_t)z[mt][2 * h + e], R[e]) + 1u;
-                Tf[e] += f;
-                row[16 * mt + 8 * h + g] = (uint16_t)f;
+                for (int r = 0; r < 2; ++r) {
+                    // acc is an integer below 2^21 in magnitude: acc + 1.5 2^23 is exact and
+                    // its bit pattern is 0x4B400000 + acc
+                    const uint32_t v0 = rq32(__float_as_int(__fadd_rn(acc[2 * r], 12582912.0f)) + b2r[nt][0], R2);
+                    const uint32_t v1 = rq32(__float_as_int(__fadd_rn(acc[2 * r + 1], 12582912.0f)) + b2r[nt][1], R2);
+                    const int l = 16 * mt + 8 * r + g;
+                    *reinterpret_cast<uint32_t *>(S.at + tc_off(32 * w + l, 8 * nt + 2 * t4)) = pack2(v0, v1);
+                }
             }
-    }
-    uint32_t pk[2];  // (remainder << 8) | argmax of context 2t + e
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-#pragma unroll
-        for (int o = 4; o < 32; o <<= 1) Tf[e] += __shfl_xor_sync(0xffffffffu, Tf[e], o);
-        pk[e] = ((65536u - Tf[e]) << 8) | (uint32_t)amax[e];
-    }
-    {
-        // context n = lane (lanes 0..7) is held by the lanes with t = n / 2, component n % 2
-        const uint32_t p0 = __shfl_sync(0xffffffffu, pk[0], (lane & 7) >> 1);
-        const uint32_t p1 = __shfl_sync(0xffffffffu, pk[1], (lane & 7) >> 1);
-        const uint32_t p = (lane & 1) ? p1 : p0;
+        }
+        tc_fence_proxy();
         __syncwarp();
-        if (lane < 8) {
-            uint16_t *fa = cdfw + lane * kCS + (p & 255u);
-            *fa = (uint16_t)(*fa + (p >> 8));  // f <= 65281
-        }
-    }
-    __syncwarp();
-    {
-        // lane -> context lane & 7, quarter lane >> 3 (64 symbols, 8 uint4); the 8 lanes of a
-        // quarter-warp touch 8 rows at the same column: 528-byte rows put them in 8 bank groups
-        const int n = lane & 7, qq = lane >> 3;
-        uint16_t *seg = cdfw + n * kCS + qq * 64;
-        // Every f >= 1 and a context's f sum to 2^16, so the even and the odd halves of a
-        // segment each sum below 2^16: the words add without carries between the halves, and
-        // so do the two halves of one word (f0 + f1 < 2^16).
-        uint4 w[8];
-        uint32_t sw = 0;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            w[j] = reinterpret_cast<const uint4 *>(seg)[j];
-            sw += (w[j].x + w[j].y) + (w[j].z + w[j].w);
-        }
-        const uint32_t sum = (sw & 0xFFFFu) + (sw >> 16);
-        uint32_t incl = sum;  // scan over the 4 quarters of context n (lanes n, n+8, n+16, n+24)
-        const uint32_t n1 = __shfl_up_sync(0xffffffffu, incl, 8);
-        if (qq >= 1) incl += n1;
-        const uint32_t n2 = __shfl_up_sync(0xffffffffu, incl, 16);
-        if (qq >= 2) incl += n2;
-        uint32_t run = incl - sum;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            uint32_t *h = reinterpret_cast<uint32_t *>(&w[j]);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                // (run, run + f0) with run + f0 <= 65535 below symbol 256; then run += f0 + f1
-                const uint32_t hv = h[k];
-                h[k] = run * 0x10001u + (hv << 16);
-                run += (hv * 0x10001u) >> 16;
-            }
-            reinterpret_cast<uint4 *>(seg)[j] = w[j];
-        }
+        if (lane == 0) mbar_arrive(&S.a_full);
     }
 }
 
-// The consumer warp: the group's 32 rANS chains over K steps.
-__device__ __forceinline__ void consume(const LearnedParams &p, LSmem2 &S, uint32_t grp, int nl,
-                                        uint32_t K, volatile int *abort_) {
+// ---- layer 3 issue (one thread)
+__device__ void mma_run(const LearnedParams &p, LSmem3 &S, uint32_t NT, volatile int *abort_) {
+    const uint32_t idesc = tc_idesc_bf16(128, 256);
+    const uint32_t a0 = smem_addr(S.at), b0 = smem_addr(S.w3t);
+    uint32_t issued = 0;
+    for (uint32_t tau = 0; tau < NT; ++tau) {
+        const int T = (int)(tau & 1);
+        const uint32_t n = tau >> 1;
+        bool ok = mbar_wait(&S.a_full, tau & 1, abort_, p.wait_limit) &&
+                  mbar_wait(&S.t_empty[T], n & 1, abort_, p.wait_limit);
+        if (!ok) {
+            if (!*abort_) set_status(p.status, SGS_E_TIMEOUT);
+            *abort_ = 1;
+            break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+            tc_mma_bf16(S.tmem + 256u * T, tc_desc(a0 + 256u * kk), tc_desc(b0 + 256u * kk), idesc, 1u);
+        tc_commit(&S.t_full[T]);
+        tc_commit(&S.a_empty);
+        ++issued;
+    }
+    // the last commit's arrival (its tile's and every earlier tile's work complete) precedes
+    // the CTA's next use of the barriers and the release of the tensor memory, also after an
+    // abort: an issued MMA ends within microseconds, so this wait keeps the default limit
+    // whatever limit the caller set for the hand-offs
+    if (issued && !mbar_wait(&S.a_empty, (issued - 1) & 1, nullptr, kWaitLimit)) {
+        set_status(p.status, SGS_E_TIMEOUT);
+        *abort_ = 1;
+    }
+}
+
+// ---- softmax teams
+__device__ __forceinline__ int32_t max32(const uint32_t (&v)[32]) {
+    int32_t m[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) m[j] = max((int32_t)v[j], (int32_t)v[j + 16]);
+#pragma unroll
+    for (int s = 8; s > 0; s >>= 1)
+#pragma unroll
+        for (int j = 0; j < s; ++j) m[j] = max(m[j], m[j + s]);
+    return m[0];
+}
+
+// The team's columns start at 1.5 2^23 for the next tile's layer 3; then the buffer is free.
+__device__ __forceinline__ void team_release(LSmem3 &S, uint32_t tb, int T) {
+    uint32_t v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = kAccBias;
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) tc_st32(tb + 32 * ch, v);
+    tc_wait_st();
+    tc_fence_before();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&S.t_empty[T]);
+}
+
+template <bool kSmallScale>
+__device__ void team_run(const LearnedParams &p, LSmem3 &S, int T, uint32_t NT, volatile int *abort_) {
+    const int lane = threadIdx.x & 31, q = (threadIdx.x >> 5) & 3;
+    const uint32_t tb = tc_taddr(S.tmem, q, 256u * T);
+    const uint32_t dcap = S.dcap, mq = S.mq, ms = S.ms, ss = S.ss;
+    const int4 *b3v = reinterpret_cast<const int4 *>(S.b3m);
+    team_release(S, tb, T);
+    for (uint32_t tau = T; tau < NT; tau += 2) {
+        if (!warp_wait(&S.t_full[T], (tau >> 1) & 1, abort_, p)) break;
+        tc_fence_after();
+        uint32_t v[32];
+        // pass 1: z = logit (bias added), written back; zmax
+        int32_t zmax = INT32_MIN;
+#pragma unroll 1
+        for (int ch = 0; ch < 8; ++ch) {
+            tc_ld32(tb + 32 * ch, v);
+            tc_wait_ld();
+#pragma unroll
+            for (int j4 = 0; j4 < 8; ++j4) {
+                const int4 b = b3v[8 * ch + j4];
+                v[4 * j4] += b.x; v[4 * j4 + 1] += b.y; v[4 * j4 + 2] += b.z; v[4 * j4 + 3] += b.w;
+            }
+            zmax = max(zmax, max32(v));
+            tc_st32(tb + 32 * ch, v);
+        }
+        tc_wait_st();
+        // pass 2: e_k = etab[t(min(zmax - z_k, dcap))] (e vanishes from d = dcap on), their
+        // sum, and the lowest k with z_k = zmax (symbols visited in descending order)
+        const int64_t zl = (int64_t)zmax - (int64_t)dcap;
+        const int32_t zlo = zl < (int64_t)INT32_MIN ? INT32_MIN : (int32_t)zl;
+        uint32_t E = 0, am = 0;
+#pragma unroll 1
+        for (int ch = 7; ch >= 0; --ch) {
+            tc_ld32(tb + 32 * ch, v);
+            tc_wait_ld();
+#pragma unroll
+            for (int j = 31; j >= 0; --j) {
+                const int32_t z = (int32_t)v[j];
+                const uint32_t d = (uint32_t)(zmax - max(z, zlo));
+                if (z == zmax) am = 32 * ch + j;
+                uint32_t t;
+                if (kSmallScale) t = __umulhi(d, mq);
+                else t = min((uint32_t)(((uint64_t)d * ms) >> ss), (uint32_t)kETop);
+                v[j] = S.etab[t];
+                E += v[j];
+            }
+            tc_st32(tb + 32 * ch, v);
+        }
+        tc_wait_st();
+        const uint32_t R = (uint32_t)((65280ull << 32) / E);  // E >= e(0) = 2^23
+        // pass 3: cumulative table of f_k = 1 + floor(e_k R / 2^32), without the remainder
+        const uint32_t i = tau / kNQ, jq = tau - i * kNQ;
+        const uint32_t c = 4 * jq + q, k = i * kNChan + c, slot = c % kNS, u = k / kNS;
+        if (u >= 1 && !warp_wait(&S.c_empty[slot], (u - 1) & 1, abort_, p)) break;
+        uint16_t *row = &S.cdf[slot][lane][0];
+        uint32_t run = 0;
+#pragma unroll 1
+        for (int ch = 0; ch < 8; ++ch) {
+            tc_ld32(tb + 32 * ch, v);
+            tc_wait_ld();
+#pragma unroll
+            for (int o = 0; o < 32; o += 8) {
+                uint32_t wv[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const uint32_t c0 = run;
+                    run += __umulhi(v[o + 2 * h], R) + 1u;
+                    const uint32_t c1 = run;
+                    run += __umulhi(v[o + 2 * h + 1], R) + 1u;
+                    wv[h] = __byte_perm(c0, c1, 0x5410);
+                }
+                *reinterpret_cast<uint4 *>(row + 32 * ch + o) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            }
+        }
+        // the remainder r = 2^16 - sum f goes to the argmax: its interval becomes
+        // [cdf[a], cdf[a + 1] + r) and every later entry moves up by r
+        const uint32_t r = 65536u - run;
+        const uint32_t lo_a = row[am], nx = am < 255 ? row[am + 1] : run;
+        S.meta[slot][lane] = make_uint2(lo_a | ((nx - lo_a + r) << 16), r | (am << 16));
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.c_full[slot]);
+        team_release(S, tb, T);
+    }
+}
+
+// Symbol of `y` (the state's low 16 bits) under a table without its remainder and the
+// record (cdf[a], f_a + r, r, a): slots inside a's widened interval are a's; above it the
+// table is searched for y - r and the interval moved up by r.
+__device__ __forceinline__ uint32_t table_sym(const uint16_t *row, uint2 mt, uint32_t y, uint32_t &lo, uint32_t &hi) {
+    const uint32_t lo_a = mt.x & 0xFFFFu, fr = mt.x >> 16, r = mt.y & 0xFFFFu, a = mt.y >> 16;
+    const bool in_a = (y - lo_a) < fr;
+    const bool up = y >= lo_a + fr;
+    const uint32_t y2 = up ? y - r : y;
+    uint32_t s = 0;
+#pragma unroll
+    for (uint32_t st = 128; st > 0; st >>= 1) s += (row[s + st] <= y2) ? st : 0u;
+    uint32_t l = row[s], h = s < 255 ? row[s + 1] : 65536u - r;
+    if (up) { l += r; h += r; }
+    if (in_a) { s = a; l = lo_a; h = lo_a + fr; }
+    lo = l;
+    hi = h;
+    return s;
+}
+
+__device__ void consume3(const LearnedParams &p, LSmem3 &S, uint32_t grp, int nl, uint32_t K,
+                         uint32_t maxrows, volatile int *abort_) {
     const int lane = threadIdx.x & 31;
     GroupStream gs;
     uint32_t x = 0x10000u;
     group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, grp, nl, lane, gs, x, S.win);
     bool aborted = false;
     for (uint32_t k = 0; k < K; ++k) {
-        const int b = (int)(k % kNB);
-        // every lane acquires the producers' release of buffer b
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(&S.full[b], (k / kNB) & 1, abort_, p.wait_limit));
-        if (!ok) {
-            if (lane == 0) { *abort_ = 1; set_status(p.status, SGS_E_TIMEOUT); }
+        const uint32_t i = k / kNChan, c = k - i * kNChan, slot = c % kNS;
+        if (!warp_wait(&S.c_full[slot], (k / kNS) & 1, abort_, p)) {
             aborted = true;
             break;
         }
-        const uint32_t i = k / kNChan;
-        const int c = (int)(k - i * kNChan);
         const bool live = lane < nl && i < S.nrows[lane];
         if (live) {
-            const uint32_t slot = x & 0xFFFFu;
-            const uint16_t *cdf = S.cdf[b][lane];
-            uint32_t s = 0;
-#pragma unroll
-            for (uint32_t st = 128; st > 0; st >>= 1)
-                if (cdf[s + st] <= slot) s += st;
-            const uint32_t lo = cdf[s];
-            const uint32_t hi = s < 255 ? cdf[s + 1] : 65536u;
-            x = (hi - lo) * (x >> 16) + slot - lo;
+            const uint32_t y = x & 0xFFFFu;
+            uint32_t lo, hi;
+            const uint32_t s = table_sym(S.cdf[slot][lane], S.meta[slot][lane], y, lo, hi);
+            x = (hi - lo) * (x >> 16) + y - lo;
             S.ctx[(lane * 4 + (i & 3)) * kNChan + c] = (uint8_t)s;
             const uint64_t row = S.row0[lane] + i;
             const uint64_t col = p.out_index ? (uint64_t)p.out_index[row] : row;
             p.out[(uint64_t)c * p.n_rows + col] = dequant(s, S.step[c], S.offset[c]);
         }
         group_refill(gs, x, live);
-        if (k + kNB < K) mbar_arrive(&S.empty[b]);
+        __syncwarp();
+        if (lane == 0) {
+            if (k + kNS < K) mbar_arrive(&S.c_empty[slot]);
+            if ((c & 3) == 3 && i + 1 < maxrows) mbar_arrive(&S.tok[c >> 2]);
+        }
     }
     if (!aborted) {
         const bool bad = gs.bad || (lane < nl && x != 0x10000u) || (gs.ptr != gs.n_words);
@@ -443,19 +548,31 @@ __device__ __forceinline__ void consume(const LearnedParams &p, LSmem2 &S, uint3
     }
 }
 
-__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
-    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+// Tensor memory of the CTA: 512 columns (two teams x 256), allocated by warp 1.  One CTA fits
+// an SM (the shared memory above), so the allocation never waits for another CTA's.
+__device__ __forceinline__ void learned_tmem_alloc(LSmem3 &S) {
+    if ((threadIdx.x >> 5) == 1) tc_alloc(&S.tmem, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+__device__ __forceinline__ void learned_tmem_free(LSmem3 &S) {
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if ((threadIdx.x >> 5) == 1) {
+        __syncwarp();
+        tc_dealloc(S.tmem, 512);
+    }
 }
 
 // One group of 32 lanes.  reload = false: the CTA's previous group was of the same scene,
 // whose model is still in shared memory (S.bad records whether it was refused).
-__device__ __forceinline__ void learned_body(const LearnedParams &p, uint32_t grp, bool reload) {
-    extern __shared__ __align__(16) uint8_t smem_raw[];
-    LSmem2 &S = *reinterpret_cast<LSmem2 *>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+__device__ __forceinline__ void learned_body(const LearnedParams &p, LSmem3 &S, uint32_t grp, bool reload) {
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int nl = (int)min(32u, p.L - grp * 32);
     if (reload) {
-        if (!load_model2(S, p.bits + p.model_off, p.status)) return;
+        if (!load_model3(S, p.bits + p.model_off, p.status)) return;
     } else {
         if (S.bad) return;
         if (tid == 0) S.abort_ = 0;
@@ -474,53 +591,71 @@ __device__ __forceinline__ void learned_body(const LearnedParams &p, uint32_t gr
         S.row0[tid] = r0;
         S.nrows[tid] = (uint32_t)(r1 - r0);
     }
-    for (int i = tid; i < 32 * 4 * kNChan; i += kLT) S.ctx[i] = 0;
     if (tid == 0) {
-        for (int b = 0; b < kNB; ++b) {
-            mbar_init(&S.full[b], 32 * kQW);  // every lane of the step's producer warps
-            mbar_init(&S.empty[b], 32);       // every consumer lane
+        mbar_init(&S.a_full, 4);
+        mbar_init(&S.a_empty, 1);
+        for (int T = 0; T < 2; ++T) {
+            mbar_init(&S.t_full[T], 1);
+            mbar_init(&S.t_empty[T], 4);
         }
+        for (int b = 0; b < kNS; ++b) {
+            mbar_init(&S.c_full[b], 1);
+            mbar_init(&S.c_empty[b], 1);
+        }
+        for (int b = 0; b < kNQ; ++b) mbar_init(&S.tok[b], 1);
     }
     __syncthreads();
     uint32_t maxrows = 0;
     for (int r = 0; r < 32; ++r) maxrows = max(maxrows, S.nrows[r]);
-    const uint32_t K = maxrows * kNChan;  // steps
+    const uint32_t K = maxrows * kNChan, NT = maxrows * kNQ;
     volatile int *abort_ = &S.abort_;
-
-    if (warp < kPW) {
-        // ---------------- producers: warp w makes contexts 8 (w % 4) .. +7 of steps w / 4 + 4 j
-        const int q = warp % kQW;
-        for (uint32_t k = warp / kQW; k < K; k += kSW) {
-            const int b = (int)(k % kNB);
-            // every lane acquires the consumer's release of buffer b (and with it the tokens
-            // the consumer wrote into the context ring)
-            const bool ok = k < (uint32_t)kNB || mbar_wait(&S.empty[b], ((k / kNB) - 1) & 1, abort_, p.wait_limit);
-            if (!__all_sync(0xffffffffu, ok)) {
-                if (lane == 0) { *abort_ = 1; set_status(p.status, SGS_E_TIMEOUT); }
-                break;
-            }
-            const uint32_t i = k / kNChan;
-            produce_pass(S, i, (int)(k - i * kNChan), b, q);
-            mbar_arrive(&S.full[b]);
-        }
+    if (warp == 0) {
+        consume3(p, S, grp, nl, K, maxrows, abort_);
+    } else if (warp == 1) {
+        if ((tid & 31) == 0) mma_run(p, S, NT, abort_);
+    } else if (warp < kWTeam) {
+        l12_run(p, S, NT, abort_);
     } else {
-        consume(p, S, grp, nl, K, abort_);
+        const int T = (warp - kWTeam) >> 2;
+        if (S.mq) team_run<true>(p, S, T, NT, abort_);
+        else team_run<false>(p, S, T, NT, abort_);
     }
     // every hand-off is over: retire the barriers (a persistent CTA initialises them again)
+    tc_fence_before();
     __syncthreads();
-    if (tid == 0)
-        for (int b = 0; b < kNB; ++b) {
-            mbar_inval(&S.full[b]);
-            mbar_inval(&S.empty[b]);
+    tc_fence_after();
+    if (tid == 0) {
+        mbar_inval(&S.a_full);
+        mbar_inval(&S.a_empty);
+        for (int T = 0; T < 2; ++T) {
+            mbar_inval(&S.t_full[T]);
+            mbar_inval(&S.t_empty[T]);
         }
+        for (int b = 0; b < kNS; ++b) {
+            mbar_inval(&S.c_full[b]);
+            mbar_inval(&S.c_empty[b]);
+        }
+        for (int b = 0; b < kNQ; ++b) mbar_inval(&S.tok[b]);
+    }
+    __syncthreads();
 }
 
-__global__ void __launch_bounds__(kLT, 1) k_learned_decode(LearnedParams p) { learned_body(p, blockIdx.x, true); }
+__global__ void __launch_bounds__(kLT, 1) k_learned_decode(LearnedParams p) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    LSmem3 &S = *reinterpret_cast<LSmem3 *>(smem_raw);
+    learned_tmem_alloc(S);
+    learned_body(p, S, blockIdx.x, true);
+    learned_tmem_free(S);
+}
 
 __global__ void __launch_bounds__(kLT, 1) k_learned_multi(MultiArgs m) {
-    run_items<LearnedParams>(m, [](const LearnedParams &p, uint32_t vb, uint32_t, bool same) {
-        learned_body(p, vb, !same);
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    LSmem3 &S = *reinterpret_cast<LSmem3 *>(smem_raw);
+    learned_tmem_alloc(S);
+    run_items<LearnedParams>(m, [&S](const LearnedParams &p, uint32_t vb, uint32_t, bool same) {
+        learned_body(p, S, vb, !same);
     });
+    learned_tmem_free(S);
 }
 
 size_t learned_work_bytes(const sgs_scene_info &) { return 0; }
@@ -548,7 +683,7 @@ static uint32_t make_learned(const uint8_t *bits, const sgs_scene_info &info, co
 
 static cudaError_t learned_smem_limit(const void *kernel, bool *done) {
     if (*done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LSmem2));
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LSmem3));
     if (e == cudaSuccess) *done = true;
     return e;
 }
@@ -562,7 +697,7 @@ cudaError_t launch_learned_decode(const uint8_t *bits, const sgs_scene_info &inf
     static bool set = false;
     cudaError_t e = learned_smem_limit(reinterpret_cast<const void *>(k_learned_decode), &set);
     if (e != cudaSuccess) return e;
-    k_learned_decode<<<grid, kLT, sizeof(LSmem2), st>>>(p);
+    k_learned_decode<<<grid, kLT, sizeof(LSmem3), st>>>(p);
     return cudaGetLastError();
 }
 
@@ -578,7 +713,7 @@ cudaError_t launch_learned_multi(const MultiArgs &m, cudaStream_t st) {
     static bool set = false;
     cudaError_t e = learned_smem_limit(reinterpret_cast<const void *>(k_learned_multi), &set);
     if (e != cudaSuccess) return e;
-    return launch_persistent(k_learned_multi, kLT, sizeof(LSmem2), m, st);
+    return launch_persistent(k_learned_multi, kLT, sizeof(LSmem3), m, st);
 }
 
 // ------------------------------------------------------------------ encoder side
