@@ -83,52 +83,67 @@ struct LearnedParams {
 //               the token history the contexts of later rows read;
 //   warp 1      allocates the tensor memory; its lane 0 issues layer 3 of every tile;
 //   warps 2-5   layers 1 and 2 of a tile, warp w taking channel 4 j + w: layer 1 on the ALU,
-//               layer 2 as mma.sync, requantised into the tile's bf16 operand of layer 3;
+//               layer 2 as mma.sync, requantised into one of two bf16 operand buffers of
+//               layer 3 (tile t uses buffer t % 2), so they run up to two tiles ahead;
 //   warps 6-13  two softmax teams: team T takes the tiles of parity T, their logits in tensor
 //               memory columns 256 T .. 256 T + 255.  A thread per context makes three passes
 //               over its row (max; e_k and their sum; floor terms and cumulative table) and
 //               writes the context's table without the remainder, with a record (argmax,
 //               remainder) that the consumer applies when it looks a slot up.
 // Tile (i, j) needs rows i-1 .. i-4 of its channels: the consumer publishes row i-1 of a
-// channel quad with one mbarrier per quad.  Hand-offs are mbarriers with bounded waits.
+// channel quad with one mbarrier per quad, and every step it finishes with a counter that
+// the teams read before they overwrite a table slot.  Waits are bounded.
+//
+// Two exact shortcuts apply when the model's integers allow them (checked per model; the
+// general forms run otherwise): with |b3| < 2^21 the layer-3 bias is preloaded into the
+// accumulator with the 1.5 2^23 offset, so the logits arrive biased; with sh <= 32, m <= 2^sh
+// (both requantisations) and |b2| < 2^21, layer 2's bias enters the mma.sync accumulator the
+// same way and each requantisation is one clamp, one wide multiply-add and one funnel shift.
 constexpr int kNQ = kNChan / 4;        // tiles per row
-constexpr int kNS = 8;                 // table ring (steps): step (i, c) uses slot c % 8
+constexpr int kNS = 6;                 // table ring (steps): step k uses slot k % kNS
+constexpr int kNA = 2;                 // layer-3 operand buffers
 constexpr int kWL12 = 2;               // first layer-1/2 warp
 constexpr int kWTeam = 6;              // first softmax warp
 constexpr int kLT = 14 * 32;           // threads
 constexpr int kCS = 264;               // table row stride (u16): 528-byte rows spread the banks
 constexpr uint32_t kWaitLimit = kDefaultWaitPolls;
 constexpr uint32_t kAccBias = 0x4B400000u;  // bit pattern of 1.5 2^23
-// A row has kNChan = 56 steps, a multiple of the ring, so a step's slot is c % 8; a row has
-// an even number of tiles, so tile (i, j) goes to team j % 2 and its channels to slots
-// 4 (j % 2) .. 4 (j % 2) + 3: each team owns four slots.
-static_assert(kNChan % kNS == 0 && kNQ % 2 == 0 && kNS == 8, "ring layout");
+constexpr int32_t kFastBias = 1 << 21;      // |bias| below this keeps every partial sum in [2^23, 2^24)
+// A row has an even number of tiles, so tile (i, j) goes to team j % 2 and to operand
+// buffer j % 2.
+static_assert(kNQ % 2 == 0 && kNA == 2, "tile parity");
 
-struct LSmem3 {
-    alignas(1024) uint8_t w3t[256 * 64 * 2];  // layer 3 B operand: W3 (symbol x unit), canonical layout
-    alignas(1024) uint8_t at[128 * 64 * 2];   // layer 3 A operand: one tile's h2 (context x unit)
-    alignas(16) __nv_bfloat16 w2[64 * kBS];   // W2 (out x in) for layer 2's B fragments
-    alignas(16) int32_t b3m[256];             // b3 - 0x4B400000
-    int32_t b2m[64];                          // b2 - 0x4B400000
+struct LSmem4 {
+    alignas(1024) uint8_t w3t[256 * 64 * 2];     // layer 3 B operand: W3 (symbol x unit), canonical layout
+    alignas(1024) uint8_t at[kNA][128 * 64 * 2]; // layer 3 A operands: a tile's h2 (context x unit)
+    alignas(16) __nv_bfloat16 w2[64 * kBS];      // W2 (out x in) for layer 2's B fragments
+    alignas(16) int32_t b3m[256];                // b3 - 0x4B400000 (general form: added in pass 1)
+    alignas(16) uint32_t b3f[256];               // 0x4B400000 + b3: 1.5 2^23 + b3 as fp32 bits
+    float b2f[64];                               // 1.5 2^23 + b2 (layer 2 accumulator input)
+    int32_t b2m[64];                             // b2 - 0x4B400000 (general form)
+    int32_t b1[kNChan * 64];
     alignas(16) int8_t w1[64 * 4];
-    uint32_t etab[kETop + 1];                 // e(t), t = 0 .. kETop
-    uint8_t ctx[32 * 4 * kNChan];             // token history [lane][row % 4][channel]
-    alignas(16) uint16_t cdf[kNS][32][kCS];   // cumulative table without the remainder
-    uint2 meta[kNS][32];                      // (cdf[a] | (f_a + r) << 16, r | a << 16), a = argmax
-    alignas(16) uint16_t win[kWinWords];      // consumer's word-stream window
+    uint32_t etab[kETop + 1];                    // e(t), t = 0 .. kETop
+    uint8_t ctx[32 * 4 * kNChan];                // token history [lane][row % 4][channel]
+    alignas(16) uint16_t cdf[kNS][32][kCS];      // cumulative table without the remainder
+    uint2 meta[kNS][32];                         // (cdf[a] | (f_a + r) << 16, r | a << 16), a = argmax
+    alignas(16) uint16_t win[kWinWords];         // consumer's word-stream window
     uint64_t row0[32];
     uint32_t nrows[32];
     float step[kNChan], offset[kNChan];
-    alignas(8) uint64_t a_full, a_empty, t_full[2], t_empty[2], c_full[kNS], c_empty[kNS], tok[kNQ];
+    alignas(8) uint64_t a_full[kNA], a_empty[kNA], t_full[2], t_empty[2], c_full[kNS], tok[kNQ];
+    uint32_t consumed;                           // steps the consumer has finished
     int32_t m1, sh1, m2, sh2, ahi1, ahi2;
     uint32_t ms, ss, dcap, mq;
+    int fast12, fast3;
     int bad;
     int abort_;
     uint32_t tmem;
 };
-static_assert(offsetof(LSmem3, at) % 1024 == 0 && offsetof(LSmem3, cdf) % 16 == 0 &&
-              offsetof(LSmem3, win) % 16 == 0 && offsetof(LSmem3, b3m) % 16 == 0, "alignment");
-static_assert(sizeof(LSmem3) + 256 <= 227 * 1024, "shared memory");
+static_assert(offsetof(LSmem4, at) % 1024 == 0 && offsetof(LSmem4, cdf) % 16 == 0 &&
+              offsetof(LSmem4, win) % 16 == 0 && offsetof(LSmem4, b3m) % 16 == 0 &&
+              offsetof(LSmem4, b3f) % 16 == 0, "alignment");
+static_assert(sizeof(LSmem4) + 256 <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -163,6 +178,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
 __device__ __forceinline__ void mbar_inval(uint64_t *bar) {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
 
 // Requantisation rq(a) = clamp((a m + 2^(sh-1)) >> sh, 0, 127) (m >= 0, 1 <= sh <= 47), on a
 // clamped to [0, ahi]: every a <= 0 gives 0, and ahi is the least a giving 127 or more, so the
@@ -194,6 +217,30 @@ __device__ __forceinline__ int32_t rq_ahi(int32_t m, int32_t sh) {
     const uint64_t a = (need + (uint64_t)m - 1) / (uint64_t)m;
     return a > 0x7FFFFFFFull ? 0x7FFFFFFF : (int32_t)a;
 }
+// The short form for sh <= 32 and m <= 2^sh, of an input x = a + base (base 0, or the fp32 bit
+// offset 0x4B400000 of an accumulator that carries it): clamping x to [base, base + ahi] makes
+// the result land in [0, 127] (at ahi it is 127 exactly: it rises by at most 1 per unit of a),
+// and (x - base) m + 2^(sh-1) = x m + (2^(sh-1) - base m) modulo 2^64.
+struct RqF {
+    uint64_t add;
+    uint32_t m, sh;
+    int32_t lo, hi;
+};
+__device__ __forceinline__ RqF make_rqf(int32_t m, int32_t sh, int32_t ahi, uint32_t base) {
+    RqF q;
+    q.m = (uint32_t)m;
+    q.sh = (uint32_t)sh;
+    q.add = (1ull << (sh - 1)) - (uint64_t)base * (uint64_t)(uint32_t)m;
+    q.lo = (int32_t)base;
+    const int64_t hi = (int64_t)base + ahi;
+    q.hi = hi > 0x7FFFFFFF ? 0x7FFFFFFF : (int32_t)hi;
+    return q;
+}
+__device__ __forceinline__ uint32_t rqf(int32_t x, const RqF &q) {
+    const uint32_t xc = (uint32_t)min(max(x, q.lo), q.hi);
+    const uint64_t P = (uint64_t)xc * q.m + q.add;
+    return __funnelshift_rc((uint32_t)P, (uint32_t)(P >> 32), q.sh);
+}
 
 // Two integers in [0, 127] as a bf16 pair, the first in the low half.
 __device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) {
@@ -201,7 +248,22 @@ __device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-__device__ bool load_model3(LSmem3 &S, const uint8_t *m, int *status) {
+// floor(65280 2^32 / E) for 2^23 <= E <= 2^31, from a float estimate and two integer
+// corrections: the estimate is within 7 of the quotient, the second one within 1.
+__device__ __forceinline__ uint32_t softmax_scale(uint32_t E) {
+    const uint64_t N = 65280ull << 32;
+    const float rf = __frcp_rn((float)E);
+    uint32_t q = (uint32_t)__fmul_rn(280375465082880.0f, rf);  // 65280 2^32 = 255 2^40, exact in fp32
+    int64_t rem = (int64_t)(N - (uint64_t)q * E);
+    const int32_t dq = (int32_t)floorf(__fmul_rn((float)rem, rf));
+    q += (uint32_t)dq;
+    rem -= (int64_t)dq * (int64_t)E;
+    if (rem < 0) q -= 1;
+    else if (rem >= (int64_t)E) q += 1;
+    return q;
+}
+
+__device__ bool load_model4(LSmem4 &S, const uint8_t *m, int *status) {
     const int tid = threadIdx.x;
     if (tid == 0) {
         const int32_t *h = reinterpret_cast<const int32_t *>(m);
@@ -218,21 +280,31 @@ __device__ bool load_model3(LSmem3 &S, const uint8_t *m, int *status) {
             S.mq = (S.ss >= 1 && S.ms < (1u << S.ss)) ? (S.ms << (32 - S.ss)) : 0u;
             S.ahi1 = rq_ahi(S.m1, S.sh1);
             S.ahi2 = rq_ahi(S.m2, S.sh2);
+            S.fast12 = S.sh1 <= 32 && S.sh2 <= 32 && (uint64_t)S.m1 <= (1ull << S.sh1) &&
+                       (uint64_t)S.m2 <= (1ull << S.sh2);
+            S.fast3 = 1;
         }
         S.abort_ = 0;
     }
     const int32_t *b1 = reinterpret_cast<const int32_t *>(m + kMB_B1);
     const int32_t *b2 = reinterpret_cast<const int32_t *>(m + kMB_B2);
     const int32_t *b3 = reinterpret_cast<const int32_t *>(m + kMB_B3);
-    bool badb = false;
-    for (int i = tid; i < kNChan * 64; i += kLT) badb |= (b1[i] >= (1 << 24) || b1[i] <= -(1 << 24));
+    bool badb = false, wide2 = false, wide3 = false;
+    for (int i = tid; i < kNChan * 64; i += kLT) {
+        S.b1[i] = b1[i];
+        badb |= (b1[i] >= (1 << 24) || b1[i] <= -(1 << 24));
+    }
     for (int i = tid; i < 64; i += kLT) {
         S.b2m[i] = b2[i] - (int32_t)kAccBias;
+        S.b2f[i] = __int_as_float((int32_t)kAccBias + b2[i]);  // 1.5 2^23 + b2 when |b2| < 2^22
         badb |= (b2[i] >= (1 << 24) || b2[i] <= -(1 << 24));
+        wide2 |= (b2[i] >= kFastBias || b2[i] <= -kFastBias);
     }
     for (int i = tid; i < 256; i += kLT) {
         S.b3m[i] = b3[i] - (int32_t)kAccBias;
+        S.b3f[i] = kAccBias + (uint32_t)b3[i];
         badb |= (b3[i] >= (1 << 24) || b3[i] <= -(1 << 24));
+        wide3 |= (b3[i] >= kFastBias || b3[i] <= -kFastBias);
         S.w1[i] = (int8_t)m[kMB_W1 + i];
     }
     for (int t = tid; t <= kETop; t += kLT) S.etab[t] = kExp2Q[t & 255] >> (t >> 8);
@@ -242,6 +314,8 @@ __device__ bool load_model3(LSmem3 &S, const uint8_t *m, int *status) {
     tc_fence_proxy();  // W3 is read by the tensor cores
     __syncthreads();
     if (badb) atomicOr(&S.bad, 1);
+    if (wide2) atomicAnd(&S.fast12, 0);
+    if (wide3) atomicAnd(&S.fast3, 0);
     __syncthreads();
     if (S.bad) {
         if (tid == 0) set_status(status, SGS_E_CORRUPT);
@@ -264,13 +338,15 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volati
 // mma.sync m16n8k16 with the contexts as M: lane 4 g + t holds contexts 16 mt + g (+ 8) and
 // layer-1 units 16 kt + 8 h + 2 t + e (its A fragments); layer 2's accumulators hold the same
 // contexts at out units 8 nt + 2 t + e.
-__device__ void l12_run(const LearnedParams &p, LSmem3 &S, uint32_t NT, volatile int *abort_) {
+template <bool kFast>
+__device__ void l12_run(const LearnedParams &p, LSmem4 &S, uint32_t NT, volatile int *abort_) {
     const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) - kWL12;
     const int g = lane >> 2, t4 = lane & 3;
     const Rq R1 = make_rq(S.m1, S.sh1, S.ahi1), R2 = make_rq(S.m2, S.sh2, S.ahi2);
+    const RqF F1 = make_rqf(S.m1, S.sh1, S.ahi1, 0u), F2 = make_rqf(S.m2, S.sh2, S.ahi2, kAccBias);
     const int32_t *w1w = reinterpret_cast<const int32_t *>(S.w1);
-    const int32_t *B1 = reinterpret_cast<const int32_t *>(p.bits + p.model_off + kMB_B1);
-    int32_t w1r[4][2][2], b2r[8][2];
+    int32_t w1r[4][2][2];
+    float b2c[8][2];  // kFast: the layer-2 accumulator input; else b2 - 0x4B400000 as bits
 #pragma unroll
     for (int kt = 0; kt < 4; ++kt)
 #pragma unroll
@@ -280,19 +356,15 @@ __device__ void l12_run(const LearnedParams &p, LSmem3 &S, uint32_t NT, volatile
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
-        for (int e = 0; e < 2; ++e) b2r[nt][e] = S.b2m[8 * nt + 2 * t4 + e];
+        for (int e = 0; e < 2; ++e)
+            b2c[nt][e] = kFast ? S.b2f[8 * nt + 2 * t4 + e] : __int_as_float(S.b2m[8 * nt + 2 * t4 + e]);
     for (uint32_t tau = 0; tau < NT; ++tau) {
         const uint32_t i = tau / kNQ, j = tau - i * kNQ;
         const int c = 4 * (int)j + w;
+        const int b = (int)(tau & 1);
         if (i >= 1 && !warp_wait(&S.tok[j], (i - 1) & 1, abort_, p)) break;
-        if (tau >= 1 && !warp_wait(&S.a_empty, (tau - 1) & 1, abort_, p)) break;
-        int32_t b1r[4][2][2];
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt)
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int e = 0; e < 2; ++e) b1r[kt][h][e] = __ldg(B1 + c * 64 + 16 * kt + 8 * h + 2 * t4 + e);
+        if (tau >= 2 && !warp_wait(&S.a_empty[b], ((tau >> 1) - 1) & 1, abort_, p)) break;
+        const int32_t *b1c = S.b1 + c * 64;
         // layer 1 into A fragments: afr[mt][kt][r + 2 h] = units 16 kt + 8 h + 2 t4 (+1) of
         // context 16 mt + 8 r + g
         uint32_t afr[2][4][4];
@@ -311,12 +383,16 @@ __device__ void l12_run(const LearnedParams &p, LSmem3 &S, uint32_t NT, volatile
                 for (int kt = 0; kt < 4; ++kt)
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const uint32_t v0 = rq32(__dp4a(w1r[kt][h][0], (int32_t)up, b1r[kt][h][0]), R1);
-                        const uint32_t v1 = rq32(__dp4a(w1r[kt][h][1], (int32_t)up, b1r[kt][h][1]), R1);
+                        const int o = 16 * kt + 8 * h + 2 * t4;
+                        const int32_t a0 = __dp4a(w1r[kt][h][0], (int32_t)up, b1c[o]);
+                        const int32_t a1 = __dp4a(w1r[kt][h][1], (int32_t)up, b1c[o + 1]);
+                        const uint32_t v0 = kFast ? rqf(a0, F1) : rq32(a0, R1);
+                        const uint32_t v1 = kFast ? rqf(a1, F1) : rq32(a1, R1);
                         afr[mt][kt][r + 2 * h] = pack2(v0, v1);
                     }
             }
         // layer 2, requantised into the operand tile
+        uint8_t *at = S.at[b];
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt) {
             uint32_t bfr[4][2];
@@ -328,36 +404,50 @@ __device__ void l12_run(const LearnedParams &p, LSmem3 &S, uint32_t NT, volatile
             }
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
-                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                float acc[4];
+                if (kFast) {
+                    // accumulated onto 1.5 2^23 + b2: every partial sum stays in [2^23, 2^24)
+                    const float c4[4] = {b2c[nt][0], b2c[nt][1], b2c[nt][0], b2c[nt][1]};
+                    mma_bf16_c(acc, c4, afr[mt][0][0], afr[mt][0][1], afr[mt][0][2], afr[mt][0][3], bfr[0][0], bfr[0][1]);
+                } else {
+                    acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
+                    mma_bf16(acc, afr[mt][0][0], afr[mt][0][1], afr[mt][0][2], afr[mt][0][3], bfr[0][0], bfr[0][1]);
+                }
 #pragma unroll
-                for (int kt = 0; kt < 4; ++kt)
+                for (int kt = 1; kt < 4; ++kt)
                     mma_bf16(acc, afr[mt][kt][0], afr[mt][kt][1], afr[mt][kt][2], afr[mt][kt][3], bfr[kt][0], bfr[kt][1]);
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
-                    // acc is an integer below 2^21 in magnitude: acc + 1.5 2^23 is exact and
-                    // its bit pattern is 0x4B400000 + acc
-                    const uint32_t v0 = rq32(__float_as_int(__fadd_rn(acc[2 * r], 12582912.0f)) + b2r[nt][0], R2);
-                    const uint32_t v1 = rq32(__float_as_int(__fadd_rn(acc[2 * r + 1], 12582912.0f)) + b2r[nt][1], R2);
+                    uint32_t v0, v1;
+                    if (kFast) {
+                        v0 = rqf(__float_as_int(acc[2 * r]), F2);
+                        v1 = rqf(__float_as_int(acc[2 * r + 1]), F2);
+                    } else {
+                        // acc is an integer below 2^21 in magnitude: acc + 1.5 2^23 is exact
+                        // and its bit pattern is 0x4B400000 + acc
+                        v0 = rq32(__float_as_int(__fadd_rn(acc[2 * r], 12582912.0f)) + __float_as_int(b2c[nt][0]), R2);
+                        v1 = rq32(__float_as_int(__fadd_rn(acc[2 * r + 1], 12582912.0f)) + __float_as_int(b2c[nt][1]), R2);
+                    }
                     const int l = 16 * mt + 8 * r + g;
-                    *reinterpret_cast<uint32_t *>(S.at + tc_off(32 * w + l, 8 * nt + 2 * t4)) = pack2(v0, v1);
+                    *reinterpret_cast<uint32_t *>(at + tc_off(32 * w + l, 8 * nt + 2 * t4)) = pack2(v0, v1);
                 }
             }
         }
         tc_fence_proxy();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&S.a_full);
+        if (lane == 0) mbar_arrive(&S.a_full[b]);
     }
 }
 
 // ---- layer 3 issue (one thread)
-__device__ void mma_run(const LearnedParams &p, LSmem3 &S, uint32_t NT, volatile int *abort_) {
+__device__ void mma_run(const LearnedParams &p, LSmem4 &S, uint32_t NT, volatile int *abort_) {
     const uint32_t idesc = tc_idesc_bf16(128, 256);
-    const uint32_t a0 = smem_addr(S.at), b0 = smem_addr(S.w3t);
+    const uint32_t b0 = smem_addr(S.w3t);
     uint32_t issued = 0;
     for (uint32_t tau = 0; tau < NT; ++tau) {
-        const int T = (int)(tau & 1);
+        const int T = (int)(tau & 1);  // team and operand buffer
         const uint32_t n = tau >> 1;
-        bool ok = mbar_wait(&S.a_full, tau & 1, abort_, p.wait_limit) &&
+        bool ok = mbar_wait(&S.a_full[T], n & 1, abort_, p.wait_limit) &&
                   mbar_wait(&S.t_empty[T], n & 1, abort_, p.wait_limit);
         if (!ok) {
             if (!*abort_) set_status(p.status, SGS_E_TIMEOUT);
@@ -365,20 +455,24 @@ __device__ void mma_run(const LearnedParams &p, LSmem3 &S, uint32_t NT, volatile
             break;
         }
         tc_fence_after();
+        const uint32_t a0 = smem_addr(S.at[T]);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
             tc_mma_bf16(S.tmem + 256u * T, tc_desc(a0 + 256u * kk), tc_desc(b0 + 256u * kk), idesc, 1u);
         tc_commit(&S.t_full[T]);
-        tc_commit(&S.a_empty);
+        tc_commit(&S.a_empty[T]);
         ++issued;
     }
     // the last commit's arrival (its tile's and every earlier tile's work complete) precedes
     // the CTA's next use of the barriers and the release of the tensor memory, also after an
     // abort: an issued MMA ends within microseconds, so this wait keeps the default limit
     // whatever limit the caller set for the hand-offs
-    if (issued && !mbar_wait(&S.a_empty, (issued - 1) & 1, nullptr, kWaitLimit)) {
-        set_status(p.status, SGS_E_TIMEOUT);
-        *abort_ = 1;
+    if (issued) {
+        const uint32_t last = issued - 1;
+        if (!mbar_wait(&S.a_empty[last & 1], (last >> 1) & 1, nullptr, kWaitLimit)) {
+            set_status(p.status, SGS_E_TIMEOUT);
+            *abort_ = 1;
+        }
     }
 }
 
@@ -394,47 +488,79 @@ __device__ __forceinline__ int32_t max32(const uint32_t (&v)[32]) {
     return m[0];
 }
 
-// The team's columns start at 1.5 2^23 for the next tile's layer 3; then the buffer is free.
-__device__ __forceinline__ void team_release(LSmem3 &S, uint32_t tb, int T) {
+// The team's columns are set up for the next tile's layer 3 (1.5 2^23, plus b3 in the short
+// form); then the buffer is free.
+template <bool kFast3>
+__device__ __forceinline__ void team_release(LSmem4 &S, uint32_t tb, int T) {
     uint32_t v[32];
+#pragma unroll 1
+    for (int ch = 0; ch < 8; ++ch) {
+        if (kFast3) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(S.b3f + 32 * ch);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = kAccBias;
+            for (int j4 = 0; j4 < 8; ++j4) {
+                const uint4 b = src[j4];
+                v[4 * j4] = b.x; v[4 * j4 + 1] = b.y; v[4 * j4 + 2] = b.z; v[4 * j4 + 3] = b.w;
+            }
+        } else {
 #pragma unroll
-    for (int ch = 0; ch < 8; ++ch) tc_st32(tb + 32 * ch, v);
+            for (int j = 0; j < 32; ++j) v[j] = kAccBias;
+        }
+        tc_st32(tb + 32 * ch, v);
+    }
     tc_wait_st();
     tc_fence_before();
     __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(&S.t_empty[T]);
 }
 
-template <bool kSmallScale>
-__device__ void team_run(const LearnedParams &p, LSmem3 &S, int T, uint32_t NT, volatile int *abort_) {
+// Bounded wait until the consumer has finished `need` steps.
+__device__ __forceinline__ bool wait_consumed(LSmem4 &S, uint32_t need, volatile int *abort_, const LearnedParams &p) {
+    bool ok = false;
+    for (uint32_t it = 0; it < p.wait_limit; ++it) {
+        if (ld_acquire(&S.consumed) >= need) { ok = true; break; }
+        if (*abort_) break;
+        if (it > 64) __nanosleep(64);
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok && (threadIdx.x & 31) == 0) {
+        if (!*abort_) set_status(p.status, SGS_E_TIMEOUT);
+        *abort_ = 1;
+    }
+    return ok;
+}
+
+template <bool kSmallScale, bool kFast3>
+__device__ void team_run(const LearnedParams &p, LSmem4 &S, int T, uint32_t NT, volatile int *abort_) {
     const int lane = threadIdx.x & 31, q = (threadIdx.x >> 5) & 3;
     const uint32_t tb = tc_taddr(S.tmem, q, 256u * T);
     const uint32_t dcap = S.dcap, mq = S.mq, ms = S.ms, ss = S.ss;
     const int4 *b3v = reinterpret_cast<const int4 *>(S.b3m);
-    team_release(S, tb, T);
+    team_release<kFast3>(S, tb, T);
     for (uint32_t tau = T; tau < NT; tau += 2) {
         if (!warp_wait(&S.t_full[T], (tau >> 1) & 1, abort_, p)) break;
         tc_fence_after();
         uint32_t v[32];
-        // pass 1: z = logit (bias added), written back; zmax
+        // pass 1: zmax (the general form adds the bias and writes the logits back)
         int32_t zmax = INT32_MIN;
 #pragma unroll 1
         for (int ch = 0; ch < 8; ++ch) {
             tc_ld32(tb + 32 * ch, v);
             tc_wait_ld();
+            if (!kFast3) {
 #pragma unroll
-            for (int j4 = 0; j4 < 8; ++j4) {
-                const int4 b = b3v[8 * ch + j4];
-                v[4 * j4] += b.x; v[4 * j4 + 1] += b.y; v[4 * j4 + 2] += b.z; v[4 * j4 + 3] += b.w;
+                for (int j4 = 0; j4 < 8; ++j4) {
+                    const int4 bb = b3v[8 * ch + j4];
+                    v[4 * j4] += bb.x; v[4 * j4 + 1] += bb.y; v[4 * j4 + 2] += bb.z; v[4 * j4 + 3] += bb.w;
+                }
+                tc_st32(tb + 32 * ch, v);
             }
             zmax = max(zmax, max32(v));
-            tc_st32(tb + 32 * ch, v);
         }
-        tc_wait_st();
+        if (!kFast3) tc_wait_st();
         // pass 2: e_k = etab[t(min(zmax - z_k, dcap))] (e vanishes from d = dcap on), their
-        // sum, and the lowest k with z_k = zmax (symbols visited in descending order)
+        // sum, and the lowest k with z_k = zmax (symbols visited in descending order).  The
+        // short form's logits carry a common offset, which no difference sees.
         const int64_t zl = (int64_t)zmax - (int64_t)dcap;
         const int32_t zlo = zl < (int64_t)INT32_MIN ? INT32_MIN : (int32_t)zl;
         uint32_t E = 0, am = 0;
@@ -456,11 +582,12 @@ __device__ void team_run(const LearnedParams &p, LSmem3 &S, int T, uint32_t NT, 
             tc_st32(tb + 32 * ch, v);
         }
         tc_wait_st();
-        const uint32_t R = (uint32_t)((65280ull << 32) / E);  // E >= e(0) = 2^23
-        // pass 3: cumulative table of f_k = 1 + floor(e_k R / 2^32), without the remainder
+        const uint32_t R = softmax_scale(E);  // E >= e(0) = 2^23
+        // pass 3: cumulative table of f_k = 1 + floor(e_k R / 2^32), without the remainder,
+        // into the slot of step k once the consumer has finished step k - kNS
         const uint32_t i = tau / kNQ, jq = tau - i * kNQ;
-        const uint32_t c = 4 * jq + q, k = i * kNChan + c, slot = c % kNS, u = k / kNS;
-        if (u >= 1 && !warp_wait(&S.c_empty[slot], (u - 1) & 1, abort_, p)) break;
+        const uint32_t c = 4 * jq + q, k = i * kNChan + c, slot = k % kNS;
+        if (k >= (uint32_t)kNS && !wait_consumed(S, k - kNS + 1, abort_, p)) break;
         uint16_t *row = &S.cdf[slot][lane][0];
         uint32_t run = 0;
 #pragma unroll 1
@@ -488,7 +615,7 @@ __device__ void team_run(const LearnedParams &p, LSmem3 &S, int T, uint32_t NT, 
         S.meta[slot][lane] = make_uint2(lo_a | ((nx - lo_a + r) << 16), r | (am << 16));
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.c_full[slot]);
-        team_release(S, tb, T);
+        team_release<kFast3>(S, tb, T);
     }
 }
 
@@ -511,36 +638,40 @@ __device__ __forceinline__ uint32_t table_sym(const uint16_t *row, uint2 mt, uin
     return s;
 }
 
-__device__ void consume3(const LearnedParams &p, LSmem3 &S, uint32_t grp, int nl, uint32_t K,
+__device__ void consume4(const LearnedParams &p, LSmem4 &S, uint32_t grp, int nl, uint32_t K,
                          uint32_t maxrows, volatile int *abort_) {
     const int lane = threadIdx.x & 31;
     GroupStream gs;
     uint32_t x = 0x10000u;
     group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, grp, nl, lane, gs, x, S.win);
+    const uint32_t my_rows = lane < nl ? S.nrows[lane] : 0u;
+    float *out_lane = p.out + (p.out_index ? 0 : S.row0[lane]);
+    const uint32_t *idx_lane = p.out_index ? p.out_index + S.row0[lane] : nullptr;
     bool aborted = false;
+    uint32_t i = 0, c = 0, slot = 0, u = 0;  // step k = i kNChan + c, slot = k % kNS, u = k / kNS
     for (uint32_t k = 0; k < K; ++k) {
-        const uint32_t i = k / kNChan, c = k - i * kNChan, slot = c % kNS;
-        if (!warp_wait(&S.c_full[slot], (k / kNS) & 1, abort_, p)) {
+        if (!warp_wait(&S.c_full[slot], u & 1, abort_, p)) {
             aborted = true;
             break;
         }
-        const bool live = lane < nl && i < S.nrows[lane];
+        const bool live = i < my_rows;
         if (live) {
             const uint32_t y = x & 0xFFFFu;
             uint32_t lo, hi;
             const uint32_t s = table_sym(S.cdf[slot][lane], S.meta[slot][lane], y, lo, hi);
             x = (hi - lo) * (x >> 16) + y - lo;
             S.ctx[(lane * 4 + (i & 3)) * kNChan + c] = (uint8_t)s;
-            const uint64_t row = S.row0[lane] + i;
-            const uint64_t col = p.out_index ? (uint64_t)p.out_index[row] : row;
-            p.out[(uint64_t)c * p.n_rows + col] = dequant(s, S.step[c], S.offset[c]);
+            const uint64_t col = idx_lane ? (uint64_t)idx_lane[i] : (uint64_t)i;
+            out_lane[(uint64_t)c * p.n_rows + col] = dequant(s, S.step[c], S.offset[c]);
         }
         group_refill(gs, x, live);
         __syncwarp();
         if (lane == 0) {
-            if (k + kNS < K) mbar_arrive(&S.c_empty[slot]);
+            st_release(&S.consumed, k + 1);
             if ((c & 3) == 3 && i + 1 < maxrows) mbar_arrive(&S.tok[c >> 2]);
         }
+        if (++c == (uint32_t)kNChan) { c = 0; ++i; }
+        if (++slot == (uint32_t)kNS) { slot = 0; ++u; }
     }
     if (!aborted) {
         const bool bad = gs.bad || (lane < nl && x != 0x10000u) || (gs.ptr != gs.n_words);
@@ -550,13 +681,13 @@ __device__ void consume3(const LearnedParams &p, LSmem3 &S, uint32_t grp, int nl
 
 // Tensor memory of the CTA: 512 columns (two teams x 256), allocated by warp 1.  One CTA fits
 // an SM (the shared memory above), so the allocation never waits for another CTA's.
-__device__ __forceinline__ void learned_tmem_alloc(LSmem3 &S) {
+__device__ __forceinline__ void learned_tmem_alloc(LSmem4 &S) {
     if ((threadIdx.x >> 5) == 1) tc_alloc(&S.tmem, 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
 }
-__device__ __forceinline__ void learned_tmem_free(LSmem3 &S) {
+__device__ __forceinline__ void learned_tmem_free(LSmem4 &S) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -568,11 +699,11 @@ __device__ __forceinline__ void learned_tmem_free(LSmem3 &S) {
 
 // One group of 32 lanes.  reload = false: the CTA's previous group was of the same scene,
 // whose model is still in shared memory (S.bad records whether it was refused).
-__device__ __forceinline__ void learned_body(const LearnedParams &p, LSmem3 &S, uint32_t grp, bool reload) {
+__device__ __forceinline__ void learned_body(const LearnedParams &p, LSmem4 &S, uint32_t grp, bool reload) {
     const int tid = threadIdx.x, warp = tid >> 5;
     const int nl = (int)min(32u, p.L - grp * 32);
     if (reload) {
-        if (!load_model3(S, p.bits + p.model_off, p.status)) return;
+        if (!load_model4(S, p.bits + p.model_off, p.status)) return;
     } else {
         if (S.bad) return;
         if (tid == 0) S.abort_ = 0;
@@ -592,17 +723,17 @@ __device__ __forceinline__ void learned_body(const LearnedParams &p, LSmem3 &S, 
         S.nrows[tid] = (uint32_t)(r1 - r0);
     }
     if (tid == 0) {
-        mbar_init(&S.a_full, 4);
-        mbar_init(&S.a_empty, 1);
+        for (int b = 0; b < kNA; ++b) {
+            mbar_init(&S.a_full[b], 4);
+            mbar_init(&S.a_empty[b], 1);
+        }
         for (int T = 0; T < 2; ++T) {
             mbar_init(&S.t_full[T], 1);
             mbar_init(&S.t_empty[T], 4);
         }
-        for (int b = 0; b < kNS; ++b) {
-            mbar_init(&S.c_full[b], 1);
-            mbar_init(&S.c_empty[b], 1);
-        }
+        for (int b = 0; b < kNS; ++b) mbar_init(&S.c_full[b], 1);
         for (int b = 0; b < kNQ; ++b) mbar_init(&S.tok[b], 1);
+        S.consumed = 0;
     }
     __syncthreads();
     uint32_t maxrows = 0;
@@ -610,31 +741,36 @@ __device__ __forceinline__ void learned_body(const LearnedParams &p, LSmem3 &S, 
     const uint32_t K = maxrows * kNChan, NT = maxrows * kNQ;
     volatile int *abort_ = &S.abort_;
     if (warp == 0) {
-        consume3(p, S, grp, nl, K, maxrows, abort_);
+        consume4(p, S, grp, nl, K, maxrows, abort_);
     } else if (warp == 1) {
         if ((tid & 31) == 0) mma_run(p, S, NT, abort_);
     } else if (warp < kWTeam) {
-        l12_run(p, S, NT, abort_);
+        if (S.fast12) l12_run<true>(p, S, NT, abort_);
+        else l12_run<false>(p, S, NT, abort_);
     } else {
         const int T = (warp - kWTeam) >> 2;
-        if (S.mq) team_run<true>(p, S, T, NT, abort_);
-        else team_run<false>(p, S, T, NT, abort_);
+        if (S.mq) {
+            if (S.fast3) team_run<true, true>(p, S, T, NT, abort_);
+            else team_run<true, false>(p, S, T, NT, abort_);
+        } else {
+            if (S.fast3) team_run<false, true>(p, S, T, NT, abort_);
+            else team_run<false, false>(p, S, T, NT, abort_);
+        }
     }
     // every hand-off is over: retire the barriers (a persistent CTA initialises them again)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (tid == 0) {
-        mbar_inval(&S.a_full);
-        mbar_inval(&S.a_empty);
+        for (int b = 0; b < kNA; ++b) {
+            mbar_inval(&S.a_full[b]);
+            mbar_inval(&S.a_empty[b]);
+        }
         for (int T = 0; T < 2; ++T) {
             mbar_inval(&S.t_full[T]);
             mbar_inval(&S.t_empty[T]);
         }
-        for (int b = 0; b < kNS; ++b) {
-            mbar_inval(&S.c_full[b]);
-            mbar_inval(&S.c_empty[b]);
-        }
+        for (int b = 0; b < kNS; ++b) mbar_inval(&S.c_full[b]);
         for (int b = 0; b < kNQ; ++b) mbar_inval(&S.tok[b]);
     }
     __syncthreads();
@@ -642,7 +778,7 @@ __device__ __forceinline__ void learned_body(const LearnedParams &p, LSmem3 &S, 
 
 __global__ void __launch_bounds__(kLT, 1) k_learned_decode(LearnedParams p) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    LSmem3 &S = *reinterpret_cast<LSmem3 *>(smem_raw);
+    LSmem4 &S = *reinterpret_cast<LSmem4 *>(smem_raw);
     learned_tmem_alloc(S);
     learned_body(p, S, blockIdx.x, true);
     learned_tmem_free(S);
@@ -650,7 +786,7 @@ __global__ void __launch_bounds__(kLT, 1) k_learned_decode(LearnedParams p) {
 
 __global__ void __launch_bounds__(kLT, 1) k_learned_multi(MultiArgs m) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    LSmem3 &S = *reinterpret_cast<LSmem3 *>(smem_raw);
+    LSmem4 &S = *reinterpret_cast<LSmem4 *>(smem_raw);
     learned_tmem_alloc(S);
     run_items<LearnedParams>(m, [&S](const LearnedParams &p, uint32_t vb, uint32_t, bool same) {
         learned_body(p, S, vb, !same);
@@ -683,7 +819,7 @@ static uint32_t make_learned(const uint8_t *bits, const sgs_scene_info &info, co
 
 static cudaError_t learned_smem_limit(const void *kernel, bool *done) {
     if (*done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LSmem3));
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LSmem4));
     if (e == cudaSuccess) *done = true;
     return e;
 }
@@ -697,7 +833,7 @@ cudaError_t launch_learned_decode(const uint8_t *bits, const sgs_scene_info &inf
     static bool set = false;
     cudaError_t e = learned_smem_limit(reinterpret_cast<const void *>(k_learned_decode), &set);
     if (e != cudaSuccess) return e;
-    k_learned_decode<<<grid, kLT, sizeof(LSmem3), st>>>(p);
+    k_learned_decode<<<grid, kLT, sizeof(LSmem4), st>>>(p);
     return cudaGetLastError();
 }
 
@@ -713,7 +849,7 @@ cudaError_t launch_learned_multi(const MultiArgs &m, cudaStream_t st) {
     static bool set = false;
     cudaError_t e = learned_smem_limit(reinterpret_cast<const void *>(k_learned_multi), &set);
     if (e != cudaSuccess) return e;
-    return launch_persistent(k_learned_multi, kLT, sizeof(LSmem3), m, st);
+    return launch_persistent(k_learned_multi, kLT, sizeof(LSmem4), m, st);
 }
 
 // ------------------------------------------------------------------ encoder side

@@ -53,6 +53,49 @@ def _random_model(seed):
                 ms=int(rng.integers(1, 1 << 24)), ss=int(rng.integers(0, 25)))
 
 
+def _shaped_model(seed, short12, short3, edge=False):
+    """A valid integer model on either side of the decoder's exact shortcuts: short12 keeps
+    sh1, sh2 <= 32, m <= 2^sh and |b2| < 2^21 (else one of them is broken), short3 keeps
+    |b3| < 2^21 (else one bias sits at 2^21); edge puts the values on the boundaries."""
+    rng = np.random.default_rng(100 + seed)
+    lim = (1 << 21) - 1
+    b2 = rng.integers(-20000, 20000, 64)
+    b3 = rng.integers(-(1 << 19), 1 << 19, 256)
+    sh1, sh2 = int(rng.integers(20, 31)), int(rng.integers(24, 32))
+    m1 = int((127 << sh1) // 30000)
+    m2 = int((127 << sh2) // 900000)
+    if edge:
+        sh2, m1 = 32, 1 << sh1
+        m2 = int((127 << sh2) // 900000)
+        b2[:2] = (lim, -lim)
+        b3[:2] = (lim, -lim)
+    if not short12:
+        if seed % 3 == 0:
+            b2[3] = 1 << 21
+        if seed % 3 == 1:
+            m1 = (1 << sh1) + 1
+        if seed % 3 == 2:
+            sh2, m2 = 33, int((127 << 33) // 900000)
+    if not short3:
+        b3[5] = 1 << 21
+    return dict(w1=rng.integers(-127, 128, (64, 4)), b1=rng.integers(-3000, 3000, (56, 64)),
+                w2=rng.integers(-127, 128, (64, 64)), b2=b2, w3=rng.integers(-127, 128, (256, 64)), b3=b3,
+                m1=m1, sh1=sh1, m2=m2, sh2=sh2, ms=int(rng.integers(200, 4000)), ss=16)
+
+
+@pytest.mark.parametrize("short12,short3,edge", [(True, True, False), (True, False, False), (False, True, False),
+                                                 (False, False, False), (True, True, True)])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_learned_decode_both_sides_of_the_shortcuts(ctx, toy, short12, short3, edge, seed):
+    """The decoder's exact shortcuts (bias folded into the accumulators, short requantisation)
+    and the general forms decode to the oracle's values bit for bit, at the limits too."""
+    sc, P, _ = toy
+    m = _shaped_model(seed, short12, short3, edge)
+    buf = S.encode(None, None, mode=S.MODE_LEARNED, depth=10, lanes=40, model=m, prep=P)
+    st, attr, pos, _, _ = gpu_decode(ctx, buf)
+    assert st == sgs.OK and same_bits(attr, P.attr) and same_bits(pos, P.pos)
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_learned_decode_random_integer_models(ctx, toy, seed):
     """Arbitrary valid integer models: extreme logits, saturated activations, near-certain
