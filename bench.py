@@ -49,6 +49,14 @@ WORKLOADS = {
                             "8-bit tokens, 28,125 lanes (W = 32 rows per lane, the paper's fast group size), "
                             "context MLP over 4 previous tokens + Fourier positional embedding of the decoded "
                             "voxel (12 bands, 75 -> 32), Laplace head"),
+    "learned_geo": dict(n=1_000_000, seed=1000, depth=16, mode=1, geo_mode=2, lanes=151552,
+                        desc="learned geometry decode: N=1,000,000 (900,000 kept), depth 16, every octree level "
+                             "of 4,096 or more nodes coded with the context MLP 4->64->64->256 conditioned on "
+                             "the level above (contexts 8 b + k), about 128 tokens per geometry lane; static "
+                             "channel-wise attributes at 151,552 lanes.  The geometry model is the architecture "
+                             "with random-init weights frozen on the scene's own occupancy samples (no trainer "
+                             "for explicit samples on the device): it times the decode, its bits are not a "
+                             "trained model's"),
     "small": dict(n=20_000, seed=0, depth=12, mode=1, geo_mode=1, lanes=32,
                   desc="small static scene decode: N=20,000 (18,000 kept), depth 12, 32 lanes"),
 }
@@ -59,6 +67,11 @@ WORKLOADS_DEFAULT = None  # the default workload's dict, set in main()
 # default workload, from an ncu --set full capture of the present kernel: 43.92 MB read +
 # 141.73 MB written (part of the 201.6 MB of output is still in L2 when the kernel ends).
 K_FIXED_TRAFFIC = 43_916_288 + 141_727_744
+# The same for one k_rans_attr launch of the static workload (151,552 lanes): 85.39 MB read +
+# 193.14 MB written; and one k_learned_decode launch of the learned workload (4,096 lanes):
+# 190.74 MB read + 297.41 MB written (the consumer's 4-byte stores, 32 lanes far apart).
+K_RANS_ATTR_TRAFFIC = {151552: 85_387_008 + 193_143_040}
+K_LEARNED_TRAFFIC = {4096: 190_743_040 + 297_414_144}
 
 
 from paper_2607_12656_b300.workloads import BATCH, SERVE  # noqa: E402
@@ -183,6 +196,10 @@ def make_bitstream(w: dict, ctx=None, sc=None):
         kw["lanes"] = w["lanes"]
     if w.get("geo_w"):  # geometry lanes for throughput: about geo_w coded tokens per lane
         kw["geo_lanes"] = geo_lanes_for(sc, w)
+    if w["geo_mode"] == 2:
+        from paper_2607_12656_b300.scenegen import kaiming_init
+        u, chan, _ = sgs.scene_geo_samples(sc.pos, sc.attr, w["depth"])
+        kw["geo_model"] = sgs.sgs_freeze_samples(sgs.pack_weights(kaiming_init(7)), u, chan, 1)
     model = None
     if w["mode"] in (2, 3):
         from paper_2607_12656_b300 import learned
@@ -206,7 +223,7 @@ def geo_lanes_for(sc, w) -> int:
 SMS = 148  # B300: 2 dies x 74 SMs
 
 
-def attr_roofline(mode: int, n: int, attr_bytes: int, attr_ms: float, pk: dict) -> dict:
+def attr_roofline(mode: int, n: int, attr_bytes: int, attr_ms: float, pk: dict, lanes: int = 0) -> dict:
     """Roofline of the attribute decoder of a coded mode over its stage time (CUDA events on the
     attribute stream).  Algorithmic work per decoded symbol (56 per Gaussian):
       static rANS: the coded attribute section read once + 4 B written (HBM);
@@ -227,7 +244,8 @@ def attr_roofline(mode: int, n: int, attr_bytes: int, attr_ms: float, pk: dict) 
         ach = alg / sec / 1e9
         return {"kernel": "k_rans_attr (static rANS + dequant + SoA store)", "bound": "hbm", "achieved": ach,
                 "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": src, "algorithmic_bytes": alg,
-                "traffic": None, "note": "issue-bound in practice: a dependent integer chain per symbol"}
+                "traffic": K_RANS_ATTR_TRAFFIC.get(lanes) if n == 900_000 else None,
+                "note": "issue-bound in practice: a dependent integer chain per symbol"}
     if mode == 2:
         mhz = pk.get("sm_max_mhz") or 2032.0
         peak = SMS * 4 * 32 * mhz * 1e6 / 1e9
@@ -237,7 +255,7 @@ def attr_roofline(mode: int, n: int, attr_bytes: int, attr_ms: float, pk: dict) 
         return {"kernel": "k_learned_decode (context MLP + integer softmax + rANS)", "bound": "alu",
                 "achieved": ach, "peak": peak, "unit": "Gop/s", "frac": ach / peak,
                 "peak_source": "derived: 148 SMs x 4 warp instructions x 32 lanes per clock at %.0f MHz" % mhz,
-                "algorithmic_ops": ops, "traffic": None,
+                "algorithmic_ops": ops, "traffic": K_LEARNED_TRAFFIC.get(lanes) if n == 900_000 else None,
                 "tensor": {"achieved": tf, "peak": bf16, "unit": "TFLOP/s", "frac": tf / bf16,
                            "peak_source": bf16_src}}
     flops = 2 * (4 * 64 + 64 * 64 + 2 * 64) * syms + 2 * 75 * 64 * n
@@ -418,7 +436,7 @@ def measure(args, w, ctx, sc=None, cpu: bool = True, headline: bool = False) -> 
                                    "unit": "GB/s"}
     else:
         line["config"]["attr_bits_per_gaussian"] = 8.0 * (info.total_len - info.off[7]) / n
-        rl = attr_roofline(w["mode"], n, info.total_len - info.off[7], line["stage_ms"]["attributes"], pk)
+        rl = attr_roofline(w["mode"], n, info.total_len - info.off[7], line["stage_ms"]["attributes"], pk, w.get("lanes", 0))
         line["roofline"] = rl
     if train is not None:
         line["training"] = {"steps": train["steps"], "batch": train["batch"], "device_ms": train["ms"],
@@ -473,7 +491,7 @@ def run_ours(args, w):
 # the same scene -- plus the small static scene of the plain method.  The fixed-length decode
 # is the headline (value); the others are sub-objects with the same measurements.
 DEFAULT_MODES = (("static", "static_4096"), ("static", "static"), ("learned", "learned"),
-                 ("learned_pe", "learned_pe"), ("small", "small"))
+                 ("learned_pe", "learned_pe"), ("learned_geo", "learned_geo"), ("small", "small"))
 
 
 def run_default(args):
@@ -505,7 +523,8 @@ def run_default(args):
                           "900,000 rows kept): fixed-length (the headline), channel-wise static rANS at "
                           "4,096 lanes and at 151,552 lanes, the learned context model at 4,096 lanes "
                           "(trained 2,000 x 65,536 tokens on the device), the position-aware model at "
-                          "28,125 lanes; 'small' is the 20,000-Gaussian plain-method scene (seed 0, "
+                          "28,125 lanes, and the learned geometry coder (static attributes); 'small' is "
+                          "the 20,000-Gaussian plain-method scene (seed 0, "
                           "depth 12, 32 lanes)")
     if rank == 0:
         print(json.dumps(_contract(head, args, world)), flush=True)
@@ -1068,6 +1087,7 @@ def main():
         w["desc"] += " [lanes=%d]" % args.lanes
     if args.train_steps is not None:
         w["train_steps"] = args.train_steps
+        w["desc"] = w["desc"].replace("trained 2,000 steps", "trained %s steps" % f"{args.train_steps:,}")
     if args.impl == "reference":
         run_reference(args, w)
     else:

@@ -249,13 +249,13 @@ struct GeoLDecParams {
     int *status;
 };
 
-// Symbol of `slot` in a table: the 16-entry block from the coarse row cdf[16 j], then the symbol
-// inside it; (lo, hi) = (cdf[s], cdf[s + 1]).  cdf is increasing, so the count of entries at or
-// below slot locates it, the largest of them is lo and the smallest above it hi.  Whatever the
-// table holds (one the model check left unwritten), every read stays inside it.
-__device__ __forceinline__ uint32_t geo_sym(const uint16_t *T, uint32_t slot, uint32_t &lo, uint32_t &hi) {
-    const uint4 *cq = reinterpret_cast<const uint4 *>(T + kNSym);
-    const uint4 c0 = cq[0], c1 = cq[1];
+// Symbol of `slot` in a table: the 16-entry block from the coarse row cdf[16 j] (c0, c1: loaded
+// one token ahead by the caller), then the symbol inside it; (lo, hi) = (cdf[s], cdf[s + 1]).
+// cdf is increasing, so the count of entries at or below slot locates it, the largest of them
+// is lo and the smallest above it hi.  Whatever the table holds (one the model check left
+// unwritten), every read stays inside it.
+__device__ __forceinline__ uint32_t geo_sym(const uint16_t *T, uint4 c0, uint4 c1, uint32_t slot, uint32_t &lo,
+                                            uint32_t &hi) {
     const uint32_t cw[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
     uint32_t jb = 0, nxt = 65536u;
 #pragma unroll
@@ -266,7 +266,7 @@ __device__ __forceinline__ uint32_t geo_sym(const uint16_t *T, uint32_t slot, ui
     }
     jb = jb ? jb - 1 : 0;  // cdf[0] = 0 <= slot in a valid table; any table stays in bounds
     const uint4 *fq = reinterpret_cast<const uint4 *>(T + 16 * jb);
-    const uint4 f0 = fq[0], f1 = fq[1];
+    const uint4 f0 = __ldg(fq), f1 = __ldg(fq + 1);
     const uint32_t fw[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
     uint32_t r = 0;
     lo = 0;
@@ -298,18 +298,32 @@ __global__ void __launch_bounds__(32 * kLDecWarps) k_geo_learned_decode(GeoLDecP
     uint32_t maxn = n;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) maxn = max(maxn, __shfl_xor_sync(0xffffffffu, maxn, o));
-    uint32_t c_next = n ? p.ctx[s0] : 0u;
+    // the table's coarse row goes on the critical path one token ahead, the context two ahead
+    auto coarse = [&](uint32_t c, uint4 &a, uint4 &b) {
+        const uint4 *cq = reinterpret_cast<const uint4 *>(p.tab + (size_t)(c & (kGCtx - 1)) * kGTabU16 + kNSym);
+        a = __ldg(cq);
+        b = __ldg(cq + 1);
+    };
+    uint32_t c_cur = n ? __ldg(p.ctx + s0) : 0u, c_nxt = n > 1 ? __ldg(p.ctx + s0 + 1) : 0u;
+    uint4 q0 = make_uint4(0u, 0u, 0u, 0u), q1 = q0;
+    if (n) coarse(c_cur, q0, q1);
     for (uint32_t t = 0; t < maxn; ++t) {
         const bool active = t < n;
         if (active) {
             const uint32_t i = s0 + t;
-            const uint16_t *T = p.tab + (size_t)(c_next & (kGCtx - 1)) * kGTabU16;
-            if (t + 1 < n) c_next = p.ctx[i + 1];  // the next token's context, ahead of time
+            const uint16_t *T = p.tab + (size_t)(c_cur & (kGCtx - 1)) * kGTabU16;
+            uint4 n0 = q0, n1 = q1;
+            if (t + 1 < n) coarse(c_nxt, n0, n1);
+            const uint32_t c_nn = t + 2 < n ? __ldg(p.ctx + i + 2) : 0u;
             const uint32_t slot = x & 0xFFFFu;
             uint32_t lo, hi;
-            const uint32_t s = geo_sym(T, slot, lo, hi);
+            const uint32_t s = geo_sym(T, q0, q1, slot, lo, hi);
             x = (hi - lo) * (x >> 16) + slot - lo;
             p.out[i] = (uint8_t)s;
+            q0 = n0;
+            q1 = n1;
+            c_cur = c_nxt;
+            c_nxt = c_nn;
         }
         group_refill(gs, x, active);
     }
