@@ -362,7 +362,11 @@ int sgs_render(sgs_ctx *ctx, const float *attr_dev, const float *pos_dev, uint32
  * the fast one); here lanes = ceil(N' / W).  sgs_autotune encodes the given scene at every
  * candidate W, decodes each bitstream on the context's device `reps` times (CUDA events,
  * median), and picks the smallest bitstream whose decode time is at most max_ms (the fastest
- * one if max_ms <= 0 or none qualifies). */
+ * one if max_ms <= 0 or none qualifies).  With shape candidates (n_shape > 0) each W is also
+ * decoded at every candidate launch shape of the attribute decoder (sgs_set_launch_shape)
+ * and keeps its fastest; the context's own shapes are restored before returning.  For
+ * SGS_MODE_FIXED (no lanes) n_cand must be 1 and rows_per_lane is ignored: only shapes are
+ * searched. */
 #define SGS_TUNE_MAX_CAND 16
 typedef struct {
     const float *pos, *attr;  /* host scene, as for scene_encode                           */
@@ -375,14 +379,26 @@ typedef struct {
     uint32_t rows_per_lane[SGS_TUNE_MAX_CAND];  /* candidate W values, >= 1              */
     float max_ms;             /* decode-time target, <= 0: fastest                         */
     uint32_t reps;            /* timed decodes per candidate (>= 1)                       */
+    uint32_t n_shape;         /* 0 .. SGS_TUNE_MAX_CAND launch shapes to try (0: built-in) */
+    uint32_t warps_per_cta[SGS_TUNE_MAX_CAND];  /* candidate shapes, as sgs_set_launch_shape */
 } sgs_tune_request;
 
 typedef struct {
     uint32_t best;            /* index of the chosen candidate                            */
     uint32_t lanes[SGS_TUNE_MAX_CAND];
     uint64_t bytes[SGS_TUNE_MAX_CAND];   /* bitstream size                                */
-    float ms[SGS_TUNE_MAX_CAND];         /* median decode time                            */
+    float ms[SGS_TUNE_MAX_CAND];         /* median decode time (at the candidate's best shape) */
+    uint32_t warps[SGS_TUNE_MAX_CAND];   /* the candidate's fastest shape (0: built-in)   */
+    uint32_t best_warps;                 /* warps[best]                                    */
 } sgs_tune_result;
+
+/* Launch shape of the attribute decoder in the context's single-scene decodes of `mode`
+ * (the autotuner's second knob besides W): SGS_MODE_FIXED, warps per CTA of the
+ * fixed-length unpack (1..8, each warp one channel x 1,024 rows); SGS_MODE_STATIC, the
+ * most groups of 32 lanes (warps) per CTA sharing one copy of the 56 tables (1..32; fewer
+ * when the scene has fewer groups than SMs x this).  0 restores the built-in shape (8; 32).
+ * Results do not depend on the shape.  Errors: SGS_E_INVALID (other mode, out of range).    */
+int sgs_set_launch_shape(sgs_ctx *ctx, uint32_t mode, uint32_t warps_per_cta);
 
 /* Allocates device memory for the trial bitstreams and outputs (freed before returning)
  * and may grow the context's scratch.  Synchronous.  Errors: SGS_E_INVALID (bad request),

@@ -120,6 +120,7 @@ extern "C" int sgs_create(sgs_ctx **out, int device, size_t scratch_bytes) {
     c->launches = 0;
     c->profile = 0;
     c->wait_limit = kDefaultWaitPolls;
+    for (int m = 0; m < 4; ++m) c->shape[m] = 0;
     c->n_marks = 0;
     for (int i = 0; i <= kMaxStages; ++i) cudaEventCreate(&c->marks[i]);
     for (int i = 0; i < 2; ++i) cudaEventCreate(&c->amarks[i]);
@@ -207,6 +208,14 @@ extern "C" uint64_t sgs_launch_count(sgs_ctx *c) { return c ? c->launches : 0; }
 extern "C" int sgs_set_wait_limit(sgs_ctx *c, uint32_t polls) {
     if (!c) return SGS_E_INVALID;
     c->wait_limit = polls ? polls : kDefaultWaitPolls;
+    return SGS_OK;
+}
+
+extern "C" int sgs_set_launch_shape(sgs_ctx *c, uint32_t mode, uint32_t warps) {
+    if (!c) return SGS_E_INVALID;
+    const uint32_t cap = mode == SGS_MODE_FIXED ? kFixWarpsMax : mode == SGS_MODE_STATIC ? kAttrWarpsMax : 0u;
+    if (cap == 0 || warps > cap) return SGS_E_INVALID;
+    c->shape[mode] = warps;
     return SGS_OK;
 }
 
@@ -380,8 +389,10 @@ static int decode_one(sgs_ctx *c, const uint8_t *bits, const sgs_scene_info &inf
         if (c->profile) cudaEventRecord(c->amarks[0], c->aux);
         if (info.n_rows) c->launches += 1;
         switch (info.mode) {
-            case SGS_MODE_FIXED: e = launch_fixed(bits, info, out, status, c->aux); break;
-            case SGS_MODE_STATIC: e = launch_rans_static_attr(bits, info, attr_tables, out, status, c->aux); break;
+            case SGS_MODE_FIXED: e = launch_fixed(bits, info, out, status, c->aux, c->shape[SGS_MODE_FIXED]); break;
+            case SGS_MODE_STATIC:
+                e = launch_rans_static_attr(bits, info, attr_tables, out, status, c->aux, c->shape[SGS_MODE_STATIC]);
+                break;
             default: e = launch_learned_decode(bits, info, out, s.learned, status, c->aux, c->wait_limit); break;
         }
         if (e != cudaSuccess) return SGS_E_CUDA;

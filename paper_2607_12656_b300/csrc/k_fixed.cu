@@ -16,11 +16,14 @@
 
 namespace sgs {
 
+static_assert(kFixWarps == (int)kFixWarpsMax, "the launch shape's cap is the staging array's size");
+
+// A CTA of blockDim.x / 32 warps (at most kFixWarps) takes that many consecutive items.
 template <bool VEC>
 __device__ __forceinline__ void fixed_body(const FixedParams &p, uint32_t vb) {
     __shared__ uint32_t s_words[kFixWarps][kFixStage];
     const int warp = threadIdx.x >> 5;
-    fixed_warp_item<VEC>(p, (uint64_t)vb * kFixWarps + warp, s_words[warp]);
+    fixed_warp_item<VEC>(p, (uint64_t)vb * (blockDim.x >> 5) + warp, s_words[warp]);
 }
 
 template <bool VEC>
@@ -54,13 +57,15 @@ uint32_t make_fixed(const uint8_t *bits, const sgs_scene_info &info, const sgs_s
 }
 
 cudaError_t launch_fixed(const uint8_t *bits, const sgs_scene_info &info,
-                         const sgs_scene_out &out, int *status, cudaStream_t st) {
+                         const sgs_scene_out &out, int *status, cudaStream_t st, uint32_t warps) {
     FixedParams p;
     bool vec;
-    const uint32_t grid = make_fixed(bits, info, out, status, &p, &vec);
-    if (grid == 0) return cudaSuccess;
-    if (vec) k_fixed<true><<<grid, 32 * kFixWarps, 0, st>>>(p);
-    else k_fixed<false><<<grid, 32 * kFixWarps, 0, st>>>(p);
+    if (make_fixed(bits, info, out, status, &p, &vec) == 0) return cudaSuccess;
+    const uint32_t w = (warps >= 1 && warps <= (uint32_t)kFixWarps) ? warps : (uint32_t)kFixWarps;
+    const uint64_t items = (uint64_t)p.n_items_per_chan * kNChan;
+    const uint32_t grid = (uint32_t)((items + w - 1) / w);
+    if (vec) k_fixed<true><<<grid, 32 * w, 0, st>>>(p);
+    else k_fixed<false><<<grid, 32 * w, 0, st>>>(p);
     return cudaGetLastError();
 }
 

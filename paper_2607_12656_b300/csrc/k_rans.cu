@@ -105,6 +105,7 @@ struct AttrParams {
 };
 
 constexpr int kAttrWarps = 32;  // one CTA per SM shares one copy of the 56 tables
+static_assert(kAttrWarps == (int)kAttrWarpsMax, "the launch shape's cap is the kernel's launch bound");
 static_assert(kNChan % 8 == 0, "channels are decoded 8 at a time");
 constexpr size_t kAttrCdfSmem = kNChan * kTabCdfWords * 4 + 2 * kNChan * 4;  // cdf, step, offset
 constexpr size_t kAttrTabSmem = kAttrCdfSmem + kNChan * kLutBuckets;
@@ -229,7 +230,7 @@ static cudaError_t allow_smem(K kernel, size_t bytes, bool *done) {
 
 cudaError_t launch_rans_static_attr(const uint8_t *bits, const sgs_scene_info &info,
                                     const uint8_t *tables, const sgs_scene_out &out, int *status,
-                                    cudaStream_t st) {
+                                    cudaStream_t st, uint32_t max_warps) {
     AttrParams p;
     const uint32_t groups = make_rans_attr(bits, info, tables, out, status, &p);
     if (groups == 0) return cudaSuccess;
@@ -237,7 +238,8 @@ cudaError_t launch_rans_static_attr(const uint8_t *bits, const sgs_scene_info &i
     cudaError_t e = allow_smem(k_rans_attr<false>, kAttrSmem, &set0);
     if (e == cudaSuccess) e = allow_smem(k_rans_attr<true>, kAttrSmem, &set1);
     if (e != cudaSuccess) return e;
-    const int w = attr_warps(groups);
+    int w = attr_warps(groups);
+    if (max_warps >= 1 && max_warps < (uint32_t)w) w = (int)max_warps;
     const uint32_t grid = (groups + w - 1) / w;
     if (p.out_index) k_rans_attr<true><<<grid, 32 * w, attr_smem(w), st>>>(p);
     else k_rans_attr<false><<<grid, 32 * w, attr_smem(w), st>>>(p);

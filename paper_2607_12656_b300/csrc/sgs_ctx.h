@@ -23,6 +23,7 @@ struct sgs_ctx {
     cudaStream_t geo;                   // geometry chain (highest priority)
     cudaEvent_t fork, join, gjoin;
     uint32_t wait_limit;                // polls of each bounded device wait (sgs_set_wait_limit)
+    uint32_t shape[4];                  // attribute decoder launch shape per coding mode (0: built-in)
     uint8_t *rws;                       // sgs_render workspace (grown on demand)
     size_t rws_bytes;
 };

@@ -79,9 +79,13 @@ __device__ __forceinline__ void set_status(int *status, int code) {
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_tables(const uint8_t *bits, const sgs_scene_info &info, int n_geo_tables,
                           uint8_t *tables, int *status, cudaStream_t st);
+// Launch shapes the attribute decoders accept (sgs_set_launch_shape): warps per CTA.
+constexpr uint32_t kAttrWarpsMax = 32;  // static rANS: groups sharing one copy of the tables
+constexpr uint32_t kFixWarpsMax = 8;    // fixed-length: (channel, 1,024-row) items per CTA
+// max_warps = 0: the built-in shape
 cudaError_t launch_rans_static_attr(const uint8_t *bits, const sgs_scene_info &info,
                                     const uint8_t *tables, const sgs_scene_out &out, int *status,
-                                    cudaStream_t st);
+                                    cudaStream_t st, uint32_t max_warps = 0);
 cudaError_t launch_rans_static_geo(const uint8_t *bits, const sgs_scene_info &info,
                                    const GeoPlan &plan, const uint8_t *tables, uint8_t *geo_bytes,
                                    int *status, cudaStream_t st);
@@ -99,7 +103,7 @@ uint64_t geo_learned_group_bytes(uint64_t n);
 cudaError_t launch_octree(const sgs_scene_info &info, const GeoPlan &plan, const uint8_t *bits,
                           const Scratch &s, const sgs_scene_out &out, int *status, cudaStream_t st);
 cudaError_t launch_fixed(const uint8_t *bits, const sgs_scene_info &info,
-                         const sgs_scene_out &out, int *status, cudaStream_t st);
+                         const sgs_scene_out &out, int *status, cudaStream_t st, uint32_t warps = 0);
 // Polls of a bounded device wait before it gives up (the default of sgs_set_wait_limit).
 constexpr uint32_t kDefaultWaitPolls = 1u << 24;
 cudaError_t launch_learned_decode(const uint8_t *bits, const sgs_scene_info &info,

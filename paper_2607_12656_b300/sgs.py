@@ -51,12 +51,13 @@ TUNE_MAX_CAND = 16
 class TuneRequest(ctypes.Structure):
     _fields_ = [("pos", P), ("attr", P), ("n", u32), ("mode", u32), ("depth", u32), ("geo_mode", u32),
                 ("model", P), ("n_cand", u32), ("rows_per_lane", u32 * TUNE_MAX_CAND), ("max_ms", ctypes.c_float),
-                ("reps", u32)]
+                ("reps", u32), ("n_shape", u32), ("warps_per_cta", u32 * TUNE_MAX_CAND)]
 
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("best", u32), ("lanes", u32 * TUNE_MAX_CAND), ("bytes", u64 * TUNE_MAX_CAND),
-                ("ms", ctypes.c_float * TUNE_MAX_CAND)]
+                ("ms", ctypes.c_float * TUNE_MAX_CAND),
+                ("warps", u32 * TUNE_MAX_CAND), ("best_warps", u32)]
 
 
 class BatchItem(ctypes.Structure):
@@ -123,6 +124,7 @@ def lib() -> ctypes.CDLL:
         L.sgs_launch_count.argtypes = [P]
         L.sgs_launch_count.restype = u64
         L.sgs_set_wait_limit.argtypes = [P, u32]
+        L.sgs_set_launch_shape.argtypes = [P, u32, u32]
         L.scene_decode_noalloc.argtypes = [P, ctypes.POINTER(SceneInfo), ctypes.POINTER(SceneOut), P]
         L.sgs_autotune.argtypes = [P, ctypes.POINTER(TuneRequest), ctypes.POINTER(TuneResult)]
         _lib = L
@@ -190,6 +192,11 @@ class Context:
 
     def launch_count(self) -> int:
         return int(lib().sgs_launch_count(self.handle))
+
+    def set_launch_shape(self, mode: int, warps_per_cta: int) -> None:
+        """Warps per CTA of the attribute decoder for this context's decodes of `mode`
+        (fixed-length 1..8, static 1..32; 0 = the built-in shape)."""
+        _check(lib().sgs_set_launch_shape(self.handle, mode, warps_per_cta), "sgs_set_launch_shape")
 
     def set_wait_limit(self, polls: int) -> None:
         """Poll budget of the learned decoders' bounded device waits (0 = the default)."""
@@ -556,9 +563,11 @@ def unpack_weights(flat: np.ndarray) -> dict:
 # ----------------------------------------------------------------------------- autotuning
 
 def autotune(ctx: Context, pos: np.ndarray, attr: np.ndarray, *, mode: int, depth: int, rows_per_lane,
-             max_ms: float = 0.0, reps: int = 5, geo_mode: int = GEO_RANS, model: bytes | None = None) -> dict:
+             max_ms: float = 0.0, reps: int = 5, geo_mode: int = GEO_RANS, model: bytes | None = None,
+             warps_per_cta=()) -> dict:
     """Encodes the scene at every candidate W (rows per lane), times each decode on the
-    context's device and returns {"best": index, "lanes": [...], "bytes": [...], "ms": [...]}."""
+    context's device (at every candidate launch shape, keeping the fastest) and returns
+    {"best": index, "lanes": [...], "bytes": [...], "ms": [...], "warps": [...], "best_warps": w}."""
     pos = np.ascontiguousarray(pos, np.float32)
     attr = np.ascontiguousarray(attr, np.float32)
     cands = list(rows_per_lane)
@@ -574,8 +583,14 @@ def autotune(ctx: Context, pos: np.ndarray, attr: np.ndarray, *, mode: int, dept
     for i, w in enumerate(cands):
         rq.rows_per_lane[i] = int(w)
     rq.max_ms, rq.reps = max_ms, reps
+    shapes = list(warps_per_cta)
+    assert len(shapes) <= TUNE_MAX_CAND
+    rq.n_shape = len(shapes)
+    for i, w in enumerate(shapes):
+        rq.warps_per_cta[i] = int(w)
     res = TuneResult()
     _check(lib().sgs_autotune(ctx.handle, ctypes.byref(rq), ctypes.byref(res)), "sgs_autotune")
     k = len(cands)
     return {"best": int(res.best), "rows_per_lane": cands, "lanes": list(res.lanes[:k]),
-            "bytes": [int(b) for b in res.bytes[:k]], "ms": list(res.ms[:k])}
+            "bytes": [int(b) for b in res.bytes[:k]], "ms": list(res.ms[:k]), "warps": list(res.warps[:k]),
+            "best_warps": int(res.best_warps)}

@@ -189,8 +189,47 @@ def test_autotune_sweeps_group_sizes(ctx, small_scene):
     t = LaneTuner()
     lanes = t.choose_lanes(ctx, sc.pos, sc.attr, mode=sgs.MODE_STATIC, depth=12, candidates=(16, 64), reps=2)
     assert lanes >= 1 and len(t.table) == 1
-    with pytest.raises(sgs.SgsError):
-        sgs.autotune(ctx, sc.pos, sc.attr, mode=sgs.MODE_FIXED, depth=12, rows_per_lane=[32])
+    with pytest.raises(sgs.SgsError):  # fixed-length scenes have no lanes: one candidate only
+        sgs.autotune(ctx, sc.pos, sc.attr, mode=sgs.MODE_FIXED, depth=12, rows_per_lane=[32, 64])
+
+
+@pytest.mark.parametrize("mode,shapes", [(S.MODE_FIXED, [1, 3, 8]), (S.MODE_STATIC, [1, 5, 32])])
+def test_launch_shapes_decode_bit_exact(ctx, mode, shapes):
+    """The attribute decoder's launch shape (warps per CTA, the autotuner's second knob) does
+    not change a bit of the result: fixed-length items and static groups land in other CTAs,
+    ragged last CTAs included."""
+    sc = make_scene(60_000, 91)
+    kw = dict(mode=mode, bits=fixed_bits(14), geo_mode=S.GEO_RAW) if mode == S.MODE_FIXED else \
+        dict(mode=mode, lanes=700, geo_mode=S.GEO_RANS)
+    try:
+        for w in shapes:
+            ctx.set_launch_shape(mode, w)
+            check(ctx, sc, 14, **dict(kw))
+    finally:
+        ctx.set_launch_shape(mode, 0)
+    for bad_mode, bad_w in ((mode, 9 if mode == S.MODE_FIXED else 33), (S.MODE_LEARNED, 4)):
+        with pytest.raises(sgs.SgsError):
+            ctx.set_launch_shape(bad_mode, bad_w)
+
+
+def test_autotune_chooses_launch_shapes(ctx, small_scene):
+    """Every W is decoded at every candidate shape and keeps its fastest; fixed-length scenes
+    tune the shape alone; the tuner sets its choice on the context, whose decodes stay exact."""
+    from paper_2607_12656_b300.tune import LaneTuner
+    sc = small_scene
+    r = sgs.autotune(ctx, sc.pos, sc.attr, mode=sgs.MODE_STATIC, depth=12, rows_per_lane=[16, 64], reps=2,
+                     warps_per_cta=[4, 32])
+    assert all(w in (4, 32) for w in r["warps"]) and r["best_warps"] == r["warps"][r["best"]]
+    f = sgs.autotune(ctx, sc.pos, sc.attr, mode=sgs.MODE_FIXED, depth=12, rows_per_lane=[1], reps=2,
+                     warps_per_cta=[2, 8], geo_mode=sgs.GEO_RAW)
+    assert f["lanes"] == [0] and f["best_warps"] in (2, 8)
+    try:
+        lanes, warps = LaneTuner().choose(ctx, sc.pos, sc.attr, mode=sgs.MODE_FIXED, depth=12, reps=2,
+                                          geo_mode=sgs.GEO_RAW)
+        assert lanes == 0 and warps in (2, 4, 8)
+        check(ctx, sc, 12, mode=S.MODE_FIXED, bits=fixed_bits(12), geo_mode=S.GEO_RAW)
+    finally:
+        ctx.set_launch_shape(sgs.MODE_FIXED, 0)
 
 
 @pytest.mark.parametrize("n,lanes", [(20_000, 40), (60_000, 2048), (30_000, 33), (5_000, 1)])
