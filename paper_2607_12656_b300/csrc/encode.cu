@@ -1,5 +1,5 @@
-// Scene encoder of the sgs library (host C++; the learned mode's per-token frequencies are
-// computed on the device).  Pipeline (Sec. 3.3-3.4):
+// Scene encoder of the sgs library (host C++; given a context, the scene's preparation --
+// prune, Morton sort, octree, quantization -- and the attribute coding run on the device).  Pipeline (Sec. 3.3-3.4):
 //   prune floor(n/10) Gaussians of lowest opacity (ties: lower index first) -> voxelize at
 //   depth D -> sort rows by (Morton code, original index) -> sparse-octree occupancy tokens
 //   per level, duplicate counts as metadata -> per-channel uniform quantization
@@ -20,25 +20,13 @@
 #include "exp2q_table.h"
 #include "sgs_ctx.h"
 #include "sgs_internal.h"
+#include "encode_prep.h"
 
 namespace sgs {
 namespace {
 
 constexpr uint32_t kM = 1u << 16;
 
-struct Prepared {
-    uint32_t depth = 0, n_in = 0;
-    std::vector<uint32_t> keep;          // row -> original index
-    std::vector<uint64_t> leaves;        // unique Morton codes
-    std::vector<uint32_t> dups;          // {rank, extra} pairs
-    std::vector<std::vector<uint8_t>> levels;
-    uint32_t bits[kNChan];
-    std::vector<uint8_t> q8;             // [rows][56] when every width <= 8
-    std::vector<uint16_t> q16;           // [rows][56]
-    std::vector<uint32_t> coord;         // [3][rows] voxel coordinates of the rows
-    float step[kNChan], offset[kNChan];
-    uint32_t rows() const { return (uint32_t)keep.size(); }
-};
 
 uint64_t morton3(uint32_t x, uint32_t y, uint32_t z, uint32_t D) {
     uint64_t m = 0;
@@ -498,8 +486,10 @@ extern "C" int scene_encode(sgs_ctx *ctx, const float *pos, const float *attr, u
     if (prm->mode == SGS_MODE_LEARNED_PE &&
         (!prm->model || !ctx || !pe_model_valid(static_cast<const uint8_t *>(prm->model))))
         return SGS_E_INVALID;
+    // with a context the scene is prepared on its device (k_prepare.cu), else on the host:
+    // the same rows, octree and quantized values either way
     Prepared P;
-    int r = prepare(pos, attr, n, prm->depth, bits, P);
+    int r = ctx ? prepare_device(ctx->device, pos, attr, n, prm->depth, bits, P) : prepare(pos, attr, n, prm->depth, bits, P);
     if (r) return r;
     const uint32_t D = prm->depth, R = P.rows();
     // geometry

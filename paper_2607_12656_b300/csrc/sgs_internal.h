@@ -79,6 +79,19 @@ __device__ __forceinline__ void set_status(int *status, int code) {
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_tables(const uint8_t *bits, const sgs_scene_info &info, int n_geo_tables,
                           uint8_t *tables, int *status, cudaStream_t st);
+// Device sort and scan (k_sort.cu).  scan_u32: out[i] = in[0] + .. + in[i-1] for i < n,
+// sums[] needs ceil(n / kScanBlock) + 1 words (sums[last] = the total).  radix_pass: one
+// stable 8-bit digit pass of an LSD radix sort of n (key, value) pairs on key bits
+// [shift, shift + 8); cnt and cnt_off need 256 ceil(n / kSortChunk) words each, csums the
+// scan's sums for that many items.
+constexpr int kScanBlock = 1024;
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 8;
+constexpr int kSortChunk = kSortThreads * kSortRounds;
+cudaError_t scan_u32(const uint32_t *in, uint64_t n, uint32_t *sums, uint32_t *out, cudaStream_t st);
+cudaError_t radix_pass(const uint32_t *keys, const uint32_t *vals, uint32_t n, int shift, uint32_t *cnt,
+                       uint32_t *cnt_off, uint32_t *csums, uint32_t *keys_out, uint32_t *vals_out, cudaStream_t st);
+
 // Launch shapes the attribute decoders accept (sgs_set_launch_shape): warps per CTA.
 constexpr uint32_t kAttrWarpsMax = 32;  // static rANS: groups sharing one copy of the tables
 constexpr uint32_t kFixWarpsMax = 8;    // fixed-length: (channel, 1,024-row) items per CTA
