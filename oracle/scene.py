@@ -124,10 +124,12 @@ def position(coord: np.ndarray, depth: int) -> np.ndarray:
 
 def quantize(v: np.ndarray, bits: int):
     """Per-channel uniform quantizer: offset = min, step = fl32((max - min) / (2^b - 1)),
-    q = clamp(rint((v - offset) / step), 0, 2^b - 1) in fp64 (ties to even); step 0 -> q 0."""
+    q = clamp(rint((v - offset) / step), 0, 2^b - 1) in fp64 (ties to even); step 0 -> q 0.
+    The minimum and maximum are the first values in row order that attain them, so a zero
+    extremum keeps the sign of its first occurrence (-0.0 and +0.0 compare equal)."""
     if v.size == 0:
         return np.zeros(0, np.uint32), np.float32(0), np.float32(0)
-    mn, mx = v.min(), v.max()
+    mn, mx = v[np.argmin(v)], v[np.argmax(v)]
     top = (1 << bits) - 1
     step = np.float32(0.0) if mx == mn else np.float32((np.float64(mx) - np.float64(mn)) / top)
     offset = np.float32(mn)

@@ -41,6 +41,23 @@ def test_quantize_constant_channel():
     assert step == 0 and np.all(q == 0) and np.all(S.dequantize(q, step, off) == v)
 
 
+@pytest.mark.parametrize("first", [0.0, -0.0])
+def test_quantize_zero_extremum_keeps_the_first_sign(first):
+    """-0.0 and +0.0 tie as the minimum (and as the maximum): the offset, whose bits the bitstream
+    stores, is the first one in row order.  Long vectors, so that a SIMD reduction order would
+    show."""
+    second = -first
+    lo = np.full(4099, 3.0, np.float32)
+    lo[[17, 700, 2048, 4098]] = [first, second, first, second]
+    q, step, off = S.quantize(lo, 8)
+    assert math.copysign(1.0, off) == math.copysign(1.0, first)
+    assert q[17] == 0 and q[0] == 255
+    hi = np.full(4099, -3.0, np.float32)
+    hi[[5, 3000]] = [first, second]
+    _, step, off = S.quantize(hi, 8)
+    assert off == np.float32(-3.0) and step == np.float32(3.0 / 255)
+
+
 def test_dequantize_two_roundings_not_fused():
     # q * step rounds to fp32 before the add: choose values where a fused form differs
     step, off = np.float32(0.1), np.float32(-0.30000001)
