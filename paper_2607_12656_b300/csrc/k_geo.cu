@@ -25,7 +25,6 @@ constexpr int kScanThreads = 256;
 constexpr int kWalkThreads = 256;
 constexpr int kWalkIlp = 8;                        // leaves a thread walks together
 constexpr uint32_t kWalkLeaves = kWalkThreads * kWalkIlp;  // leaves per CTA
-constexpr uint64_t kM21 = (1ull << 21) - 1;
 
 struct LeafOut {
     float *pos;
@@ -37,13 +36,19 @@ struct LeafOut {
     float scale, half;          // 2^-D, 2^-(D+1)
 };
 
-__device__ __forceinline__ uint64_t child_code(uint64_t pc, uint32_t k) {
-    return (pc << 1) | ((uint64_t)((k >> 2) & 1u) << 42) | ((uint64_t)((k >> 1) & 1u) << 21) |
-           (uint64_t)(k & 1u);
+// Every third bit of v, from bit 0 (the inverse of spreading a coordinate over a Morton code).
+__device__ __forceinline__ uint32_t compact3(uint64_t v) {
+    v &= 0x1249249249249249ull;
+    v = (v | (v >> 2)) & 0x10C30C30C30C30C3ull;
+    v = (v | (v >> 4)) & 0x100F00F00F00F00Full;
+    v = (v | (v >> 8)) & 0x001F0000FF0000FFull;
+    v = (v | (v >> 16)) & 0x001F00000000FFFFull;
+    v = (v | (v >> 32)) & 0x00000000001FFFFFull;
+    return (uint32_t)v;
 }
 
-// Writes the rows of leaf u (Morton rank) with packed coordinates pc.
-__device__ __forceinline__ void write_leaf(const LeafOut &o, uint32_t u, uint64_t pc, int *status) {
+// Writes the rows of leaf u (Morton rank) with Morton code mc (x the high bit of each triple).
+__device__ __forceinline__ void write_leaf(const LeafOut &o, uint32_t u, uint64_t mc, int *status) {
     uint32_t row = u, mult = 1;
     if (o.n_dup) {
         uint32_t lo = 0, hi = o.n_dup;  // first dup entry with rank >= u
@@ -55,8 +60,7 @@ __device__ __forceinline__ void write_leaf(const LeafOut &o, uint32_t u, uint64_
         if (lo < o.n_dup && o.dup[2 * lo] == u) mult += o.dup[2 * lo + 1];
     }
     if ((uint64_t)row + mult > o.n_rows) { set_status(status, SGS_E_CORRUPT); return; }
-    const uint32_t x = (uint32_t)(pc >> 42), y = (uint32_t)((pc >> 21) & kM21),
-                   z = (uint32_t)(pc & kM21);
+    const uint32_t x = compact3(mc >> 2), y = compact3(mc >> 1), z = compact3(mc);
     // voxel centre coord * 2^-D + 2^-(D+1): exact in fp32 (both operations are exact)
     const float px = __fadd_rn(__fmul_rn((float)x, o.scale), o.half);
     const float py = __fadd_rn(__fmul_rn((float)y, o.scale), o.half);
@@ -196,30 +200,34 @@ constexpr uint32_t kScatterNodes = kScanThreads * kScatterIlp;
 
 __device__ __forceinline__ void scatter_body(const ScanParams &sp, uint32_t vb) {
     const uint32_t total = sp.level_off[sp.depth + 1];
+    const uint32_t n = (uint32_t)sp.n;  // at most 2^29 internal nodes
+    const uint32_t x0 = vb * kScatterNodes + threadIdx.x;
+    const uint32_t *B32 = reinterpret_cast<const uint32_t *>(sp.B);
     uint32_t byte[kScatterIlp], y[kScatterIlp];
 #pragma unroll
     for (int q = 0; q < kScatterIlp; ++q) {
-        const uint32_t x = vb * kScatterNodes + q * kScanThreads + threadIdx.x;
+        const uint32_t x = x0 + q * kScanThreads, k = x >> 2, sh = 8u * (x & 3u);
         byte[q] = 0;
         y[q] = 0;
-        if (x < sp.n) {
-            node_at(sp.B, sp.n, sp.P4, x, byte[q], y[q]);
-            ++y[q];
+        if (x < n) {
+            // whole words load directly; only the stream's last word is assembled byte by byte
+            const uint32_t w = 4 * k + 4 <= n ? __ldg(B32 + k) : word_at(sp.B, n, k);
+            byte[q] = (w >> sh) & 0xFFu;
+            y[q] = 1u + __ldg(sp.P4 + k) + __popc(w & ((1u << sh) - 1u));
         }
     }
 #pragma unroll
     for (int q = 0; q < kScatterIlp; ++q) {
-        const uint32_t x = vb * kScatterNodes + q * kScanThreads + threadIdx.x;
+        const uint32_t x = x0 + q * kScanThreads;
         uint32_t b = byte[q], yy = y[q];
+        if (yy + __popc(b) > total) {
+            set_status(sp.status, SGS_E_CORRUPT);
+            continue;
+        }
+        const uint32_t xe = x << 3;
         while (b) {
-            const uint32_t kc = __ffs(b) - 1;
+            sp.par[yy++] = xe | (uint32_t)(__ffs(b) - 1);
             b &= b - 1;
-            if (yy >= total) {
-                set_status(sp.status, SGS_E_CORRUPT);
-                break;
-            }
-            sp.par[yy] = (x << 3) | kc;
-            ++yy;
         }
     }
 }
@@ -306,34 +314,34 @@ struct WalkParams {
 // bit s stays inside its 21-bit field).
 __device__ __forceinline__ void walk_body(const WalkParams &p, uint32_t vb) {
     if (p.check && vb == 0) check_levels(p.B, p.n_geo, p.P4, p.level_off, p.depth, p.status);
-    uint32_t y[kWalkIlp];
-    uint64_t code[kWalkIlp];  // packed x:21 | y:21 | z:21
+    uint32_t y[kWalkIlp], lo[kWalkIlp], hi[kWalkIlp];  // node; Morton code so far (top 3 st bits)
     bool on[kWalkIlp];
+    const uint32_t u0 = vb * kWalkLeaves + threadIdx.x;
 #pragma unroll
     for (int j = 0; j < kWalkIlp; ++j) {
-        const uint32_t u = vb * kWalkLeaves + j * kWalkThreads + threadIdx.x;
+        const uint32_t u = u0 + j * kWalkThreads;
         on[j] = u < p.n_leaves;
-        y[j] = p.leaf_lo + (on[j] ? u : 0u);
-        code[j] = 0;
+        y[j] = on[j] ? p.leaf_lo + u : 0u;
+        lo[j] = hi[j] = 0u;
     }
     bool bad = false;
     for (int st = 0; st < p.depth; ++st) {
         uint32_t e[kWalkIlp];
 #pragma unroll
-        for (int j = 0; j < kWalkIlp; ++j) e[j] = on[j] ? p.par[y[j]] : 0u;
+        for (int j = 0; j < kWalkIlp; ++j) e[j] = on[j] ? __ldg(p.par + y[j]) : 0u;
 #pragma unroll
         for (int j = 0; j < kWalkIlp; ++j) {
-            if (!on[j]) continue;
-            const uint32_t up = e[j] >> 3, k = e[j] & 7u;
-            if (up >= y[j]) {
-                bad = true;
-                on[j] = false;
-                continue;
-            }
-            code[j] |= (((uint64_t)((k >> 2) & 1u) << 42) | ((uint64_t)((k >> 1) & 1u) << 21) | (k & 1u)) << st;
+            const uint32_t up = e[j] >> 3;
+            const bool ok = up < y[j];
+            bad |= on[j] & !ok;
+            on[j] &= ok;
             y[j] = up;
+            // the 64-bit code shifts right by 3 and takes k = e & 7 into its top bits 61..63
+            lo[j] = __funnelshift_r(lo[j], hi[j], 3);
+            hi[j] = __funnelshift_r(hi[j], e[j], 3);
         }
     }
+    const uint32_t sh = 64u - 3u * (uint32_t)p.depth;
 #pragma unroll
     for (int j = 0; j < kWalkIlp; ++j) {
         if (!on[j]) continue;
@@ -341,7 +349,9 @@ __device__ __forceinline__ void walk_body(const WalkParams &p, uint32_t vb) {
             bad = true;
             continue;
         }
-        write_leaf(p.leaf, vb * kWalkLeaves + j * kWalkThreads + threadIdx.x, code[j], p.status);
+        // triple st of the code is the child index taken at step st: (x, y, z) bits st
+        const uint64_t code = (((uint64_t)hi[j] << 32) | lo[j]) >> sh;
+        write_leaf(p.leaf, u0 + j * kWalkThreads, code, p.status);
     }
     if (bad) set_status(p.status, SGS_E_CORRUPT);
 }

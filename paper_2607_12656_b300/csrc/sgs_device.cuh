@@ -20,6 +20,13 @@ __device__ __forceinline__ float dequant(uint32_t q, float step, float offset) {
     return __fadd_rn(__fmul_rn((float)q, step), offset);
 }
 
+// The same for q < 2^23 without an integer conversion: 2^23 + q is exact in fp32 (its bits
+// are 0x4B000000 | q), so subtracting 2^23 leaves (float)q exactly.
+__device__ __forceinline__ float dequant_small(uint32_t q, float step, float offset) {
+    const float qf = __fsub_rn(__uint_as_float(0x4B000000u | q), 8388608.0f);
+    return __fadd_rn(__fmul_rn(qf, step), offset);
+}
+
 __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -170,7 +177,7 @@ __device__ __forceinline__ void group_refill(GroupStream &gs, uint32_t &x, bool 
 constexpr int kFixWarps = 8;          // warps of a k_fixed CTA
 constexpr int kFixRows = 1024;        // rows per warp item
 constexpr int kFixMaxBits = 16;
-constexpr int kFixStage = 32 * kFixMaxBits + 1;  // staged words per warp
+constexpr int kFixStage = 32 * kFixMaxBits + 2;  // staged words per warp (an item's + 2)
 
 struct FixedParams {
     const uint8_t *bits;
@@ -182,6 +189,32 @@ struct FixedParams {
     int *status;
 };
 
+// A whole item of B-bit values, VEC layout: lane j's rows 128 k + 4 j .. + 3 start at bit
+// 128 B k + 4 B j, i.e. word 4 B k + (4 B j >> 5) at the lane's fixed shift (4 B j) & 31, so
+// two funnel shifts of three staged words give the 64-bit window holding all four values
+// (4 B <= 64) and every further offset is a constant.
+template <int B>
+__device__ __forceinline__ void fixed_full_vec(const uint32_t *sw, float *outc, float step, float offset,
+                                               uint32_t lane) {
+    constexpr uint32_t mask = (1u << B) - 1u;
+    const uint32_t bl = 4u * B * lane;
+    const uint32_t *q0 = sw + (bl >> 5);
+    const uint32_t s = bl & 31u;
+#pragma unroll
+    for (int k = 0; k < kFixRows / 128; ++k) {
+        const uint32_t *q = q0 + 4 * B * k;
+        const uint32_t t0 = __funnelshift_r(q[0], q[1], s), t1 = __funnelshift_r(q[1], q[2], s);
+        float v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int o = i * B;
+            const uint32_t x = o == 0 ? t0 : (o < 32 ? __funnelshift_r(t0, t1, o & 31) : t1 >> ((o - 32) & 31));
+            v[i] = dequant_small(x & mask, step, offset);
+        }
+        __stcs(reinterpret_cast<float4 *>(outc + 128 * k + 4 * lane), make_float4(v[0], v[1], v[2], v[3]));
+    }
+}
+
 // Warp item `item` (channel item / n_items_per_chan); sw = this warp's kFixStage staging
 // words in shared memory.  VEC: every channel's output base is 16-byte aligned and there is
 // no out_index, so lane j writes rows 4j..4j+3 (+128 k) with one 16-byte store; otherwise one
@@ -189,9 +222,9 @@ struct FixedParams {
 template <bool VEC>
 __device__ __forceinline__ void fixed_warp_item(const FixedParams &p, uint64_t item, uint32_t *sw) {
     const int lane = threadIdx.x & 31;
-    const uint32_t c = (uint32_t)(item / p.n_items_per_chan);
-    if (c >= (uint32_t)kNChan) return;
-    const uint32_t blk = (uint32_t)(item - (uint64_t)c * p.n_items_per_chan);
+    if (item >= (uint64_t)kNChan * p.n_items_per_chan) return;  // n_items_per_chan < 2^22
+    const uint32_t c = (uint32_t)item / p.n_items_per_chan;
+    const uint32_t blk = (uint32_t)item - c * p.n_items_per_chan;
     const uint32_t b = *reinterpret_cast<const uint32_t *>(p.bits + p.chan_off + 4 * (2 * kNChan + c));
     const float step = ld_f32(p.bits + p.chan_off + 4 * c);
     const float offset = ld_f32(p.bits + p.chan_off + 4 * (kNChan + c));
@@ -209,14 +242,23 @@ __device__ __forceinline__ void fixed_warp_item(const FixedParams &p, uint64_t i
     __syncwarp();  // the previous item's reads of sw are done
     // packed words and outputs are touched once: streaming (evict-first) accesses keep them
     // from displacing the octree's working set in L2 while the two halves run together
-    for (uint32_t i = lane; i <= nw; i += 32)
+    for (uint32_t i = lane; i < nw + 2; i += 32)
         sw[i] = (w0 + i < nwords_chan) ? __ldcs(w + w0 + i) : 0u;
     __syncwarp();
     const uint32_t mask = (1u << b) - 1u;  // b <= 16
     const uint32_t r0 = blk * kFixRows;
     const uint32_t rows = p.n_rows - r0 < (uint32_t)kFixRows ? p.n_rows - r0 : (uint32_t)kFixRows;
     float *outc = p.out + (size_t)c * p.n_rows + r0;
-    if (VEC) {
+    if (VEC && rows == (uint32_t)kFixRows) {
+        switch (b) {
+#define SGS_FIX_CASE(B) \
+    case B: fixed_full_vec<B>(sw, outc, step, offset, (uint32_t)lane); break;
+            SGS_FIX_CASE(1) SGS_FIX_CASE(2) SGS_FIX_CASE(3) SGS_FIX_CASE(4) SGS_FIX_CASE(5) SGS_FIX_CASE(6)
+            SGS_FIX_CASE(7) SGS_FIX_CASE(8) SGS_FIX_CASE(9) SGS_FIX_CASE(10) SGS_FIX_CASE(11) SGS_FIX_CASE(12)
+            SGS_FIX_CASE(13) SGS_FIX_CASE(14) SGS_FIX_CASE(15) SGS_FIX_CASE(16)
+#undef SGS_FIX_CASE
+        }
+    } else if (VEC) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const uint32_t rl = (uint32_t)k * 128 + 4 * lane;
