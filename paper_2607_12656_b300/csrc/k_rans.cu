@@ -114,64 +114,80 @@ constexpr size_t kAttrSmem = attr_smem(kAttrWarps);
 static_assert(kAttrCdfSmem % 16 == 0 && kAttrTabSmem % 16 == 0, "lookup and windows must be 16-byte aligned");
 static_assert(kAttrSmem <= 227 * 1024, "attribute decoder shared memory");
 
+// One symbol of a channel (tables tc / lut, dequantization so) for every lane of the group,
+// then the group's renormalisation.  PRED: some lanes hold no row at this step (`active`);
+// otherwise every lane decodes and no lane predicate is evaluated.
+template <bool PRED>
+__device__ __forceinline__ void attr_symbol(const uint32_t *tc, const uint8_t *lut, float2 so, float *dst, uint32_t &x,
+                                            GroupStream &gs, uint32_t &wrel, uint32_t lt, bool active) {
+    if (!PRED || active) __stcs(dst, dequant_small(rans_symbol(tc, lut, x), so.x, so.y));
+    group_renorm<false>(gs, x, wrel, lt, !PRED || active);
+}
+
 template <bool IDX>
 __device__ __forceinline__ void rans_attr_body(const AttrParams &p, uint32_t vb, bool reload) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *s_cdf = (uint32_t *)smem;                          // [56][257]
-    float *s_step = (float *)(smem + kNChan * kTabCdfWords * 4);  // [56]
-    float *s_off = s_step + kNChan;                               // [56]
+    float2 *s_so = (float2 *)(smem + kNChan * kTabCdfWords * 4);  // [56] (step, offset)
     uint8_t *s_lut = smem + kAttrCdfSmem;                         // [56][1024]
     uint16_t *s_win = reinterpret_cast<uint16_t *>(smem + kAttrTabSmem) + (threadIdx.x >> 5) * kWinWords;
     if (reload) {  // (a CTA's next item of the same scene finds the tables in place)
         load_cdf_smem(p.tables, kNChan, s_cdf, s_lut);
-        for (int c = threadIdx.x; c < kNChan; c += blockDim.x) {  // (a CTA may be a single warp)
-            s_step[c] = ld_f32(p.bits + p.chan_off + 4 * c);
-            s_off[c] = ld_f32(p.bits + p.chan_off + 4 * (kNChan + c));
-        }
+        for (int c = threadIdx.x; c < kNChan; c += blockDim.x)  // (a CTA may be a single warp)
+            s_so[c] = make_float2(ld_f32(p.bits + p.chan_off + 4 * c), ld_f32(p.bits + p.chan_off + 4 * (kNChan + c)));
         __syncthreads();
     }
-    const int lane = threadIdx.x & 31;
+    const uint32_t lane = threadIdx.x & 31;
     const uint32_t g = vb * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (g >= p.G) return;
     // the group's rows, dealt round robin to its lanes: lane j holds rows R0 + j + k nl
     const uint32_t nl = min(32u, p.L - g * 32);
     const uint32_t R0 = (uint32_t)((uint64_t)g * 32 * p.n_rows / p.L);
     const uint32_t R1 = (uint32_t)((uint64_t)(g * 32 + nl) * p.n_rows / p.L);
-    const uint32_t my_rows = ((uint32_t)lane < nl && R0 + lane < R1) ? (R1 - R0 - lane + nl - 1) / nl : 0;
-    const uint32_t n = my_rows * kNChan;
+    const uint32_t my_rows = (lane < nl && R0 + lane < R1) ? (R1 - R0 - lane + nl - 1) / nl : 0;
     GroupStream gs;
     uint32_t x;
-    group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, g, (int)nl, lane, gs, x, s_win);
-    uint32_t maxn = n;
+    group_open(p.bits, p.grp_sec, p.pay_off, p.pay_len, p.G, g, (int)nl, (int)lane, gs, x, s_win);
+    // rows [0, minr) every lane holds (none when the group has fewer than 32 lanes), then the
+    // rows only some lanes hold
+    uint32_t minr = lane < nl ? my_rows : 0u, maxr = my_rows;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) maxn = max(maxn, __shfl_xor_sync(0xffffffffu, maxn, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        minr = min(minr, __shfl_xor_sync(0xffffffffu, minr, o));
+        maxr = max(maxr, __shfl_xor_sync(0xffffffffu, maxr, o));
+    }
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t wrel = gs.ptr - gs.wbase;
+    const size_t nr = p.n_rows;
+    uint32_t row = R0 + lane, rr = 0;
     // row by row, the 56 channels of a row in order (the coding order); channels unrolled by
     // 8 so table and constant offsets are immediates
-    const uint32_t maxr = (maxn + kNChan - 1) / kNChan;
-    uint32_t row = R0 + lane;
-    for (uint32_t rr = 0; rr < maxr; ++rr, row += nl) {
+    for (; rr < minr; ++rr, row += nl) {
+        float *o = p.out + (IDX ? p.out_index[row] : row);
+        const uint32_t *cdf = s_cdf;
+        const uint8_t *lut = s_lut;
+        for (int c0 = 0; c0 < kNChan; c0 += 8, cdf += 8 * kTabCdfWords, lut += 8 * kLutBuckets, o += 8 * nr) {
+            window_ensure(gs, wrel, 8 * 32);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                attr_symbol<false>(cdf + k * kTabCdfWords, lut + k * kLutBuckets, s_so[c0 + k], o + k * nr, x, gs, wrel,
+                                   lt, true);
+        }
+    }
+    for (; rr < maxr; ++rr, row += nl) {
         const bool active = rr < my_rows;
         float *o = p.out + (IDX ? (active ? p.out_index[row] : 0u) : row);
         const uint32_t *cdf = s_cdf;
         const uint8_t *lut = s_lut;
-        for (int c0 = 0; c0 < kNChan; c0 += 8) {
+        for (int c0 = 0; c0 < kNChan; c0 += 8, cdf += 8 * kTabCdfWords, lut += 8 * kLutBuckets, o += 8 * nr) {
+            window_ensure(gs, wrel, 8 * 32);
 #pragma unroll
-            for (int c = c0; c < c0 + 8; ++c) {
-                if (active) {
-                    const uint32_t *tc = cdf + (c - c0) * kTabCdfWords;
-                    const uint32_t slot = x & 0xFFFFu;
-                    const uint32_t sym = lut_search(tc, lut + (c - c0) * kLutBuckets, slot);
-                    const uint32_t lo = tc[sym], hi = tc[sym + 1];
-                    x = (hi - lo) * (x >> 16) + slot - lo;
-                    o[(size_t)c * p.n_rows] = dequant(sym, s_step[c], s_off[c]);
-                }
-                group_refill(gs, x, active);
-            }
-            cdf += 8 * kTabCdfWords;
-            lut += 8 * kLutBuckets;
+            for (int k = 0; k < 8; ++k)
+                attr_symbol<true>(cdf + k * kTabCdfWords, lut + k * kLutBuckets, s_so[c0 + k], o + k * nr, x, gs, wrel,
+                                  lt, active);
         }
     }
-    const bool bad = gs.bad || (lane < (int)nl && x != 0x10000u) || (gs.ptr != gs.n_words);
+    const bool bad = gs.bad || (lane < nl && x != 0x10000u) || (gs.wbase + wrel != gs.n_words);
     if (bad) set_status(p.status, SGS_E_CORRUPT);
 }
 
@@ -294,6 +310,8 @@ __device__ __forceinline__ void rans_geo_body(const GeoParams &p, uint32_t vb) {
     uint32_t maxn = n;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) maxn = max(maxn, __shfl_xor_sync(0xffffffffu, maxn, o));
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t wrel = gs.ptr - gs.wbase;
     uint32_t i = I0 + lane;
     // coded level k of token i: its table, the token's offset into the level, and where the
     // next coded level starts
@@ -306,23 +324,21 @@ __device__ __forceinline__ void rans_geo_body(const GeoParams &p, uint32_t vb) {
     for (uint32_t t = 0; t < maxn; ++t) {
         const bool active = t < n;
         if (active) {
-            while (i >= next && k + 1 < nt) {
-                ++k;
-                cdf += kTabCdfWords;
-                lut += kLutBuckets;
-                next = s_start[k + 1];
-                dbase = s_dbase[k];
+            if (i >= next) {  // a lane crosses into the next coded level every few thousand tokens
+                while (i >= next && k + 1 < nt) {
+                    ++k;
+                    cdf += kTabCdfWords;
+                    lut += kLutBuckets;
+                    next = s_start[k + 1];
+                    dbase = s_dbase[k];
+                }
             }
-            const uint32_t slot = x & 0xFFFFu;
-            const uint32_t sym = lut_search(cdf, lut, slot);
-            const uint32_t lo = cdf[sym], hi = cdf[sym + 1];
-            x = (hi - lo) * (x >> 16) + slot - lo;
-            p.geo_bytes[dbase + i] = (uint8_t)sym;
+            p.geo_bytes[dbase + i] = (uint8_t)rans_symbol(cdf, lut, x);
             i += nl;
         }
-        group_refill(gs, x, active);
+        group_renorm(gs, x, wrel, lt, active);
     }
-    const bool bad = gs.bad || (lane < nl && x != 0x10000u) || (gs.ptr != gs.n_words);
+    const bool bad = gs.bad || (lane < nl && x != 0x10000u) || (gs.wbase + wrel != gs.n_words);
     if (bad) set_status(p.status, SGS_E_CORRUPT);
 }
 

@@ -171,6 +171,60 @@ __device__ __forceinline__ void group_refill(GroupStream &gs, uint32_t &x, bool 
     gs.ptr += __popc(mask);
 }
 
+// One static-table symbol from state x (tables: cdf[257] and the 1,024-bucket slot lookup):
+// the symbol s with cdf[s] <= slot < cdf[s + 1] lies between the symbols holding the bucket's
+// first slot (lut[b]) and the next bucket's first slot (lut[b + 1]).  One advance from lut[b] is
+// predicated; lanes that need more (a slot among many rare symbols crowded into one bucket)
+// binary-search the rest of that range, so a warp never walks a crowded bucket linearly.
+// Then the state update.
+__device__ __forceinline__ uint32_t rans_symbol(const uint32_t *cdf, const uint8_t *lut, uint32_t &x) {
+    const uint32_t slot = x & 0xFFFFu, b = slot >> kLutShift;
+    uint32_t s = lut[b];
+    uint32_t lo = cdf[s], hi = cdf[s + 1];
+    if (hi <= slot) {
+        lo = hi;
+        hi = cdf[++s + 1];
+    }
+    if (hi <= slot) {
+        // cdf[s + 1] <= slot: the answer is in [s + 1, e], e = the symbol holding the next
+        // bucket's first slot (255 for the last bucket; cdf[256] = 2^16 > slot)
+        uint32_t a = s + 1, e = b + 1 < (uint32_t)kLutBuckets ? lut[b + 1] : 255u;
+        while (a < e) {  // largest m in [a, e] with cdf[m] <= slot
+            const uint32_t m = (a + e + 1) >> 1;
+            if (cdf[m] <= slot) a = m; else e = m - 1;
+        }
+        s = a;
+        lo = cdf[s];
+        hi = cdf[s + 1];
+    }
+    x = (hi - lo) * (x >> 16) + slot - lo;
+    return s;
+}
+
+// group_refill with the window position kept relative (wrel = next word's index in the window)
+// and no per-word bound: words past the group's stream read as zero from the window (never
+// from memory past the payload), and the caller's final check wbase + wrel == n_words turns
+// any over-read into a corrupt-stream status.  lt = the lanes below this one.
+// Refills the window unless `room` more words can be read from it.
+__device__ __forceinline__ void window_ensure(GroupStream &gs, uint32_t &wrel, uint32_t room) {
+    if (wrel > kWinWords - room) {
+        const uint32_t ptr = gs.wbase + wrel;
+        window_fill(gs, ptr & ~7u);
+        wrel = ptr - gs.wbase;
+    }
+}
+
+// CHECK: the window is checked here (room for this step's 32 words); otherwise the caller
+// made room for several steps with window_ensure.
+template <bool CHECK = true>
+__device__ __forceinline__ void group_renorm(GroupStream &gs, uint32_t &x, uint32_t &wrel, uint32_t lt, bool can) {
+    const bool need = can && x < 0x10000u;
+    const uint32_t mask = __ballot_sync(0xffffffffu, need);
+    if (CHECK) window_ensure(gs, wrel, 32);
+    if (need) x = __byte_perm(x, gs.win[wrel + __popc(mask & lt)], 0x1054);  // x << 16 | word
+    wrel += __popc(mask);
+}
+
 // ------------------------------------------------------------------ fixed-length items
 
 // Channel-wise fixed-length decoding (Sec. 3.4.1): one warp item = one channel x 1,024 rows.
