@@ -65,6 +65,7 @@ struct PeSmem {
     float b3[2], s1, s2, smu, slr;
     int bad;
     uint32_t hist[kPeGroups][kNChan * 32];  // per channel and lane: s_{i-1} .. s_{i-4}, one byte each
+    uint32_t hist2[kPeGroups][kNChan * 32]; // the four tokens before those (s_{i-5} .. s_{i-8})
     uint32_t par[kPeGroups][kNChan * 32];   // per channel and lane: mu8 | n << 16
 };
 static_assert(offsetof(PeSmem, win) % 16 == 0 && sizeof(PeSmem::win[0]) % 16 == 0, "16-byte window stores");
@@ -301,6 +302,7 @@ struct PeParams {
     float *out;
     const uint32_t *out_index;
     int *status;
+    int vec;  // no out_index, 16-byte aligned channels (n_rows % 4 == 0): 8-row stores
 };
 
 // The two warps of a group's team synchronise on a named barrier of their own (ids 1..3;
@@ -317,7 +319,7 @@ __device__ __forceinline__ void team_sync(int slot) {
 // stream is read by one warp, in lane order).
 __device__ void pe_group(const PeParams &p, PeSmem &S, uint32_t grp, int slot, int member) {
     const int lane = threadIdx.x & 31;
-    uint32_t *hist = S.hist[slot], *par = S.par[slot];
+    uint32_t *hist = S.hist[slot], *hist2 = S.hist2[slot], *par = S.par[slot];
     const int nl = (int)min(32u, p.L - grp * 32);
     uint64_t r0 = 0, r1 = 0;
     if (lane < nl) {
@@ -325,6 +327,12 @@ __device__ void pe_group(const PeParams &p, PeSmem &S, uint32_t grp, int slot, i
         r0 = j * p.n_rows / p.L;
         r1 = (j + 1) * p.n_rows / p.L;
     }
+    // A lane's rows are contiguous, so at one row step the warp's stores are W rows apart: each
+    // 32-byte sector would fill over 8 steps and leave L2 partly written in between.  Rows in
+    // the aligned 8-row blocks inside [r0, r1) are therefore stored when a block's last row is
+    // decoded, 8 values (hist2, hist) of each channel as two 16-byte stores; the rows outside
+    // those blocks, and every row when the outputs are scattered or unaligned, one by one.
+    const uint32_t b0 = ((uint32_t)r0 + 7u) & ~7u, b1 = (uint32_t)r1 & ~7u;  // [b0, b1): rows of whole blocks
     const uint32_t nrows = (uint32_t)(r1 - r0);
     uint32_t maxrows = nrows;
 #pragma unroll
@@ -351,6 +359,7 @@ __device__ void pe_group(const PeParams &p, PeSmem &S, uint32_t grp, int slot, i
         pe_model_half(S, hist, par, v0, v1, v2, D, member);
         team_sync(slot);  // both halves of the row's (mean, rate) are in par
         if (member == 0) {
+            const bool defer = p.vec && live && (uint32_t)row >= b0 && (uint32_t)row < b1;
             for (int c = 0; c < kNChan; ++c) {
                 if (live) {
                     const uint32_t pr = par[c * 32 + lane];
@@ -370,10 +379,24 @@ __device__ void pe_group(const PeParams &p, PeSmem &S, uint32_t grp, int slot, i
                         else { hi = c1; }
                     }
                     x = (hi - lo) * (x >> 16) + slot_ - lo;
-                    hist[c * 32 + lane] = (hist[c * 32 + lane] << 8) | s;
-                    p.out[(uint64_t)c * p.n_rows + col] = dequant(s, S.step[c], S.offset[c]);
+                    const uint32_t h = hist[c * 32 + lane];
+                    hist[c * 32 + lane] = (h << 8) | s;
+                    hist2[c * 32 + lane] = (hist2[c * 32 + lane] << 8) | (h >> 24);
+                    if (!defer) p.out[(uint64_t)c * p.n_rows + col] = dequant(s, S.step[c], S.offset[c]);
                 }
                 group_refill(gs, x, live);
+            }
+            if (defer && (row & 7) == 7) {  // rows row - 7 .. row, oldest in hist2's top byte
+#pragma unroll 1
+                for (int c = 0; c < kNChan; ++c) {
+                    const uint32_t ha = hist2[c * 32 + lane], hb = hist[c * 32 + lane];
+                    const float st = S.step[c], of = S.offset[c];
+                    float4 *dst = reinterpret_cast<float4 *>(p.out + (uint64_t)c * p.n_rows + row - 7);
+                    dst[0] = make_float4(dequant(ha >> 24, st, of), dequant((ha >> 16) & 0xFFu, st, of),
+                                         dequant((ha >> 8) & 0xFFu, st, of), dequant(ha & 0xFFu, st, of));
+                    dst[1] = make_float4(dequant(hb >> 24, st, of), dequant((hb >> 16) & 0xFFu, st, of),
+                                         dequant((hb >> 8) & 0xFFu, st, of), dequant(hb & 0xFFu, st, of));
+                }
             }
         }
         team_sync(slot);  // the row's tokens are in hist before the next row's model
@@ -485,6 +508,7 @@ uint32_t make_pe(const uint8_t *bits, const sgs_scene_info &info, const sgs_scen
     p.out = out.attr;
     p.out_index = out.out_index;
     p.status = status;
+    p.vec = !out.out_index && info.n_rows % 4 == 0 && ((uintptr_t)out.attr & 15) == 0;
     return info.n_rows ? (p.G + kPeGroups - 1) / kPeGroups : 0;
 }
 
