@@ -107,7 +107,7 @@ struct AttrParams {
 constexpr int kAttrWarps = 32;  // one CTA per SM shares one copy of the 56 tables
 static_assert(kAttrWarps == (int)kAttrWarpsMax, "the launch shape's cap is the kernel's launch bound");
 static_assert(kNChan % 8 == 0, "channels are decoded 8 at a time");
-constexpr size_t kAttrCdfSmem = kNChan * kTabCdfWords * 4 + 2 * kNChan * 4;  // cdf, step, offset
+constexpr size_t kAttrCdfSmem = kNChan * kTabCdfBytes + 2 * kNChan * 4;  // cdf, step, offset
 constexpr size_t kAttrTabSmem = kAttrCdfSmem + kNChan * kLutBuckets;
 constexpr size_t attr_smem(int warps) { return kAttrTabSmem + (size_t)warps * kWinWords * 2; }
 constexpr size_t kAttrSmem = attr_smem(kAttrWarps);
@@ -127,8 +127,8 @@ __device__ __forceinline__ void attr_symbol(const uint32_t *tc, const uint8_t *l
 template <bool IDX>
 __device__ __forceinline__ void rans_attr_body(const AttrParams &p, uint32_t vb, bool reload) {
     extern __shared__ __align__(16) uint8_t smem[];
-    uint32_t *s_cdf = (uint32_t *)smem;                          // [56][257]
-    float2 *s_so = (float2 *)(smem + kNChan * kTabCdfWords * 4);  // [56] (step, offset)
+    uint32_t *s_cdf = (uint32_t *)smem;                          // [56][kTabCdfStride]
+    float2 *s_so = (float2 *)(smem + kNChan * kTabCdfBytes);  // [56] (step, offset)
     uint8_t *s_lut = smem + kAttrCdfSmem;                         // [56][1024]
     uint16_t *s_win = reinterpret_cast<uint16_t *>(smem + kAttrTabSmem) + (threadIdx.x >> 5) * kWinWords;
     if (reload) {  // (a CTA's next item of the same scene finds the tables in place)
@@ -166,11 +166,11 @@ __device__ __forceinline__ void rans_attr_body(const AttrParams &p, uint32_t vb,
         float *o = p.out + (IDX ? p.out_index[row] : row);
         const uint32_t *cdf = s_cdf;
         const uint8_t *lut = s_lut;
-        for (int c0 = 0; c0 < kNChan; c0 += 8, cdf += 8 * kTabCdfWords, lut += 8 * kLutBuckets, o += 8 * nr) {
+        for (int c0 = 0; c0 < kNChan; c0 += 8, cdf += 8 * kTabCdfStride, lut += 8 * kLutBuckets, o += 8 * nr) {
             window_ensure(gs, wrel, 8 * 32);
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-                attr_symbol<false>(cdf + k * kTabCdfWords, lut + k * kLutBuckets, s_so[c0 + k], o + k * nr, x, gs, wrel,
+                attr_symbol<false>(cdf + k * kTabCdfStride, lut + k * kLutBuckets, s_so[c0 + k], o + k * nr, x, gs, wrel,
                                    lt, true);
         }
     }
@@ -179,11 +179,11 @@ __device__ __forceinline__ void rans_attr_body(const AttrParams &p, uint32_t vb,
         float *o = p.out + (IDX ? (active ? p.out_index[row] : 0u) : row);
         const uint32_t *cdf = s_cdf;
         const uint8_t *lut = s_lut;
-        for (int c0 = 0; c0 < kNChan; c0 += 8, cdf += 8 * kTabCdfWords, lut += 8 * kLutBuckets, o += 8 * nr) {
+        for (int c0 = 0; c0 < kNChan; c0 += 8, cdf += 8 * kTabCdfStride, lut += 8 * kLutBuckets, o += 8 * nr) {
             window_ensure(gs, wrel, 8 * 32);
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-                attr_symbol<true>(cdf + k * kTabCdfWords, lut + k * kLutBuckets, s_so[c0 + k], o + k * nr, x, gs, wrel,
+                attr_symbol<true>(cdf + k * kTabCdfStride, lut + k * kLutBuckets, s_so[c0 + k], o + k * nr, x, gs, wrel,
                                   lt, active);
         }
     }
@@ -276,9 +276,9 @@ struct GeoParams {
 };
 
 constexpr int kGeoWarps = 8;
-// Shared memory of the geometry decoder for nt coded levels: cdf [nt][257], lookup
+// Shared memory of the geometry decoder for nt coded levels: cdf [nt][kTabCdfStride], lookup
 // [nt][1024], then one word-stream window per warp.
-__host__ __device__ constexpr size_t geo_cdf_smem(int nt) { return ((size_t)nt * kTabCdfWords * 4 + 15) & ~size_t(15); }
+__host__ __device__ constexpr size_t geo_cdf_smem(int nt) { return (size_t)nt * kTabCdfBytes; }
 __host__ __device__ constexpr size_t geo_tab_smem(int nt) { return geo_cdf_smem(nt) + (size_t)nt * kLutBuckets; }
 constexpr size_t kGeoTabSmem = geo_tab_smem(SGS_MAX_DEPTH);
 
@@ -317,7 +317,7 @@ __device__ __forceinline__ void rans_geo_body(const GeoParams &p, uint32_t vb) {
     // next coded level starts
     int k = 0;
     while (k + 1 < nt && s_start[k + 1] <= i) ++k;
-    const uint32_t *cdf = s_cdf + k * kTabCdfWords;
+    const uint32_t *cdf = s_cdf + k * kTabCdfStride;
     const uint8_t *lut = s_lut + k * kLutBuckets;
     uint32_t next = s_start[k + 1];
     uint32_t dbase = s_dbase[k];
@@ -327,7 +327,7 @@ __device__ __forceinline__ void rans_geo_body(const GeoParams &p, uint32_t vb) {
             if (i >= next) {  // a lane crosses into the next coded level every few thousand tokens
                 while (i >= next && k + 1 < nt) {
                     ++k;
-                    cdf += kTabCdfWords;
+                    cdf += kTabCdfStride;
                     lut += kLutBuckets;
                     next = s_start[k + 1];
                     dbase = s_dbase[k];

@@ -60,20 +60,21 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *to
     return wbase + incl - v;
 }
 
-// Copies the cdf[257] of n expanded tables into shared memory (s_cdf [n][257]), and, if
-// s_lut is not NULL, their slot lookups (s_lut [n][kLutBuckets], 16-byte aligned).
+// Copies n expanded tables into shared memory: each table's cdf[257] (padded to
+// kTabCdfStride words, s_cdf [n][kTabCdfStride]) and, if s_lut is not NULL, its slot lookup
+// (s_lut [n][kLutBuckets]); both 16-byte aligned.  A table is its padded cdf followed by its
+// lookup, so the copy is 16-byte units throughout, all of a thread's loads in flight together.
 __device__ __forceinline__ void load_cdf_smem(const uint8_t *tables, int n, uint32_t *s_cdf, uint8_t *s_lut = nullptr) {
-    for (int i = threadIdx.x; i < n * kTabCdfWords; i += blockDim.x) {
-        const int t = i / kTabCdfWords, k = i - t * kTabCdfWords;
-        s_cdf[i] = reinterpret_cast<const uint32_t *>(tables + (size_t)t * kTabBytes)[k];
-    }
-    if (s_lut) {
-        constexpr int kV = kLutBuckets / 16;  // uint4 per table
-        for (int i = threadIdx.x; i < n * kV; i += blockDim.x) {
-            const int t = i / kV, k = i - t * kV;
-            reinterpret_cast<uint4 *>(s_lut)[i] =
-                reinterpret_cast<const uint4 *>(tables + (size_t)t * kTabBytes + kTabCdfBytes)[k];
-        }
+    constexpr int kC = kTabCdfBytes / 16, kT = kTabBytes / 16;  // uint4 of a cdf row, of a table
+    static_assert(kTabBytes == kTabCdfBytes + kLutBuckets && kTabBytes % 16 == 0, "table layout");
+    const int per = s_lut ? kT : kC;
+    const uint4 *src = reinterpret_cast<const uint4 *>(tables);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < n * per; i += blockDim.x) {
+        const int t = i / per, k = i - t * per;
+        const uint4 v = src[t * kT + k];
+        if (k < kC) reinterpret_cast<uint4 *>(s_cdf)[t * kC + k] = v;
+        else reinterpret_cast<uint4 *>(s_lut)[t * (kLutBuckets / 16) + (k - kC)] = v;
     }
 }
 

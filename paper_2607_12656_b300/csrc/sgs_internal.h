@@ -39,6 +39,7 @@ enum Sec { S_LEVELS = 0, S_DUP, S_CHAN, S_GEO_RAW, S_GEO_TAB, S_GEO_GRP, S_GEO_P
 // lut[slot >> 6] or one of the symbols that start in the same 64-slot bucket after it.
 constexpr int kTabCdfWords = 257;
 constexpr int kTabCdfBytes = (kTabCdfWords * 4 + 15) & ~15;  // 1040
+constexpr int kTabCdfStride = kTabCdfBytes / 4;               // 260: a table's cdf row in shared memory
 constexpr int kLutShift = 6;
 constexpr int kLutBuckets = 65536 >> kLutShift;              // 1024
 constexpr int kTabBytes = kTabCdfBytes + kLutBuckets;         // 2064
