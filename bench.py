@@ -64,9 +64,9 @@ METRIC = "decoded Gaussians/s"
 WORKLOADS_DEFAULT = None  # the default workload's dict, set in main()
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_fixed launch on the
-# default workload, from an ncu capture of the present kernel: 43.96 MB read + 140.61 MB
-# written (part of the 201.6 MB of output is still in L2 when the kernel ends).
-K_FIXED_TRAFFIC = 43_964_416 + 140_614_144
+# default workload, from an ncu --set full capture of the present kernel: 43.95 MB read +
+# 142.94 MB written (part of the 201.6 MB of output is still in L2 when the kernel ends).
+K_FIXED_TRAFFIC = 43_947_776 + 142_937_344
 # The same for one k_rans_attr launch of the static workload (151,552 lanes): 85.73 MB read +
 # 192.72 MB written; and one k_learned_decode launch of the learned workload (4,096 lanes):
 # 190.74 MB read + 297.41 MB written (the consumer's 4-byte stores, 32 lanes far apart).

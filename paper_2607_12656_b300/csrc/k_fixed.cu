@@ -18,9 +18,6 @@ namespace sgs {
 
 static_assert(kFixWarps == (int)kFixWarpsMax, "the launch shape's cap is the staging array's size");
 
-// Resident CTAs of kFixWarps warps per SM the single-scene decoder asks for (0: no cap).
-constexpr uint32_t kFixCtasPerSm = 0;
-
 // A CTA of blockDim.x / 32 warps (at most kFixWarps) takes that many consecutive items.
 template <bool VEC>
 __device__ __forceinline__ void fixed_body(const FixedParams &p, uint32_t vb) {
@@ -29,12 +26,8 @@ __device__ __forceinline__ void fixed_body(const FixedParams &p, uint32_t vb) {
     fixed_warp_item<VEC>(p, (uint64_t)vb * (blockDim.x >> 5) + warp, s_words[warp]);
 }
 
-// Blocks vb = blockIdx.x + k gridDim.x < n_blocks: the grid is capped at kFixCtasPerSm per SM
-// so that the geometry stream's kernels, which run beside this one, find room on every SM.
 template <bool VEC>
-__global__ void __launch_bounds__(32 * kFixWarps) k_fixed(FixedParams p, uint32_t n_blocks) {
-    for (uint32_t vb = blockIdx.x; vb < n_blocks; vb += gridDim.x) fixed_body<VEC>(p, vb);
-}
+__global__ void __launch_bounds__(32 * kFixWarps) k_fixed(FixedParams p) { fixed_body<VEC>(p, blockIdx.x); }
 
 template <bool VEC>
 __global__ void __launch_bounds__(32 * kFixWarps) k_fixed_multi(MultiArgs m) {
@@ -70,17 +63,9 @@ cudaError_t launch_fixed(const uint8_t *bits, const sgs_scene_info &info,
     if (make_fixed(bits, info, out, status, &p, &vec) == 0) return cudaSuccess;
     const uint32_t w = (warps >= 1 && warps <= (uint32_t)kFixWarps) ? warps : (uint32_t)kFixWarps;
     const uint64_t items = (uint64_t)p.n_items_per_chan * kNChan;
-    const uint32_t n_blocks = (uint32_t)((items + w - 1) / w);
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            sms = 148;
-    }
-    const uint32_t cap = kFixCtasPerSm * (uint32_t)sms * kFixWarps / w;
-    const uint32_t grid = kFixCtasPerSm && n_blocks > cap ? cap : n_blocks;
-    if (vec) k_fixed<true><<<grid, 32 * w, 0, st>>>(p, n_blocks);
-    else k_fixed<false><<<grid, 32 * w, 0, st>>>(p, n_blocks);
+    const uint32_t grid = (uint32_t)((items + w - 1) / w);
+    if (vec) k_fixed<true><<<grid, 32 * w, 0, st>>>(p);
+    else k_fixed<false><<<grid, 32 * w, 0, st>>>(p);
     return cudaGetLastError();
 }
 
