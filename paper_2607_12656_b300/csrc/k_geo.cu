@@ -23,7 +23,7 @@ namespace sgs {
 
 constexpr int kScanThreads = 256;
 constexpr int kWalkThreads = 256;
-constexpr int kWalkIlp = 8;                        // leaves a thread walks together
+constexpr int kWalkIlp = 4;                        // leaves a thread walks together
 constexpr uint32_t kWalkLeaves = kWalkThreads * kWalkIlp;  // leaves per CTA
 
 struct LeafOut {
