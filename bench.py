@@ -834,7 +834,7 @@ def run_sweep(args):
                                                 seed=1)
         r = sgs.autotune(ctx, sc.pos, sc.attr, mode=mode, depth=16, rows_per_lane=ws, reps=5 if mode == 1 else 3,
                          model=model)
-        # whole scene_encode (prepare on the host, attribute coding on the device or host), W = 32
+        # whole scene_encode at W = 32, with a context (device preparation and coding) and without
         lanes = -(-900_000 // 32)
         for where, c in (("device", ctx), ("host", None)):
             if mode != 1 and c is None:
@@ -856,8 +856,10 @@ def run_sweep(args):
                                    "(sgs_autotune), L2 not flushed", "rows_per_lane": ws},
             "curves": curves,
             "encode": {"seconds": encode_s, "gaussians": 1_000_000, "threads": os.cpu_count(),
-                       "note": "whole scene_encode of the 1M scene at W = 32: prepare (prune, Morton sort, octree, "
-                               "quantize) on the host cores, attribute rANS coding on the device or on the host"}}
+                       "note": "whole scene_encode of the 1M scene at W = 32: with a context (device) the scene "
+                               "is prepared (prune, Morton sort, octree, quantize) and its attributes coded on "
+                               "the GPU, the geometry streams on the host; without one (host) everything runs "
+                               "on the host cores"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
