@@ -325,3 +325,32 @@ def test_corrupt_raw_geometry_detected(ctx, small_scene):
         else:
             assert st == sgs.OK and not same_bits(pos, P.pos)
     assert flagged >= 10
+
+
+def _crowded_scene(n, seed):
+    """Eight channels whose values sit mostly at two levels and otherwise on ~250 rare ones,
+    each seen a few times: their static tables pack many small-frequency symbols into single
+    64-slot buckets, so the decoder's bucket search must step past several symbol starts."""
+    sc = make_scene(n, seed)
+    attr = sc.attr.copy()
+    rng = np.random.default_rng(seed)
+    for c in range(8):
+        common = rng.choice(np.array([0.0, 1.0]), n)
+        rare = rng.integers(2, 255, n) / 255.0
+        v = np.where(rng.random(n) < 0.97, common, rare).astype(np.float32)
+        v[:2] = (0.0, 1.0)
+        attr[c] = v
+    return type("Scene", (), {"pos": sc.pos, "attr": attr})()
+
+
+@pytest.mark.parametrize("lanes", [33, 100, 1000])
+def test_static_crowded_buckets(ctx, lanes):
+    sc = _crowded_scene(20_000, 71 + lanes)
+    P = S.prepare(sc.pos, sc.attr, 12, 8)
+    crowded = 0
+    for c in range(8):
+        f = S.normalize_freq(np.bincount(P.q[:, c], minlength=256))
+        starts = np.cumsum(f)[:-1][f[1:] > 0]  # first slot of every present symbol after the first
+        crowded = max(crowded, int(np.bincount(starts >> 6, minlength=1024).max()))
+    assert crowded >= 3, "the scene must put several symbol starts into one bucket"
+    check(ctx, sc, 12, mode=S.MODE_STATIC, lanes=lanes, geo_mode=S.GEO_RANS)
