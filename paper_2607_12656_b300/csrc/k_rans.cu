@@ -321,18 +321,38 @@ __device__ __forceinline__ void rans_geo_body(const GeoParams &p, uint32_t vb) {
     const uint8_t *lut = s_lut + k * kLutBuckets;
     uint32_t next = s_start[k + 1];
     uint32_t dbase = s_dbase[k];
-    for (uint32_t t = 0; t < maxn; ++t) {
+    // a lane crosses into the next coded level every few thousand tokens
+    auto level_of = [&]() {
+        if (i >= next) {
+            while (i >= next && k + 1 < nt) {
+                ++k;
+                cdf += kTabCdfStride;
+                lut += kLutBuckets;
+                next = s_start[k + 1];
+                dbase = s_dbase[k];
+            }
+        }
+    };
+    // steps every lane of the group takes (none when the group has fewer than 32 lanes), eight
+    // at a time with one window check, then the steps only some lanes take
+    uint32_t minn = lane < nl ? n : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) minn = min(minn, __shfl_xor_sync(0xffffffffu, minn, o));
+    uint32_t t = 0;
+    for (; t + 8 <= minn; t += 8) {
+        window_ensure(gs, wrel, 8 * 32);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            level_of();
+            p.geo_bytes[dbase + i] = (uint8_t)rans_symbol(cdf, lut, x);
+            i += nl;
+            group_renorm<false>(gs, x, wrel, lt, true);
+        }
+    }
+    for (; t < maxn; ++t) {
         const bool active = t < n;
         if (active) {
-            if (i >= next) {  // a lane crosses into the next coded level every few thousand tokens
-                while (i >= next && k + 1 < nt) {
-                    ++k;
-                    cdf += kTabCdfStride;
-                    lut += kLutBuckets;
-                    next = s_start[k + 1];
-                    dbase = s_dbase[k];
-                }
-            }
+            level_of();
             p.geo_bytes[dbase + i] = (uint8_t)rans_symbol(cdf, lut, x);
             i += nl;
         }
