@@ -67,10 +67,10 @@ WORKLOADS_DEFAULT = None  # the default workload's dict, set in main()
 # default workload, from an ncu --set full capture of the present kernel: 43.95 MB read +
 # 142.94 MB written (part of the 201.6 MB of output is still in L2 when the kernel ends).
 K_FIXED_TRAFFIC = 43_947_776 + 142_937_344
-# The same for one k_rans_attr launch of the static workload (151,552 lanes): 85.73 MB read +
-# 192.72 MB written; and one k_learned_decode launch of the learned workload (4,096 lanes):
+# The same for one k_rans_attr launch of the static workload (151,552 lanes): 85.51 MB read +
+# 192.59 MB written; and one k_learned_decode launch of the learned workload (4,096 lanes):
 # 190.74 MB read + 297.41 MB written (the consumer's 4-byte stores, 32 lanes far apart).
-K_RANS_ATTR_TRAFFIC = {151552: 85_727_232 + 192_722_944}
+K_RANS_ATTR_TRAFFIC = {151552: 85_508_096 + 192_589_312}
 K_LEARNED_TRAFFIC = {4096: 190_743_040 + 297_414_144}
 
 
