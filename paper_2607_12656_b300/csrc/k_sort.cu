@@ -105,15 +105,20 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t *k
     const uint64_t base = (uint64_t)blockIdx.x * kSortChunk;
     uint32_t key[kSortRounds];
     uint32_t val[kSortRounds], dig[kSortRounds], lrank[kSortRounds];
+    // every round's items are loaded before the first barrier: all of a thread's loads in flight
 #pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
-        for (int w = 0; w < kSortThreads / 32; ++w) cnt[w][threadIdx.x] = 0;
-        __syncthreads();
         const uint64_t i = base + (uint64_t)r * kSortThreads + threadIdx.x;
         const bool live = i < n;
         key[r] = live ? keys[i] : 0u;
         val[r] = live ? vals[i] : 0u;
         dig[r] = live ? digit_of(key[r], shift) : 256u;  // no digit: matches no real one
+    }
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        for (int w = 0; w < kSortThreads / 32; ++w) cnt[w][threadIdx.x] = 0;
+        __syncthreads();
+        const bool live = dig[r] < 256u;
         const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
         const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
         if (live && rank == 0) cnt[warp][dig[r]] = __popc(peers);
