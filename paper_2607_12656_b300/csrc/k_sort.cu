@@ -80,10 +80,15 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_count(const uint32_t *key
     h[threadIdx.x] = 0;
     __syncthreads();
     const uint64_t base = (uint64_t)blockIdx.x * kSortChunk;
+    uint32_t d[kSortRounds];  // the keys are loaded before any count is added: all in flight
+#pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
         const uint64_t i = base + (uint64_t)r * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[digit_of(keys[i], shift)], 1u);
+        d[r] = i < n ? digit_of(keys[i], shift) : 256u;
     }
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r)
+        if (d[r] < 256u) atomicAdd(&h[d[r]], 1u);
     __syncthreads();
     counts[(size_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
