@@ -150,18 +150,47 @@ __global__ void k_rs_emit(uint32_t n, Pre P, const uint32_t *sidx, const uint32_
     const uint2 r = P.rect[i];
     const uint32_t x0 = r.x & 0xFFFFu, y0 = r.x >> 16, w = (r.y & 0xFFFFu) - x0;
     const uint32_t base = off[k];
+    // entry j covers tile (x0 + j % w, y0 + j / w): one division per lane, then steps of 32
+    uint32_t q = lane / w, rr = lane - q * w;
+    const uint32_t dq = 32u / w, dr = 32u - dq * w;
     for (uint32_t j = lane; j < cnt; j += 32) {
-        keys[base + j] = (y0 + j / w) * (uint32_t)tiles_x + x0 + j % w;
+        keys[base + j] = (y0 + q) * (uint32_t)tiles_x + x0 + rr;
         vals[base + j] = i;
+        q += dq;
+        rr += dr;
+        if (rr >= w) {
+            rr -= w;
+            ++q;
+        }
     }
 }
 
-__global__ void k_rs_ranges(const uint32_t *keys, uint32_t n, uint2 *ranges) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t t = keys[i];
-    if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
-    if (i + 1 == n || keys[i + 1] != t) ranges[t].y = i + 1;
+// Each warp takes kRngIlp x 32 consecutive entries (all loaded first), their neighbours by
+// shuffles, and only the entries just outside its run from memory.
+constexpr int kRngIlp = 8;
+constexpr uint32_t kRngEntries = 256 * kRngIlp;  // per CTA of 256 threads
+
+__global__ void __launch_bounds__(256) k_rs_ranges(const uint32_t *keys, uint32_t n, uint2 *ranges) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t wbase = (uint64_t)blockIdx.x * kRngEntries + (uint64_t)(threadIdx.x >> 5) * 32 * kRngIlp;
+    uint32_t t[kRngIlp];
+#pragma unroll
+    for (int r = 0; r < kRngIlp; ++r) {
+        const uint64_t i = wbase + 32 * r + lane;
+        t[r] = i < n ? keys[i] : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int r = 0; r < kRngIlp; ++r) {
+        const uint32_t up = __shfl_up_sync(0xffffffffu, t[r], 1), dn = __shfl_down_sync(0xffffffffu, t[r], 1);
+        const uint32_t before = __shfl_sync(0xffffffffu, r > 0 ? t[r > 0 ? r - 1 : 0] : 0u, 31);
+        const uint32_t after = __shfl_sync(0xffffffffu, r + 1 < kRngIlp ? t[r + 1 < kRngIlp ? r + 1 : r] : 0u, 0);
+        const uint64_t i = wbase + 32 * r + lane;
+        if (i >= n) continue;
+        const uint32_t prev = lane ? up : (r > 0 ? before : (i ? keys[i - 1] : 0u));
+        const uint32_t next = lane < 31 ? dn : (r + 1 < kRngIlp ? after : (i + 1 < n ? keys[i + 1] : 0u));
+        if (i == 0 || prev != t[r]) ranges[t[r]].x = (uint32_t)i;
+        if (i + 1 == n || next != t[r]) ranges[t[r]].y = (uint32_t)i + 1;
+    }
 }
 
 __global__ void __launch_bounds__(kTile * kTile) k_rs_render(const uint2 *ranges, const uint32_t *vals, Pre P, Cam c,
@@ -352,7 +381,7 @@ extern "C" int sgs_render(sgs_ctx *ctx, const float *attr, const float *pos, uin
         cur = radix(keys, vals, E, tile_bits, reinterpret_cast<uint32_t *>(b + o_c),
                     reinterpret_cast<uint32_t *>(b + o_co2), reinterpret_cast<uint32_t *>(b + o_cs2));
         if (cur < 0) return SGS_E_CUDA;
-        k_rs_ranges<<<(E + 255) / 256, 256, 0, st>>>(keys[cur], E, ranges);
+        k_rs_ranges<<<(uint32_t)((E + kRngEntries - 1) / kRngEntries), 256, 0, st>>>(keys[cur], E, ranges);
         ctx->launches += 2;
     }
     ctx->launches += 1;
