@@ -27,15 +27,6 @@ __device__ __forceinline__ float dequant_small(uint32_t q, float step, float off
     return __fadd_rn(__fmul_rn(qf, step), offset);
 }
 
-__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        uint64_t n = __shfl_xor_sync(0xffffffffu, v, o);
-        v = n > v ? n : v;
-    }
-    return v;
-}
-
 // Block-wide exclusive scan of one u32 per thread (blockDim.x == 256); *total = sum.
 __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *total,
                                                         uint32_t *sm /*[8]*/) {
@@ -76,16 +67,6 @@ __device__ __forceinline__ void load_cdf_smem(const uint8_t *tables, int n, uint
         if (k < kC) reinterpret_cast<uint4 *>(s_cdf)[t * kC + k] = v;
         else reinterpret_cast<uint4 *>(s_lut)[t * (kLutBuckets / 16) + (k - kC)] = v;
     }
-}
-
-// The symbol s with cdf[s] <= slot < cdf[s+1], starting from the bucket's first symbol: at
-// most the symbols that start inside slot's 64-slot bucket are stepped over (absent symbols,
-// whose cdf equals the next one's, included), so the loop ends below symbol 256 (cdf[256] =
-// 2^16 > slot).
-__device__ __forceinline__ uint32_t lut_search(const uint32_t *cdf, const uint8_t *lut, uint32_t slot) {
-    uint32_t s = lut[slot >> kLutShift];
-    while (cdf[s + 1] <= slot) ++s;
-    return s;
 }
 
 // The symbol s with cdf[s] <= slot < cdf[s+1] (cdf[0] = 0, cdf[256] = 2^16 > slot): the
