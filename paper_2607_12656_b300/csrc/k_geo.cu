@@ -481,8 +481,7 @@ static cudaError_t launch_after(bool pdl, void (*kernel)(P), uint32_t grid, uint
         kernel<<<grid, block, 0, st>>>(p);
         return cudaGetLastError();
     }
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
     cfg.stream = st;
