@@ -223,9 +223,11 @@ int scene_decode(sgs_ctx *ctx, const uint8_t *bits_dev, const sgs_scene_info *in
  * device copy of the whole bitstream, 16-byte aligned; info from scene_query; out:
  * caller-allocated device outputs), on the current CUDA device, on `stream`.
  *   - Synchronous: returns after the decode has completed on `stream`, with its status
- *     (SGS_OK, SGS_E_CORRUPT, SGS_E_TIMEOUT).
+ *     (SGS_OK, SGS_E_CORRUPT, SGS_E_TIMEOUT).  It reads the status back and synchronizes
+ *     the stream, so it must never be called while a stream is being captured into a CUDA
+ *     graph (scene_decode is the call to capture).
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress).
  *   - Every call on a device shares the one array and finds the previous call's contents
  *     (the call clears what must start at zero).  Calls that overlap on the GPU -- from two
  *     host threads, or on two streams -- race on the array and must not be made.
